@@ -1,0 +1,215 @@
+"""O1: the discrete PSWF-LR algorithm, plain PyTorch FP64 on the CPU.
+
+Follows Methods, "Accelerating atom-grid spreading with PSWFs":
+
+* window W(r) = prod_d W_pswf(r_d), W_pswf(a) = psi_0^{c_w}(a / omega) for
+  |a| <= omega, omega = P h / 2;  W-hat_pswf(k) = omega lambda_0
+  psi_0^{c_w}(omega k / c_w);
+* Eq. (EthetaLR): insert W-hat^-2 W-hat^2 into Eq. (Fourier);
+* step (i) spreading rho_grid = sum_j q_j [W(r - r_j)]_*, step (ii) forward
+  FFT, step (iii) diagonal scaling by W-hat^-2 Phi-hat_p / (2V), step (iv)
+  reduction over modes and channels;
+* then (not printed in the paper, but implied by forces from the energy) the
+  inverse transform and the gather of potentials and forces.
+
+With rho-hat(m) = sum_g rho_g exp(-i k_m . x_g) and Delta V = V / M the grid
+cell volume, Delta V rho-hat approximates sum_j q_j W-hat(k) exp(-i k . r_j),
+so the energy is
+
+    E_k = Delta V^2 / (2V) * sum_{m != 0} G(k_m) |rho-hat(m)|^2,
+    G(k) = Phi-hat_p(|k|) / W-hat(k)^2,
+
+the grid potential is Psi = (Delta V^2 / V) * IDFT[G rho-hat] (unnormalised
+inverse), and for each atom phi_i = sum_g Psi_g W(x_g - r_i) and
+F_i = q_i sum_g Psi_g (grad W)(x_g - r_i) = -dE/dr_i.
+
+Stencil (reading C5): with u = r / h, the P points of each dimension are
+i0 .. i0 + P - 1 with i0 = ceil(u - P/2), taken modulo M.  Reading C6: the
+DFT sign does not matter (G is even and rho is real); m = 0 is excluded.
+
+Nothing here is blocked, fused or reordered: atoms are spread by index_add_,
+the transform is torch.fft.fftn over the full (not half) spectrum.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .mollifiers import Mollifier, window_hat
+from .pswf import PSWF
+
+f64 = torch.float64
+
+
+@dataclass
+class GridConfig:
+    box: tuple            # (L_x, L_y, L_z) in Angstrom, orthorhombic
+    M: tuple              # grid points per dimension
+    P: int                # stencil width
+    c: float              # mollifier bandwidth
+    r_c: float            # mollifier cutoff
+    ps: tuple             # exponent p of each channel
+    c_w: float | None = None   # window bandwidth (defaults to c)
+
+
+class DiscretePSWF:
+    """O1 oracle for one periodic orthorhombic system."""
+
+    def __init__(self, cfg: GridConfig):
+        self.cfg = cfg
+        self.box = np.asarray(cfg.box, dtype=np.float64)
+        self.M = np.asarray(cfg.M, dtype=np.int64)
+        self.P = int(cfg.P)
+        self.V = float(np.prod(self.box))
+        self.h = self.box / self.M
+        self.dV = self.V / float(np.prod(self.M))
+        self.omega = self.P * self.h / 2.0
+        self.moll = Mollifier(cfg.c, cfg.r_c)
+        c_w = cfg.c if cfg.c_w is None else cfg.c_w
+        self.psi_w = self.moll.psi if c_w == cfg.c else PSWF(c_w)
+        self._G = {}
+
+    # ---- multiplier over the full spectrum --------------------------------
+    def multiplier(self, p: int) -> torch.Tensor:
+        """G(k_m) on the full M_x x M_y x M_z spectrum (zero at m = 0 and for
+        |k| >= k_c, where Phi-hat_p vanishes under reading C1)."""
+        if p in self._G:
+            return self._G[p]
+        ks = [2.0 * math.pi * np.fft.fftfreq(int(M), d=1.0 / int(M)) / L
+              for M, L in zip(self.M, self.box)]
+        kx, ky, kz = np.meshgrid(*ks, indexing="ij")
+        kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+        inside = (kk > 0) & (kk < self.moll.k_c)
+        G = np.zeros(kk.shape)
+        if np.any(inside):
+            uniq, inv = np.unique(kk[inside], return_inverse=True)
+            phi = self.moll.phi_hat(p, uniq)[inv]
+            what = (window_hat(self.psi_w, self.omega[0], kx[inside])
+                    * window_hat(self.psi_w, self.omega[1], ky[inside])
+                    * window_hat(self.psi_w, self.omega[2], kz[inside]))
+            G[inside] = phi / what ** 2
+        self._G[p] = torch.tensor(G, dtype=f64)
+        return self._G[p]
+
+    # ---- window ---------------------------------------------------------
+    def stencil(self, pos: torch.Tensor):
+        """Indices [N,3,P] (mod M), weights W_d and dW_d/d(alpha) [N,3,P],
+        where alpha = x_g - r along each dimension."""
+        h = torch.tensor(self.h, dtype=f64)
+        u = pos / h                                           # [N,3]
+        i0 = torch.ceil(u - self.P / 2.0)                      # [N,3]
+        j = torch.arange(self.P, dtype=f64)
+        idx = i0.unsqueeze(-1) + j                             # [N,3,P]
+        alpha = (idx - u.unsqueeze(-1)) * h.view(1, 3, 1)      # x_g - r
+        om = torch.tensor(self.omega, dtype=f64).view(1, 3, 1)
+        x = alpha / om
+        inside = (x.abs() <= 1.0).to(f64)
+        W = self.psi_w.torch(x) * inside
+        dW = self.psi_w.torch(x, 1) / om * inside
+        M = torch.tensor(self.M, dtype=torch.int64).view(1, 3, 1)
+        idx = torch.remainder(idx.to(torch.int64), M)
+        return idx, W, dW
+
+    def _flat(self, idx):
+        My, Mz = int(self.M[1]), int(self.M[2])
+        ix, iy, iz = idx[:, 0], idx[:, 1], idx[:, 2]          # [N,P] each
+        return (ix[:, :, None, None] * My + iy[:, None, :, None]) * Mz + iz[:, None, None, :]
+
+    # ---- step (i) ---------------------------------------------------------
+    def spread(self, pos: torch.Tensor, q: torch.Tensor, chunk: int = 131072) -> torch.Tensor:
+        """rho[K, Mx, My, Mz] = sum_j q_j W(x_g - r_j), periodised."""
+        K = q.shape[0]
+        Mtot = int(np.prod(self.M))
+        rho = torch.zeros(K, Mtot, dtype=f64)
+        for s in range(0, pos.shape[0], chunk):
+            idx, W, _ = self.stencil(pos[s:s + chunk])
+            flat = self._flat(idx).reshape(-1)
+            w3 = (W[:, 0, :, None, None] * W[:, 1, None, :, None] * W[:, 2, None, None, :])
+            for c in range(K):
+                vals = (q[c, s:s + chunk, None, None, None] * w3).reshape(-1)
+                rho[c] = rho[c].index_add(0, flat, vals)
+        return rho.reshape(K, *[int(m) for m in self.M])
+
+    # ---- steps (ii)-(iv) and the inverse transform ------------------------
+    def solve(self, rho: torch.Tensor):
+        """Returns (E_k per channel [K], Psi [K, Mx, My, Mz])."""
+        K = rho.shape[0]
+        Mtot = float(np.prod(self.M))
+        E = []
+        Psi = []
+        for c in range(K):
+            G = self.multiplier(self.cfg.ps[c])
+            rh = torch.fft.fftn(rho[c])
+            E.append(self.dV ** 2 / (2.0 * self.V) * torch.sum(G * (rh.real ** 2 + rh.imag ** 2)))
+            Psi.append((self.dV ** 2 / self.V) * torch.fft.ifftn(G * rh).real * Mtot)
+        return torch.stack(E), torch.stack(Psi)
+
+    # ---- gather -----------------------------------------------------------
+    def gather(self, Psi: torch.Tensor, pos: torch.Tensor, chunk: int = 131072):
+        """phi [K,N] = sum_g Psi_g W(x_g - r_i) and per-unit-charge force
+        f [K,N,3] = sum_g Psi_g (grad W)(x_g - r_i)."""
+        K = Psi.shape[0]
+        flatPsi = Psi.reshape(K, -1)
+        phis, fs = [], []
+        for s in range(0, pos.shape[0], chunk):
+            idx, W, dW = self.stencil(pos[s:s + chunk])
+            flat = self._flat(idx)
+            Wx, Wy, Wz = W[:, 0], W[:, 1], W[:, 2]
+            dx, dy, dz = dW[:, 0], dW[:, 1], dW[:, 2]
+            ph_c, f_c = [], []
+            for c in range(K):
+                g = flatPsi[c][flat]                           # [n,P,P,P]
+                ph_c.append(torch.einsum("nabc,na,nb,nc->n", g, Wx, Wy, Wz))
+                f_c.append(torch.stack([torch.einsum("nabc,na,nb,nc->n", g, dx, Wy, Wz),
+                                        torch.einsum("nabc,na,nb,nc->n", g, Wx, dy, Wz),
+                                        torch.einsum("nabc,na,nb,nc->n", g, Wx, Wy, dz)], -1))
+            phis.append(torch.stack(ph_c))
+            fs.append(torch.stack(f_c))
+        if not phis:
+            return torch.zeros(K, 0, dtype=f64), torch.zeros(K, 0, 3, dtype=f64)
+        return torch.cat(phis, 1), torch.cat(fs, 1)
+
+    # ---- the whole forward evaluation ---------------------------------------
+    def evaluate(self, pos, q):
+        """pos [N,3], q [K,N] (array-like or tensors).  Returns a dict with
+        E (total), E_ch [K] (E_k + E^0 per channel), E_k [K], E0 [K],
+        phi [K,N] (including d E^0 / d q_i), F [N,3], f [K,N,3], Psi."""
+        pos = torch.as_tensor(pos, dtype=f64)
+        q = torch.as_tensor(q, dtype=f64)
+        rho = self.spread(pos, q)
+        E_k, Psi = self.solve(rho)
+        phi, f = self.gather(Psi, pos)
+        Qnet = q.sum(dim=1)
+        a = torch.tensor([self.moll.zero_freq_coef(p, self.V) for p in self.cfg.ps], dtype=f64)
+        E0 = a * Qnet ** 2
+        phi = phi + (2.0 * a * Qnet).unsqueeze(1)
+        F = torch.einsum("kn,knd->nd", q, f)
+        return dict(E=float((E_k + E0).sum().detach()), E_ch=(E_k + E0).detach(), E_k=E_k.detach(), E0=E0.detach(),
+                    phi=phi.detach(), F=F.detach(), f=f.detach(), Psi=Psi.detach(), E_tensor=(E_k + E0).sum())
+
+    def self_energy(self, q) -> np.ndarray:
+        """E_self^(p) per channel (Implementation details)."""
+        q = np.asarray(q, dtype=np.float64)
+        return np.array([self.moll.self_coef(p) * float(np.sum(q[c] ** 2))
+                         for c, p in enumerate(self.cfg.ps)])
+
+    # ---- naive DFT (tiny grids only) ---------------------------------------
+    def naive_dft(self, rho: torch.Tensor) -> torch.Tensor:
+        """rho-hat(m) = sum_g rho_g exp(-2 pi i m.g / M), written out as an
+        explicit O(M^2) sum over grid points (cross-check of fftn usage)."""
+        Mx, My, Mz = [int(m) for m in self.M]
+        g = [torch.arange(m, dtype=f64) for m in (Mx, My, Mz)]
+        ex = torch.exp(-2j * math.pi * torch.outer(g[0], g[0]) / Mx)
+        ey = torch.exp(-2j * math.pi * torch.outer(g[1], g[1]) / My)
+        ez = torch.exp(-2j * math.pi * torch.outer(g[2], g[2]) / Mz)
+        out = torch.zeros(Mx, My, Mz, dtype=torch.complex128)
+        r = rho.to(torch.complex128)
+        for a in range(Mx):
+            for b in range(My):
+                for cc in range(Mz):
+                    phase = ex[a][:, None, None] * ey[b][None, :, None] * ez[cc][None, None, :]
+                    out[a, b, cc] = torch.sum(r * phase)
+        return out

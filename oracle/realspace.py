@@ -1,0 +1,67 @@
+"""PSWF real-space complement and the assembled PSWF-LR total (oracle).
+
+Methods, "Implementation details": pairing Eq. (Fourier) with the real-space
+term (1 - G_p(r)) / r^p and subtracting E_self^(p) gives the complete
+1/r^p lattice energy, which Ewald (O3) computes independently.  Under
+reading C3 (G_p = 1 for r >= r_c) the real-space term only involves pairs
+closer than r_c.  Forces and potentials come from torch autograd in FP64.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .mollifiers import Mollifier
+
+f64 = torch.float64
+
+
+def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
+    """E_real = 1/2 sum_{|r_ij + nL| < r_c}' q_i q_j (1 - G_p(r)) / r^p.
+    Returns dict(E, phi [N], F [N,3])."""
+    moll = moll or Mollifier(c, r_c)
+    box_t = torch.tensor(np.asarray(box, dtype=np.float64), dtype=f64)
+    pos_t = torch.tensor(np.asarray(pos, dtype=np.float64), dtype=f64, requires_grad=True)
+    q_t = torch.tensor(np.asarray(q, dtype=np.float64), dtype=f64, requires_grad=True)
+    nmax = [int(np.ceil(r_c / float(L))) + 1 for L in box]
+    shifts = torch.stack(torch.meshgrid(*[torch.arange(-m, m + 1, dtype=f64) for m in nmax],
+                                        indexing="ij"), -1).reshape(-1, 3) * box_t
+    N = pos_t.shape[0]
+    E = torch.zeros((), dtype=f64)
+    B = max(1, int(2e6 // max(1, N * shifts.shape[0])))
+    for i0 in range(0, N, B):
+        with torch.no_grad():
+            d0 = pos_t[i0:i0 + B, None, None, :] - pos_t[None, None, :, :] + shifts[None, :, None, :]
+            r2 = (d0 * d0).sum(-1)
+            mask = (r2 < r_c * r_c) & (r2 > 0)
+            ii, ss, jj = torch.nonzero(mask, as_tuple=True)
+        if ii.numel() == 0:
+            continue
+        d = pos_t[i0 + ii] - pos_t[jj] + shifts[ss]
+        r = torch.sqrt((d * d).sum(-1))
+        g = (1.0 - moll.G_torch(p, r)) / r ** p
+        E = E + 0.5 * torch.sum(q_t[i0 + ii] * q_t[jj] * g)
+    if not E.requires_grad:
+        return dict(E=0.0, phi=np.zeros(N), F=np.zeros((N, 3)))
+    gpos, gq = torch.autograd.grad(E, (pos_t, q_t), allow_unused=True)
+    gpos = torch.zeros_like(pos_t) if gpos is None else gpos
+    gq = torch.zeros_like(q_t) if gq is None else gq
+    return dict(E=float(E.detach()), phi=gq.numpy(), F=(-gpos).numpy())
+
+
+def pswf_total(recip: dict, pos, q, box, ps, c: float, r_c: float):
+    """Assemble E = E_k + E^0 + E_real - E_self per channel from a reciprocal
+    result (O1 or O2 dict with E_ch [K], phi [K,N], f [K,N,3]).
+    Returns dict(E, E_ch [K], phi [K,N], F [N,3], F_ch [K,N,3])."""
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    moll = Mollifier(c, r_c)
+    E_ch = np.array(recip["E_ch"], dtype=np.float64).copy()
+    phi = np.array(recip["phi"], dtype=np.float64).copy()
+    F_ch = np.einsum("kn,knd->knd", q, np.asarray(recip["f"], dtype=np.float64))
+    for ci, p in enumerate(ps):
+        rs = real_space(pos, q[ci], box, p, c, r_c, moll)
+        sc = moll.self_coef(p)
+        E_ch[ci] += rs["E"] - sc * float(np.sum(q[ci] ** 2))
+        phi[ci] += rs["phi"] - 2.0 * sc * q[ci]
+        F_ch[ci] += rs["F"]
+    return dict(E=float(E_ch.sum()), E_ch=E_ch, phi=phi, F=F_ch.sum(0), F_ch=F_ch)
