@@ -1,0 +1,167 @@
+/*
+ * pswf_lr.h -- C-ABI of the PSWF-LR reciprocal-space evaluation on B300.
+ *
+ * What is computed (paper: "Prolate spheroidal wave functions enable fast
+ * and exponent-aware long-range machine learning interatomic potentials"):
+ * for a periodic orthorhombic box of volume V, N atoms at r_i and K latent
+ * charge channels q_i^(c), each with its own exponent p_c in 1..6,
+ *
+ *   E_c = 1/(2V) sum_{k != 0} Phi-hat_{p_c}(k) |rho^(c)(k)|^2 + E^{0,(p_c)}
+ *                                                   (Eq. Fourier)
+ * evaluated by PSWF spreading on a uniform grid, a batched 3-D FFT, the
+ * mollified multiplier W-hat(k)^-2 Phi-hat_p(k) and the inverse FFT
+ * (Methods, "Accelerating atom-grid spreading with PSWFs", Eq. EthetaLR,
+ * steps (i)-(iv)), then the gather of per-atom potentials
+ * phi_i^(c) = dE/dq_i^(c) and forces F_i = -dE/dr_i.
+ * Phi-hat_p is Eq. (PhiH); E^{0,(p)} is the zero-frequency correction of
+ * "Implementation details" (Eq. Correction and the p > 3 formula); the
+ * self-energy E_self^(p) of the same section is returned separately.
+ * Hyperparameters follow "Parameter selection".
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (PSWF_OK) or a negative PSWF_E* status; nothing throws and no
+ *    entry point aborts the process.  pswf_strerror() names a status and
+ *    pswf_plan_last_error() gives the plan's last message.
+ *  - "device" pointers are CUDA global memory on the plan's device, owned by
+ *    the caller; "host" pointers are ordinary CPU memory owned by the caller.
+ *  - Work is enqueued on the plan's CUDA stream; only calls documented as
+ *    synchronising wait for it.
+ *  - Lengths are Angstrom; energies are in q^2 / Angstrom^p (Coulomb
+ *    constant 1).
+ *  - Real arrays on the device are float (precision 0, FP32 path) or double
+ *    (precision 1, FP64 path) as chosen at plan creation ("real" below).
+ */
+#ifndef PSWF_LR_H
+#define PSWF_LR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PSWF_OK 0
+#define PSWF_EINVAL (-1)           /* bad argument (p outside 1..6, box <= 0, n > n_max, ...) */
+#define PSWF_ENOMEM (-2)           /* device allocation failed or workspace too small */
+#define PSWF_ECUFFT (-3)           /* a cuFFT call failed */
+#define PSWF_ECUDA (-4)            /* a CUDA runtime call or kernel launch failed */
+#define PSWF_ETIMEOUT (-5)         /* a bounded device wait ran out */
+#define PSWF_ENONFINITE (-6)       /* NaN or Inf in the positions */
+#define PSWF_ETOLUNREACHABLE (-7)  /* grid too coarse for the mollifier band (h k_c >= pi) */
+#define PSWF_ESTATE (-8)           /* call out of order (e.g. execute before set_points) */
+
+/* ---- options ----------------------------------------------------------- */
+#define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */
+
+typedef struct {
+  double tol;      /* target LR tolerance eps_tot (default 1e-5) */
+  double r_c;      /* mollifier cutoff r_c in Angstrom (required, > 0) */
+  double c;        /* mollifier bandwidth; 0 -> log(3 / tol) ("Parameter selection") */
+  double c_w;      /* window bandwidth; 0 -> P pi (1 - eta / 2) */
+  double eta;      /* Nyquist factor of h <= eta pi / k_c; 0 -> 0.5 */
+  int P;           /* stencil width per dimension; 0 -> smallest meeting tol / 3 */
+  int grid[3];     /* grid points per dimension; 0 -> ceil(L / h) rounded to 2^a 3^b 5^c 7^d */
+  int precision;   /* 0: FP32 spread/FFT/interp (FP64 tables and reductions); 1: all FP64 */
+  int flags;       /* PSWF_FLAG_* */
+} pswf_opts;
+
+typedef struct {
+  double c, c_w, r_c, k_c, eta, tol;
+  double est_err_spread;   /* planner's estimate of the spreading error */
+  double est_err_band;     /* psi_0^c(1), size of the band truncation */
+  double lambda0, C0;      /* eigenvalue lambda_0 of psi_0^c and C_0 = int_0^1 psi_0^c */
+  double box[3], h[3];
+  int grid[3];
+  int P, K, precision, deg_window, deg_mult, flags;
+  int64_t n_max;
+  int64_t workspace_bytes; /* device bytes pswf_plan_set_workspace wants */
+} pswf_info;
+
+typedef struct pswf_plan_s* pswf_plan;
+
+/* Fills *o with the defaults above (r_c left at 0: the caller must set it). */
+void pswf_opts_default(pswf_opts* o);
+
+/* Host-only parameter selection ("Parameter selection"): runs the planner
+ * without touching a GPU and fills *out (n_max and workspace_bytes are 0).
+ * box: host [3] edge lengths; p: host [K] exponents in 1..6; opts: host,
+ * required (r_c has no default).  Returns PSWF_EINVAL or
+ * PSWF_ETOLUNREACHABLE on bad input. */
+int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* opts, pswf_info* out);
+
+/* Creates a plan for up to n_max atoms on the current CUDA device: runs the
+ * planner, builds the batched cuFFT plans (no cuFFT allocation) and records
+ * the stream (a cudaStream_t, NULL = legacy default stream).  Device memory is
+ * not allocated here: attach a workspace with pswf_plan_set_workspace, or the
+ * first pswf_set_points allocates one (cudaMalloc) that the plan owns. */
+int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p,
+                     const pswf_opts* opts, void* stream, pswf_plan* out);
+
+/* Fills *out; synchronous, host only. */
+int pswf_plan_info(pswf_plan plan, pswf_info* out);
+
+/* Attaches caller-owned device memory of at least info.workspace_bytes bytes,
+ * 256-byte aligned, which must outlive the plan's use of it.  Uploads the
+ * plan's tables into it (synchronous copies). */
+int pswf_plan_set_workspace(pswf_plan plan, void* workspace, int64_t bytes);
+
+/* Changes the stream later calls enqueue on. */
+int pswf_plan_set_stream(pswf_plan plan, void* stream);
+
+/* Bins and sorts the atoms by grid tile (new positions and/or charges).
+ * pos: device [n][3] float (pos_dtype 0) or double (pos_dtype 1), any real
+ *   values (wrapped into the box);
+ * q:   device [K][n] real latent charges.
+ * Both are read during this call's kernels only (stream-ordered).
+ * n must be 0..n_max.  NaN/Inf positions are reported by the next
+ * synchronising call as PSWF_ENONFINITE (those atoms are binned at 0). */
+int pswf_set_points(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q);
+
+/* Forward evaluation of the points last set (asynchronous).
+ * energy: device double [K + 1] (may be NULL): E_c per channel (Eq. Fourier,
+ *   reciprocal sum plus zero-frequency term), total at [K];
+ * phi:    device real [K][n] (may be NULL): phi_i^(c) = dE/dq_i^(c);
+ * forces: device real [n][3] (may be NULL): F_i = -dE/dr_i summed over channels.
+ * When the plan has PSWF_FLAG_BACKWARD the grid potential is kept for
+ * pswf_backward. */
+int pswf_execute(pswf_plan plan, double* energy, void* phi, void* forces);
+
+/* Vector-Jacobian product of the last pswf_execute (asynchronous; needs
+ * PSWF_FLAG_BACKWARD and the same points).  Upstream gradients, each may be
+ * NULL (= zero): g_energy device double [K] (d loss / d E_c), g_phi device
+ * real [K][n], g_forces device real [n][3].  Outputs (may be NULL):
+ * grad_q device real [K][n], grad_pos device real [n][3]. */
+int pswf_backward(pswf_plan plan, const double* g_energy, const void* g_phi,
+                  const void* g_forces, void* grad_q, void* grad_pos);
+
+/* Self energies E_self^(p) ("Implementation details") of the points last set,
+ * host double [K].  Synchronises the stream. */
+int pswf_self_energy(pswf_plan plan, double* out);
+
+/* Waits for the plan's stream and returns the first device-side status
+ * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */
+int pswf_sync(pswf_plan plan);
+
+/* End-to-end evaluation from host memory (synchronising): copies positions
+ * (host double [n][3]) and charges (host double [K][n]) to the device,
+ * runs set_points + execute, and copies back energy (host double [K + 1]),
+ * phi (host double [K][n], may be NULL) and forces (host double [n][3], may
+ * be NULL).  Uses pinned staging buffers owned by the plan. */
+int pswf_compute_host(pswf_plan plan, int64_t n, const double* pos, const double* q,
+                      double* energy, double* phi, double* forces);
+
+/* Releases everything the plan owns (not a caller-attached workspace). */
+void pswf_plan_destroy(pswf_plan plan);
+
+/* Human-readable name of a status code (static string). */
+const char* pswf_strerror(int status);
+
+/* Copies the plan's last error message into buf (NUL-terminated). */
+int pswf_plan_last_error(pswf_plan plan, char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSWF_LR_H */

@@ -1,0 +1,727 @@
+// C-ABI of the PSWF-LR hot path: plan, workspace, launches, cuFFT.
+// The public contract is in include/pswf_lr.h.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "launch.cuh"
+#include "planner.hpp"
+#include "pswf_lr.h"
+
+namespace pswf {
+
+// ---- small non-templated kernels ---------------------------------------------------
+__global__ void k_charge_final(int nblk, int K, const double* __restrict__ part, double* __restrict__ charges) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    a += part[(size_t(i) * K + c) * 2 + 0];
+    b += part[(size_t(i) * K + c) * 2 + 1];
+  }
+  charges[c * 2 + 0] = a;
+  charges[c * 2 + 1] = b;
+}
+
+__global__ void k_scan_block_sums(int n, const int* __restrict__ in, int* __restrict__ sums, int per_block) {
+  __shared__ int sh[32];
+  const int64_t base = int64_t(blockIdx.x) * per_block;
+  int s = 0;
+  for (int i = threadIdx.x; i < per_block; i += blockDim.x) {
+    const int64_t j = base + i;
+    if (j < n) s += in[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Single thread: exclusive scan of the (few) block sums in place.
+__global__ void k_scan_sums(int nb, int* __restrict__ sums) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < nb; ++i) {
+      const int v = sums[i];
+      sums[i] = acc;
+      acc += v;
+    }
+  }
+}
+
+// Each block scans its chunk: per-thread strips, block-wide inclusive scan of
+// strip sums, then writes the exclusive prefix; out[n] = total.
+__global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __restrict__ sums, int per_block,
+                             int* __restrict__ out) {
+  __shared__ int sh[kScanBlock];
+  const int64_t base = int64_t(blockIdx.x) * per_block;
+  const int per_thread = (per_block + blockDim.x - 1) / blockDim.x;
+  const int64_t my0 = base + int64_t(threadIdx.x) * per_thread;
+  int local = 0;
+  for (int i = 0; i < per_thread; ++i) {
+    const int64_t j = my0 + i;
+    if (j < n && j < base + per_block) local += in[j];
+  }
+  sh[threadIdx.x] = local;
+  __syncthreads();
+  for (int o = 1; o < int(blockDim.x); o <<= 1) {
+    const int v = (int(threadIdx.x) >= o) ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int acc = sums[blockIdx.x] + sh[threadIdx.x] - local;
+  for (int i = 0; i < per_thread; ++i) {
+    const int64_t j = my0 + i;
+    if (j < n && j < base + per_block) {
+      out[j] = acc;
+      acc += in[j];
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = acc;
+}
+
+// energy[c] = sum of partials + zero_coef[c] * Q_net^2; energy[K] = total.
+__global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
+                               const double* __restrict__ charges, double* __restrict__ energy) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  if (threadIdx.x == 0) tot = 0.0;
+  for (int c = 0; c < K; ++c) {
+    double e = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) e += part[size_t(c) * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+      const double Q = charges[2 * c];
+      const double ec = t + zero_coef[c] * Q * Q;
+      energy[c] = ec;
+      tot += ec;
+    }
+  }
+  if (threadIdx.x == 0) energy[K] = tot;
+}
+
+}  // namespace pswf
+
+using namespace pswf;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kEnergyBlocks = 592;   // 4 x 148 SMs
+constexpr int kQBlocks = 148;
+
+int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
+
+}  // namespace
+
+struct pswf_plan_s {
+  Plan host;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n_max = 0;
+  int64_t n = -1;            // atoms of the last set_points (-1: none)
+  int flags = 0;
+  size_t real_size = 4;
+  Geometry geo{};
+  int ntiles = 0;
+  int scan_blocks = 0;
+  int scan_per_block = 0;
+  int64_t grid_elems = 0;    // K * Mz * My * Mxp
+  // workspace
+  void* ws = nullptr;
+  int64_t ws_bytes = 0;
+  bool ws_owned = false;
+  // device pointers inside the workspace
+  void* grid = nullptr;      // real [K][Mz][My][Mxp]
+  void* grid2 = nullptr;     // second grid (backward)
+  void* st = nullptr;        // real [3][n_max]
+  uint64_t* scell = nullptr; // [n_max]
+  void* sq = nullptr;        // real [K][n_max]
+  int* sperm = nullptr;      // [n_max]
+  int* tile_of = nullptr;    // [n_max]
+  int* rank = nullptr;       // [n_max]
+  int* tile_count = nullptr; // [ntiles]
+  int* tile_start = nullptr; // [ntiles + 1]
+  int* scan_sums = nullptr;  // [scan_blocks]
+  double* qpart = nullptr;   // [kQBlocks][K][2]
+  double* charges = nullptr; // [K][2]: Q_net, Q_self
+  double* epart = nullptr;   // [K][kEnergyBlocks]
+  double* energy_tmp = nullptr; // [K + 1]
+  int* err = nullptr;        // device status flag
+  int* pch = nullptr;        // [K] exponents
+  double* scale = nullptr;   // [K] multiplier scale (includes dV^2 / V)
+  double* zero_coef = nullptr;  // [K]
+  void* coef_m = nullptr;    // real [K][kMultSeg][deg_m + 1]
+  void* iw2[3] = {nullptr, nullptr, nullptr};  // real [M_d / 2 + 1]
+  void* fft_work = nullptr;
+  // cuFFT
+  cufftHandle fwd = 0, inv = 0;
+  bool fft_made = false;
+  size_t fft_work_bytes = 0;
+  // host staging for pswf_compute_host
+  double* h_pin = nullptr;
+  int64_t h_pin_elems = 0;
+  void* d_stage = nullptr;
+  int64_t d_stage_bytes = 0;
+  std::string last_error;
+};
+
+namespace {
+
+int set_err(pswf_plan p, int code, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return code;
+}
+
+int cuda_check(pswf_plan p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PSWF_OK;
+  return set_err(p, e == cudaErrorMemoryAllocation ? PSWF_ENOMEM : PSWF_ECUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int launch_check(pswf_plan p, const char* what) { return cuda_check(p, cudaGetLastError(), what); }
+
+// Workspace layout (each region 256-byte aligned).  Returns total bytes and,
+// when base != nullptr, assigns the pointers.
+int64_t layout(pswf_plan p, char* base) {
+  const Plan& h = p->host;
+  const int K = h.K;
+  const int64_t rs = int64_t(p->real_size);
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off += align256(std::max<int64_t>(bytes, 1));
+    return ptr;
+  };
+  p->grid = take(p->grid_elems * rs);
+  p->grid2 = (p->flags & PSWF_FLAG_BACKWARD) ? take(p->grid_elems * rs) : nullptr;
+  const int64_t nm = std::max<int64_t>(p->n_max, 1);
+  p->st = take(3 * nm * rs);
+  p->scell = reinterpret_cast<uint64_t*>(take(nm * 8));
+  p->sq = take(K * nm * rs);
+  p->sperm = reinterpret_cast<int*>(take(nm * 4));
+  p->tile_of = reinterpret_cast<int*>(take(nm * 4));
+  p->rank = reinterpret_cast<int*>(take(nm * 4));
+  p->tile_count = reinterpret_cast<int*>(take(int64_t(p->ntiles) * 4));
+  p->tile_start = reinterpret_cast<int*>(take(int64_t(p->ntiles + 1) * 4));
+  p->scan_sums = reinterpret_cast<int*>(take(int64_t(p->scan_blocks) * 4));
+  p->qpart = reinterpret_cast<double*>(take(int64_t(kQBlocks) * K * 2 * 8));
+  p->charges = reinterpret_cast<double*>(take(int64_t(K) * 2 * 8));
+  p->epart = reinterpret_cast<double*>(take(int64_t(K) * kEnergyBlocks * 8));
+  p->energy_tmp = reinterpret_cast<double*>(take(int64_t(K + 1) * 8));
+  p->err = reinterpret_cast<int*>(take(4));
+  p->pch = reinterpret_cast<int*>(take(int64_t(K) * 4));
+  p->scale = reinterpret_cast<double*>(take(int64_t(K) * 8));
+  p->zero_coef = reinterpret_cast<double*>(take(int64_t(K) * 8));
+  p->coef_m = take(int64_t(K) * kMultSeg * (h.deg_m + 1) * rs);
+  for (int d = 0; d < 3; ++d) p->iw2[d] = take(int64_t(h.M[d] / 2 + 1) * rs);
+  p->fft_work = take(int64_t(p->fft_work_bytes));
+  return off;
+}
+
+template <typename R>
+std::vector<R> to_real(const std::vector<double>& v) {
+  return std::vector<R>(v.begin(), v.end());
+}
+
+template <typename T>
+int upload(pswf_plan p, void* dst, const std::vector<T>& v, const char* what) {
+  return cuda_check(p, cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+}
+
+int upload_tables(pswf_plan p) {
+  const Plan& h = p->host;
+  const int K = h.K;
+  int rc;
+  std::vector<double> scale(K);
+  const double dv2v = h.dV * h.dV / h.V;
+  for (int k = 0; k < K; ++k) scale[k] = h.mult_scale[k] * dv2v;
+  if ((rc = upload(p, p->pch, h.p, "upload p"))) return rc;
+  if ((rc = upload(p, p->scale, scale, "upload scale"))) return rc;
+  if ((rc = upload(p, p->zero_coef, h.zero_coef, "upload zero"))) return rc;
+  if (p->real_size == 4) {
+    if ((rc = upload(p, p->coef_m, to_real<float>(h.coef_m), "upload coef"))) return rc;
+    for (int d = 0; d < 3; ++d)
+      if ((rc = upload(p, p->iw2[d], to_real<float>(h.iw2[d]), "upload iw2"))) return rc;
+  } else {
+    if ((rc = upload(p, p->coef_m, h.coef_m, "upload coef"))) return rc;
+    for (int d = 0; d < 3; ++d)
+      if ((rc = upload(p, p->iw2[d], h.iw2[d], "upload iw2"))) return rc;
+  }
+  return cuda_check(p, cudaMemset(p->err, 0, 4), "clear err");
+}
+
+int attach_fft_work(pswf_plan p) {
+  if (!p->fft_made) return PSWF_OK;
+  if (cufftSetWorkArea(p->fwd, p->fft_work) != CUFFT_SUCCESS || cufftSetWorkArea(p->inv, p->fft_work) != CUFFT_SUCCESS)
+    return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
+  return PSWF_OK;
+}
+
+int ensure_workspace(pswf_plan p) {
+  if (p->ws) return PSWF_OK;
+  void* mem = nullptr;
+  int rc = cuda_check(p, cudaMalloc(&mem, size_t(p->ws_bytes)), "workspace cudaMalloc");
+  if (rc) return rc;
+  p->ws = mem;
+  p->ws_owned = true;
+  layout(p, static_cast<char*>(mem));
+  if ((rc = attach_fft_work(p))) return rc;
+  return upload_tables(p);
+}
+
+LaunchCtx make_ctx(pswf_plan p) {
+  LaunchCtx c;
+  c.geo = p->geo;
+  c.nmax = p->n_max;
+  c.n = p->n;
+  c.ntiles = p->ntiles;
+  c.tile_start = p->tile_start;
+  c.st = p->st;
+  c.scell = p->scell;
+  c.sq = p->sq;
+  c.sperm = p->sperm;
+  c.grid = p->grid;
+  c.zero_coef = p->zero_coef;
+  c.charges = p->charges;
+  c.coef_w = p->host.coef_w.data();
+  c.deg_w = p->host.deg_w;
+  c.stream = p->stream;
+  return c;
+}
+
+template <typename R>
+int multiply(pswf_plan p, int want_energy) {
+  const Plan& h = p->host;
+  MultParams mp;
+  for (int d = 0; d < 3; ++d) {
+    mp.kfac[d] = 2.0 * M_PI / h.box[d];
+    mp.M[d] = h.M[d];
+  }
+  mp.inv_kc = 1.0 / h.k_c;
+  mp.Mxh = h.M[0] / 2 + 1;
+  mp.deg = h.deg_m;
+  mp.K = h.K;
+  dim3 grid(kEnergyBlocks, h.K);
+  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->grid), mp, p->pch, p->scale,
+                                                  static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2[0]),
+                                                  static_cast<const R*>(p->iw2[1]), static_cast<const R*>(p->iw2[2]),
+                                                  p->epart, want_energy);
+  return launch_check(p, "k_multiply");
+}
+
+int fft_exec(pswf_plan p, void* data, bool forward) {
+  cufftResult r;
+  cufftHandle hdl = forward ? p->fwd : p->inv;
+  if (cufftSetStream(hdl, p->stream) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftSetStream failed");
+  if (p->real_size == 4) {
+    r = forward ? cufftExecR2C(hdl, static_cast<cufftReal*>(data), static_cast<cufftComplex*>(data))
+                : cufftExecC2R(hdl, static_cast<cufftComplex*>(data), static_cast<cufftReal*>(data));
+  } else {
+    r = forward ? cufftExecD2Z(hdl, static_cast<cufftDoubleReal*>(data), static_cast<cufftDoubleComplex*>(data))
+                : cufftExecZ2D(hdl, static_cast<cufftDoubleComplex*>(data), static_cast<cufftDoubleReal*>(data));
+  }
+  if (r != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftExec failed (" + std::to_string(int(r)) + ")");
+  return PSWF_OK;
+}
+
+template <typename R>
+int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const void* q) {
+  cudaStream_t s = p->stream;
+  int rc;
+  p->n = n;
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 148 * 32)));
+  if (n > 0) {
+    if (pos_dtype == 0)
+      k_bin<float><<<blocks, kThreads, 0, s>>>(n, static_cast<const float*>(pos), p->geo, p->tile_of, p->rank,
+                                              p->tile_count, p->err);
+    else
+      k_bin<double><<<blocks, kThreads, 0, s>>>(n, static_cast<const double*>(pos), p->geo, p->tile_of, p->rank,
+                                               p->tile_count, p->err);
+    if ((rc = launch_check(p, "k_bin"))) return rc;
+  }
+  k_scan_block_sums<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block);
+  if ((rc = launch_check(p, "k_scan_block_sums"))) return rc;
+  k_scan_sums<<<1, 32, 0, s>>>(p->scan_blocks, p->scan_sums);
+  if ((rc = launch_check(p, "k_scan_sums"))) return rc;
+  k_scan_apply<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block,
+                                                      p->tile_start);
+  if ((rc = launch_check(p, "k_scan_apply"))) return rc;
+  if (n > 0) {
+    if (pos_dtype == 0)
+      k_scatter<float, R><<<blocks, kThreads, 0, s>>>(n, p->n_max, static_cast<const float*>(pos),
+                                                      static_cast<const R*>(q), p->geo, p->tile_of, p->rank,
+                                                      p->tile_start, static_cast<R*>(p->st), p->scell,
+                                                      static_cast<R*>(p->sq), p->sperm);
+    else
+      k_scatter<double, R><<<blocks, kThreads, 0, s>>>(n, p->n_max, static_cast<const double*>(pos),
+                                                       static_cast<const R*>(q), p->geo, p->tile_of, p->rank,
+                                                       p->tile_start, static_cast<R*>(p->st), p->scell,
+                                                       static_cast<R*>(p->sq), p->sperm);
+    if ((rc = launch_check(p, "k_scatter"))) return rc;
+  }
+  k_charge_partials<R><<<kQBlocks, kThreads, 0, s>>>(n, static_cast<const R*>(q), p->host.K, p->qpart);
+  if ((rc = launch_check(p, "k_charge_partials"))) return rc;
+  k_charge_final<<<1, 64, 0, s>>>(kQBlocks, p->host.K, p->qpart, p->charges);
+  return launch_check(p, "k_charge_final");
+}
+
+template <typename R>
+int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
+  cudaStream_t s = p->stream;
+  int rc;
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid"))) return rc;
+  const LaunchCtx ctx = make_ctx(p);
+  if (p->n > 0) {
+    cudaError_t e = sizeof(R) == 4 ? launch_spread_float(ctx) : launch_spread_double(ctx);
+    if ((rc = cuda_check(p, e, "spread"))) return rc;
+  }
+  if ((rc = fft_exec(p, p->grid, true))) return rc;
+  if ((rc = multiply<R>(p, 1))) return rc;
+  k_energy_final<<<1, 256, 0, s>>>(p->host.K, kEnergyBlocks, p->epart, p->zero_coef, p->charges,
+                                   energy ? energy : p->energy_tmp);
+  if ((rc = launch_check(p, "k_energy_final"))) return rc;
+  if ((phi || forces) && p->n > 0) {
+    if ((rc = fft_exec(p, p->grid, false))) return rc;
+    cudaError_t e = sizeof(R) == 4 ? launch_interp_float(ctx, phi, forces) : launch_interp_double(ctx, phi, forces);
+    if ((rc = cuda_check(p, e, "interp"))) return rc;
+  }
+  return PSWF_OK;
+}
+
+int make_fft(pswf_plan p) {
+  const Plan& h = p->host;
+  int n[3] = {h.M[2], h.M[1], h.M[0]};
+  const int Mxh = h.M[0] / 2 + 1;
+  int embed_r[3] = {h.M[2], h.M[1], 2 * Mxh};
+  int embed_c[3] = {h.M[2], h.M[1], Mxh};
+  const int dist_r = h.M[2] * h.M[1] * 2 * Mxh;
+  const int dist_c = h.M[2] * h.M[1] * Mxh;
+  const cufftType tf = p->real_size == 4 ? CUFFT_R2C : CUFFT_D2Z;
+  const cufftType ti = p->real_size == 4 ? CUFFT_C2R : CUFFT_Z2D;
+  if (cufftCreate(&p->fwd) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
+  if (cufftCreate(&p->inv) != CUFFT_SUCCESS) {
+    cufftDestroy(p->fwd);
+    return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
+  }
+  p->fft_made = true;
+  cufftSetAutoAllocation(p->fwd, 0);
+  cufftSetAutoAllocation(p->inv, 0);
+  size_t w1 = 0, w2 = 0;
+  const cufftResult r1 = cufftMakePlanMany(p->fwd, 3, n, embed_r, 1, dist_r, embed_c, 1, dist_c, tf, h.K, &w1);
+  const cufftResult r2 = cufftMakePlanMany(p->inv, 3, n, embed_c, 1, dist_c, embed_r, 1, dist_r, ti, h.K, &w2);
+  if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
+    return set_err(p, PSWF_ECUFFT,
+                   "cufftMakePlanMany failed (" + std::to_string(int(r1)) + "," + std::to_string(int(r2)) + ")");
+  p->fft_work_bytes = std::max(w1, w2);
+  return PSWF_OK;
+}
+
+Options to_options(const pswf_opts* opts) {
+  Options o;
+  o.tol = opts->tol > 0 ? opts->tol : 1e-5;
+  o.r_c = opts->r_c;
+  o.c = opts->c;
+  o.c_w = opts->c_w;
+  o.eta = opts->eta;
+  o.P = opts->P;
+  for (int d = 0; d < 3; ++d) o.grid[d] = opts->grid[d];
+  o.precision = opts->precision;
+  return o;
+}
+
+void fill_info(const Plan& h, int flags, pswf_info* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->c = h.c;
+  out->c_w = h.c_w;
+  out->r_c = h.r_c;
+  out->k_c = h.k_c;
+  out->eta = h.eta;
+  out->tol = h.tol;
+  out->est_err_spread = h.est_spread;
+  out->est_err_band = h.est_band;
+  out->lambda0 = h.moll.lambda0;
+  out->C0 = h.moll.C0;
+  for (int d = 0; d < 3; ++d) {
+    out->box[d] = h.box[d];
+    out->h[d] = h.h[d];
+    out->grid[d] = h.M[d];
+  }
+  out->P = h.P;
+  out->K = h.K;
+  out->precision = h.opt.precision;
+  out->deg_window = h.deg_w;
+  out->deg_mult = h.deg_m;
+  out->flags = flags;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pswf_opts_default(pswf_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-5;
+}
+
+int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* opts, pswf_info* out) {
+  if (!box || !p || !opts || !out) return PSWF_EINVAL;
+  Plan h;
+  const int rc = make_plan(box, K, p, to_options(opts), h);
+  if (rc) return rc;
+  fill_info(h, opts->flags, out);
+  return PSWF_OK;
+}
+
+int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p, const pswf_opts* opts, void* stream,
+                     pswf_plan* out) {
+  if (!out) return PSWF_EINVAL;
+  *out = nullptr;
+  if (!box || !p || !opts || n_max < 0 || n_max > (int64_t(1) << 31) - 1) return PSWF_EINVAL;
+  pswf_plan pl = new (std::nothrow) pswf_plan_s();
+  if (!pl) return PSWF_ENOMEM;
+  int rc = make_plan(box, K, p, to_options(opts), pl->host);
+  if (rc) {
+    delete pl;
+    return rc;
+  }
+  cudaGetDevice(&pl->device);
+  pl->stream = static_cast<cudaStream_t>(stream);
+  pl->n_max = n_max;
+  pl->flags = opts->flags;
+  pl->real_size = opts->precision == 1 ? 8 : 4;
+  const Plan& h = pl->host;
+  for (int d = 0; d < 3; ++d) {
+    pl->geo.L[d] = h.box[d];
+    pl->geo.M[d] = h.M[d];
+    pl->geo.ntile[d] = (h.M[d] + kTile - 1) / kTile;
+  }
+  pl->geo.Mxp = 2 * (h.M[0] / 2 + 1);
+  pl->geo.P = h.P;
+  pl->geo.K = h.K;
+  pl->ntiles = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
+  pl->scan_per_block = 16384;
+  pl->scan_blocks = (pl->ntiles + pl->scan_per_block - 1) / pl->scan_per_block;
+  pl->grid_elems = int64_t(h.K) * h.M[2] * h.M[1] * pl->geo.Mxp;
+  if ((rc = make_fft(pl))) {
+    pswf_plan_destroy(pl);
+    return rc;
+  }
+  pl->ws_bytes = layout(pl, nullptr);
+  *out = pl;
+  return PSWF_OK;
+}
+
+int pswf_plan_info(pswf_plan pl, pswf_info* out) {
+  if (!pl || !out) return PSWF_EINVAL;
+  fill_info(pl->host, pl->flags, out);
+  out->n_max = pl->n_max;
+  out->workspace_bytes = pl->ws_bytes;
+  return PSWF_OK;
+}
+
+int pswf_plan_set_workspace(pswf_plan pl, void* ws, int64_t bytes) {
+  if (!pl || !ws) return PSWF_EINVAL;
+  if (bytes < pl->ws_bytes) return set_err(pl, PSWF_ENOMEM, "workspace smaller than info.workspace_bytes");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return set_err(pl, PSWF_EINVAL, "workspace must be 256-byte aligned");
+  if (pl->ws_owned) {
+    cudaFree(pl->ws);
+    pl->ws_owned = false;
+  }
+  pl->ws = ws;
+  layout(pl, static_cast<char*>(ws));
+  pl->n = -1;
+  int rc = attach_fft_work(pl);
+  if (rc) return rc;
+  return upload_tables(pl);
+}
+
+int pswf_plan_set_stream(pswf_plan pl, void* stream) {
+  if (!pl) return PSWF_EINVAL;
+  pl->stream = static_cast<cudaStream_t>(stream);
+  return PSWF_OK;
+}
+
+int pswf_set_points(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, const void* q) {
+  if (!pl) return PSWF_EINVAL;
+  if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
+  if (n > 0 && (!pos || !q)) return set_err(pl, PSWF_EINVAL, "pos and q are required");
+  if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
+  const int rc = ensure_workspace(pl);
+  if (rc) return rc;
+  return pl->real_size == 4 ? do_set_points<float>(pl, n, pos, pos_dtype, q)
+                            : do_set_points<double>(pl, n, pos, pos_dtype, q);
+}
+
+int pswf_execute(pswf_plan pl, double* energy, void* phi, void* forces) {
+  if (!pl) return PSWF_EINVAL;
+  if (pl->n < 0) return set_err(pl, PSWF_ESTATE, "pswf_execute before pswf_set_points");
+  return pl->real_size == 4 ? do_execute<float>(pl, energy, phi, forces) : do_execute<double>(pl, energy, phi, forces);
+}
+
+int pswf_backward(pswf_plan pl, const double* g_energy, const void* g_phi, const void* g_forces, void* grad_q,
+                  void* grad_pos) {
+  (void)g_energy;
+  (void)g_phi;
+  (void)g_forces;
+  (void)grad_q;
+  (void)grad_pos;
+  if (!pl) return PSWF_EINVAL;
+  return set_err(pl, PSWF_ESTATE, "backward is not available in this build");
+}
+
+int pswf_self_energy(pswf_plan pl, double* out) {
+  if (!pl || !out) return PSWF_EINVAL;
+  if (pl->n < 0) return set_err(pl, PSWF_ESTATE, "pswf_self_energy before pswf_set_points");
+  const int K = pl->host.K;
+  std::vector<double> ch(2 * K);
+  int rc = cuda_check(pl, cudaMemcpyAsync(ch.data(), pl->charges, 2 * K * sizeof(double), cudaMemcpyDeviceToHost,
+                                          pl->stream), "read charges");
+  if (rc) return rc;
+  if ((rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "sync"))) return rc;
+  for (int k = 0; k < K; ++k) out[k] = pl->host.self_coef[k] * ch[2 * k + 1];
+  return PSWF_OK;
+}
+
+int pswf_sync(pswf_plan pl) {
+  if (!pl) return PSWF_EINVAL;
+  int rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "stream synchronize");
+  if (rc) return rc;
+  if (!pl->err) return PSWF_OK;
+  int flag = 0;
+  if ((rc = cuda_check(pl, cudaMemcpy(&flag, pl->err, 4, cudaMemcpyDeviceToHost), "read status"))) return rc;
+  if (flag) {
+    cudaMemset(pl->err, 0, 4);
+    return set_err(pl, flag, flag == PSWF_ENONFINITE ? "non-finite positions" : "device status");
+  }
+  return PSWF_OK;
+}
+
+int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+                      double* forces) {
+  if (!pl || !energy || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
+  if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
+  const int K = pl->host.K;
+  const int64_t rs = int64_t(pl->real_size);
+  int rc = ensure_workspace(pl);
+  if (rc) return rc;
+  // device staging: pos double [n][3] | q real [K][n] | energy [K+1] | phi real [K][n] | forces real [n][3]
+  const int64_t need = align256(n * 3 * 8) + align256(K * n * rs) + align256((K + 1) * 8) + align256(K * n * rs) +
+                       align256(n * 3 * rs);
+  if (need > pl->d_stage_bytes) {
+    if (pl->d_stage) cudaFree(pl->d_stage);
+    pl->d_stage = nullptr;
+    pl->d_stage_bytes = 0;
+    if ((rc = cuda_check(pl, cudaMalloc(&pl->d_stage, size_t(need)), "staging cudaMalloc"))) return rc;
+    pl->d_stage_bytes = need;
+  }
+  const int64_t hneed = std::max<int64_t>(n * 3 + K * n + K + 1 + K * n + n * 3, 1);
+  if (hneed > pl->h_pin_elems) {
+    if (pl->h_pin) cudaFreeHost(pl->h_pin);
+    pl->h_pin = nullptr;
+    pl->h_pin_elems = 0;
+    if ((rc = cuda_check(pl, cudaMallocHost(&pl->h_pin, size_t(hneed) * 8), "pinned cudaMallocHost"))) return rc;
+    pl->h_pin_elems = hneed;
+  }
+  char* d = static_cast<char*>(pl->d_stage);
+  double* d_pos = reinterpret_cast<double*>(d);
+  d += align256(n * 3 * 8);
+  void* d_q = d;
+  d += align256(K * n * rs);
+  double* d_e = reinterpret_cast<double*>(d);
+  d += align256((K + 1) * 8);
+  void* d_phi = d;
+  d += align256(K * n * rs);
+  void* d_f = d;
+  double* h_pos = pl->h_pin;
+  double* h_q = h_pos + n * 3;
+  double* h_e = h_q + K * n;
+  double* h_phi = h_e + K + 1;
+  double* h_f = h_phi + K * n;
+  if (n > 0) std::memcpy(h_pos, pos, size_t(n) * 24);
+  if (rs == 4) {
+    float* hq = reinterpret_cast<float*>(h_q);
+    for (int64_t i = 0; i < K * n; ++i) hq[i] = float(q[i]);
+  } else if (n > 0) {
+    std::memcpy(h_q, q, size_t(K * n) * 8);
+  }
+  cudaStream_t s = pl->stream;
+  if ((rc = cuda_check(pl, cudaMemcpyAsync(d_pos, h_pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos"))) return rc;
+  if ((rc = cuda_check(pl, cudaMemcpyAsync(d_q, h_q, size_t(K * n) * rs, cudaMemcpyHostToDevice, s), "h2d q"))) return rc;
+  if ((rc = pswf_set_points(pl, n, d_pos, 1, d_q))) return rc;
+  if ((rc = pswf_execute(pl, d_e, phi ? d_phi : nullptr, forces ? d_f : nullptr))) return rc;
+  if ((rc = cuda_check(pl, cudaMemcpyAsync(h_e, d_e, size_t(K + 1) * 8, cudaMemcpyDeviceToHost, s), "d2h energy"))) return rc;
+  if (phi && (rc = cuda_check(pl, cudaMemcpyAsync(h_phi, d_phi, size_t(K * n) * rs, cudaMemcpyDeviceToHost, s), "d2h phi")))
+    return rc;
+  if (forces && (rc = cuda_check(pl, cudaMemcpyAsync(h_f, d_f, size_t(n) * 3 * rs, cudaMemcpyDeviceToHost, s), "d2h forces")))
+    return rc;
+  if ((rc = pswf_sync(pl))) return rc;
+  std::memcpy(energy, h_e, size_t(K + 1) * 8);
+  if (rs == 4) {
+    const float* fp = reinterpret_cast<const float*>(h_phi);
+    const float* ff = reinterpret_cast<const float*>(h_f);
+    if (phi)
+      for (int64_t i = 0; i < K * n; ++i) phi[i] = fp[i];
+    if (forces)
+      for (int64_t i = 0; i < 3 * n; ++i) forces[i] = ff[i];
+  } else {
+    if (phi && n > 0) std::memcpy(phi, h_phi, size_t(K * n) * 8);
+    if (forces && n > 0) std::memcpy(forces, h_f, size_t(n) * 24);
+  }
+  return PSWF_OK;
+}
+
+void pswf_plan_destroy(pswf_plan pl) {
+  if (!pl) return;
+  if (pl->fft_made) {
+    cufftDestroy(pl->fwd);
+    cufftDestroy(pl->inv);
+  }
+  if (pl->ws_owned && pl->ws) cudaFree(pl->ws);
+  if (pl->d_stage) cudaFree(pl->d_stage);
+  if (pl->h_pin) cudaFreeHost(pl->h_pin);
+  delete pl;
+}
+
+const char* pswf_strerror(int status) {
+  switch (status) {
+    case PSWF_OK: return "ok";
+    case PSWF_EINVAL: return "invalid argument";
+    case PSWF_ENOMEM: return "out of device memory";
+    case PSWF_ECUFFT: return "cuFFT error";
+    case PSWF_ECUDA: return "CUDA error";
+    case PSWF_ETIMEOUT: return "device wait timed out";
+    case PSWF_ENONFINITE: return "non-finite positions";
+    case PSWF_ETOLUNREACHABLE: return "tolerance unreachable on this grid";
+    case PSWF_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+int pswf_plan_last_error(pswf_plan pl, char* buf, int len) {
+  if (!pl || !buf || len <= 0) return PSWF_EINVAL;
+  std::snprintf(buf, size_t(len), "%s", pl->last_error.c_str());
+  return PSWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,396 @@
+// Device kernels of the PSWF-LR hot path (sm_103a).
+//
+// Data layout in HBM (one plan):
+//   grid   real [K][M_z][M_y][M_xp], M_xp = 2 (M_x / 2 + 1): the spread
+//          density, overwritten in place by the R2C transform, the multiplier
+//          and the C2R transform (the grid potential Psi);
+//   sorted atoms (tile order): st[3][n] real window offsets t_d in [0, 1),
+//          scell[n] packed stencil-start cell, sq[K][n] real charges,
+//          sperm[n] original index;
+//   tile_start[n_tiles + 1] int32 offsets of each tile's atoms.
+// Tiles are kTile^3 blocks of stencil-start cells.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "planner.hpp"
+
+namespace pswf {
+
+constexpr int kTile = 8;
+
+struct Geometry {
+  double L[3];       // box edges
+  int M[3];          // grid points per dimension
+  int Mxp;           // padded row length (real elements)
+  int P;             // stencil width
+  int ntile[3];      // tiles per dimension
+  int K;             // channels
+};
+
+template <typename R>
+struct WinCoef {
+  int deg;
+  R c[kMaxP * (kMaxDeg + 1)];   // piece j, monomial n at [j * (deg + 1) + n]
+};
+
+struct MultParams {
+  double kfac[3];     // 2 pi / L_d
+  double inv_kc;      // 1 / k_c
+  int M[3];
+  int Mxh;            // M_x / 2 + 1
+  int deg;            // multiplier polynomial degree
+  int K;
+};
+
+template <typename R>
+struct Cplx {
+  R x, y;
+};
+
+__host__ __device__ inline uint64_t pack_cell(int x, int y, int z) {
+  return uint64_t(uint32_t(x)) | (uint64_t(uint32_t(y)) << 21) | (uint64_t(uint32_t(z)) << 42);
+}
+__host__ __device__ inline void unpack_cell(uint64_t c, int& x, int& y, int& z) {
+  x = int(c & 0x1FFFFF);
+  y = int((c >> 21) & 0x1FFFFF);
+  z = int((c >> 42) & 0x1FFFFF);
+}
+
+// Stencil start (reading C5): u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2 - u
+// in [0, 1), in FP64 once per atom; i0 wrapped into [0, M).  Rounding can put
+// t at 1.0; then the equivalent (i0 - 1, t - 1) is used.
+__device__ inline void locate(double x, double L, int M, int P, int& i0w, double& t) {
+  x = x - L * floor(x / L);
+  if (!(x < L) || x < 0.0) x = 0.0;
+  const double u = x * (double(M) / L);
+  const double half = 0.5 * P;
+  const double fi0 = ceil(u - half);
+  int i0 = int(fi0);
+  t = fi0 + half - u;
+  if (t >= 1.0) {
+    t -= 1.0;
+    i0 -= 1;
+  }
+  if (t < 0.0) t = 0.0;
+  i0 %= M;
+  if (i0 < 0) i0 += M;
+  i0w = i0;
+}
+
+// Window weights W_j(t) and dW_j/ds (s = 2t - 1) for the P pieces (Horner).
+template <typename R, int P>
+__device__ inline void window_weights(R t, const WinCoef<R>& wc, R (&w)[P], R (&dw)[P]) {
+  const R s = R(2) * t - R(1);
+  const int deg = wc.deg;
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const R* c = wc.c + j * (deg + 1);
+    R v = c[deg], dv = R(0);
+    for (int n = deg - 1; n >= 0; --n) {
+      dv = dv * s + v;
+      v = v * s + c[n];
+    }
+    w[j] = v;
+    dw[j] = dv;
+  }
+}
+
+template <typename R, int P>
+__device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
+  const R s = R(2) * t - R(1);
+  const int deg = wc.deg;
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const R* c = wc.c + j * (deg + 1);
+    R v = c[deg];
+    for (int n = deg - 1; n >= 0; --n) v = v * s + c[n];
+    w[j] = v;
+  }
+}
+
+// ---- binning -----------------------------------------------------------------
+template <typename PosT>
+__global__ void k_bin(int64_t n, const PosT* __restrict__ pos, Geometry g, int* __restrict__ tile_of,
+                      int* __restrict__ rank, int* __restrict__ tile_count, int* __restrict__ err) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    int tc[3];
+    for (int d = 0; d < 3; ++d) {
+      double x = double(pos[3 * i + d]);
+      if (!isfinite(x)) {
+        atomicCAS(err, 0, -6);
+        x = 0.0;
+      }
+      int i0;
+      double t;
+      locate(x, g.L[d], g.M[d], g.P, i0, t);
+      tc[d] = i0 / kTile;
+    }
+    const int tile = (tc[2] * g.ntile[1] + tc[1]) * g.ntile[0] + tc[0];
+    tile_of[i] = tile;
+    rank[i] = atomicAdd(tile_count + tile, 1);
+  }
+}
+
+template <typename PosT, typename R>
+__global__ void k_scatter(int64_t n, int64_t nmax, const PosT* __restrict__ pos, const R* __restrict__ q, Geometry g,
+                          const int* __restrict__ tile_of, const int* __restrict__ rank,
+                          const int* __restrict__ tile_start, R* __restrict__ st, uint64_t* __restrict__ scell,
+                          R* __restrict__ sq, int* __restrict__ sperm) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    int i0[3];
+    double t[3];
+    for (int d = 0; d < 3; ++d) {
+      double x = double(pos[3 * i + d]);
+      if (!isfinite(x)) x = 0.0;
+      locate(x, g.L[d], g.M[d], g.P, i0[d], t[d]);
+    }
+    const int64_t dst = int64_t(tile_start[tile_of[i]]) + rank[i];
+    st[dst] = R(t[0]);
+    st[nmax + dst] = R(t[1]);
+    st[2 * nmax + dst] = R(t[2]);
+    scell[dst] = pack_cell(i0[0], i0[1], i0[2]);
+    for (int c = 0; c < g.K; ++c) sq[c * nmax + dst] = q[c * n + i];
+    sperm[dst] = int(i);
+  }
+}
+
+// Per-block FP64 partial sums of q and q^2 per channel: part[(blk * K + c) * 2 + {0,1}].
+template <typename R>
+__global__ void k_charge_partials(int64_t n, const R* __restrict__ q, int K, double* __restrict__ part) {
+  __shared__ double sh[2][32];
+  for (int c = 0; c < K; ++c) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+      const double v = double(q[c * n + i]);
+      s1 += v;
+      s2 += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      sh[0][wid] = s1;
+      sh[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+        a += sh[0][w];
+        b += sh[1][w];
+      }
+      part[(size_t(blockIdx.x) * K + c) * 2 + 0] = a;
+      part[(size_t(blockIdx.x) * K + c) * 2 + 1] = b;
+    }
+    __syncthreads();
+  }
+}
+
+// charges[c*2+0] = Q_net, charges[c*2+1] = Q_self; one thread per channel.
+__global__ void k_charge_final(int nblk, int K, const double* __restrict__ part, double* __restrict__ charges);
+
+// ---- exclusive scan of tile counts (three passes) -------------------------------
+constexpr int kScanBlock = 1024;
+__global__ void k_scan_block_sums(int n, const int* __restrict__ in, int* __restrict__ sums, int per_block);
+__global__ void k_scan_sums(int nb, int* __restrict__ sums);
+__global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __restrict__ sums, int per_block,
+                             int* __restrict__ out);
+__global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
+                               const double* __restrict__ charges, double* __restrict__ energy);
+
+// ---- spreading (step (i)) ----------------------------------------------------------
+// One block per tile: accumulate the padded (T + P - 1)^3 tile for a chunk of
+// channels in shared memory, then add it into the grid (periodic wrap).
+template <typename R, int P>
+__global__ void k_spread(Geometry g, int64_t nmax, const int* __restrict__ tile_start, const R* __restrict__ st,
+                         const uint64_t* __restrict__ scell, const R* __restrict__ sq, int c0, int kc,
+                         WinCoef<R> wc, R* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  constexpr int S = kTile + P - 1;
+  constexpr int S3 = S * S * S;
+  const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
+    if (a0 == a1) continue;
+    const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
+    const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
+    for (int i = threadIdx.x; i < kc * S3; i += blockDim.x) sm[i] = R(0);
+    __syncthreads();
+    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+      R wx[P], wy[P], wz[P];
+      window_values<R, P>(st[a], wc, wx);
+      window_values<R, P>(st[nmax + a], wc, wy);
+      window_values<R, P>(st[2 * nmax + a], wc, wz);
+      int cx, cy, cz;
+      unpack_cell(scell[a], cx, cy, cz);
+      const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
+      for (int c = 0; c < kc; ++c) {
+        const R qc = sq[(c0 + c) * nmax + a];
+        R* smc = sm + c * S3;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const R wzq = wz[k] * qc;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const R wyz = wy[j] * wzq;
+            R* row = smc + ((lz + k) * S + (ly + j)) * S + lx;
+#pragma unroll
+            for (int i = 0; i < P; ++i) atomicAdd(row + i, wx[i] * wyz);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kc * S3; idx += blockDim.x) {
+      const R v = sm[idx];
+      if (v != R(0)) {
+        const int c = idx / S3, r = idx % S3;
+        const int lz = r / (S * S), ly = (r / S) % S, lx = r % S;
+        const int gx = (ox + lx) % g.M[0], gy = (oy + ly) % g.M[1], gz = (oz + lz) % g.M[2];
+        atomicAdd(grid + ((int64_t(c0 + c) * g.M[2] + gz) * g.M[1] + gy) * g.Mxp + gx, v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- multiplier and energy (steps (iii)-(iv)) --------------------------------------
+// blockIdx.y = channel.  For each half-spectrum mode m != 0 with u = |k|/k_c < 1:
+//   G = scale_c * sing_p(k) * (S_p(u) + log part) * iw2x * iw2y * iw2z  (times dV^2/V,
+//   folded into scale_c), energy += w_m G |rho-hat|^2 / 2, rho-hat <- G rho-hat;
+// all other modes are set to zero.  Energy partials per block in FP64.
+template <typename R>
+__global__ void k_multiply(Cplx<R>* __restrict__ data, MultParams mp, const int* __restrict__ pch,
+                           const double* __restrict__ scale, const R* __restrict__ coef,
+                           const R* __restrict__ iw2x, const R* __restrict__ iw2y, const R* __restrict__ iw2z,
+                           double* __restrict__ part, int want_energy) {
+  const int c = blockIdx.y;
+  const int p = pch[c];
+  const R sc = R(scale[c]);
+  const int64_t nh = int64_t(mp.Mxh) * mp.M[1] * mp.M[2];
+  Cplx<R>* d = data + int64_t(c) * nh;
+  const R* cf = coef + size_t(c) * kMultSeg * (mp.deg + 1);
+  double e = 0.0;
+  for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < nh; idx += int64_t(gridDim.x) * blockDim.x) {
+    const int ix = int(idx % mp.Mxh);
+    const int iy = int((idx / mp.Mxh) % mp.M[1]);
+    const int iz = int(idx / (int64_t(mp.Mxh) * mp.M[1]));
+    const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
+    const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
+    const R kx = R(mp.kfac[0] * ix), ky = R(mp.kfac[1] * my), kz = R(mp.kfac[2] * mz);
+    const R k2 = kx * kx + ky * ky + kz * kz;
+    const R k = sqrt(k2);
+    const R u = k * R(mp.inv_kc);
+    if (!(u < R(1)) || (ix == 0 && my == 0 && mz == 0)) {
+      d[idx] = Cplx<R>{R(0), R(0)};
+      continue;
+    }
+    int seg = int(u * R(kMultSeg));
+    if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+    const R s = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+    const R* cs = cf + seg * (mp.deg + 1);
+    R S = cs[mp.deg];
+    for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * s + cs[nn];
+    R phi;
+    switch (p) {
+      case 1: phi = S / k2; break;
+      case 2: phi = S / k; break;
+      case 3: phi = S - log(u); break;
+      case 5: phi = S - u * u * log(u); break;
+      default: phi = S; break;
+    }
+    const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
+    const R G = sc * phi * iw2x[ix] * iw2y[ay] * iw2z[az];
+    Cplx<R> v = d[idx];
+    if (want_energy) {
+      const bool edge = (ix == 0) || ((mp.M[0] % 2 == 0) && ix == mp.Mxh - 1);
+      const R wm = edge ? R(0.5) : R(1);
+      e += double(wm * G * (v.x * v.x + v.y * v.y));
+    }
+    v.x *= G;
+    v.y *= G;
+    d[idx] = v;
+  }
+  if (!want_energy) return;
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+    part[size_t(c) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// ---- interpolation (gather of phi and forces) --------------------------------------
+// One thread per sorted atom.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W,
+// with grad_d W = (2 / h_d) dW/ds.  Writes in the original atom order.
+template <typename R, int P>
+__global__ void k_interp(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
+                         const uint64_t* __restrict__ scell, const R* __restrict__ sq, const int* __restrict__ sperm,
+                         WinCoef<R> wc, const R* __restrict__ grid, const double* __restrict__ zero_coef,
+                         const double* __restrict__ charges, R* __restrict__ phi, R* __restrict__ forces) {
+  const R two_hx = R(2.0 * g.M[0] / g.L[0]), two_hy = R(2.0 * g.M[1] / g.L[1]), two_hz = R(2.0 * g.M[2] / g.L[2]);
+  for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+    R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P];
+    window_weights<R, P>(st[a], wc, wx, dx);
+    window_weights<R, P>(st[nmax + a], wc, wy, dy);
+    window_weights<R, P>(st[2 * nmax + a], wc, wz, dz);
+    int cx, cy, cz;
+    unpack_cell(scell[a], cx, cy, cz);
+    int ix[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      int v = cx + i;
+      while (v >= g.M[0]) v -= g.M[0];
+      ix[i] = v;
+    }
+    const int orig = sperm[a];
+    R F0 = 0, F1 = 0, F2 = 0;
+    for (int c = 0; c < g.K; ++c) {
+      const R* gc = grid + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
+      R ph = 0, f0 = 0, f1 = 0, f2 = 0;
+      for (int k = 0; k < P; ++k) {
+        int z = cz + k;
+        while (z >= g.M[2]) z -= g.M[2];
+        for (int j = 0; j < P; ++j) {
+          int y = cy + j;
+          while (y >= g.M[1]) y -= g.M[1];
+          const R* row = gc + (int64_t(z) * g.M[1] + y) * g.Mxp;
+          R sx = 0, dsx = 0;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const R v = __ldg(row + ix[i]);
+            sx += v * wx[i];
+            dsx += v * dx[i];
+          }
+          const R wyz = wy[j] * wz[k];
+          ph += sx * wyz;
+          f0 += dsx * wyz;
+          f1 += sx * dy[j] * wz[k];
+          f2 += sx * wy[j] * dz[k];
+        }
+      }
+      const double Q = charges[2 * c];
+      ph += R(2.0 * zero_coef[c] * Q);
+      if (phi) phi[int64_t(c) * n + orig] = ph;
+      const R qc = sq[int64_t(c) * nmax + a];
+      F0 += qc * f0;
+      F1 += qc * f1;
+      F2 += qc * f2;
+    }
+    if (forces) {
+      forces[3 * int64_t(orig) + 0] = F0 * two_hx;
+      forces[3 * int64_t(orig) + 1] = F1 * two_hy;
+      forces[3 * int64_t(orig) + 2] = F2 * two_hz;
+    }
+  }
+}
+
+}  // namespace pswf

@@ -1,0 +1,37 @@
+// Launch interface between the host API (api.cu) and the stencil kernels,
+// which are instantiated per precision in launch.cu (compiled once with
+// PSWF_REAL=float and once with PSWF_REAL=double).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace pswf {
+
+struct LaunchCtx {
+  Geometry geo;
+  int64_t nmax = 0;        // capacity of the sorted atom arrays
+  int64_t n = 0;           // atoms of the last set_points
+  int ntiles = 0;
+  const int* tile_start = nullptr;
+  const void* st = nullptr;         // real [3][nmax]
+  const uint64_t* scell = nullptr;  // [nmax]
+  const void* sq = nullptr;         // real [K][nmax]
+  const int* sperm = nullptr;       // [nmax]
+  void* grid = nullptr;             // real [K][Mz][My][Mxp]
+  const double* zero_coef = nullptr;
+  const double* charges = nullptr;
+  const double* coef_w = nullptr;   // host [P][deg_w + 1]
+  int deg_w = 0;
+  cudaStream_t stream = nullptr;
+};
+
+// Each returns cudaSuccess or the launch error.
+cudaError_t launch_spread_float(const LaunchCtx& c);
+cudaError_t launch_spread_double(const LaunchCtx& c);
+cudaError_t launch_interp_float(const LaunchCtx& c, void* phi, void* forces);
+cudaError_t launch_interp_double(const LaunchCtx& c, void* phi, void* forces);
+
+}  // namespace pswf

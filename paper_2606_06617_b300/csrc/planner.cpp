@@ -1,0 +1,424 @@
+// Host planner for PSWF-LR: see planner.hpp.  Plain C++17, FP64.
+#include "planner.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+
+#include "pswf_lr.h"
+
+namespace pswf {
+
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+
+// Symmetric eigenproblem by cyclic Jacobi rotations (small dense matrices).
+void jacobi_eigen(std::vector<double> A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
+  evecs.assign(size_t(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) evecs[size_t(i) * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[size_t(i) * n + j] * A[size_t(i) * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[size_t(p) * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = A[size_t(p) * n + p], aqq = A[size_t(q) * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[size_t(k) * n + p], akq = A[size_t(k) * n + q];
+          A[size_t(k) * n + p] = cs * akp - sn * akq;
+          A[size_t(k) * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[size_t(p) * n + k], aqk = A[size_t(q) * n + k];
+          A[size_t(p) * n + k] = cs * apk - sn * aqk;
+          A[size_t(q) * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = evecs[size_t(k) * n + p], vkq = evecs[size_t(k) * n + q];
+          evecs[size_t(k) * n + p] = cs * vkp - sn * vkq;
+          evecs[size_t(k) * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+    }
+  }
+  evals.resize(n);
+  for (int i = 0; i < n; ++i) evals[i] = A[size_t(i) * n + i];
+}
+
+// P_n^{(m)}(x) for n <= nmax, m <= mmax (unnormalised Legendre), via
+// (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1} and
+// P^{(m)}_{n+1} = P^{(m)}_{n-1} + (2n+1) P^{(m-1)}_n.
+void legendre_table(double x, int nmax, int mmax, std::vector<double>& T) {
+  T.assign(size_t(mmax + 1) * (nmax + 1), 0.0);
+  auto at = [&](int m, int n) -> double& { return T[size_t(m) * (nmax + 1) + n]; };
+  at(0, 0) = 1.0;
+  if (nmax >= 1) at(0, 1) = x;
+  for (int n = 1; n < nmax; ++n) at(0, n + 1) = ((2.0 * n + 1.0) * x * at(0, n) - n * at(0, n - 1)) / (n + 1.0);
+  for (int m = 1; m <= mmax; ++m) {
+    if (nmax >= 1) at(m, 1) = (m == 1) ? 1.0 : 0.0;
+    for (int n = 1; n < nmax; ++n) at(m, n + 1) = at(m, n - 1) + (2.0 * n + 1.0) * at(m - 1, n);
+  }
+}
+
+// Chebyshev interpolation of f on [-1, 1] at n nodes; returns coefficients.
+std::vector<double> cheb_fit(const std::function<double(double)>& f, int n) {
+  std::vector<double> fx(n), a(n, 0.0);
+  for (int k = 0; k < n; ++k) fx[k] = f(std::cos(kPi * (k + 0.5) / n));
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += fx[k] * std::cos(kPi * j * (k + 0.5) / n);
+    a[j] = 2.0 * s / n;
+  }
+  a[0] *= 0.5;
+  return a;
+}
+
+// Chebyshev coefficients a[0..deg] -> monomial coefficients in s.
+std::vector<double> cheb_to_monomial(const std::vector<double>& a, int deg) {
+  std::vector<double> out(deg + 1, 0.0);
+  std::vector<double> tprev(deg + 1, 0.0), tcur(deg + 1, 0.0), tnext(deg + 1, 0.0);
+  tprev[0] = 1.0;               // T_0
+  if (deg >= 1) tcur[1] = 1.0;  // T_1
+  for (int i = 0; i <= deg; ++i) out[i] += a[0] * tprev[i];
+  if (deg >= 1)
+    for (int i = 0; i <= deg; ++i) out[i] += a[1] * tcur[i];
+  for (int j = 2; j <= deg; ++j) {
+    std::fill(tnext.begin(), tnext.end(), 0.0);
+    for (int i = 0; i < deg; ++i) tnext[i + 1] += 2.0 * tcur[i];
+    for (int i = 0; i <= deg; ++i) tnext[i] -= tprev[i];
+    for (int i = 0; i <= deg; ++i) out[i] += a[j] * tnext[i];
+    tprev.swap(tcur);
+    tcur.swap(tnext);
+  }
+  return out;
+}
+
+// Degree kept by the paper's filter (drop trailing |a_n| <= 0.01 eps max|a|)
+// over a family of expansions, max|a| taken over the whole family so that
+// pieces where the function is tiny do not chase round-off.
+int family_degree(const std::vector<std::vector<double>>& fam, double eps) {
+  double amax = 0.0;
+  for (const auto& a : fam)
+    for (double v : a) amax = std::max(amax, std::fabs(v));
+  int d = 1;
+  for (const auto& a : fam)
+    for (int j = 0; j < int(a.size()); ++j)
+      if (std::fabs(a[j]) > 0.01 * eps * amax) d = std::max(d, j);
+  return d;
+}
+
+int fail(Plan& plan, int code, const char* msg) {
+  plan.error = msg;
+  return code;
+}
+}  // namespace
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 1; k < n; ++k) {
+      const double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int64_t next_fft_size(int64_t n) {
+  if (n < 1) n = 1;
+  for (int64_t m = n;; ++m) {
+    int64_t r = m;
+    for (int f : {2, 3, 5, 7})
+      while (r % f == 0) r /= f;
+    if (r == 1) return m;
+  }
+}
+
+Prolate::Prolate(double c_) : c(c_) {
+  // Even Legendre coefficients only (psi_0 is even).
+  const int N = std::max(30, int(1.2 * c) + 30);
+  auto alpha = [](int n) -> double {
+    if (n < 0) return 0.0;
+    return (n + 1.0) / std::sqrt((2.0 * n + 1.0) * (2.0 * n + 3.0));
+  };
+  // Prolate operator -(d/dx)(1-x^2)(d/dx) + c^2 x^2 in the basis Pbar_{2k}:
+  // x Pbar_n = alpha_n Pbar_{n+1} + alpha_{n-1} Pbar_{n-1}, so the matrix has
+  // diagonal n(n+1) + c^2 (alpha_n^2 + alpha_{n-1}^2) and off-diagonal
+  // (n, n+2) entries c^2 alpha_n alpha_{n+1}.
+  std::vector<double> A(size_t(N) * N, 0.0);
+  for (int k = 0; k < N; ++k) {
+    const int n = 2 * k;
+    A[size_t(k) * N + k] = n * (n + 1.0) + c * c * (alpha(n) * alpha(n) + alpha(n - 1) * alpha(n - 1));
+    if (k + 1 < N) {
+      const double e = c * c * alpha(n) * alpha(n + 1);
+      A[size_t(k) * N + k + 1] = e;
+      A[size_t(k + 1) * N + k] = e;
+    }
+  }
+  std::vector<double> ev, V;
+  jacobi_eigen(A, N, ev, V);
+  int imin = 0;
+  for (int i = 1; i < N; ++i)
+    if (ev[i] < ev[imin]) imin = i;
+  chi = ev[imin];
+  beta.resize(N);
+  for (int k = 0; k < N; ++k) beta[k] = V[size_t(k) * N + imin];
+  double s = 0.0;
+  {
+    std::vector<double> T;
+    legendre_table(0.0, 2 * N, 0, T);
+    for (int k = 0; k < N; ++k) s += beta[k] * std::sqrt(2 * k + 0.5) * T[2 * k];
+  }
+  for (double& b : beta) b /= s;  // psi(0) = 1
+  // lambda_0 = int_{-1}^{1} psi = beta_0 int Pbar_0 = beta_0 sqrt(2)
+  lambda0 = beta[0] * std::sqrt(2.0);
+  C0 = 0.5 * lambda0;
+}
+
+double Prolate::eval(double x, int m) const {
+  const int N = int(beta.size());
+  std::vector<double> T;
+  legendre_table(x, 2 * N, m, T);
+  const double* Pm = T.data() + size_t(m) * (2 * N + 1);
+  double s = 0.0;
+  for (int k = 0; k < N; ++k) s += beta[k] * std::sqrt(2 * k + 0.5) * Pm[2 * k];
+  return s;
+}
+
+double Prolate::integral(double a, double b, int power) const {
+  static thread_local std::vector<double> gx, gw;
+  if (gx.size() != 64) gauss_legendre(64, gx, gw);
+  const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+  double s = 0.0;
+  for (int i = 0; i < 64; ++i) {
+    const double t = mid + half * gx[i];
+    s += gw[i] * std::pow(t, power) * eval(t);
+  }
+  return s * half;
+}
+
+// Smooth parts of Eq. (PhiH) after the substitution x = c s, reading C1
+// (psi_0(x/c) = 0 for x > c), u = k r_c / c, with
+//   I(u) = int_0^u psi, J1(u) = int_u^1 s psi, J3(u) = int_u^1 s^3 psi,
+//   H(u) = int_u^1 (psi(s) - 1) / s ds:
+//   p=1: Phi = 4 pi / k^2           * psi(u)
+//   p=2: Phi = 2 pi^2 / k            * (1 - I/C0)
+//   p=3: Phi = 4 pi                  * (-log u + H)
+//   p=4: Phi = pi^2 c / r_c          * (J1/C0 - u (1 - I/C0))
+//   p=5: Phi = -2 pi c^2 / (3 r_c^2) * (u^2 (-log u + H) - J1)
+//   p=6: Phi = pi^2 c^3/(12 r_c^3)   * (u^3 (1 - I/C0) - 3 u^2 J1/(2 C0) + J3/(2 C0))
+// This function returns the log-free part (H in place of -log u + H).
+double mult_smooth(const Prolate& ps, int p, double u) {
+  const double C0 = ps.C0;
+  auto I = [&]() { return u > 0 ? ps.integral(0.0, u, 0) : 0.0; };
+  auto J1 = [&]() { return u < 1 ? ps.integral(u, 1.0, 1) : 0.0; };
+  auto J3 = [&]() { return u < 1 ? ps.integral(u, 1.0, 3) : 0.0; };
+  auto H = [&]() {
+    if (u >= 1) return 0.0;
+    static thread_local std::vector<double> gx, gw;
+    if (gx.size() != 64) gauss_legendre(64, gx, gw);
+    const double half = 0.5 * (1.0 - u), mid = 0.5 * (1.0 + u);
+    double s = 0.0;
+    for (int i = 0; i < 64; ++i) {
+      const double t = mid + half * gx[i];
+      s += gw[i] * (ps.eval(t) - 1.0) / t;
+    }
+    return s * half;
+  };
+  switch (p) {
+    case 1: return ps.eval(u);
+    case 2: return 1.0 - I() / C0;
+    case 3: return H();
+    case 4: return J1() / C0 - u * (1.0 - I() / C0);
+    case 5: return u * u * H() - J1();
+    case 6: return u * u * u * (1.0 - I() / C0) - 1.5 * u * u * J1() / C0 + 0.5 * J3() / C0;
+    default: return 0.0;
+  }
+}
+
+int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan& plan) {
+  plan = Plan();
+  plan.opt = opt;
+  for (int d = 0; d < 3; ++d) {
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(plan, PSWF_EINVAL, "box edges must be positive and finite");
+    plan.box[d] = box[d];
+  }
+  if (K < 1 || K > kMaxK) return fail(plan, PSWF_EINVAL, "number of channels must be in 1..64");
+  plan.K = K;
+  plan.p.assign(p, p + K);
+  for (int k = 0; k < K; ++k)
+    if (p[k] < 1 || p[k] > 6) return fail(plan, PSWF_EINVAL, "channel exponent p must be in 1..6");
+  if (!(opt.r_c > 0.0) || !std::isfinite(opt.r_c)) return fail(plan, PSWF_EINVAL, "r_c must be positive");
+  if (!(opt.tol > 0.0 && opt.tol < 1.0)) return fail(plan, PSWF_EINVAL, "tol must be in (0, 1)");
+  if (opt.precision != 0 && opt.precision != 1) return fail(plan, PSWF_EINVAL, "precision must be 0 (fp32) or 1 (fp64)");
+  plan.tol = opt.tol;
+  plan.r_c = opt.r_c;
+  // ---- Parameter selection: eps_band = eps_grid = eps_spread = tol / 3 ----
+  plan.c = opt.c > 0 ? opt.c : std::log(3.0 / opt.tol);
+  if (plan.c > 60.0) return fail(plan, PSWF_EINVAL, "c must be <= 60");
+  plan.k_c = plan.c / plan.r_c;
+  const double eta_t = opt.eta > 0 ? opt.eta : 0.5;
+  if (eta_t >= 1.0) return fail(plan, PSWF_EINVAL, "eta must be in (0, 1)");
+  for (int d = 0; d < 3; ++d) {
+    const int64_t M = opt.grid[d] > 0 ? opt.grid[d]
+                                      : next_fft_size(int64_t(std::ceil(box[d] * plan.k_c / (eta_t * kPi))));
+    if (M < 2 || M > 4096) return fail(plan, PSWF_EINVAL, "grid size per dimension must be in 2..4096");
+    plan.M[d] = int(M);
+    plan.h[d] = box[d] / double(M);
+  }
+  plan.eta = 0.0;
+  for (int d = 0; d < 3; ++d) plan.eta = std::max(plan.eta, plan.h[d] * plan.k_c / kPi);
+  if (plan.eta >= 1.0) return fail(plan, PSWF_ETOLUNREACHABLE, "grid too coarse: h k_c / pi >= 1 (Nyquist criterion)");
+  plan.moll = Prolate(plan.c);
+  plan.est_band = std::fabs(plan.moll.eval(1.0));
+  // Window bandwidth: the largest c_w whose main lobe does not alias onto the
+  // band |k| < k_c: c_w = P pi (1 - eta / 2).  Spreading-error estimate
+  // 10 psi_0^{c_w}(1) / eta (calibrated against the direct-sum oracle).
+  auto cw_for = [&](int P) { return opt.c_w > 0 ? opt.c_w : P * kPi * (1.0 - 0.5 * plan.eta); };
+  auto est_for = [&](const Prolate& w) { return 10.0 * std::fabs(w.eval(1.0)) / plan.eta; };
+  if (opt.P > 0) {
+    if (opt.P < 2 || opt.P > kMaxP) return fail(plan, PSWF_EINVAL, "P must be in 2..16");
+    plan.P = opt.P;
+    plan.c_w = cw_for(opt.P);
+    if (!(plan.c_w > 0.0) || plan.c_w > 80.0) return fail(plan, PSWF_EINVAL, "c_w must be in (0, 80]");
+    plan.win = (plan.c_w == plan.c) ? plan.moll : Prolate(plan.c_w);
+  } else {
+    for (int P = 2; P <= kMaxP; ++P) {
+      const double cw = cw_for(P);
+      if (!(cw > 0.0) || cw > 80.0) return fail(plan, PSWF_EINVAL, "c_w must be in (0, 80]");
+      plan.P = P;
+      plan.c_w = cw;
+      plan.win = Prolate(cw);
+      if (est_for(plan.win) <= opt.tol / 3.0) break;
+    }
+  }
+  plan.est_spread = est_for(plan.win);
+  for (int d = 0; d < 3; ++d) {
+    plan.omega[d] = plan.P * plan.h[d] / 2.0;
+    if (plan.omega[d] * plan.k_c / plan.c_w >= 1.0)
+      return fail(plan, PSWF_EINVAL, "window band c_w / omega does not cover k_c");
+  }
+  plan.V = box[0] * box[1] * box[2];
+  plan.dV = plan.V / (double(plan.M[0]) * plan.M[1] * plan.M[2]);
+  const double eps_poly = opt.precision == 1 ? 1e-15 : 1e-9;
+  // ---- window pieces: W_j(t) = psi^{c_w}((2j - P + 2t)/P), s = 2t - 1 ----
+  {
+    const int nfit = 41;
+    std::vector<std::vector<double>> cheb(plan.P);
+    const double P = plan.P;
+    for (int j = 0; j < plan.P; ++j)
+      cheb[j] = cheb_fit([&](double s) { return plan.win.eval((2.0 * j - P + 1.0 + s) / P); }, nfit);
+    const int deg = std::min(family_degree(cheb, eps_poly), kMaxDeg);
+    plan.deg_w = deg;
+    plan.coef_w.assign(size_t(plan.P) * (deg + 1), 0.0);
+    for (int j = 0; j < plan.P; ++j) {
+      const auto mono = cheb_to_monomial(cheb[j], deg);
+      for (int n = 0; n <= deg; ++n) plan.coef_w[size_t(j) * (deg + 1) + n] = mono[n];
+    }
+  }
+  // ---- multiplier pieces ----
+  {
+    const int nfit = 33;
+    std::vector<std::vector<double>> cheb(size_t(K) * kMultSeg);
+    int deg = 1;
+    for (int k = 0; k < K; ++k) {
+      std::vector<std::vector<double>> fam(kMultSeg);
+      for (int i = 0; i < kMultSeg; ++i) {
+        const double a = double(i) / kMultSeg, b = double(i + 1) / kMultSeg;
+        fam[i] = cheb_fit([&](double s) { return mult_smooth(plan.moll, plan.p[k], a + (b - a) * 0.5 * (s + 1.0)); }, nfit);
+        cheb[size_t(k) * kMultSeg + i] = fam[i];
+      }
+      deg = std::max(deg, family_degree(fam, eps_poly));
+    }
+    deg = std::min(deg, kMaxMultDeg);
+    plan.deg_m = deg;
+    plan.coef_m.assign(size_t(K) * kMultSeg * (deg + 1), 0.0);
+    for (size_t i = 0; i < cheb.size(); ++i) {
+      const auto mono = cheb_to_monomial(cheb[i], deg);
+      for (int n = 0; n <= deg; ++n) plan.coef_m[i * (deg + 1) + n] = mono[n];
+    }
+  }
+  // ---- per-channel constants ----
+  const double c = plan.c, rc = plan.r_c, C0 = plan.moll.C0, lam = plan.moll.lambda0, V = plan.V;
+  plan.mult_scale.resize(K);
+  plan.self_coef.resize(K);
+  plan.zero_coef.resize(K);
+  const double d2 = plan.moll.eval(0.0, 2), d4 = plan.moll.eval(0.0, 4), d6 = plan.moll.eval(0.0, 6);
+  for (int k = 0; k < K; ++k) {
+    switch (plan.p[k]) {
+      case 1:
+        plan.mult_scale[k] = 4.0 * kPi;
+        plan.self_coef[k] = 1.0 / (2.0 * C0 * rc);
+        // -(2 pi / V) int_0^{r_c} r (1 - G_1) dr = -(pi r_c^2 / (V C0)) int_0^1 x^2 psi
+        plan.zero_coef[k] = -kPi * rc * rc / (V * C0) * plan.moll.integral(0.0, 1.0, 2);
+        break;
+      case 2:
+        plan.mult_scale[k] = 2.0 * kPi * kPi;
+        plan.self_coef[k] = -d2 / (4.0 * rc * rc);
+        plan.zero_coef[k] = -2.0 * kPi / V * rc * C0;
+        break;
+      case 3:
+        plan.mult_scale[k] = 2.0 * kPi * lam / C0;
+        plan.self_coef[k] = -d2 / (6.0 * C0 * rc * rc * rc);
+        plan.zero_coef[k] = 2.0 * kPi / V * (std::log(c / rc) + mult_smooth(plan.moll, 3, 0.0));
+        break;
+      case 4:
+        plan.mult_scale[k] = kPi * kPi * c / rc;
+        plan.self_coef[k] = d4 / (48.0 * std::pow(rc, 4));
+        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 4, 0.0) / (2.0 * V);
+        break;
+      case 5:
+        plan.mult_scale[k] = -kPi * lam * c * c / (3.0 * C0 * rc * rc);
+        plan.self_coef[k] = d4 / (90.0 * C0 * std::pow(rc, 5));
+        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 5, 0.0) / (2.0 * V);
+        break;
+      case 6:
+        plan.mult_scale[k] = kPi * kPi * c * c * c / (12.0 * rc * rc * rc);
+        plan.self_coef[k] = -d6 / (1440.0 * std::pow(rc, 6));
+        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 6, 0.0) / (2.0 * V);
+        break;
+    }
+  }
+  // ---- W-hat^-2 tables (indexed by |frequency|) ----
+  for (int d = 0; d < 3; ++d) {
+    const int nf = plan.M[d] / 2 + 1;
+    plan.iw2[d].assign(nf, 0.0);
+    for (int m = 0; m < nf; ++m) {
+      const double kd = 2.0 * kPi * m / box[d];
+      const double arg = plan.omega[d] * kd / plan.c_w;
+      if (arg <= 1.0) {
+        const double what = plan.omega[d] * plan.win.lambda0 * plan.win.eval(arg);
+        plan.iw2[d][m] = 1.0 / (what * what);
+      }
+    }
+  }
+  return PSWF_OK;
+}
+
+}  // namespace pswf

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libpswf_lr.so (include/pswf_lr.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  PyTorch supplies device memory (outputs and the plan workspace) and
+the current CUDA stream.  If the library is missing this module raises on
+first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
+
+PSWF_FLAG_BACKWARD = 1
+
+
+class PswfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class PswfOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("r_c", ctypes.c_double), ("c", ctypes.c_double),
+                ("c_w", ctypes.c_double), ("eta", ctypes.c_double), ("P", ctypes.c_int),
+                ("grid", ctypes.c_int * 3), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class PswfInfo(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("c_w", ctypes.c_double), ("r_c", ctypes.c_double),
+                ("k_c", ctypes.c_double), ("eta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("est_err_spread", ctypes.c_double), ("est_err_band", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("C0", ctypes.c_double),
+                ("box", ctypes.c_double * 3), ("h", ctypes.c_double * 3), ("grid", ctypes.c_int * 3),
+                ("P", ctypes.c_int), ("K", ctypes.c_int), ("precision", ctypes.c_int),
+                ("deg_window", ctypes.c_int), ("deg_mult", ctypes.c_int), ("flags", ctypes.c_int),
+                ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+# name -> (argtypes, restype); mirrors include/pswf_lr.h
+SIGNATURES = {
+    "pswf_opts_default": ([ctypes.POINTER(PswfOpts)], None),
+    "pswf_plan_params": ([_dp, ctypes.c_int, _ip, ctypes.POINTER(PswfOpts), ctypes.POINTER(PswfInfo)], ctypes.c_int),
+    "pswf_plan_create": ([_dp, _i64, ctypes.c_int, _ip, ctypes.POINTER(PswfOpts), _vp, ctypes.POINTER(_vp)],
+                         ctypes.c_int),
+    "pswf_plan_info": ([_vp, ctypes.POINTER(PswfInfo)], ctypes.c_int),
+    "pswf_plan_set_workspace": ([_vp, _vp, _i64], ctypes.c_int),
+    "pswf_plan_set_stream": ([_vp, _vp], ctypes.c_int),
+    "pswf_set_points": ([_vp, _i64, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pswf_execute": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "pswf_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "pswf_self_energy": ([_vp, _dp], ctypes.c_int),
+    "pswf_sync": ([_vp], ctypes.c_int),
+    "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "pswf_plan_destroy": ([_vp], None),
+    "pswf_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "pswf_plan_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
+}
+
+
+def lib():
+    """Loads libpswf_lr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_2606_06617_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(status: int, handle=None):
+    if status == 0:
+        return
+    L = lib()
+    msg = L.pswf_strerror(status).decode()
+    if handle:
+        buf = ctypes.create_string_buffer(512)
+        L.pswf_plan_last_error(handle, buf, 512)
+        if buf.value:
+            msg = f"{msg}: {buf.value.decode()}"
+    raise PswfError(status, msg)
+
+
+def make_opts(r_c: float, tol: float = 1e-5, c: float = 0.0, c_w: float = 0.0, eta: float = 0.0,
+              P: int = 0, grid=None, precision: int = 0, flags: int = 0) -> PswfOpts:
+    o = PswfOpts()
+    lib().pswf_opts_default(ctypes.byref(o))
+    o.tol, o.r_c, o.c, o.c_w, o.eta, o.P = tol, r_c, c, c_w, eta, P
+    if grid is not None:
+        g = [int(grid)] * 3 if np.isscalar(grid) else [int(x) for x in grid]
+        for d in range(3):
+            o.grid[d] = g[d]
+    o.precision, o.flags = precision, flags
+    return o
+
+
+def _info_dict(info: PswfInfo) -> dict:
+    out = {}
+    for name, _ in PswfInfo._fields_:
+        v = getattr(info, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
+
+
+def plan_params(box, ps, **opts) -> dict:
+    """Host-only parameter selection (no GPU).  ``opts`` as make_opts."""
+    L = lib()
+    box_a = (ctypes.c_double * 3)(*[float(b) for b in box])
+    p_a = (ctypes.c_int * len(ps))(*[int(p) for p in ps])
+    o = make_opts(**opts)
+    info = PswfInfo()
+    _check(L.pswf_plan_params(box_a, len(ps), p_a, ctypes.byref(o), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+class Plan:
+    """One periodic system: PSWF-LR plan with a torch-allocated workspace.
+
+    Calls enqueue on the current torch CUDA stream of the plan's device."""
+
+    def __init__(self, box, n_max: int, ps, r_c: float, *, tol: float = 1e-5, c: float = 0.0,
+                 c_w: float = 0.0, eta: float = 0.0, P: int = 0, grid=None, precision: int = 0,
+                 flags: int = 0, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PSWF-LR needs a CUDA device")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.K = len(ps)
+        self.ps = tuple(int(p) for p in ps)
+        self.box = tuple(float(b) for b in box)
+        self.dtype = torch.float64 if precision == 1 else torch.float32
+        L = lib()
+        box_a = (ctypes.c_double * 3)(*self.box)
+        p_a = (ctypes.c_int * self.K)(*self.ps)
+        o = make_opts(r_c=r_c, tol=tol, c=c, c_w=c_w, eta=eta, P=P, grid=grid, precision=precision, flags=flags)
+        h = _vp()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            _check(L.pswf_plan_create(box_a, int(n_max), self.K, p_a, ctypes.byref(o), _vp(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_max = int(n_max)
+        info = PswfInfo()
+        _check(L.pswf_plan_info(self._h, ctypes.byref(info)), self._h)
+        self.info = _info_dict(info)
+        nbytes = max(int(self.info["workspace_bytes"]), 256)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self._ws.data_ptr() + 255) & ~255
+        with torch.cuda.device(self.device):
+            _check(L.pswf_plan_set_workspace(self._h, _vp(aligned), nbytes), self._h)
+        self.n = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().pswf_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def _stream(self):
+        import torch
+        _check(lib().pswf_plan_set_stream(self._h, _vp(torch.cuda.current_stream(self.device).cuda_stream)), self._h)
+
+    def set_points(self, pos, q):
+        """pos: cuda tensor [n, 3] float32/float64; q: cuda tensor [K, n]."""
+        import torch
+        if not (pos.is_cuda and q.is_cuda) or pos.device != self.device or q.device != self.device:
+            raise ValueError("pos and q must be CUDA tensors on the plan's device")
+        if pos.dtype not in (torch.float32, torch.float64):
+            pos = pos.double()
+        pos = pos.contiguous()
+        q = q.to(self.dtype).contiguous()
+        n = pos.shape[0]
+        if pos.shape != (n, 3) or q.shape != (self.K, n):
+            raise ValueError("pos must be [n, 3] and q [K, n]")
+        self._stream()
+        _check(lib().pswf_set_points(self._h, n, _vp(pos.data_ptr()), 1 if pos.dtype == torch.float64 else 0,
+                                     _vp(q.data_ptr())), self._h)
+        self._keep = (pos, q)
+        self.n = n
+
+    def execute(self, energy: bool = True, phi: bool = True, forces: bool = True, out=None):
+        """Returns (energy [K+1] float64, phi [K, n] or None, forces [n, 3] or None) on the device."""
+        import torch
+        if self.n is None:
+            raise PswfError(-8, "execute before set_points")
+        n = self.n
+        if out is not None:
+            e, ph, f = out
+        else:
+            e = torch.empty(self.K + 1, dtype=torch.float64, device=self.device) if energy else None
+            ph = torch.empty(self.K, n, dtype=self.dtype, device=self.device) if phi else None
+            f = torch.empty(n, 3, dtype=self.dtype, device=self.device) if forces else None
+        ptr = lambda t: _vp(t.data_ptr() if (t is not None and t.numel() > 0) else 0)
+        self._stream()
+        _check(lib().pswf_execute(self._h, ptr(e), ptr(ph), ptr(f)), self._h)
+        return e, ph, f
+
+    def backward(self, g_energy=None, g_phi=None, g_forces=None, grad_q: bool = True, grad_pos: bool = True):
+        import torch
+        n = self.n
+        gq = torch.empty(self.K, n, dtype=self.dtype, device=self.device) if grad_q else None
+        gr = torch.empty(n, 3, dtype=self.dtype, device=self.device) if grad_pos else None
+        ge = g_energy.to(torch.float64).contiguous() if g_energy is not None else None
+        gp = g_phi.to(self.dtype).contiguous() if g_phi is not None else None
+        gf = g_forces.to(self.dtype).contiguous() if g_forces is not None else None
+        ptr = lambda t: _vp(t.data_ptr() if (t is not None and t.numel() > 0) else 0)
+        self._stream()
+        _check(lib().pswf_backward(self._h, ptr(ge), ptr(gp), ptr(gf), ptr(gq), ptr(gr)), self._h)
+        return gq, gr
+
+    def self_energy(self) -> np.ndarray:
+        out = (ctypes.c_double * self.K)()
+        self._stream()
+        _check(lib().pswf_self_energy(self._h, out), self._h)
+        return np.array(out[:])
+
+    def sync(self):
+        _check(lib().pswf_sync(self._h), self._h)
+
+    def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True):
+        """End-to-end from host arrays (float64); returns numpy (energy, phi, forces)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = pos.shape[0]
+        e = np.empty(self.K + 1)
+        ph = np.empty((self.K, n)) if phi else None
+        f = np.empty((n, 3)) if forces else None
+        dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
+        self._stream()
+        _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)
+        return e, ph, f

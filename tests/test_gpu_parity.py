@@ -1,0 +1,151 @@
+"""Parity of the CUDA path (through the C-ABI) with the O1 oracle.
+
+Same seeded inputs and the same explicit parameters (c, c_w, P, grid) on both
+sides; FP32 path within 2e-6 relative RMS on phi and forces (and relative
+energy), FP64 path within 2e-9."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import rel_rms
+from gpu_helpers import TOL_FP32, TOL_FP64, run_gpu, run_oracle, window_cw
+from paper_2606_06617_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+C_TOL = math.log(3.0 / 1e-5)
+
+
+def _compare(g, o, tol, what=""):
+    for c in range(len(o["E_ch"])):
+        assert abs(g["E_ch"][c] - o["E_ch"][c]) <= tol * max(abs(o["E_ch"][c]), 1e-300) + 1e-13, \
+            (what, c, g["E_ch"], o["E_ch"])
+    assert rel_rms(g["phi"], o["phi"]) <= tol, (what, rel_rms(g["phi"], o["phi"]))
+    assert rel_rms(g["F"], o["F"]) <= tol, (what, rel_rms(g["F"], o["F"]))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP32), (1, TOL_FP64)])
+def test_random_charges_24(precision, tol):
+    """64 charges +-1 in L = 12, p = 1, P = 6, grid 24^3."""
+    s = wl.random_charges()
+    M = (24, 24, 24)
+    cw = window_cw(s.box, M, 6, C_TOL, 4.0)
+    g = run_gpu(s, 4.0, 6, M, C_TOL, cw, precision=precision)
+    o = run_oracle(s, 4.0, 6, M, C_TOL, cw)
+    _compare(g, o, tol, "random_charges")
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP32), (1, TOL_FP64)])
+def test_water_3000(precision, tol):
+    """1000 three-site molecules, L = 31, channels p = 1 and p = 6 (non-neutral),
+    grid 64^3, P = 8."""
+    s = wl.water_box()
+    M = (64, 64, 64)
+    cw = window_cw(s.box, M, 8, C_TOL, 4.0)
+    g = run_gpu(s, 4.0, 8, M, C_TOL, cw, precision=precision)
+    o = run_oracle(s, 4.0, 8, M, C_TOL, cw)
+    _compare(g, o, tol, "water")
+
+
+@pytest.mark.parametrize("P", [4, 5, 7])
+def test_ragged_box_all_exponents(P):
+    """Orthorhombic box with odd / mixed grid sizes (ragged tiles), six channels
+    p = 1..6, atoms outside the primary cell (wrapped)."""
+    rng = np.random.default_rng(7)
+    box = (13.0, 17.5, 11.0)
+    s = wl.random_system(300, box, (1, 2, 3, 4, 5, 6), seed=11, neutral=True)
+    s.pos = s.pos + rng.integers(-3, 4, size=s.pos.shape) * np.asarray(box)   # far images
+    M = (27, 35, 21)
+    c = 11.0
+    cw = window_cw(box, M, P, c, 4.5)
+    g = run_gpu(s, 4.5, P, M, c, cw)
+    o = run_oracle(s, 4.5, P, M, c, cw)
+    _compare(g, o, TOL_FP32, f"ragged P={P}")
+
+
+def test_float32_positions_small_grid():
+    """float32 positions, grid smaller than the stencil tile (M = 6 < 8) and
+    P = 4: the stencil wraps over the whole grid."""
+    s = wl.random_system(40, (5.0, 5.0, 6.0), (1, 6), seed=3, neutral=False)
+    s.pos = s.pos.astype(np.float32).astype(np.float64)
+    M = (6, 6, 8)
+    c = 6.0
+    cw = window_cw(s.box, M, 4, c, 2.5)
+    g = run_gpu(s, 2.5, 4, M, c, cw, pos_dtype="float32")
+    o = run_oracle(s, 2.5, 4, M, c, cw)
+    _compare(g, o, TOL_FP32, "small grid")
+
+
+def test_single_atom_and_empty():
+    """n = 1 (self-interaction through the periodic images only; its force is
+    pure discretisation noise, so it is compared on an absolute scale) and n = 0."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    s = wl.random_system(1, (9.0, 9.0, 9.0), (1,), seed=5, neutral=False)
+    M = (18, 18, 18)
+    cw = window_cw(s.box, M, 6, 10.0, 3.0)
+    g = run_gpu(s, 3.0, 6, M, 10.0, cw)
+    o = run_oracle(s, 3.0, 6, M, 10.0, cw)
+    assert abs(g["E"] - o["E"]) <= TOL_FP32 * abs(o["E"])
+    assert rel_rms(g["phi"], o["phi"]) <= TOL_FP32
+    scale = abs(s.q[0, 0] * o["phi"][0, 0]) / min(s.box)      # force scale q phi / L
+    assert np.max(np.abs(g["F"] - o["F"])) <= TOL_FP32 * scale
+    plan = lr.Plan(s.box, 16, s.ps, 3.0, grid=M, P=6)
+    dev = torch.device("cuda", 0)
+    plan.set_points(torch.zeros(0, 3, device=dev, dtype=torch.float64), torch.zeros(1, 0, device=dev))
+    e, phi, f = plan.execute()
+    plan.sync()
+    assert float(e[-1]) == 0.0 and phi.numel() == 0 and f.numel() == 0
+
+
+def test_energy_is_half_q_phi():
+    """Quadratic form: E_k = 1/2 sum_i q_i phi_i for neutral channels (GPU only)."""
+    s = wl.random_system(500, (14.0, 14.0, 14.0), (1, 2, 4, 6), seed=2, neutral=True)
+    M = (28, 28, 28)
+    cw = window_cw(s.box, M, 6, C_TOL, 4.0)
+    g = run_gpu(s, 4.0, 6, M, C_TOL, cw)
+    half = 0.5 * np.sum(s.q * g["phi"], axis=1)
+    np.testing.assert_allclose(g["E_ch"], half, rtol=2e-6)
+
+
+def test_nonfinite_positions_reported():
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    plan = lr.Plan((10.0, 10.0, 10.0), 8, (1,), 3.0, grid=16, P=4)
+    pos = torch.rand(8, 3, device=dev, dtype=torch.float64) * 10
+    pos[3, 1] = float("nan")
+    plan.set_points(pos, torch.randn(1, 8, device=dev))
+    with pytest.raises(lr.PswfError) as ei:
+        plan.sync()
+    assert ei.value.status == -6
+    plan.set_points(torch.rand(8, 3, device=dev, dtype=torch.float64), torch.randn(1, 8, device=dev))
+    plan.execute()
+    plan.sync()
+
+
+def test_compute_host_matches_device_path():
+    """pswf_compute_host (host buffers, copies inside) equals the device path."""
+    s = wl.water_box(n_side=6, L=18.6, seed=1)
+    M = (36, 36, 36)
+    cw = window_cw(s.box, M, 6, C_TOL, 4.0)
+    g = run_gpu(s, 4.0, 6, M, C_TOL, cw)
+    e, phi, f = g["plan"].compute_host(s.pos, s.q)
+    np.testing.assert_allclose(e[:-1], g["E_ch"], rtol=1e-6)
+    assert rel_rms(phi, g["phi"]) < 1e-6 and rel_rms(f, g["F"]) < 1e-6
+
+
+def test_self_energy_matches_oracle():
+    """E_self from the device FP64 reduction of the (FP32-stored) charges."""
+    s = wl.water_box(n_side=5, L=15.5, seed=2)
+    M = (32, 32, 32)
+    cw = window_cw(s.box, M, 6, C_TOL, 4.0)
+    g = run_gpu(s, 4.0, 6, M, C_TOL, cw)
+    o = run_oracle(s, 4.0, 6, M, C_TOL, cw)
+    q32 = s.q.astype(np.float32).astype(np.float64)
+    from oracle.mollifiers import Mollifier
+    m = Mollifier(C_TOL, 4.0)
+    ref32 = [m.self_coef(p) * float(np.sum(q32[c] ** 2)) for c, p in enumerate(s.ps)]
+    np.testing.assert_allclose(g["plan"].self_energy(), ref32, rtol=1e-12)
+    np.testing.assert_allclose(g["plan"].self_energy(), o["self"], rtol=1e-7)
