@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the PSWF-LR reciprocal-space evaluation on B300.
+
+One step = the whole hot path on one batch of synthetic input:
+pswf_set_points (bin/sort) + pswf_execute (spread, batched R2C FFT,
+multiplier + energy reduction, batched C2R FFT, gather of potentials and
+forces).  Default workload: the large ionic melt (4,194,304 atoms, cubic
+L = 350 A, K = 4 channels p = 1, 2, 4, 6, grid 384^3, stencil P = 8), FP32
+with FP64 tables and reductions.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload melt|water]
+
+Under torchrun each rank evaluates its own replica (seed = rank): the single
+system does not shard, so N > 1 is N independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Workloads: box, atoms, channels, mollifier and grid parameters.
+WORKLOADS = {
+    "melt": dict(name="ionic_melt_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0, tol=5e-6, P=8,
+                 grid=384),
+    "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=1e-5, P=8, grid=64),
+}
+METRIC = "LR energy+force atoms/s"
+
+
+def make_system(wk: str, seed: int):
+    from paper_2606_06617_b300 import workloads as wl
+    w = WORKLOADS[wk]
+    if wk == "melt":
+        return wl.ionic_melt(w["N"], w["L"], seed=seed)
+    return wl.water_box(seed=seed)
+
+
+def algorithmic_bytes(w, K: int, n: int, rs: int = 4) -> dict:
+    """Minimum HBM bytes per launch of each of our stages (FP32 path)."""
+    M = w["grid"] ** 3
+    Mh = (w["grid"] // 2 + 1) * w["grid"] ** 2
+    # in-sphere half-spectrum modes (|k| < k_c): the multiplier must read only these
+    c = math.log(3.0 / w["tol"])
+    kc = c / w["r_c"]
+    m = np.arange(w["grid"])
+    m = np.where(m <= w["grid"] // 2, m, m - w["grid"]) * (2 * math.pi / w["L"])
+    mx = np.arange(w["grid"] // 2 + 1) * (2 * math.pi / w["L"])
+    k2yz = (m[:, None] ** 2 + m[None, :] ** 2).ravel()
+    inside = int(sum(np.count_nonzero(k2yz + kx * kx < kc * kc) for kx in mx))
+    atom_sorted = n * (3 * rs + 8 + K * rs)            # t (3 real), cell (8 B), q (K real)
+    return {
+        "set_points": n * (24 + K * rs) + atom_sorted + n * 4,
+        "spread": atom_sorted + K * M * rs,
+        "multiply": K * inside * 2 * rs + K * Mh * 2 * rs,
+        "interp": K * M * rs + atom_sorted + n * 4 + n * (K * rs + 3 * rs),
+    }
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2606_06617_b300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def load_traffic(workload: str, stage: str):
+    """Per-launch DRAM bytes of a stage from a committed ncu summary, only if
+    the kernel sources are unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("csrc_sha") != csrc_digest():
+        return None
+    return d.get("dram_bytes_per_launch", {}).get(stage)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd[1:1] = ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
+    """The FP64 oracle (O1) on a bounded, density-matched sample of the
+    workload, on this host's cores.  Returns (atoms/s, cores, description)."""
+    import torch
+    from oracle.grid import DiscretePSWF, GridConfig
+    from paper_2606_06617_b300 import workloads as wl
+    w = WORKLOADS[wk]
+    if wk == "melt":
+        Msub = 64
+        Lsub = w["L"] * Msub / w["grid"]
+        n = int(round(w["N"] * (Lsub / w["L"]) ** 3))
+        s = wl.ionic_melt(n, Lsub, seed=1)
+        M = (Msub,) * 3
+        desc = f"density-matched sub-box L={Lsub:.2f} A, {n} atoms, grid {Msub}^3, K=4, P={w['P']}"
+    else:
+        s = wl.water_box(seed=1)
+        M = (w["grid"],) * 3
+        desc = "whole water box"
+    c = math.log(3.0 / w["tol"])
+    eta = (s.box[0] / M[0]) * (c / w["r_c"]) / math.pi
+    cw = w["P"] * math.pi * (1 - eta / 2)
+    o = DiscretePSWF(GridConfig(s.box, M, w["P"], c, w["r_c"], s.ps, c_w=cw))
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        o.evaluate(s.pos, s.q)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target or reps >= 20:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return s.n / dt, torch.get_num_threads(), f"{desc}; {reps} oracle evaluations, {dt:.2f} s each"
+
+
+def run_reference(args, rank: int):
+    """--impl reference: the CPU oracle as it stands, bounded sample per step."""
+    import torch
+    from oracle.grid import DiscretePSWF, GridConfig
+    from paper_2606_06617_b300 import workloads as wl
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    Msub = 64 if args.workload == "melt" else w["grid"]
+    Lsub = w["L"] * Msub / w["grid"]
+    n = int(round(w["N"] * (Lsub / w["L"]) ** 3)) if args.workload == "melt" else 3000
+    s = wl.ionic_melt(n, Lsub, seed=1) if args.workload == "melt" else wl.water_box(seed=1)
+    M = (Msub,) * 3
+    c = math.log(3.0 / w["tol"])
+    eta = (s.box[0] / M[0]) * (c / w["r_c"]) / math.pi
+    o = DiscretePSWF(GridConfig(s.box, M, w["P"], c, w["r_c"], s.ps, c_w=w["P"] * math.pi * (1 - eta / 2)))
+    for _ in range(args.warmup):
+        o.evaluate(s.pos, s.q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.evaluate(s.pos, s.q)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = s.n / dt
+    sample = f"density-matched sample of {w['name']}: {s.n} atoms, grid {Msub}^3, P={w['P']}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "sample": sample, "oracle": "O1 discrete PSWF-LR, torch FP64 CPU"},
+        "cpu_baseline": {"value": value, "unit": "atoms/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="melt")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2606_06617_b300 import lr
+    lr.lib()                                     # fails loudly if the library is missing
+
+    w = WORKLOADS[args.workload]
+    sysm = make_system(args.workload, seed=rank)
+    plan = lr.Plan(sysm.box, sysm.n, sysm.ps, w["r_c"], tol=w["tol"], P=w["P"], grid=w["grid"], device=dev)
+    pos = torch.tensor(sysm.pos, device=dev)
+    q = torch.tensor(sysm.q, dtype=torch.float32, device=dev)
+    out = (torch.empty(len(sysm.ps) + 1, dtype=torch.float64, device=dev),
+           torch.empty(len(sysm.ps), sysm.n, dtype=torch.float32, device=dev),
+           torch.empty(sysm.n, 3, dtype=torch.float32, device=dev))
+
+    def step():
+        plan.set_points(pos, q)
+        plan.execute(out=out)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    plan.profile_read()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.profile(False)
+    stage_ms, launches = plan.profile_read()
+    plan.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    value = world * sysm.n / (ms * 1e-3)
+
+    # roofline of the dominant kernel of ours (by summed event time)
+    alg = algorithmic_bytes(w, len(sysm.ps), sysm.n)
+    own = {k: stage_ms[k] for k in ("set_points", "spread", "multiply", "interp")}
+    dom = max(own, key=own.get)
+    per_launch_ms = stage_ms[dom] / args.steps
+    achieved = alg[dom] / (per_launch_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # end-to-end through the C-ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        pos_h = np.ascontiguousarray(sysm.pos)
+        q_h = np.ascontiguousarray(sysm.q)
+        for _ in range(2):
+            plan.compute_host(pos_h, q_h)
+        if dist:
+            dist.barrier()
+        ne = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            plan.compute_host(pos_h, q_h)
+        te = (time.perf_counter() - t0) / ne
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t)
+        K = len(sysm.ps)
+        e2e = {"value": world * sysm.n / te, "unit": "atoms/s",
+               "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * 4),
+               "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 4 + sysm.n * 12),
+               "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc = cpu_oracle_sample(args.workload)
+        cpu = {"value": v, "unit": "atoms/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "atoms": sysm.n, "box_A": w["L"], "channels_p": list(sysm.ps),
+                       "grid": plan.info["grid"], "P": plan.info["P"], "r_c": w["r_c"], "c": plan.info["c"],
+                       "c_w": plan.info["c_w"], "tol": w["tol"], "l2": "working set (grid 0.91 GB) > L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": load_traffic(args.workload, dom),
+                         "algorithmic_bytes_per_launch": alg[dom]},
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "gpu_launches": int(sum(launches.values())),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

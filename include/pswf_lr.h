@@ -160,6 +160,29 @@ const char* pswf_strerror(int status);
 /* Copies the plan's last error message into buf (NUL-terminated). */
 int pswf_plan_last_error(pswf_plan plan, char* buf, int len);
 
+/* ---- measurement support (not part of the paper's method) -------------- */
+#define PSWF_NSTAGE 8
+/* Stage indices for pswf_profile_read. */
+#define PSWF_STAGE_SET_POINTS 0   /* binning, sort, charge sums */
+#define PSWF_STAGE_SPREAD 1       /* step (i) */
+#define PSWF_STAGE_FFT_FWD 2      /* step (ii), cuFFT */
+#define PSWF_STAGE_MULTIPLY 3     /* steps (iii)-(iv) and the energy reduction */
+#define PSWF_STAGE_FFT_INV 4      /* inverse transform, cuFFT */
+#define PSWF_STAGE_INTERP 5       /* gather of potentials and forces */
+#define PSWF_STAGE_BACKWARD 6     /* pswf_backward */
+#define PSWF_STAGE_OTHER 7
+
+/* enable != 0: later calls record a CUDA event pair around each stage on the
+ * plan's stream (costs one event record per stage boundary). */
+int pswf_profile_enable(pswf_plan plan, int enable);
+
+/* Synchronises the stream and returns, per stage, the summed event time in
+ * milliseconds (host double [PSWF_NSTAGE], may be NULL) and the number of
+ * this library's own kernels launched (host int64 [PSWF_NSTAGE], may be NULL;
+ * cuFFT's kernels and memsets are not counted) since the last read; then
+ * resets both. */
+int pswf_profile_read(pswf_plan plan, double* stage_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

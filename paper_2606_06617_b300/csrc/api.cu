@@ -182,6 +182,15 @@ struct pswf_plan_s {
   void* d_stage = nullptr;
   int64_t d_stage_bytes = 0;
   std::string last_error;
+  // measurement: stage event pairs (when enabled) and own-kernel launch counts
+  struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<StageRec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[PSWF_NSTAGE] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -198,6 +207,38 @@ int cuda_check(pswf_plan p, cudaError_t e, const char* what) {
 }
 
 int launch_check(pswf_plan p, const char* what) { return cuda_check(p, cudaGetLastError(), what); }
+
+cudaEvent_t take_event(pswf_plan p) {
+  cudaEvent_t e = nullptr;
+  if (!p->pool.empty()) {
+    e = p->pool.back();
+    p->pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+
+// Records an event pair around one stage on the plan's stream when
+// measurement is enabled.
+struct StageScope {
+  pswf_plan p;
+  int stage;
+  cudaEvent_t a = nullptr;
+  StageScope(pswf_plan p_, int stage_) : p(p_), stage(stage_) {
+    if (p->prof_on) {
+      a = take_event(p);
+      cudaEventRecord(a, p->stream);
+    }
+  }
+  ~StageScope() {
+    if (a) {
+      cudaEvent_t b = take_event(p);
+      cudaEventRecord(b, p->stream);
+      p->recs.push_back({stage, a, b});
+    }
+  }
+};
 
 // Workspace layout (each region 256-byte aligned).  Returns total bytes and,
 // when base != nullptr, assigns the pointers.
@@ -348,6 +389,8 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   cudaStream_t s = p->stream;
   int rc;
   p->n = n;
+  StageScope scope(p, PSWF_STAGE_SET_POINTS);
+  p->launches[PSWF_STAGE_SET_POINTS] += (n > 0 ? 7 : 5);
   if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 148 * 32)));
   if (n > 0) {
@@ -389,20 +432,39 @@ template <typename R>
 int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   cudaStream_t s = p->stream;
   int rc;
-  if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid"))) return rc;
   const LaunchCtx ctx = make_ctx(p);
-  if (p->n > 0) {
-    cudaError_t e = sizeof(R) == 4 ? launch_spread_float(ctx) : launch_spread_double(ctx);
-    if ((rc = cuda_check(p, e, "spread"))) return rc;
+  {
+    StageScope scope(p, PSWF_STAGE_SPREAD);
+    if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid"))) return rc;
+    if (p->n > 0) {
+      int nl = 0;
+      cudaError_t e = sizeof(R) == 4 ? launch_spread_float(ctx, &nl) : launch_spread_double(ctx, &nl);
+      p->launches[PSWF_STAGE_SPREAD] += nl;
+      if ((rc = cuda_check(p, e, "spread"))) return rc;
+    }
   }
-  if ((rc = fft_exec(p, p->grid, true))) return rc;
-  if ((rc = multiply<R>(p, 1))) return rc;
-  k_energy_final<<<1, 256, 0, s>>>(p->host.K, kEnergyBlocks, p->epart, p->zero_coef, p->charges,
-                                   energy ? energy : p->energy_tmp);
-  if ((rc = launch_check(p, "k_energy_final"))) return rc;
+  {
+    StageScope scope(p, PSWF_STAGE_FFT_FWD);
+    if ((rc = fft_exec(p, p->grid, true))) return rc;
+  }
+  {
+    StageScope scope(p, PSWF_STAGE_MULTIPLY);
+    if ((rc = multiply<R>(p, 1))) return rc;
+    k_energy_final<<<1, 256, 0, s>>>(p->host.K, kEnergyBlocks, p->epart, p->zero_coef, p->charges,
+                                     energy ? energy : p->energy_tmp);
+    if ((rc = launch_check(p, "k_energy_final"))) return rc;
+    p->launches[PSWF_STAGE_MULTIPLY] += 2;
+  }
   if ((phi || forces) && p->n > 0) {
-    if ((rc = fft_exec(p, p->grid, false))) return rc;
-    cudaError_t e = sizeof(R) == 4 ? launch_interp_float(ctx, phi, forces) : launch_interp_double(ctx, phi, forces);
+    {
+      StageScope scope(p, PSWF_STAGE_FFT_INV);
+      if ((rc = fft_exec(p, p->grid, false))) return rc;
+    }
+    StageScope scope(p, PSWF_STAGE_INTERP);
+    int nl = 0;
+    cudaError_t e = sizeof(R) == 4 ? launch_interp_float(ctx, phi, forces, &nl)
+                                   : launch_interp_double(ctx, phi, forces, &nl);
+    p->launches[PSWF_STAGE_INTERP] += nl;
     if ((rc = cuda_check(p, e, "interp"))) return rc;
   }
   return PSWF_OK;
@@ -700,7 +762,38 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (pl->ws_owned && pl->ws) cudaFree(pl->ws);
   if (pl->d_stage) cudaFree(pl->d_stage);
   if (pl->h_pin) cudaFreeHost(pl->h_pin);
+  for (auto& r : pl->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : pl->pool) cudaEventDestroy(e);
   delete pl;
+}
+
+int pswf_profile_enable(pswf_plan pl, int enable) {
+  if (!pl) return PSWF_EINVAL;
+  pl->prof_on = enable != 0;
+  return PSWF_OK;
+}
+
+int pswf_profile_read(pswf_plan pl, double* stage_ms, int64_t* launches) {
+  if (!pl) return PSWF_EINVAL;
+  int rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "stream synchronize");
+  if (rc) return rc;
+  double ms[PSWF_NSTAGE] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (auto& r : pl->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
+    pl->pool.push_back(r.a);
+    pl->pool.push_back(r.b);
+  }
+  pl->recs.clear();
+  for (int i = 0; i < PSWF_NSTAGE; ++i) {
+    if (stage_ms) stage_ms[i] = ms[i];
+    if (launches) launches[i] = pl->launches[i];
+    pl->launches[i] = 0;
+  }
+  return PSWF_OK;
 }
 
 const char* pswf_strerror(int status) {

@@ -27,7 +27,7 @@ WinCoef<R> win_coef(const LaunchCtx& c) {
 }
 
 template <int P>
-cudaError_t spread_P(const LaunchCtx& c) {
+cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   constexpr int S = kTile + P - 1;
   const int64_t S3 = int64_t(S) * S * S;
   const int max_smem = 96 * 1024;
@@ -47,13 +47,15 @@ cudaError_t spread_P(const LaunchCtx& c) {
                                                          static_cast<R*>(c.grid));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    ++*nlaunch;
   }
   return cudaSuccess;
 }
 
 template <int P>
-cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces) {
+cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
+  ++*nlaunch;
   const WinCoef<R> wc = win_coef(c);
   const int blocks = int(std::min<int64_t>((c.n + kThreads - 1) / kThreads, 148 * 32));
   k_interp<R, P><<<blocks, kThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell,
@@ -75,10 +77,12 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces) {
   }                                                                                                       \
   return cudaErrorInvalidValue;
 
-cudaError_t PSWF_CAT(launch_spread, PSWF_REAL)(const LaunchCtx& c) { PSWF_P_CASES(spread_P, c) }
+cudaError_t PSWF_CAT(launch_spread, PSWF_REAL)(const LaunchCtx& c, int* nlaunch) {
+  PSWF_P_CASES(spread_P, c, nlaunch)
+}
 
-cudaError_t PSWF_CAT(launch_interp, PSWF_REAL)(const LaunchCtx& c, void* phi, void* forces) {
-  PSWF_P_CASES(interp_P, c, phi, forces)
+cudaError_t PSWF_CAT(launch_interp, PSWF_REAL)(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
+  PSWF_P_CASES(interp_P, c, phi, forces, nlaunch)
 }
 
 }  // namespace pswf

@@ -29,9 +29,9 @@ struct LaunchCtx {
 };
 
 // Each returns cudaSuccess or the launch error.
-cudaError_t launch_spread_float(const LaunchCtx& c);
-cudaError_t launch_spread_double(const LaunchCtx& c);
-cudaError_t launch_interp_float(const LaunchCtx& c, void* phi, void* forces);
-cudaError_t launch_interp_double(const LaunchCtx& c, void* phi, void* forces);
+cudaError_t launch_spread_float(const LaunchCtx& c, int* nlaunch);
+cudaError_t launch_spread_double(const LaunchCtx& c, int* nlaunch);
+cudaError_t launch_interp_float(const LaunchCtx& c, void* phi, void* forces, int* nlaunch);
+cudaError_t launch_interp_double(const LaunchCtx& c, void* phi, void* forces, int* nlaunch);
 
 }  // namespace pswf

@@ -65,7 +65,12 @@ SIGNATURES = {
     "pswf_plan_destroy": ([_vp], None),
     "pswf_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "pswf_plan_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
+    "pswf_profile_enable": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pswf_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
+
+NSTAGE = 8
+STAGES = ("set_points", "spread", "fft_fwd", "multiply", "fft_inv", "interp", "backward", "other")
 
 
 def lib():
@@ -234,6 +239,17 @@ class Plan:
 
     def sync(self):
         _check(lib().pswf_sync(self._h), self._h)
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around each stage of later calls."""
+        _check(lib().pswf_profile_enable(self._h, 1 if enable else 0), self._h)
+
+    def profile_read(self):
+        """(stage ms dict, own-kernel launch counts dict) since the last read."""
+        ms = (ctypes.c_double * NSTAGE)()
+        nl = (ctypes.c_int64 * NSTAGE)()
+        _check(lib().pswf_profile_read(self._h, ms, nl), self._h)
+        return dict(zip(STAGES, ms[:])), dict(zip(STAGES, nl[:]))
 
     def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True):
         """End-to-end from host arrays (float64); returns numpy (energy, phi, forces)."""

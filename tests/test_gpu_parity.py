@@ -147,5 +147,6 @@ def test_self_energy_matches_oracle():
     from oracle.mollifiers import Mollifier
     m = Mollifier(C_TOL, 4.0)
     ref32 = [m.self_coef(p) * float(np.sum(q32[c] ** 2)) for c, p in enumerate(s.ps)]
-    np.testing.assert_allclose(g["plan"].self_energy(), ref32, rtol=1e-12)
+    # self_coef: planner (Legendre) vs oracle (Nystrom) derivatives of psi_0 at 0
+    np.testing.assert_allclose(g["plan"].self_energy(), ref32, rtol=1e-9)
     np.testing.assert_allclose(g["plan"].self_energy(), o["self"], rtol=1e-7)
