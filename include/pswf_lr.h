@@ -139,6 +139,29 @@ int pswf_backward(pswf_plan plan, const double* g_energy, const void* g_phi,
  * host double [K].  Synchronises the stream. */
 int pswf_self_energy(pswf_plan plan, double* out);
 
+/* Self energies like pswf_self_energy, for callers that must not allocate
+ * device memory while they run -- for example a plug-in inside a molecular
+ * dynamics engine that owns every GPU buffer and forbids allocation once the
+ * simulation loop has started, or a process that has handed all free device
+ * memory to its own pool.  The paper has no counterpart: it is a different
+ * way to run the same per-channel reduction.
+ *   plan:   read only for its host-side constants (the self-energy
+ *           coefficients); its workspace, stream and points are not used;
+ *   n, q:   device real [K][n] latent charges (plan precision), n <= n_max;
+ *   out:    device double [K]: E_self^(p) per channel (caller-owned);
+ *   stream: cudaStream_t the work is enqueued on (asynchronous).
+ * Allocates nothing: the FP64 partial sums live in a 152,576-byte array of
+ * static device memory inside this library, which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call on a
+ * device shares the one array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and give wrong results; serialise them.  Each
+ * call writes every scratch entry before reading it, so nothing has to be
+ * cleared.  Returns PSWF_EINVAL for n outside 0..n_max or more than 64
+ * channels (the array's limit). */
+int pswf_self_energy_noalloc(pswf_plan plan, int64_t n, const void* q, double* out, void* stream);
+
 /* Waits for the plan's stream and returns the first device-side status
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */
 int pswf_sync(pswf_plan plan);

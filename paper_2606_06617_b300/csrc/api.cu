@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -538,7 +539,71 @@ void fill_info(const Plan& h, int flags, pswf_info* out) {
 
 }  // namespace
 
+// ---- allocation-free self energy ------------------------------------------------
+// Scratch of pswf_self_energy_noalloc: the per-block FP64 partial sums of q and
+// q^2 ([kQBlocks][kMaxK][2]) followed by the per-channel totals ([kMaxK][2]),
+// 152,576 bytes in all, resident on every GPU that loads this library.
+static __device__ __align__(256) double pswf_noalloc_scratch[kQBlocks * kMaxK * 2 + kMaxK * 2];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+struct SelfCoef {
+  double s[kMaxK];
+};
+
+// out[c] = s_c * Q_self^(c) from the charge totals in charges[c][2].
+__global__ void k_self_energy_out(int K, SelfCoef sc, const double* __restrict__ charges, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < K) out[c] = sc.s[c] * charges[2 * c + 1];
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device with that device current (cudaGetSymbolAddress, no allocation).
+int noalloc_scratch(pswf_plan p, double** out) {
+  int dev = 0;
+  int rc = cuda_check(p, cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_err(p, PSWF_EINVAL, "pswf_self_energy_noalloc: device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if ((rc = cuda_check(p, cudaGetSymbolAddress(&ptr, pswf_noalloc_scratch), "cudaGetSymbolAddress"))) return rc;
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return PSWF_OK;
+}
+}  // namespace
+
 extern "C" {
+
+int pswf_self_energy_noalloc(pswf_plan pl, int64_t n, const void* q, double* out, void* stream) {
+  if (!pl || !out || (n > 0 && !q)) return PSWF_EINVAL;
+  const int K = pl->host.K;
+  if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "pswf_self_energy_noalloc: n outside 0..n_max");
+  if (K > kMaxK) return set_err(pl, PSWF_EINVAL, "pswf_self_energy_noalloc: more than 64 channels do not fit the scratch");
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(pl, &scratch);
+  if (rc) return rc;
+  double* part = scratch;                           // [kQBlocks][K][2], every entry written below
+  double* charges = scratch + kQBlocks * kMaxK * 2; // [K][2]
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (pl->real_size == 4)
+    k_charge_partials<float><<<kQBlocks, kThreads, 0, s>>>(n, static_cast<const float*>(q), K, part);
+  else
+    k_charge_partials<double><<<kQBlocks, kThreads, 0, s>>>(n, static_cast<const double*>(q), K, part);
+  if ((rc = launch_check(pl, "k_charge_partials (noalloc)"))) return rc;
+  k_charge_final<<<1, 64, 0, s>>>(kQBlocks, K, part, charges);
+  if ((rc = launch_check(pl, "k_charge_final (noalloc)"))) return rc;
+  SelfCoef sc;
+  for (int k = 0; k < kMaxK; ++k) sc.s[k] = k < K ? pl->host.self_coef[k] : 0.0;
+  k_self_energy_out<<<1, 64, 0, s>>>(K, sc, charges, out);
+  return launch_check(pl, "k_self_energy_out (noalloc)");
+}
 
 void pswf_opts_default(pswf_opts* o) {
   if (!o) return;

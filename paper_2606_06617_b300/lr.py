@@ -65,6 +65,7 @@ SIGNATURES = {
     "pswf_plan_destroy": ([_vp], None),
     "pswf_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "pswf_plan_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
+    "pswf_self_energy_noalloc": ([_vp, _i64, _vp, _vp, _vp], ctypes.c_int),
     "pswf_profile_enable": ([_vp, ctypes.c_int], ctypes.c_int),
     "pswf_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
