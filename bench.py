@@ -34,9 +34,9 @@ sys.path.insert(0, ROOT)
 
 # Workloads: box, atoms, channels, mollifier and grid parameters.
 WORKLOADS = {
-    "melt": dict(name="ionic_melt_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0, tol=5e-6, P=8,
+    "melt": dict(name="ionic_melt_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0, tol=1e-5, P=7,
                  grid=384),
-    "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=1e-5, P=8, grid=64),
+    "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=5e-6, P=8, grid=64),
 }
 METRIC = "LR energy+force atoms/s"
 

@@ -173,12 +173,7 @@ class DiscretePSWF:
         return torch.cat(phis, 1), torch.cat(fs, 1)
 
     # ---- the whole forward evaluation ---------------------------------------
-    def evaluate(self, pos, q):
-        """pos [N,3], q [K,N] (array-like or tensors).  Returns a dict with
-        E (total), E_ch [K] (E_k + E^0 per channel), E_k [K], E0 [K],
-        phi [K,N] (including d E^0 / d q_i), F [N,3], f [K,N,3], Psi."""
-        pos = torch.as_tensor(pos, dtype=f64)
-        q = torch.as_tensor(q, dtype=f64)
+    def _forward(self, pos: torch.Tensor, q: torch.Tensor):
         rho = self.spread(pos, q)
         E_k, Psi = self.solve(rho)
         phi, f = self.gather(Psi, pos)
@@ -187,8 +182,41 @@ class DiscretePSWF:
         E0 = a * Qnet ** 2
         phi = phi + (2.0 * a * Qnet).unsqueeze(1)
         F = torch.einsum("kn,knd->nd", q, f)
+        return E_k, E0, phi, F, f, Psi
+
+    def evaluate(self, pos, q):
+        """pos [N,3], q [K,N] (array-like or tensors).  Returns a dict with
+        E (total), E_ch [K] (E_k + E^0 per channel), E_k [K], E0 [K],
+        phi [K,N] (including d E^0 / d q_i), F [N,3], f [K,N,3], Psi."""
+        pos = torch.as_tensor(pos, dtype=f64)
+        q = torch.as_tensor(q, dtype=f64)
+        E_k, E0, phi, F, f, Psi = self._forward(pos, q)
         return dict(E=float((E_k + E0).sum().detach()), E_ch=(E_k + E0).detach(), E_k=E_k.detach(), E0=E0.detach(),
                     phi=phi.detach(), F=F.detach(), f=f.detach(), Psi=Psi.detach(), E_tensor=(E_k + E0).sum())
+
+    def vjp(self, pos, q, g_E=None, g_phi=None, g_F=None):
+        """Vector-Jacobian product of evaluate's (E_ch, phi, F): for
+        L = sum_c g_E[c] E_c + sum g_phi * phi + sum g_F * F returns
+        (dL/dq [K,N], dL/dr [N,3]), by reverse-mode differentiation (torch
+        autograd, a library primitive) of exactly the steps of evaluate.
+        F = -dE/dr makes the g_F term a second derivative of E: W is
+        differentiated twice through psi_w.torch."""
+        pos = torch.as_tensor(pos, dtype=f64).clone().requires_grad_(True)
+        q = torch.as_tensor(q, dtype=f64).clone().requires_grad_(True)
+        E_k, E0, phi, F, _, _ = self._forward(pos, q)
+        L = torch.zeros((), dtype=f64)
+        if g_E is not None:
+            L = L + (torch.as_tensor(g_E, dtype=f64) * (E_k + E0)).sum()
+        if g_phi is not None:
+            L = L + (torch.as_tensor(g_phi, dtype=f64) * phi).sum()
+        if g_F is not None:
+            L = L + (torch.as_tensor(g_F, dtype=f64) * F).sum()
+        if not L.requires_grad:
+            return torch.zeros_like(q).detach(), torch.zeros_like(pos).detach()
+        gq, gr = torch.autograd.grad(L, [q, pos], allow_unused=True)
+        gq = torch.zeros_like(q) if gq is None else gq
+        gr = torch.zeros_like(pos) if gr is None else gr
+        return gq.detach(), gr.detach()
 
     def self_energy(self, q) -> np.ndarray:
         """E_self^(p) per channel (Implementation details)."""

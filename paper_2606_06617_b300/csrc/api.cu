@@ -139,6 +139,7 @@ struct pswf_plan_s {
   cudaStream_t stream = nullptr;
   int64_t n_max = 0;
   int64_t n = -1;            // atoms of the last set_points (-1: none)
+  bool psi_valid = false;    // grid holds Psi of the last execute (backward plans)
   int flags = 0;
   size_t real_size = 4;
   Geometry geo{};
@@ -164,6 +165,7 @@ struct pswf_plan_s {
   int* scan_sums = nullptr;  // [scan_blocks]
   double* qpart = nullptr;   // [kQBlocks][K][2]
   double* charges = nullptr; // [K][2]: Q_net, Q_self
+  double* bsum = nullptr;    // [K][2]: sum and sum of squares of the upstream gphi (backward)
   double* epart = nullptr;   // [K][kEnergyBlocks]
   double* energy_tmp = nullptr; // [K + 1]
   int* err = nullptr;        // device status flag
@@ -267,6 +269,7 @@ int64_t layout(pswf_plan p, char* base) {
   p->scan_sums = reinterpret_cast<int*>(take(int64_t(p->scan_blocks) * 4));
   p->qpart = reinterpret_cast<double*>(take(int64_t(kQBlocks) * K * 2 * 8));
   p->charges = reinterpret_cast<double*>(take(int64_t(K) * 2 * 8));
+  p->bsum = reinterpret_cast<double*>(take(int64_t(K) * 2 * 8));
   p->epart = reinterpret_cast<double*>(take(int64_t(K) * kEnergyBlocks * 8));
   p->energy_tmp = reinterpret_cast<double*>(take(int64_t(K + 1) * 8));
   p->err = reinterpret_cast<int*>(take(4));
@@ -347,11 +350,13 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.coef_w = p->host.coef_w.data();
   c.deg_w = p->host.deg_w;
   c.stream = p->stream;
+  c.grid2 = p->grid2;
+  c.gsum = p->bsum;
   return c;
 }
 
 template <typename R>
-int multiply(pswf_plan p, int want_energy) {
+int multiply(pswf_plan p, int want_energy, void* data) {
   const Plan& h = p->host;
   MultParams mp;
   for (int d = 0; d < 3; ++d) {
@@ -363,7 +368,7 @@ int multiply(pswf_plan p, int want_energy) {
   mp.deg = h.deg_m;
   mp.K = h.K;
   dim3 grid(kEnergyBlocks, h.K);
-  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->grid), mp, p->pch, p->scale,
+  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2[0]),
                                                   static_cast<const R*>(p->iw2[1]), static_cast<const R*>(p->iw2[2]),
                                                   p->epart, want_energy);
@@ -390,6 +395,7 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   cudaStream_t s = p->stream;
   int rc;
   p->n = n;
+  p->psi_valid = false;
   StageScope scope(p, PSWF_STAGE_SET_POINTS);
   p->launches[PSWF_STAGE_SET_POINTS] += (n > 0 ? 7 : 5);
   if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
@@ -450,17 +456,24 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   }
   {
     StageScope scope(p, PSWF_STAGE_MULTIPLY);
-    if ((rc = multiply<R>(p, 1))) return rc;
+    if ((rc = multiply<R>(p, 1, p->grid))) return rc;
     k_energy_final<<<1, 256, 0, s>>>(p->host.K, kEnergyBlocks, p->epart, p->zero_coef, p->charges,
                                      energy ? energy : p->energy_tmp);
     if ((rc = launch_check(p, "k_energy_final"))) return rc;
     p->launches[PSWF_STAGE_MULTIPLY] += 2;
   }
-  if ((phi || forces) && p->n > 0) {
+  const bool keep_psi = (p->flags & PSWF_FLAG_BACKWARD) != 0;
+  if (p->n == 0) {
+    p->psi_valid = keep_psi;   // nothing to gather; a backward has nothing to do
+    return PSWF_OK;
+  }
+  if (phi || forces || keep_psi) {
     {
       StageScope scope(p, PSWF_STAGE_FFT_INV);
       if ((rc = fft_exec(p, p->grid, false))) return rc;
     }
+    p->psi_valid = keep_psi;
+    if (!(phi || forces)) return PSWF_OK;
     StageScope scope(p, PSWF_STAGE_INTERP);
     int nl = 0;
     cudaError_t e = sizeof(R) == 4 ? launch_interp_float(ctx, phi, forces, &nl)
@@ -469,6 +482,46 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
     if ((rc = cuda_check(p, e, "interp"))) return rc;
   }
   return PSWF_OK;
+}
+
+// Vector-Jacobian product (the formulas are on the kernels in backward.cuh):
+// sum of the upstream gphi per channel, rhobar spread into the second grid,
+// FFT / the same multiplier / inverse FFT (A is symmetric), then one gather
+// that reads Psi (kept by execute) and A rhobar.
+template <typename R>
+int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const void* g_forces, void* grad_q,
+                void* grad_pos) {
+  cudaStream_t s = p->stream;
+  int rc;
+  if (!grad_q && !grad_pos) return PSWF_OK;
+  StageScope scope(p, PSWF_STAGE_BACKWARD);
+  const LaunchCtx ctx = make_ctx(p);
+  const BackwardArgs b{g_energy, g_phi, g_forces, grad_q, grad_pos};
+  const int K = p->host.K;
+  int nl = 0;
+  cudaError_t e;
+  if (g_phi) {
+    k_charge_partials<R><<<kQBlocks, kThreads, 0, s>>>(p->n, static_cast<const R*>(g_phi), K, p->qpart);
+    if ((rc = launch_check(p, "k_charge_partials (backward)"))) return rc;
+    k_charge_final<<<1, 64, 0, s>>>(kQBlocks, K, p->qpart, p->bsum);
+    if ((rc = launch_check(p, "k_charge_final (backward)"))) return rc;
+    nl += 2;
+  } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(K) * 2 * sizeof(double), s), "clear bsum"))) {
+    return rc;
+  }
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->grid2, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid2")))
+    return rc;
+  if (g_phi || g_forces) {
+    e = sizeof(R) == 4 ? launch_backward_float(ctx, b, 0, &nl) : launch_backward_double(ctx, b, 0, &nl);
+    if ((rc = cuda_check(p, e, "backward spread"))) return rc;
+    if ((rc = fft_exec(p, p->grid2, true))) return rc;
+    if ((rc = multiply<R>(p, 0, p->grid2))) return rc;
+    ++nl;
+    if ((rc = fft_exec(p, p->grid2, false))) return rc;
+  }
+  e = sizeof(R) == 4 ? launch_backward_float(ctx, b, 1, &nl) : launch_backward_double(ctx, b, 1, &nl);
+  p->launches[PSWF_STAGE_BACKWARD] += nl;
+  return cuda_check(p, e, "backward gather");
 }
 
 int make_fft(pswf_plan p) {
@@ -708,13 +761,12 @@ int pswf_execute(pswf_plan pl, double* energy, void* phi, void* forces) {
 
 int pswf_backward(pswf_plan pl, const double* g_energy, const void* g_phi, const void* g_forces, void* grad_q,
                   void* grad_pos) {
-  (void)g_energy;
-  (void)g_phi;
-  (void)g_forces;
-  (void)grad_q;
-  (void)grad_pos;
   if (!pl) return PSWF_EINVAL;
-  return set_err(pl, PSWF_ESTATE, "backward is not available in this build");
+  if (!(pl->flags & PSWF_FLAG_BACKWARD)) return set_err(pl, PSWF_ESTATE, "plan was created without PSWF_FLAG_BACKWARD");
+  if (pl->n < 0 || !pl->psi_valid) return set_err(pl, PSWF_ESTATE, "pswf_backward needs a preceding pswf_execute");
+  if (pl->n == 0) return PSWF_OK;
+  return pl->real_size == 4 ? do_backward<float>(pl, g_energy, g_phi, g_forces, grad_q, grad_pos)
+                            : do_backward<double>(pl, g_energy, g_phi, g_forces, grad_q, grad_pos);
 }
 
 int pswf_self_energy(pswf_plan pl, double* out) {

@@ -18,7 +18,8 @@
 
 namespace pswf {
 
-constexpr int kTile = 8;
+constexpr int kTile = 16;     // tile edge in stencil-start cells
+constexpr int kBatch = 256;   // atoms whose window weights are staged in shared memory at once
 
 struct Geometry {
   double L[3];       // box edges
@@ -202,119 +203,77 @@ __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __res
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy);
 
-// ---- spreading (step (i)) ----------------------------------------------------------
-// One block per tile: accumulate the padded (T + P - 1)^3 tile for a chunk of
-// channels in shared memory, then add it into the grid (periodic wrap).
-template <typename R, int P>
-__global__ void k_spread(Geometry g, int64_t nmax, const int* __restrict__ tile_start, const R* __restrict__ st,
-                         const uint64_t* __restrict__ scell, const R* __restrict__ sq, int c0, int kc,
-                         WinCoef<R> wc, R* __restrict__ grid) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);
-  constexpr int S = kTile + P - 1;
-  constexpr int S3 = S * S * S;
-  const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
-    if (a0 == a1) continue;
-    const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
-    const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
-    for (int i = threadIdx.x; i < kc * S3; i += blockDim.x) sm[i] = R(0);
-    __syncthreads();
-    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
-      R wx[P], wy[P], wz[P];
-      window_values<R, P>(st[a], wc, wx);
-      window_values<R, P>(st[nmax + a], wc, wy);
-      window_values<R, P>(st[2 * nmax + a], wc, wz);
-      int cx, cy, cz;
-      unpack_cell(scell[a], cx, cy, cz);
-      const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
-      for (int c = 0; c < kc; ++c) {
-        const R qc = sq[(c0 + c) * nmax + a];
-        R* smc = sm + c * S3;
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          const R wzq = wz[k] * qc;
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            const R wyz = wy[j] * wzq;
-            R* row = smc + ((lz + k) * S + (ly + j)) * S + lx;
-#pragma unroll
-            for (int i = 0; i < P; ++i) atomicAdd(row + i, wx[i] * wyz);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kc * S3; idx += blockDim.x) {
-      const R v = sm[idx];
-      if (v != R(0)) {
-        const int c = idx / S3, r = idx % S3;
-        const int lz = r / (S * S), ly = (r / S) % S, lx = r % S;
-        const int gx = (ox + lx) % g.M[0], gy = (oy + ly) % g.M[1], gz = (oz + lz) % g.M[2];
-        atomicAdd(grid + ((int64_t(c0 + c) * g.M[2] + gz) * g.M[1] + gy) * g.Mxp + gx, v);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // ---- multiplier and energy (steps (iii)-(iv)) --------------------------------------
 // blockIdx.y = channel.  For each half-spectrum mode m != 0 with u = |k|/k_c < 1:
 //   G = scale_c * sing_p(k) * (S_p(u) + log part) * iw2x * iw2y * iw2z  (times dV^2/V,
 //   folded into scale_c), energy += w_m G |rho-hat|^2 / 2, rho-hat <- G rho-hat;
 // all other modes are set to zero.  Energy partials per block in FP64.
 template <typename R>
-__global__ void k_multiply(Cplx<R>* __restrict__ data, MultParams mp, const int* __restrict__ pch,
-                           const double* __restrict__ scale, const R* __restrict__ coef,
-                           const R* __restrict__ iw2x, const R* __restrict__ iw2y, const R* __restrict__ iw2z,
-                           double* __restrict__ part, int want_energy) {
+__global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, MultParams mp,
+                                                  const int* __restrict__ pch, const double* __restrict__ scale,
+                                                  const R* __restrict__ coef, const R* __restrict__ iw2x,
+                                                  const R* __restrict__ iw2y, const R* __restrict__ iw2z,
+                                                  double* __restrict__ part, int want_energy) {
+  // One (y, z) row of the half spectrum per block iteration; rows outside the
+  // band |k| < k_c are zero-filled without reading them.
   const int c = blockIdx.y;
   const int p = pch[c];
   const R sc = R(scale[c]);
-  const int64_t nh = int64_t(mp.Mxh) * mp.M[1] * mp.M[2];
-  Cplx<R>* d = data + int64_t(c) * nh;
+  const int nrow = mp.M[1] * mp.M[2];
+  Cplx<R>* d = data + int64_t(c) * nrow * mp.Mxh;
   const R* cf = coef + size_t(c) * kMultSeg * (mp.deg + 1);
+  const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
+  const R inv_kc = R(mp.inv_kc);
+  const R kf0 = R(mp.kfac[0]), kf1 = R(mp.kfac[1]), kf2 = R(mp.kfac[2]);
+  const bool even_x = (mp.M[0] % 2) == 0;
   double e = 0.0;
-  for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < nh; idx += int64_t(gridDim.x) * blockDim.x) {
-    const int ix = int(idx % mp.Mxh);
-    const int iy = int((idx / mp.Mxh) % mp.M[1]);
-    const int iz = int(idx / (int64_t(mp.Mxh) * mp.M[1]));
+  for (int row = blockIdx.x; row < nrow; row += gridDim.x) {
+    const int iy = row % mp.M[1], iz = row / mp.M[1];
     const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
     const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
-    const R kx = R(mp.kfac[0] * ix), ky = R(mp.kfac[1] * my), kz = R(mp.kfac[2] * mz);
-    const R k2 = kx * kx + ky * ky + kz * kz;
-    const R k = sqrt(k2);
-    const R u = k * R(mp.inv_kc);
-    if (!(u < R(1)) || (ix == 0 && my == 0 && mz == 0)) {
-      d[idx] = Cplx<R>{R(0), R(0)};
+    const R ky = kf1 * R(my), kz = kf2 * R(mz);
+    const R kyz2 = ky * ky + kz * kz;
+    Cplx<R>* dr = d + int64_t(row) * mp.Mxh;
+    if (!(kyz2 < kc2)) {
+      for (int ix = threadIdx.x; ix < mp.Mxh; ix += blockDim.x) dr[ix] = Cplx<R>{R(0), R(0)};
       continue;
     }
-    int seg = int(u * R(kMultSeg));
-    if (seg > kMultSeg - 1) seg = kMultSeg - 1;
-    const R s = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
-    const R* cs = cf + seg * (mp.deg + 1);
-    R S = cs[mp.deg];
-    for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * s + cs[nn];
-    R phi;
-    switch (p) {
-      case 1: phi = S / k2; break;
-      case 2: phi = S / k; break;
-      case 3: phi = S - log(u); break;
-      case 5: phi = S - u * u * log(u); break;
-      default: phi = S; break;
-    }
     const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
-    const R G = sc * phi * iw2x[ix] * iw2y[ay] * iw2z[az];
-    Cplx<R> v = d[idx];
-    if (want_energy) {
-      const bool edge = (ix == 0) || ((mp.M[0] % 2 == 0) && ix == mp.Mxh - 1);
-      const R wm = edge ? R(0.5) : R(1);
-      e += double(wm * G * (v.x * v.x + v.y * v.y));
+    const R wyz = sc * iw2y[ay] * iw2z[az];
+    for (int ix = threadIdx.x; ix < mp.Mxh; ix += blockDim.x) {
+      const R kx = kf0 * R(ix);
+      const R k2 = kx * kx + kyz2;
+      if (!(k2 < kc2) || k2 == R(0)) {
+        dr[ix] = Cplx<R>{R(0), R(0)};
+        continue;
+      }
+      const R k = sqrt(k2);
+      R u = k * inv_kc;
+      if (u >= R(1)) u = R(1) - R(1e-7);
+      int seg = int(u * R(kMultSeg));
+      if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+      const R s = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+      const R* cs = cf + seg * (mp.deg + 1);
+      R S = cs[mp.deg];
+      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * s + cs[nn];
+      R phi;
+      switch (p) {
+        case 1: phi = S / k2; break;
+        case 2: phi = S / k; break;
+        case 3: phi = S - log(u); break;
+        case 5: phi = S - u * u * log(u); break;
+        default: phi = S; break;
+      }
+      const R G = phi * wyz * iw2x[ix];
+      Cplx<R> v = dr[ix];
+      if (want_energy) {
+        const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
+        e += double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
+      }
+      v.x *= G;
+      v.y *= G;
+      dr[ix] = v;
     }
-    v.x *= G;
-    v.y *= G;
-    d[idx] = v;
   }
   if (!want_energy) return;
   __shared__ double sh[32];
@@ -328,11 +287,11 @@ __global__ void k_multiply(Cplx<R>* __restrict__ data, MultParams mp, const int*
   }
 }
 
-// ---- interpolation (gather of phi and forces) --------------------------------------
+// ---- interpolation, direct from global memory (reference kernel) -------------------
 // One thread per sorted atom.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W,
 // with grad_d W = (2 / h_d) dW/ds.  Writes in the original atom order.
 template <typename R, int P>
-__global__ void k_interp(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
+__global__ void k_interp_direct(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
                          const uint64_t* __restrict__ scell, const R* __restrict__ sq, const int* __restrict__ sperm,
                          WinCoef<R> wc, const R* __restrict__ grid, const double* __restrict__ zero_coef,
                          const double* __restrict__ charges, R* __restrict__ phi, R* __restrict__ forces) {

@@ -4,6 +4,8 @@
 #include <cstring>
 
 #include "launch.cuh"
+#include "stencil.cuh"
+#include "backward.cuh"
 
 #ifndef PSWF_REAL
 #error "define PSWF_REAL as float or double"
@@ -15,7 +17,10 @@ namespace pswf {
 namespace {
 
 using R = PSWF_REAL;
-constexpr int kThreads = 256;
+constexpr int kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA on sm_103a
+constexpr int kSpreadThreads = 512;
+constexpr int kGatherThreads = kGatherThreadsFor<R>;
+constexpr int kDirectThreads = 256;
 
 WinCoef<R> win_coef(const LaunchCtx& c) {
   WinCoef<R> w;
@@ -26,48 +31,109 @@ WinCoef<R> win_coef(const LaunchCtx& c) {
   return w;
 }
 
+// Largest staging batch (<= kBatch, multiple of 32) whose shared memory fits.
+template <typename F>
+int pick_batch(F bytes) {
+  for (int b = kBatch; b >= 32; b -= 32)
+    if (bytes(b) <= size_t(kSmemLimit)) return b;
+  return 0;
+}
+
 template <int P>
 cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
-  constexpr int S = kTile + P - 1;
-  const int64_t S3 = int64_t(S) * S * S;
-  const int max_smem = 96 * 1024;
-  int kc = int(std::max<int64_t>(1, max_smem / (S3 * int64_t(sizeof(R)))));
-  kc = std::min(kc, c.geo.K);
-  const size_t smem = size_t(kc) * S3 * sizeof(R);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_spread<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-  }
   const WinCoef<R> wc = win_coef(c);
-  const int blocks = std::min(c.ntiles, 148 * 16);
-  for (int c0 = 0; c0 < c.geo.K; c0 += kc) {
-    const int nk = std::min(kc, c.geo.K - c0);
-    k_spread<R, P><<<blocks, kThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
-                                                         c.scell, static_cast<const R*>(c.sq), c0, nk, wc,
-                                                         static_cast<R*>(c.grid));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  const int batch = pick_batch([](int b) { return spread_smem_bytes<R, P>(b); });
+  if (batch == 0) {
+    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+    k_spread_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st),
+                                                                   c.scell, static_cast<const R*>(c.sq), wc,
+                                                                   static_cast<R*>(c.grid));
     ++*nlaunch;
+    return cudaGetLastError();
   }
-  return cudaSuccess;
+  const size_t smem = spread_smem_bytes<R, P>(batch);
+  cudaError_t e = cudaFuncSetAttribute(k_spread<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int blocks = std::min(c.ntiles, 148 * 8);
+  k_spread<R, P><<<blocks, kSpreadThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
+                                                             c.scell, static_cast<const R*>(c.sq), wc, batch,
+                                                             static_cast<R*>(c.grid));
+  ++*nlaunch;
+  return cudaGetLastError();
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
 }
 
 template <int P>
 cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
-  ++*nlaunch;
   const WinCoef<R> wc = win_coef(c);
-  const int blocks = int(std::min<int64_t>((c.n + kThreads - 1) / kThreads, 148 * 32));
-  k_interp<R, P><<<blocks, kThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell,
-                                                    static_cast<const R*>(c.sq), c.sperm, wc,
-                                                    static_cast<const R*>(c.grid), c.zero_coef, c.charges,
-                                                    static_cast<R*>(phi), static_cast<R*>(forces));
+  // Stage as many channels as a warp has slots (all of them when K is
+  // small), within the shared-memory limit.
+  int kc = std::min(c.geo.K, GatherPad<P>::NS);
+  while (kc > 0 && gather_smem_bytes<R, P>(kc) > size_t(kSmemLimit)) --kc;
+  if (kc == 0) {
+    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+    k_interp_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
+        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
+        static_cast<const R*>(c.grid), c.zero_coef, c.charges, static_cast<R*>(phi), static_cast<R*>(forces));
+    ++*nlaunch;
+    return cudaGetLastError();
+  }
+  const int nchunk = (c.geo.K + kc - 1) / kc;
+  cudaError_t e;
+  if (nchunk > 1 && forces) {
+    e = cudaMemsetAsync(forces, 0, size_t(c.n) * 3 * sizeof(R), c.stream);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = gather_smem_bytes<R, P>(kc);
+  e = cudaFuncSetAttribute(k_interp<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int threads = kGatherThreads;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp<R, P>, threads, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t items = int64_t(c.ntiles) * nchunk;
+  const int blocks = int(std::min<int64_t>(items, int64_t(sm_count()) * std::max(per_sm, 1)));
+  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.n, c.nmax, c.geo, c.tile_start, static_cast<const R*>(c.st),
+                                                      c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc,
+                                                      static_cast<const R*>(c.grid), c.zero_coef, c.charges,
+                                                      static_cast<R*>(phi), static_cast<R*>(forces));
+  ++*nlaunch;
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch) {
+  if (c.n == 0) return cudaSuccess;
+  const WinCoef<R> wc = win_coef(c);
+  const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+  ++*nlaunch;
+  if (stage == 0) {
+    k_spread_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
+        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
+        static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces), static_cast<R*>(c.grid2));
+  } else {
+    k_interp_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
+        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
+        static_cast<const R*>(c.grid), static_cast<const R*>(c.grid2), c.zero_coef, c.charges, c.gsum, b.g_energy,
+        static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces), static_cast<R*>(b.grad_q),
+        static_cast<R*>(b.grad_pos));
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-#define PSWF_P_CASES(F, ...)                                                                              \
+#define PSWF_P_CASES(F, ...)                                                                           \
   switch (c.geo.P) {                                                                                      \
     case 2: return F<2>(__VA_ARGS__);   case 3: return F<3>(__VA_ARGS__);   case 4: return F<4>(__VA_ARGS__); \
     case 5: return F<5>(__VA_ARGS__);   case 6: return F<6>(__VA_ARGS__);   case 7: return F<7>(__VA_ARGS__); \
@@ -83,6 +149,11 @@ cudaError_t PSWF_CAT(launch_spread, PSWF_REAL)(const LaunchCtx& c, int* nlaunch)
 
 cudaError_t PSWF_CAT(launch_interp, PSWF_REAL)(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   PSWF_P_CASES(interp_P, c, phi, forces, nlaunch)
+}
+
+cudaError_t PSWF_CAT(launch_backward, PSWF_REAL)(const LaunchCtx& c, const BackwardArgs& b, int stage,
+                                                 int* nlaunch) {
+  PSWF_P_CASES(backward_P, c, b, stage, nlaunch)
 }
 
 }  // namespace pswf

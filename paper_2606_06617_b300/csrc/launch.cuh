@@ -26,6 +26,17 @@ struct LaunchCtx {
   const double* coef_w = nullptr;   // host [P][deg_w + 1]
   int deg_w = 0;
   cudaStream_t stream = nullptr;
+  // backward
+  void* grid2 = nullptr;            // real [K][Mz][My][Mxp]
+  const double* gsum = nullptr;     // [K][2]: sum_j gphi_j^c (first entry)
+};
+
+struct BackwardArgs {
+  const double* g_energy;   // device [K] or null
+  const void* g_phi;        // device real [K][n] or null
+  const void* g_forces;     // device real [n][3] or null
+  void* grad_q;             // device real [K][n] or null
+  void* grad_pos;           // device real [n][3] or null
 };
 
 // Each returns cudaSuccess or the launch error.
@@ -33,5 +44,8 @@ cudaError_t launch_spread_float(const LaunchCtx& c, int* nlaunch);
 cudaError_t launch_spread_double(const LaunchCtx& c, int* nlaunch);
 cudaError_t launch_interp_float(const LaunchCtx& c, void* phi, void* forces, int* nlaunch);
 cudaError_t launch_interp_double(const LaunchCtx& c, void* phi, void* forces, int* nlaunch);
+// backward: spread of rhobar into grid2 (stage 0) or the final gather (stage 1)
+cudaError_t launch_backward_float(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch);
+cudaError_t launch_backward_double(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch);
 
 }  // namespace pswf

@@ -170,6 +170,8 @@ class Plan:
         with torch.cuda.device(self.device):
             _check(L.pswf_plan_set_workspace(self._h, _vp(aligned), nbytes), self._h)
         self.n = None
+        self.flags = int(flags)
+        self.generation = 0
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -201,6 +203,7 @@ class Plan:
                                      _vp(q.data_ptr())), self._h)
         self._keep = (pos, q)
         self.n = n
+        self.generation += 1
 
     def execute(self, energy: bool = True, phi: bool = True, forces: bool = True, out=None):
         """Returns (energy [K+1] float64, phi [K, n] or None, forces [n, 3] or None) on the device."""
@@ -264,3 +267,56 @@ class Plan:
         self._stream()
         _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)
         return e, ph, f
+
+
+def _make_function():
+    import torch
+
+    class _LongRange(torch.autograd.Function):
+        """(pos [n,3], q [K,n]) -> (E [K], phi [K,n], F [n,3]) through one
+        plan; the backward is the plan's hand-written VJP (pswf_backward),
+        which needs a plan created with PSWF_FLAG_BACKWARD."""
+
+        @staticmethod
+        def forward(ctx, pos, q, plan):
+            plan.set_points(pos.detach(), q.detach())
+            e, ph, f = plan.execute()
+            ctx.plan = plan
+            ctx.gen = plan.generation
+            ctx.pos_dtype = pos.dtype
+            ctx.q_dtype = q.dtype
+            return e[:-1].clone(), ph, f
+
+        @staticmethod
+        @torch.autograd.function.once_differentiable
+        def backward(ctx, g_e, g_phi, g_f):
+            plan = ctx.plan
+            if plan.generation != ctx.gen:
+                raise PswfError(-8, "the plan was re-run since this forward; its backward state is gone")
+            need_q, need_pos = ctx.needs_input_grad[1], ctx.needs_input_grad[0]
+            if not (need_q or need_pos):
+                return None, None, None
+            gq, gr = plan.backward(g_e, g_phi, g_f, grad_q=need_q, grad_pos=need_pos)
+            gr = gr.to(ctx.pos_dtype) if gr is not None else None
+            gq = gq.to(ctx.q_dtype) if gq is not None else None
+            return gr, gq, None
+
+    return _LongRange
+
+
+_FN = None
+
+
+def long_range(plan: "Plan", pos, q):
+    """Differentiable long-range evaluation: returns (E [K] float64, phi
+    [K, n], forces [n, 3]) with gradients to pos and q through the plan's
+    backward kernels.  The plan must be created with flags=PSWF_FLAG_BACKWARD,
+    and calls on one plan are sequential: a later forward on the same plan
+    replaces the state the pending backward needs (the binding checks this
+    through a generation counter)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    if not (plan.flags & PSWF_FLAG_BACKWARD):
+        raise PswfError(-8, "long_range needs a plan created with flags=PSWF_FLAG_BACKWARD")
+    return _FN.apply(pos, q, plan)

@@ -117,3 +117,42 @@ def test_pswf_total_charged_channels(p):
     tol = {1: 2e-5, 2: 1e-4, 4: 1e-3, 6: 1e-3}[p]
     assert abs(tot["E"] - ew["E"]) < tol * abs(ew["E_self"])
     assert rel_rms(tot["phi"][0], ew["phi"]) < tol
+
+
+def test_o1_vjp_matches_finite_differences():
+    """The oracle's vector-jacobian product (used as the reference of the
+    GPU backward) against central finite differences of evaluate itself, for
+    a loss touching the energies, the potentials and the forces.  A dropped
+    term of the VJP (the zero-frequency part of phi, the second derivative of
+    W in the force term, the grid-mediated part) fails one of the checks."""
+    s = wl.random_system(12, (6.0, 6.5, 7.0), (1, 4), seed=11, neutral=False)
+    M = (12, 13, 14)
+    o = DiscretePSWF(GridConfig(s.box, M, 6, C, 2.5, s.ps, c_w=cw_max(s.box, M, 6, C, 2.5)))
+    rng = np.random.default_rng(3)
+    gE = rng.normal(size=2)
+    gphi = rng.normal(size=(2, 12))
+    gF = rng.normal(size=(12, 3))
+
+    def loss(pos, q):
+        r = o.evaluate(pos, q)
+        return float(np.dot(gE, r["E_ch"].numpy()) + np.sum(gphi * r["phi"].numpy()) + np.sum(gF * r["F"].numpy()))
+
+    gq, gr = o.vjp(s.pos, s.q, gE, gphi, gF)
+    eps = 1e-5
+    for (c, i) in [(0, 0), (1, 5), (0, 11)]:
+        qp, qm = s.q.copy(), s.q.copy()
+        qp[c, i] += eps
+        qm[c, i] -= eps
+        fd = (loss(s.pos, qp) - loss(s.pos, qm)) / (2 * eps)
+        assert abs(fd - float(gq[c, i])) < 1e-6 * max(1.0, abs(fd))
+    for (i, d) in [(0, 0), (3, 1), (7, 2), (11, 0)]:
+        pp, pm = s.pos.copy(), s.pos.copy()
+        pp[i, d] += eps
+        pm[i, d] -= eps
+        fd = (loss(pp, s.q) - loss(pm, s.q)) / (2 * eps)
+        assert abs(fd - float(gr[i, d])) < 1e-6 * max(1.0, abs(fd))
+    # energy-only upstream: dE/dq = phi and dE/dr = -F
+    r = o.evaluate(s.pos, s.q)
+    gq1, gr1 = o.vjp(s.pos, s.q, np.ones(2))
+    assert rel_rms(gq1.numpy(), r["phi"].numpy()) < 1e-12
+    assert rel_rms(gr1.numpy(), -r["F"].numpy()) < 1e-12
