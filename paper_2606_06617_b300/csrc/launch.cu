@@ -18,7 +18,6 @@ namespace {
 
 using R = PSWF_REAL;
 constexpr int kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA on sm_103a
-constexpr int kSpreadThreads = 512;
 constexpr int kGatherThreads = kGatherThreadsFor<R>;
 constexpr int kDirectThreads = 256;
 
@@ -31,37 +30,6 @@ WinCoef<R> win_coef(const LaunchCtx& c) {
   return w;
 }
 
-// Largest staging batch (<= kBatch, multiple of 32) whose shared memory fits.
-template <typename F>
-int pick_batch(F bytes) {
-  for (int b = kBatch; b >= 32; b -= 32)
-    if (bytes(b) <= size_t(kSmemLimit)) return b;
-  return 0;
-}
-
-template <int P>
-cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
-  const WinCoef<R> wc = win_coef(c);
-  const int batch = pick_batch([](int b) { return spread_smem_bytes<R, P>(b); });
-  if (batch == 0) {
-    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
-    k_spread_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st),
-                                                                   c.scell, static_cast<const R*>(c.sq), wc,
-                                                                   static_cast<R*>(c.grid));
-    ++*nlaunch;
-    return cudaGetLastError();
-  }
-  const size_t smem = spread_smem_bytes<R, P>(batch);
-  cudaError_t e = cudaFuncSetAttribute(k_spread<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  const int blocks = std::min(c.ntiles, 148 * 8);
-  k_spread<R, P><<<blocks, kSpreadThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
-                                                             c.scell, static_cast<const R*>(c.sq), wc, batch,
-                                                             static_cast<R*>(c.grid));
-  ++*nlaunch;
-  return cudaGetLastError();
-}
-
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -72,14 +40,55 @@ int sm_count() {
   return n;
 }
 
+// Channels staged per work item: as many as a warp has slots (all of them
+// when K is small), within the shared-memory limit; 0 if not even one fits.
+template <int P, typename F>
+int pick_kc(int K, F bytes) {
+  int kc = std::min(K, TilePad<P>::NS);
+  while (kc > 0 && bytes(kc) > size_t(kSmemLimit)) --kc;
+  return kc;
+}
+
+template <int P, typename Kern>
+cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherThreads, smem);
+  if (e != cudaSuccess) return e;
+  *blocks = int(std::min<int64_t>(items, int64_t(sm_count()) * std::max(per_sm, 1)));
+  return cudaSuccess;
+}
+
+template <int P>
+cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
+  const WinCoef<R> wc = win_coef(c);
+  const int kc = pick_kc<P>(c.geo.K, [](int k) { return spread_smem_bytes<R, P>(k); });
+  if (kc == 0) {
+    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+    k_spread_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st),
+                                                                   c.scell, static_cast<const R*>(c.sq), wc,
+                                                                   static_cast<R*>(c.grid));
+    ++*nlaunch;
+    return cudaGetLastError();
+  }
+  const size_t smem = spread_smem_bytes<R, P>(kc);
+  const int nchunk = (c.geo.K + kc - 1) / kc;
+  int blocks = 0;
+  cudaError_t e = persistent_blocks<P>(k_spread<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
+  if (e != cudaSuccess) return e;
+  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
+                                                             c.scell, static_cast<const R*>(c.sq), wc, kc,
+                                                             static_cast<R*>(c.grid));
+  ++*nlaunch;
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
   const WinCoef<R> wc = win_coef(c);
-  // Stage as many channels as a warp has slots (all of them when K is
-  // small), within the shared-memory limit.
-  int kc = std::min(c.geo.K, GatherPad<P>::NS);
-  while (kc > 0 && gather_smem_bytes<R, P>(kc) > size_t(kSmemLimit)) --kc;
+  const int kc = pick_kc<P>(c.geo.K, [](int k) { return gather_smem_bytes<R, P>(k); });
   if (kc == 0) {
     const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_interp_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
@@ -95,14 +104,10 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
     if (e != cudaSuccess) return e;
   }
   const size_t smem = gather_smem_bytes<R, P>(kc);
-  e = cudaFuncSetAttribute(k_interp<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  int blocks = 0;
+  e = persistent_blocks<P>(k_interp<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
   const int threads = kGatherThreads;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp<R, P>, threads, smem);
-  if (e != cudaSuccess) return e;
-  const int64_t items = int64_t(c.ntiles) * nchunk;
-  const int blocks = int(std::min<int64_t>(items, int64_t(sm_count()) * std::max(per_sm, 1)));
   k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.n, c.nmax, c.geo, c.tile_start, static_cast<const R*>(c.st),
                                                       c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc,
                                                       static_cast<const R*>(c.grid), c.zero_coef, c.charges,

@@ -150,3 +150,19 @@ def test_self_energy_matches_oracle():
     # self_coef: planner (Legendre) vs oracle (Nystrom) derivatives of psi_0 at 0
     np.testing.assert_allclose(g["plan"].self_energy(), ref32, rtol=1e-9)
     np.testing.assert_allclose(g["plan"].self_energy(), o["self"], rtol=1e-7)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP32), (1, TOL_FP64)])
+def test_ionic_melt_subbox(precision, tol):
+    """The ionic-melt workload shape (K = 4 channels p = 1, 2, 4, 6, P = 7,
+    r_c = 7, tol 1e-5) on a density-matched 64^3 sub-box (19,418 atoms,
+    L = 58.33): the same kernels and channel chunking as the 384^3 run."""
+    L = 350.0 * 64 / 384
+    n = int(round(4194304 * (L / 350.0) ** 3))
+    s = wl.ionic_melt(n, L, seed=3)
+    M = (64, 64, 64)
+    c = math.log(3.0 / 1e-5)
+    cw = window_cw(s.box, M, 7, c, 7.0)
+    g = run_gpu(s, 7.0, 7, M, c, cw, precision=precision)
+    o = run_oracle(s, 7.0, 7, M, c, cw)
+    _compare(g, o, tol, "melt sub-box")
