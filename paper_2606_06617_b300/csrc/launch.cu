@@ -40,13 +40,22 @@ int sm_count() {
   return n;
 }
 
-// Channels staged per work item: as many as a warp has slots (all of them
-// when K is small), within the shared-memory limit; 0 if not even one fits.
-template <int P, typename F>
-int pick_kc(int K, F bytes) {
-  int kc = std::min(K, TilePad<P>::NS);
-  while (kc > 0 && bytes(kc) > size_t(kSmemLimit)) --kc;
-  return kc;
+// Channels staged per work item (as many as a warp has slots, all of them
+// when K is small) and atoms per table batch, within the shared memory left
+// beside the kernel's static arrays; false if not even one channel fits.
+template <int P, typename Kern, typename F>
+bool pick_kc_kb(Kern kern, int K, F bytes, int* kc_out, int* kb_out) {
+  cudaFuncAttributes attr;
+  if (cudaFuncGetAttributes(&attr, kern) != cudaSuccess) return false;
+  const size_t budget = size_t(kSmemLimit) - attr.sharedSizeBytes;
+  for (int kc = std::min(K, TilePad<P>::NS); kc >= 1; --kc)
+    for (int kb = 256; kb >= 64; kb -= 32)
+      if (bytes(kc, kb) <= budget) {
+        *kc_out = kc;
+        *kb_out = kb;
+        return true;
+      }
+  return false;
 }
 
 template <int P, typename Kern>
@@ -63,8 +72,8 @@ cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks
 template <int P>
 cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   const WinCoef<R> wc = win_coef(c);
-  const int kc = pick_kc<P>(c.geo.K, [](int k) { return spread_smem_bytes<R, P>(k); });
-  if (kc == 0) {
+  int kc = 0, kb = 0;
+  if (!pick_kc_kb<P>(k_spread<R, P>, c.geo.K, [](int k, int b) { return spread_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
     const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_spread_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st),
                                                                    c.scell, static_cast<const R*>(c.sq), wc,
@@ -72,13 +81,13 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
     ++*nlaunch;
     return cudaGetLastError();
   }
-  const size_t smem = spread_smem_bytes<R, P>(kc);
+  const size_t smem = spread_smem_bytes<R, P>(kc, kb);
   const int nchunk = (c.geo.K + kc - 1) / kc;
   int blocks = 0;
   cudaError_t e = persistent_blocks<P>(k_spread<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
   k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
-                                                             c.scell, static_cast<const R*>(c.sq), wc, kc,
+                                                             c.scell, static_cast<const R*>(c.sq), wc, kc, kb,
                                                              static_cast<R*>(c.grid));
   ++*nlaunch;
   return cudaGetLastError();
@@ -88,8 +97,8 @@ template <int P>
 cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
   const WinCoef<R> wc = win_coef(c);
-  const int kc = pick_kc<P>(c.geo.K, [](int k) { return gather_smem_bytes<R, P>(k); });
-  if (kc == 0) {
+  int kc = 0, kb = 0;
+  if (!pick_kc_kb<P>(k_interp<R, P>, c.geo.K, [](int k, int b) { return gather_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
     const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_interp_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
         c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
@@ -103,13 +112,13 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
     e = cudaMemsetAsync(forces, 0, size_t(c.n) * 3 * sizeof(R), c.stream);
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = gather_smem_bytes<R, P>(kc);
+  const size_t smem = gather_smem_bytes<R, P>(kc, kb);
   int blocks = 0;
   e = persistent_blocks<P>(k_interp<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
   const int threads = kGatherThreads;
   k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.n, c.nmax, c.geo, c.tile_start, static_cast<const R*>(c.st),
-                                                      c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc,
+                                                      c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc, kb,
                                                       static_cast<const R*>(c.grid), c.zero_coef, c.charges,
                                                       static_cast<R*>(phi), static_cast<R*>(forces));
   ++*nlaunch;

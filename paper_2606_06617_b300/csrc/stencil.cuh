@@ -58,9 +58,44 @@ struct TilePad {
 template <typename R>
 constexpr int kGatherThreadsFor = sizeof(R) == 4 ? 1024 : 512;
 
+// Per-batch window tables in shared memory: for each atom of a batch, rows
+// of PW >= P entries (16-byte aligned, read as vectors): W_x, W_y, W_z and,
+// for the gather, (2/h_d) dW/ds in x, y, z.  One thread per (atom, direction)
+// evaluates the P pieces (coefficient reads uniform across the warp).
+template <int P>
+constexpr int kRowW = P <= 4 ? 4 : P <= 8 ? 8 : 16;
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 template <typename R, int P>
-constexpr size_t gather_smem_bytes(int kc) {
-  return size_t(kc) * TilePad<P>::N * sizeof(R);
+constexpr size_t stencil_smem_bytes(int kc, int kb, int rows, size_t acc_size) {
+  return align16(size_t(kc) * TilePad<P>::N * acc_size) + size_t(kb) * (rows * kRowW<P> * sizeof(R) + 2 * sizeof(int));
+}
+template <typename R, int P>
+constexpr size_t gather_smem_bytes(int kc, int kb) {
+  return stencil_smem_bytes<R, P>(kc, kb, 6, sizeof(R));
+}
+
+// P consecutive reals from 16-byte-aligned shared memory, as vector loads.
+template <typename R, int P>
+__device__ inline void lds_row(const R* p, R (&v)[P]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int i = 0; i < P; i += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + i);
+      v[i] = t.x;
+      if (i + 1 < P) v[i + 1] = t.y;
+      if (i + 2 < P) v[i + 2] = t.z;
+      if (i + 3 < P) v[i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < P; i += 2) {
+      const double2 t = *reinterpret_cast<const double2*>(p + i);
+      v[i] = t.x;
+      if (i + 1 < P) v[i + 1] = t.y;
+    }
+  }
 }
 
 template <typename R>
@@ -70,14 +105,84 @@ __device__ inline void cp_async_elem(R* dst, const R* src) {
 }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Slot bookkeeping shared by the spread and the gather.  kc channels are
+// staged; the slots of one atom are a power-of-two group of kcp >= kc slots
+// (slots beyond kc idle), so xor shuffles over the slot bits reduce exactly
+// over one atom's channels.
+struct Slots {
+  int lane, warp, nwarp, j, sbase, kcp, apw, asub, cc;
+  bool used;
+  template <int G, int NS>
+  __device__ static Slots make(int kc) {
+    Slots s;
+    s.lane = threadIdx.x & 31;
+    s.warp = threadIdx.x >> 5;
+    s.nwarp = blockDim.x >> 5;
+    const int slot = s.lane / G;
+    s.j = s.lane % G;
+    s.sbase = s.lane - s.j;
+    s.kcp = 1;
+    while (s.kcp < kc) s.kcp <<= 1;
+    s.apw = NS / s.kcp;
+    s.asub = slot / s.kcp;
+    s.cc = slot - s.asub * s.kcp;
+    s.used = s.asub < s.apw && s.cc < kc;
+    return s;
+  }
+};
+
+template <typename R, int P>
+__device__ inline void tile_origin(const Geometry& g, int tile, int& ox, int& oy, int& oz) {
+  const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
+  ox = tx * kTile;
+  oy = ty * kTile;
+  oz = tz * kTile;
+}
+
+// Fills the batch's window rows (values, and scaled derivatives when
+// rows == 6), the packed local start cell and (gather) the original index.
+template <typename R, int P, int ROWS>
+__device__ inline void batch_tables(const Geometry& g, int64_t nmax, int b0, int nb, int ox, int oy, int oz,
+                                    const R* __restrict__ st, const uint64_t* __restrict__ scell,
+                                    const int* __restrict__ sperm, const WinCoef<R>& wc, R* wts, int* loc,
+                                    int* perm) {
+  constexpr int PW = kRowW<P>;
+  for (int t = threadIdx.x; t < nb * 3; t += blockDim.x) {
+    const int a = t / 3, d = t - 3 * a;
+    R* row = wts + (a * ROWS + d) * PW;
+    if constexpr (ROWS == 6) {
+      R w[P], dw[P];
+      window_weights<R, P>(st[d * nmax + b0 + a], wc, w, dw);
+      const R two_h = R(2.0 * g.M[d] / g.L[d]);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        row[i] = w[i];
+        row[3 * PW + i] = dw[i] * two_h;
+      }
+    } else {
+      R w[P];
+      window_values<R, P>(st[d * nmax + b0 + a], wc, w);
+#pragma unroll
+      for (int i = 0; i < P; ++i) row[i] = w[i];
+    }
+  }
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    int cx, cy, cz;
+    unpack_cell(scell[b0 + t], cx, cy, cz);
+    loc[t] = (cx - ox) | ((cy - oy) << 8) | ((cz - oz) << 16);
+    if (perm) perm[t] = sperm[b0 + t];
+  }
+}
+
 // Spreading (step (i)).  Work items are (tile, chunk of kc channels); the
-// kc padded regions live in shared memory with the layout above.  Lane j of
-// a slot adds the contributions q W_x(i) W_y(j) W_z(k) of its row j for all
-// (i, k) with shared-memory atomics; the slots of a warp are the channels of
-// one atom (or several atoms when K is small), so no two lanes of a warp
-// touch the same bank.  The region is then added into the grid with global
-// atomics, one warp per (channel, z) plane, lanes along x (neighbouring
-// tiles overlap by P - 1 planes); the grid is zeroed before the launch.
+// kc padded regions live in shared memory with the layout above.  The tile's
+// atoms go in batches of kb: their window rows are tabulated, then each warp
+// takes an atom (several when K is small) and lane j of slot cc adds
+// q_c W_x(i) W_y(j) W_z(k) for all (i, k) of row j with shared-memory atomics
+// (the warp's lanes hit 32 distinct banks).  The region is then added into
+// the grid with global atomics, one warp per (channel, z) plane, lanes along
+// x (neighbouring tiles overlap by P - 1 planes); the grid is zeroed before
+// the launch.
 //
 // FP32 path: contributions are rounded to integers of a per-(tile, channel)
 // fixed point 1/s and summed exactly in 32 bits.  The rounding is one FFMA
@@ -87,8 +192,8 @@ __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n"
 // and every grid sum below 2^31 (the window is at most 1).  FP64 path:
 // double atomics.
 template <typename R, int P>
-constexpr size_t spread_smem_bytes(int kc) {
-  return size_t(kc) * TilePad<P>::N * sizeof(typename SpreadAcc<R>::T);
+constexpr size_t spread_smem_bytes(int kc, int kb) {
+  return stencil_smem_bytes<R, P>(kc, kb, 3, sizeof(typename SpreadAcc<R>::T));
 }
 
 template <typename R, int P>
@@ -97,22 +202,20 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
                                                                    const R* __restrict__ st,
                                                                    const uint64_t* __restrict__ scell,
                                                                    const R* __restrict__ sq, WinCoef<R> wc, int kc,
-                                                                   R* __restrict__ grid) {
+                                                                   int kb, R* __restrict__ grid) {
   using A = typename SpreadAcc<R>::T;
   constexpr bool kFixed = std::is_same<A, int>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   using L = TilePad<P>;
-  constexpr int G = L::G, NS = L::NS, S = L::S, R1 = L::R1, R2 = L::R2, N = L::N;
+  constexpr int G = L::G, NS = L::NS, S = L::S, R1 = L::R1, R2 = L::R2, N = L::N, PW = kRowW<P>;
   A* region = reinterpret_cast<A*>(smraw);   // [kc][N]
+  R* wts = reinterpret_cast<R*>(smraw + align16(size_t(kc) * N * sizeof(A)));   // [kb][3][PW]
+  int* loc = reinterpret_cast<int*>(wts + kb * 3 * PW);
   __shared__ float red_sum[32][NS], red_max[32][NS];
   __shared__ float sscale[NS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int slot = lane / G, j = lane % G, sbase = lane - j;
+  const Slots sl = Slots::template make<G, NS>(kc);
+  const int lane = sl.lane, warp = sl.warp, nwarp = sl.nwarp, j = sl.j, cc = sl.cc;
   const int nchunk = (g.K + kc - 1) / kc;
-  const int apw = NS / kc;
-  const int asub = slot / kc, cc = slot - asub * kc;
-  const bool slot_used = asub < apw;
-  const int jr = j < P ? j : P - 1;
   const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   for (int item = blockIdx.x; item < ntiles * nchunk; item += gridDim.x) {
@@ -120,8 +223,8 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
     if (a0 == a1) continue;
     const int c0 = chunk * kc, nk = min(kc, g.K - c0);
-    const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
-    const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
+    int ox, oy, oz;
+    tile_origin<R, P>(g, tile, ox, oy, oz);
     __syncthreads();   // the previous item's flush is done with the region
     {
       const int nbytes = nk * N * int(sizeof(A));
@@ -130,7 +233,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
       int* r1 = reinterpret_cast<int*>(region);
       for (int t = (nbytes / 16) * 4 + threadIdx.x; t < nbytes / 4; t += blockDim.x) r1[t] = 0;
     }
-    if (kFixed) {
+    if constexpr (kFixed) {
       float s1[NS], mx[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) s1[c] = mx[c] = 0.0f;
@@ -160,43 +263,27 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
           tot += red_sum[w][threadIdx.x];
           m = fmaxf(m, red_max[w][threadIdx.x]);
         }
-        sscale[threadIdx.x] = tot > 0.0f ? fminf(0.99f * 4194304.0f / m, 0.999f * 2147483647.0f / (tot * 1.0001f)) : 1.0f;
+        sscale[threadIdx.x] =
+            tot > 0.0f ? fminf(0.99f * 4194304.0f / m, 0.999f * 2147483647.0f / (tot * 1.0001f)) : 1.0f;
       }
     }
-    __syncthreads();
-    const bool use_slot = slot_used && cc < nk;
-    const R qscale = kFixed && use_slot ? R(sscale[cc]) : R(1);
-    for (int base = a0 + warp * apw; base < a1; base += nwarp * apw) {
-      const int a_raw = base + asub;
-      const bool valid = use_slot && a_raw < a1;
-      const int a = min(a_raw, a1 - 1);
-      R wj[3];
-      {
-        const R s0 = R(2) * st[a] - R(1), s1 = R(2) * st[nmax + a] - R(1), s2 = R(2) * st[2 * nmax + a] - R(1);
-        const int deg = wc.deg;
-        const R* c = wc.c + jr * (deg + 1);
-        R v0 = c[deg], v1 = v0, v2 = v0;
-        for (int m = deg - 1; m >= 0; --m) {
-          const R cm = c[m];
-          v0 = v0 * s0 + cm;
-          v1 = v1 * s1 + cm;
-          v2 = v2 * s2 + cm;
-        }
-        wj[0] = v0;
-        wj[1] = v1;
-        wj[2] = v2;
-      }
-      R wx[P], wz[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        wx[i] = __shfl_sync(0xffffffffu, wj[0], sbase + i);
-        wz[i] = __shfl_sync(0xffffffffu, wj[2], sbase + i);
-      }
-      if (valid && j < P) {
-        int cx, cy, cz;
-        unpack_cell(scell[a], cx, cy, cz);
-        A* row = region + cc * N + (cz - oz) * R2 + (cy - oy + j) * R1 + (cx - ox);
-        const R qy = sq[int64_t(c0 + cc) * nmax + a] * qscale * wj[1];
+    const bool use_slot = sl.used && cc < nk;
+    for (int b0 = a0; b0 < a1; b0 += kb) {
+      const int nb = min(kb, a1 - b0);
+      __syncthreads();   // previous batch done with the tables (and sscale written)
+      batch_tables<R, P, 3>(g, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
+      __syncthreads();
+      const R qscale = kFixed && use_slot ? R(sscale[cc]) : R(1);
+      for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
+        const int al = ab + sl.asub;
+        if (!(use_slot && al < nb && j < P)) continue;
+        const R* wa = wts + al * 3 * PW;
+        R wx[P], wz[P];
+        lds_row<R, P>(wa, wx);
+        lds_row<R, P>(wa + 2 * PW, wz);
+        const int l = loc[al];
+        A* row = region + cc * N + ((l >> 16) & 0xff) * R2 + (((l >> 8) & 0xff) + j) * R1 + (l & 0xff);
+        const R qy = sq[int64_t(c0 + cc) * nmax + b0 + al] * qscale * wa[PW + j];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
           const R coef = qy * wz[k];
@@ -267,31 +354,37 @@ __global__ void k_spread_direct(int64_t n, int64_t nmax, Geometry g, const R* __
 // Gather of phi_c = sum Psi_c W + 2 a_c Q_c and F = sum_c q_c sum Psi_c grad W
 // (grad_d W = (2 / h_d) dW/ds).  Work items are (tile, chunk of kc channels);
 // per item the kc padded regions of Psi are staged with asynchronous copies
-// (one warp per (channel, z) plane, lanes along x), then every warp walks the
-// tile's atoms.  Lane j of a slot evaluates window piece j in x, y and z and
-// the slot exchanges them by shuffles; the potential of a channel is reduced
-// over its slot, the force over the atom's slots.  With more than one chunk
-// the force is accumulated with global atomics (zeroed before the launch).
+// (one warp per (channel, z) plane, lanes along x) while the first batch's
+// window rows are tabulated.  Lane j of slot cc sweeps row j of the atom's
+// stencil in channel cc.  The four sums (phi, and the three components of
+// q_c f_c) are reduced over the slot's lanes by a transposing butterfly
+// (after it, lane group v of the slot holds sum v), the force components
+// then over the atom's slots.  With more than one chunk the force is
+// accumulated with global atomics (zeroed before the launch).
 template <typename R, int P>
 __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, int64_t nmax, Geometry g,
-                                                   const int* __restrict__ tile_start, const R* __restrict__ st,
-                                                   const uint64_t* __restrict__ scell, const R* __restrict__ sq,
-                                                   const int* __restrict__ sperm, WinCoef<R> wc, int kc,
-                                                   const R* __restrict__ grid, const double* __restrict__ zero_coef,
-                                                   const double* __restrict__ charges, R* __restrict__ phi,
-                                                   R* __restrict__ forces) {
+                                                                   const int* __restrict__ tile_start,
+                                                                   const R* __restrict__ st,
+                                                                   const uint64_t* __restrict__ scell,
+                                                                   const R* __restrict__ sq,
+                                                                   const int* __restrict__ sperm, WinCoef<R> wc,
+                                                                   int kc, int kb, const R* __restrict__ grid,
+                                                                   const double* __restrict__ zero_coef,
+                                                                   const double* __restrict__ charges,
+                                                                   R* __restrict__ phi, R* __restrict__ forces) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using L = TilePad<P>;
-  constexpr int G = L::G, NS = L::NS, S = L::S, R1 = L::R1, R2 = L::R2, N = L::N;
+  constexpr int G = L::G, NS = L::NS, S = L::S, R1 = L::R1, R2 = L::R2, N = L::N, PW = kRowW<P>;
+  constexpr int GQ = G / 4;   // lanes per reduced sum after the butterfly
   R* region = reinterpret_cast<R*>(smraw);   // [kc][N]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int slot = lane / G, j = lane % G, sbase = lane - j;
+  R* wts = reinterpret_cast<R*>(smraw + align16(size_t(kc) * N * sizeof(R)));   // [kb][6][PW]
+  int* loc = reinterpret_cast<int*>(wts + kb * 6 * PW);
+  int* perm = loc + kb;
+  const Slots sl = Slots::template make<G, NS>(kc);
+  const int lane = sl.lane, warp = sl.warp, nwarp = sl.nwarp, j = sl.j, cc = sl.cc;
   const int nchunk = (g.K + kc - 1) / kc;
-  const int apw = NS / kc;                 // atoms per warp
-  const int asub = slot / kc, cc = slot - asub * kc;
-  const bool slot_used = asub < apw;
   const int jr = j < P ? j : P - 1;        // row read by lanes beyond the stencil
-  const R two_h[3] = {R(2.0 * g.M[0] / g.L[0]), R(2.0 * g.M[1] / g.L[1]), R(2.0 * g.M[2] / g.L[2])};
+  const int vi = j / GQ;                   // which sum this lane ends up holding
   const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   for (int item = blockIdx.x; item < ntiles * nchunk; item += gridDim.x) {
@@ -299,9 +392,9 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, i
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
     if (a0 == a1) continue;
     const int c0 = chunk * kc, nk = min(kc, g.K - c0);
-    const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
-    const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
-    __syncthreads();   // the previous item's reads of the region are done
+    int ox, oy, oz;
+    tile_origin<R, P>(g, tile, ox, oy, oz);
+    __syncthreads();   // the previous item's reads of the region and tables are done
     {
       const int gx = lane < S ? wrap_index(ox + lane, g.M[0]) : 0;
       for (int pl = warp; pl < nk * S; pl += nwarp) {
@@ -317,94 +410,71 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, i
           }
         }
       }
-      cp_async_wait_all();
     }
-    __syncthreads();
-    const bool use_slot = slot_used && cc < nk;
-    for (int base = a0 + warp * apw; base < a1; base += nwarp * apw) {
-      const int a_raw = base + asub;
-      const bool valid = use_slot && a_raw < a1;
-      const int a = min(a_raw, a1 - 1);
-      // window pieces: lane j of the slot evaluates piece j in each direction
-      R wj[3], dj[3];
-      {
-        const R s0 = R(2) * st[a] - R(1), s1 = R(2) * st[nmax + a] - R(1), s2 = R(2) * st[2 * nmax + a] - R(1);
-        const int deg = wc.deg;
-        const R* c = wc.c + jr * (deg + 1);
-        R v0 = c[deg], v1 = v0, v2 = v0, e0 = 0, e1 = 0, e2 = 0;
-        for (int m = deg - 1; m >= 0; --m) {
-          const R cm = c[m];
-          e0 = e0 * s0 + v0;
-          e1 = e1 * s1 + v1;
-          e2 = e2 * s2 + v2;
-          v0 = v0 * s0 + cm;
-          v1 = v1 * s1 + cm;
-          v2 = v2 * s2 + cm;
+    const bool use_slot = sl.used && cc < nk;
+    for (int b0 = a0; b0 < a1; b0 += kb) {
+      const int nb = min(kb, a1 - b0);
+      if (b0 != a0) __syncthreads();   // previous batch done with the tables
+      batch_tables<R, P, 6>(g, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
+      if (b0 == a0) cp_async_wait_all();
+      __syncthreads();
+      for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
+        const int al_raw = ab + sl.asub;
+        const bool valid = use_slot && al_raw < nb;
+        const int al = min(al_raw, nb - 1);
+        const R* wa = wts + al * 6 * PW;
+        R wx[P], dx[P], wz[P], dz[P];
+        lds_row<R, P>(wa, wx);
+        lds_row<R, P>(wa + 3 * PW, dx);
+        lds_row<R, P>(wa + 2 * PW, wz);
+        lds_row<R, P>(wa + 5 * PW, dz);
+        const R wy = j < P ? wa[PW + j] : R(0), dy = j < P ? wa[4 * PW + j] : R(0);
+        const int l = loc[al];
+        const R* row = region + (use_slot ? cc : 0) * N + ((l >> 16) & 0xff) * R2 + (((l >> 8) & 0xff) + jr) * R1 +
+                       (l & 0xff);
+        R A = 0, Az = 0, B = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          R sx = 0, dsx = 0;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const R v = row[k * R2 + i];
+            sx += v * wx[i];
+            dsx += v * dx[i];
+          }
+          A += sx * wz[k];
+          Az += sx * dz[k];
+          B += dsx * wz[k];
         }
-        wj[0] = v0; wj[1] = v1; wj[2] = v2;
-        dj[0] = e0 * two_h[0]; dj[1] = e1 * two_h[1]; dj[2] = e2 * two_h[2];
-      }
-      R wx[P], dx[P], wz[P], dz[P];
+        const R q = valid ? sq[int64_t(c0 + cc) * nmax + b0 + al] : R(0);
+        // butterfly over the slot: (phi, q f_x, q f_y, q f_z) -> one sum per lane group
+        R v;
+        {
+          const R v0 = A * wy, v1 = q * B * wy, v2 = q * A * dy, v3 = q * Az * wy;
+          const bool hi = (j & (G / 2)) != 0;
+          R k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+          const R s0 = hi ? v0 : v2, s1 = hi ? v1 : v3;
+          k0 += __shfl_xor_sync(0xffffffffu, s0, G / 2);
+          k1 += __shfl_xor_sync(0xffffffffu, s1, G / 2);
+          const bool hi2 = (j & GQ) != 0;
+          v = hi2 ? k1 : k0;
+          v += __shfl_xor_sync(0xffffffffu, hi2 ? k0 : k1, GQ);
 #pragma unroll
-      for (int i = 0; i < P; ++i) {
-        wx[i] = __shfl_sync(0xffffffffu, wj[0], sbase + i);
-        dx[i] = __shfl_sync(0xffffffffu, dj[0], sbase + i);
-        wz[i] = __shfl_sync(0xffffffffu, wj[2], sbase + i);
-        dz[i] = __shfl_sync(0xffffffffu, dj[2], sbase + i);
-      }
-      const R wy = j < P ? wj[1] : R(0), dy = j < P ? dj[1] : R(0);
-      int cx, cy, cz;
-      unpack_cell(scell[a], cx, cy, cz);
-      const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
-      const R* row = region + (use_slot ? cc : 0) * N + lz * R2 + (ly + jr) * R1 + lx;
-      R A = 0, Az = 0, B = 0;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        R sx = 0, dsx = 0;
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          const R v = row[k * R2 + i];
-          sx += v * wx[i];
-          dsx += v * dx[i];
+          for (int o = GQ / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         }
-        A += sx * wz[k];
-        Az += sx * dz[k];
-        B += dsx * wz[k];
-      }
-      const R q = valid ? sq[int64_t(c0 + cc) * nmax + a] : R(0);
-      R ph = A * wy, f0 = q * B * wy, f1 = q * A * dy, f2 = q * Az * wy;
-#pragma unroll
-      for (int o = 1; o < G; o <<= 1) {
-        ph += __shfl_xor_sync(0xffffffffu, ph, o);
-        f0 += __shfl_xor_sync(0xffffffffu, f0, o);
-        f1 += __shfl_xor_sync(0xffffffffu, f1, o);
-        f2 += __shfl_xor_sync(0xffffffffu, f2, o);
-      }
-      // channels of the same atom sit in neighbouring slots: cc = 0 collects
-      const R e0 = f0, e1 = f1, e2 = f2;
-      for (int s2 = 1; s2 < kc; ++s2) {
-        const int src = min(lane + s2 * G, 31);
-        const R g0 = __shfl_sync(0xffffffffu, e0, src), g1 = __shfl_sync(0xffffffffu, e1, src),
-                g2 = __shfl_sync(0xffffffffu, e2, src);
-        if (cc + s2 < nk) {
-          f0 += g0;
-          f1 += g1;
-          f2 += g2;
-        }
-      }
-      if (valid && j == 0) {
-        const int o = sperm[a];
-        if (phi) phi[int64_t(c0 + cc) * n + o] = ph + R(2.0 * zero_coef[c0 + cc] * charges[2 * (c0 + cc)]);
-        if (forces && cc == 0) {
-          R* fo = forces + 3 * int64_t(o);
-          if (nchunk == 1) {
-            fo[0] = f0;
-            fo[1] = f1;
-            fo[2] = f2;
-          } else {
-            atomicAdd(fo, f0);
-            atomicAdd(fo + 1, f1);
-            atomicAdd(fo + 2, f2);
+        // force components over the atom's slots (idle slots carry q = 0)
+        R fsum = v;
+        for (int o = G; o < G * sl.kcp; o <<= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+        if (valid && j % GQ == 0) {
+          const int o = perm[al];
+          if (vi == 0) {
+            if (phi) phi[int64_t(c0 + cc) * n + o] = v + R(2.0 * zero_coef[c0 + cc] * charges[2 * (c0 + cc)]);
+          } else if (forces && cc == 0) {
+            R* fo = forces + 3 * int64_t(o) + (vi - 1);
+            if (nchunk == 1)
+              *fo = fsum;
+            else
+              atomicAdd(fo, fsum);
           }
         }
       }
