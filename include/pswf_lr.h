@@ -76,6 +76,8 @@ typedef struct {
   int P, K, precision, deg_window, deg_mult, flags;
   int64_t n_max;
   int64_t workspace_bytes; /* device bytes pswf_plan_set_workspace wants */
+  int B;                   /* structures per call (1 for single-structure plans) */
+  int batch;               /* 1 for plans made by pswf_batch_plan_create */
 } pswf_info;
 
 typedef struct pswf_plan_s* pswf_plan;
@@ -126,6 +128,40 @@ int pswf_set_points(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, c
  * When the plan has PSWF_FLAG_BACKWARD the grid potential is kept for
  * pswf_backward. */
 int pswf_execute(pswf_plan plan, double* energy, void* phi, void* forces);
+
+/* ---- batches of structures ---------------------------------------------
+ * A batch plan evaluates up to b_max independent structures per call, each
+ * with its own orthorhombic box and atoms, all on one grid size (the serving
+ * and training workloads: many small systems).  Per structure the result is
+ * the same computation as a single-structure plan with the same grid, c_w
+ * and P; the paper evaluates one structure at a time and has no counterpart
+ * for the batching itself.
+ *
+ * pswf_batch_plan_create: box_max host [3] is the largest box edge per axis
+ * any structure may have; the grid (opts->grid or the planner's choice),
+ * eta, c_w and P are chosen at box_max, so every smaller box is on a finer
+ * grid (smaller eta: the same window stays alias-free).  pset host [npset]
+ * lists the exponents channels may use (multiplier tables are built for
+ * these only).  n_max is the total atom capacity of one call.  The energy of
+ * pswf_execute becomes device double [b_max][K + 1]; phi and forces keep the
+ * [K][n] and [n][3] layouts over the concatenated atoms but must hold n_max
+ * entries (rows) each; pswf_self_energy fills host double [b_max][K];
+ * pswf_backward takes g_energy as device double [b_max][K].
+ * pswf_set_points, pswf_compute_host and pswf_self_energy_noalloc reject
+ * batch plans (PSWF_EINVAL). */
+int pswf_batch_plan_create(const double box_max[3], int b_max, int64_t n_max, int K, const int* pset, int npset,
+                           const pswf_opts* opts, void* stream, pswf_plan* out);
+
+/* Sets the structures of the next pswf_execute.  b (0..b_max) structures;
+ * boxes host double [b][3] (each edge <= box_max); ps host int [b][K]
+ * exponents (from the plan's pset); offsets host int64 [b + 1], offsets[0] =
+ * 0, non-decreasing: structure s owns atoms offsets[s] .. offsets[s+1] - 1 of
+ * pos (device [n][3], float or double) and of q (device real [K][n]), n =
+ * offsets[b] <= n_max.  Slots b..b_max-1 are empty (zero energy).  The box
+ * tables are computed on the host into a pinned buffer owned by the plan and
+ * copied on the plan's stream; a later call first waits for that copy. */
+int pswf_batch_set_points(pswf_plan plan, int b, const double* boxes, const int* ps, const int64_t* offsets,
+                          const void* pos, int pos_dtype, const void* q);
 
 /* Vector-Jacobian product of the last pswf_execute (asynchronous; needs
  * PSWF_FLAG_BACKWARD and the same points).  Upstream gradients, each may be

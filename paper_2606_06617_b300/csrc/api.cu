@@ -94,15 +94,18 @@ __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __res
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = acc;
 }
 
-// energy[c] = sum of partials + zero_coef[c] * Q_net^2; energy[K] = total.
+// One block per structure s: energy[s][c] = sum of the partials of channel
+// g = s K + c + zero_coef[g] Q_net^2; energy[s][K] = total.
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy) {
   __shared__ double sh[32];
   __shared__ double tot;
+  const int s = blockIdx.x;
   if (threadIdx.x == 0) tot = 0.0;
   for (int c = 0; c < K; ++c) {
+    const int g = s * K + c;
     double e = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) e += part[size_t(c) * nblk + i];
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) e += part[size_t(g) * nblk + i];
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
@@ -110,13 +113,35 @@ __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part,
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-      const double Q = charges[2 * c];
-      const double ec = t + zero_coef[c] * Q * Q;
-      energy[c] = ec;
+      const double Q = charges[2 * g];
+      const double ec = t + zero_coef[g] * Q * Q;
+      energy[size_t(s) * (K + 1) + c] = ec;
       tot += ec;
     }
   }
-  if (threadIdx.x == 0) energy[K] = tot;
+  if (threadIdx.x == 0) energy[size_t(s) * (K + 1) + K] = tot;
+}
+
+__global__ void k_set_count(int* __restrict__ soff, int n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    soff[0] = 0;
+    soff[1] = n;
+  }
+}
+
+__global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
+                                   double* __restrict__ charges) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B * K) return;
+  const int s = g / K, c = g - s * K;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    const size_t o = ((size_t(s) * nblk + i) * K + c) * 2;
+    a += part[o];
+    b += part[o + 1];
+  }
+  charges[2 * g] = a;
+  charges[2 * g + 1] = b;
 }
 
 }  // namespace pswf
@@ -127,7 +152,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kEnergyBlocks = 592;   // 4 x 148 SMs
-constexpr int kQBlocks = 148;
+constexpr int kQBlocks = 148;        // charge-sum blocks of a single-structure plan
+constexpr int kQBlocksBatch = 8;     // per structure in a batch plan
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
@@ -141,6 +167,12 @@ struct pswf_plan_s {
   int64_t n = -1;            // atoms of the last set_points (-1: none)
   bool psi_valid = false;    // grid holds Psi of the last execute (backward plans)
   int flags = 0;
+  bool batch = false;        // created by pswf_batch_plan_create
+  int B = 1;                 // structures (slots)
+  int nts = 0;               // tiles per structure
+  int nqb = kQBlocks;        // charge-sum blocks per structure
+  int eblk = kEnergyBlocks;  // multiplier blocks per (structure, channel)
+  int Mh = 0;                // max_d (M_d / 2 + 1): row stride of the iw2 tables
   size_t real_size = 4;
   Geometry geo{};
   int ntiles = 0;
@@ -154,6 +186,8 @@ struct pswf_plan_s {
   // device pointers inside the workspace
   void* grid = nullptr;      // real [K][Mz][My][Mxp]
   void* grid2 = nullptr;     // second grid (backward)
+  void* tmp_t = nullptr;     // real [3][n_max] window offsets, caller order
+  uint64_t* tmp_cell = nullptr;  // [n_max] packed start cells, caller order
   void* st = nullptr;        // real [3][n_max]
   uint64_t* scell = nullptr; // [n_max]
   void* sq = nullptr;        // real [K][n_max]
@@ -163,17 +197,26 @@ struct pswf_plan_s {
   int* tile_count = nullptr; // [ntiles]
   int* tile_start = nullptr; // [ntiles + 1]
   int* scan_sums = nullptr;  // [scan_blocks]
-  double* qpart = nullptr;   // [kQBlocks][K][2]
-  double* charges = nullptr; // [K][2]: Q_net, Q_self
-  double* bsum = nullptr;    // [K][2]: sum and sum of squares of the upstream gphi (backward)
-  double* epart = nullptr;   // [K][kEnergyBlocks]
-  double* energy_tmp = nullptr; // [K + 1]
+  double* qpart = nullptr;   // [B][nqb][K][2]
+  double* charges = nullptr; // [B K][2]: Q_net, Q_self
+  double* bsum = nullptr;    // [B K][2]: sum and sum of squares of the upstream gphi (backward)
+  double* epart = nullptr;   // [B K][eblk]
+  double* energy_tmp = nullptr; // [B][K + 1]
   int* err = nullptr;        // device status flag
-  int* pch = nullptr;        // [K] exponents
-  double* scale = nullptr;   // [K] multiplier scale (includes dV^2 / V)
-  double* zero_coef = nullptr;  // [K]
-  void* coef_m = nullptr;    // real [K][kMultSeg][deg_m + 1]
-  void* iw2[3] = {nullptr, nullptr, nullptr};  // real [M_d / 2 + 1]
+  void* coef_m = nullptr;    // real [6][kMultSeg][deg_m + 1], row p - 1
+  // per-structure tables, one contiguous region (uploaded in one copy):
+  void* stab = nullptr;
+  int64_t stab_bytes = 0;
+  int64_t stab_off[6] = {0, 0, 0, 0, 0, 0};
+  double* sbox = nullptr;    // [B][3] box edges
+  double* scale = nullptr;   // [B K] multiplier scale (includes dV^2 / V)
+  double* zero_coef = nullptr;  // [B K]
+  int* soff = nullptr;       // [B + 1] atom offsets per structure
+  int* pch = nullptr;        // [B K] exponents
+  void* iw2 = nullptr;       // real [B][3][Mh]
+  void* h_stab = nullptr;    // pinned host mirror of stab (batch plans)
+  cudaEvent_t stab_ev = nullptr;  // last upload from h_stab
+  std::vector<int> h_pch;    // host copy of pch
   void* fft_work = nullptr;
   // cuFFT
   cufftHandle fwd = 0, inv = 0;
@@ -243,11 +286,27 @@ struct StageScope {
   }
 };
 
+// Layout of the per-structure table region (also the pinned host mirror):
+// sbox double [B][3] | scale double [B K] | zero_coef double [B K] |
+// soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh]; returns bytes.
+int64_t stab_layout(pswf_plan p) {
+  const int64_t B = p->B, K = p->host.K, rs = int64_t(p->real_size);
+  auto a16 = [](int64_t b) { return (b + 15) & ~int64_t(15); };
+  int64_t off = 0;
+  p->stab_off[0] = off; off = a16(off + B * 3 * 8);
+  p->stab_off[1] = off; off = a16(off + B * K * 8);
+  p->stab_off[2] = off; off = a16(off + B * K * 8);
+  p->stab_off[3] = off; off = a16(off + (B + 1) * 4);
+  p->stab_off[4] = off; off = a16(off + B * K * 4);
+  p->stab_off[5] = off; off = a16(off + B * 3 * int64_t(p->Mh) * rs);
+  return off;
+}
+
 // Workspace layout (each region 256-byte aligned).  Returns total bytes and,
 // when base != nullptr, assigns the pointers.
 int64_t layout(pswf_plan p, char* base) {
   const Plan& h = p->host;
-  const int K = h.K;
+  const int64_t K = h.K, B = p->B, BK = B * K;
   const int64_t rs = int64_t(p->real_size);
   int64_t off = 0;
   auto take = [&](int64_t bytes) -> char* {
@@ -258,6 +317,8 @@ int64_t layout(pswf_plan p, char* base) {
   p->grid = take(p->grid_elems * rs);
   p->grid2 = (p->flags & PSWF_FLAG_BACKWARD) ? take(p->grid_elems * rs) : nullptr;
   const int64_t nm = std::max<int64_t>(p->n_max, 1);
+  p->tmp_t = take(3 * nm * rs);
+  p->tmp_cell = reinterpret_cast<uint64_t*>(take(nm * 8));
   p->st = take(3 * nm * rs);
   p->scell = reinterpret_cast<uint64_t*>(take(nm * 8));
   p->sq = take(K * nm * rs);
@@ -267,17 +328,24 @@ int64_t layout(pswf_plan p, char* base) {
   p->tile_count = reinterpret_cast<int*>(take(int64_t(p->ntiles) * 4));
   p->tile_start = reinterpret_cast<int*>(take(int64_t(p->ntiles + 1) * 4));
   p->scan_sums = reinterpret_cast<int*>(take(int64_t(p->scan_blocks) * 4));
-  p->qpart = reinterpret_cast<double*>(take(int64_t(kQBlocks) * K * 2 * 8));
-  p->charges = reinterpret_cast<double*>(take(int64_t(K) * 2 * 8));
-  p->bsum = reinterpret_cast<double*>(take(int64_t(K) * 2 * 8));
-  p->epart = reinterpret_cast<double*>(take(int64_t(K) * kEnergyBlocks * 8));
-  p->energy_tmp = reinterpret_cast<double*>(take(int64_t(K + 1) * 8));
+  p->qpart = reinterpret_cast<double*>(take(B * p->nqb * K * 2 * 8));
+  p->charges = reinterpret_cast<double*>(take(BK * 2 * 8));
+  p->bsum = reinterpret_cast<double*>(take(BK * 2 * 8));
+  p->epart = reinterpret_cast<double*>(take(BK * p->eblk * 8));
+  p->energy_tmp = reinterpret_cast<double*>(take(B * (K + 1) * 8));
   p->err = reinterpret_cast<int*>(take(4));
-  p->pch = reinterpret_cast<int*>(take(int64_t(K) * 4));
-  p->scale = reinterpret_cast<double*>(take(int64_t(K) * 8));
-  p->zero_coef = reinterpret_cast<double*>(take(int64_t(K) * 8));
-  p->coef_m = take(int64_t(K) * kMultSeg * (h.deg_m + 1) * rs);
-  for (int d = 0; d < 3; ++d) p->iw2[d] = take(int64_t(h.M[d] / 2 + 1) * rs);
+  p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
+  p->stab_bytes = stab_layout(p);
+  char* st = take(p->stab_bytes);
+  p->stab = st;
+  if (st) {
+    p->sbox = reinterpret_cast<double*>(st + p->stab_off[0]);
+    p->scale = reinterpret_cast<double*>(st + p->stab_off[1]);
+    p->zero_coef = reinterpret_cast<double*>(st + p->stab_off[2]);
+    p->soff = reinterpret_cast<int*>(st + p->stab_off[3]);
+    p->pch = reinterpret_cast<int*>(st + p->stab_off[4]);
+    p->iw2 = st + p->stab_off[5];
+  }
   p->fft_work = take(int64_t(p->fft_work_bytes));
   return off;
 }
@@ -292,25 +360,75 @@ int upload(pswf_plan p, void* dst, const std::vector<T>& v, const char* what) {
   return cuda_check(p, cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
 }
 
+// Fills a host image of the table region for structures 0..b-1 (boxes
+// [b][3], exponents [b][K], atom offsets [b + 1]); slots b..B-1 are empty
+// (no atoms, zero scale).  Exponents must be ones the plan was built for.
+int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int64_t* offsets, char* dst) {
+  const Plan& h = p->host;
+  const int K = h.K, B = p->B;
+  double* sbox = reinterpret_cast<double*>(dst + p->stab_off[0]);
+  double* scale = reinterpret_cast<double*>(dst + p->stab_off[1]);
+  double* zero = reinterpret_cast<double*>(dst + p->stab_off[2]);
+  int* soff = reinterpret_cast<int*>(dst + p->stab_off[3]);
+  int* pch = reinterpret_cast<int*>(dst + p->stab_off[4]);
+  char* iw2 = dst + p->stab_off[5];
+  int pdef = 0;
+  for (int q = 1; q <= 6 && !pdef; ++q)
+    if (h.mult_scale_p[q] != 0.0) pdef = q;
+  p->h_pch.assign(size_t(B) * K, pdef);
+  StructTables t;
+  std::string err;
+  for (int sidx = 0; sidx < B; ++sidx) {
+    const bool used = sidx < b;
+    if (used) {
+      int rc = struct_tables(h, boxes + 3 * sidx, t, err);
+      if (rc) return set_err(p, rc, "structure " + std::to_string(sidx) + ": " + err);
+    } else {
+      int rc = struct_tables(h, h.box_max, t, err);
+      if (rc) return set_err(p, rc, err);
+    }
+    for (int d = 0; d < 3; ++d) sbox[3 * sidx + d] = t.box[d];
+    const double dv2v = t.dV * t.dV / t.V;
+    for (int c = 0; c < K; ++c) {
+      const int g = sidx * K + c;
+      const int pp = used ? ps[size_t(sidx) * K + c] : pdef;
+      if (pp < 1 || pp > 6 || h.mult_scale_p[pp] == 0.0)
+        return set_err(p, PSWF_EINVAL, "exponent p of structure " + std::to_string(sidx) + " was not planned for");
+      pch[g] = pp;
+      p->h_pch[g] = pp;
+      scale[g] = used ? h.mult_scale_p[pp] * dv2v : 0.0;
+      zero[g] = used ? h.zero_num_p[pp] / t.V : 0.0;
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int m = 0; m < p->Mh; ++m) {
+        const double v = m < int(t.iw2[d].size()) ? t.iw2[d][m] : 0.0;
+        const size_t o = (size_t(sidx) * 3 + d) * p->Mh + m;
+        if (p->real_size == 4)
+          reinterpret_cast<float*>(iw2)[o] = float(v);
+        else
+          reinterpret_cast<double*>(iw2)[o] = v;
+      }
+  }
+  for (int sidx = 0; sidx <= B; ++sidx) soff[sidx] = int(offsets ? offsets[std::min(sidx, b)] : 0);
+  return PSWF_OK;
+}
+
 int upload_tables(pswf_plan p) {
   const Plan& h = p->host;
-  const int K = h.K;
   int rc;
-  std::vector<double> scale(K);
-  const double dv2v = h.dV * h.dV / h.V;
-  for (int k = 0; k < K; ++k) scale[k] = h.mult_scale[k] * dv2v;
-  if ((rc = upload(p, p->pch, h.p, "upload p"))) return rc;
-  if ((rc = upload(p, p->scale, scale, "upload scale"))) return rc;
-  if ((rc = upload(p, p->zero_coef, h.zero_coef, "upload zero"))) return rc;
   if (p->real_size == 4) {
     if ((rc = upload(p, p->coef_m, to_real<float>(h.coef_m), "upload coef"))) return rc;
-    for (int d = 0; d < 3; ++d)
-      if ((rc = upload(p, p->iw2[d], to_real<float>(h.iw2[d]), "upload iw2"))) return rc;
   } else {
     if ((rc = upload(p, p->coef_m, h.coef_m, "upload coef"))) return rc;
-    for (int d = 0; d < 3; ++d)
-      if ((rc = upload(p, p->iw2[d], h.iw2[d], "upload iw2"))) return rc;
   }
+  std::vector<char> img(size_t(p->stab_bytes), 0);
+  if (!p->batch) {
+    const int64_t offs[2] = {0, 0};
+    if ((rc = fill_stab(p, 1, h.box, h.p.data(), offs, img.data()))) return rc;
+  } else {
+    if ((rc = fill_stab(p, 0, nullptr, nullptr, nullptr, img.data()))) return rc;
+  }
+  if ((rc = upload(p, p->stab, img, "upload structure tables"))) return rc;
   return cuda_check(p, cudaMemset(p->err, 0, 4), "clear err");
 }
 
@@ -337,8 +455,12 @@ LaunchCtx make_ctx(pswf_plan p) {
   LaunchCtx c;
   c.geo = p->geo;
   c.nmax = p->n_max;
-  c.n = p->n;
+  // batch plans: outputs hold n_max rows and every launch is made whatever
+  // the count (so that a captured sequence serves any batch)
+  c.n = p->batch ? p->n_max : p->n;
   c.ntiles = p->ntiles;
+  c.sbox = p->sbox;
+  c.soff = p->soff;
   c.tile_start = p->tile_start;
   c.st = p->st;
   c.scell = p->scell;
@@ -359,19 +481,15 @@ template <typename R>
 int multiply(pswf_plan p, int want_energy, void* data) {
   const Plan& h = p->host;
   MultParams mp;
-  for (int d = 0; d < 3; ++d) {
-    mp.kfac[d] = 2.0 * M_PI / h.box[d];
-    mp.M[d] = h.M[d];
-  }
+  for (int d = 0; d < 3; ++d) mp.M[d] = h.M[d];
   mp.inv_kc = 1.0 / h.k_c;
   mp.Mxh = h.M[0] / 2 + 1;
   mp.deg = h.deg_m;
   mp.K = h.K;
-  dim3 grid(kEnergyBlocks, h.K);
-  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale,
-                                                  static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2[0]),
-                                                  static_cast<const R*>(p->iw2[1]), static_cast<const R*>(p->iw2[2]),
-                                                  p->epart, want_energy);
+  dim3 grid(p->eblk, p->B * h.K);
+  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->sbox,
+                                                  static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
+                                                  p->Mh, p->epart, want_energy);
   return launch_check(p, "k_multiply");
 }
 
@@ -390,6 +508,22 @@ int fft_exec(pswf_plan p, void* data, bool forward) {
   return PSWF_OK;
 }
 
+// Q_net and Q_self per (structure, channel) of values [K][n] in caller order.
+template <typename R>
+int charge_sums(pswf_plan p, const void* vals, double* out) {
+  const int K = p->host.K;
+  k_charge_partials_seg<R><<<dim3(p->nqb, p->B), kThreads, 0, p->stream>>>(static_cast<const R*>(vals), K, p->B,
+                                                                          p->soff, p->qpart);
+  int rc = launch_check(p, "k_charge_partials_seg");
+  if (rc) return rc;
+  k_charge_final_seg<<<(p->B * K + 63) / 64, 64, 0, p->stream>>>(p->nqb, K, p->B, p->qpart, out);
+  return launch_check(p, "k_charge_final_seg");
+}
+
+// Counts (batch plans: the atom offsets arrive with the structure tables;
+// single plans: written here), bins, scans, scatters, and sums the charges.
+// Launch shapes depend only on the plan's capacity; kernels read the atom
+// count from soff.
 template <typename R>
 int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const void* q) {
   cudaStream_t s = p->stream;
@@ -397,18 +531,22 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   p->n = n;
   p->psi_valid = false;
   StageScope scope(p, PSWF_STAGE_SET_POINTS);
-  p->launches[PSWF_STAGE_SET_POINTS] += (n > 0 ? 7 : 5);
-  if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
-  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 148 * 32)));
-  if (n > 0) {
-    if (pos_dtype == 0)
-      k_bin<float><<<blocks, kThreads, 0, s>>>(n, static_cast<const float*>(pos), p->geo, p->tile_of, p->rank,
-                                              p->tile_count, p->err);
-    else
-      k_bin<double><<<blocks, kThreads, 0, s>>>(n, static_cast<const double*>(pos), p->geo, p->tile_of, p->rank,
-                                               p->tile_count, p->err);
-    if ((rc = launch_check(p, "k_bin"))) return rc;
+  p->launches[PSWF_STAGE_SET_POINTS] += p->batch ? 7 : 8;
+  if (!p->batch) {
+    k_set_count<<<1, 32, 0, s>>>(p->soff, int(n));
+    if ((rc = launch_check(p, "k_set_count"))) return rc;
   }
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((p->n_max + kThreads - 1) / kThreads, 148 * 32)));
+  if (pos_dtype == 0)
+    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), p->geo, p->sbox, p->soff, p->tile_of,
+                                                p->rank, p->tile_count, static_cast<R*>(p->tmp_t), p->tmp_cell,
+                                                p->n_max, p->err);
+  else
+    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), p->geo, p->sbox, p->soff,
+                                                 p->tile_of, p->rank, p->tile_count, static_cast<R*>(p->tmp_t),
+                                                 p->tmp_cell, p->n_max, p->err);
+  if ((rc = launch_check(p, "k_bin"))) return rc;
   k_scan_block_sums<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block);
   if ((rc = launch_check(p, "k_scan_block_sums"))) return rc;
   k_scan_sums<<<1, 32, 0, s>>>(p->scan_blocks, p->scan_sums);
@@ -416,23 +554,11 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   k_scan_apply<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block,
                                                       p->tile_start);
   if ((rc = launch_check(p, "k_scan_apply"))) return rc;
-  if (n > 0) {
-    if (pos_dtype == 0)
-      k_scatter<float, R><<<blocks, kThreads, 0, s>>>(n, p->n_max, static_cast<const float*>(pos),
-                                                      static_cast<const R*>(q), p->geo, p->tile_of, p->rank,
-                                                      p->tile_start, static_cast<R*>(p->st), p->scell,
-                                                      static_cast<R*>(p->sq), p->sperm);
-    else
-      k_scatter<double, R><<<blocks, kThreads, 0, s>>>(n, p->n_max, static_cast<const double*>(pos),
-                                                       static_cast<const R*>(q), p->geo, p->tile_of, p->rank,
-                                                       p->tile_start, static_cast<R*>(p->st), p->scell,
-                                                       static_cast<R*>(p->sq), p->sperm);
-    if ((rc = launch_check(p, "k_scatter"))) return rc;
-  }
-  k_charge_partials<R><<<kQBlocks, kThreads, 0, s>>>(n, static_cast<const R*>(q), p->host.K, p->qpart);
-  if ((rc = launch_check(p, "k_charge_partials"))) return rc;
-  k_charge_final<<<1, 64, 0, s>>>(kQBlocks, p->host.K, p->qpart, p->charges);
-  return launch_check(p, "k_charge_final");
+  k_scatter<R><<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const R*>(q), p->geo, p->soff, p->tile_of, p->rank,
+                                           p->tile_start, static_cast<const R*>(p->tmp_t), p->tmp_cell,
+                                           static_cast<R*>(p->st), p->scell, static_cast<R*>(p->sq), p->sperm);
+  if ((rc = launch_check(p, "k_scatter"))) return rc;
+  return charge_sums<R>(p, q, p->charges);
 }
 
 template <typename R>
@@ -443,7 +569,7 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   {
     StageScope scope(p, PSWF_STAGE_SPREAD);
     if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid"))) return rc;
-    if (p->n > 0) {
+    if (p->n > 0 || p->batch) {
       int nl = 0;
       cudaError_t e = sizeof(R) == 4 ? launch_spread_float(ctx, &nl) : launch_spread_double(ctx, &nl);
       p->launches[PSWF_STAGE_SPREAD] += nl;
@@ -457,13 +583,13 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   {
     StageScope scope(p, PSWF_STAGE_MULTIPLY);
     if ((rc = multiply<R>(p, 1, p->grid))) return rc;
-    k_energy_final<<<1, 256, 0, s>>>(p->host.K, kEnergyBlocks, p->epart, p->zero_coef, p->charges,
-                                     energy ? energy : p->energy_tmp);
+    k_energy_final<<<p->B, 256, 0, s>>>(p->host.K, p->eblk, p->epart, p->zero_coef, p->charges,
+                                        energy ? energy : p->energy_tmp);
     if ((rc = launch_check(p, "k_energy_final"))) return rc;
     p->launches[PSWF_STAGE_MULTIPLY] += 2;
   }
   const bool keep_psi = (p->flags & PSWF_FLAG_BACKWARD) != 0;
-  if (p->n == 0) {
+  if (p->n == 0 && !p->batch) {
     p->psi_valid = keep_psi;   // nothing to gather; a backward has nothing to do
     return PSWF_OK;
   }
@@ -501,12 +627,10 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
   int nl = 0;
   cudaError_t e;
   if (g_phi) {
-    k_charge_partials<R><<<kQBlocks, kThreads, 0, s>>>(p->n, static_cast<const R*>(g_phi), K, p->qpart);
-    if ((rc = launch_check(p, "k_charge_partials (backward)"))) return rc;
-    k_charge_final<<<1, 64, 0, s>>>(kQBlocks, K, p->qpart, p->bsum);
-    if ((rc = launch_check(p, "k_charge_final (backward)"))) return rc;
+    if ((rc = charge_sums<R>(p, g_phi, p->bsum))) return rc;
     nl += 2;
-  } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(K) * 2 * sizeof(double), s), "clear bsum"))) {
+  } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(p->B) * K * 2 * sizeof(double), s),
+                              "clear bsum"))) {
     return rc;
   }
   if ((rc = cuda_check(p, cudaMemsetAsync(p->grid2, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid2")))
@@ -522,6 +646,24 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
   e = sizeof(R) == 4 ? launch_backward_float(ctx, b, 1, &nl) : launch_backward_double(ctx, b, 1, &nl);
   p->launches[PSWF_STAGE_BACKWARD] += nl;
   return cuda_check(p, e, "backward gather");
+}
+
+// Per-batch structure tables: filled on the host into the plan's pinned
+// mirror (after the previous upload from it has completed) and copied to the
+// device on the plan's stream.
+int batch_tables_async(pswf_plan p, int b, const double* boxes, const int* ps, const int64_t* offsets) {
+  int rc;
+  if (!p->h_stab) {
+    if ((rc = cuda_check(p, cudaMallocHost(&p->h_stab, size_t(p->stab_bytes)), "pinned table mirror"))) return rc;
+    if ((rc = cuda_check(p, cudaEventCreateWithFlags(&p->stab_ev, cudaEventDisableTiming), "table event"))) return rc;
+  } else if ((rc = cuda_check(p, cudaEventSynchronize(p->stab_ev), "wait for the previous table upload"))) {
+    return rc;
+  }
+  if ((rc = fill_stab(p, b, boxes, ps, offsets, static_cast<char*>(p->h_stab)))) return rc;
+  if ((rc = cuda_check(p, cudaMemcpyAsync(p->stab, p->h_stab, size_t(p->stab_bytes), cudaMemcpyHostToDevice,
+                                          p->stream), "upload structure tables")))
+    return rc;
+  return cuda_check(p, cudaEventRecord(p->stab_ev, p->stream), "record table upload");
 }
 
 int make_fft(pswf_plan p) {
@@ -543,8 +685,9 @@ int make_fft(pswf_plan p) {
   cufftSetAutoAllocation(p->fwd, 0);
   cufftSetAutoAllocation(p->inv, 0);
   size_t w1 = 0, w2 = 0;
-  const cufftResult r1 = cufftMakePlanMany(p->fwd, 3, n, embed_r, 1, dist_r, embed_c, 1, dist_c, tf, h.K, &w1);
-  const cufftResult r2 = cufftMakePlanMany(p->inv, 3, n, embed_c, 1, dist_c, embed_r, 1, dist_r, ti, h.K, &w2);
+  const int nb = p->B * h.K;
+  const cufftResult r1 = cufftMakePlanMany(p->fwd, 3, n, embed_r, 1, dist_r, embed_c, 1, dist_c, tf, nb, &w1);
+  const cufftResult r2 = cufftMakePlanMany(p->inv, 3, n, embed_c, 1, dist_c, embed_r, 1, dist_r, ti, nb, &w2);
   if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
     return set_err(p, PSWF_ECUFFT,
                    "cufftMakePlanMany failed (" + std::to_string(int(r1)) + "," + std::to_string(int(r2)) + ")");
@@ -588,6 +731,8 @@ void fill_info(const Plan& h, int flags, pswf_info* out) {
   out->deg_window = h.deg_w;
   out->deg_mult = h.deg_m;
   out->flags = flags;
+  out->B = 1;
+  out->batch = 0;
 }
 
 }  // namespace
@@ -636,6 +781,7 @@ extern "C" {
 
 int pswf_self_energy_noalloc(pswf_plan pl, int64_t n, const void* q, double* out, void* stream) {
   if (!pl || !out || (n > 0 && !q)) return PSWF_EINVAL;
+  if (pl->batch) return set_err(pl, PSWF_EINVAL, "pswf_self_energy_noalloc takes a single-structure plan");
   const int K = pl->host.K;
   if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "pswf_self_energy_noalloc: n outside 0..n_max");
   if (K > kMaxK) return set_err(pl, PSWF_EINVAL, "pswf_self_energy_noalloc: more than 64 channels do not fit the scratch");
@@ -673,6 +819,46 @@ int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* 
   return PSWF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Device-side shape of a plan whose host tables are made: geometry, tiles,
+// scan, grid size, cuFFT plans and the workspace size.
+int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, void* stream) {
+  cudaGetDevice(&pl->device);
+  pl->stream = static_cast<cudaStream_t>(stream);
+  pl->n_max = n_max;
+  pl->flags = opts->flags;
+  pl->real_size = opts->precision == 1 ? 8 : 4;
+  pl->B = b;
+  const Plan& h = pl->host;
+  pl->Mh = 0;
+  for (int d = 0; d < 3; ++d) {
+    pl->geo.M[d] = h.M[d];
+    pl->geo.ntile[d] = (h.M[d] + kTile - 1) / kTile;
+    pl->Mh = std::max(pl->Mh, h.M[d] / 2 + 1);
+  }
+  pl->geo.Mxp = 2 * (h.M[0] / 2 + 1);
+  pl->geo.P = h.P;
+  pl->geo.K = h.K;
+  pl->geo.nts = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
+  pl->geo.B = b;
+  pl->nts = pl->geo.nts;
+  pl->ntiles = b * pl->nts;
+  pl->nqb = b > 1 ? kQBlocksBatch : kQBlocks;
+  pl->eblk = int(std::max<int64_t>(1, std::min<int64_t>(kEnergyBlocks, int64_t(h.M[1]) * h.M[2] / 8)));
+  pl->scan_per_block = 16384;
+  pl->scan_blocks = (pl->ntiles + pl->scan_per_block - 1) / pl->scan_per_block;
+  pl->grid_elems = int64_t(b) * h.K * h.M[2] * h.M[1] * pl->geo.Mxp;
+  int rc = make_fft(pl);
+  if (rc) return rc;
+  pl->ws_bytes = layout(pl, nullptr);
+  return PSWF_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p, const pswf_opts* opts, void* stream,
                      pswf_plan* out) {
   if (!out) return PSWF_EINVAL;
@@ -685,31 +871,58 @@ int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p, co
     delete pl;
     return rc;
   }
-  cudaGetDevice(&pl->device);
-  pl->stream = static_cast<cudaStream_t>(stream);
-  pl->n_max = n_max;
-  pl->flags = opts->flags;
-  pl->real_size = opts->precision == 1 ? 8 : 4;
-  const Plan& h = pl->host;
-  for (int d = 0; d < 3; ++d) {
-    pl->geo.L[d] = h.box[d];
-    pl->geo.M[d] = h.M[d];
-    pl->geo.ntile[d] = (h.M[d] + kTile - 1) / kTile;
-  }
-  pl->geo.Mxp = 2 * (h.M[0] / 2 + 1);
-  pl->geo.P = h.P;
-  pl->geo.K = h.K;
-  pl->ntiles = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
-  pl->scan_per_block = 16384;
-  pl->scan_blocks = (pl->ntiles + pl->scan_per_block - 1) / pl->scan_per_block;
-  pl->grid_elems = int64_t(h.K) * h.M[2] * h.M[1] * pl->geo.Mxp;
-  if ((rc = make_fft(pl))) {
+  if ((rc = finish_create(pl, n_max, 1, opts, stream))) {
     pswf_plan_destroy(pl);
     return rc;
   }
-  pl->ws_bytes = layout(pl, nullptr);
   *out = pl;
   return PSWF_OK;
+}
+
+int pswf_batch_plan_create(const double box_max[3], int b_max, int64_t n_max, int K, const int* pset, int npset,
+                           const pswf_opts* opts, void* stream, pswf_plan* out) {
+  if (!out) return PSWF_EINVAL;
+  *out = nullptr;
+  if (!box_max || !pset || !opts || b_max < 1 || b_max > (1 << 16) || n_max < 0 ||
+      n_max > (int64_t(1) << 31) - 1)
+    return PSWF_EINVAL;
+  pswf_plan pl = new (std::nothrow) pswf_plan_s();
+  if (!pl) return PSWF_ENOMEM;
+  int rc = make_batch_plan(box_max, K, pset, npset, to_options(opts), pl->host);
+  if (rc) {
+    delete pl;
+    return rc;
+  }
+  pl->batch = true;
+  if ((rc = finish_create(pl, n_max, b_max, opts, stream))) {
+    pswf_plan_destroy(pl);
+    return rc;
+  }
+  *out = pl;
+  return PSWF_OK;
+}
+
+int pswf_batch_set_points(pswf_plan pl, int b, const double* boxes, const int* ps, const int64_t* offsets,
+                          const void* pos, int pos_dtype, const void* q) {
+  if (!pl) return PSWF_EINVAL;
+  if (!pl->batch) return set_err(pl, PSWF_EINVAL, "pswf_batch_set_points needs a batch plan");
+  if (b < 0 || b > pl->B) return set_err(pl, PSWF_EINVAL, "number of structures outside 0..b_max");
+  if (b > 0 && (!boxes || !ps || !offsets)) return set_err(pl, PSWF_EINVAL, "boxes, ps and offsets are required");
+  if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
+  int64_t n = 0;
+  if (b > 0) {
+    if (offsets[0] != 0) return set_err(pl, PSWF_EINVAL, "offsets[0] must be 0");
+    for (int i = 0; i < b; ++i)
+      if (offsets[i + 1] < offsets[i]) return set_err(pl, PSWF_EINVAL, "offsets must be non-decreasing");
+    n = offsets[b];
+  }
+  if (n > pl->n_max) return set_err(pl, PSWF_EINVAL, "total atoms exceed n_max");
+  if (n > 0 && (!pos || !q)) return set_err(pl, PSWF_EINVAL, "pos and q are required");
+  int rc = ensure_workspace(pl);
+  if (rc) return rc;
+  if ((rc = batch_tables_async(pl, b, boxes, ps, offsets))) return rc;
+  return pl->real_size == 4 ? do_set_points<float>(pl, n, pos, pos_dtype, q)
+                            : do_set_points<double>(pl, n, pos, pos_dtype, q);
 }
 
 int pswf_plan_info(pswf_plan pl, pswf_info* out) {
@@ -717,6 +930,8 @@ int pswf_plan_info(pswf_plan pl, pswf_info* out) {
   fill_info(pl->host, pl->flags, out);
   out->n_max = pl->n_max;
   out->workspace_bytes = pl->ws_bytes;
+  out->B = pl->B;
+  out->batch = pl->batch ? 1 : 0;
   return PSWF_OK;
 }
 
@@ -744,6 +959,7 @@ int pswf_plan_set_stream(pswf_plan pl, void* stream) {
 
 int pswf_set_points(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, const void* q) {
   if (!pl) return PSWF_EINVAL;
+  if (pl->batch) return set_err(pl, PSWF_EINVAL, "batch plans take pswf_batch_set_points");
   if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
   if (n > 0 && (!pos || !q)) return set_err(pl, PSWF_EINVAL, "pos and q are required");
   if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
@@ -772,13 +988,13 @@ int pswf_backward(pswf_plan pl, const double* g_energy, const void* g_phi, const
 int pswf_self_energy(pswf_plan pl, double* out) {
   if (!pl || !out) return PSWF_EINVAL;
   if (pl->n < 0) return set_err(pl, PSWF_ESTATE, "pswf_self_energy before pswf_set_points");
-  const int K = pl->host.K;
-  std::vector<double> ch(2 * K);
-  int rc = cuda_check(pl, cudaMemcpyAsync(ch.data(), pl->charges, 2 * K * sizeof(double), cudaMemcpyDeviceToHost,
+  const int BK = pl->B * pl->host.K;
+  std::vector<double> ch(2 * size_t(BK));
+  int rc = cuda_check(pl, cudaMemcpyAsync(ch.data(), pl->charges, 2 * BK * sizeof(double), cudaMemcpyDeviceToHost,
                                           pl->stream), "read charges");
   if (rc) return rc;
   if ((rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "sync"))) return rc;
-  for (int k = 0; k < K; ++k) out[k] = pl->host.self_coef[k] * ch[2 * k + 1];
+  for (int g = 0; g < BK; ++g) out[g] = pl->host.self_coef_p[pl->h_pch[g]] * ch[2 * g + 1];
   return PSWF_OK;
 }
 
@@ -799,6 +1015,7 @@ int pswf_sync(pswf_plan pl) {
 int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* q, double* energy, double* phi,
                       double* forces) {
   if (!pl || !energy || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
+  if (pl->batch) return set_err(pl, PSWF_EINVAL, "pswf_compute_host takes a single-structure plan");
   if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
   const int K = pl->host.K;
   const int64_t rs = int64_t(pl->real_size);
@@ -879,6 +1096,8 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (pl->ws_owned && pl->ws) cudaFree(pl->ws);
   if (pl->d_stage) cudaFree(pl->d_stage);
   if (pl->h_pin) cudaFreeHost(pl->h_pin);
+  if (pl->h_stab) cudaFreeHost(pl->h_stab);
+  if (pl->stab_ev) cudaEventDestroy(pl->stab_ev);
   for (auto& r : pl->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -12,6 +12,7 @@
 //   dL/dr_i   = sum_c [ -(gE_c q_i^c + gphi_i^c) f_i^c
 //                       - q_i^c sum_g Psibar^c_g D_i(g)
 //                       - q_i^c (sum_g Psi^c_g H_i(g)) gF_i ].
+// (Per structure s of a batch plan, with E_c, Q_c, a_c of channel g = s K + c.)
 // Kernels here are one thread per sorted atom, reading and writing the grids
 // directly (global atomics for the spread).
 #pragma once
@@ -42,12 +43,16 @@ __device__ inline void window_weights2(R t, const WinCoef<R>& wc, R (&w)[P], R (
 
 // rhobar^c(g) = sum_i gphi_i^c W_i(g) + q_i^c gF_i . D_i(g)  (grid2 zeroed before).
 template <typename R, int P>
-__global__ void k_spread_bw(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
+__global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__ sbox, const int* __restrict__ soff,
+                            const int* __restrict__ tile_start, const R* __restrict__ st,
                             const uint64_t* __restrict__ scell, const R* __restrict__ sq,
                             const int* __restrict__ sperm, WinCoef<R> wc, const R* __restrict__ gphi,
                             const R* __restrict__ gF, R* __restrict__ grid2) {
-  const R two_h[3] = {R(2.0 * g.M[0] / g.L[0]), R(2.0 * g.M[1] / g.L[1]), R(2.0 * g.M[2] / g.L[2])};
+  const int64_t n = soff[g.B];
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+    const int sidx = find_struct(tile_start, g.nts, g.B, a);
+    const double* box = sbox + 3 * sidx;
+    const R two_h[3] = {R(2.0 * g.M[0] / box[0]), R(2.0 * g.M[1] / box[1]), R(2.0 * g.M[2] / box[2])};
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P];
     window_weights<R, P>(st[a], wc, wx, dx);
     window_weights<R, P>(st[nmax + a], wc, wy, dy);
@@ -67,7 +72,7 @@ __global__ void k_spread_bw(int64_t n, int64_t nmax, Geometry g, const R* __rest
       const R qc = sq[int64_t(c) * nmax + a];
       const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
       const R v0 = qc * g0, v1 = qc * g1, v2 = qc * g2;
-      R* gc = grid2 + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
+      R* gc = grid2 + (int64_t(sidx) * g.K + c) * g.M[2] * g.M[1] * g.Mxp;
       for (int k = 0; k < P; ++k) {
         const int z = wrap_index(cz + k, g.M[2]);
         for (int j = 0; j < P; ++j) {
@@ -88,15 +93,19 @@ __global__ void k_spread_bw(int64_t n, int64_t nmax, Geometry g, const R* __rest
 // Hessian contraction from Psi (grid), W and D contractions from Psibar
 // (grid2); writes dL/dq and dL/dr in the original atom order.
 template <typename R, int P>
-__global__ void k_interp_bw(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
+__global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__ sbox, const int* __restrict__ soff,
+                            const int* __restrict__ tile_start, const R* __restrict__ st,
                             const uint64_t* __restrict__ scell, const R* __restrict__ sq,
                             const int* __restrict__ sperm, WinCoef<R> wc, const R* __restrict__ grid,
                             const R* __restrict__ grid2, const double* __restrict__ zero_coef,
                             const double* __restrict__ charges, const double* __restrict__ gsum,
                             const double* __restrict__ gE, const R* __restrict__ gphi, const R* __restrict__ gF,
                             R* __restrict__ grad_q, R* __restrict__ grad_r) {
-  const R th[3] = {R(2.0 * g.M[0] / g.L[0]), R(2.0 * g.M[1] / g.L[1]), R(2.0 * g.M[2] / g.L[2])};
+  const int64_t n = soff[g.B];
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+    const int sidx = find_struct(tile_start, g.nts, g.B, a);
+    const double* box = sbox + 3 * sidx;
+    const R th[3] = {R(2.0 * g.M[0] / box[0]), R(2.0 * g.M[1] / box[1]), R(2.0 * g.M[2] / box[2])};
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P], hx[P], hy[P], hz[P];
     window_weights2<R, P>(st[a], wc, wx, dx, hx);
     window_weights2<R, P>(st[nmax + a], wc, wy, dy, hy);
@@ -117,8 +126,9 @@ __global__ void k_interp_bw(int64_t n, int64_t nmax, Geometry g, const R* __rest
             g2 = gF ? gF[3 * int64_t(o) + 2] : R(0);
     R gr0 = 0, gr1 = 0, gr2 = 0;
     for (int c = 0; c < g.K; ++c) {
-      const R* pc = grid + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
-      const R* bc = grid2 + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
+      const int gi = sidx * g.K + c;
+      const R* pc = grid + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
+      const R* bc = grid2 + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
       R ph = 0, f0 = 0, f1 = 0, f2 = 0, sb = 0, b0 = 0, b1 = 0, b2 = 0;
       R h00 = 0, h11 = 0, h22 = 0, h01 = 0, h02 = 0, h12 = 0;
       for (int k = 0; k < P; ++k) {
@@ -156,11 +166,11 @@ __global__ void k_interp_bw(int64_t n, int64_t nmax, Geometry g, const R* __rest
         }
       }
       const R qc = sq[int64_t(c) * nmax + a];
-      const R ge = gE ? R(gE[c]) : R(0);
+      const R ge = gE ? R(gE[gi]) : R(0);
       const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
-      const R phi_c = ph + R(2.0 * zero_coef[c] * charges[2 * c]);
+      const R phi_c = ph + R(2.0 * zero_coef[gi] * charges[2 * gi]);
       if (grad_q)
-        grad_q[int64_t(c) * n + o] = ge * phi_c + R(2.0 * zero_coef[c] * gsum[2 * c]) + g0 * f0 + g1 * f1 + g2 * f2 + sb;
+        grad_q[int64_t(c) * n + o] = ge * phi_c + R(2.0 * zero_coef[gi] * gsum[2 * gi]) + g0 * f0 + g1 * f1 + g2 * f2 + sb;
       const R w = ge * qc + gp;
       gr0 -= w * f0 + qc * b0 + qc * (h00 * g0 + h01 * g1 + h02 * g2);
       gr1 -= w * f1 + qc * b1 + qc * (h01 * g0 + h11 * g1 + h12 * g2);

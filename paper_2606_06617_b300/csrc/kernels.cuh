@@ -1,14 +1,18 @@
 // Device kernels of the PSWF-LR hot path (sm_103a).
 //
+// A plan holds B structures (B = 1 for a single system) that share one grid
+// size M and K channels; structure s has its own box (sbox[s][3]) and its
+// atoms are soff[s] .. soff[s+1] - 1 of the caller's arrays.
 // Data layout in HBM (one plan):
-//   grid   real [K][M_z][M_y][M_xp], M_xp = 2 (M_x / 2 + 1): the spread
+//   grid   real [B][K][M_z][M_y][M_xp], M_xp = 2 (M_x / 2 + 1): the spread
 //          density, overwritten in place by the R2C transform, the multiplier
 //          and the C2R transform (the grid potential Psi);
-//   sorted atoms (tile order): st[3][n] real window offsets t_d in [0, 1),
-//          scell[n] packed stencil-start cell, sq[K][n] real charges,
-//          sperm[n] original index;
-//   tile_start[n_tiles + 1] int32 offsets of each tile's atoms.
-// Tiles are kTile^3 blocks of stencil-start cells.
+//   sorted atoms (structure, then tile order): st[3][n] real window offsets
+//          t_d in [0, 1), scell[n] packed stencil-start cell, sq[K][n] real
+//          charges, sperm[n] original index;
+//   tile_start[B * nts + 1] int32 offsets of each tile's atoms.
+// Tiles are kTile^3 blocks of stencil-start cells, nts per structure.
+// Per-(structure, channel) values are indexed g = s * K + c.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,15 +23,15 @@
 namespace pswf {
 
 constexpr int kTile = 16;     // tile edge in stencil-start cells
-constexpr int kBatch = 256;   // atoms whose window weights are staged in shared memory at once
 
 struct Geometry {
-  double L[3];       // box edges
   int M[3];          // grid points per dimension
   int Mxp;           // padded row length (real elements)
   int P;             // stencil width
-  int ntile[3];      // tiles per dimension
+  int ntile[3];      // tiles per dimension (of one structure)
+  int nts;           // tiles per structure
   int K;             // channels
+  int B;             // structures
 };
 
 template <typename R>
@@ -37,7 +41,6 @@ struct WinCoef {
 };
 
 struct MultParams {
-  double kfac[3];     // 2 pi / L_d
   double inv_kc;      // 1 / k_c
   int M[3];
   int Mxh;            // M_x / 2 + 1
@@ -59,25 +62,45 @@ __host__ __device__ inline void unpack_cell(uint64_t c, int& x, int& y, int& z) 
   z = int((c >> 42) & 0x1FFFFF);
 }
 
-// Stencil start (reading C5): u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2 - u
-// in [0, 1), in FP64 once per atom; i0 wrapped into [0, M).  Rounding can put
-// t at 1.0; then the equivalent (i0 - 1, t - 1) is used.
-__device__ inline void locate(double x, double L, int M, int P, int& i0w, double& t) {
-  x = x - L * floor(x / L);
-  if (!(x < L) || x < 0.0) x = 0.0;
-  const double u = x * (double(M) / L);
-  const double half = 0.5 * P;
-  const double fi0 = ceil(u - half);
-  int i0 = int(fi0);
-  t = fi0 + half - u;
-  if (t >= 1.0) {
-    t -= 1.0;
-    i0 -= 1;
+// Stencil start (reading C5): u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2
+// - u in [0, 1); i0 wrapped into [0, M).  With u = fl + f (fl = floor(u),
+// f in [0, 1)): for even P, i0 = fl - P/2 + [f > 0] and t = [f > 0] - f; for
+// odd P = 2k + 1, i0 = fl - k + [f > 1/2] and t = [f > 1/2] + 1/2 - f.  The
+// FP64 work is one multiply, one floor and one subtraction per direction (the
+// FP64 pipe is narrow on this GPU); the rest is integer.
+__device__ inline void locate(double x, double m_over_l, int M, int P, int& i0w, double& t) {
+  const double u = x * m_over_l;
+  const double fl = floor(u);
+  const double f = u - fl;
+  int64_t i0;
+  if ((P & 1) == 0) {
+    const int c = f > 0.0 ? 1 : 0;
+    i0 = int64_t(fl) - P / 2 + c;
+    t = double(c) - f;
+  } else {
+    const int c = f > 0.5 ? 1 : 0;
+    i0 = int64_t(fl) - P / 2 + c;
+    t = double(c) + 0.5 - f;
   }
   if (t < 0.0) t = 0.0;
-  i0 %= M;
-  if (i0 < 0) i0 += M;
-  i0w = i0;
+  if (t >= 1.0) t = 0.0;   // f rounded to 1: u sits on a grid point
+  int64_t r = i0 % M;
+  if (r < 0) r += M;
+  i0w = int(r);
+}
+
+// Structure of an atom: the s with off[s] <= i < off[s + 1] (off has B + 1
+// non-decreasing entries read with the given stride).
+__device__ inline int find_struct(const int* __restrict__ off, int stride, int B, int64_t i) {
+  int lo = 0, hi = B;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (int64_t(off[int64_t(mid) * stride]) <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
 }
 
 // Window weights W_j(t) and dW_j/ds (s = 2t - 1) for the P pieces (Horner).
@@ -112,48 +135,92 @@ __device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
 }
 
 // ---- binning -----------------------------------------------------------------
-template <typename PosT>
-__global__ void k_bin(int64_t n, const PosT* __restrict__ pos, Geometry g, int* __restrict__ tile_of,
-                      int* __restrict__ rank, int* __restrict__ tile_count, int* __restrict__ err) {
+// k_bin: locate each atom (original order), count it into its tile and keep
+// its rank there, its offsets t and its packed start cell for k_scatter.
+template <typename PosT, typename R>
+__global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __restrict__ sbox,
+                      const int* __restrict__ soff, int* __restrict__ tile_of, int* __restrict__ rank,
+                      int* __restrict__ tile_count, R* __restrict__ tmp_t, uint64_t* __restrict__ tmp_cell,
+                      int64_t nmax, int* __restrict__ err) {
+  const int64_t n = soff[g.B];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    int tc[3];
+    const int s = find_struct(soff, 1, g.B, i);
+    int i0[3];
     for (int d = 0; d < 3; ++d) {
       double x = double(pos[3 * i + d]);
       if (!isfinite(x)) {
         atomicCAS(err, 0, -6);
         x = 0.0;
       }
-      int i0;
       double t;
-      locate(x, g.L[d], g.M[d], g.P, i0, t);
-      tc[d] = i0 / kTile;
+      locate(x, double(g.M[d]) / sbox[3 * s + d], g.M[d], g.P, i0[d], t);
+      tmp_t[d * nmax + i] = R(t);
     }
-    const int tile = (tc[2] * g.ntile[1] + tc[1]) * g.ntile[0] + tc[0];
+    const int tile = s * g.nts + ((i0[2] / kTile) * g.ntile[1] + i0[1] / kTile) * g.ntile[0] + i0[0] / kTile;
     tile_of[i] = tile;
+    tmp_cell[i] = pack_cell(i0[0], i0[1], i0[2]);
     rank[i] = atomicAdd(tile_count + tile, 1);
   }
 }
 
-template <typename PosT, typename R>
-__global__ void k_scatter(int64_t n, int64_t nmax, const PosT* __restrict__ pos, const R* __restrict__ q, Geometry g,
+template <typename R>
+__global__ void k_scatter(int64_t nmax, const R* __restrict__ q, Geometry g, const int* __restrict__ soff,
                           const int* __restrict__ tile_of, const int* __restrict__ rank,
-                          const int* __restrict__ tile_start, R* __restrict__ st, uint64_t* __restrict__ scell,
+                          const int* __restrict__ tile_start, const R* __restrict__ tmp_t,
+                          const uint64_t* __restrict__ tmp_cell, R* __restrict__ st, uint64_t* __restrict__ scell,
                           R* __restrict__ sq, int* __restrict__ sperm) {
+  const int64_t n = soff[g.B];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    int i0[3];
-    double t[3];
-    for (int d = 0; d < 3; ++d) {
-      double x = double(pos[3 * i + d]);
-      if (!isfinite(x)) x = 0.0;
-      locate(x, g.L[d], g.M[d], g.P, i0[d], t[d]);
-    }
     const int64_t dst = int64_t(tile_start[tile_of[i]]) + rank[i];
-    st[dst] = R(t[0]);
-    st[nmax + dst] = R(t[1]);
-    st[2 * nmax + dst] = R(t[2]);
-    scell[dst] = pack_cell(i0[0], i0[1], i0[2]);
+    st[dst] = tmp_t[i];
+    st[nmax + dst] = tmp_t[nmax + i];
+    st[2 * nmax + dst] = tmp_t[2 * nmax + i];
+    scell[dst] = tmp_cell[i];
     for (int c = 0; c < g.K; ++c) sq[c * nmax + dst] = q[c * n + i];
     sperm[dst] = int(i);
+  }
+}
+
+// The single-structure set_points writes its atom count here (soff = {0, n}).
+__global__ void k_set_count(int* __restrict__ soff, int n);
+
+// Per-(structure, block) FP64 partial sums of q and q^2 per channel over the
+// structure's atoms (caller order, q [K][n]): blockIdx.y = structure,
+// part[((s * gridDim.x + blk) * K + c) * 2 + {0, 1}].
+template <typename R>
+__global__ void k_charge_partials_seg(const R* __restrict__ q, int K, int B, const int* __restrict__ soff,
+                                      double* __restrict__ part) {
+  __shared__ double sh[2][32];
+  const int s = blockIdx.y;
+  const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
+  for (int c = 0; c < K; ++c) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a1; i += int64_t(gridDim.x) * blockDim.x) {
+      const double v = double(q[c * n + i]);
+      s1 += v;
+      s2 += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      sh[0][wid] = s1;
+      sh[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double x = 0.0, y = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+        x += sh[0][w];
+        y += sh[1][w];
+      }
+      const size_t o = ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2;
+      part[o] = x;
+      part[o + 1] = y;
+    }
+    __syncthreads();
   }
 }
 
@@ -200,31 +267,43 @@ __global__ void k_scan_block_sums(int n, const int* __restrict__ in, int* __rest
 __global__ void k_scan_sums(int nb, int* __restrict__ sums);
 __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __restrict__ sums, int per_block,
                              int* __restrict__ out);
+// k_charge_final_seg: charges[g][0] = Q_net, charges[g][1] = Q_self from the
+// k_charge_partials_seg partials, one thread per (structure, channel).
+__global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
+                                   double* __restrict__ charges);
+// One block per structure: energy[s][c] = sum of the multiplier partials of
+// channel g = s K + c plus zero_coef[g] Q_net^2; energy[s][K] = their total.
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy);
 
 // ---- multiplier and energy (steps (iii)-(iv)) --------------------------------------
-// blockIdx.y = channel.  For each half-spectrum mode m != 0 with u = |k|/k_c < 1:
-//   G = scale_c * sing_p(k) * (S_p(u) + log part) * iw2x * iw2y * iw2z  (times dV^2/V,
-//   folded into scale_c), energy += w_m G |rho-hat|^2 / 2, rho-hat <- G rho-hat;
+// blockIdx.y = g = s K + c.  For each half-spectrum mode m != 0 with
+// u = |k|/k_c < 1 (k from structure s's box):
+//   G = scale_g * sing_p(k) * (S_p(u) + log part) * iw2x * iw2y * iw2z  (times dV^2/V,
+//   folded into scale_g), energy += w_m G |rho-hat|^2 / 2, rho-hat <- G rho-hat;
 // all other modes are set to zero.  Energy partials per block in FP64.
 template <typename R>
 __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, MultParams mp,
                                                   const int* __restrict__ pch, const double* __restrict__ scale,
-                                                  const R* __restrict__ coef, const R* __restrict__ iw2x,
-                                                  const R* __restrict__ iw2y, const R* __restrict__ iw2z,
+                                                  const double* __restrict__ sbox, const R* __restrict__ coef,
+                                                  const R* __restrict__ iw2, int iw2_stride,
                                                   double* __restrict__ part, int want_energy) {
   // One (y, z) row of the half spectrum per block iteration; rows outside the
   // band |k| < k_c are zero-filled without reading them.
-  const int c = blockIdx.y;
-  const int p = pch[c];
-  const R sc = R(scale[c]);
+  const int g = blockIdx.y;
+  const int s = g / mp.K;
+  const int p = pch[g];
+  const R sc = R(scale[g]);
   const int nrow = mp.M[1] * mp.M[2];
-  Cplx<R>* d = data + int64_t(c) * nrow * mp.Mxh;
-  const R* cf = coef + size_t(c) * kMultSeg * (mp.deg + 1);
+  Cplx<R>* d = data + int64_t(g) * nrow * mp.Mxh;
+  const R* cf = coef + size_t(p - 1) * kMultSeg * (mp.deg + 1);
+  const R* iw2x = iw2 + size_t(3 * s) * iw2_stride;
+  const R* iw2y = iw2x + iw2_stride;
+  const R* iw2z = iw2y + iw2_stride;
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
-  const R kf0 = R(mp.kfac[0]), kf1 = R(mp.kfac[1]), kf2 = R(mp.kfac[2]);
+  constexpr double kTwoPi = 6.283185307179586476925;
+  const R kf0 = R(kTwoPi / sbox[3 * s]), kf1 = R(kTwoPi / sbox[3 * s + 1]), kf2 = R(kTwoPi / sbox[3 * s + 2]);
   const bool even_x = (mp.M[0] % 2) == 0;
   double e = 0.0;
   for (int row = blockIdx.x; row < nrow; row += gridDim.x) {
@@ -252,10 +331,10 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
       if (u >= R(1)) u = R(1) - R(1e-7);
       int seg = int(u * R(kMultSeg));
       if (seg > kMultSeg - 1) seg = kMultSeg - 1;
-      const R s = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+      const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
       const R* cs = cf + seg * (mp.deg + 1);
       R S = cs[mp.deg];
-      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * s + cs[nn];
+      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
       R phi;
       switch (p) {
         case 1: phi = S / k2; break;
@@ -283,20 +362,27 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-    part[size_t(c) * gridDim.x + blockIdx.x] = t;
+    part[size_t(g) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// ---- interpolation, direct from global memory (reference kernel) -------------------
-// One thread per sorted atom.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W,
-// with grad_d W = (2 / h_d) dW/ds.  Writes in the original atom order.
+// ---- interpolation, direct from global memory (fallback kernel) ---------------------
+// One thread per sorted atom, for plans whose padded regions do not fit in
+// shared memory.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W, with
+// grad_d W = (2 / h_d) dW/ds.  Writes in the original atom order.
 template <typename R, int P>
-__global__ void k_interp_direct(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
-                         const uint64_t* __restrict__ scell, const R* __restrict__ sq, const int* __restrict__ sperm,
-                         WinCoef<R> wc, const R* __restrict__ grid, const double* __restrict__ zero_coef,
-                         const double* __restrict__ charges, R* __restrict__ phi, R* __restrict__ forces) {
-  const R two_hx = R(2.0 * g.M[0] / g.L[0]), two_hy = R(2.0 * g.M[1] / g.L[1]), two_hz = R(2.0 * g.M[2] / g.L[2]);
+__global__ void k_interp_direct(int64_t nmax, Geometry g, const double* __restrict__ sbox,
+                                const int* __restrict__ soff, const int* __restrict__ tile_start,
+                                const R* __restrict__ st, const uint64_t* __restrict__ scell,
+                                const R* __restrict__ sq, const int* __restrict__ sperm, WinCoef<R> wc,
+                                const R* __restrict__ grid, const double* __restrict__ zero_coef,
+                                const double* __restrict__ charges, R* __restrict__ phi, R* __restrict__ forces) {
+  const int64_t n = soff[g.B];
+  const int64_t chan = int64_t(g.M[2]) * g.M[1] * g.Mxp;
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+    const int sidx = find_struct(tile_start, g.nts, g.B, a);
+    const R two_hx = R(2.0 * g.M[0] / sbox[3 * sidx]), two_hy = R(2.0 * g.M[1] / sbox[3 * sidx + 1]),
+            two_hz = R(2.0 * g.M[2] / sbox[3 * sidx + 2]);
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P];
     window_weights<R, P>(st[a], wc, wx, dx);
     window_weights<R, P>(st[nmax + a], wc, wy, dy);
@@ -313,7 +399,8 @@ __global__ void k_interp_direct(int64_t n, int64_t nmax, Geometry g, const R* __
     const int orig = sperm[a];
     R F0 = 0, F1 = 0, F2 = 0;
     for (int c = 0; c < g.K; ++c) {
-      const R* gc = grid + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
+      const int gc_idx = sidx * g.K + c;
+      const R* gc = grid + gc_idx * chan;
       R ph = 0, f0 = 0, f1 = 0, f2 = 0;
       for (int k = 0; k < P; ++k) {
         int z = cz + k;
@@ -336,8 +423,7 @@ __global__ void k_interp_direct(int64_t n, int64_t nmax, Geometry g, const R* __
           f2 += sx * wy[j] * dz[k];
         }
       }
-      const double Q = charges[2 * c];
-      ph += R(2.0 * zero_coef[c] * Q);
+      ph += R(2.0 * zero_coef[gc_idx] * charges[2 * gc_idx]);
       if (phi) phi[int64_t(c) * n + orig] = ph;
       const R qc = sq[int64_t(c) * nmax + a];
       F0 += qc * f0;

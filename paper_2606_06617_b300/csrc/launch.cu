@@ -21,7 +21,7 @@ constexpr int kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA on sm_1
 constexpr int kGatherThreads = kGatherThreadsFor<R>;
 constexpr int kDirectThreads = 256;
 
-WinCoef<R> win_coef(const LaunchCtx& c) {
+static WinCoef<R> win_coef(const LaunchCtx& c) {
   WinCoef<R> w;
   std::memset(&w, 0, sizeof(w));
   w.deg = c.deg_w;
@@ -30,7 +30,7 @@ WinCoef<R> win_coef(const LaunchCtx& c) {
   return w;
 }
 
-int sm_count() {
+static int sm_count() {
   static int n = 0;
   if (n == 0) {
     int dev = 0;
@@ -74,10 +74,10 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
   if (!pick_kc_kb<P>(k_spread<R, P>, c.geo.K, [](int k, int b) { return spread_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
-    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
-    k_spread_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(c.n, c.nmax, c.geo, static_cast<const R*>(c.st),
-                                                                   c.scell, static_cast<const R*>(c.sq), wc,
-                                                                   static_cast<R*>(c.grid));
+    const int blocks = int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+    k_spread_direct<R, P><<<std::max(blocks, 1), kDirectThreads, 0, c.stream>>>(
+        c.nmax, c.geo, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), wc,
+        static_cast<R*>(c.grid));
     ++*nlaunch;
     return cudaGetLastError();
   }
@@ -86,7 +86,7 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   int blocks = 0;
   cudaError_t e = persistent_blocks<P>(k_spread<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
-  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.nmax, c.tile_start, static_cast<const R*>(c.st),
+  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.sbox, c.nmax, c.tile_start, static_cast<const R*>(c.st),
                                                              c.scell, static_cast<const R*>(c.sq), wc, kc, kb,
                                                              static_cast<R*>(c.grid));
   ++*nlaunch;
@@ -99,10 +99,11 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
   if (!pick_kc_kb<P>(k_interp<R, P>, c.geo.K, [](int k, int b) { return gather_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
-    const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
-    k_interp_direct<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
-        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
-        static_cast<const R*>(c.grid), c.zero_coef, c.charges, static_cast<R*>(phi), static_cast<R*>(forces));
+    const int blocks = int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+    k_interp_direct<R, P><<<std::max(blocks, 1), kDirectThreads, 0, c.stream>>>(
+        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        static_cast<const R*>(c.sq), c.sperm, wc, static_cast<const R*>(c.grid), c.zero_coef, c.charges,
+        static_cast<R*>(phi), static_cast<R*>(forces));
     ++*nlaunch;
     return cudaGetLastError();
   }
@@ -117,7 +118,8 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   e = persistent_blocks<P>(k_interp<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
   const int threads = kGatherThreads;
-  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.n, c.nmax, c.geo, c.tile_start, static_cast<const R*>(c.st),
+  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.nmax, c.geo, c.sbox, c.soff, c.tile_start,
+                                                      static_cast<const R*>(c.st),
                                                       c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc, kb,
                                                       static_cast<const R*>(c.grid), c.zero_coef, c.charges,
                                                       static_cast<R*>(phi), static_cast<R*>(forces));
@@ -129,15 +131,17 @@ template <int P>
 cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
   const WinCoef<R> wc = win_coef(c);
-  const int blocks = int(std::min<int64_t>((c.n + kDirectThreads - 1) / kDirectThreads, 148 * 32));
+  const int blocks = std::max(1, int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32)));
   ++*nlaunch;
   if (stage == 0) {
     k_spread_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
-        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
-        static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces), static_cast<R*>(c.grid2));
+        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        static_cast<const R*>(c.sq), c.sperm, wc, static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces),
+        static_cast<R*>(c.grid2));
   } else {
     k_interp_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
-        c.n, c.nmax, c.geo, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), c.sperm, wc,
+        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        static_cast<const R*>(c.sq), c.sperm, wc,
         static_cast<const R*>(c.grid), static_cast<const R*>(c.grid2), c.zero_coef, c.charges, c.gsum, b.g_energy,
         static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces), static_cast<R*>(b.grad_q),
         static_cast<R*>(b.grad_pos));

@@ -13,26 +13,28 @@ namespace pswf {
 struct LaunchCtx {
   Geometry geo;
   int64_t nmax = 0;        // capacity of the sorted atom arrays
-  int64_t n = 0;           // atoms of the last set_points
-  int ntiles = 0;
+  int64_t n = 0;           // atoms of the last set_points (host copy; kernels read soff[B])
+  int ntiles = 0;          // B * nts
+  const double* sbox = nullptr;     // [B][3] box edges
+  const int* soff = nullptr;        // [B + 1] atom offsets per structure (device)
   const int* tile_start = nullptr;
   const void* st = nullptr;         // real [3][nmax]
   const uint64_t* scell = nullptr;  // [nmax]
   const void* sq = nullptr;         // real [K][nmax]
   const int* sperm = nullptr;       // [nmax]
-  void* grid = nullptr;             // real [K][Mz][My][Mxp]
-  const double* zero_coef = nullptr;
-  const double* charges = nullptr;
+  void* grid = nullptr;             // real [B][K][Mz][My][Mxp]
+  const double* zero_coef = nullptr;   // [B K]
+  const double* charges = nullptr;     // [B K][2]
   const double* coef_w = nullptr;   // host [P][deg_w + 1]
   int deg_w = 0;
   cudaStream_t stream = nullptr;
   // backward
-  void* grid2 = nullptr;            // real [K][Mz][My][Mxp]
-  const double* gsum = nullptr;     // [K][2]: sum_j gphi_j^c (first entry)
+  void* grid2 = nullptr;            // real [B][K][Mz][My][Mxp]
+  const double* gsum = nullptr;     // [B K][2]: sum_j gphi_j^c (first entry)
 };
 
 struct BackwardArgs {
-  const double* g_energy;   // device [K] or null
+  const double* g_energy;   // device [B K] or null
   const void* g_phi;        // device real [K][n] or null
   const void* g_forces;     // device real [n][3] or null
   void* grad_q;             // device real [K][n] or null

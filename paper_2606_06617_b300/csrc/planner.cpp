@@ -262,18 +262,25 @@ double mult_smooth(const Prolate& ps, int p, double u) {
   }
 }
 
-int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan& plan) {
-  plan = Plan();
+namespace {
+
+// Everything that depends on the grid spacing at box_max and on the set of
+// exponents, but not on a particular structure.
+int plan_core(const double box_max[3], int K, const int* pset, int npset, const Options& opt, Plan& plan) {
   plan.opt = opt;
   for (int d = 0; d < 3; ++d) {
-    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(plan, PSWF_EINVAL, "box edges must be positive and finite");
-    plan.box[d] = box[d];
+    if (!(box_max[d] > 0.0) || !std::isfinite(box_max[d]))
+      return fail(plan, PSWF_EINVAL, "box edges must be positive and finite");
+    plan.box_max[d] = box_max[d];
+    plan.box[d] = box_max[d];
   }
   if (K < 1 || K > kMaxK) return fail(plan, PSWF_EINVAL, "number of channels must be in 1..64");
   plan.K = K;
-  plan.p.assign(p, p + K);
-  for (int k = 0; k < K; ++k)
-    if (p[k] < 1 || p[k] > 6) return fail(plan, PSWF_EINVAL, "channel exponent p must be in 1..6");
+  bool use_p[7] = {false, false, false, false, false, false, false};
+  for (int k = 0; k < npset; ++k) {
+    if (pset[k] < 1 || pset[k] > 6) return fail(plan, PSWF_EINVAL, "channel exponent p must be in 1..6");
+    use_p[pset[k]] = true;
+  }
   if (!(opt.r_c > 0.0) || !std::isfinite(opt.r_c)) return fail(plan, PSWF_EINVAL, "r_c must be positive");
   if (!(opt.tol > 0.0 && opt.tol < 1.0)) return fail(plan, PSWF_EINVAL, "tol must be in (0, 1)");
   if (opt.precision != 0 && opt.precision != 1) return fail(plan, PSWF_EINVAL, "precision must be 0 (fp32) or 1 (fp64)");
@@ -287,10 +294,10 @@ int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan
   if (eta_t >= 1.0) return fail(plan, PSWF_EINVAL, "eta must be in (0, 1)");
   for (int d = 0; d < 3; ++d) {
     const int64_t M = opt.grid[d] > 0 ? opt.grid[d]
-                                      : next_fft_size(int64_t(std::ceil(box[d] * plan.k_c / (eta_t * kPi))));
+                                      : next_fft_size(int64_t(std::ceil(box_max[d] * plan.k_c / (eta_t * kPi))));
     if (M < 2 || M > 4096) return fail(plan, PSWF_EINVAL, "grid size per dimension must be in 2..4096");
     plan.M[d] = int(M);
-    plan.h[d] = box[d] / double(M);
+    plan.h[d] = box_max[d] / double(M);
   }
   plan.eta = 0.0;
   for (int d = 0; d < 3; ++d) plan.eta = std::max(plan.eta, plan.h[d] * plan.k_c / kPi);
@@ -299,7 +306,9 @@ int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan
   plan.est_band = std::fabs(plan.moll.eval(1.0));
   // Window bandwidth: the largest c_w whose main lobe does not alias onto the
   // band |k| < k_c: c_w = P pi (1 - eta / 2).  Spreading-error estimate
-  // 10 psi_0^{c_w}(1) / eta (calibrated against the direct-sum oracle).
+  // 10 psi_0^{c_w}(1) / eta (calibrated against the direct-sum oracle).  A
+  // structure with a finer spacing than box_max gives has a smaller eta, for
+  // which the same c_w and P are alias-free with more margin.
   auto cw_for = [&](int P) { return opt.c_w > 0 ? opt.c_w : P * kPi * (1.0 - 0.5 * plan.eta); };
   auto est_for = [&](const Prolate& w) { return 10.0 * std::fabs(w.eval(1.0)) / plan.eta; };
   if (opt.P > 0) {
@@ -324,7 +333,7 @@ int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan
     if (plan.omega[d] * plan.k_c / plan.c_w >= 1.0)
       return fail(plan, PSWF_EINVAL, "window band c_w / omega does not cover k_c");
   }
-  plan.V = box[0] * box[1] * box[2];
+  plan.V = box_max[0] * box_max[1] * box_max[2];
   plan.dV = plan.V / (double(plan.M[0]) * plan.M[1] * plan.M[2]);
   const double eps_poly = opt.precision == 1 ? 1e-15 : 1e-9;
   // ---- window pieces: W_j(t) = psi^{c_w}((2j - P + 2t)/P), s = 2t - 1 ----
@@ -342,81 +351,129 @@ int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan
       for (int n = 0; n <= deg; ++n) plan.coef_w[size_t(j) * (deg + 1) + n] = mono[n];
     }
   }
-  // ---- multiplier pieces ----
+  // ---- multiplier pieces, one row per exponent in use ----
   {
     const int nfit = 33;
-    std::vector<std::vector<double>> cheb(size_t(K) * kMultSeg);
+    std::vector<std::vector<double>> cheb(size_t(6) * kMultSeg);
     int deg = 1;
-    for (int k = 0; k < K; ++k) {
+    for (int pp = 1; pp <= 6; ++pp) {
+      if (!use_p[pp]) continue;
       std::vector<std::vector<double>> fam(kMultSeg);
       for (int i = 0; i < kMultSeg; ++i) {
         const double a = double(i) / kMultSeg, b = double(i + 1) / kMultSeg;
-        fam[i] = cheb_fit([&](double s) { return mult_smooth(plan.moll, plan.p[k], a + (b - a) * 0.5 * (s + 1.0)); }, nfit);
-        cheb[size_t(k) * kMultSeg + i] = fam[i];
+        fam[i] = cheb_fit([&](double s) { return mult_smooth(plan.moll, pp, a + (b - a) * 0.5 * (s + 1.0)); }, nfit);
+        cheb[size_t(pp - 1) * kMultSeg + i] = fam[i];
       }
       deg = std::max(deg, family_degree(fam, eps_poly));
     }
     deg = std::min(deg, kMaxMultDeg);
     plan.deg_m = deg;
-    plan.coef_m.assign(size_t(K) * kMultSeg * (deg + 1), 0.0);
+    plan.coef_m.assign(size_t(6) * kMultSeg * (deg + 1), 0.0);
     for (size_t i = 0; i < cheb.size(); ++i) {
+      if (cheb[i].empty()) continue;
       const auto mono = cheb_to_monomial(cheb[i], deg);
       for (int n = 0; n <= deg; ++n) plan.coef_m[i * (deg + 1) + n] = mono[n];
     }
   }
-  // ---- per-channel constants ----
-  const double c = plan.c, rc = plan.r_c, C0 = plan.moll.C0, lam = plan.moll.lambda0, V = plan.V;
-  plan.mult_scale.resize(K);
-  plan.self_coef.resize(K);
-  plan.zero_coef.resize(K);
+  // ---- per-exponent constants ----
+  const double c = plan.c, rc = plan.r_c, C0 = plan.moll.C0, lam = plan.moll.lambda0;
   const double d2 = plan.moll.eval(0.0, 2), d4 = plan.moll.eval(0.0, 4), d6 = plan.moll.eval(0.0, 6);
-  for (int k = 0; k < K; ++k) {
-    switch (plan.p[k]) {
+  for (int pp = 1; pp <= 6; ++pp) {
+    if (!use_p[pp]) continue;
+    double& ms = plan.mult_scale_p[pp];
+    double& sc = plan.self_coef_p[pp];
+    double& zn = plan.zero_num_p[pp];
+    switch (pp) {
       case 1:
-        plan.mult_scale[k] = 4.0 * kPi;
-        plan.self_coef[k] = 1.0 / (2.0 * C0 * rc);
+        ms = 4.0 * kPi;
+        sc = 1.0 / (2.0 * C0 * rc);
         // -(2 pi / V) int_0^{r_c} r (1 - G_1) dr = -(pi r_c^2 / (V C0)) int_0^1 x^2 psi
-        plan.zero_coef[k] = -kPi * rc * rc / (V * C0) * plan.moll.integral(0.0, 1.0, 2);
+        zn = -kPi * rc * rc / C0 * plan.moll.integral(0.0, 1.0, 2);
         break;
       case 2:
-        plan.mult_scale[k] = 2.0 * kPi * kPi;
-        plan.self_coef[k] = -d2 / (4.0 * rc * rc);
-        plan.zero_coef[k] = -2.0 * kPi / V * rc * C0;
+        ms = 2.0 * kPi * kPi;
+        sc = -d2 / (4.0 * rc * rc);
+        zn = -2.0 * kPi * rc * C0;
         break;
       case 3:
-        plan.mult_scale[k] = 2.0 * kPi * lam / C0;
-        plan.self_coef[k] = -d2 / (6.0 * C0 * rc * rc * rc);
-        plan.zero_coef[k] = 2.0 * kPi / V * (std::log(c / rc) + mult_smooth(plan.moll, 3, 0.0));
+        ms = 2.0 * kPi * lam / C0;
+        sc = -d2 / (6.0 * C0 * rc * rc * rc);
+        zn = 2.0 * kPi * (std::log(c / rc) + mult_smooth(plan.moll, 3, 0.0));
         break;
       case 4:
-        plan.mult_scale[k] = kPi * kPi * c / rc;
-        plan.self_coef[k] = d4 / (48.0 * std::pow(rc, 4));
-        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 4, 0.0) / (2.0 * V);
+        ms = kPi * kPi * c / rc;
+        sc = d4 / (48.0 * std::pow(rc, 4));
+        zn = ms * mult_smooth(plan.moll, 4, 0.0) / 2.0;
         break;
       case 5:
-        plan.mult_scale[k] = -kPi * lam * c * c / (3.0 * C0 * rc * rc);
-        plan.self_coef[k] = d4 / (90.0 * C0 * std::pow(rc, 5));
-        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 5, 0.0) / (2.0 * V);
+        ms = -kPi * lam * c * c / (3.0 * C0 * rc * rc);
+        sc = d4 / (90.0 * C0 * std::pow(rc, 5));
+        zn = ms * mult_smooth(plan.moll, 5, 0.0) / 2.0;
         break;
       case 6:
-        plan.mult_scale[k] = kPi * kPi * c * c * c / (12.0 * rc * rc * rc);
-        plan.self_coef[k] = -d6 / (1440.0 * std::pow(rc, 6));
-        plan.zero_coef[k] = plan.mult_scale[k] * mult_smooth(plan.moll, 6, 0.0) / (2.0 * V);
+        ms = kPi * kPi * c * c * c / (12.0 * rc * rc * rc);
+        sc = -d6 / (1440.0 * std::pow(rc, 6));
+        zn = ms * mult_smooth(plan.moll, 6, 0.0) / 2.0;
         break;
     }
   }
-  // ---- W-hat^-2 tables (indexed by |frequency|) ----
+  return PSWF_OK;
+}
+
+}  // namespace
+
+int struct_tables(const Plan& plan, const double box[3], StructTables& out, std::string& error) {
   for (int d = 0; d < 3; ++d) {
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) {
+      error = "box edges must be positive and finite";
+      return PSWF_EINVAL;
+    }
+    if (box[d] > plan.box_max[d] * (1.0 + 1e-12)) {
+      error = "box edge exceeds the plan's box_max";
+      return PSWF_EINVAL;
+    }
+  }
+  out.V = box[0] * box[1] * box[2];
+  out.dV = out.V / (double(plan.M[0]) * plan.M[1] * plan.M[2]);
+  for (int d = 0; d < 3; ++d) {
+    out.box[d] = box[d];
+    out.h[d] = box[d] / double(plan.M[d]);
+    out.omega[d] = plan.P * out.h[d] / 2.0;
     const int nf = plan.M[d] / 2 + 1;
-    plan.iw2[d].assign(nf, 0.0);
+    out.iw2[d].assign(nf, 0.0);
     for (int m = 0; m < nf; ++m) {
       const double kd = 2.0 * kPi * m / box[d];
-      const double arg = plan.omega[d] * kd / plan.c_w;
+      const double arg = out.omega[d] * kd / plan.c_w;
       if (arg <= 1.0) {
-        const double what = plan.omega[d] * plan.win.lambda0 * plan.win.eval(arg);
-        plan.iw2[d][m] = 1.0 / (what * what);
+        const double what = out.omega[d] * plan.win.lambda0 * plan.win.eval(arg);
+        out.iw2[d][m] = 1.0 / (what * what);
       }
     }
+  }
+  return PSWF_OK;
+}
+
+int make_batch_plan(const double box_max[3], int K, const int* pset, int npset, const Options& opt, Plan& plan) {
+  plan = Plan();
+  if (npset < 1 || !pset) return fail(plan, PSWF_EINVAL, "at least one channel exponent is required");
+  return plan_core(box_max, K, pset, npset, opt, plan);
+}
+
+int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan& plan) {
+  plan = Plan();
+  if (K < 1 || K > kMaxK) return fail(plan, PSWF_EINVAL, "number of channels must be in 1..64");
+  int rc = plan_core(box, K, p, K, opt, plan);
+  if (rc) return rc;
+  plan.p.assign(p, p + K);
+  if ((rc = struct_tables(plan, box, plan.st, plan.error))) return rc;
+  for (int d = 0; d < 3; ++d) plan.iw2[d] = plan.st.iw2[d];
+  plan.mult_scale.resize(K);
+  plan.self_coef.resize(K);
+  plan.zero_coef.resize(K);
+  for (int k = 0; k < K; ++k) {
+    plan.mult_scale[k] = plan.mult_scale_p[p[k]];
+    plan.self_coef[k] = plan.self_coef_p[p[k]];
+    plan.zero_coef[k] = plan.zero_num_p[p[k]] / plan.V;
   }
   return PSWF_OK;
 }

@@ -59,13 +59,23 @@ struct Options {
   int precision = 0;      // 0 fp32 path, 1 fp64 path
 };
 
+// Box-dependent tables of one structure on a plan's grid.
+struct StructTables {
+  double box[3] = {0, 0, 0};
+  double h[3] = {0, 0, 0};
+  double omega[3] = {0, 0, 0};
+  double V = 0, dV = 0;
+  std::vector<double> iw2[3];      // W-hat_d^-2 by |frequency| (0 .. M_d/2)
+};
+
 struct Plan {
   // inputs
-  double box[3] = {0, 0, 0};
+  double box[3] = {0, 0, 0};       // the box of a single-structure plan
+  double box_max[3] = {0, 0, 0};   // largest box a structure of this plan may have
   int K = 0;
-  std::vector<int> p;            // exponent per channel
+  std::vector<int> p;              // exponent per channel (single-structure plans)
   Options opt;
-  // chosen parameters
+  // chosen parameters (h, omega, eta: at box_max)
   double c = 0, c_w = 0, r_c = 0, k_c = 0, eta = 0, tol = 0;
   double h[3] = {0, 0, 0};
   double omega[3] = {0, 0, 0};
@@ -78,20 +88,35 @@ struct Plan {
   // window pieces: coef_w[j][n], monomials in s = 2t - 1, j = 0..P-1
   int deg_w = 0;
   std::vector<double> coef_w;    // P * (deg_w + 1)
-  // multiplier smooth parts: per channel, kMultSeg pieces on u in [0, 1]
+  // multiplier smooth parts: per exponent p (row p - 1; rows of exponents the
+  // plan does not use are zero), kMultSeg pieces on u in [0, 1]
   int deg_m = 0;
-  std::vector<double> coef_m;    // K * kMultSeg * (deg_m + 1)
-  std::vector<double> mult_scale;  // per channel constant in front of S_p
-  // 1-D tables of W-hat_d^-2 indexed by |frequency| (0 .. M_d/2)
-  std::vector<double> iw2[3];
-  // per channel constants
-  std::vector<double> self_coef;   // E_self = self_coef * sum q^2
-  std::vector<double> zero_coef;   // E^0 = zero_coef * Q_net^2
+  std::vector<double> coef_m;    // 6 * kMultSeg * (deg_m + 1)
+  // per exponent p (index p, 1..6): constant in front of S_p, self-energy
+  // coefficient, and V times the zero-frequency coefficient
+  double mult_scale_p[7] = {0, 0, 0, 0, 0, 0, 0};
+  double self_coef_p[7] = {0, 0, 0, 0, 0, 0, 0};
+  double zero_num_p[7] = {0, 0, 0, 0, 0, 0, 0};
+  // tables of the single-structure box (box == box_max)
+  StructTables st;
+  std::vector<double> iw2[3];      // = st.iw2
+  std::vector<double> mult_scale;  // per channel
+  std::vector<double> self_coef;   // E_self = self_coef * sum q^2, per channel
+  std::vector<double> zero_coef;   // E^0 = zero_coef * Q_net^2, per channel
   std::string error;
 };
 
 // Returns 0 on success, or a negative pswf status with plan.error set.
+// Single structure: the grid, stencil and window are chosen for `box`.
 int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan& plan);
+
+// Batch of structures sharing one grid: parameters chosen at `box_max` (the
+// coarsest spacing any structure will have), multiplier tables built for the
+// exponents in pset[0 .. npset-1]; plan.p stays empty.
+int make_batch_plan(const double box_max[3], int K, const int* pset, int npset, const Options& opt, Plan& plan);
+
+// Tables of one structure with edges `box` (each <= box_max) on the plan's grid.
+int struct_tables(const Plan& plan, const double box[3], StructTables& out, std::string& error);
 
 // Smooth part S_p(u) of Phi-hat_p = mult_scale_p * singular_p(k) * S_p(u),
 // u = k / k_c in [0, 1] (host FP64 reference used to fit the polynomials).

@@ -131,7 +131,7 @@ struct Slots {
   }
 };
 
-template <typename R, int P>
+// Origin (in grid points) of tile `tile` (index within its structure).
 __device__ inline void tile_origin(const Geometry& g, int tile, int& ox, int& oy, int& oz) {
   const int tx = tile % g.ntile[0], ty = (tile / g.ntile[0]) % g.ntile[1], tz = tile / (g.ntile[0] * g.ntile[1]);
   ox = tx * kTile;
@@ -142,7 +142,8 @@ __device__ inline void tile_origin(const Geometry& g, int tile, int& ox, int& oy
 // Fills the batch's window rows (values, and scaled derivatives when
 // rows == 6), the packed local start cell and (gather) the original index.
 template <typename R, int P, int ROWS>
-__device__ inline void batch_tables(const Geometry& g, int64_t nmax, int b0, int nb, int ox, int oy, int oz,
+__device__ inline void batch_tables(const Geometry& g, const double* __restrict__ box, int64_t nmax, int b0, int nb,
+                                    int ox, int oy, int oz,
                                     const R* __restrict__ st, const uint64_t* __restrict__ scell,
                                     const int* __restrict__ sperm, const WinCoef<R>& wc, R* wts, int* loc,
                                     int* perm) {
@@ -153,7 +154,7 @@ __device__ inline void batch_tables(const Geometry& g, int64_t nmax, int b0, int
     if constexpr (ROWS == 6) {
       R w[P], dw[P];
       window_weights<R, P>(st[d * nmax + b0 + a], wc, w, dw);
-      const R two_h = R(2.0 * g.M[d] / g.L[d]);
+      const R two_h = R(2.0 * g.M[d] / box[d]);
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         row[i] = w[i];
@@ -197,8 +198,8 @@ constexpr size_t spread_smem_bytes(int kc, int kb) {
 }
 
 template <typename R, int P>
-__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, int64_t nmax,
-                                                                   const int* __restrict__ tile_start,
+__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, const double* __restrict__ sbox,
+                                                                   int64_t nmax, const int* __restrict__ tile_start,
                                                                    const R* __restrict__ st,
                                                                    const uint64_t* __restrict__ scell,
                                                                    const R* __restrict__ sq, WinCoef<R> wc, int kc,
@@ -216,15 +217,17 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
   const Slots sl = Slots::template make<G, NS>(kc);
   const int lane = sl.lane, warp = sl.warp, nwarp = sl.nwarp, j = sl.j, cc = sl.cc;
   const int nchunk = (g.K + kc - 1) / kc;
-  const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
+  const int ntiles = g.B * g.nts;
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   for (int item = blockIdx.x; item < ntiles * nchunk; item += gridDim.x) {
     const int tile = item / nchunk, chunk = item - tile * nchunk;
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
     if (a0 == a1) continue;
+    const int sidx = tile / g.nts;
     const int c0 = chunk * kc, nk = min(kc, g.K - c0);
+    const int gc0 = sidx * g.K + c0;   // first grid channel of the item
     int ox, oy, oz;
-    tile_origin<R, P>(g, tile, ox, oy, oz);
+    tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
     __syncthreads();   // the previous item's flush is done with the region
     {
       const int nbytes = nk * N * int(sizeof(A));
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       __syncthreads();   // previous batch done with the tables (and sscale written)
-      batch_tables<R, P, 3>(g, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
+      batch_tables<R, P, 3>(g, sbox + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
       __syncthreads();
       const R qscale = kFixed && use_slot ? R(sscale[cc]) : R(1);
       for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
       for (int pl = warp; pl < nk * S; pl += nwarp) {
         const int c = pl / S, lz = pl - c * S;
         const R inv = kFixed ? R(1) / R(sscale[c]) : R(1);
-        R* dst = grid + (c0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane + gx;
+        R* dst = grid + (gc0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane + gx;
         const A* src = region + c * N + lz * R2 + lane;
         if (lane < S) {
           int gy = oy;
@@ -324,10 +327,14 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
 // not fit in shared memory (FP64 with large P): one thread per sorted atom,
 // global atomics.
 template <typename R, int P>
-__global__ void k_spread_direct(int64_t n, int64_t nmax, Geometry g, const R* __restrict__ st,
+__global__ void k_spread_direct(int64_t nmax, Geometry g, const int* __restrict__ soff,
+                                const int* __restrict__ tile_start, const R* __restrict__ st,
                                 const uint64_t* __restrict__ scell, const R* __restrict__ sq, WinCoef<R> wc,
                                 R* __restrict__ grid) {
+  const int64_t n = soff[g.B];
+  const int64_t chan = int64_t(g.M[2]) * g.M[1] * g.Mxp;
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+    const int sidx = find_struct(tile_start, g.nts, g.B, a);
     R wx[P], wy[P], wz[P];
     window_values<R, P>(st[a], wc, wx);
     window_values<R, P>(st[nmax + a], wc, wy);
@@ -336,7 +343,7 @@ __global__ void k_spread_direct(int64_t n, int64_t nmax, Geometry g, const R* __
     unpack_cell(scell[a], cx, cy, cz);
     for (int c = 0; c < g.K; ++c) {
       const R qc = sq[int64_t(c) * nmax + a];
-      R* gc = grid + int64_t(c) * g.M[2] * g.M[1] * g.Mxp;
+      R* gc = grid + (int64_t(sidx) * g.K + c) * chan;
       for (int k = 0; k < P; ++k) {
         const int z = wrap_index(cz + k, g.M[2]);
         for (int j = 0; j < P; ++j) {
@@ -362,7 +369,9 @@ __global__ void k_spread_direct(int64_t n, int64_t nmax, Geometry g, const R* __
 // then over the atom's slots.  With more than one chunk the force is
 // accumulated with global atomics (zeroed before the launch).
 template <typename R, int P>
-__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, int64_t nmax, Geometry g,
+__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax, Geometry g,
+                                                                   const double* __restrict__ sbox,
+                                                                   const int* __restrict__ soff,
                                                                    const int* __restrict__ tile_start,
                                                                    const R* __restrict__ st,
                                                                    const uint64_t* __restrict__ scell,
@@ -385,21 +394,24 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, i
   const int nchunk = (g.K + kc - 1) / kc;
   const int jr = j < P ? j : P - 1;        // row read by lanes beyond the stencil
   const int vi = j / GQ;                   // which sum this lane ends up holding
-  const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
+  const int64_t n = soff[g.B];
+  const int ntiles = g.B * g.nts;
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   for (int item = blockIdx.x; item < ntiles * nchunk; item += gridDim.x) {
     const int tile = item / nchunk, chunk = item - tile * nchunk;
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
     if (a0 == a1) continue;
+    const int sidx = tile / g.nts;
     const int c0 = chunk * kc, nk = min(kc, g.K - c0);
+    const int gc0 = sidx * g.K + c0;   // first grid channel of the item
     int ox, oy, oz;
-    tile_origin<R, P>(g, tile, ox, oy, oz);
+    tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
     __syncthreads();   // the previous item's reads of the region and tables are done
     {
       const int gx = lane < S ? wrap_index(ox + lane, g.M[0]) : 0;
       for (int pl = warp; pl < nk * S; pl += nwarp) {
         const int c = pl / S, lz = pl - c * S;
-        const R* src = grid + (c0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane + gx;
+        const R* src = grid + (gc0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane + gx;
         R* dst = region + c * N + lz * R2 + lane;
         if (lane < S) {
           int gy = oy;
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, i
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       if (b0 != a0) __syncthreads();   // previous batch done with the tables
-      batch_tables<R, P, 6>(g, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
+      batch_tables<R, P, 6>(g, sbox + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
       if (b0 == a0) cp_async_wait_all();
       __syncthreads();
       for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
@@ -468,7 +480,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t n, i
         if (valid && j % GQ == 0) {
           const int o = perm[al];
           if (vi == 0) {
-            if (phi) phi[int64_t(c0 + cc) * n + o] = v + R(2.0 * zero_coef[c0 + cc] * charges[2 * (c0 + cc)]);
+            if (phi) phi[int64_t(c0 + cc) * n + o] = v + R(2.0 * zero_coef[gc0 + cc] * charges[2 * (gc0 + cc)]);
           } else if (forces && cc == 0) {
             R* fo = forces + 3 * int64_t(o) + (vi - 1);
             if (nchunk == 1)

@@ -38,7 +38,8 @@ class PswfInfo(ctypes.Structure):
                 ("box", ctypes.c_double * 3), ("h", ctypes.c_double * 3), ("grid", ctypes.c_int * 3),
                 ("P", ctypes.c_int), ("K", ctypes.c_int), ("precision", ctypes.c_int),
                 ("deg_window", ctypes.c_int), ("deg_mult", ctypes.c_int), ("flags", ctypes.c_int),
-                ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+                ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("B", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 _lib = None
@@ -68,6 +69,10 @@ SIGNATURES = {
     "pswf_self_energy_noalloc": ([_vp, _i64, _vp, _vp, _vp], ctypes.c_int),
     "pswf_profile_enable": ([_vp, ctypes.c_int], ctypes.c_int),
     "pswf_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "pswf_batch_plan_create": ([_dp, ctypes.c_int, _i64, ctypes.c_int, _ip, ctypes.c_int, ctypes.POINTER(PswfOpts),
+                                _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pswf_batch_set_points": ([_vp, ctypes.c_int, _dp, _ip, ctypes.POINTER(ctypes.c_int64), _vp, ctypes.c_int, _vp],
+                              ctypes.c_int),
 }
 
 NSTAGE = 8
@@ -267,6 +272,96 @@ class Plan:
         self._stream()
         _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)
         return e, ph, f
+
+
+class BatchPlan(Plan):
+    """Up to b_max independent structures per call on one grid size (see
+    pswf_batch_plan_create).  execute() returns energy [b_max, K+1] and phi /
+    forces over the concatenated atoms (buffers of n_max rows)."""
+
+    def __init__(self, box_max, b_max: int, n_max: int, K: int, pset, r_c: float, *, tol: float = 1e-5,
+                 c: float = 0.0, c_w: float = 0.0, eta: float = 0.0, P: int = 0, grid=None, precision: int = 0,
+                 flags: int = 0, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PSWF-LR needs a CUDA device")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.K = int(K)
+        self.B = int(b_max)
+        self.pset = tuple(int(p) for p in pset)
+        self.box = tuple(float(b) for b in box_max)
+        self.dtype = torch.float64 if precision == 1 else torch.float32
+        L = lib()
+        box_a = (ctypes.c_double * 3)(*self.box)
+        p_a = (ctypes.c_int * len(self.pset))(*self.pset)
+        o = make_opts(r_c=r_c, tol=tol, c=c, c_w=c_w, eta=eta, P=P, grid=grid, precision=precision, flags=flags)
+        h = _vp()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            _check(L.pswf_batch_plan_create(box_a, self.B, int(n_max), self.K, p_a, len(self.pset), ctypes.byref(o),
+                                            _vp(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_max = int(n_max)
+        info = PswfInfo()
+        _check(L.pswf_plan_info(self._h, ctypes.byref(info)), self._h)
+        self.info = _info_dict(info)
+        nbytes = max(int(self.info["workspace_bytes"]), 256)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self._ws.data_ptr() + 255) & ~255
+        with torch.cuda.device(self.device):
+            _check(L.pswf_plan_set_workspace(self._h, _vp(aligned), nbytes), self._h)
+        self.n = None
+        self.flags = int(flags)
+        self.generation = 0
+
+    def set_points(self, boxes, ps, offsets, pos, q):
+        """boxes [b, 3], ps [b, K] (host), offsets [b+1] (host int64),
+        pos cuda [n, 3], q cuda [K, n] over the concatenated atoms."""
+        import torch
+        boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        b = boxes.shape[0]
+        ps = np.ascontiguousarray(ps, dtype=np.int32).reshape(b, self.K)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        if offsets.shape != (b + 1,):
+            raise ValueError("offsets must have b + 1 entries")
+        n = int(offsets[-1]) if b > 0 else 0
+        if pos.dtype not in (torch.float32, torch.float64):
+            pos = pos.double()
+        pos = pos.contiguous()
+        q = q.to(self.dtype).contiguous()
+        if pos.shape != (n, 3) or q.shape != (self.K, n):
+            raise ValueError("pos must be [n, 3] and q [K, n] with n = offsets[-1]")
+        self._stream()
+        self._tables = (boxes, ps, offsets)
+        _check(lib().pswf_batch_set_points(self._h, b, boxes.ctypes.data_as(_dp), ps.ctypes.data_as(_ip),
+                                           offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           _vp(pos.data_ptr() if n else 0), 1 if pos.dtype == torch.float64 else 0,
+                                           _vp(q.data_ptr() if n else 0)), self._h)
+        self._keep = (pos, q)
+        self.n = n
+        self.generation += 1
+
+    def execute(self, energy: bool = True, phi: bool = True, forces: bool = True, out=None):
+        """Returns (energy [b_max, K+1], phi [K, n_max] or None, forces [n_max, 3] or None)."""
+        import torch
+        if self.n is None:
+            raise PswfError(-8, "execute before set_points")
+        if out is None:
+            e = torch.empty(self.B, self.K + 1, dtype=torch.float64, device=self.device) if energy else None
+            ph = torch.empty(self.K, self.n_max, dtype=self.dtype, device=self.device) if phi else None
+            f = torch.empty(self.n_max, 3, dtype=self.dtype, device=self.device) if forces else None
+            out = (e, ph, f)
+        e, ph, f = out
+        ptr = lambda t: _vp(t.data_ptr() if (t is not None and t.numel() > 0) else 0)
+        self._stream()
+        _check(lib().pswf_execute(self._h, ptr(e), ptr(ph), ptr(f)), self._h)
+        return e, ph, f
+
+    def self_energy(self) -> np.ndarray:
+        out = (ctypes.c_double * (self.B * self.K))()
+        self._stream()
+        _check(lib().pswf_self_energy(self._h, out), self._h)
+        return np.array(out[:]).reshape(self.B, self.K)
 
 
 def _make_function():
