@@ -219,6 +219,75 @@ const char* pswf_strerror(int status);
 /* Copies the plan's last error message into buf (NUL-terminated). */
 int pswf_plan_last_error(pswf_plan plan, char* buf, int len);
 
+/* ---- request server (continuous batching; not part of the paper) ------
+ * Serves independent structures (each: n atoms, an orthorhombic box, K
+ * channels with exponents from pset) over batch plans.  Every structure is
+ * routed to the smallest bucket whose cubic grid covers its largest box edge
+ * at spacing h_max and whose batch holds its atoms; its result is what a
+ * batch plan of that bucket gives for it alone.  Each bucket owns `inflight`
+ * batch contexts (plan, stream, device buffers, pinned staging) allocated at
+ * creation, so device memory is fixed; a scheduler thread hands the
+ * bucket's oldest requests to every free context (up to b_max structures and
+ * n_max atoms), and with use_graphs the context's kernels run as one
+ * captured CUDA graph per batch.  Submit and wait are thread-safe. */
+#define PSWF_MAX_BUCKETS 16
+typedef struct pswf_server_s* pswf_server;
+
+typedef struct {
+  double r_c, tol, c;             /* method parameters as in pswf_opts (c 0 -> log(3 / tol)) */
+  double h_max;                   /* largest grid spacing (A); 0 -> 0.5 pi r_c / c (eta = 0.5) */
+  int K;                          /* channels per structure */
+  int npset;                      /* number of exponents in pset */
+  int pset[6];                    /* exponents channels may use */
+  int nbucket;                    /* buckets, 1..PSWF_MAX_BUCKETS */
+  int grid[PSWF_MAX_BUCKETS];     /* cubic grid size per bucket, strictly ascending */
+  int b_max[PSWF_MAX_BUCKETS];    /* structures per batch of each bucket */
+  int64_t n_max[PSWF_MAX_BUCKETS];/* atoms per batch of each bucket */
+  int inflight;                   /* batch contexts per bucket (default 2) */
+  int precision;                  /* 0: FP32 path, 1: FP64 */
+  int use_graphs;                 /* 1 (default): replay one captured CUDA graph per batch */
+  int P;                          /* stencil width; 0 -> planner */
+} pswf_server_opts;
+
+/* Defaults: tol 1e-5, inflight 2, use_graphs 1, everything else 0. */
+void pswf_server_opts_default(pswf_server_opts* o);
+
+/* Creates the buckets' plans and buffers on the current device and starts
+ * the scheduler thread.  PSWF_EINVAL for bad options, PSWF_ENOMEM if the
+ * contexts do not fit. */
+int pswf_server_create(const pswf_server_opts* opts, pswf_server* out);
+
+/* Bucket a structure of n atoms with edges box (host [3]) would use: returns
+ * its index (>= 0) and, if info != NULL, fills it with that bucket's plan
+ * parameters (grid, P, c, c_w, ...); PSWF_EINVAL if no bucket holds it. */
+int pswf_server_route(pswf_server srv, int64_t n, const double box[3], pswf_info* info);
+
+/* Queues one structure: box host [3], ps host [K], pos host double [n][3],
+ * q host double [K][n] (copied before returning; FP32 plans round q).
+ * *ticket identifies it for pswf_server_wait.  PSWF_EINVAL if no bucket
+ * holds it or an exponent is not in pset; a failed server returns its
+ * status. */
+int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const int* ps, const double* pos,
+                       const double* q, int64_t* ticket);
+
+/* Blocks until the structure is done and copies its results: energy host
+ * double [K + 1] (per channel, total last), phi host double [K][n] and forces
+ * host double [n][3] (either may be NULL); latency_ms (may be NULL) = time
+ * from submit to the completion of its batch.  The ticket is released. */
+int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
+                     double* latency_ms);
+
+/* Counters since creation (any may be NULL); returns the server's failure
+ * status (0 if healthy). */
+int pswf_server_stats(pswf_server srv, int64_t* batches, int64_t* requests, int64_t* atoms);
+
+/* Message of the last server failure. */
+int pswf_server_last_error(pswf_server srv, char* buf, int len);
+
+/* Stops the scheduler, waits for batches in flight and frees everything;
+ * tickets not yet waited for are dropped. */
+void pswf_server_destroy(pswf_server srv);
+
 /* ---- measurement support (not part of the paper's method) -------------- */
 #define PSWF_NSTAGE 8
 /* Stage indices for pswf_profile_read. */

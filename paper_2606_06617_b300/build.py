@@ -25,6 +25,7 @@ UNITS = [
     ("launch.cu", "launch_f32.o", ["-DPSWF_REAL=float"]),
     ("launch.cu", "launch_f64.o", ["-DPSWF_REAL=double"]),
     ("planner.cpp", "planner.o", []),
+    ("server.cu", "server.o", []),
 ]
 
 

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "internal.hpp"
 #include "kernels.cuh"
 #include "launch.cuh"
 #include "planner.hpp"
@@ -665,6 +666,41 @@ int batch_tables_async(pswf_plan p, int b, const double* boxes, const int* ps, c
     return rc;
   return cuda_check(p, cudaEventRecord(p->stab_ev, p->stream), "record table upload");
 }
+
+}  // namespace
+
+namespace pswf {
+
+int plan_fill_tables(pswf_plan p, int b, const double* boxes, const int* ps, const int64_t* offsets) {
+  int rc = ensure_workspace(p);
+  if (rc) return rc;
+  if (!p->h_stab) {
+    if ((rc = cuda_check(p, cudaMallocHost(&p->h_stab, size_t(p->stab_bytes)), "pinned table mirror"))) return rc;
+    if ((rc = cuda_check(p, cudaEventCreateWithFlags(&p->stab_ev, cudaEventDisableTiming), "table event"))) return rc;
+  }
+  return fill_stab(p, b, boxes, ps, offsets, static_cast<char*>(p->h_stab));
+}
+
+int plan_upload_tables(pswf_plan p) {
+  return cuda_check(p, cudaMemcpyAsync(p->stab, p->h_stab, size_t(p->stab_bytes), cudaMemcpyHostToDevice, p->stream),
+                    "upload structure tables");
+}
+
+int plan_run_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const void* q) {
+  return p->real_size == 4 ? do_set_points<float>(p, n, pos, pos_dtype, q) : do_set_points<double>(p, n, pos, pos_dtype, q);
+}
+
+int plan_run_execute(pswf_plan p, double* energy, void* phi, void* forces) {
+  return p->real_size == 4 ? do_execute<float>(p, energy, phi, forces) : do_execute<double>(p, energy, phi, forces);
+}
+
+cudaStream_t plan_stream(pswf_plan p) { return p->stream; }
+int plan_precision(pswf_plan p) { return p->real_size == 8 ? 1 : 0; }
+const char* plan_error(pswf_plan p) { return p->last_error.c_str(); }
+
+}  // namespace pswf
+
+namespace {
 
 int make_fft(pswf_plan p) {
   const Plan& h = p->host;

@@ -1,0 +1,505 @@
+// Request server: continuous batching of independent structures over batch
+// plans (include/pswf_lr.h, "request server").
+//
+// Structures are routed to the smallest grid bucket that holds their box at
+// the server's largest grid spacing h_max.  Each bucket owns a fixed number
+// of batch contexts (a batch plan on its own stream, device buffers for one
+// batch, pinned staging); device memory is therefore bounded at creation and
+// a request waits in its bucket's queue until a context is free (admission
+// by memory).  A scheduler thread takes, for every free context, the
+// bucket's oldest pending requests up to the context's structure and atom
+// capacity, stages them, and launches: table and input copies, the batch
+// kernels (one captured CUDA graph per context, replayed for every batch:
+// the plan's launch shapes depend only on its capacity), output copies, and
+// a host callback that marks the context finished.  Requests that arrive
+// while batches run are admitted as soon as a context frees up; batches of
+// different contexts overlap on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.hpp"
+#include "pswf_lr.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id = 0;
+  int64_t n = 0;
+  double box[3] = {0, 0, 0};
+  std::vector<int> ps;          // [K]
+  std::vector<double> pos;      // [n][3]
+  std::vector<double> q;        // [K][n]
+  int bucket = 0;
+  int status = 1;               // 1 pending, 0 done, < 0 failed
+  Clock::time_point t_submit, t_done;
+  std::vector<double> energy;   // [K + 1]
+  std::vector<double> phi;      // [K][n]
+  std::vector<double> forces;   // [n][3]
+};
+
+struct Context {
+  pswf_plan plan = nullptr;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  double* d_pos = nullptr;   // [n_max][3]
+  void* d_q = nullptr;       // real [K][n_max]
+  double* d_e = nullptr;     // [b_max][K + 1]
+  void* d_phi = nullptr;     // real [K][n_max]
+  void* d_f = nullptr;       // real [n_max][3]
+  double* h_pos = nullptr;   // pinned mirrors
+  void* h_q = nullptr;
+  double* h_e = nullptr;
+  void* h_phi = nullptr;
+  void* h_f = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool busy = false;
+  bool finished = false;     // set by the host callback
+  std::vector<Request*> reqs;
+  std::vector<int64_t> offsets;
+  struct pswf_server_s* srv = nullptr;
+};
+
+struct Bucket {
+  int grid = 0;
+  int b_max = 0;
+  int64_t n_max = 0;
+  double box_max[3] = {0, 0, 0};
+  std::deque<Request*> pending;
+  std::vector<std::unique_ptr<Context>> ctx;
+};
+
+}  // namespace
+
+struct pswf_server_s {
+  pswf_server_opts opt{};
+  int K = 0;
+  size_t rs = 4;
+  int device = 0;
+  std::vector<std::unique_ptr<Bucket>> buckets;
+  std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_done;
+  std::thread th;
+  bool stop = false;
+  int64_t next_id = 1;
+  int64_t n_batches = 0, n_requests = 0, n_atoms = 0;
+  int fatal = 0;
+  std::string error;
+};
+
+namespace {
+
+int cuda_ok(pswf_server srv, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PSWF_OK;
+  srv->error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PSWF_ENOMEM : PSWF_ECUDA;
+}
+
+void CUDART_CB on_batch_done(void* arg) {
+  Context* c = static_cast<Context*>(arg);
+  pswf_server srv = c->srv;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    c->finished = true;
+  }
+  srv->cv_sched.notify_one();
+}
+
+int make_context(pswf_server srv, Bucket& b, Context& c) {
+  const pswf_server_opts& o = srv->opt;
+  const int K = srv->K;
+  const size_t rs = srv->rs;
+  int rc;
+  c.srv = srv;
+  if ((rc = cuda_ok(srv, cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "stream"))) return rc;
+  pswf_opts po;
+  pswf_opts_default(&po);
+  po.tol = o.tol;
+  po.r_c = o.r_c;
+  po.c = o.c;
+  po.P = o.P;
+  po.precision = o.precision;
+  for (int d = 0; d < 3; ++d) po.grid[d] = b.grid;
+  if ((rc = pswf_batch_plan_create(b.box_max, b.b_max, b.n_max, K, o.pset, o.npset, &po, c.stream, &c.plan))) {
+    srv->error = "batch plan for grid " + std::to_string(b.grid) + ": " + pswf_strerror(rc);
+    return rc;
+  }
+  pswf_info info;
+  pswf_plan_info(c.plan, &info);
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.ws, size_t(info.workspace_bytes)), "workspace"))) return rc;
+  if ((rc = pswf_plan_set_workspace(c.plan, c.ws, info.workspace_bytes))) {
+    srv->error = "workspace";
+    return rc;
+  }
+  const size_t n = size_t(std::max<int64_t>(b.n_max, 1));
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.d_pos, n * 3 * 8), "buffers"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.d_q, n * K * rs), "buffers"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.d_e, size_t(b.b_max) * (K + 1) * 8), "buffers"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.d_phi, n * K * rs), "buffers"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMalloc(&c.d_f, n * 3 * rs), "buffers"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMallocHost(&c.h_pos, n * 3 * 8), "pinned"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMallocHost(&c.h_q, n * K * rs), "pinned"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMallocHost(&c.h_e, size_t(b.b_max) * (K + 1) * 8), "pinned"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMallocHost(&c.h_phi, n * K * rs), "pinned"))) return rc;
+  if ((rc = cuda_ok(srv, cudaMallocHost(&c.h_f, n * 3 * rs), "pinned"))) return rc;
+  return PSWF_OK;
+}
+
+void free_context(Context& c) {
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  if (c.plan) pswf_plan_destroy(c.plan);
+  for (void* p : {static_cast<void*>(c.d_pos), c.d_q, static_cast<void*>(c.d_e), c.d_phi, c.d_f, c.ws})
+    if (p) cudaFree(p);
+  for (void* p : {static_cast<void*>(c.h_pos), c.h_q, static_cast<void*>(c.h_e), c.h_phi, c.h_f})
+    if (p) cudaFreeHost(p);
+  if (c.stream) cudaStreamDestroy(c.stream);
+}
+
+// Stages the batch in c.reqs and enqueues it on the context's stream.
+int launch_batch(pswf_server srv, Bucket& b, Context& c) {
+  const int K = srv->K;
+  const size_t rs = srv->rs;
+  const int nb = int(c.reqs.size());
+  c.offsets.assign(nb + 1, 0);
+  std::vector<double> boxes(size_t(nb) * 3);
+  std::vector<int> ps(size_t(nb) * K);
+  for (int i = 0; i < nb; ++i) {
+    const Request* r = c.reqs[i];
+    c.offsets[i + 1] = c.offsets[i] + r->n;
+    for (int d = 0; d < 3; ++d) boxes[3 * i + d] = r->box[d];
+    for (int k = 0; k < K; ++k) ps[size_t(i) * K + k] = r->ps[k];
+  }
+  const int64_t n = c.offsets[nb];
+  for (int i = 0; i < nb; ++i) {
+    const Request* r = c.reqs[i];
+    if (r->n) std::memcpy(c.h_pos + 3 * c.offsets[i], r->pos.data(), size_t(r->n) * 24);
+    for (int k = 0; k < K; ++k) {
+      const double* src = r->q.data() + size_t(k) * r->n;
+      if (rs == 4) {
+        float* dst = static_cast<float*>(c.h_q) + size_t(k) * n + c.offsets[i];
+        for (int64_t a = 0; a < r->n; ++a) dst[a] = float(src[a]);
+      } else {
+        double* dst = static_cast<double*>(c.h_q) + size_t(k) * n + c.offsets[i];
+        std::memcpy(dst, src, size_t(r->n) * 8);
+      }
+    }
+  }
+  int rc;
+  if ((rc = pswf::plan_fill_tables(c.plan, nb, boxes.data(), ps.data(), c.offsets.data()))) {
+    srv->error = pswf::plan_error(c.plan);
+    return rc;
+  }
+  if ((rc = pswf::plan_upload_tables(c.plan))) return rc;
+  if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.d_pos, c.h_pos, size_t(n) * 24, cudaMemcpyHostToDevice, c.stream), "h2d")))
+    return rc;
+  if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.d_q, c.h_q, size_t(n) * K * rs, cudaMemcpyHostToDevice, c.stream), "h2d")))
+    return rc;
+  if (srv->opt.use_graphs) {
+    if (!c.gexec) {
+      cudaGraph_t g = nullptr;
+      if ((rc = cuda_ok(srv, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed), "begin capture")))
+        return rc;
+      int rc1 = pswf::plan_run_set_points(c.plan, b.n_max, c.d_pos, 1, c.d_q);
+      int rc2 = rc1 ? rc1 : pswf::plan_run_execute(c.plan, c.d_e, c.d_phi, c.d_f);
+      const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
+      if (rc2) {
+        if (g) cudaGraphDestroy(g);
+        srv->error = pswf::plan_error(c.plan);
+        return rc2;
+      }
+      if ((rc = cuda_ok(srv, ec, "end capture"))) return rc;
+      const cudaError_t ei = cudaGraphInstantiate(&c.gexec, g, 0);
+      cudaGraphDestroy(g);
+      if ((rc = cuda_ok(srv, ei, "graph instantiate"))) return rc;
+    }
+    if ((rc = cuda_ok(srv, cudaGraphLaunch(c.gexec, c.stream), "graph launch"))) return rc;
+  } else {
+    if ((rc = pswf::plan_run_set_points(c.plan, n, c.d_pos, 1, c.d_q))) return rc;
+    if ((rc = pswf::plan_run_execute(c.plan, c.d_e, c.d_phi, c.d_f))) return rc;
+  }
+  if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.h_e, c.d_e, size_t(nb) * (K + 1) * 8, cudaMemcpyDeviceToHost, c.stream),
+                    "d2h")))
+    return rc;
+  if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.h_phi, c.d_phi, size_t(n) * K * rs, cudaMemcpyDeviceToHost, c.stream),
+                    "d2h")))
+    return rc;
+  if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.h_f, c.d_f, size_t(n) * 3 * rs, cudaMemcpyDeviceToHost, c.stream), "d2h")))
+    return rc;
+  return cuda_ok(srv, cudaLaunchHostFunc(c.stream, on_batch_done, &c), "host callback");
+}
+
+// Copies a finished batch's results into its requests (outside the lock).
+void collect_batch(pswf_server srv, Context& c) {
+  const int K = srv->K;
+  const size_t rs = srv->rs;
+  const int nb = int(c.reqs.size());
+  const int64_t n = c.offsets[nb];
+  for (int i = 0; i < nb; ++i) {
+    Request* r = c.reqs[i];
+    r->energy.assign(c.h_e + size_t(i) * (K + 1), c.h_e + size_t(i + 1) * (K + 1));
+    r->phi.resize(size_t(K) * r->n);
+    r->forces.resize(size_t(r->n) * 3);
+    for (int k = 0; k < K; ++k)
+      for (int64_t a = 0; a < r->n; ++a) {
+        const size_t src = size_t(k) * n + c.offsets[i] + a;
+        r->phi[size_t(k) * r->n + a] =
+            rs == 4 ? double(static_cast<const float*>(c.h_phi)[src]) : static_cast<const double*>(c.h_phi)[src];
+      }
+    for (int64_t a = 0; a < 3 * r->n; ++a) {
+      const size_t src = size_t(3 * c.offsets[i] + a);
+      r->forces[a] = rs == 4 ? double(static_cast<const float*>(c.h_f)[src]) : static_cast<const double*>(c.h_f)[src];
+    }
+  }
+}
+
+void fail_requests(std::vector<Request*>& rs, int status) {
+  for (Request* r : rs) {
+    r->status = status;
+    r->t_done = Clock::now();
+  }
+}
+
+void scheduler(pswf_server srv) {
+  cudaSetDevice(srv->device);
+  std::unique_lock<std::mutex> lk(srv->mu);
+  while (!srv->stop) {
+    bool progress = false;
+    for (auto& bp : srv->buckets) {
+      Bucket& b = *bp;
+      for (auto& cp : b.ctx) {
+        Context& c = *cp;
+        if (c.busy && c.finished) {
+          lk.unlock();
+          collect_batch(srv, c);
+          lk.lock();
+          const auto now = Clock::now();
+          for (Request* r : c.reqs) {
+            r->status = 0;
+            r->t_done = now;
+          }
+          c.reqs.clear();
+          c.busy = false;
+          c.finished = false;
+          progress = true;
+          srv->cv_done.notify_all();
+        }
+        if (!c.busy && !b.pending.empty() && !srv->fatal) {
+          int64_t atoms = 0;
+          while (!b.pending.empty() && int(c.reqs.size()) < b.b_max && atoms + b.pending.front()->n <= b.n_max) {
+            atoms += b.pending.front()->n;
+            c.reqs.push_back(b.pending.front());
+            b.pending.pop_front();
+          }
+          if (c.reqs.empty()) continue;
+          c.busy = true;
+          lk.unlock();
+          const int rc = launch_batch(srv, b, c);
+          lk.lock();
+          if (rc) {
+            srv->fatal = rc;
+            fail_requests(c.reqs, rc);
+            c.reqs.clear();
+            c.busy = false;
+            srv->cv_done.notify_all();
+          } else {
+            ++srv->n_batches;
+            srv->n_requests += int64_t(c.reqs.size());
+            srv->n_atoms += atoms;
+          }
+          progress = true;
+        }
+      }
+    }
+    if (srv->fatal) {
+      for (auto& bp : srv->buckets) {
+        Bucket& b = *bp;
+        std::vector<Request*> rs(b.pending.begin(), b.pending.end());
+        b.pending.clear();
+        fail_requests(rs, srv->fatal);
+      }
+      srv->cv_done.notify_all();
+    }
+    if (!progress) srv->cv_sched.wait_for(lk, std::chrono::milliseconds(2));
+  }
+}
+
+int route(pswf_server srv, int64_t n, const double box[3]) {
+  const double lmax = std::max(box[0], std::max(box[1], box[2]));
+  for (size_t i = 0; i < srv->buckets.size(); ++i) {
+    const Bucket& b = *srv->buckets[i];
+    if (lmax <= b.box_max[0] * (1.0 + 1e-12) && n <= b.n_max) return int(i);
+  }
+  return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pswf_server_opts_default(pswf_server_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-5;
+  o->inflight = 2;
+  o->use_graphs = 1;
+}
+
+int pswf_server_create(const pswf_server_opts* opts, pswf_server* out) {
+  if (!opts || !out) return PSWF_EINVAL;
+  *out = nullptr;
+  const pswf_server_opts& o = *opts;
+  if (o.K < 1 || o.K > 64 || o.npset < 1 || o.npset > 6 || o.nbucket < 1 || o.nbucket > PSWF_MAX_BUCKETS ||
+      !(o.r_c > 0) || o.inflight < 1 || o.inflight > 16 || (o.precision != 0 && o.precision != 1))
+    return PSWF_EINVAL;
+  pswf_server srv = new (std::nothrow) pswf_server_s();
+  if (!srv) return PSWF_ENOMEM;
+  srv->opt = o;
+  srv->K = o.K;
+  srv->rs = o.precision == 1 ? 8 : 4;
+  cudaGetDevice(&srv->device);
+  const double tol = o.tol > 0 ? o.tol : 1e-5;
+  srv->opt.tol = tol;
+  const double c = o.c > 0 ? o.c : std::log(3.0 / tol);
+  const double h_max = o.h_max > 0 ? o.h_max : 0.5 * 3.14159265358979323846 * o.r_c / c;
+  int rc = PSWF_OK;
+  for (int i = 0; i < o.nbucket && !rc; ++i) {
+    if (o.grid[i] < 4 || o.b_max[i] < 1 || o.n_max[i] < 1 || (i > 0 && o.grid[i] <= o.grid[i - 1])) {
+      rc = PSWF_EINVAL;
+      srv->error = "buckets need ascending grids >= 4 and positive capacities";
+      break;
+    }
+    auto b = std::make_unique<Bucket>();
+    b->grid = o.grid[i];
+    b->b_max = o.b_max[i];
+    b->n_max = o.n_max[i];
+    for (int d = 0; d < 3; ++d) b->box_max[d] = o.grid[i] * h_max;
+    srv->buckets.push_back(std::move(b));
+  }
+  for (size_t i = 0; i < srv->buckets.size() && !rc; ++i) {
+    Bucket& b = *srv->buckets[i];
+    for (int j = 0; j < o.inflight && !rc; ++j) {
+      b.ctx.push_back(std::make_unique<Context>());
+      rc = make_context(srv, b, *b.ctx.back());
+    }
+  }
+  if (rc) {
+    for (auto& b : srv->buckets)
+      for (auto& c : b->ctx) free_context(*c);
+    delete srv;
+    return rc;
+  }
+  srv->th = std::thread(scheduler, srv);
+  *out = srv;
+  return PSWF_OK;
+}
+
+int pswf_server_route(pswf_server srv, int64_t n, const double box[3], pswf_info* info) {
+  if (!srv || !box || n < 0) return PSWF_EINVAL;
+  const int bi = route(srv, n, box);
+  if (bi < 0) return PSWF_EINVAL;
+  if (info) pswf_plan_info(srv->buckets[bi]->ctx[0]->plan, info);
+  return bi;
+}
+
+int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const int* ps, const double* pos,
+                       const double* q, int64_t* ticket) {
+  if (!srv || !box || !ps || !ticket || n < 0 || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0.0)) return PSWF_EINVAL;
+  const int K = srv->K;
+  for (int k = 0; k < K; ++k) {
+    bool ok = false;
+    for (int i = 0; i < srv->opt.npset; ++i) ok = ok || srv->opt.pset[i] == ps[k];
+    if (!ok) return PSWF_EINVAL;
+  }
+  const int bi = route(srv, n, box);
+  if (bi < 0) return PSWF_EINVAL;
+  auto r = std::make_unique<Request>();
+  r->n = n;
+  for (int d = 0; d < 3; ++d) r->box[d] = box[d];
+  r->ps.assign(ps, ps + K);
+  r->pos.assign(pos, pos + 3 * n);
+  r->q.assign(q, q + size_t(K) * n);
+  r->bucket = bi;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->fatal) return srv->fatal;
+    r->id = srv->next_id++;
+    *ticket = r->id;
+    srv->buckets[bi]->pending.push_back(r.get());
+    srv->reqs.emplace(r->id, std::move(r));
+  }
+  srv->cv_sched.notify_one();
+  return PSWF_OK;
+}
+
+int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
+                     double* latency_ms) {
+  if (!srv) return PSWF_EINVAL;
+  std::unique_ptr<Request> r;
+  {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return PSWF_EINVAL;
+    Request* rp = it->second.get();
+    srv->cv_done.wait(lk, [&] { return rp->status != 1; });
+    r = std::move(it->second);
+    srv->reqs.erase(it);
+  }
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  if (r->status) return r->status;
+  const int K = srv->K;
+  if (energy) std::memcpy(energy, r->energy.data(), size_t(K + 1) * 8);
+  if (phi && r->n) std::memcpy(phi, r->phi.data(), size_t(K) * r->n * 8);
+  if (forces && r->n) std::memcpy(forces, r->forces.data(), size_t(r->n) * 24);
+  return PSWF_OK;
+}
+
+int pswf_server_stats(pswf_server srv, int64_t* batches, int64_t* requests, int64_t* atoms) {
+  if (!srv) return PSWF_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (batches) *batches = srv->n_batches;
+  if (requests) *requests = srv->n_requests;
+  if (atoms) *atoms = srv->n_atoms;
+  return srv->fatal;
+}
+
+int pswf_server_last_error(pswf_server srv, char* buf, int len) {
+  if (!srv || !buf || len <= 0) return PSWF_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  std::snprintf(buf, size_t(len), "%s", srv->error.c_str());
+  return PSWF_OK;
+}
+
+void pswf_server_destroy(pswf_server srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_sched.notify_all();
+  if (srv->th.joinable()) srv->th.join();
+  for (auto& b : srv->buckets)
+    for (auto& c : b->ctx) free_context(*c);
+  delete srv;
+}
+
+}  // extern "C"

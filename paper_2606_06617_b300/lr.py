@@ -8,6 +8,7 @@ first use; there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -42,6 +43,18 @@ class PswfInfo(ctypes.Structure):
                 ("B", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
+MAX_BUCKETS = 16
+
+
+class PswfServerOpts(ctypes.Structure):
+    _fields_ = [("r_c", ctypes.c_double), ("tol", ctypes.c_double), ("c", ctypes.c_double),
+                ("h_max", ctypes.c_double), ("K", ctypes.c_int), ("npset", ctypes.c_int),
+                ("pset", ctypes.c_int * 6), ("nbucket", ctypes.c_int), ("grid", ctypes.c_int * MAX_BUCKETS),
+                ("b_max", ctypes.c_int * MAX_BUCKETS), ("n_max", ctypes.c_int64 * MAX_BUCKETS),
+                ("inflight", ctypes.c_int), ("precision", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("P", ctypes.c_int)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -73,6 +86,15 @@ SIGNATURES = {
                                 _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "pswf_batch_set_points": ([_vp, ctypes.c_int, _dp, _ip, ctypes.POINTER(ctypes.c_int64), _vp, ctypes.c_int, _vp],
                               ctypes.c_int),
+    "pswf_server_opts_default": ([ctypes.POINTER(PswfServerOpts)], None),
+    "pswf_server_create": ([ctypes.POINTER(PswfServerOpts), ctypes.POINTER(_vp)], ctypes.c_int),
+    "pswf_server_route": ([_vp, _i64, _dp, ctypes.POINTER(PswfInfo)], ctypes.c_int),
+    "pswf_server_submit": ([_vp, _i64, _dp, _ip, _dp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "pswf_server_wait": ([_vp, _i64, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "pswf_server_stats": ([_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "pswf_server_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
+    "pswf_server_destroy": ([_vp], None),
 }
 
 NSTAGE = 8
@@ -362,6 +384,109 @@ class BatchPlan(Plan):
         self._stream()
         _check(lib().pswf_self_energy(self._h, out), self._h)
         return np.array(out[:]).reshape(self.B, self.K)
+
+
+class Server:
+    """Continuous-batching request server (pswf_server_*).  buckets: list of
+    (grid, b_max, n_max) with ascending grids."""
+
+    def __init__(self, K: int, pset, r_c: float, buckets, *, tol: float = 1e-5, c: float = 0.0, h_max: float = 0.0,
+                 inflight: int = 2, precision: int = 0, use_graphs: bool = True, P: int = 0, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PSWF-LR needs a CUDA device")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.K = int(K)
+        L = lib()
+        o = PswfServerOpts()
+        L.pswf_server_opts_default(ctypes.byref(o))
+        o.r_c, o.tol, o.c, o.h_max, o.K = r_c, tol, c, h_max, self.K
+        pset = [int(p) for p in pset]
+        o.npset = len(pset)
+        for i, p in enumerate(pset):
+            o.pset[i] = p
+        o.nbucket = len(buckets)
+        for i, (g, b, n) in enumerate(buckets):
+            o.grid[i], o.b_max[i], o.n_max[i] = int(g), int(b), int(n)
+        o.inflight, o.precision, o.use_graphs, o.P = inflight, precision, 1 if use_graphs else 0, P
+        h = _vp()
+        with torch.cuda.device(self.device):
+            st = L.pswf_server_create(ctypes.byref(o), ctypes.byref(h))
+        if st:
+            raise PswfError(st, f"{L.pswf_strerror(st).decode()}: server creation failed")
+        self._h = h
+
+    def route(self, n: int, box) -> tuple:
+        """(bucket index, plan info dict of that bucket)."""
+        box_a = (ctypes.c_double * 3)(*[float(b) for b in box])
+        info = PswfInfo()
+        r = lib().pswf_server_route(self._h, int(n), box_a, ctypes.byref(info))
+        if r < 0:
+            raise PswfError(r, "no bucket holds this structure")
+        return r, _info_dict(info)
+
+    def submit(self, pos: np.ndarray, q: np.ndarray, box, ps) -> int:
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        n = pos.shape[0]
+        if q.shape != (self.K, n):
+            raise ValueError("q must be [K, n]")
+        box_a = (ctypes.c_double * 3)(*[float(b) for b in box])
+        ps_a = (ctypes.c_int * self.K)(*[int(p) for p in ps])
+        t = ctypes.c_int64()
+        self._check(lib().pswf_server_submit(self._h, n, box_a, ps_a, pos.ctypes.data_as(_dp), q.ctypes.data_as(_dp),
+                                             ctypes.byref(t)))
+        self._n = getattr(self, "_n", {})
+        self._n[t.value] = n
+        return t.value
+
+    def wait(self, ticket: int, phi: bool = True, forces: bool = True):
+        """(energy [K+1], phi [K, n] or None, forces [n, 3] or None, latency ms)."""
+        n = self._n.pop(ticket)
+        e = np.empty(self.K + 1)
+        ph = np.empty((self.K, n)) if phi else None
+        f = np.empty((n, 3)) if forces else None
+        lat = ctypes.c_double()
+        dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
+        self._check(lib().pswf_server_wait(self._h, ticket, dp(e), dp(ph), dp(f), ctypes.byref(lat)))
+        return e, ph, f, lat.value
+
+    def stats(self) -> dict:
+        b, r, a = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        st = lib().pswf_server_stats(self._h, ctypes.byref(b), ctypes.byref(r), ctypes.byref(a))
+        return {"batches": b.value, "requests": r.value, "atoms": a.value, "status": st}
+
+    def _check(self, st: int):
+        if st:
+            buf = ctypes.create_string_buffer(512)
+            lib().pswf_server_last_error(self._h, buf, 512)
+            raise PswfError(st, f"{lib().pswf_strerror(st).decode()}: {buf.value.decode()}")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().pswf_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serving_buckets(K: int, h_max: float, grids=(16, 24, 32, 40, 48, 56, 64, 72), n_cap: int = 2048,
+                    density: float = 0.1, target_atoms: int = 16384):
+    """Bucket list for structures up to n_cap atoms at the given density:
+    per grid, structures per batch so that a batch holds about target_atoms
+    (at least 4), and the atom capacity for that many of the largest
+    structures the grid admits."""
+    out = []
+    for g in grids:
+        n_struct = int(min(n_cap, math.ceil(density * (g * h_max) ** 3 * 1.05)))
+        b = max(4, min(64, target_atoms // max(n_struct, 1)))
+        out.append((g, b, b * n_struct))
+    return out
 
 
 def _make_function():
