@@ -41,6 +41,7 @@ WORKLOADS = {
                  grid=384),
     "melt_quarter": dict(name="ionic_melt_1242757", N=1242757, L=350.0 * 256 / 384, ps=(1, 2, 4, 6), r_c=7.0,
                          tol=1e-5, P=7, grid=256),
+    "serving": dict(name="serving_stream_4096"),
     "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=5e-6, P=8, grid=64),
 }
 METRIC = "LR energy+force atoms/s at 1e-5 force err"
@@ -180,6 +181,117 @@ def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
     return s.n / dt, torch.get_num_threads(), f"{desc}; {reps} oracle evaluations, {dt:.2f} s each"
 
 
+def _percentiles(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99)),
+            "mean_ms": float(x.mean())}
+
+
+def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, seed: int = 0) -> dict:
+    """The serving stream (K = 8 channels, p in {1, 6} per request, 32-2048
+    atoms, density 0.1, Poisson arrivals) through the request server (FP32,
+    continuous batching, captured graphs), open loop at `rate` and as one
+    burst; and the plain path -- one FP64 single-structure plan per request,
+    created, run and read back one at a time -- on the first n_plain requests
+    of the same stream at the same arrival times.  Latency: arrival (submit)
+    to results ready."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    from paper_2606_06617_b300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    r_c, tol = 4.0, 1e-5
+    reqs = wl.serving_stream(n_req, rate=rate, seed=seed)
+    K = 8
+    h_max = 0.5 * math.pi * r_c / math.log(3.0 / tol)
+    buckets = lr.serving_buckets(K, h_max)
+    srv = lr.Server(K, (1, 6), r_c, buckets, tol=tol, inflight=2, device=dev)
+    atoms = sum(r.system.n for r in reqs)
+
+    def burst(sub):
+        t0 = time.perf_counter()
+        tk = [srv.submit(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub]
+        lat = [srv.wait(t, phi=False)[3] for t in tk]
+        return time.perf_counter() - t0, lat
+
+    burst(reqs[:512])                      # capture every context's graph
+    burst(reqs)
+    t_burst, lat_burst = burst(reqs)
+
+    # open loop: submit at the arrival times from a second thread
+    tickets = [None] * len(reqs)
+
+    def producer(t0):
+        for i, r in enumerate(reqs):
+            while time.perf_counter() - t0 < r.t_arrival:
+                pass
+            tickets[i] = srv.submit(r.system.pos, r.system.q, r.system.box, r.system.ps)
+
+    t0 = time.perf_counter() + 0.05
+    th = threading.Thread(target=producer, args=(t0,))
+    th.start()
+    lat_open = []
+    res_server = {}
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(1e-5)
+        e, phi, f, ms = srv.wait(tickets[i])
+        lat_open.append(ms)
+        if i < 16:
+            res_server[i] = f
+    t_open = time.perf_counter() - t0
+    th.join()
+    stats = srv.stats()
+    srv.close()
+
+    # plain path: one FP64 plan per request, sequential, same arrival times
+    def plain_one(r):
+        s = r.system
+        plan = lr.Plan(s.box, s.n, s.ps, r_c, tol=tol, precision=1, device=dev)
+        plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=torch.float64, device=dev))
+        e, phi, f = plan.execute()
+        out = (e.cpu().numpy(), phi.cpu().numpy(), f.cpu().numpy())
+        del plan
+        return out
+
+    sub = reqs[:n_plain]
+    for r in sub[:8]:
+        plain_one(r)                       # warm-up (allocator, library)
+    lat_plain = []
+    agree = []
+    t0 = time.perf_counter()
+    for i, r in enumerate(sub):
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        e, phi, f = plain_one(r)
+        lat_plain.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
+        if i in res_server and r.system.n > 1:
+            agree.append(float(np.sqrt(np.sum((res_server[i] - f) ** 2) / np.sum(f ** 2))))
+    t_plain_total = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for r in sub:
+        plain_one(r)
+    t_plain_burst = time.perf_counter() - t1
+    atoms_plain = sum(r.system.n for r in sub)
+    ours_burst = atoms / t_burst
+    plain_burst = atoms_plain / t_plain_burst
+    return {
+        "workload": f"serving stream: {n_req} requests, 32-2048 atoms (log-uniform), K=8, p in {{1,6}}, "
+                    f"density 0.1, Poisson {rate:.0f}/s, tol {tol:g}, r_c {r_c}",
+        "buckets": [list(b) for b in buckets],
+        "ours": {"path": "request server, FP32, continuous batching, CUDA graphs",
+                 "open_loop": {**_percentiles(lat_open), "atoms_per_s": atoms / t_open,
+                               "offered_atoms_per_s": atoms / reqs[-1].t_arrival},
+                 "burst": {**_percentiles(lat_burst), "atoms_per_s": ours_burst},
+                 "batches": stats["batches"], "requests": stats["requests"]},
+        "plain_fp64": {"path": "one FP64 plan per request, created, run and read back sequentially",
+                       "requests": n_plain,
+                       "open_loop": {**_percentiles(lat_plain), "atoms_per_s": atoms_plain / t_plain_total},
+                       "burst": {"atoms_per_s": plain_burst}},
+        "speedup_atoms_per_s_burst": ours_burst / plain_burst,
+        "force_rel_rms_ours_vs_plain": float(np.max(agree)) if agree else None,
+    }
+
+
 def run_reference(args, rank: int):
     """--impl reference: the CPU oracle as it stands, bounded sample per step."""
     import torch
@@ -226,6 +338,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="melt")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -234,6 +347,16 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            sv = run_serving()
+            o = sv["ours"]["open_loop"]
+            print(json.dumps({"metric": "serve p50 ms (open loop, 2000 req/s)", "value": o["p50_ms"], "unit": "ms",
+                              "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                              "config": {"workload": "serving_stream_4096"}, "serving": sv}), flush=True)
         return
 
     import torch
@@ -350,6 +473,13 @@ def main():
                "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 4 + sysm.n * 12),
                "ms_per_step": te * 1e3}
 
+    serving = None
+    info = dict(plan.info)
+    if rank == 0 and world == 1 and not args.no_serving and args.workload.startswith("melt"):
+        del plan, pos, q, out
+        torch.cuda.empty_cache()
+        serving = run_serving()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = cpu_oracle_sample(args.workload)
@@ -361,8 +491,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "atoms": sysm.n, "box_A": w["L"], "channels_p": list(sysm.ps),
-                       "grid": plan.info["grid"], "P": plan.info["P"], "r_c": w["r_c"], "c": plan.info["c"],
-                       "c_w": plan.info["c_w"], "tol": w["tol"],
+                       "grid": info["grid"], "P": info["P"], "r_c": w["r_c"], "c": info["c"],
+                       "c_w": info["c_w"], "tol": w["tol"],
                        "l2": "L2 flushed (256 MB write) between timed steps" if small
                              else f"inputs larger than L2: grid {grid_bytes / 1e9:.2f} GB per pass",
                        "parallelism": f"replicas x{world}"},
@@ -375,6 +505,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist:

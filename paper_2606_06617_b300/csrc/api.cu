@@ -385,8 +385,12 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
       int rc = struct_tables(h, boxes + 3 * sidx, t, err);
       if (rc) return set_err(p, rc, "structure " + std::to_string(sidx) + ": " + err);
     } else {
-      int rc = struct_tables(h, h.box_max, t, err);
-      if (rc) return set_err(p, rc, err);
+      // empty slot: valid box, zero multiplier (no W-hat tables needed)
+      for (int d = 0; d < 3; ++d) {
+        t.box[d] = h.box_max[d];
+        t.iw2[d].clear();
+      }
+      t.V = t.dV = 1.0;
     }
     for (int d = 0; d < 3; ++d) sbox[3 * sidx + d] = t.box[d];
     const double dv2v = t.dV * t.dV / t.V;

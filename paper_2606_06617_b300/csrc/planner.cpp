@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "pswf_lr.h"
 
@@ -11,45 +14,6 @@ namespace pswf {
 
 namespace {
 constexpr double kPi = 3.14159265358979323846;
-
-// Symmetric eigenproblem by cyclic Jacobi rotations (small dense matrices).
-void jacobi_eigen(std::vector<double> A, int n, std::vector<double>& evals, std::vector<double>& evecs) {
-  evecs.assign(size_t(n) * n, 0.0);
-  for (int i = 0; i < n; ++i) evecs[size_t(i) * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) off += A[size_t(i) * n + j] * A[size_t(i) * n + j];
-    if (off < 1e-30) break;
-    for (int p = 0; p < n; ++p) {
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[size_t(p) * n + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = A[size_t(p) * n + p], aqq = A[size_t(q) * n + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A[size_t(k) * n + p], akq = A[size_t(k) * n + q];
-          A[size_t(k) * n + p] = cs * akp - sn * akq;
-          A[size_t(k) * n + q] = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A[size_t(p) * n + k], aqk = A[size_t(q) * n + k];
-          A[size_t(p) * n + k] = cs * apk - sn * aqk;
-          A[size_t(q) * n + k] = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = evecs[size_t(k) * n + p], vkq = evecs[size_t(k) * n + q];
-          evecs[size_t(k) * n + p] = cs * vkp - sn * vkq;
-          evecs[size_t(k) * n + q] = sn * vkp + cs * vkq;
-        }
-      }
-    }
-  }
-  evals.resize(n);
-  for (int i = 0; i < n; ++i) evals[i] = A[size_t(i) * n + i];
-}
 
 // P_n^{(m)}(x) for n <= nmax, m <= mmax (unnormalised Legendre), via
 // (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1} and
@@ -171,24 +135,59 @@ Prolate::Prolate(double c_) : c(c_) {
   // x Pbar_n = alpha_n Pbar_{n+1} + alpha_{n-1} Pbar_{n-1}, so the matrix has
   // diagonal n(n+1) + c^2 (alpha_n^2 + alpha_{n-1}^2) and off-diagonal
   // (n, n+2) entries c^2 alpha_n alpha_{n+1}.
-  std::vector<double> A(size_t(N) * N, 0.0);
+  std::vector<double> dg(N), of(N > 1 ? N - 1 : 1, 0.0);
   for (int k = 0; k < N; ++k) {
     const int n = 2 * k;
-    A[size_t(k) * N + k] = n * (n + 1.0) + c * c * (alpha(n) * alpha(n) + alpha(n - 1) * alpha(n - 1));
-    if (k + 1 < N) {
-      const double e = c * c * alpha(n) * alpha(n + 1);
-      A[size_t(k) * N + k + 1] = e;
-      A[size_t(k + 1) * N + k] = e;
-    }
+    dg[k] = n * (n + 1.0) + c * c * (alpha(n) * alpha(n) + alpha(n - 1) * alpha(n - 1));
+    if (k + 1 < N) of[k] = c * c * alpha(n) * alpha(n + 1);
   }
-  std::vector<double> ev, V;
-  jacobi_eigen(A, N, ev, V);
-  int imin = 0;
-  for (int i = 1; i < N; ++i)
-    if (ev[i] < ev[imin]) imin = i;
-  chi = ev[imin];
-  beta.resize(N);
-  for (int k = 0; k < N; ++k) beta[k] = V[size_t(k) * N + imin];
+  // The matrix is symmetric tridiagonal: smallest eigenvalue by Sturm-count
+  // bisection, its eigenvector by inverse iteration (Thomas solves).
+  auto below = [&](double x) {   // eigenvalues < x
+    int cnt = 0;
+    double q = dg[0] - x;
+    if (q < 0) ++cnt;
+    for (int k = 1; k < N; ++k) {
+      const double qq = (q != 0.0) ? q : 1e-300;
+      q = dg[k] - x - of[k - 1] * of[k - 1] / qq;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  double lo = dg[0], hi = dg[0];
+  for (int k = 0; k < N; ++k) {
+    const double r = (k > 0 ? std::fabs(of[k - 1]) : 0.0) + (k + 1 < N ? std::fabs(of[k]) : 0.0);
+    lo = std::min(lo, dg[k] - r);
+    hi = std::max(hi, dg[k] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) >= 1)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  chi = 0.5 * (lo + hi);
+  std::vector<double> v(N, 1.0), w(N), cp(N), dp(N);
+  const double shift = chi - 1e-10 * std::max(1.0, std::fabs(chi));
+  for (int it = 0; it < 4; ++it) {
+    // solve (T - shift I) w = v
+    double den = dg[0] - shift;
+    cp[0] = (N > 1 ? of[0] : 0.0) / den;
+    dp[0] = v[0] / den;
+    for (int k = 1; k < N; ++k) {
+      den = dg[k] - shift - of[k - 1] * cp[k - 1];
+      cp[k] = (k + 1 < N ? of[k] : 0.0) / den;
+      dp[k] = (v[k] - of[k - 1] * dp[k - 1]) / den;
+    }
+    w[N - 1] = dp[N - 1];
+    for (int k = N - 2; k >= 0; --k) w[k] = dp[k] - cp[k] * w[k + 1];
+    double nrm = 0.0;
+    for (int k = 0; k < N; ++k) nrm += w[k] * w[k];
+    nrm = std::sqrt(nrm);
+    for (int k = 0; k < N; ++k) v[k] = w[k] / nrm;
+  }
+  beta = v;
   double s = 0.0;
   {
     std::vector<double> T;
@@ -196,6 +195,8 @@ Prolate::Prolate(double c_) : c(c_) {
     for (int k = 0; k < N; ++k) s += beta[k] * std::sqrt(2 * k + 0.5) * T[2 * k];
   }
   for (double& b : beta) b /= s;  // psi(0) = 1
+  bs.resize(N);
+  for (int k = 0; k < N; ++k) bs[k] = beta[k] * std::sqrt(2 * k + 0.5);
   // lambda_0 = int_{-1}^{1} psi = beta_0 int Pbar_0 = beta_0 sqrt(2)
   lambda0 = beta[0] * std::sqrt(2.0);
   C0 = 0.5 * lambda0;
@@ -203,6 +204,17 @@ Prolate::Prolate(double c_) : c(c_) {
 
 double Prolate::eval(double x, int m) const {
   const int N = int(beta.size());
+  if (m == 0) {
+    // sum_k bs_k P_{2k}(x) along the three-term recurrence (no table)
+    double p0 = 1.0, p1 = x, sum = bs[0];
+    for (int n = 1; n + 1 <= 2 * N - 2; ++n) {
+      const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+      p0 = p1;
+      p1 = p2;
+      if (((n + 1) & 1) == 0) sum += bs[(n + 1) / 2] * p1;
+    }
+    return sum;
+  }
   std::vector<double> T;
   legendre_table(x, 2 * N, m, T);
   const double* Pm = T.data() + size_t(m) * (2 * N + 1);
@@ -263,6 +275,34 @@ double mult_smooth(const Prolate& ps, int p, double u) {
 }
 
 namespace {
+
+// Chebyshev fits of the multiplier smooth part S_p on the kMultSeg pieces of
+// [0, 1]: they depend only on (c, p, precision), so plans share them.
+struct MultFit {
+  int deg = 1;
+  std::vector<std::vector<double>> cheb;   // [kMultSeg]
+};
+
+const MultFit& mult_fit(const Prolate& moll, int p, double eps_poly) {
+  static std::mutex mu;
+  static std::map<std::tuple<double, int, double>, MultFit> cache;
+  const auto key = std::make_tuple(moll.c, p, eps_poly);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  MultFit f;
+  const int nfit = 33;
+  f.cheb.resize(kMultSeg);
+  for (int i = 0; i < kMultSeg; ++i) {
+    const double a = double(i) / kMultSeg, b = double(i + 1) / kMultSeg;
+    f.cheb[i] = cheb_fit([&](double sv) { return mult_smooth(moll, p, a + (b - a) * 0.5 * (sv + 1.0)); }, nfit);
+  }
+  f.deg = family_degree(f.cheb, eps_poly);
+  std::lock_guard<std::mutex> lk(mu);
+  return cache.emplace(key, std::move(f)).first->second;
+}
 
 // Everything that depends on the grid spacing at box_max and on the set of
 // exponents, but not on a particular structure.
@@ -353,18 +393,13 @@ int plan_core(const double box_max[3], int K, const int* pset, int npset, const 
   }
   // ---- multiplier pieces, one row per exponent in use ----
   {
-    const int nfit = 33;
     std::vector<std::vector<double>> cheb(size_t(6) * kMultSeg);
     int deg = 1;
     for (int pp = 1; pp <= 6; ++pp) {
       if (!use_p[pp]) continue;
-      std::vector<std::vector<double>> fam(kMultSeg);
-      for (int i = 0; i < kMultSeg; ++i) {
-        const double a = double(i) / kMultSeg, b = double(i + 1) / kMultSeg;
-        fam[i] = cheb_fit([&](double s) { return mult_smooth(plan.moll, pp, a + (b - a) * 0.5 * (s + 1.0)); }, nfit);
-        cheb[size_t(pp - 1) * kMultSeg + i] = fam[i];
-      }
-      deg = std::max(deg, family_degree(fam, eps_poly));
+      const MultFit& f = mult_fit(plan.moll, pp, eps_poly);
+      for (int i = 0; i < kMultSeg; ++i) cheb[size_t(pp - 1) * kMultSeg + i] = f.cheb[i];
+      deg = std::max(deg, f.deg);
     }
     deg = std::min(deg, kMaxMultDeg);
     plan.deg_m = deg;

@@ -33,6 +33,7 @@ struct Prolate {
   double lambda0 = 0.0;   // eigenvalue of F_c, = int_{-1}^{1} psi
   double C0 = 0.0;        // int_0^1 psi
   std::vector<double> beta;
+  std::vector<double> bs;  // beta_k sqrt(2k + 1/2): psi = sum_k bs_k P_{2k}
 
   explicit Prolate(double c_);
   Prolate() = default;
