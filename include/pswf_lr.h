@@ -157,7 +157,9 @@ int pswf_batch_plan_create(const double box_max[3], int b_max, int64_t n_max, in
  * exponents (from the plan's pset); offsets host int64 [b + 1], offsets[0] =
  * 0, non-decreasing: structure s owns atoms offsets[s] .. offsets[s+1] - 1 of
  * pos (device [n][3], float or double) and of q (device real [K][n]), n =
- * offsets[b] <= n_max.  Slots b..b_max-1 are empty (zero energy).  The box
+ * offsets[b] <= n_max.  Slots b..b_max-1 are empty (zero energy).  Later
+ * launches cover only the smallest planned slot count >= b (1, 2, 4, ...,
+ * b_max; one cuFFT plan pair each), so a small batch costs little.  The box
  * tables are computed on the host into a pinned buffer owned by the plan and
  * copied on the plan's stream; a later call first waits for that copy. */
 int pswf_batch_set_points(pswf_plan plan, int b, const double* boxes, const int* ps, const int64_t* offsets,

@@ -170,6 +170,7 @@ struct pswf_plan_s {
   int flags = 0;
   bool batch = false;        // created by pswf_batch_plan_create
   int B = 1;                 // structures (slots)
+  int nrun = 1;              // slots processed per launch (a planned size >= the set count)
   int nts = 0;               // tiles per structure
   int nqb = kQBlocks;        // charge-sum blocks per structure
   int eblk = kEnergyBlocks;  // multiplier blocks per (structure, channel)
@@ -219,8 +220,10 @@ struct pswf_plan_s {
   cudaEvent_t stab_ev = nullptr;  // last upload from h_stab
   std::vector<int> h_pch;    // host copy of pch
   void* fft_work = nullptr;
-  // cuFFT
-  cufftHandle fwd = 0, inv = 0;
+  // cuFFT: one plan pair per planned launch size (single plans: 1; batch
+  // plans: 1, 2, 4, ... and b_max), all on one work area
+  std::vector<int> fft_sizes;
+  std::vector<cufftHandle> fwd, inv;
   bool fft_made = false;
   size_t fft_work_bytes = 0;
   // host staging for pswf_compute_host
@@ -286,6 +289,16 @@ struct StageScope {
     }
   }
 };
+
+// Grid elements of the slots processed per launch.
+int64_t run_grid_elems(pswf_plan p) { return p->grid_elems / p->B * p->nrun; }
+
+// Smallest planned launch size holding b structures.
+int run_size(pswf_plan p, int b) {
+  for (int sz : p->fft_sizes)
+    if (sz >= b) return sz;
+  return p->B;
+}
 
 // Layout of the per-structure table region (also the pinned host mirror):
 // sbox double [B][3] | scale double [B K] | zero_coef double [B K] |
@@ -439,8 +452,10 @@ int upload_tables(pswf_plan p) {
 
 int attach_fft_work(pswf_plan p) {
   if (!p->fft_made) return PSWF_OK;
-  if (cufftSetWorkArea(p->fwd, p->fft_work) != CUFFT_SUCCESS || cufftSetWorkArea(p->inv, p->fft_work) != CUFFT_SUCCESS)
-    return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
+  for (size_t i = 0; i < p->fwd.size(); ++i)
+    if (cufftSetWorkArea(p->fwd[i], p->fft_work) != CUFFT_SUCCESS ||
+        cufftSetWorkArea(p->inv[i], p->fft_work) != CUFFT_SUCCESS)
+      return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
   return PSWF_OK;
 }
 
@@ -459,11 +474,12 @@ int ensure_workspace(pswf_plan p) {
 LaunchCtx make_ctx(pswf_plan p) {
   LaunchCtx c;
   c.geo = p->geo;
+  c.geo.B = p->nrun;
   c.nmax = p->n_max;
   // batch plans: outputs hold n_max rows and every launch is made whatever
   // the count (so that a captured sequence serves any batch)
   c.n = p->batch ? p->n_max : p->n;
-  c.ntiles = p->ntiles;
+  c.ntiles = p->nrun * p->nts;
   c.sbox = p->sbox;
   c.soff = p->soff;
   c.tile_start = p->tile_start;
@@ -491,7 +507,7 @@ int multiply(pswf_plan p, int want_energy, void* data) {
   mp.Mxh = h.M[0] / 2 + 1;
   mp.deg = h.deg_m;
   mp.K = h.K;
-  dim3 grid(p->eblk, p->B * h.K);
+  dim3 grid(p->eblk, p->nrun * h.K);
   k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->sbox,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
                                                   p->Mh, p->epart, want_energy);
@@ -500,7 +516,9 @@ int multiply(pswf_plan p, int want_energy, void* data) {
 
 int fft_exec(pswf_plan p, void* data, bool forward) {
   cufftResult r;
-  cufftHandle hdl = forward ? p->fwd : p->inv;
+  size_t fi = 0;
+  while (fi + 1 < p->fft_sizes.size() && p->fft_sizes[fi] != p->nrun) ++fi;
+  cufftHandle hdl = forward ? p->fwd[fi] : p->inv[fi];
   if (cufftSetStream(hdl, p->stream) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftSetStream failed");
   if (p->real_size == 4) {
     r = forward ? cufftExecR2C(hdl, static_cast<cufftReal*>(data), static_cast<cufftComplex*>(data))
@@ -517,11 +535,11 @@ int fft_exec(pswf_plan p, void* data, bool forward) {
 template <typename R>
 int charge_sums(pswf_plan p, const void* vals, double* out) {
   const int K = p->host.K;
-  k_charge_partials_seg<R><<<dim3(p->nqb, p->B), kThreads, 0, p->stream>>>(static_cast<const R*>(vals), K, p->B,
+  k_charge_partials_seg<R><<<dim3(p->nqb, p->nrun), kThreads, 0, p->stream>>>(static_cast<const R*>(vals), K, p->nrun,
                                                                           p->soff, p->qpart);
   int rc = launch_check(p, "k_charge_partials_seg");
   if (rc) return rc;
-  k_charge_final_seg<<<(p->B * K + 63) / 64, 64, 0, p->stream>>>(p->nqb, K, p->B, p->qpart, out);
+  k_charge_final_seg<<<(p->nrun * K + 63) / 64, 64, 0, p->stream>>>(p->nqb, K, p->nrun, p->qpart, out);
   return launch_check(p, "k_charge_final_seg");
 }
 
@@ -541,25 +559,29 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
     k_set_count<<<1, 32, 0, s>>>(p->soff, int(n));
     if ((rc = launch_check(p, "k_set_count"))) return rc;
   }
-  if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(p->ntiles) * 4, s), "clear counts"))) return rc;
+  const int ntl = p->nrun * p->nts;
+  const int nsb = (ntl + p->scan_per_block - 1) / p->scan_per_block;
+  Geometry geo = p->geo;
+  geo.B = p->nrun;
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(ntl) * 4, s), "clear counts"))) return rc;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((p->n_max + kThreads - 1) / kThreads, 148 * 32)));
   if (pos_dtype == 0)
-    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), p->geo, p->sbox, p->soff, p->tile_of,
+    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), geo, p->sbox, p->soff, p->tile_of,
                                                 p->rank, p->tile_count, static_cast<R*>(p->tmp_t), p->tmp_cell,
                                                 p->n_max, p->err);
   else
-    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), p->geo, p->sbox, p->soff,
+    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), geo, p->sbox, p->soff,
                                                  p->tile_of, p->rank, p->tile_count, static_cast<R*>(p->tmp_t),
                                                  p->tmp_cell, p->n_max, p->err);
   if ((rc = launch_check(p, "k_bin"))) return rc;
-  k_scan_block_sums<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block);
+  k_scan_block_sums<<<nsb, kScanBlock, 0, s>>>(ntl, p->tile_count, p->scan_sums, p->scan_per_block);
   if ((rc = launch_check(p, "k_scan_block_sums"))) return rc;
-  k_scan_sums<<<1, 32, 0, s>>>(p->scan_blocks, p->scan_sums);
+  k_scan_sums<<<1, 32, 0, s>>>(nsb, p->scan_sums);
   if ((rc = launch_check(p, "k_scan_sums"))) return rc;
-  k_scan_apply<<<p->scan_blocks, kScanBlock, 0, s>>>(p->ntiles, p->tile_count, p->scan_sums, p->scan_per_block,
+  k_scan_apply<<<nsb, kScanBlock, 0, s>>>(ntl, p->tile_count, p->scan_sums, p->scan_per_block,
                                                       p->tile_start);
   if ((rc = launch_check(p, "k_scan_apply"))) return rc;
-  k_scatter<R><<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const R*>(q), p->geo, p->soff, p->tile_of, p->rank,
+  k_scatter<R><<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const R*>(q), geo, p->soff, p->tile_of, p->rank,
                                            p->tile_start, static_cast<const R*>(p->tmp_t), p->tmp_cell,
                                            static_cast<R*>(p->st), p->scell, static_cast<R*>(p->sq), p->sperm);
   if ((rc = launch_check(p, "k_scatter"))) return rc;
@@ -573,7 +595,8 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   const LaunchCtx ctx = make_ctx(p);
   {
     StageScope scope(p, PSWF_STAGE_SPREAD);
-    if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid"))) return rc;
+    if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * sizeof(R), s), "clear grid")))
+      return rc;
     if (p->n > 0 || p->batch) {
       int nl = 0;
       cudaError_t e = sizeof(R) == 4 ? launch_spread_float(ctx, &nl) : launch_spread_double(ctx, &nl);
@@ -588,8 +611,12 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   {
     StageScope scope(p, PSWF_STAGE_MULTIPLY);
     if ((rc = multiply<R>(p, 1, p->grid))) return rc;
-    k_energy_final<<<p->B, 256, 0, s>>>(p->host.K, p->eblk, p->epart, p->zero_coef, p->charges,
-                                        energy ? energy : p->energy_tmp);
+    k_energy_final<<<p->nrun, 256, 0, s>>>(p->host.K, p->eblk, p->epart, p->zero_coef, p->charges,
+                                           energy ? energy : p->energy_tmp);
+    if (energy && p->nrun < p->B &&
+        (rc = cuda_check(p, cudaMemsetAsync(energy + size_t(p->nrun) * (p->host.K + 1), 0,
+                                            size_t(p->B - p->nrun) * (p->host.K + 1) * 8, s), "clear energies")))
+      return rc;
     if ((rc = launch_check(p, "k_energy_final"))) return rc;
     p->launches[PSWF_STAGE_MULTIPLY] += 2;
   }
@@ -634,11 +661,11 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
   if (g_phi) {
     if ((rc = charge_sums<R>(p, g_phi, p->bsum))) return rc;
     nl += 2;
-  } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(p->B) * K * 2 * sizeof(double), s),
+  } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(p->nrun) * K * 2 * sizeof(double), s),
                               "clear bsum"))) {
     return rc;
   }
-  if ((rc = cuda_check(p, cudaMemsetAsync(p->grid2, 0, size_t(p->grid_elems) * sizeof(R), s), "clear grid2")))
+  if ((rc = cuda_check(p, cudaMemsetAsync(p->grid2, 0, size_t(run_grid_elems(p)) * sizeof(R), s), "clear grid2")))
     return rc;
   if (g_phi || g_forces) {
     e = sizeof(R) == 4 ? launch_backward_float(ctx, b, 0, &nl) : launch_backward_double(ctx, b, 0, &nl);
@@ -682,8 +709,12 @@ int plan_fill_tables(pswf_plan p, int b, const double* boxes, const int* ps, con
     if ((rc = cuda_check(p, cudaMallocHost(&p->h_stab, size_t(p->stab_bytes)), "pinned table mirror"))) return rc;
     if ((rc = cuda_check(p, cudaEventCreateWithFlags(&p->stab_ev, cudaEventDisableTiming), "table event"))) return rc;
   }
-  return fill_stab(p, b, boxes, ps, offsets, static_cast<char*>(p->h_stab));
+  if ((rc = fill_stab(p, b, boxes, ps, offsets, static_cast<char*>(p->h_stab)))) return rc;
+  p->nrun = run_size(p, b);
+  return PSWF_OK;
 }
+
+int plan_run_size(pswf_plan p) { return p->nrun; }
 
 int plan_upload_tables(pswf_plan p) {
   return cuda_check(p, cudaMemcpyAsync(p->stab, p->h_stab, size_t(p->stab_bytes), cudaMemcpyHostToDevice, p->stream),
@@ -716,22 +747,28 @@ int make_fft(pswf_plan p) {
   const int dist_c = h.M[2] * h.M[1] * Mxh;
   const cufftType tf = p->real_size == 4 ? CUFFT_R2C : CUFFT_D2Z;
   const cufftType ti = p->real_size == 4 ? CUFFT_C2R : CUFFT_Z2D;
-  if (cufftCreate(&p->fwd) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
-  if (cufftCreate(&p->inv) != CUFFT_SUCCESS) {
-    cufftDestroy(p->fwd);
-    return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
-  }
+  p->fft_sizes.clear();
+  for (int sz = 1; sz < p->B; sz *= 2) p->fft_sizes.push_back(sz);
+  p->fft_sizes.push_back(p->B);
   p->fft_made = true;
-  cufftSetAutoAllocation(p->fwd, 0);
-  cufftSetAutoAllocation(p->inv, 0);
-  size_t w1 = 0, w2 = 0;
-  const int nb = p->B * h.K;
-  const cufftResult r1 = cufftMakePlanMany(p->fwd, 3, n, embed_r, 1, dist_r, embed_c, 1, dist_c, tf, nb, &w1);
-  const cufftResult r2 = cufftMakePlanMany(p->inv, 3, n, embed_c, 1, dist_c, embed_r, 1, dist_r, ti, nb, &w2);
-  if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
-    return set_err(p, PSWF_ECUFFT,
-                   "cufftMakePlanMany failed (" + std::to_string(int(r1)) + "," + std::to_string(int(r2)) + ")");
-  p->fft_work_bytes = std::max(w1, w2);
+  p->fft_work_bytes = 0;
+  for (int sz : p->fft_sizes) {
+    cufftHandle f = 0, g = 0;
+    if (cufftCreate(&f) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
+    p->fwd.push_back(f);
+    if (cufftCreate(&g) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
+    p->inv.push_back(g);
+    cufftSetAutoAllocation(f, 0);
+    cufftSetAutoAllocation(g, 0);
+    size_t w1 = 0, w2 = 0;
+    const int nb = sz * h.K;
+    const cufftResult r1 = cufftMakePlanMany(f, 3, n, embed_r, 1, dist_r, embed_c, 1, dist_c, tf, nb, &w1);
+    const cufftResult r2 = cufftMakePlanMany(g, 3, n, embed_c, 1, dist_c, embed_r, 1, dist_r, ti, nb, &w2);
+    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
+      return set_err(p, PSWF_ECUFFT,
+                     "cufftMakePlanMany failed (" + std::to_string(int(r1)) + "," + std::to_string(int(r2)) + ")");
+    p->fft_work_bytes = std::max(p->fft_work_bytes, std::max(w1, w2));
+  }
   return PSWF_OK;
 }
 
@@ -961,6 +998,7 @@ int pswf_batch_set_points(pswf_plan pl, int b, const double* boxes, const int* p
   int rc = ensure_workspace(pl);
   if (rc) return rc;
   if ((rc = batch_tables_async(pl, b, boxes, ps, offsets))) return rc;
+  pl->nrun = run_size(pl, b);
   return pl->real_size == 4 ? do_set_points<float>(pl, n, pos, pos_dtype, q)
                             : do_set_points<double>(pl, n, pos, pos_dtype, q);
 }
@@ -1034,7 +1072,8 @@ int pswf_self_energy(pswf_plan pl, double* out) {
                                           pl->stream), "read charges");
   if (rc) return rc;
   if ((rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "sync"))) return rc;
-  for (int g = 0; g < BK; ++g) out[g] = pl->host.self_coef_p[pl->h_pch[g]] * ch[2 * g + 1];
+  const int nk = pl->nrun * pl->host.K;   // slots beyond the last launch hold no atoms
+  for (int g = 0; g < BK; ++g) out[g] = g < nk ? pl->host.self_coef_p[pl->h_pch[g]] * ch[2 * g + 1] : 0.0;
   return PSWF_OK;
 }
 
@@ -1129,10 +1168,8 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
 
 void pswf_plan_destroy(pswf_plan pl) {
   if (!pl) return;
-  if (pl->fft_made) {
-    cufftDestroy(pl->fwd);
-    cufftDestroy(pl->inv);
-  }
+  for (auto hdl : pl->fwd) cufftDestroy(hdl);
+  for (auto hdl : pl->inv) cufftDestroy(hdl);
   if (pl->ws_owned && pl->ws) cudaFree(pl->ws);
   if (pl->d_stage) cudaFree(pl->d_stage);
   if (pl->h_pin) cudaFreeHost(pl->h_pin);

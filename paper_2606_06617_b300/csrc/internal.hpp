@@ -13,6 +13,9 @@ namespace pswf {
 // 0..b-1 (allocating it on first use).  The caller guarantees that no upload
 // from the mirror is in flight.
 int plan_fill_tables(pswf_plan p, int b, const double* boxes, const int* ps, const int64_t* offsets);
+// Slots the next launch processes (a planned size >= b, set by
+// plan_fill_tables); captured sequences are per size.
+int plan_run_size(pswf_plan p);
 // Copies the mirror to the device on the plan's stream (plain async copy).
 int plan_upload_tables(pswf_plan p);
 // The kernels of set_points / execute on the plan's stream; for a batch plan

@@ -9,8 +9,9 @@
 // by memory).  A scheduler thread takes, for every free context, the
 // bucket's oldest pending requests up to the context's structure and atom
 // capacity, stages them, and launches: table and input copies, the batch
-// kernels (one captured CUDA graph per context, replayed for every batch:
-// the plan's launch shapes depend only on its capacity), output copies, and
+// kernels (a captured CUDA graph per context and launch size -- a power of
+// two >= the batch's structures -- replayed for every batch of that size:
+// the plan's launch shapes depend only on that size), output copies, and
 // a host callback that marks the context finished.  Requests that arrive
 // while batches run are admitted as soon as a context frees up; batches of
 // different contexts overlap on the device.
@@ -67,7 +68,7 @@ struct Context {
   double* h_e = nullptr;
   void* h_phi = nullptr;
   void* h_f = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per launch size
   bool busy = false;
   bool finished = false;     // set by the host callback
   std::vector<Request*> reqs;
@@ -163,7 +164,7 @@ int make_context(pswf_server srv, Bucket& b, Context& c) {
 
 void free_context(Context& c) {
   if (c.stream) cudaStreamSynchronize(c.stream);
-  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  for (auto& g : c.graphs) cudaGraphExecDestroy(g.second);
   if (c.plan) pswf_plan_destroy(c.plan);
   for (void* p : {static_cast<void*>(c.d_pos), c.d_q, static_cast<void*>(c.d_e), c.d_phi, c.d_f, c.ws})
     if (p) cudaFree(p);
@@ -212,7 +213,11 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.d_q, c.h_q, size_t(n) * K * rs, cudaMemcpyHostToDevice, c.stream), "h2d")))
     return rc;
   if (srv->opt.use_graphs) {
-    if (!c.gexec) {
+    const int nrun = pswf::plan_run_size(c.plan);
+    cudaGraphExec_t gexec = nullptr;
+    for (auto& g : c.graphs)
+      if (g.first == nrun) gexec = g.second;
+    if (!gexec) {
       cudaGraph_t g = nullptr;
       if ((rc = cuda_ok(srv, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed), "begin capture")))
         return rc;
@@ -225,11 +230,12 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
         return rc2;
       }
       if ((rc = cuda_ok(srv, ec, "end capture"))) return rc;
-      const cudaError_t ei = cudaGraphInstantiate(&c.gexec, g, 0);
+      const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
       cudaGraphDestroy(g);
       if ((rc = cuda_ok(srv, ei, "graph instantiate"))) return rc;
+      c.graphs.emplace_back(nrun, gexec);
     }
-    if ((rc = cuda_ok(srv, cudaGraphLaunch(c.gexec, c.stream), "graph launch"))) return rc;
+    if ((rc = cuda_ok(srv, cudaGraphLaunch(gexec, c.stream), "graph launch"))) return rc;
   } else {
     if ((rc = pswf::plan_run_set_points(c.plan, n, c.d_pos, 1, c.d_q))) return rc;
     if ((rc = pswf::plan_run_execute(c.plan, c.d_e, c.d_phi, c.d_f))) return rc;
