@@ -5,11 +5,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.hpp"
@@ -157,6 +160,93 @@ constexpr int kQBlocks = 148;        // charge-sum blocks of a single-structure 
 constexpr int kQBlocksBatch = 8;     // per structure in a batch plan
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
+
+// Host worker threads for the copies and conversions of the end-to-end path:
+// created once, woken per parallel_for (up to 15 workers plus the caller).
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  int size() const { return int(workers_.size()) + 1; }
+  // Runs f(t) for t in [0, nt) on nt threads (the caller runs t = 0).
+  void run(int nt, const std::function<void(int)>& f) {
+    std::lock_guard<std::mutex> one_job(run_mu_);   // callers from several threads take turns
+    nt = std::min(nt, size());
+    if (nt <= 1) {
+      f(0);
+      return;
+    }
+    {
+      std::unique_lock<std::mutex> lk(mu_);
+      job_ = &f;
+      njobs_ = nt;
+      next_ = 1;
+      pending_ = nt - 1;
+      ++gen_;
+    }
+    cv_.notify_all();
+    f(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  HostPool() {
+    const int hw = int(std::max<unsigned>(1, std::thread::hardware_concurrency()));
+    const int nw = std::min(15, hw - 1);
+    for (int i = 0; i < nw; ++i) workers_.emplace_back([this] { loop(); });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : workers_) t.join();
+  }
+  void loop() {
+    int64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return stop_ || (gen_ != seen && next_ < njobs_); });
+      if (stop_) return;
+      const int t = next_++;
+      if (next_ >= njobs_) seen = gen_;
+      const std::function<void(int)>* f = job_;
+      lk.unlock();
+      (*f)(t);
+      lk.lock();
+      if (--pending_ == 0) done_.notify_all();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* job_ = nullptr;
+  int njobs_ = 0, next_ = 0, pending_ = 0;
+  int64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+// Splits [0, n) into contiguous shares over the host pool; small ranges run
+// inline.
+template <typename F>
+void parallel_for(int64_t n, F f) {
+  HostPool& pool = HostPool::get();
+  const int nt = int(std::min<int64_t>(pool.size(), std::max<int64_t>(1, n / 16384)));
+  if (nt <= 1) {
+    f(0, n);
+    return;
+  }
+  const int64_t per = (n + nt - 1) / nt;
+  pool.run(nt, [&](int t) {
+    const int64_t lo = t * per, hi = std::min(n, lo + per);
+    if (lo < hi) f(lo, hi);
+  });
+}
 
 }  // namespace
 
@@ -1110,7 +1200,9 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
     if ((rc = cuda_check(pl, cudaMalloc(&pl->d_stage, size_t(need)), "staging cudaMalloc"))) return rc;
     pl->d_stage_bytes = need;
   }
-  const int64_t hneed = std::max<int64_t>(n * 3 + K * n + K + 1 + K * n + n * 3, 1);
+  // pinned host staging (bytes): pos double [n][3] | q real [K][n] | energy | phi real [K][n] | forces real [n][3]
+  const int64_t hneed_b = std::max<int64_t>(n * 24 + K * n * rs + (K + 1) * 8 + K * n * rs + n * 3 * rs, 8);
+  const int64_t hneed = (hneed_b + 7) / 8;
   if (hneed > pl->h_pin_elems) {
     if (pl->h_pin) cudaFreeHost(pl->h_pin);
     pl->h_pin = nullptr;
@@ -1121,48 +1213,86 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   char* d = static_cast<char*>(pl->d_stage);
   double* d_pos = reinterpret_cast<double*>(d);
   d += align256(n * 3 * 8);
-  void* d_q = d;
+  char* d_q = d;
   d += align256(K * n * rs);
   double* d_e = reinterpret_cast<double*>(d);
   d += align256((K + 1) * 8);
-  void* d_phi = d;
+  char* d_phi = d;
   d += align256(K * n * rs);
-  void* d_f = d;
-  double* h_pos = pl->h_pin;
-  double* h_q = h_pos + n * 3;
-  double* h_e = h_q + K * n;
-  double* h_phi = h_e + K + 1;
-  double* h_f = h_phi + K * n;
-  if (n > 0) std::memcpy(h_pos, pos, size_t(n) * 24);
-  if (rs == 4) {
-    float* hq = reinterpret_cast<float*>(h_q);
-    for (int64_t i = 0; i < K * n; ++i) hq[i] = float(q[i]);
-  } else if (n > 0) {
-    std::memcpy(h_q, q, size_t(K * n) * 8);
-  }
+  char* d_f = d;
+  char* hb = reinterpret_cast<char*>(pl->h_pin);
+  double* h_pos = reinterpret_cast<double*>(hb);
+  char* h_q = hb + n * 24;
+  double* h_e = reinterpret_cast<double*>(h_q + K * n * rs);
+  char* h_phi = reinterpret_cast<char*>(h_e + K + 1);
+  char* h_f = h_phi + K * n * rs;
   cudaStream_t s = pl->stream;
-  if ((rc = cuda_check(pl, cudaMemcpyAsync(d_pos, h_pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos"))) return rc;
-  if ((rc = cuda_check(pl, cudaMemcpyAsync(d_q, h_q, size_t(K * n) * rs, cudaMemcpyHostToDevice, s), "h2d q"))) return rc;
+  // Inputs in chunks of atoms: the host threads fill chunk i of the pinned
+  // staging (q rounded to the plan's precision) while chunk i - 1 is copied.
+  const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(8, n / 65536));
+  const int64_t csz = (n + nchunk - 1) / nchunk;
+  for (int64_t ci = 0; ci < nchunk && n > 0; ++ci) {
+    const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
+    if (a0 >= a1) break;
+    parallel_for(a1 - a0, [&](int64_t lo, int64_t hi) {
+      std::memcpy(h_pos + 3 * (a0 + lo), pos + 3 * (a0 + lo), size_t(hi - lo) * 24);
+      for (int k = 0; k < K; ++k) {
+        const double* src = q + size_t(k) * n + a0;
+        if (rs == 4) {
+          float* dst = reinterpret_cast<float*>(h_q) + size_t(k) * n + a0;
+          for (int64_t i = lo; i < hi; ++i) dst[i] = float(src[i]);
+        } else {
+          std::memcpy(reinterpret_cast<double*>(h_q) + size_t(k) * n + a0 + lo, src + lo, size_t(hi - lo) * 8);
+        }
+      }
+    });
+    if ((rc = cuda_check(pl, cudaMemcpyAsync(d_pos + 3 * a0, h_pos + 3 * a0, size_t(a1 - a0) * 24,
+                                             cudaMemcpyHostToDevice, s), "h2d pos")))
+      return rc;
+    if ((rc = cuda_check(pl, cudaMemcpy2DAsync(d_q + a0 * rs, size_t(n * rs), h_q + a0 * rs, size_t(n * rs),
+                                               size_t((a1 - a0) * rs), size_t(K), cudaMemcpyHostToDevice, s),
+                         "h2d q")))
+      return rc;
+  }
   if ((rc = pswf_set_points(pl, n, d_pos, 1, d_q))) return rc;
   if ((rc = pswf_execute(pl, d_e, phi ? d_phi : nullptr, forces ? d_f : nullptr))) return rc;
-  if ((rc = cuda_check(pl, cudaMemcpyAsync(h_e, d_e, size_t(K + 1) * 8, cudaMemcpyDeviceToHost, s), "d2h energy"))) return rc;
-  if (phi && (rc = cuda_check(pl, cudaMemcpyAsync(h_phi, d_phi, size_t(K * n) * rs, cudaMemcpyDeviceToHost, s), "d2h phi")))
+  if ((rc = cuda_check(pl, cudaMemcpyAsync(h_e, d_e, size_t(K + 1) * 8, cudaMemcpyDeviceToHost, s), "d2h energy")))
     return rc;
-  if (forces && (rc = cuda_check(pl, cudaMemcpyAsync(h_f, d_f, size_t(n) * 3 * rs, cudaMemcpyDeviceToHost, s), "d2h forces")))
-    return rc;
+  // Outputs in chunks: copy chunk i down, then the host threads widen it
+  // into the caller's arrays while chunk i + 1 is in flight.
+  std::vector<cudaEvent_t> evs;
+  for (int64_t ci = 0; ci < nchunk && n > 0; ++ci) {
+    const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
+    if (a0 >= a1) break;
+    if (phi && (rc = cuda_check(pl, cudaMemcpy2DAsync(h_phi + a0 * rs, size_t(n * rs), d_phi + a0 * rs, size_t(n * rs),
+                                                      size_t((a1 - a0) * rs), size_t(K), cudaMemcpyDeviceToHost, s),
+                                "d2h phi")))
+      return rc;
+    if (forces && (rc = cuda_check(pl, cudaMemcpyAsync(h_f + 3 * a0 * rs, d_f + 3 * a0 * rs, size_t(a1 - a0) * 3 * rs,
+                                                       cudaMemcpyDeviceToHost, s), "d2h forces")))
+      return rc;
+    cudaEvent_t ev = take_event(pl);
+    if ((rc = cuda_check(pl, cudaEventRecord(ev, s), "record chunk"))) return rc;
+    evs.push_back(ev);
+  }
+  for (int64_t ci = 0; ci < int64_t(evs.size()); ++ci) {
+    const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
+    if ((rc = cuda_check(pl, cudaEventSynchronize(evs[ci]), "wait for chunk"))) break;
+    parallel_for(a1 - a0, [&](int64_t lo, int64_t hi) {
+      if (phi)
+        for (int k = 0; k < K; ++k)
+          for (int64_t i = a0 + lo; i < a0 + hi; ++i)
+            phi[size_t(k) * n + i] = rs == 4 ? double(reinterpret_cast<const float*>(h_phi)[size_t(k) * n + i])
+                                             : reinterpret_cast<const double*>(h_phi)[size_t(k) * n + i];
+      if (forces)
+        for (int64_t i = 3 * (a0 + lo); i < 3 * (a0 + hi); ++i)
+          forces[i] = rs == 4 ? double(reinterpret_cast<const float*>(h_f)[i]) : reinterpret_cast<const double*>(h_f)[i];
+    });
+  }
+  for (auto e : evs) pl->pool.push_back(e);
+  if (rc) return rc;
   if ((rc = pswf_sync(pl))) return rc;
   std::memcpy(energy, h_e, size_t(K + 1) * 8);
-  if (rs == 4) {
-    const float* fp = reinterpret_cast<const float*>(h_phi);
-    const float* ff = reinterpret_cast<const float*>(h_f);
-    if (phi)
-      for (int64_t i = 0; i < K * n; ++i) phi[i] = fp[i];
-    if (forces)
-      for (int64_t i = 0; i < 3 * n; ++i) forces[i] = ff[i];
-  } else {
-    if (phi && n > 0) std::memcpy(phi, h_phi, size_t(K * n) * 8);
-    if (forces && n > 0) std::memcpy(forces, h_f, size_t(n) * 24);
-  }
   return PSWF_OK;
 }
 

@@ -282,14 +282,22 @@ class Plan:
         _check(lib().pswf_profile_read(self._h, ms, nl), self._h)
         return dict(zip(STAGES, ms[:])), dict(zip(STAGES, nl[:]))
 
-    def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True):
-        """End-to-end from host arrays (float64); returns numpy (energy, phi, forces)."""
+    def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True, out=None):
+        """End-to-end from host arrays (float64); returns numpy (energy, phi,
+        forces).  out = (energy [K+1], phi [K, n] or None, forces [n, 3] or
+        None) float64 C-contiguous arrays to fill instead of new ones."""
         pos = np.ascontiguousarray(pos, dtype=np.float64)
         q = np.ascontiguousarray(q, dtype=np.float64)
         n = pos.shape[0]
-        e = np.empty(self.K + 1)
-        ph = np.empty((self.K, n)) if phi else None
-        f = np.empty((n, 3)) if forces else None
+        if out is not None:
+            e, ph, f = out
+            for a, shape in ((e, (self.K + 1,)), (ph, (self.K, n)), (f, (n, 3))):
+                if a is not None and (a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous):
+                    raise ValueError("out arrays must be float64, C-contiguous, of shapes [K+1], [K, n], [n, 3]")
+        else:
+            e = np.empty(self.K + 1)
+            ph = np.empty((self.K, n)) if phi else None
+            f = np.empty((n, 3)) if forces else None
         dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
         self._stream()
         _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)

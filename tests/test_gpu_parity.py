@@ -136,6 +136,25 @@ def test_compute_host_matches_device_path():
     assert rel_rms(phi, g["phi"]) < 1e-6 and rel_rms(f, g["F"]) < 1e-6
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_compute_host_chunked_matches_device_path(precision):
+    """300,000 atoms: the host path splits copies and conversions into chunks
+    over several threads; results equal the device path on the same plan up
+    to the order of the flush's global atomics (float sums, ~1e-8)."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.random_system(300000, (60.0, 62.0, 64.0), (1, 6, 4), seed=13, neutral=True)
+    plan = lr.Plan(s.box, s.n, s.ps, 6.0, P=6, grid=(64, 64, 64), precision=precision, device=dev)
+    plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=plan.dtype, device=dev))
+    e0, phi0, f0 = plan.execute()
+    plan.sync()
+    e, phi, f = plan.compute_host(s.pos, s.q)
+    np.testing.assert_allclose(e, e0.cpu().numpy(), rtol=1e-6)
+    assert rel_rms(phi, phi0.cpu().double().numpy()) < 1e-6
+    assert rel_rms(f, f0.cpu().double().numpy()) < 1e-6
+
+
 def test_self_energy_matches_oracle():
     """E_self from the device FP64 reduction of the (FP32-stored) charges."""
     s = wl.water_box(n_side=5, L=15.5, seed=2)
