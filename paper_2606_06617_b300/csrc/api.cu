@@ -315,6 +315,14 @@ struct pswf_plan_s {
   std::vector<int> fft_sizes;
   std::vector<cufftHandle> fwd, inv;
   bool fft_made = false;
+  // Pruned transform of single-structure plans: only the nkx lowest x
+  // frequencies can be inside the band |k| < k_c, so the 3-D transform is a
+  // 1-D real transform along x over all rows plus 2-D (z, y) transforms of
+  // those nkx columns only (per channel).
+  bool pruned = false;
+  int nkx = 0;
+  cufftHandle pr_r2c = 0, pr_c2r = 0, pr_2d = 0;
+  void* spec = nullptr;      // complex [K][Mxh][Mz][My] (pruned plans)
   size_t fft_work_bytes = 0;
   // host staging for pswf_compute_host
   double* h_pin = nullptr;
@@ -420,6 +428,7 @@ int64_t layout(pswf_plan p, char* base) {
   };
   p->grid = take(p->grid_elems * rs);
   p->grid2 = (p->flags & PSWF_FLAG_BACKWARD) ? take(p->grid_elems * rs) : nullptr;
+  p->spec = p->pruned ? take(int64_t(h.K) * (h.M[0] / 2 + 1) * h.M[1] * h.M[2] * 2 * rs) : nullptr;
   const int64_t nm = std::max<int64_t>(p->n_max, 1);
   p->tmp_t = take(3 * nm * rs);
   p->tmp_cell = reinterpret_cast<uint64_t*>(take(nm * 8));
@@ -542,6 +551,10 @@ int upload_tables(pswf_plan p) {
 
 int attach_fft_work(pswf_plan p) {
   if (!p->fft_made) return PSWF_OK;
+  if (p->pruned && (cufftSetWorkArea(p->pr_r2c, p->fft_work) != CUFFT_SUCCESS ||
+                    cufftSetWorkArea(p->pr_c2r, p->fft_work) != CUFFT_SUCCESS ||
+                    cufftSetWorkArea(p->pr_2d, p->fft_work) != CUFFT_SUCCESS))
+    return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
   for (size_t i = 0; i < p->fwd.size(); ++i)
     if (cufftSetWorkArea(p->fwd[i], p->fft_work) != CUFFT_SUCCESS ||
         cufftSetWorkArea(p->inv[i], p->fft_work) != CUFFT_SUCCESS)
@@ -598,13 +611,68 @@ int multiply(pswf_plan p, int want_energy, void* data) {
   mp.deg = h.deg_m;
   mp.K = h.K;
   dim3 grid(p->eblk, p->nrun * h.K);
+  if (p->pruned) {
+    (void)data;   // the pruned spectrum lives in p->spec
+    k_multiply_planes<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->spec), mp, p->nkx, p->pch, p->scale,
+                                                           p->sbox, static_cast<const R*>(p->coef_m),
+                                                           static_cast<const R*>(p->iw2), p->Mh, p->epart,
+                                                           want_energy);
+    return launch_check(p, "k_multiply_planes");
+  }
   k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->sbox,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
                                                   p->Mh, p->epart, want_energy);
   return launch_check(p, "k_multiply");
 }
 
+// Pruned 3-D transform of a single structure (per channel): forward = 1-D
+// R2C along x writing the spectrum in [kx][z][y] order, zero the planes
+// kx >= nkx, 2-D (z, y) transforms of the nkx planes that can hold band
+// modes; inverse = the 2-D transforms, then 1-D C2R along x back to the grid.
+int fft_exec_pruned(pswf_plan p, void* data, bool forward) {
+  const Plan& h = p->host;
+  const int Mxh = h.M[0] / 2 + 1;
+  const int64_t plane = int64_t(h.M[2]) * h.M[1];
+  const int64_t spec_ch = int64_t(Mxh) * plane;                 // complex per channel
+  const int64_t grid_ch = plane * 2 * Mxh;                       // real per channel
+  for (cufftHandle hd : {p->pr_r2c, p->pr_c2r, p->pr_2d})
+    if (cufftSetStream(hd, p->stream) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftSetStream failed");
+  cufftResult r = CUFFT_SUCCESS;
+  const bool f32 = p->real_size == 4;
+  auto cplx = [&](int c) -> void* {
+    return static_cast<char*>(p->spec) + size_t(c) * spec_ch * 2 * p->real_size;
+  };
+  auto real = [&](int c) -> void* { return static_cast<char*>(data) + size_t(c) * grid_ch * p->real_size; };
+  auto planes = [&](int c) {
+    const int dir = forward ? CUFFT_FORWARD : CUFFT_INVERSE;
+    if (f32) return cufftExecC2C(p->pr_2d, static_cast<cufftComplex*>(cplx(c)), static_cast<cufftComplex*>(cplx(c)), dir);
+    return cufftExecZ2Z(p->pr_2d, static_cast<cufftDoubleComplex*>(cplx(c)), static_cast<cufftDoubleComplex*>(cplx(c)),
+                        dir);
+  };
+  if (forward) {
+    for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c)
+      r = f32 ? cufftExecR2C(p->pr_r2c, static_cast<cufftReal*>(real(c)), static_cast<cufftComplex*>(cplx(c)))
+              : cufftExecD2Z(p->pr_r2c, static_cast<cufftDoubleReal*>(real(c)), static_cast<cufftDoubleComplex*>(cplx(c)));
+    if (r == CUFFT_SUCCESS && p->nkx < Mxh) {
+      const size_t cs = 2 * p->real_size;
+      int rc = cuda_check(p, cudaMemset2DAsync(static_cast<char*>(p->spec) + size_t(p->nkx) * plane * cs,
+                                               size_t(spec_ch) * cs, 0, size_t(Mxh - p->nkx) * plane * cs, size_t(h.K),
+                                               p->stream), "clear pruned planes");
+      if (rc) return rc;
+    }
+    for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
+  } else {
+    for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
+    for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c)
+      r = f32 ? cufftExecC2R(p->pr_c2r, static_cast<cufftComplex*>(cplx(c)), static_cast<cufftReal*>(real(c)))
+              : cufftExecZ2D(p->pr_c2r, static_cast<cufftDoubleComplex*>(cplx(c)), static_cast<cufftDoubleReal*>(real(c)));
+  }
+  if (r != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftExec failed (" + std::to_string(int(r)) + ")");
+  return PSWF_OK;
+}
+
 int fft_exec(pswf_plan p, void* data, bool forward) {
+  if (p->pruned) return fft_exec_pruned(p, data, forward);
   cufftResult r;
   size_t fi = 0;
   while (fi + 1 < p->fft_sizes.size() && p->fft_sizes[fi] != p->nrun) ++fi;
@@ -837,11 +905,37 @@ int make_fft(pswf_plan p) {
   const int dist_c = h.M[2] * h.M[1] * Mxh;
   const cufftType tf = p->real_size == 4 ? CUFFT_R2C : CUFFT_D2Z;
   const cufftType ti = p->real_size == 4 ? CUFFT_C2R : CUFFT_Z2D;
+  p->fft_made = true;
+  p->fft_work_bytes = 0;
+  if (p->B == 1) {
+    const double kmax_idx = h.k_c * h.box[0] / (2.0 * 3.14159265358979323846);
+    p->nkx = int(std::min<double>(Mxh, std::floor(kmax_idx) + 2));
+    p->pruned = p->nkx * 4 <= Mxh * 3 && h.M[0] >= 64;
+  }
+  if (p->pruned) {
+    const cufftType c2c = p->real_size == 4 ? CUFFT_C2C : CUFFT_Z2Z;
+    const int plane = h.M[2] * h.M[1];
+    int n1[1] = {h.M[0]};
+    int er[1] = {2 * Mxh}, ec[1] = {Mxh};
+    int n2[2] = {h.M[2], h.M[1]};
+    size_t w1 = 0, w2 = 0, w3 = 0;
+    for (cufftHandle* hd : {&p->pr_r2c, &p->pr_c2r, &p->pr_2d}) {
+      if (cufftCreate(hd) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
+      cufftSetAutoAllocation(*hd, 0);
+    }
+    // rows (z, y) of the grid -> spectrum element (kx, z, y) at kx * plane + (z My + y)
+    const cufftResult r1 = cufftMakePlanMany(p->pr_r2c, 1, n1, er, 1, 2 * Mxh, ec, plane, 1, tf, plane, &w1);
+    const cufftResult r2 = cufftMakePlanMany(p->pr_c2r, 1, n1, ec, plane, 1, er, 1, 2 * Mxh, ti, plane, &w2);
+    const cufftResult r3 = cufftMakePlanMany(p->pr_2d, 2, n2, n2, 1, plane, n2, 1, plane, c2c, p->nkx, &w3);
+    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS || r3 != CUFFT_SUCCESS)
+      return set_err(p, PSWF_ECUFFT, "cufftMakePlanMany (pruned) failed");
+    p->fft_work_bytes = std::max(w1, std::max(w2, w3));
+    p->fft_sizes.assign(1, 1);
+    return PSWF_OK;
+  }
   p->fft_sizes.clear();
   for (int sz = 1; sz < p->B; sz *= 2) p->fft_sizes.push_back(sz);
   p->fft_sizes.push_back(p->B);
-  p->fft_made = true;
-  p->fft_work_bytes = 0;
   for (int sz : p->fft_sizes) {
     cufftHandle f = 0, g = 0;
     if (cufftCreate(&f) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
@@ -1300,6 +1394,8 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (!pl) return;
   for (auto hdl : pl->fwd) cufftDestroy(hdl);
   for (auto hdl : pl->inv) cufftDestroy(hdl);
+  for (cufftHandle hdl : {pl->pr_r2c, pl->pr_c2r, pl->pr_2d})
+    if (hdl) cufftDestroy(hdl);
   if (pl->ws_owned && pl->ws) cudaFree(pl->ws);
   if (pl->d_stage) cudaFree(pl->d_stage);
   if (pl->h_pin) cudaFreeHost(pl->h_pin);

@@ -366,6 +366,91 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   }
 }
 
+// Multiplier on the pruned spectrum of a single structure: layout
+// [c][kx][z][y] (kx = 0 .. Mxh-1 allocated; only kx < nkx can be inside the
+// band).  One (kx, z) line of y per block iteration; the same G, energy
+// weights (kx = 0 counted once) and zeroing as k_multiply.
+template <typename R>
+__global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ data, MultParams mp, int nkx,
+                                                         const int* __restrict__ pch,
+                                                         const double* __restrict__ scale,
+                                                         const double* __restrict__ sbox, const R* __restrict__ coef,
+                                                         const R* __restrict__ iw2, int iw2_stride,
+                                                         double* __restrict__ part, int want_energy) {
+  const int c = blockIdx.y;
+  const int p = pch[c];
+  const R sc = R(scale[c]);
+  const int64_t plane = int64_t(mp.M[1]) * mp.M[2];
+  Cplx<R>* d = data + int64_t(c) * mp.Mxh * plane;
+  const R* cf = coef + size_t(p - 1) * kMultSeg * (mp.deg + 1);
+  const R* iw2x = iw2;
+  const R* iw2y = iw2x + iw2_stride;
+  const R* iw2z = iw2y + iw2_stride;
+  const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
+  const R inv_kc = R(mp.inv_kc);
+  constexpr double kTwoPi = 6.283185307179586476925;
+  const R kf0 = R(kTwoPi / sbox[0]), kf1 = R(kTwoPi / sbox[1]), kf2 = R(kTwoPi / sbox[2]);
+  double e = 0.0;
+  const int nline = nkx * mp.M[2];
+  for (int line = blockIdx.x; line < nline; line += gridDim.x) {
+    const int ix = line / mp.M[2], iz = line - ix * mp.M[2];
+    const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
+    const R kx = kf0 * R(ix), kz = kf2 * R(mz);
+    const R kxz2 = kx * kx + kz * kz;
+    Cplx<R>* dl = d + (int64_t(ix) * mp.M[2] + iz) * mp.M[1];
+    if (!(kxz2 < kc2)) {
+      for (int iy = threadIdx.x; iy < mp.M[1]; iy += blockDim.x) dl[iy] = Cplx<R>{R(0), R(0)};
+      continue;
+    }
+    const int az = mz < 0 ? -mz : mz;
+    const R wxz = sc * iw2x[ix] * iw2z[az];
+    const R wedge = ix == 0 ? R(0.5) : R(1);
+    for (int iy = threadIdx.x; iy < mp.M[1]; iy += blockDim.x) {
+      const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
+      const R ky = kf1 * R(my);
+      const R k2 = kxz2 + ky * ky;
+      if (!(k2 < kc2) || k2 == R(0)) {
+        dl[iy] = Cplx<R>{R(0), R(0)};
+        continue;
+      }
+      const R k = sqrt(k2);
+      R u = k * inv_kc;
+      if (u >= R(1)) u = R(1) - R(1e-7);
+      int seg = int(u * R(kMultSeg));
+      if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+      const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+      const R* cs = cf + seg * (mp.deg + 1);
+      R S = cs[mp.deg];
+      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
+      R phi;
+      switch (p) {
+        case 1: phi = S / k2; break;
+        case 2: phi = S / k; break;
+        case 3: phi = S - log(u); break;
+        case 5: phi = S - u * u * log(u); break;
+        default: phi = S; break;
+      }
+      const int ay = my < 0 ? -my : my;
+      const R G = phi * wxz * iw2y[ay];
+      Cplx<R> v = dl[iy];
+      if (want_energy) e += double(wedge * G * (v.x * v.x + v.y * v.y));
+      v.x *= G;
+      v.y *= G;
+      dl[iy] = v;
+    }
+  }
+  if (!want_energy) return;
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+    part[size_t(c) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // ---- interpolation, direct from global memory (fallback kernel) ---------------------
 // One thread per sorted atom, for plans whose padded regions do not fit in
 // shared memory.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W, with
