@@ -71,9 +71,11 @@ template <typename R, int P>
 constexpr size_t stencil_smem_bytes(int kc, int kb, int rows, size_t acc_size) {
   return align16(size_t(kc) * TilePad<P>::N * acc_size) + size_t(kb) * (rows * kRowW<P> * sizeof(R) + 2 * sizeof(int));
 }
+// The gather's batch also holds each atom's charges of the staged channels
+// (8 entries: the most slots a warp has).
 template <typename R, int P>
 constexpr size_t gather_smem_bytes(int kc, int kb) {
-  return stencil_smem_bytes<R, P>(kc, kb, 6, sizeof(R));
+  return stencil_smem_bytes<R, P>(kc, kb, 6, sizeof(R)) + size_t(kb) * 8 * sizeof(R);
 }
 
 // P consecutive reals from 16-byte-aligned shared memory, as vector loads.
@@ -304,19 +306,32 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
     }
     __syncthreads();
     {
-      const int gx = lane < S ? wrap_index(ox + lane, g.M[0]) : 0;
+      // two rows per warp iteration (half-warps), each lane adds an x pair;
+      // FP32 pairs that do not straddle the periodic wrap go as one 8-byte
+      // atomic (grid rows start at even offsets, tile origins are even)
+      const int half = lane >> 4, x0 = 2 * (lane & 15);
+      const bool has0 = x0 < S, has1 = x0 + 1 < S;
+      const int gx0 = has0 ? wrap_index(ox + x0, g.M[0]) : 0;
+      const int gx1 = has1 ? wrap_index(ox + x0 + 1, g.M[0]) : 0;
+      const bool pair = has1 && gx1 == gx0 + 1 && (gx0 & 1) == 0;
       for (int pl = warp; pl < nk * S; pl += nwarp) {
         const int c = pl / S, lz = pl - c * S;
         const R inv = kFixed ? R(1) / R(sscale[c]) : R(1);
-        R* dst = grid + (gc0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane + gx;
-        const A* src = region + c * N + lz * R2 + lane;
-        if (lane < S) {
-          int gy = oy;
-          for (int ly = 0; ly < S; ++ly, ++gy) {
-            if (gy == g.M[1]) gy = 0;
-            const A v = src[ly * R1];
-            if (v != A(0)) atomicAdd(dst + int64_t(gy) * g.Mxp, R(v) * inv);
+        R* base = grid + (gc0 + c) * chan + wrap_index(oz + lz, g.M[2]) * plane;
+        const A* src = region + c * N + lz * R2;
+        if (!has0) continue;
+        for (int ly = half; ly < S; ly += 2) {
+          R* row = base + int64_t(wrap_index(oy + ly, g.M[1])) * g.Mxp;
+          const A v0 = src[ly * R1 + x0];
+          const A v1 = has1 ? src[ly * R1 + x0 + 1] : A(0);
+          if constexpr (kFixed) {
+            if (pair) {
+              atomicAdd(reinterpret_cast<float2*>(row + gx0), make_float2(float(v0) * inv, float(v1) * inv));
+              continue;
+            }
           }
+          atomicAdd(row + gx0, R(v0) * inv);
+          if (has1) atomicAdd(row + gx1, R(v1) * inv);
         }
       }
     }
@@ -387,7 +402,8 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
   constexpr int GQ = G / 4;   // lanes per reduced sum after the butterfly
   R* region = reinterpret_cast<R*>(smraw);   // [kc][N]
   R* wts = reinterpret_cast<R*>(smraw + align16(size_t(kc) * N * sizeof(R)));   // [kb][6][PW]
-  int* loc = reinterpret_cast<int*>(wts + kb * 6 * PW);
+  R* qs = wts + kb * 6 * PW;                                                     // [kb][8]
+  int* loc = reinterpret_cast<int*>(qs + kb * 8);
   int* perm = loc + kb;
   const Slots sl = Slots::template make<G, NS>(kc);
   const int lane = sl.lane, warp = sl.warp, nwarp = sl.nwarp, j = sl.j, cc = sl.cc;
@@ -424,10 +440,16 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
       }
     }
     const bool use_slot = sl.used && cc < nk;
+    // zero-frequency shift 2 a_c Q_c of the lane's channel
+    const R zshift = use_slot ? R(2.0 * zero_coef[gc0 + cc] * charges[2 * (gc0 + cc)]) : R(0);
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       if (b0 != a0) __syncthreads();   // previous batch done with the tables
       batch_tables<R, P, 6>(g, sbox + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
+      for (int t = threadIdx.x; t < nb * nk; t += blockDim.x) {
+        const int a = t / nk, c = t - a * nk;
+        qs[a * 8 + c] = sq[int64_t(c0 + c) * nmax + b0 + a];
+      }
       if (b0 == a0) cp_async_wait_all();
       __syncthreads();
       for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
@@ -458,7 +480,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
           Az += sx * dz[k];
           B += dsx * wz[k];
         }
-        const R q = valid ? sq[int64_t(c0 + cc) * nmax + b0 + al] : R(0);
+        const R q = valid ? qs[al * 8 + cc] : R(0);
         // butterfly over the slot: (phi, q f_x, q f_y, q f_z) -> one sum per lane group
         R v;
         {
@@ -480,7 +502,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
         if (valid && j % GQ == 0) {
           const int o = perm[al];
           if (vi == 0) {
-            if (phi) phi[int64_t(c0 + cc) * n + o] = v + R(2.0 * zero_coef[gc0 + cc] * charges[2 * (gc0 + cc)]);
+            if (phi) phi[int64_t(c0 + cc) * n + o] = v + zshift;
           } else if (forces && cc == 0) {
             R* fo = forces + 3 * int64_t(o) + (vi - 1);
             if (nchunk == 1)
