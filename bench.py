@@ -42,6 +42,7 @@ WORKLOADS = {
     "melt_quarter": dict(name="ionic_melt_1242757", N=1242757, L=350.0 * 256 / 384, ps=(1, 2, 4, 6), r_c=7.0,
                          tol=1e-5, P=7, grid=256),
     "serving": dict(name="serving_stream_4096"),
+    "training": dict(name="training_batch_64x16"),
     "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=5e-6, P=8, grid=64),
 }
 METRIC = "LR energy+force atoms/s at 1e-5 force err"
@@ -292,6 +293,53 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, see
     }
 
 
+def run_training(steps: int = 20, warmup: int = 5, seed: int = 0) -> dict:
+    """Training-step shape: 64 structures of 200-600 atoms (cubic boxes at 0.1
+    atoms/A^3), 16 channels with p alternating 1, 6, one batch plan (grid 40^3,
+    r_c 4, tol 1e-5) with the backward: each step is set_points + forward
+    (energies, potentials, forces) + the VJP of a force-matching loss
+    sum |F - F_ref|^2 + sum E (gradients to positions and charges)."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    from paper_2606_06617_b300 import workloads as wl
+    dev = torch.device("cuda", 0)
+    K = 16
+    structs = wl.training_batch(n_struct=64, K=K, seed=seed)
+    n_tot = sum(s.n for s in structs)
+    Lmax = max(s.box[0] for s in structs)
+    plan = lr.BatchPlan((Lmax, Lmax, Lmax), 64, n_tot, K, (1, 6), 4.0, tol=1e-5, grid=40,
+                        flags=lr.PSWF_FLAG_BACKWARD, device=dev)
+    off = np.concatenate([[0], np.cumsum([s.n for s in structs])]).astype(np.int64)
+    boxes = np.array([s.box for s in structs])
+    ps = np.array([s.ps for s in structs], dtype=np.int32)
+    pos = torch.tensor(np.concatenate([s.pos for s in structs]), device=dev)
+    q = torch.tensor(np.concatenate([s.q for s in structs], axis=1), dtype=torch.float32, device=dev)
+    f_ref = torch.randn(n_tot, 3, device=dev) * 0.1
+    gE = torch.ones(64 * K, dtype=torch.float64, device=dev)
+
+    def step():
+        plan.set_points(boxes, ps, off, pos, q)
+        e, phi, f = plan.execute()
+        gF = 2.0 * (f[:n_tot] - f_ref)
+        return plan.backward(gE, None, gF)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    stage_ms, launches = plan.profile_read()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"64 structures, {n_tot} atoms, K=16 (p 1/6), grid 40^3, forward + force-matching backward",
+            "ms_per_step": ms, "structures_per_s": 64 / (ms * 1e-3), "atoms_per_s": n_tot / (ms * 1e-3),
+            "stages_ms_per_step": {k: v / steps for k, v in stage_ms.items()}}
+
+
 def run_reference(args, rank: int):
     """--impl reference: the CPU oracle as it stands, bounded sample per step."""
     import torch
@@ -347,6 +395,17 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "training":
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            tr = run_training(steps=args.steps, warmup=args.warmup)
+            print(json.dumps({"metric": "training step atoms/s (forward + backward)", "value": tr["atoms_per_s"],
+                              "unit": "atoms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": tr["ms_per_step"], "higher_is_better": True, "dtype": "f32",
+                              "data": "synthetic", "config": {"workload": "training_batch_64x16"},
+                              "training": tr}), flush=True)
         return
     if args.workload == "serving":
         if rank == 0:

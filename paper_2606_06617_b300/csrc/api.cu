@@ -1107,7 +1107,9 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->nts = pl->geo.nts;
   pl->ntiles = b * pl->nts;
   pl->nqb = b > 1 ? kQBlocksBatch : kQBlocks;
-  pl->eblk = int(std::max<int64_t>(1, std::min<int64_t>(kEnergyBlocks, int64_t(h.M[1]) * h.M[2] / 8)));
+  // multiplier blocks per channel: about 8 half-spectrum elements a thread
+  pl->eblk = int(std::max<int64_t>(
+      1, std::min<int64_t>(kEnergyBlocks, int64_t(h.M[1]) * h.M[2] * (h.M[0] / 2 + 1) / (8 * kThreads))));
   pl->scan_per_block = 16384;
   pl->scan_blocks = (pl->ntiles + pl->scan_per_block - 1) / pl->scan_per_block;
   pl->grid_elems = int64_t(b) * h.K * h.M[2] * h.M[1] * pl->geo.Mxp;

@@ -288,8 +288,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
                                                   const double* __restrict__ sbox, const R* __restrict__ coef,
                                                   const R* __restrict__ iw2, int iw2_stride,
                                                   double* __restrict__ part, int want_energy) {
-  // One (y, z) row of the half spectrum per block iteration; rows outside the
-  // band |k| < k_c are zero-filled without reading them.
+  // Modes outside the band |k| < k_c are zero-filled without being read.
   const int g = blockIdx.y;
   const int s = g / mp.K;
   const int p = pch[g];
@@ -306,53 +305,49 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   const R kf0 = R(kTwoPi / sbox[3 * s]), kf1 = R(kTwoPi / sbox[3 * s + 1]), kf2 = R(kTwoPi / sbox[3 * s + 2]);
   const bool even_x = (mp.M[0] % 2) == 0;
   double e = 0.0;
-  for (int row = blockIdx.x; row < nrow; row += gridDim.x) {
+  // Elements of the half spectrum in storage order, spread over the
+  // channel's blocks (rows of small grids are shorter than a block).
+  const int64_t nel = int64_t(nrow) * mp.Mxh;
+  for (int64_t el = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; el < nel; el += int64_t(gridDim.x) * blockDim.x) {
+    const int row = int(el / mp.Mxh), ix = int(el - int64_t(row) * mp.Mxh);
     const int iy = row % mp.M[1], iz = row / mp.M[1];
     const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
     const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
     const R ky = kf1 * R(my), kz = kf2 * R(mz);
-    const R kyz2 = ky * ky + kz * kz;
-    Cplx<R>* dr = d + int64_t(row) * mp.Mxh;
-    if (!(kyz2 < kc2)) {
-      for (int ix = threadIdx.x; ix < mp.Mxh; ix += blockDim.x) dr[ix] = Cplx<R>{R(0), R(0)};
+    const R kx = kf0 * R(ix);
+    const R k2 = kx * kx + ky * ky + kz * kz;
+    Cplx<R>* dp = d + el;
+    if (!(k2 < kc2) || k2 == R(0)) {
+      *dp = Cplx<R>{R(0), R(0)};
       continue;
     }
     const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
-    const R wyz = sc * iw2y[ay] * iw2z[az];
-    for (int ix = threadIdx.x; ix < mp.Mxh; ix += blockDim.x) {
-      const R kx = kf0 * R(ix);
-      const R k2 = kx * kx + kyz2;
-      if (!(k2 < kc2) || k2 == R(0)) {
-        dr[ix] = Cplx<R>{R(0), R(0)};
-        continue;
-      }
-      const R k = sqrt(k2);
-      R u = k * inv_kc;
-      if (u >= R(1)) u = R(1) - R(1e-7);
-      int seg = int(u * R(kMultSeg));
-      if (seg > kMultSeg - 1) seg = kMultSeg - 1;
-      const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
-      const R* cs = cf + seg * (mp.deg + 1);
-      R S = cs[mp.deg];
-      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
-      R phi;
-      switch (p) {
-        case 1: phi = S / k2; break;
-        case 2: phi = S / k; break;
-        case 3: phi = S - log(u); break;
-        case 5: phi = S - u * u * log(u); break;
-        default: phi = S; break;
-      }
-      const R G = phi * wyz * iw2x[ix];
-      Cplx<R> v = dr[ix];
-      if (want_energy) {
-        const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
-        e += double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
-      }
-      v.x *= G;
-      v.y *= G;
-      dr[ix] = v;
+    const R k = sqrt(k2);
+    R u = k * inv_kc;
+    if (u >= R(1)) u = R(1) - R(1e-7);
+    int seg = int(u * R(kMultSeg));
+    if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+    const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+    const R* cs = cf + seg * (mp.deg + 1);
+    R S = cs[mp.deg];
+    for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
+    R phi;
+    switch (p) {
+      case 1: phi = S / k2; break;
+      case 2: phi = S / k; break;
+      case 3: phi = S - log(u); break;
+      case 5: phi = S - u * u * log(u); break;
+      default: phi = S; break;
     }
+    const R G = phi * sc * iw2x[ix] * iw2y[ay] * iw2z[az];
+    Cplx<R> v = *dp;
+    if (want_energy) {
+      const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
+      e += double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
+    }
+    v.x *= G;
+    v.y *= G;
+    *dp = v;
   }
   if (!want_energy) return;
   __shared__ double sh[32];
