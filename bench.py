@@ -182,6 +182,24 @@ def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
     return s.n / dt, torch.get_num_threads(), f"{desc}; {reps} oracle evaluations, {dt:.2f} s each"
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks (the job is as slow as its slowest
+    replica); x itself without a process group.  Works with NCCL (device
+    tensor) and gloo (CPU tensor)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each process
+    units_per_rank units: all units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _percentiles(x):
     x = np.asarray(x, dtype=np.float64)
     return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99)),
@@ -487,12 +505,8 @@ def main():
     plan.profile(False)
     stage_ms, launches = plan.profile_read()
     plan.sync()
-    ms = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
-    value = world * sysm.n / (ms * 1e-3)
+    ms = max_over_ranks(total_ms / args.steps, dist, dev)
+    value = replica_throughput(sysm.n, world, ms * 1e-3)
 
     # roofline of the dominant kernel of ours (by summed event time)
     alg = algorithmic_bytes(w, len(sysm.ps), sysm.n)
@@ -524,13 +538,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(ne):
             plan.compute_host(pos_h, q_h, out=res_h)
-        te = (time.perf_counter() - t0) / ne
-        if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t)
+        te = max_over_ranks((time.perf_counter() - t0) / ne, dist, dev)
         K = len(sysm.ps)
-        e2e = {"value": world * sysm.n / te, "unit": "atoms/s",
+        e2e = {"value": replica_throughput(sysm.n, world, te), "unit": "atoms/s",
                "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * 4),
                "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 4 + sysm.n * 12),
                "ms_per_step": te * 1e3}
