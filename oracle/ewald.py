@@ -49,6 +49,12 @@ def upper_gamma(s: float, x):
     raise ValueError(f"unsupported s = {s}")
 
 
+def screening(p: int, x):
+    """Ewald screening G_p = Gamma(p/2, x^2) / Gamma(p/2), x = alpha r
+    (regularised upper incomplete gamma)."""
+    return gammaincc(p / 2.0, np.asarray(x, dtype=np.float64) ** 2)
+
+
 def _images(box, r_cut):
     box = np.asarray(box, dtype=np.float64)
     nmax = np.ceil(r_cut / box).astype(int) + 1
@@ -91,7 +97,7 @@ def ewald(pos, q, box, p: int, alpha: float | None = None, r_cut: float | None =
         mask = (r < r_cut) & (r > 0)
         rr = np.where(mask, r, 1.0)
         x2 = (alpha * rr) ** 2
-        Qg = gammaincc(s, x2)
+        Qg = screening(p, alpha * rr)
         g = np.where(mask, Qg / rr ** p, 0.0)
         phi[i0:i0 + B] += np.einsum("bsn,n->b", g, q)
         # d/dr [Q(s, a^2 r^2) r^-p] = -2 a^p e^{-a^2 r^2} / (Gamma(s) r) - p Q r^{-p-1}

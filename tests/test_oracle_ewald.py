@@ -63,3 +63,31 @@ def test_quadratic_form(p):
     s = wl.random_system(10, (6.0, 6.0, 6.0), (p,), seed=1, neutral=False)
     e = ewald(s.pos, s.q[0], s.box, p)
     assert abs(0.5 * np.dot(s.q[0], e["phi"]) / e["E"] - 1) < 1e-12
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    return [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+
+
+def test_screening_special_cases_from_the_paper():
+    """The oracle's real-space screening Gamma(p/2, x^2)/Gamma(p/2) (library
+    incomplete gamma) against the paper's closed forms for p = 1 and p = 6
+    (tests/golden/ewald_screening.txt)."""
+    import math
+    from oracle.ewald import screening
+    for p_s, x_s in _golden("ewald_screening.txt"):
+        p, x = int(p_s), float(x_s)
+        got = float(screening(p, x))
+        if p == 1:
+            ref = math.erfc(x)
+        else:
+            ref = math.exp(-x * x) * (1 + x * x + x ** 4 / 2)
+        assert abs(got - ref) <= 1e-13 * max(1.0, abs(ref)), (p, x, got, ref)
+
+
+def test_madelung_constant_golden():
+    """The stored Madelung constant is the one the NaCl pin uses."""
+    (val,), = _golden("nacl_madelung.txt")
+    assert abs(float(val) - 1.747564594633182) < 1e-15
