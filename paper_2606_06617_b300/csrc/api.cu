@@ -299,13 +299,14 @@ struct pswf_plan_s {
   // per-structure tables, one contiguous region (uploaded in one copy):
   void* stab = nullptr;
   int64_t stab_bytes = 0;
-  int64_t stab_off[6] = {0, 0, 0, 0, 0, 0};
+  int64_t stab_off[7] = {0, 0, 0, 0, 0, 0, 0};
   double* sbox = nullptr;    // [B][3] box edges
   double* scale = nullptr;   // [B K] multiplier scale (includes dV^2 / V)
   double* zero_coef = nullptr;  // [B K]
   int* soff = nullptr;       // [B + 1] atom offsets per structure
   int* pch = nullptr;        // [B K] exponents
   void* iw2 = nullptr;       // real [B][3][Mh]
+  double* smol = nullptr;    // [B][3] M_d / L_d (stencil location without a division)
   void* h_stab = nullptr;    // pinned host mirror of stab (batch plans)
   cudaEvent_t stab_ev = nullptr;  // last upload from h_stab
   std::vector<int> h_pch;    // host copy of pch
@@ -400,7 +401,8 @@ int run_size(pswf_plan p, int b) {
 
 // Layout of the per-structure table region (also the pinned host mirror):
 // sbox double [B][3] | scale double [B K] | zero_coef double [B K] |
-// soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh]; returns bytes.
+// soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh] | M/L double [B][3];
+// returns bytes.
 int64_t stab_layout(pswf_plan p) {
   const int64_t B = p->B, K = p->host.K, rs = int64_t(p->real_size);
   auto a16 = [](int64_t b) { return (b + 15) & ~int64_t(15); };
@@ -411,6 +413,7 @@ int64_t stab_layout(pswf_plan p) {
   p->stab_off[3] = off; off = a16(off + (B + 1) * 4);
   p->stab_off[4] = off; off = a16(off + B * K * 4);
   p->stab_off[5] = off; off = a16(off + B * 3 * int64_t(p->Mh) * rs);
+  p->stab_off[6] = off; off = a16(off + B * 3 * 8);
   return off;
 }
 
@@ -458,6 +461,7 @@ int64_t layout(pswf_plan p, char* base) {
     p->soff = reinterpret_cast<int*>(st + p->stab_off[3]);
     p->pch = reinterpret_cast<int*>(st + p->stab_off[4]);
     p->iw2 = st + p->stab_off[5];
+    p->smol = reinterpret_cast<double*>(st + p->stab_off[6]);
   }
   p->fft_work = take(int64_t(p->fft_work_bytes));
   return off;
@@ -485,6 +489,7 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
   int* soff = reinterpret_cast<int*>(dst + p->stab_off[3]);
   int* pch = reinterpret_cast<int*>(dst + p->stab_off[4]);
   char* iw2 = dst + p->stab_off[5];
+  double* smol = reinterpret_cast<double*>(dst + p->stab_off[6]);
   int pdef = 0;
   for (int q = 1; q <= 6 && !pdef; ++q)
     if (h.mult_scale_p[q] != 0.0) pdef = q;
@@ -504,7 +509,10 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
       }
       t.V = t.dV = 1.0;
     }
-    for (int d = 0; d < 3; ++d) sbox[3 * sidx + d] = t.box[d];
+    for (int d = 0; d < 3; ++d) {
+      sbox[3 * sidx + d] = t.box[d];
+      smol[3 * sidx + d] = double(h.M[d]) / t.box[d];
+    }
     const double dv2v = t.dV * t.dV / t.V;
     for (int c = 0; c < K; ++c) {
       const int g = sidx * K + c;
@@ -724,11 +732,11 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(ntl) * 4, s), "clear counts"))) return rc;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((p->n_max + kThreads - 1) / kThreads, 148 * 32)));
   if (pos_dtype == 0)
-    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), geo, p->sbox, p->soff, p->tile_of,
+    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), geo, p->smol, p->soff, p->tile_of,
                                                 p->rank, p->tile_count, static_cast<R*>(p->tmp_t), p->tmp_cell,
                                                 p->n_max, p->err);
   else
-    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), geo, p->sbox, p->soff,
+    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), geo, p->smol, p->soff,
                                                  p->tile_of, p->rank, p->tile_count, static_cast<R*>(p->tmp_t),
                                                  p->tmp_cell, p->n_max, p->err);
   if ((rc = launch_check(p, "k_bin"))) return rc;

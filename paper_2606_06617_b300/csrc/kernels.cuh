@@ -137,8 +137,9 @@ __device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
 // ---- binning -----------------------------------------------------------------
 // k_bin: locate each atom (original order), count it into its tile and keep
 // its rank there, its offsets t and its packed start cell for k_scatter.
+// smol[s][d] = M_d / L_d of structure s.
 template <typename PosT, typename R>
-__global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __restrict__ sbox,
+__global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __restrict__ smol,
                       const int* __restrict__ soff, int* __restrict__ tile_of, int* __restrict__ rank,
                       int* __restrict__ tile_count, R* __restrict__ tmp_t, uint64_t* __restrict__ tmp_cell,
                       int64_t nmax, int* __restrict__ err) {
@@ -153,7 +154,7 @@ __global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __
         x = 0.0;
       }
       double t;
-      locate(x, double(g.M[d]) / sbox[3 * s + d], g.M[d], g.P, i0[d], t);
+      locate(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
       tmp_t[d * nmax + i] = R(t);
     }
     const int tile = s * g.nts + ((i0[2] / kTile) * g.ntile[1] + i0[1] / kTile) * g.ntile[0] + i0[0] / kTile;
