@@ -156,7 +156,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kEnergyBlocks = 592;   // 4 x 148 SMs
-constexpr int kQBlocks = 148;        // charge-sum blocks of a single-structure plan
+constexpr int kQBlocks = 148;        // charge-sum blocks of pswf_self_energy_noalloc
+constexpr int kQBlocksPlan = 592;    // charge-sum blocks of a single-structure plan (4 per SM)
 constexpr int kQBlocksBatch = 8;     // per structure in a batch plan
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
@@ -1114,7 +1115,7 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->geo.B = b;
   pl->nts = pl->geo.nts;
   pl->ntiles = b * pl->nts;
-  pl->nqb = b > 1 ? kQBlocksBatch : kQBlocks;
+  pl->nqb = b > 1 ? kQBlocksBatch : kQBlocksPlan;
   // multiplier blocks per channel: about 8 half-spectrum elements a thread
   pl->eblk = int(std::max<int64_t>(
       1, std::min<int64_t>(kEnergyBlocks, int64_t(h.M[1]) * h.M[2] * (h.M[0] / 2 + 1) / (8 * kThreads))));
