@@ -24,13 +24,14 @@ namespace pswf {
 // Window values, first and second s-derivatives (Horner).
 template <typename R, int P>
 __device__ inline void window_weights2(R t, const WinCoef<R>& wc, R (&w)[P], R (&dw)[P], R (&d2w)[P]) {
+  constexpr int D = WinCoef<R>::kDeg;
   const R s = R(2) * t - R(1);
-  const int deg = wc.deg;
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    const R* c = wc.c + j * (deg + 1);
-    R v = c[deg], dv = R(0), d2v = R(0);
-    for (int n = deg - 1; n >= 0; --n) {
+    const R* c = wc.c + j * (D + 1);
+    R v = c[D], dv = R(0), d2v = R(0);
+#pragma unroll
+    for (int n = D - 1; n >= 0; --n) {
       d2v = d2v * s + R(2) * dv;
       dv = dv * s + v;
       v = v * s + c[n];

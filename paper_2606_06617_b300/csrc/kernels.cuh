@@ -34,10 +34,14 @@ struct Geometry {
   int B;             // structures
 };
 
+// Window pieces as monomials in s = 2t - 1, each padded with zero leading
+// coefficients to a fixed degree (14 in FP32, 24 in FP64) so that Horner
+// loops unroll and read the coefficients as constant operands.
 template <typename R>
 struct WinCoef {
-  int deg;
-  R c[kMaxP * (kMaxDeg + 1)];   // piece j, monomial n at [j * (deg + 1) + n]
+  static constexpr int kDeg = sizeof(R) == 4 ? 14 : 24;
+  int deg;                          // the planner's degree (<= kDeg)
+  R c[kMaxP * (kDeg + 1)];          // piece j, monomial n at [j * (kDeg + 1) + n]
 };
 
 struct MultParams {
@@ -106,13 +110,14 @@ __device__ inline int find_struct(const int* __restrict__ off, int stride, int B
 // Window weights W_j(t) and dW_j/ds (s = 2t - 1) for the P pieces (Horner).
 template <typename R, int P>
 __device__ inline void window_weights(R t, const WinCoef<R>& wc, R (&w)[P], R (&dw)[P]) {
+  constexpr int D = WinCoef<R>::kDeg;
   const R s = R(2) * t - R(1);
-  const int deg = wc.deg;
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    const R* c = wc.c + j * (deg + 1);
-    R v = c[deg], dv = R(0);
-    for (int n = deg - 1; n >= 0; --n) {
+    const R* c = wc.c + j * (D + 1);
+    R v = c[D], dv = R(0);
+#pragma unroll
+    for (int n = D - 1; n >= 0; --n) {
       dv = dv * s + v;
       v = v * s + c[n];
     }
@@ -123,13 +128,14 @@ __device__ inline void window_weights(R t, const WinCoef<R>& wc, R (&w)[P], R (&
 
 template <typename R, int P>
 __device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
+  constexpr int D = WinCoef<R>::kDeg;
   const R s = R(2) * t - R(1);
-  const int deg = wc.deg;
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    const R* c = wc.c + j * (deg + 1);
-    R v = c[deg];
-    for (int n = deg - 1; n >= 0; --n) v = v * s + c[n];
+    const R* c = wc.c + j * (D + 1);
+    R v = c[D];
+#pragma unroll
+    for (int n = D - 1; n >= 0; --n) v = v * s + c[n];
     w[j] = v;
   }
 }

@@ -22,11 +22,12 @@ constexpr int kGatherThreads = kGatherThreadsFor<R>;
 constexpr int kDirectThreads = 256;
 
 static WinCoef<R> win_coef(const LaunchCtx& c) {
+  constexpr int D = WinCoef<R>::kDeg;
   WinCoef<R> w;
   std::memset(&w, 0, sizeof(w));
   w.deg = c.deg_w;
-  const int n = c.geo.P * (c.deg_w + 1);
-  for (int i = 0; i < n; ++i) w.c[i] = R(c.coef_w[i]);
+  for (int j = 0; j < c.geo.P; ++j)
+    for (int n = 0; n <= c.deg_w && n <= D; ++n) w.c[j * (D + 1) + n] = R(c.coef_w[j * (c.deg_w + 1) + n]);
   return w;
 }
 

@@ -383,7 +383,8 @@ int plan_core(const double box_max[3], int K, const int* pset, int npset, const 
     const double P = plan.P;
     for (int j = 0; j < plan.P; ++j)
       cheb[j] = cheb_fit([&](double s) { return plan.win.eval((2.0 * j - P + 1.0 + s) / P); }, nfit);
-    const int deg = std::min(family_degree(cheb, eps_poly), kMaxDeg);
+    // the device pads FP32 pieces to degree 14 and FP64 pieces to 24
+    const int deg = std::min(family_degree(cheb, eps_poly), opt.precision == 1 ? kMaxDeg : 14);
     plan.deg_w = deg;
     plan.coef_w.assign(size_t(plan.P) * (deg + 1), 0.0);
     for (int j = 0; j < plan.P; ++j) {
