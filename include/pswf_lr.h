@@ -53,6 +53,7 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------- */
 #define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */
+#define PSWF_FLAG_VIRIAL 2         /* pswf_execute also reduces the diagonal virial (pswf_virial) */
 
 typedef struct {
   double tol;      /* target LR tolerance eps_tot (default 1e-5) */
@@ -199,6 +200,17 @@ int pswf_self_energy(pswf_plan plan, double* out);
  * cleared.  Returns PSWF_EINVAL for n outside 0..n_max or more than 64
  * channels (the array's limit). */
 int pswf_self_energy_noalloc(pswf_plan plan, int64_t n, const void* q, double* out, void* stream);
+
+/* Diagonal virial of the last pswf_execute (plan created with
+ * PSWF_FLAG_VIRIAL), device double [B][K][3] (B = 1 for single structures):
+ * W_cd = -L_d dE_c/dL_d at fixed fractional coordinates, E_c the channel
+ * energy of pswf_execute (reciprocal sum and zero-frequency term; the
+ * self-energy does not depend on the box).  The grid density and the window
+ * transform are invariant under that scaling, so W_cd = E_c + sum_m e_m
+ * (d ln Phi-hat_p / d ln k) k_d^2 / k^2 over the band modes m with energy
+ * terms e_m (Eq. (Fourier), Eq. (PhiH)); orthorhombic cells only.  The
+ * stress of the cell is -W / V.  Asynchronous on the plan's stream. */
+int pswf_virial(pswf_plan plan, double* virial);
 
 /* Waits for the plan's stream and returns the first device-side status
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */

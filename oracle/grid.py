@@ -218,6 +218,34 @@ class DiscretePSWF:
         gr = torch.zeros_like(pos) if gr is None else gr
         return gq.detach(), gr.detach()
 
+    def virial_fd(self, pos, q, eps: float = 5e-5) -> np.ndarray:
+        """Diagonal virial W[c, d] = -L_d dE_c/dL_d at fixed fractional
+        coordinates, by central differences of evaluate (E_c = E_k + E^0)
+        under the scaling L_d -> L_d (1 +- h) of the box and the positions,
+        at the same grid size, P, c and c_w; Richardson-extrapolated from
+        h = eps and 2 eps (truncation O(eps^4), rounding ~1e-12 / eps)."""
+        pos = np.asarray(pos, dtype=np.float64)
+        K = len(self.cfg.ps)
+        c_w = self.cfg.c if self.cfg.c_w is None else self.cfg.c_w
+
+        def central(h):
+            W = np.zeros((K, 3))
+            for d in range(3):
+                Es = []
+                for sgn in (1.0, -1.0):
+                    f = 1.0 + sgn * h
+                    box = list(self.cfg.box)
+                    box[d] *= f
+                    p2 = pos.copy()
+                    p2[:, d] *= f
+                    cfg = GridConfig(tuple(box), self.cfg.M, self.cfg.P, self.cfg.c, self.cfg.r_c, self.cfg.ps,
+                                     c_w=c_w)
+                    Es.append(DiscretePSWF(cfg).evaluate(p2, q)["E_ch"].numpy())
+                W[:, d] = -(Es[0] - Es[1]) / (2.0 * h)
+            return W
+
+        return (4.0 * central(eps) - central(2.0 * eps)) / 3.0
+
     def self_energy(self, q) -> np.ndarray:
         """E_self^(p) per channel (Implementation details)."""
         q = np.asarray(q, dtype=np.float64)

@@ -101,26 +101,38 @@ __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __res
 // One block per structure s: energy[s][c] = sum of the partials of channel
 // g = s K + c + zero_coef[g] Q_net^2; energy[s][K] = total.
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
-                               const double* __restrict__ charges, double* __restrict__ energy) {
-  __shared__ double sh[32];
+                               const double* __restrict__ charges, double* __restrict__ energy,
+                               const double* __restrict__ vpart, double* __restrict__ virial) {
+  __shared__ double sh[4][32];
   __shared__ double tot;
   const int s = blockIdx.x;
   if (threadIdx.x == 0) tot = 0.0;
   for (int c = 0; c < K; ++c) {
     const int g = s * K + c;
-    double e = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) e += part[size_t(g) * nblk + i];
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    double t4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+      t4[0] += part[size_t(g) * nblk + i];
+      if (vpart)
+        for (int d = 0; d < 3; ++d) t4[1 + d] += vpart[(size_t(g) * nblk + i) * 3 + d];
+    }
+    for (int q = 0; q < 4; ++q)
+      for (int o = 16; o > 0; o >>= 1) t4[q] += __shfl_down_sync(0xffffffffu, t4[q], o);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+    if ((threadIdx.x & 31) == 0)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x >> 5] = t4[q];
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int w = 0; w < int(blockDim.x >> 5); ++w)
+        for (int q = 0; q < 4; ++q) t[q] += sh[q][w];
       const double Q = charges[2 * g];
-      const double ec = t + zero_coef[g] * Q * Q;
+      const double ec = t[0] + zero_coef[g] * Q * Q;
       energy[size_t(s) * (K + 1) + c] = ec;
       tot += ec;
+      // W_d = -L_d dE/dL_d: E (the 1/V prefactor and E^0 ~ 1/V) plus the
+      // log-derivative sum of the multiplier
+      if (vpart && virial)
+        for (int d = 0; d < 3; ++d) virial[size_t(g) * 3 + d] = ec + t[1 + d];
     }
   }
   if (threadIdx.x == 0) energy[size_t(s) * (K + 1) + K] = tot;
@@ -294,6 +306,9 @@ struct pswf_plan_s {
   double* charges = nullptr; // [B K][2]: Q_net, Q_self
   double* bsum = nullptr;    // [B K][2]: sum and sum of squares of the upstream gphi (backward)
   double* epart = nullptr;   // [B K][eblk]
+  double* vpart = nullptr;   // [B K][eblk][3] (PSWF_FLAG_VIRIAL)
+  double* virial = nullptr;  // [B][K][3] (PSWF_FLAG_VIRIAL)
+  bool virial_valid = false;
   double* energy_tmp = nullptr; // [B][K + 1]
   int* err = nullptr;        // device status flag
   void* coef_m = nullptr;    // real [6][kMultSeg][deg_m + 1], row p - 1
@@ -450,6 +465,9 @@ int64_t layout(pswf_plan p, char* base) {
   p->bsum = reinterpret_cast<double*>(take(BK * 2 * 8));
   p->epart = reinterpret_cast<double*>(take(BK * p->eblk * 8));
   p->energy_tmp = reinterpret_cast<double*>(take(B * (K + 1) * 8));
+  const bool vir = (p->flags & PSWF_FLAG_VIRIAL) != 0;
+  p->vpart = vir ? reinterpret_cast<double*>(take(BK * p->eblk * 3 * 8)) : nullptr;
+  p->virial = vir ? reinterpret_cast<double*>(take(BK * 3 * 8)) : nullptr;
   p->err = reinterpret_cast<int*>(take(4));
   p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
   p->stab_bytes = stab_layout(p);
@@ -625,12 +643,13 @@ int multiply(pswf_plan p, int want_energy, void* data) {
     k_multiply_planes<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->spec), mp, p->nkx, p->pch, p->scale,
                                                            p->sbox, static_cast<const R*>(p->coef_m),
                                                            static_cast<const R*>(p->iw2), p->Mh, p->epart,
-                                                           want_energy);
+                                                           want_energy, want_energy ? p->vpart : nullptr);
     return launch_check(p, "k_multiply_planes");
   }
   k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->sbox,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
-                                                  p->Mh, p->epart, want_energy);
+                                                  p->Mh, p->epart, want_energy,
+                                                  want_energy ? p->vpart : nullptr);
   return launch_check(p, "k_multiply");
 }
 
@@ -720,6 +739,7 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   int rc;
   p->n = n;
   p->psi_valid = false;
+  p->virial_valid = false;
   StageScope scope(p, PSWF_STAGE_SET_POINTS);
   p->launches[PSWF_STAGE_SET_POINTS] += p->batch ? 7 : 8;
   if (!p->batch) {
@@ -779,7 +799,8 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
     StageScope scope(p, PSWF_STAGE_MULTIPLY);
     if ((rc = multiply<R>(p, 1, p->grid))) return rc;
     k_energy_final<<<p->nrun, 256, 0, s>>>(p->host.K, p->eblk, p->epart, p->zero_coef, p->charges,
-                                           energy ? energy : p->energy_tmp);
+                                           energy ? energy : p->energy_tmp, p->vpart, p->virial);
+    p->virial_valid = p->virial != nullptr;
     if (energy && p->nrun < p->B &&
         (rc = cuda_check(p, cudaMemsetAsync(energy + size_t(p->nrun) * (p->host.K + 1), 0,
                                             size_t(p->B - p->nrun) * (p->host.K + 1) * 8, s), "clear energies")))
@@ -1270,6 +1291,19 @@ int pswf_self_energy(pswf_plan pl, double* out) {
   const int nk = pl->nrun * pl->host.K;   // slots beyond the last launch hold no atoms
   for (int g = 0; g < BK; ++g) out[g] = g < nk ? pl->host.self_coef_p[pl->h_pch[g]] * ch[2 * g + 1] : 0.0;
   return PSWF_OK;
+}
+
+int pswf_virial(pswf_plan pl, double* virial) {
+  if (!pl || !virial) return PSWF_EINVAL;
+  if (!(pl->flags & PSWF_FLAG_VIRIAL)) return set_err(pl, PSWF_ESTATE, "plan was created without PSWF_FLAG_VIRIAL");
+  if (!pl->virial_valid) return set_err(pl, PSWF_ESTATE, "pswf_virial needs a preceding pswf_execute");
+  const size_t bytes = size_t(pl->B) * pl->host.K * 3 * 8;
+  if (pl->nrun < pl->B) {
+    int rc = cuda_check(pl, cudaMemsetAsync(virial, 0, bytes, pl->stream), "clear virial");
+    if (rc) return rc;
+  }
+  return cuda_check(pl, cudaMemcpyAsync(virial, pl->virial, size_t(pl->nrun) * pl->host.K * 3 * 8,
+                                        cudaMemcpyDeviceToDevice, pl->stream), "copy virial");
 }
 
 int pswf_sync(pswf_plan pl) {

@@ -280,8 +280,79 @@ __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restr
                                    double* __restrict__ charges);
 // One block per structure: energy[s][c] = sum of the multiplier partials of
 // channel g = s K + c plus zero_coef[g] Q_net^2; energy[s][K] = their total.
+// With vpart: virial[g][d] = energy[s][c] + sum of the virial partials.
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
-                               const double* __restrict__ charges, double* __restrict__ energy);
+                               const double* __restrict__ charges, double* __restrict__ energy,
+                               const double* __restrict__ vpart, double* __restrict__ virial);
+
+// ---- multiplier helpers ----------------------------------------------------------
+// S_p on one piece and dS/ds by Horner (runtime degree, coefficients in
+// global memory).
+template <typename R>
+__device__ inline void mult_horner(const R* __restrict__ cs, int deg, R sv, R& S, R& dS) {
+  S = cs[deg];
+  dS = R(0);
+  for (int nn = deg - 1; nn >= 0; --nn) {
+    dS = dS * sv + S;
+    S = S * sv + cs[nn];
+  }
+}
+
+// Phi-hat_p / scale_p from its smooth part: the singular factor per p.
+template <typename R>
+__device__ inline R mult_value(int p, R S, R k, R k2, R u) {
+  switch (p) {
+    case 1: return S / k2;
+    case 2: return S / k;
+    case 3: return S - log(u);
+    case 5: return S - u * u * log(u);
+    default: return S;
+  }
+}
+
+// d ln Phi-hat_p / d ln k = u (d phi / du) / phi, with dSu = dS/du.
+template <typename R>
+__device__ inline R mult_dlog(int p, R S, R dSu, R u, R phi) {
+  if (phi == R(0)) return R(0);
+  switch (p) {
+    case 1: return u * dSu / S - R(2);
+    case 2: return u * dSu / S - R(1);
+    case 3: return (u * dSu - R(1)) / phi;
+    case 5: return u * (dSu - R(2) * u * log(u) - u) / phi;
+    default: return u * dSu / phi;
+  }
+}
+
+// Block sums of the energy partial (and, with vpart, the three virial
+// partials) written at index `slot` of part / vpart[slot][3].
+__device__ inline void block_partials(double e, double vx, double vy, double vz, double* __restrict__ part,
+                                      double* __restrict__ vpart, size_t slot) {
+  __shared__ double sh[4][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    vx += __shfl_down_sync(0xffffffffu, vx, o);
+    vy += __shfl_down_sync(0xffffffffu, vy, o);
+    vz += __shfl_down_sync(0xffffffffu, vz, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = e;
+    sh[1][threadIdx.x >> 5] = vx;
+    sh[2][threadIdx.x >> 5] = vy;
+    sh[3][threadIdx.x >> 5] = vz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < int(blockDim.x >> 5); ++w)
+      for (int i = 0; i < 4; ++i) t[i] += sh[i][w];
+    part[slot] = t[0];
+    if (vpart) {
+      vpart[3 * slot] = t[1];
+      vpart[3 * slot + 1] = t[2];
+      vpart[3 * slot + 2] = t[3];
+    }
+  }
+}
 
 // ---- multiplier and energy (steps (iii)-(iv)) --------------------------------------
 // blockIdx.y = g = s K + c.  For each half-spectrum mode m != 0 with
@@ -294,7 +365,8 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
                                                   const int* __restrict__ pch, const double* __restrict__ scale,
                                                   const double* __restrict__ sbox, const R* __restrict__ coef,
                                                   const R* __restrict__ iw2, int iw2_stride,
-                                                  double* __restrict__ part, int want_energy) {
+                                                  double* __restrict__ part, int want_energy,
+                                                  double* __restrict__ vpart) {
   // Modes outside the band |k| < k_c are zero-filled without being read.
   const int g = blockIdx.y;
   const int s = g / mp.K;
@@ -311,7 +383,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   constexpr double kTwoPi = 6.283185307179586476925;
   const R kf0 = R(kTwoPi / sbox[3 * s]), kf1 = R(kTwoPi / sbox[3 * s + 1]), kf2 = R(kTwoPi / sbox[3 * s + 2]);
   const bool even_x = (mp.M[0] % 2) == 0;
-  double e = 0.0;
+  double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
   // Elements of the half spectrum in storage order, spread over the
   // channel's blocks (rows of small grids are shorter than a block).
   const int64_t nel = int64_t(nrow) * mp.Mxh;
@@ -336,36 +408,28 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
     if (seg > kMultSeg - 1) seg = kMultSeg - 1;
     const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
     const R* cs = cf + seg * (mp.deg + 1);
-    R S = cs[mp.deg];
-    for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
-    R phi;
-    switch (p) {
-      case 1: phi = S / k2; break;
-      case 2: phi = S / k; break;
-      case 3: phi = S - log(u); break;
-      case 5: phi = S - u * u * log(u); break;
-      default: phi = S; break;
-    }
+    R S, dS;
+    mult_horner(cs, mp.deg, sv, S, dS);
+    const R phi = mult_value(p, S, k, k2, u);
     const R G = phi * sc * iw2x[ix] * iw2y[ay] * iw2z[az];
     Cplx<R> v = *dp;
     if (want_energy) {
       const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
-      e += double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
+      const double em = double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
+      e += em;
+      if (vpart) {
+        const double dl = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
+        vx += em * dl * double(kx * kx);
+        vy += em * dl * double(ky * ky);
+        vz += em * dl * double(kz * kz);
+      }
     }
     v.x *= G;
     v.y *= G;
     *dp = v;
   }
   if (!want_energy) return;
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-    part[size_t(g) * gridDim.x + blockIdx.x] = t;
-  }
+  block_partials(e, vx, vy, vz, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
 }
 
 // Multiplier on the pruned spectrum of a single structure: layout
@@ -378,7 +442,8 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
                                                          const double* __restrict__ scale,
                                                          const double* __restrict__ sbox, const R* __restrict__ coef,
                                                          const R* __restrict__ iw2, int iw2_stride,
-                                                         double* __restrict__ part, int want_energy) {
+                                                         double* __restrict__ part, int want_energy,
+                                                         double* __restrict__ vpart) {
   const int c = blockIdx.y;
   const int p = pch[c];
   const R sc = R(scale[c]);
@@ -392,7 +457,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
   const R inv_kc = R(mp.inv_kc);
   constexpr double kTwoPi = 6.283185307179586476925;
   const R kf0 = R(kTwoPi / sbox[0]), kf1 = R(kTwoPi / sbox[1]), kf2 = R(kTwoPi / sbox[2]);
-  double e = 0.0;
+  double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
   const int nline = nkx * mp.M[2];
   for (int line = blockIdx.x; line < nline; line += gridDim.x) {
     const int ix = line / mp.M[2], iz = line - ix * mp.M[2];
@@ -422,35 +487,29 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
       if (seg > kMultSeg - 1) seg = kMultSeg - 1;
       const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
       const R* cs = cf + seg * (mp.deg + 1);
-      R S = cs[mp.deg];
-      for (int nn = mp.deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
-      R phi;
-      switch (p) {
-        case 1: phi = S / k2; break;
-        case 2: phi = S / k; break;
-        case 3: phi = S - log(u); break;
-        case 5: phi = S - u * u * log(u); break;
-        default: phi = S; break;
-      }
+      R S, dS;
+      mult_horner(cs, mp.deg, sv, S, dS);
+      const R phi = mult_value(p, S, k, k2, u);
       const int ay = my < 0 ? -my : my;
       const R G = phi * wxz * iw2y[ay];
       Cplx<R> v = dl[iy];
-      if (want_energy) e += double(wedge * G * (v.x * v.x + v.y * v.y));
+      if (want_energy) {
+        const double em = double(wedge * G * (v.x * v.x + v.y * v.y));
+        e += em;
+        if (vpart) {
+          const double dlg = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
+          vx += em * dlg * double(kx * kx);
+          vy += em * dlg * double(ky * ky);
+          vz += em * dlg * double(kz * kz);
+        }
+      }
       v.x *= G;
       v.y *= G;
       dl[iy] = v;
     }
   }
   if (!want_energy) return;
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += sh[w];
-    part[size_t(c) * gridDim.x + blockIdx.x] = t;
-  }
+  block_partials(e, vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
 }
 
 // ---- interpolation, direct from global memory (fallback kernel) ---------------------

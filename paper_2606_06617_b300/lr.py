@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
 
 PSWF_FLAG_BACKWARD = 1
+PSWF_FLAG_VIRIAL = 2
 
 
 class PswfError(RuntimeError):
@@ -74,6 +75,7 @@ SIGNATURES = {
     "pswf_execute": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_self_energy": ([_vp, _dp], ctypes.c_int),
+    "pswf_virial": ([_vp, _vp], ctypes.c_int),
     "pswf_sync": ([_vp], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_plan_destroy": ([_vp], None),
@@ -261,6 +263,17 @@ class Plan:
         self._stream()
         _check(lib().pswf_backward(self._h, ptr(ge), ptr(gp), ptr(gf), ptr(gq), ptr(gr)), self._h)
         return gq, gr
+
+    def virial(self):
+        """Diagonal virial W[c, d] = -L_d dE_c/dL_d of the last execute (device
+        float64 [K, 3]; batch plans [B, K, 3]); needs flags=PSWF_FLAG_VIRIAL."""
+        import torch
+        B = getattr(self, "B", None)
+        shape = (self.K, 3) if B is None else (B, self.K, 3)
+        out = torch.empty(*shape, dtype=torch.float64, device=self.device)
+        self._stream()
+        _check(lib().pswf_virial(self._h, _vp(out.data_ptr())), self._h)
+        return out
 
     def self_energy(self) -> np.ndarray:
         out = (ctypes.c_double * self.K)()

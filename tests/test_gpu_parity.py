@@ -185,3 +185,58 @@ def test_ionic_melt_subbox(precision, tol):
     g = run_gpu(s, 7.0, 7, M, c, cw, precision=precision)
     o = run_oracle(s, 7.0, 7, M, c, cw)
     _compare(g, o, tol, "melt sub-box")
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 2e-5), (1, 1e-7)])
+def test_virial_matches_oracle(precision, tol):
+    """Diagonal virial W_cd = -L_d dE_c/dL_d (PSWF_FLAG_VIRIAL) against the
+    oracle's central differences of E_c under box scaling, all six
+    exponents, an orthorhombic box."""
+    import torch
+    from oracle.grid import DiscretePSWF, GridConfig
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (12.0, 13.5, 11.0)
+    s = wl.random_system(200, box, (1, 2, 3, 4, 5, 6), seed=31, neutral=False)
+    M = (24, 27, 22)
+    c = 11.0
+    cw = window_cw(box, M, 7, c, 4.5)
+    plan = lr.Plan(box, s.n, s.ps, 4.5, c=c, c_w=cw, P=7, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_VIRIAL, device=dev)
+    plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=plan.dtype, device=dev))
+    e, _, _ = plan.execute()
+    W = plan.virial().cpu().numpy()
+    plan.sync()
+    ref = DiscretePSWF(GridConfig(box, M, 7, c, 4.5, s.ps, c_w=cw)).virial_fd(s.pos, s.q)
+    assert rel_rms(W, ref) <= tol, (rel_rms(W, ref), W, ref)
+    E = e.cpu().numpy()
+    for ci in range(6):
+        # per channel, relative to the channel's energy scale as well (its
+        # virial can be much smaller than its energy)
+        bound = 3 * tol * max(np.abs(ref[ci]).max(), abs(E[ci]))
+        assert np.abs(W[ci] - ref[ci]).max() <= bound, (ci, W[ci], ref[ci])
+
+
+def test_virial_batch_plan():
+    """Batch plans: per-slot virials equal single-structure plans' (FP32)."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    structs = [wl.random_system(n, b, (1, 6), seed=n, neutral=True)
+               for n, b in ((80, (9.0, 10.0, 9.5)), (150, (11.0, 9.0, 12.0)))]
+    M = (28, 28, 28)
+    plan = lr.BatchPlan((12.0, 12.0, 12.0), 4, 230, 2, (1, 6), 4.0, grid=M, flags=lr.PSWF_FLAG_VIRIAL, device=dev)
+    off = np.array([0, 80, 230], dtype=np.int64)
+    plan.set_points(np.array([s.box for s in structs]), np.array([s.ps for s in structs], dtype=np.int32), off,
+                    torch.tensor(np.concatenate([s.pos for s in structs]), device=dev),
+                    torch.tensor(np.concatenate([s.q for s in structs], axis=1), dtype=torch.float32, device=dev))
+    plan.execute()
+    W = plan.virial().cpu().numpy()
+    info = plan.info
+    for i, s in enumerate(structs):
+        sp = lr.Plan(s.box, s.n, s.ps, 4.0, c=info["c"], c_w=info["c_w"], P=info["P"], grid=M,
+                     flags=lr.PSWF_FLAG_VIRIAL, device=dev)
+        sp.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=torch.float32, device=dev))
+        sp.execute()
+        assert np.allclose(W[i], sp.virial().cpu().numpy(), rtol=1e-5, atol=1e-8)
+    assert np.all(W[2:] == 0.0)

@@ -156,3 +156,33 @@ def test_o1_vjp_matches_finite_differences():
     gq1, gr1 = o.vjp(s.pos, s.q, np.ones(2))
     assert rel_rms(gq1.numpy(), r["phi"].numpy()) < 1e-12
     assert rel_rms(gr1.numpy(), -r["F"].numpy()) < 1e-12
+
+
+def test_o1_virial_homogeneity():
+    """The oracle's virial (central differences of E_c under L_d -> L_d (1 +-
+    eps), fractional coordinates fixed) plus the real-space complement's
+    virial equals p E for the assembled 1/r^p total (a lattice sum of a
+    degree -p homogeneous kernel), to the method's accuracy; and the
+    difference quotient is converged (two step sizes agree)."""
+    from oracle.realspace import real_space
+    s = wl.random_system(60, (9.0, 10.0, 11.0), (1,), seed=5, neutral=True)
+    M, P, rc = (24, 27, 30), 8, 4.0
+    o = DiscretePSWF(GridConfig(s.box, M, P, C, rc, s.ps, c_w=cw_max(s.box, M, P, C, rc)))
+    r = o.evaluate(s.pos, s.q)
+    W = o.virial_fd(s.pos, s.q)
+    W2 = o.virial_fd(s.pos, s.q, eps=1e-4)
+    assert np.allclose(W, W2, rtol=1e-7, atol=1e-9)
+    eps = 1e-5
+    W_real = 0.0
+    for d in range(3):
+        Es = []
+        for sg in (1, -1):
+            box = list(s.box)
+            box[d] *= 1 + sg * eps
+            pp = s.pos.copy()
+            pp[:, d] *= 1 + sg * eps
+            Es.append(real_space(pp, s.q[0], box, 1, C, rc)["E"])
+        W_real += -(Es[0] - Es[1]) / (2 * eps)
+    tot = pswf_total({"E_ch": r["E_ch"].numpy(), "phi": r["phi"].numpy(), "f": r["f"].numpy()},
+                     s.pos, s.q, s.box, s.ps, C, rc)
+    assert abs(W.sum() + W_real - tot["E"]) <= 1e-3 * abs(tot["E"])
