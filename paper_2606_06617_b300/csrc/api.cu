@@ -315,14 +315,15 @@ struct pswf_plan_s {
   // per-structure tables, one contiguous region (uploaded in one copy):
   void* stab = nullptr;
   int64_t stab_bytes = 0;
-  int64_t stab_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t stab_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double* sbox = nullptr;    // [B][3] box edges
   double* scale = nullptr;   // [B K] multiplier scale (includes dV^2 / V)
   double* zero_coef = nullptr;  // [B K]
   int* soff = nullptr;       // [B + 1] atom offsets per structure
   int* pch = nullptr;        // [B K] exponents
   void* iw2 = nullptr;       // real [B][3][Mh]
-  double* smol = nullptr;    // [B][3] M_d / L_d (stencil location without a division)
+  double* smol = nullptr;    // [B][3] M_d / L_d (stencil location and 2/h without a division)
+  double* kfac = nullptr;    // [B][3] 2 pi / L_d
   void* h_stab = nullptr;    // pinned host mirror of stab (batch plans)
   cudaEvent_t stab_ev = nullptr;  // last upload from h_stab
   std::vector<int> h_pch;    // host copy of pch
@@ -417,8 +418,8 @@ int run_size(pswf_plan p, int b) {
 
 // Layout of the per-structure table region (also the pinned host mirror):
 // sbox double [B][3] | scale double [B K] | zero_coef double [B K] |
-// soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh] | M/L double [B][3];
-// returns bytes.
+// soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh] | M/L double [B][3] |
+// 2 pi / L double [B][3]; returns bytes.
 int64_t stab_layout(pswf_plan p) {
   const int64_t B = p->B, K = p->host.K, rs = int64_t(p->real_size);
   auto a16 = [](int64_t b) { return (b + 15) & ~int64_t(15); };
@@ -430,6 +431,7 @@ int64_t stab_layout(pswf_plan p) {
   p->stab_off[4] = off; off = a16(off + B * K * 4);
   p->stab_off[5] = off; off = a16(off + B * 3 * int64_t(p->Mh) * rs);
   p->stab_off[6] = off; off = a16(off + B * 3 * 8);
+  p->stab_off[7] = off; off = a16(off + B * 3 * 8);
   return off;
 }
 
@@ -481,6 +483,7 @@ int64_t layout(pswf_plan p, char* base) {
     p->pch = reinterpret_cast<int*>(st + p->stab_off[4]);
     p->iw2 = st + p->stab_off[5];
     p->smol = reinterpret_cast<double*>(st + p->stab_off[6]);
+    p->kfac = reinterpret_cast<double*>(st + p->stab_off[7]);
   }
   p->fft_work = take(int64_t(p->fft_work_bytes));
   return off;
@@ -509,6 +512,7 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
   int* pch = reinterpret_cast<int*>(dst + p->stab_off[4]);
   char* iw2 = dst + p->stab_off[5];
   double* smol = reinterpret_cast<double*>(dst + p->stab_off[6]);
+  double* kfac = reinterpret_cast<double*>(dst + p->stab_off[7]);
   int pdef = 0;
   for (int q = 1; q <= 6 && !pdef; ++q)
     if (h.mult_scale_p[q] != 0.0) pdef = q;
@@ -531,6 +535,7 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
     for (int d = 0; d < 3; ++d) {
       sbox[3 * sidx + d] = t.box[d];
       smol[3 * sidx + d] = double(h.M[d]) / t.box[d];
+      kfac[3 * sidx + d] = 2.0 * 3.14159265358979323846 / t.box[d];
     }
     const double dv2v = t.dV * t.dV / t.V;
     for (int c = 0; c < K; ++c) {
@@ -610,7 +615,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   // the count (so that a captured sequence serves any batch)
   c.n = p->batch ? p->n_max : p->n;
   c.ntiles = p->nrun * p->nts;
-  c.sbox = p->sbox;
+  c.smol = p->smol;
   c.soff = p->soff;
   c.tile_start = p->tile_start;
   c.st = p->st;
@@ -641,12 +646,12 @@ int multiply(pswf_plan p, int want_energy, void* data) {
   if (p->pruned) {
     (void)data;   // the pruned spectrum lives in p->spec
     k_multiply_planes<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->spec), mp, p->nkx, p->pch, p->scale,
-                                                           p->sbox, static_cast<const R*>(p->coef_m),
+                                                           p->kfac, static_cast<const R*>(p->coef_m),
                                                            static_cast<const R*>(p->iw2), p->Mh, p->epart,
                                                            want_energy, want_energy ? p->vpart : nullptr);
     return launch_check(p, "k_multiply_planes");
   }
-  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->sbox,
+  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->kfac,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
                                                   p->Mh, p->epart, want_energy,
                                                   want_energy ? p->vpart : nullptr);

@@ -44,7 +44,7 @@ __device__ inline void window_weights2(R t, const WinCoef<R>& wc, R (&w)[P], R (
 
 // rhobar^c(g) = sum_i gphi_i^c W_i(g) + q_i^c gF_i . D_i(g)  (grid2 zeroed before).
 template <typename R, int P>
-__global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__ sbox, const int* __restrict__ soff,
+__global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__ smol, const int* __restrict__ soff,
                             const int* __restrict__ tile_start, const R* __restrict__ st,
                             const uint64_t* __restrict__ scell, const R* __restrict__ sq,
                             const int* __restrict__ sperm, WinCoef<R> wc, const R* __restrict__ gphi,
@@ -52,8 +52,8 @@ __global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__
   const int64_t n = soff[g.B];
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
     const int sidx = find_struct(tile_start, g.nts, g.B, a);
-    const double* box = sbox + 3 * sidx;
-    const R two_h[3] = {R(2.0 * g.M[0] / box[0]), R(2.0 * g.M[1] / box[1]), R(2.0 * g.M[2] / box[2])};
+    const double* mol = smol + 3 * sidx;
+    const R two_h[3] = {R(2.0 * mol[0]), R(2.0 * mol[1]), R(2.0 * mol[2])};
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P];
     window_weights<R, P>(st[a], wc, wx, dx);
     window_weights<R, P>(st[nmax + a], wc, wy, dy);
@@ -94,7 +94,7 @@ __global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__
 // Hessian contraction from Psi (grid), W and D contractions from Psibar
 // (grid2); writes dL/dq and dL/dr in the original atom order.
 template <typename R, int P>
-__global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__ sbox, const int* __restrict__ soff,
+__global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__ smol, const int* __restrict__ soff,
                             const int* __restrict__ tile_start, const R* __restrict__ st,
                             const uint64_t* __restrict__ scell, const R* __restrict__ sq,
                             const int* __restrict__ sperm, WinCoef<R> wc, const R* __restrict__ grid,
@@ -105,8 +105,8 @@ __global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__
   const int64_t n = soff[g.B];
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
     const int sidx = find_struct(tile_start, g.nts, g.B, a);
-    const double* box = sbox + 3 * sidx;
-    const R th[3] = {R(2.0 * g.M[0] / box[0]), R(2.0 * g.M[1] / box[1]), R(2.0 * g.M[2] / box[2])};
+    const double* mol = smol + 3 * sidx;
+    const R th[3] = {R(2.0 * mol[0]), R(2.0 * mol[1]), R(2.0 * mol[2])};
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P], hx[P], hy[P], hz[P];
     window_weights2<R, P>(st[a], wc, wx, dx, hx);
     window_weights2<R, P>(st[nmax + a], wc, wy, dy, hy);

@@ -1,7 +1,8 @@
 // Device kernels of the PSWF-LR hot path (sm_103a).
 //
 // A plan holds B structures (B = 1 for a single system) that share one grid
-// size M and K channels; structure s has its own box (sbox[s][3]) and its
+// size M and K channels; structure s has its own box (tables smol[s][3] =
+// M_d / L_d and kfac[s][3] = 2 pi / L_d) and its
 // atoms are soff[s] .. soff[s+1] - 1 of the caller's arrays.
 // Data layout in HBM (one plan):
 //   grid   real [B][K][M_z][M_y][M_xp], M_xp = 2 (M_x / 2 + 1): the spread
@@ -363,7 +364,7 @@ __device__ inline void block_partials(double e, double vx, double vy, double vz,
 template <typename R>
 __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, MultParams mp,
                                                   const int* __restrict__ pch, const double* __restrict__ scale,
-                                                  const double* __restrict__ sbox, const R* __restrict__ coef,
+                                                  const double* __restrict__ kfac, const R* __restrict__ coef,
                                                   const R* __restrict__ iw2, int iw2_stride,
                                                   double* __restrict__ part, int want_energy,
                                                   double* __restrict__ vpart) {
@@ -380,8 +381,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   const R* iw2z = iw2y + iw2_stride;
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
-  constexpr double kTwoPi = 6.283185307179586476925;
-  const R kf0 = R(kTwoPi / sbox[3 * s]), kf1 = R(kTwoPi / sbox[3 * s + 1]), kf2 = R(kTwoPi / sbox[3 * s + 2]);
+  const R kf0 = R(kfac[3 * s]), kf1 = R(kfac[3 * s + 1]), kf2 = R(kfac[3 * s + 2]);
   const bool even_x = (mp.M[0] % 2) == 0;
   double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
   // Elements of the half spectrum in storage order, spread over the
@@ -440,7 +440,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ data, MultParams mp, int nkx,
                                                          const int* __restrict__ pch,
                                                          const double* __restrict__ scale,
-                                                         const double* __restrict__ sbox, const R* __restrict__ coef,
+                                                         const double* __restrict__ kfac, const R* __restrict__ coef,
                                                          const R* __restrict__ iw2, int iw2_stride,
                                                          double* __restrict__ part, int want_energy,
                                                          double* __restrict__ vpart) {
@@ -455,8 +455,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
   const R* iw2z = iw2y + iw2_stride;
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
-  constexpr double kTwoPi = 6.283185307179586476925;
-  const R kf0 = R(kTwoPi / sbox[0]), kf1 = R(kTwoPi / sbox[1]), kf2 = R(kTwoPi / sbox[2]);
+  const R kf0 = R(kfac[0]), kf1 = R(kfac[1]), kf2 = R(kfac[2]);
   double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
   const int nline = nkx * mp.M[2];
   for (int line = blockIdx.x; line < nline; line += gridDim.x) {
@@ -517,7 +516,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
 // shared memory.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W, with
 // grad_d W = (2 / h_d) dW/ds.  Writes in the original atom order.
 template <typename R, int P>
-__global__ void k_interp_direct(int64_t nmax, Geometry g, const double* __restrict__ sbox,
+__global__ void k_interp_direct(int64_t nmax, Geometry g, const double* __restrict__ smol,
                                 const int* __restrict__ soff, const int* __restrict__ tile_start,
                                 const R* __restrict__ st, const uint64_t* __restrict__ scell,
                                 const R* __restrict__ sq, const int* __restrict__ sperm, WinCoef<R> wc,
@@ -527,8 +526,8 @@ __global__ void k_interp_direct(int64_t nmax, Geometry g, const double* __restri
   const int64_t chan = int64_t(g.M[2]) * g.M[1] * g.Mxp;
   for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
     const int sidx = find_struct(tile_start, g.nts, g.B, a);
-    const R two_hx = R(2.0 * g.M[0] / sbox[3 * sidx]), two_hy = R(2.0 * g.M[1] / sbox[3 * sidx + 1]),
-            two_hz = R(2.0 * g.M[2] / sbox[3 * sidx + 2]);
+    const R two_hx = R(2.0 * smol[3 * sidx]), two_hy = R(2.0 * smol[3 * sidx + 1]),
+            two_hz = R(2.0 * smol[3 * sidx + 2]);
     R wx[P], wy[P], wz[P], dx[P], dy[P], dz[P];
     window_weights<R, P>(st[a], wc, wx, dx);
     window_weights<R, P>(st[nmax + a], wc, wy, dy);

@@ -87,7 +87,7 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   int blocks = 0;
   cudaError_t e = persistent_blocks<P>(k_spread<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
-  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.sbox, c.nmax, c.tile_start, static_cast<const R*>(c.st),
+  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.smol, c.nmax, c.tile_start, static_cast<const R*>(c.st),
                                                              c.scell, static_cast<const R*>(c.sq), wc, kc, kb,
                                                              static_cast<R*>(c.grid));
   ++*nlaunch;
@@ -102,7 +102,7 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   if (!pick_kc_kb<P>(k_interp<R, P>, c.geo.K, [](int k, int b) { return gather_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
     const int blocks = int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_interp_direct<R, P><<<std::max(blocks, 1), kDirectThreads, 0, c.stream>>>(
-        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
         static_cast<const R*>(c.sq), c.sperm, wc, static_cast<const R*>(c.grid), c.zero_coef, c.charges,
         static_cast<R*>(phi), static_cast<R*>(forces));
     ++*nlaunch;
@@ -119,7 +119,7 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   e = persistent_blocks<P>(k_interp<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
   const int threads = kGatherThreads;
-  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.nmax, c.geo, c.sbox, c.soff, c.tile_start,
+  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.nmax, c.geo, c.smol, c.soff, c.tile_start,
                                                       static_cast<const R*>(c.st),
                                                       c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc, kb,
                                                       static_cast<const R*>(c.grid), c.zero_coef, c.charges,
@@ -136,12 +136,12 @@ cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int
   ++*nlaunch;
   if (stage == 0) {
     k_spread_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
-        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
         static_cast<const R*>(c.sq), c.sperm, wc, static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces),
         static_cast<R*>(c.grid2));
   } else {
     k_interp_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
-        c.nmax, c.geo, c.sbox, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+        c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
         static_cast<const R*>(c.sq), c.sperm, wc,
         static_cast<const R*>(c.grid), static_cast<const R*>(c.grid2), c.zero_coef, c.charges, c.gsum, b.g_energy,
         static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces), static_cast<R*>(b.grad_q),

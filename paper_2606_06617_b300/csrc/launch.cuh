@@ -15,7 +15,7 @@ struct LaunchCtx {
   int64_t nmax = 0;        // capacity of the sorted atom arrays
   int64_t n = 0;           // atoms of the last set_points (host copy; kernels read soff[B])
   int ntiles = 0;          // B * nts
-  const double* sbox = nullptr;     // [B][3] box edges
+  const double* smol = nullptr;     // [B][3] M_d / L_d
   const int* soff = nullptr;        // [B + 1] atom offsets per structure (device)
   const int* tile_start = nullptr;
   const void* st = nullptr;         // real [3][nmax]

@@ -144,7 +144,7 @@ __device__ inline void tile_origin(const Geometry& g, int tile, int& ox, int& oy
 // Fills the batch's window rows (values, and scaled derivatives when
 // rows == 6), the packed local start cell and (gather) the original index.
 template <typename R, int P, int ROWS>
-__device__ inline void batch_tables(const Geometry& g, const double* __restrict__ box, int64_t nmax, int b0, int nb,
+__device__ inline void batch_tables(const Geometry& g, const double* __restrict__ mol, int64_t nmax, int b0, int nb,
                                     int ox, int oy, int oz,
                                     const R* __restrict__ st, const uint64_t* __restrict__ scell,
                                     const int* __restrict__ sperm, const WinCoef<R>& wc, R* wts, int* loc,
@@ -156,7 +156,7 @@ __device__ inline void batch_tables(const Geometry& g, const double* __restrict_
     if constexpr (ROWS == 6) {
       R w[P], dw[P];
       window_weights<R, P>(st[d * nmax + b0 + a], wc, w, dw);
-      const R two_h = R(2.0 * g.M[d] / box[d]);
+      const R two_h = R(2.0 * mol[d]);   // 2 / h_d = 2 M_d / L_d
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         row[i] = w[i];
@@ -200,7 +200,7 @@ constexpr size_t spread_smem_bytes(int kc, int kb) {
 }
 
 template <typename R, int P>
-__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, const double* __restrict__ sbox,
+__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, const double* __restrict__ smol,
                                                                    int64_t nmax, const int* __restrict__ tile_start,
                                                                    const R* __restrict__ st,
                                                                    const uint64_t* __restrict__ scell,
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       __syncthreads();   // previous batch done with the tables (and sscale written)
-      batch_tables<R, P, 3>(g, sbox + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
+      batch_tables<R, P, 3>(g, smol + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
       __syncthreads();
       const R qscale = kFixed && use_slot ? R(sscale[cc]) : R(1);
       for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
@@ -385,7 +385,7 @@ __global__ void k_spread_direct(int64_t nmax, Geometry g, const int* __restrict_
 // accumulated with global atomics (zeroed before the launch).
 template <typename R, int P>
 __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax, Geometry g,
-                                                                   const double* __restrict__ sbox,
+                                                                   const double* __restrict__ smol,
                                                                    const int* __restrict__ soff,
                                                                    const int* __restrict__ tile_start,
                                                                    const R* __restrict__ st,
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       if (b0 != a0) __syncthreads();   // previous batch done with the tables
-      batch_tables<R, P, 6>(g, sbox + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
+      batch_tables<R, P, 6>(g, smol + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
       for (int t = threadIdx.x; t < nb * nk; t += blockDim.x) {
         const int a = t / nk, c = t - a * nk;
         qs[a * 8 + c] = sq[int64_t(c0 + c) * nmax + b0 + a];
