@@ -614,6 +614,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   // batch plans: outputs hold n_max rows and every launch is made whatever
   // the count (so that a captured sequence serves any batch)
   c.n = p->batch ? p->n_max : p->n;
+  c.n_set = p->n;
   c.ntiles = p->nrun * p->nts;
   c.smol = p->smol;
   c.soff = p->soff;

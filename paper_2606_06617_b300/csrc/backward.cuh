@@ -13,8 +13,8 @@
 //                       - q_i^c sum_g Psibar^c_g D_i(g)
 //                       - q_i^c (sum_g Psi^c_g H_i(g)) gF_i ].
 // (Per structure s of a batch plan, with E_c, Q_c, a_c of channel g = s K + c.)
-// Kernels here are one thread per sorted atom, reading and writing the grids
-// directly (global atomics for the spread).
+// Kernels here are one thread per (channel, sorted atom), reading and writing
+// the grids directly (global atomics for the spread and for dL/dr).
 #pragma once
 
 #include "stencil.cuh"
@@ -42,7 +42,8 @@ __device__ inline void window_weights2(R t, const WinCoef<R>& wc, R (&w)[P], R (
   }
 }
 
-// rhobar^c(g) = sum_i gphi_i^c W_i(g) + q_i^c gF_i . D_i(g)  (grid2 zeroed before).
+// rhobar^c(g) = sum_i gphi_i^c W_i(g) + q_i^c gF_i . D_i(g)  (grid2 zeroed
+// before).  One thread per (channel, sorted atom), channel-major.
 template <typename R, int P>
 __global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__ smol, const int* __restrict__ soff,
                             const int* __restrict__ tile_start, const R* __restrict__ st,
@@ -50,7 +51,9 @@ __global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__
                             const int* __restrict__ sperm, WinCoef<R> wc, const R* __restrict__ gphi,
                             const R* __restrict__ gF, R* __restrict__ grid2) {
   const int64_t n = soff[g.B];
-  for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n * g.K; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / n);
+    const int64_t a = t - int64_t(c) * n;
     const int sidx = find_struct(tile_start, g.nts, g.B, a);
     const double* mol = smol + 3 * sidx;
     const R two_h[3] = {R(2.0 * mol[0]), R(2.0 * mol[1]), R(2.0 * mol[2])};
@@ -69,30 +72,32 @@ __global__ void k_spread_bw(int64_t nmax, Geometry g, const double* __restrict__
     const int o = sperm[a];
     const R g0 = gF ? gF[3 * int64_t(o)] : R(0), g1 = gF ? gF[3 * int64_t(o) + 1] : R(0),
             g2 = gF ? gF[3 * int64_t(o) + 2] : R(0);
-    for (int c = 0; c < g.K; ++c) {
-      const R qc = sq[int64_t(c) * nmax + a];
-      const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
-      const R v0 = qc * g0, v1 = qc * g1, v2 = qc * g2;
-      R* gc = grid2 + (int64_t(sidx) * g.K + c) * g.M[2] * g.M[1] * g.Mxp;
-      for (int k = 0; k < P; ++k) {
-        const int z = wrap_index(cz + k, g.M[2]);
-        for (int j = 0; j < P; ++j) {
-          const int y = wrap_index(cy + j, g.M[1]);
-          // value(i) = wx[i] * A + dx[i] * B with the (j, k) factors folded in
-          const R A = gp * wy[j] * wz[k] + v1 * dy[j] * wz[k] + v2 * wy[j] * dz[k];
-          const R B = v0 * wy[j] * wz[k];
-          R* row = gc + (int64_t(z) * g.M[1] + y) * g.Mxp;
+    const R qc = sq[int64_t(c) * nmax + a];
+    const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
+    const R v0 = qc * g0, v1 = qc * g1, v2 = qc * g2;
+    R* gc = grid2 + (int64_t(sidx) * g.K + c) * g.M[2] * g.M[1] * g.Mxp;
+    int ix[P];
 #pragma unroll
-          for (int i = 0; i < P; ++i) atomicAdd(row + wrap_index(cx + i, g.M[0]), wx[i] * A + dx[i] * B);
-        }
+    for (int i = 0; i < P; ++i) ix[i] = wrap_index(cx + i, g.M[0]);
+    for (int k = 0; k < P; ++k) {
+      const int z = wrap_index(cz + k, g.M[2]);
+      for (int j = 0; j < P; ++j) {
+        const int y = wrap_index(cy + j, g.M[1]);
+        // value(i) = wx[i] * A + dx[i] * B with the (j, k) factors folded in
+        const R A = gp * wy[j] * wz[k] + v1 * dy[j] * wz[k] + v2 * wy[j] * dz[k];
+        const R B = v0 * wy[j] * wz[k];
+        R* row = gc + (int64_t(z) * g.M[1] + y) * g.Mxp;
+#pragma unroll
+        for (int i = 0; i < P; ++i) atomicAdd(row + ix[i], wx[i] * A + dx[i] * B);
       }
     }
   }
 }
 
-// Gather of the backward: per atom and channel, phi (recomputed), f and the
-// Hessian contraction from Psi (grid), W and D contractions from Psibar
-// (grid2); writes dL/dq and dL/dr in the original atom order.
+// Gather of the backward, one thread per (channel, sorted atom): phi
+// (recomputed), f and the Hessian contraction from Psi (grid), W and D
+// contractions from Psibar (grid2); writes dL/dq and adds the channel's part
+// of dL/dr (grad_r zeroed before) in the original atom order.
 template <typename R, int P>
 __global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__ smol, const int* __restrict__ soff,
                             const int* __restrict__ tile_start, const R* __restrict__ st,
@@ -103,7 +108,9 @@ __global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__
                             const double* __restrict__ gE, const R* __restrict__ gphi, const R* __restrict__ gF,
                             R* __restrict__ grad_q, R* __restrict__ grad_r) {
   const int64_t n = soff[g.B];
-  for (int64_t a = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; a < n; a += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n * g.K; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / n);
+    const int64_t a = t - int64_t(c) * n;
     const int sidx = find_struct(tile_start, g.nts, g.B, a);
     const double* mol = smol + 3 * sidx;
     const R th[3] = {R(2.0 * mol[0]), R(2.0 * mol[1]), R(2.0 * mol[2])};
@@ -125,62 +132,58 @@ __global__ void k_interp_bw(int64_t nmax, Geometry g, const double* __restrict__
     const int o = sperm[a];
     const R g0 = gF ? gF[3 * int64_t(o)] : R(0), g1 = gF ? gF[3 * int64_t(o) + 1] : R(0),
             g2 = gF ? gF[3 * int64_t(o) + 2] : R(0);
-    R gr0 = 0, gr1 = 0, gr2 = 0;
-    for (int c = 0; c < g.K; ++c) {
-      const int gi = sidx * g.K + c;
-      const R* pc = grid + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
-      const R* bc = grid2 + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
-      R ph = 0, f0 = 0, f1 = 0, f2 = 0, sb = 0, b0 = 0, b1 = 0, b2 = 0;
-      R h00 = 0, h11 = 0, h22 = 0, h01 = 0, h02 = 0, h12 = 0;
-      for (int k = 0; k < P; ++k) {
-        const int z = wrap_index(cz + k, g.M[2]);
-        for (int j = 0; j < P; ++j) {
-          const int y = wrap_index(cy + j, g.M[1]);
-          const R* prow = pc + (int64_t(z) * g.M[1] + y) * g.Mxp;
-          const R* brow = bc + (int64_t(z) * g.M[1] + y) * g.Mxp;
-          R s_w = 0, s_d = 0, s_h = 0, t_w = 0, t_d = 0;
+    int ix[P];
 #pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const int x = wrap_index(cx + i, g.M[0]);
-            const R v = prow[x], u = brow[x];
-            s_w += v * wx[i];
-            s_d += v * dx[i];
-            s_h += v * hx[i];
-            t_w += u * wx[i];
-            t_d += u * dx[i];
-          }
-          const R yz = wy[j] * wz[k];
-          ph += s_w * yz;
-          f0 += s_d * yz;
-          f1 += s_w * dy[j] * wz[k];
-          f2 += s_w * wy[j] * dz[k];
-          h00 += s_h * yz;
-          h11 += s_w * hy[j] * wz[k];
-          h22 += s_w * wy[j] * hz[k];
-          h01 += s_d * dy[j] * wz[k];
-          h02 += s_d * wy[j] * dz[k];
-          h12 += s_w * dy[j] * dz[k];
-          sb += t_w * yz;
-          b0 += t_d * yz;
-          b1 += t_w * dy[j] * wz[k];
-          b2 += t_w * wy[j] * dz[k];
+    for (int i = 0; i < P; ++i) ix[i] = wrap_index(cx + i, g.M[0]);
+    const int gi = sidx * g.K + c;
+    const R* pc = grid + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
+    const R* bc = grid2 + int64_t(gi) * g.M[2] * g.M[1] * g.Mxp;
+    R ph = 0, f0 = 0, f1 = 0, f2 = 0, sb = 0, b0 = 0, b1 = 0, b2 = 0;
+    R h00 = 0, h11 = 0, h22 = 0, h01 = 0, h02 = 0, h12 = 0;
+    for (int k = 0; k < P; ++k) {
+      const int z = wrap_index(cz + k, g.M[2]);
+      for (int j = 0; j < P; ++j) {
+        const int y = wrap_index(cy + j, g.M[1]);
+        const R* prow = pc + (int64_t(z) * g.M[1] + y) * g.Mxp;
+        const R* brow = bc + (int64_t(z) * g.M[1] + y) * g.Mxp;
+        R s_w = 0, s_d = 0, s_h = 0, t_w = 0, t_d = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const R v = prow[ix[i]], u = brow[ix[i]];
+          s_w += v * wx[i];
+          s_d += v * dx[i];
+          s_h += v * hx[i];
+          t_w += u * wx[i];
+          t_d += u * dx[i];
         }
+        const R yz = wy[j] * wz[k];
+        ph += s_w * yz;
+        f0 += s_d * yz;
+        f1 += s_w * dy[j] * wz[k];
+        f2 += s_w * wy[j] * dz[k];
+        h00 += s_h * yz;
+        h11 += s_w * hy[j] * wz[k];
+        h22 += s_w * wy[j] * hz[k];
+        h01 += s_d * dy[j] * wz[k];
+        h02 += s_d * wy[j] * dz[k];
+        h12 += s_w * dy[j] * dz[k];
+        sb += t_w * yz;
+        b0 += t_d * yz;
+        b1 += t_w * dy[j] * wz[k];
+        b2 += t_w * wy[j] * dz[k];
       }
-      const R qc = sq[int64_t(c) * nmax + a];
-      const R ge = gE ? R(gE[gi]) : R(0);
-      const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
-      const R phi_c = ph + R(2.0 * zero_coef[gi] * charges[2 * gi]);
-      if (grad_q)
-        grad_q[int64_t(c) * n + o] = ge * phi_c + R(2.0 * zero_coef[gi] * gsum[2 * gi]) + g0 * f0 + g1 * f1 + g2 * f2 + sb;
-      const R w = ge * qc + gp;
-      gr0 -= w * f0 + qc * b0 + qc * (h00 * g0 + h01 * g1 + h02 * g2);
-      gr1 -= w * f1 + qc * b1 + qc * (h01 * g0 + h11 * g1 + h12 * g2);
-      gr2 -= w * f2 + qc * b2 + qc * (h02 * g0 + h12 * g1 + h22 * g2);
     }
+    const R qc = sq[int64_t(c) * nmax + a];
+    const R ge = gE ? R(gE[gi]) : R(0);
+    const R gp = gphi ? gphi[int64_t(c) * n + o] : R(0);
+    const R phi_c = ph + R(2.0 * zero_coef[gi] * charges[2 * gi]);
+    if (grad_q)
+      grad_q[int64_t(c) * n + o] = ge * phi_c + R(2.0 * zero_coef[gi] * gsum[2 * gi]) + g0 * f0 + g1 * f1 + g2 * f2 + sb;
     if (grad_r) {
-      grad_r[3 * int64_t(o)] = gr0;
-      grad_r[3 * int64_t(o) + 1] = gr1;
-      grad_r[3 * int64_t(o) + 2] = gr2;
+      const R w = ge * qc + gp;
+      atomicAdd(grad_r + 3 * int64_t(o), -(w * f0 + qc * b0 + qc * (h00 * g0 + h01 * g1 + h02 * g2)));
+      atomicAdd(grad_r + 3 * int64_t(o) + 1, -(w * f1 + qc * b1 + qc * (h01 * g0 + h11 * g1 + h12 * g2)));
+      atomicAdd(grad_r + 3 * int64_t(o) + 2, -(w * f2 + qc * b2 + qc * (h02 * g0 + h12 * g1 + h22 * g2)));
     }
   }
 }

@@ -68,11 +68,12 @@ __host__ __device__ inline void unpack_cell(uint64_t c, int& x, int& y, int& z) 
 }
 
 // Stencil start (reading C5): u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2
-// - u in [0, 1); i0 wrapped into [0, M).  With u = fl + f (fl = floor(u),
+// - u in [0, 1]; i0 wrapped into [0, M).  With u = fl + f (fl = floor(u),
 // f in [0, 1)): for even P, i0 = fl - P/2 + [f > 0] and t = [f > 0] - f; for
 // odd P = 2k + 1, i0 = fl - k + [f > 1/2] and t = [f > 1/2] + 1/2 - f.  The
-// FP64 work is one multiply, one floor and one subtraction per direction (the
-// FP64 pipe is narrow on this GPU); the rest is integer.
+// FP64 work is one multiply, one floor and one subtraction per direction.
+// (t = 1 only when 1 - f rounds up, f tiny: the stencil and t then still
+// describe u.)
 __device__ inline void locate(double x, double m_over_l, int M, int P, int& i0w, double& t) {
   const double u = x * m_over_l;
   const double fl = floor(u);
@@ -88,10 +89,61 @@ __device__ inline void locate(double x, double m_over_l, int M, int P, int& i0w,
     t = double(c) + 0.5 - f;
   }
   if (t < 0.0) t = 0.0;
-  if (t >= 1.0) t = 0.0;   // f rounded to 1: u sits on a grid point
+  if (t > 1.0) t = 1.0;
   int64_t r = i0 % M;
   if (r < 0) r += M;
   i0w = int(r);
+}
+
+// The same for the FP32 path with a single FP64 instruction (the multiply;
+// the FP64 pipe is narrow on this GPU): u is read from its bits as 32.32
+// fixed point F = floor(u 2^32) plus a sticky flag for nonzero bits below
+// 2^-32, so that fl = F >> 32 and the decisions f > 0, f > 1/2 are exactly
+// those of the FP64 rule; t is one integer difference modulo 2^32 converted
+// once: 2^32 [f > 0] - f 2^32 (even P), 2^31 + 2^32 [f > 1/2] - f 2^32 (odd
+// P), with the bits below 2^-32 dropped (t = 1 where that difference wraps
+// to 0).  |u| >= 2^30 takes the FP64 route.
+__device__ inline void locate_fx(double x, double m_over_l, int M, int P, int& i0w, float& t) {
+  const double u = x * m_over_l;
+  const long long bits = __double_as_longlong(u);
+  const int bexp = int((bits >> 52) & 0x7FF);
+  const int ex = bexp - 1075;   // |u| = m 2^ex
+  if (ex > -23) {
+    double td;
+    locate(x, m_over_l, M, P, i0w, td);
+    t = float(td);
+    return;
+  }
+  const long long m = bexp == 0 ? 0LL : ((bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL);
+  const int sh = ex + 32;
+  long long F;
+  bool sticky;
+  if (sh >= 0) {
+    F = m << sh;
+    sticky = false;
+  } else if (sh > -64) {
+    F = m >> -sh;
+    sticky = (m & ((1LL << -sh) - 1)) != 0;
+  } else {
+    F = 0;
+    sticky = m != 0;
+  }
+  if (bits < 0) F = -F - (sticky ? 1 : 0);
+  const int fl = int(F >> 32);
+  const unsigned fq = unsigned(F & 0xFFFFFFFFLL);
+  int c;
+  unsigned d;
+  if ((P & 1) == 0) {
+    c = (fq != 0u || sticky) ? 1 : 0;
+    d = 0u - fq;
+  } else {
+    c = (fq > 0x80000000u || (fq == 0x80000000u && sticky)) ? 1 : 0;
+    d = 0x80000000u - fq;
+  }
+  t = (d == 0u && c) ? 1.0f : __uint2float_rn(d) * 2.3283064365386963e-10f;   // 2^-32
+  int r = (fl - P / 2 + c) % M;
+  if (r < 0) r += M;
+  i0w = r;
 }
 
 // Structure of an atom: the s with off[s] <= i < off[s + 1] (off has B + 1
@@ -156,13 +208,19 @@ __global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __
     int i0[3];
     for (int d = 0; d < 3; ++d) {
       double x = double(pos[3 * i + d]);
-      if (!isfinite(x)) {
+      if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) {   // inf or nan
         atomicCAS(err, 0, -6);
         x = 0.0;
       }
-      double t;
-      locate(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
-      tmp_t[d * nmax + i] = R(t);
+      if constexpr (sizeof(R) == 4) {
+        float t;
+        locate_fx(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
+        tmp_t[d * nmax + i] = t;
+      } else {
+        double t;
+        locate(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
+        tmp_t[d * nmax + i] = R(t);
+      }
     }
     const int tile = s * g.nts + ((i0[2] / kTile) * g.ntile[1] + i0[1] / kTile) * g.ntile[0] + i0[0] / kTile;
     tile_of[i] = tile;
@@ -192,77 +250,90 @@ __global__ void k_scatter(int64_t nmax, const R* __restrict__ q, Geometry g, con
 // The single-structure set_points writes its atom count here (soff = {0, n}).
 __global__ void k_set_count(int* __restrict__ soff, int n);
 
-// Per-(structure, block) FP64 partial sums of q and q^2 per channel over the
+// Per-thread sums of q and q^2.  FP32 charges: double-float sums (a float
+// sum and its running rounding error by TwoSum; q^2 split exactly into
+// v*v and fma(v, v, -v*v)), converted to FP64 once per thread, so the FP64
+// pipe (narrow on this GPU) only sees the reductions across threads.  FP64
+// charges: FP64 sums.
+template <typename R>
+struct ChargeAcc {
+  double a = 0.0, b = 0.0;
+  __device__ void add(R v) {
+    const double d = double(v);
+    a += d;
+    b += d * d;
+  }
+  __device__ double sum() const { return a; }
+  __device__ double sumsq() const { return b; }
+};
+template <>
+struct ChargeAcc<float> {
+  float a = 0.f, ae = 0.f, b = 0.f, be = 0.f;
+  __device__ static void two_sum(float& s, float& e, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ void add(float v) {
+    const float p = v * v;
+    be += fmaf(v, v, -p);
+    two_sum(a, ae, v);
+    two_sum(b, be, p);
+  }
+  __device__ double sum() const { return double(a) + double(ae); }
+  __device__ double sumsq() const { return double(b) + double(be); }
+};
+
+// Block sums of the two per-thread values, written by thread 0.
+__device__ inline void charge_block_sums(double s1, double s2, double* __restrict__ out) {
+  __shared__ double sh[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = s1;
+    sh[1][wid] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      x += sh[0][w];
+      y += sh[1][w];
+    }
+    out[0] = x;
+    out[1] = y;
+  }
+  __syncthreads();
+}
+
+// Per-(structure, block) partial sums of q and q^2 per channel over the
 // structure's atoms (caller order, q [K][n]): blockIdx.y = structure,
 // part[((s * gridDim.x + blk) * K + c) * 2 + {0, 1}].
 template <typename R>
 __global__ void k_charge_partials_seg(const R* __restrict__ q, int K, int B, const int* __restrict__ soff,
                                       double* __restrict__ part) {
-  __shared__ double sh[2][32];
   const int s = blockIdx.y;
   const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
   for (int c = 0; c < K; ++c) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a1; i += int64_t(gridDim.x) * blockDim.x) {
-      const double v = double(q[c * n + i]);
-      s1 += v;
-      s2 += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s1 += __shfl_down_sync(0xffffffffu, s1, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-      sh[0][wid] = s1;
-      sh[1][wid] = s2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double x = 0.0, y = 0.0;
-      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
-        x += sh[0][w];
-        y += sh[1][w];
-      }
-      const size_t o = ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2;
-      part[o] = x;
-      part[o + 1] = y;
-    }
-    __syncthreads();
+    ChargeAcc<R> acc;
+    for (int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a1; i += int64_t(gridDim.x) * blockDim.x)
+      acc.add(q[c * n + i]);
+    charge_block_sums(acc.sum(), acc.sumsq(), part + ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2);
   }
 }
 
-// Per-block FP64 partial sums of q and q^2 per channel: part[(blk * K + c) * 2 + {0,1}].
+// Per-block partial sums of q and q^2 per channel: part[(blk * K + c) * 2 + {0,1}].
 template <typename R>
 __global__ void k_charge_partials(int64_t n, const R* __restrict__ q, int K, double* __restrict__ part) {
-  __shared__ double sh[2][32];
   for (int c = 0; c < K; ++c) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-      const double v = double(q[c * n + i]);
-      s1 += v;
-      s2 += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s1 += __shfl_down_sync(0xffffffffu, s1, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-      sh[0][wid] = s1;
-      sh[1][wid] = s2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < int(blockDim.x >> 5); ++w) {
-        a += sh[0][w];
-        b += sh[1][w];
-      }
-      part[(size_t(blockIdx.x) * K + c) * 2 + 0] = a;
-      part[(size_t(blockIdx.x) * K + c) * 2 + 1] = b;
-    }
-    __syncthreads();
+    ChargeAcc<R> acc;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+      acc.add(q[c * n + i]);
+    charge_block_sums(acc.sum(), acc.sumsq(), part + (size_t(blockIdx.x) * K + c) * 2);
   }
 }
 
@@ -287,17 +358,42 @@ __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part,
                                const double* __restrict__ vpart, double* __restrict__ virial);
 
 // ---- multiplier helpers ----------------------------------------------------------
-// S_p on one piece and dS/ds by Horner (runtime degree, coefficients in
+// S_p on one piece by Horner, and dS/ds (runtime degree, coefficients in
 // global memory).
 template <typename R>
-__device__ inline void mult_horner(const R* __restrict__ cs, int deg, R sv, R& S, R& dS) {
-  S = cs[deg];
-  dS = R(0);
-  for (int nn = deg - 1; nn >= 0; --nn) {
-    dS = dS * sv + S;
-    S = S * sv + cs[nn];
-  }
+__device__ inline R mult_horner(const R* __restrict__ cs, int deg, R sv) {
+  R S = cs[deg];
+  for (int nn = deg - 1; nn >= 0; --nn) S = S * sv + cs[nn];
+  return S;
 }
+template <typename R>
+__device__ inline R mult_horner_d(const R* __restrict__ cs, int deg, R sv) {
+  R dS = R(deg) * cs[deg];
+  for (int nn = deg - 1; nn >= 1; --nn) dS = dS * sv + R(nn) * cs[nn];
+  return dS;
+}
+
+// Per-thread energy accumulator.  FP64 sums are plain; FP32 terms are summed
+// with Kahan compensation (error about one FP32 rounding of the total,
+// independent of the count) and handed to the FP64 block reduction, which
+// keeps FP64 arithmetic, narrow on this GPU, out of the per-mode loop.
+template <typename R>
+struct EnergyAcc {
+  double s = 0.0;
+  __device__ void add(double x) { s += x; }
+  __device__ double value() const { return s; }
+};
+template <>
+struct EnergyAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ double value() const { return double(s) - double(c); }
+};
 
 // Phi-hat_p / scale_p from its smooth part: the singular factor per p.
 template <typename R>
@@ -383,13 +479,26 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   const R inv_kc = R(mp.inv_kc);
   const R kf0 = R(kfac[3 * s]), kf1 = R(kfac[3 * s + 1]), kf2 = R(kfac[3 * s + 2]);
   const bool even_x = (mp.M[0] % 2) == 0;
-  double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+  EnergyAcc<R> e;
+  double vx = 0.0, vy = 0.0, vz = 0.0;
   // Elements of the half spectrum in storage order, spread over the
-  // channel's blocks (rows of small grids are shorter than a block).
+  // channel's blocks (rows of small grids are shorter than a block).  The
+  // element's (ix, iy, iz) advance by the grid stride's own digits with
+  // carries: no divisions in the loop.
   const int64_t nel = int64_t(nrow) * mp.Mxh;
-  for (int64_t el = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; el < nel; el += int64_t(gridDim.x) * blockDim.x) {
-    const int row = int(el / mp.Mxh), ix = int(el - int64_t(row) * mp.Mxh);
-    const int iy = row % mp.M[1], iz = row / mp.M[1];
+  const int64_t el0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int ix, iy, iz, sx, sy, sz;
+  {
+    const int64_t r0 = el0 / mp.Mxh, rs = stride / mp.Mxh;
+    ix = int(el0 - r0 * mp.Mxh);
+    sx = int(stride - rs * mp.Mxh);
+    iz = int(r0 / mp.M[1]);
+    iy = int(r0 - int64_t(iz) * mp.M[1]);
+    sz = int(rs / mp.M[1]);
+    sy = int(rs - int64_t(sz) * mp.M[1]);
+  }
+  for (int64_t el = el0; el < nel; el += stride) {
     const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
     const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
     const R ky = kf1 * R(my), kz = kf2 * R(mz);
@@ -398,38 +507,47 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
     Cplx<R>* dp = d + el;
     if (!(k2 < kc2) || k2 == R(0)) {
       *dp = Cplx<R>{R(0), R(0)};
-      continue;
-    }
-    const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
-    const R k = sqrt(k2);
-    R u = k * inv_kc;
-    if (u >= R(1)) u = R(1) - R(1e-7);
-    int seg = int(u * R(kMultSeg));
-    if (seg > kMultSeg - 1) seg = kMultSeg - 1;
-    const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
-    const R* cs = cf + seg * (mp.deg + 1);
-    R S, dS;
-    mult_horner(cs, mp.deg, sv, S, dS);
-    const R phi = mult_value(p, S, k, k2, u);
-    const R G = phi * sc * iw2x[ix] * iw2y[ay] * iw2z[az];
-    Cplx<R> v = *dp;
-    if (want_energy) {
-      const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
-      const double em = double((edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y));
-      e += em;
-      if (vpart) {
-        const double dl = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
-        vx += em * dl * double(kx * kx);
-        vy += em * dl * double(ky * ky);
-        vz += em * dl * double(kz * kz);
+    } else {
+      const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
+      const R k = sqrt(k2);
+      R u = k * inv_kc;
+      if (u >= R(1)) u = R(1) - R(1e-7);
+      int seg = int(u * R(kMultSeg));
+      if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+      const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+      const R* cs = cf + seg * (mp.deg + 1);
+      const R S = mult_horner(cs, mp.deg, sv);
+      const R phi = mult_value(p, S, k, k2, u);
+      const R G = phi * sc * iw2x[ix] * iw2y[ay] * iw2z[az];
+      Cplx<R> v = *dp;
+      if (want_energy) {
+        const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
+        const R em = (edge ? R(0.5) : R(1)) * G * (v.x * v.x + v.y * v.y);
+        e.add(em);
+        if (vpart) {
+          const R dS = mult_horner_d(cs, mp.deg, sv);
+          const double dl = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
+          vx += double(em) * dl * double(kx * kx);
+          vy += double(em) * dl * double(ky * ky);
+          vz += double(em) * dl * double(kz * kz);
+        }
       }
+      v.x *= G;
+      v.y *= G;
+      *dp = v;
     }
-    v.x *= G;
-    v.y *= G;
-    *dp = v;
+    ix += sx;
+    const int carry = ix >= mp.Mxh;
+    if (carry) ix -= mp.Mxh;
+    iy += sy + carry;
+    if (iy >= mp.M[1]) {
+      iy -= mp.M[1];
+      ++iz;
+    }
+    iz += sz;
   }
   if (!want_energy) return;
-  block_partials(e, vx, vy, vz, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
+  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
 }
 
 // Multiplier on the pruned spectrum of a single structure: layout
@@ -456,7 +574,8 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
   const R kf0 = R(kfac[0]), kf1 = R(kfac[1]), kf2 = R(kfac[2]);
-  double e = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
+  EnergyAcc<R> e;
+  double vx = 0.0, vy = 0.0, vz = 0.0;
   const int nline = nkx * mp.M[2];
   for (int line = blockIdx.x; line < nline; line += gridDim.x) {
     const int ix = line / mp.M[2], iz = line - ix * mp.M[2];
@@ -486,20 +605,20 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
       if (seg > kMultSeg - 1) seg = kMultSeg - 1;
       const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
       const R* cs = cf + seg * (mp.deg + 1);
-      R S, dS;
-      mult_horner(cs, mp.deg, sv, S, dS);
+      const R S = mult_horner(cs, mp.deg, sv);
       const R phi = mult_value(p, S, k, k2, u);
       const int ay = my < 0 ? -my : my;
       const R G = phi * wxz * iw2y[ay];
       Cplx<R> v = dl[iy];
       if (want_energy) {
-        const double em = double(wedge * G * (v.x * v.x + v.y * v.y));
-        e += em;
+        const R em = wedge * G * (v.x * v.x + v.y * v.y);
+        e.add(em);
         if (vpart) {
+          const R dS = mult_horner_d(cs, mp.deg, sv);
           const double dlg = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
-          vx += em * dlg * double(kx * kx);
-          vy += em * dlg * double(ky * ky);
-          vz += em * dlg * double(kz * kz);
+          vx += double(em) * dlg * double(kx * kx);
+          vy += double(em) * dlg * double(ky * ky);
+          vz += double(em) * dlg * double(kz * kz);
         }
       }
       v.x *= G;
@@ -508,7 +627,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
     }
   }
   if (!want_energy) return;
-  block_partials(e, vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
+  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
 }
 
 // ---- interpolation, direct from global memory (fallback kernel) ---------------------

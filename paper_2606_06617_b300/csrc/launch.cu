@@ -132,7 +132,8 @@ template <int P>
 cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
   const WinCoef<R> wc = win_coef(c);
-  const int blocks = std::max(1, int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32)));
+  const int64_t work = std::max<int64_t>(1, c.nmax * c.geo.K);
+  const int blocks = int(std::min<int64_t>((work + kDirectThreads - 1) / kDirectThreads, 148 * 64));
   ++*nlaunch;
   if (stage == 0) {
     k_spread_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
@@ -140,6 +141,10 @@ cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int
         static_cast<const R*>(c.sq), c.sperm, wc, static_cast<const R*>(b.g_phi), static_cast<const R*>(b.g_forces),
         static_cast<R*>(c.grid2));
   } else {
+    if (b.grad_pos) {
+      const cudaError_t e = cudaMemsetAsync(b.grad_pos, 0, size_t(c.n_set) * 3 * sizeof(R), c.stream);
+      if (e != cudaSuccess) return e;
+    }
     k_interp_bw<R, P><<<blocks, kDirectThreads, 0, c.stream>>>(
         c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
         static_cast<const R*>(c.sq), c.sperm, wc,

@@ -13,7 +13,8 @@ namespace pswf {
 struct LaunchCtx {
   Geometry geo;
   int64_t nmax = 0;        // capacity of the sorted atom arrays
-  int64_t n = 0;           // atoms of the last set_points (host copy; kernels read soff[B])
+  int64_t n = 0;           // output rows: atoms of the last set_points (batch plans: n_max)
+  int64_t n_set = 0;       // atoms of the last set_points
   int ntiles = 0;          // B * nts
   const double* smol = nullptr;     // [B][3] M_d / L_d
   const int* soff = nullptr;        // [B + 1] atom offsets per structure (device)

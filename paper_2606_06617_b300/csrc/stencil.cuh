@@ -141,10 +141,11 @@ __device__ inline void tile_origin(const Geometry& g, int tile, int& ox, int& oy
   oz = tz * kTile;
 }
 
-// Fills the batch's window rows (values, and scaled derivatives when
-// rows == 6), the packed local start cell and (gather) the original index.
+// Fills the batch's window rows (values, and derivatives times two_h[d] =
+// 2 / h_d when rows == 6), the packed local start cell and (gather) the
+// original index.
 template <typename R, int P, int ROWS>
-__device__ inline void batch_tables(const Geometry& g, const double* __restrict__ mol, int64_t nmax, int b0, int nb,
+__device__ inline void batch_tables(const Geometry& g, const R* two_h, int64_t nmax, int b0, int nb,
                                     int ox, int oy, int oz,
                                     const R* __restrict__ st, const uint64_t* __restrict__ scell,
                                     const int* __restrict__ sperm, const WinCoef<R>& wc, R* wts, int* loc,
@@ -156,11 +157,11 @@ __device__ inline void batch_tables(const Geometry& g, const double* __restrict_
     if constexpr (ROWS == 6) {
       R w[P], dw[P];
       window_weights<R, P>(st[d * nmax + b0 + a], wc, w, dw);
-      const R two_h = R(2.0 * mol[d]);   // 2 / h_d = 2 M_d / L_d
+      const R th = two_h[d];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         row[i] = w[i];
-        row[3 * PW + i] = dw[i] * two_h;
+        row[3 * PW + i] = dw[i] * th;
       }
     } else {
       R w[P];
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, 
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       __syncthreads();   // previous batch done with the tables (and sscale written)
-      batch_tables<R, P, 3>(g, smol + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
+      batch_tables<R, P, 3>(g, nullptr, nmax, b0, nb, ox, oy, oz, st, scell, nullptr, wc, wts, loc, nullptr);
       __syncthreads();
       const R qscale = kFixed && use_slot ? R(sscale[cc]) : R(1);
       for (int ab = warp * sl.apw; ab < nb; ab += nwarp * sl.apw) {
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
   R* qs = wts + kb * 6 * PW;                                                     // [kb][8]
   int* loc = reinterpret_cast<int*>(qs + kb * 8);
   int* perm = loc + kb;
+  __shared__ R two_h[3];   // 2 / h_d = 2 M_d / L_d of the item's structure
   const Slots sl = Slots::template make<G, NS>(kc);
   const int lane = sl.lane, warp = sl.warp, nwarp = sl.nwarp, j = sl.j, cc = sl.cc;
   const int nchunk = (g.K + kc - 1) / kc;
@@ -422,6 +424,8 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
     const int gc0 = sidx * g.K + c0;   // first grid channel of the item
     int ox, oy, oz;
     tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
+    // (every thread is past the previous item's last table fill)
+    if (threadIdx.x < 3) two_h[threadIdx.x] = R(2.0 * smol[3 * sidx + threadIdx.x]);
     __syncthreads();   // the previous item's reads of the region and tables are done
     {
       const int gx = lane < S ? wrap_index(ox + lane, g.M[0]) : 0;
@@ -445,7 +449,7 @@ __global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax
     for (int b0 = a0; b0 < a1; b0 += kb) {
       const int nb = min(kb, a1 - b0);
       if (b0 != a0) __syncthreads();   // previous batch done with the tables
-      batch_tables<R, P, 6>(g, smol + 3 * sidx, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
+      batch_tables<R, P, 6>(g, two_h, nmax, b0, nb, ox, oy, oz, st, scell, sperm, wc, wts, loc, perm);
       for (int t = threadIdx.x; t < nb * nk; t += blockDim.x) {
         const int a = t / nk, c = t - a * nk;
         qs[a * 8 + c] = sq[int64_t(c0 + c) * nmax + b0 + a];
