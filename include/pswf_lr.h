@@ -79,7 +79,19 @@ typedef struct {
   int64_t workspace_bytes; /* device bytes pswf_plan_set_workspace wants */
   int B;                   /* structures per call (1 for single-structure plans) */
   int batch;               /* 1 for plans made by pswf_batch_plan_create */
+  int transform;           /* pswf_plan_info: PSWF_TRANSFORM_* of the plan (0 from pswf_plan_params) */
+  int nkx;                 /* pruned transforms: x frequencies 0..nkx-1 kept (others are out of band) */
 } pswf_info;
+
+/* Transform of a plan.  FULL: cuFFT 3-D real transforms of every structure
+ * slot.  PRUNED: single-structure plans whose band |k| < k_c reaches only
+ * kx < nkx <= 3/4 (Mx/2 + 1): 1-D transforms along x, then 2-D (z, y)
+ * transforms of the nkx planes only (cuFFT).  PRUNED_X: the same with the
+ * x passes done by this library's kernels (FP32, Mx = 32 N1 with
+ * 2 <= N1 <= 16), which write and read only the nkx planes. */
+#define PSWF_TRANSFORM_FULL 0
+#define PSWF_TRANSFORM_PRUNED 1
+#define PSWF_TRANSFORM_PRUNED_X 2
 
 typedef struct pswf_plan_s* pswf_plan;
 

@@ -26,6 +26,7 @@ UNITS = [
     ("launch.cu", "launch_f64.o", ["-DPSWF_REAL=double"]),
     ("planner.cpp", "planner.o", []),
     ("server.cu", "server.o", []),
+    ("fft_x.cu", "fft_x.o", []),
 ]
 
 

@@ -15,6 +15,7 @@
 #include <thread>
 #include <vector>
 
+#include "fft_x.hpp"
 #include "internal.hpp"
 #include "kernels.cuh"
 #include "launch.cuh"
@@ -341,6 +342,10 @@ struct pswf_plan_s {
   int nkx = 0;
   cufftHandle pr_r2c = 0, pr_c2r = 0, pr_2d = 0;
   void* spec = nullptr;      // complex [K][Mxh][Mz][My] (pruned plans)
+  // FP32 pruned plans with Mx = 32 N1: the x passes are the kernels of
+  // fft_x.cu (only the kx < nkx planes written and read) instead of cuFFT
+  bool xfft = false;
+  void* xtw = nullptr;       // their twiddle table (float2)
   size_t fft_work_bytes = 0;
   // host staging for pswf_compute_host
   double* h_pin = nullptr;
@@ -357,6 +362,7 @@ struct pswf_plan_s {
   std::vector<StageRec> recs;
   std::vector<cudaEvent_t> pool;
   int64_t launches[PSWF_NSTAGE] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int cur_stage = PSWF_STAGE_OTHER;   // innermost open StageScope
 };
 
 namespace {
@@ -389,15 +395,17 @@ cudaEvent_t take_event(pswf_plan p) {
 // measurement is enabled.
 struct StageScope {
   pswf_plan p;
-  int stage;
+  int stage, outer;
   cudaEvent_t a = nullptr;
-  StageScope(pswf_plan p_, int stage_) : p(p_), stage(stage_) {
+  StageScope(pswf_plan p_, int stage_) : p(p_), stage(stage_), outer(p_->cur_stage) {
+    p->cur_stage = stage;
     if (p->prof_on) {
       a = take_event(p);
       cudaEventRecord(a, p->stream);
     }
   }
   ~StageScope() {
+    p->cur_stage = outer;
     if (a) {
       cudaEvent_t b = take_event(p);
       cudaEventRecord(b, p->stream);
@@ -472,6 +480,7 @@ int64_t layout(pswf_plan p, char* base) {
   p->virial = vir ? reinterpret_cast<double*>(take(BK * 3 * 8)) : nullptr;
   p->err = reinterpret_cast<int*>(take(4));
   p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
+  p->xtw = p->xfft ? take(int64_t(xfft_table_size(h.M[0])) * 8) : nullptr;
   p->stab_bytes = stab_layout(p);
   char* st = take(p->stab_bytes);
   p->stab = st;
@@ -567,6 +576,11 @@ int upload_tables(pswf_plan p) {
   int rc;
   if (p->real_size == 4) {
     if ((rc = upload(p, p->coef_m, to_real<float>(h.coef_m), "upload coef"))) return rc;
+    if (p->xfft) {
+      std::vector<float> tw;
+      xfft_twiddles(h.M[0], tw);
+      if ((rc = upload(p, p->xtw, tw, "upload x twiddles"))) return rc;
+    }
   } else {
     if ((rc = upload(p, p->coef_m, h.coef_m, "upload coef"))) return rc;
   }
@@ -583,10 +597,8 @@ int upload_tables(pswf_plan p) {
 
 int attach_fft_work(pswf_plan p) {
   if (!p->fft_made) return PSWF_OK;
-  if (p->pruned && (cufftSetWorkArea(p->pr_r2c, p->fft_work) != CUFFT_SUCCESS ||
-                    cufftSetWorkArea(p->pr_c2r, p->fft_work) != CUFFT_SUCCESS ||
-                    cufftSetWorkArea(p->pr_2d, p->fft_work) != CUFFT_SUCCESS))
-    return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
+  for (cufftHandle hd : {p->pr_r2c, p->pr_c2r, p->pr_2d})
+    if (hd && cufftSetWorkArea(hd, p->fft_work) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftSetWorkArea failed");
   for (size_t i = 0; i < p->fwd.size(); ++i)
     if (cufftSetWorkArea(p->fwd[i], p->fft_work) != CUFFT_SUCCESS ||
         cufftSetWorkArea(p->inv[i], p->fft_work) != CUFFT_SUCCESS)
@@ -670,7 +682,8 @@ int fft_exec_pruned(pswf_plan p, void* data, bool forward) {
   const int64_t spec_ch = int64_t(Mxh) * plane;                 // complex per channel
   const int64_t grid_ch = plane * 2 * Mxh;                       // real per channel
   for (cufftHandle hd : {p->pr_r2c, p->pr_c2r, p->pr_2d})
-    if (cufftSetStream(hd, p->stream) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftSetStream failed");
+    if (hd && cufftSetStream(hd, p->stream) != CUFFT_SUCCESS)
+      return set_err(p, PSWF_ECUFFT, "cufftSetStream failed");
   cufftResult r = CUFFT_SUCCESS;
   const bool f32 = p->real_size == 4;
   auto cplx = [&](int c) -> void* {
@@ -683,6 +696,26 @@ int fft_exec_pruned(pswf_plan p, void* data, bool forward) {
     return cufftExecZ2Z(p->pr_2d, static_cast<cufftDoubleComplex*>(cplx(c)), static_cast<cufftDoubleComplex*>(cplx(c)),
                         dir);
   };
+  if (p->xfft) {
+    // x passes by the pruned kernels: planes kx >= nkx are never touched
+    if (forward) {
+      int rc = cuda_check(p, launch_rfft_x(static_cast<const float*>(data), h.M[0], h.M[1], h.M[2], h.K, p->nkx,
+                                           p->xtw, p->spec, p->stream), "k_rfft_x");
+      if (rc) return rc;
+      ++p->launches[p->cur_stage];
+      for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
+    } else {
+      for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
+      if (r == CUFFT_SUCCESS) {
+        int rc = cuda_check(p, launch_irfft_x(p->spec, h.M[0], h.M[1], h.M[2], h.K, p->nkx, p->xtw,
+                                              static_cast<float*>(data), p->stream), "k_irfft_x");
+        if (rc) return rc;
+        ++p->launches[p->cur_stage];
+      }
+    }
+    if (r != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftExec failed (" + std::to_string(int(r)) + ")");
+    return PSWF_OK;
+  }
   if (forward) {
     for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c)
       r = f32 ? cufftExecR2C(p->pr_r2c, static_cast<cufftReal*>(real(c)), static_cast<cufftComplex*>(cplx(c)))
@@ -947,6 +980,7 @@ int make_fft(pswf_plan p) {
     const double kmax_idx = h.k_c * h.box[0] / (2.0 * 3.14159265358979323846);
     p->nkx = int(std::min<double>(Mxh, std::floor(kmax_idx) + 2));
     p->pruned = p->nkx * 4 <= Mxh * 3 && h.M[0] >= 64;
+    p->xfft = p->pruned && p->real_size == 4 && xfft_supported(h.M[0]);
   }
   if (p->pruned) {
     const cufftType c2c = p->real_size == 4 ? CUFFT_C2C : CUFFT_Z2Z;
@@ -956,12 +990,15 @@ int make_fft(pswf_plan p) {
     int n2[2] = {h.M[2], h.M[1]};
     size_t w1 = 0, w2 = 0, w3 = 0;
     for (cufftHandle* hd : {&p->pr_r2c, &p->pr_c2r, &p->pr_2d}) {
+      if (p->xfft && hd != &p->pr_2d) continue;
       if (cufftCreate(hd) != CUFFT_SUCCESS) return set_err(p, PSWF_ECUFFT, "cufftCreate failed");
       cufftSetAutoAllocation(*hd, 0);
     }
     // rows (z, y) of the grid -> spectrum element (kx, z, y) at kx * plane + (z My + y)
-    const cufftResult r1 = cufftMakePlanMany(p->pr_r2c, 1, n1, er, 1, 2 * Mxh, ec, plane, 1, tf, plane, &w1);
-    const cufftResult r2 = cufftMakePlanMany(p->pr_c2r, 1, n1, ec, plane, 1, er, 1, 2 * Mxh, ti, plane, &w2);
+    const cufftResult r1 =
+        p->xfft ? CUFFT_SUCCESS : cufftMakePlanMany(p->pr_r2c, 1, n1, er, 1, 2 * Mxh, ec, plane, 1, tf, plane, &w1);
+    const cufftResult r2 =
+        p->xfft ? CUFFT_SUCCESS : cufftMakePlanMany(p->pr_c2r, 1, n1, ec, plane, 1, er, 1, 2 * Mxh, ti, plane, &w2);
     const cufftResult r3 = cufftMakePlanMany(p->pr_2d, 2, n2, n2, 1, plane, n2, 1, plane, c2c, p->nkx, &w3);
     if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS || r3 != CUFFT_SUCCESS)
       return set_err(p, PSWF_ECUFFT, "cufftMakePlanMany (pruned) failed");
@@ -1232,6 +1269,8 @@ int pswf_plan_info(pswf_plan pl, pswf_info* out) {
   out->workspace_bytes = pl->ws_bytes;
   out->B = pl->B;
   out->batch = pl->batch ? 1 : 0;
+  out->transform = pl->xfft ? PSWF_TRANSFORM_PRUNED_X : pl->pruned ? PSWF_TRANSFORM_PRUNED : PSWF_TRANSFORM_FULL;
+  out->nkx = pl->pruned ? pl->nkx : 0;
   return PSWF_OK;
 }
 

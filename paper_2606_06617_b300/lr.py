@@ -18,6 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
 
 PSWF_FLAG_BACKWARD = 1
 PSWF_FLAG_VIRIAL = 2
+PSWF_TRANSFORM_FULL = 0
+PSWF_TRANSFORM_PRUNED = 1
+PSWF_TRANSFORM_PRUNED_X = 2
 
 
 class PswfError(RuntimeError):
@@ -41,7 +44,8 @@ class PswfInfo(ctypes.Structure):
                 ("P", ctypes.c_int), ("K", ctypes.c_int), ("precision", ctypes.c_int),
                 ("deg_window", ctypes.c_int), ("deg_mult", ctypes.c_int), ("flags", ctypes.c_int),
                 ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("B", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("B", ctypes.c_int), ("batch", ctypes.c_int), ("transform", ctypes.c_int),
+                ("nkx", ctypes.c_int)]
 
 
 MAX_BUCKETS = 16
