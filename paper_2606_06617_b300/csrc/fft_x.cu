@@ -1,21 +1,26 @@
 // Pruned real transforms along x (FP32), see fft_x.hpp.
 //
 // One warp transforms one complex row of length N = 32 N1 holding two real
-// grid rows (real and imaginary parts).  Lane l starts with the N1 samples
-// x[brev5(l) + 32 m], m < N1, and the transform is the four-step split
-// N = N1 x 32:
-//   1. an N1-point DFT over m in registers (radix 2, odd remainders directly,
-//      twiddles compile-time constants),
-//   2. the twiddle e^{-+2 pi i brev5(l) k1 / N},
-//   3. a 32-point transform across the lanes (decimation in time: the lanes
-//      hold bit-reversed inputs, five butterfly stages of xor shuffles),
-// after which lane l, register k1 holds X[k1 + N1 l].  The two real rows'
-// spectra are split from X[k] and X[N - k] (one more shuffle), and a CTA of
-// 16 warps (32 rows of one (c, z) line) stages the kx < nkx part as
-// [kx][y] in shared memory so that each kx is one 256-byte store.  The
-// inverse runs the same steps backwards: staged loads, the Hermitian
-// completion of both rows' spectra packed as A + i B, the inverse transform,
-// and the two real rows as the real and imaginary parts.
+// grid rows (real and imaginary parts), as the four-step split N = N1 x 32:
+// an N1-point DFT in registers (radix 2, odd remainders directly, twiddles
+// compile-time constants), a twiddle, and a 32-point DFT across the lanes
+// (decimation in frequency, five butterfly stages of xor shuffles; each lane
+// applies v' = (v + s p) w with its own sign s and pre-signed twiddle w, so
+// that the lanes' outputs come in bit-reversed order r = brev5(lane)).
+//
+// Forward (coalesced loads): lane l holds x[l + 32 m]; registers first, then
+// the twiddle e^{-2 pi i l k1 / N}, then the lanes: register k1 of lane l
+// ends as X[k1 + N1 r].  The two real rows' spectra are split from X[k] and
+// X[N - k] (one more shuffle) and staged per row.  Inverse (coalesced
+// stores): lane l takes X[n1 + N1 l] from the staged rows; lanes first, then
+// the twiddle e^{+2 pi i n1 r / N}, then registers: register k1 of lane l
+// ends as x[32 k1 + r].
+//
+// A CTA of 8 warps covers 16 rows of one (c, z) line; the staged spectra
+// are [y][pos(kx)] with pos(k) = k + k / N1 for even N1 (so that the lanes'
+// strided accesses fall in distinct banks) and an odd row stride, and each
+// kx plane gets one 128-byte store (forward) or load (inverse).  Planes
+// kx >= nkx are neither written nor read.
 #include "fft_x.hpp"
 
 #include <cmath>
@@ -25,8 +30,8 @@
 namespace pswf {
 namespace {
 
-constexpr int kXThreads = 512;     // 16 warps, two rows each: 32 rows of a (c, z) line
-constexpr int kStage = 33;         // float2 per kx in the staging tile (32 rows + 1)
+constexpr int kRows = 16;                // rows of a (c, z) line per CTA
+constexpr int kXThreads = 16 * kRows;    // a warp per pair of rows
 constexpr unsigned kFull = 0xffffffffu;
 
 // cos and sin of 2 pi j / n by their Taylor series after reducing the angle
@@ -129,165 +134,185 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[N]) {
   }
 }
 
-// Length-32 N1 transform of a warp's row (layout in the file comment).
+// The 32-point DFT across the lanes (bit-reversed output order); stw are the
+// five stages' pre-signed twiddles.
 template <int N1, bool INV>
-__device__ __forceinline__ void warp_fft(float2 (&v)[N1], const float2* __restrict__ tw, int lane) {
-  constexpr int N = 32 * N1;
-  dft_reg<N1, INV>(v);
+__device__ __forceinline__ void lane_dft(float2 (&v)[N1], const float2* __restrict__ stw, int lane) {
 #pragma unroll
-  for (int k1 = 1; k1 < N1; ++k1) {
-    float2 w = __ldg(tw + k1 * 32 + lane);
+  for (int st = 0; st < 5; ++st) {
+    const int d = 16 >> st;
+    // lower lane: a + b; upper lane: (a - b) W_{2d}^{lane mod d}, as
+    // (v + s p) w with s = -1 and w = -W on the upper lane
+    float2 w = __ldg(stw + st * 32 + lane);
     if (INV) w.y = -w.y;
-    v[k1] = cmul(v[k1], w);
-  }
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 1 << s;
-    float2 w = __ldg(tw + N + s * 32 + lane);   // W_{2d}^{lane mod d}
-    if (INV) w.y = -w.y;
-    const bool upper = (lane & d) != 0;
+    const float sg = (lane & d) ? -1.0f : 1.0f;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
-      float2 p;
-      p.x = __shfl_xor_sync(kFull, v[k1].x, d);
-      p.y = __shfl_xor_sync(kFull, v[k1].y, d);
-      // lower lane: a + W b (b = partner); upper lane: a - W b (a = partner)
-      const float2 a = upper ? p : v[k1];
-      const float2 t = cmul(upper ? v[k1] : p, w);
-      v[k1] = upper ? csub(a, t) : cadd(a, t);
+      const float px = __shfl_xor_sync(kFull, v[k1].x, d);
+      const float py = __shfl_xor_sync(kFull, v[k1].y, d);
+      v[k1] = cmul(make_float2(fmaf(sg, px, v[k1].x), fmaf(sg, py, v[k1].y)), w);
     }
+  }
+}
+
+// Register j of the lane times tw[j * 32 + lane] (conjugated for INV), j >= 1.
+template <int N1, bool INV>
+__device__ __forceinline__ void lane_twiddle(float2 (&v)[N1], const float2* __restrict__ tw, int lane) {
+#pragma unroll
+  for (int j = 1; j < N1; ++j) {
+    float2 w = __ldg(tw + j * 32 + lane);
+    if (INV) w.y = -w.y;
+    v[j] = cmul(v[j], w);
+  }
+}
+
+// Position of frequency k in a staged row.
+template <int N1>
+__device__ __forceinline__ int stage_pos(int k) {
+  if constexpr (N1 % 2 == 0) {
+    return k + k / N1;
+  } else {
+    return k;
   }
 }
 
 template <int N1>
 __global__ void __launch_bounds__(kXThreads) k_rfft_x(const float* __restrict__ grid, int My, int Mz, int nkx,
-                                                      const float2* __restrict__ tw, float2* __restrict__ spec) {
+                                                      int rs, const float2* __restrict__ tw,
+                                                      float2* __restrict__ spec) {
   constexpr int N = 32 * N1, Mxp = N + 2;
-  extern __shared__ float2 stage[];   // [nkx][kStage]
+  extern __shared__ float2 stage[];   // [kRows][rs]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ychunks = (My + 31) >> 5;
+  const int ychunks = (My + kRows - 1) / kRows;
   const int yc = blockIdx.x % ychunks, cz = blockIdx.x / ychunks;   // cz = c Mz + z
   const int z = cz % Mz, c = cz / Mz;
-  const int y0 = yc * 32, ya = y0 + 2 * warp;
+  const int y0 = yc * kRows, ya = y0 + 2 * warp;
   const int64_t plane = int64_t(Mz) * My;
   if (ya < My) {
     const bool hasb = ya + 1 < My;
     const float* ra = grid + (int64_t(cz) * My + ya) * Mxp;
-    const int n2 = int(__brev(unsigned(lane)) >> 27);
     float2 v[N1];
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      v[m].x = ra[n2 + 32 * m];
-      v[m].y = hasb ? ra[Mxp + n2 + 32 * m] : 0.0f;
+      v[m].x = ra[lane + 32 * m];
+      v[m].y = hasb ? ra[Mxp + lane + 32 * m] : 0.0f;
     }
-    warp_fft<N1, false>(v, tw, lane);
-    // Z[k], k = k1 + N1 lane; Z[N - k] is register N1 - k1 of lane 31 - lane
-    // (k1 > 0) or register 0 of lane (32 - lane) mod 32 (k1 = 0).  Row a's
-    // spectrum is (Z[k] + conj Z[N-k]) / 2, row b's (Z[k] - conj Z[N-k]) / 2i.
+    dft_reg<N1, false>(v);
+    lane_twiddle<N1, false>(v, tw, lane);
+    lane_dft<N1, false>(v, tw + N, lane);
+    // Z[k], k = k1 + N1 r with r = brev5(lane); Z[N - k] is register N1 - k1
+    // of lane 31 - lane (k1 > 0) or register 0 of lane brev5((32 - r) mod 32)
+    // (k1 = 0).  Row a's spectrum is (Z[k] + conj Z[N-k]) / 2, row b's
+    // (Z[k] - conj Z[N-k]) / 2i.
+    const int r = int(__brev(unsigned(lane)) >> 27);
+    float2* sa = stage + (2 * warp) * rs;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       float2 zm;
       if (k1 == 0) {
-        const int src = (32 - lane) & 31;
+        const int src = int(__brev(unsigned((32 - r) & 31)) >> 27);
         zm.x = __shfl_sync(kFull, v[0].x, src);
         zm.y = __shfl_sync(kFull, v[0].y, src);
       } else {
         zm.x = __shfl_xor_sync(kFull, v[N1 - k1].x, 31);
         zm.y = __shfl_xor_sync(kFull, v[N1 - k1].y, 31);
       }
-      const int k = k1 + N1 * lane;
+      const int k = k1 + N1 * r;
       if (k < nkx) {
         const float2 zk = v[k1];
-        stage[k * kStage + 2 * warp] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        stage[k * kStage + 2 * warp + 1] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        const int pk = stage_pos<N1>(k);
+        sa[pk] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        sa[rs + pk] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
       }
     }
   }
   __syncthreads();
-  const int ny = min(32, My - y0);
+  const int ny = min(kRows, My - y0);
   float2* out = spec + int64_t(c) * (N / 2 + 1) * plane + int64_t(z) * My + y0;
-  for (int e = threadIdx.x; e < nkx * 32; e += kXThreads) {
-    const int k = e >> 5, yl = e & 31;
-    if (yl < ny) out[int64_t(k) * plane + yl] = stage[k * kStage + yl];
+  for (int e = threadIdx.x; e < nkx * kRows; e += kXThreads) {
+    const int k = e / kRows, yl = e % kRows;
+    if (yl < ny) out[int64_t(k) * plane + yl] = stage[yl * rs + stage_pos<N1>(k)];
   }
 }
 
 template <int N1>
 __global__ void __launch_bounds__(kXThreads) k_irfft_x(const float2* __restrict__ spec, int My, int Mz, int nkx,
-                                                       const float2* __restrict__ tw, float* __restrict__ grid) {
+                                                       int rs, const float2* __restrict__ tw,
+                                                       float* __restrict__ grid) {
   constexpr int N = 32 * N1, Mxp = N + 2;
-  extern __shared__ float2 stage[];   // [nkx][kStage]
+  extern __shared__ float2 stage[];   // [kRows][rs]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ychunks = (My + 31) >> 5;
+  const int ychunks = (My + kRows - 1) / kRows;
   const int yc = blockIdx.x % ychunks, cz = blockIdx.x / ychunks;
   const int z = cz % Mz, c = cz / Mz;
-  const int y0 = yc * 32, ya = y0 + 2 * warp;
+  const int y0 = yc * kRows, ya = y0 + 2 * warp;
   const int64_t plane = int64_t(Mz) * My;
-  const int ny = min(32, My - y0);
+  const int ny = min(kRows, My - y0);
   const float2* in = spec + int64_t(c) * (N / 2 + 1) * plane + int64_t(z) * My + y0;
-  for (int e = threadIdx.x; e < nkx * 32; e += kXThreads) {
-    const int k = e >> 5, yl = e & 31;
-    stage[k * kStage + yl] = yl < ny ? in[int64_t(k) * plane + yl] : make_float2(0.0f, 0.0f);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < nkx * kRows; e += kXThreads) {
+    const int k = e / kRows, yl = e % kRows;
+    stage[yl * rs + stage_pos<N1>(k)] = yl < ny ? in[int64_t(k) * plane + yl] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   if (ya >= My) return;
   const bool hasb = ya + 1 < My;
-  const int n2 = int(__brev(unsigned(lane)) >> 27);
+  const float2* sa = stage + (2 * warp) * rs;
   float2 v[N1];
 #pragma unroll
-  for (int m = 0; m < N1; ++m) {
+  for (int n1 = 0; n1 < N1; ++n1) {
     // both rows' Hermitian spectra at k: given for k < nkx, conjugate
     // mirrors for N - k < nkx, zero between; the DC imaginary parts dropped
-    const int k = n2 + 32 * m;
+    const int k = n1 + N1 * lane;
     float2 a = make_float2(0.0f, 0.0f), b = a;
     if (k < nkx) {
-      a = stage[k * kStage + 2 * warp];
-      b = stage[k * kStage + 2 * warp + 1];
+      const int pk = stage_pos<N1>(k);
+      a = sa[pk];
+      b = sa[rs + pk];
       if (k == 0) a.y = b.y = 0.0f;
     } else if (N - k < nkx) {
-      a = stage[(N - k) * kStage + 2 * warp];
-      b = stage[(N - k) * kStage + 2 * warp + 1];
+      const int pk = stage_pos<N1>(N - k);
+      a = sa[pk];
+      b = sa[rs + pk];
       a.y = -a.y;
       b.y = -b.y;
     }
-    v[m] = make_float2(a.x - b.y, a.y + b.x);   // A + i B
+    v[n1] = make_float2(a.x - b.y, a.y + b.x);   // A + i B
   }
-  warp_fft<N1, true>(v, tw, lane);
-  float* ra = grid + (int64_t(cz) * My + ya) * Mxp + N1 * lane;
-  if constexpr (N1 % 2 == 0) {
+  lane_dft<N1, true>(v, tw + N, lane);
+  lane_twiddle<N1, true>(v, tw + N + 160, lane);
+  dft_reg<N1, true>(v);
+  // register k1 of lane l is x[32 k1 + brev5(l)]: 128 contiguous bytes per store
+  float* ra = grid + (int64_t(cz) * My + ya) * Mxp + int(__brev(unsigned(lane)) >> 27);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; k1 += 2) {
-      *reinterpret_cast<float2*>(ra + k1) = make_float2(v[k1].x, v[k1 + 1].x);
-      if (hasb) *reinterpret_cast<float2*>(ra + Mxp + k1) = make_float2(v[k1].y, v[k1 + 1].y);
-    }
-  } else {
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      ra[k1] = v[k1].x;
-      if (hasb) ra[Mxp + k1] = v[k1].y;
-    }
+  for (int k1 = 0; k1 < N1; ++k1) {
+    ra[32 * k1] = v[k1].x;
+    if (hasb) ra[Mxp + 32 * k1] = v[k1].y;
   }
 }
 
 template <int N1>
 cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int nkx, const void* tw, void* out,
                       cudaStream_t s) {
-  const size_t smem = size_t(nkx) * kStage * sizeof(float2);
-  const int64_t blocks = int64_t(K) * Mz * ((My + 31) / 32);
+  // staged row stride: past the last position, odd
+  int rs = (nkx - 1) + ((N1 % 2 == 0) ? (nkx - 1) / N1 : 0) + 1;
+  rs += (rs % 2 == 0) ? 1 : 0;
+  const size_t smem = size_t(kRows) * rs * sizeof(float2);
+  const int64_t blocks = int64_t(K) * Mz * ((My + kRows - 1) / kRows);
   if (blocks == 0 || nkx <= 0) return cudaSuccess;
   if (forward) {
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(k_rfft_x<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
     }
-    k_rfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float*>(in), My, Mz, nkx,
+    k_rfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float*>(in), My, Mz, nkx, rs,
                                                              static_cast<const float2*>(tw), static_cast<float2*>(out));
   } else {
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(k_irfft_x<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
     }
-    k_irfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float2*>(in), My, Mz, nkx,
+    k_irfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float2*>(in), My, Mz, nkx, rs,
                                                               static_cast<const float2*>(tw), static_cast<float*>(out));
   }
   return cudaGetLastError();
@@ -320,7 +345,7 @@ cudaError_t dispatch(bool forward, int Mx, const void* in, int My, int Mz, int K
 
 bool xfft_supported(int Mx) { return Mx % 32 == 0 && Mx >= 64 && Mx <= 512; }
 
-int xfft_table_size(int Mx) { return Mx + 5 * 32; }
+int xfft_table_size(int Mx) { return 2 * Mx + 5 * 32; }
 
 void xfft_twiddles(int Mx, std::vector<float>& out) {
   const int N1 = Mx / 32;
@@ -332,13 +357,30 @@ void xfft_twiddles(int Mx, std::vector<float>& out) {
     out[2 * size_t(idx) + 1] = float(-std::sin(a));
   };
   for (int k1 = 0; k1 < N1; ++k1)
+    for (int l = 0; l < 32; ++l) put(k1 * 32 + l, long(l) * k1, Mx);
+  // stage st (distance d = 16 >> st): 1 on lower lanes, -W_{2d}^{l mod d}
+  // on upper lanes
+  for (int st = 0; st < 5; ++st) {
+    const int d = 16 >> st;
+    for (int l = 0; l < 32; ++l) {
+      const int idx = Mx + st * 32 + l;
+      if (l & d) {
+        put(idx, l % d, 2L * d);
+        out[2 * size_t(idx)] = -out[2 * size_t(idx)];
+        out[2 * size_t(idx) + 1] = -out[2 * size_t(idx) + 1];
+      } else {
+        out[2 * size_t(idx)] = 1.0f;
+        out[2 * size_t(idx) + 1] = 0.0f;
+      }
+    }
+  }
+  // inverse twiddles between the lanes and the registers
+  for (int n1 = 0; n1 < N1; ++n1)
     for (int l = 0; l < 32; ++l) {
       int r = 0;
       for (int b = 0; b < 5; ++b) r |= ((l >> b) & 1) << (4 - b);
-      put(k1 * 32 + l, long(r) * k1, Mx);
+      put(Mx + 160 + n1 * 32 + l, long(n1) * r, Mx);
     }
-  for (int s = 0; s < 5; ++s)
-    for (int l = 0; l < 32; ++l) put(Mx + s * 32 + l, l % (1 << s), 2L << s);
 }
 
 cudaError_t launch_rfft_x(const float* grid, int Mx, int My, int Mz, int K, int nkx, const void* tw, void* spec,

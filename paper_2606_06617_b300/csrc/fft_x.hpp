@@ -20,8 +20,11 @@ namespace pswf {
 bool xfft_supported(int Mx);
 
 // Twiddle table of a row length (host, float pairs): entries [k1 * 32 + l] =
-// e^{-2 pi i brev5(l) k1 / Mx} for k1 < N1, then [Mx + s * 32 + l] =
-// e^{-2 pi i (l mod 2^s) / 2^(s+1)} for s < 5; xfft_table_size() pairs.
+// e^{-2 pi i l k1 / Mx} for k1 < N1 (forward); for the lane stages s < 5
+// (distance d = 16 >> s) [Mx + s * 32 + l] = 1 on lanes with l & d = 0 and
+// -e^{-2 pi i (l mod d) / 2d} on the others; then [Mx + 160 + n1 * 32 + l] =
+// e^{-2 pi i n1 brev5(l) / Mx} for n1 < N1 (inverse, conjugated in use);
+// xfft_table_size() pairs.
 int xfft_table_size(int Mx);
 void xfft_twiddles(int Mx, std::vector<float>& out);
 
