@@ -88,10 +88,13 @@ typedef struct {
  * kx < nkx <= 3/4 (Mx/2 + 1): 1-D transforms along x, then 2-D (z, y)
  * transforms of the nkx planes only (cuFFT).  PRUNED_X: the same with the
  * x passes done by this library's kernels (FP32, Mx = 32 N1 with
- * 2 <= N1 <= 16), which write and read only the nkx planes. */
+ * 2 <= N1 <= 16), which write and read only the nkx planes.  OWN: when My
+ * and Mz are of that form too, every pass is this library's: x, z, then the
+ * multiplier fused with the y transforms, z and x back. */
 #define PSWF_TRANSFORM_FULL 0
 #define PSWF_TRANSFORM_PRUNED 1
 #define PSWF_TRANSFORM_PRUNED_X 2
+#define PSWF_TRANSFORM_OWN 3
 
 typedef struct pswf_plan_s* pswf_plan;
 

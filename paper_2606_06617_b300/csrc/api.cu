@@ -345,7 +345,14 @@ struct pswf_plan_s {
   // FP32 pruned plans with Mx = 32 N1: the x passes are the kernels of
   // fft_x.cu (only the kx < nkx planes written and read) instead of cuFFT
   bool xfft = false;
-  void* xtw = nullptr;       // their twiddle table (float2)
+  // ... and when My and Mz are of that form too, the (z, y) passes as well:
+  // z pass, then the multiplier fused with the y transforms (no cuFFT)
+  bool yzfft = false;
+  void* xtw = nullptr;       // twiddle tables (float2) of Mx, then My and Mz (yzfft)
+  int64_t tw_off[3] = {0, 0, 0};
+  unsigned char* lmask = nullptr;   // yzfft: [nkx][Mz] lines that can hold band modes
+  int* lines = nullptr;             // yzfft: those lines, kx << 16 | pz
+  int nlines = 0;
   size_t fft_work_bytes = 0;
   // host staging for pswf_compute_host
   double* h_pin = nullptr;
@@ -480,7 +487,17 @@ int64_t layout(pswf_plan p, char* base) {
   p->virial = vir ? reinterpret_cast<double*>(take(BK * 3 * 8)) : nullptr;
   p->err = reinterpret_cast<int*>(take(4));
   p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
-  p->xtw = p->xfft ? take(int64_t(xfft_table_size(h.M[0])) * 8) : nullptr;
+  {
+    int64_t tw_pairs = 0;
+    for (int d = 0; d < (p->yzfft ? 3 : p->xfft ? 1 : 0); ++d) {
+      p->tw_off[d] = tw_pairs;
+      tw_pairs += xfft_table_size(h.M[d]);
+    }
+    p->xtw = tw_pairs ? take(tw_pairs * 8) : nullptr;
+    const int64_t nl = p->yzfft ? int64_t(p->nkx) * h.M[2] : 0;
+    p->lmask = p->yzfft ? reinterpret_cast<unsigned char*>(take(nl)) : nullptr;
+    p->lines = p->yzfft ? reinterpret_cast<int*>(take(nl * 4)) : nullptr;
+  }
   p->stab_bytes = stab_layout(p);
   char* st = take(p->stab_bytes);
   p->stab = st;
@@ -577,9 +594,21 @@ int upload_tables(pswf_plan p) {
   if (p->real_size == 4) {
     if ((rc = upload(p, p->coef_m, to_real<float>(h.coef_m), "upload coef"))) return rc;
     if (p->xfft) {
-      std::vector<float> tw;
-      xfft_twiddles(h.M[0], tw);
-      if ((rc = upload(p, p->xtw, tw, "upload x twiddles"))) return rc;
+      std::vector<float> all, tw;
+      for (int d = 0; d < (p->yzfft ? 3 : 1); ++d) {
+        xfft_twiddles(h.M[d], tw);
+        all.insert(all.end(), tw.begin(), tw.end());
+      }
+      if ((rc = upload(p, p->xtw, all, "upload transform twiddles"))) return rc;
+    }
+    if (p->yzfft) {
+      std::vector<unsigned char> mask;
+      std::vector<int> lines;
+      const double two_pi = 2.0 * 3.14159265358979323846;
+      xfft_band_lines(p->nkx, h.M[2], two_pi / h.box[0], two_pi / h.box[2], h.k_c, mask, lines);
+      p->nlines = int(lines.size());
+      if ((rc = upload(p, p->lmask, mask, "upload band mask"))) return rc;
+      if (!lines.empty() && (rc = upload(p, p->lines, lines, "upload band lines"))) return rc;
     }
   } else {
     if ((rc = upload(p, p->coef_m, h.coef_m, "upload coef"))) return rc;
@@ -656,6 +685,28 @@ int multiply(pswf_plan p, int want_energy, void* data) {
   mp.deg = h.deg_m;
   mp.K = h.K;
   dim3 grid(p->eblk, p->nrun * h.K);
+  if (p->yzfft) {
+    MultArgs a;
+    a.spec = p->spec;
+    a.mp = mp;
+    a.lines = p->lines;
+    a.nlines = p->nlines;
+    a.nkx = p->nkx;
+    a.K = h.K;
+    a.blocks = p->eblk;
+    a.chan = int64_t(mp.Mxh) * h.M[1] * h.M[2];
+    a.pch = p->pch;
+    a.scale = p->scale;
+    a.kfac = p->kfac;
+    a.coef = p->coef_m;
+    a.iw2 = p->iw2;
+    a.iw2_stride = p->Mh;
+    a.tw = static_cast<const float2*>(p->xtw) + p->tw_off[1];
+    a.part = p->epart;
+    a.want_energy = want_energy;
+    a.vpart = want_energy ? p->vpart : nullptr;
+    return cuda_check(p, launch_mult_y(a, p->stream), "k_mult_y");
+  }
   if (p->pruned) {
     (void)data;   // the pruned spectrum lives in p->spec
     k_multiply_planes<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->spec), mp, p->nkx, p->pch, p->scale,
@@ -697,15 +748,28 @@ int fft_exec_pruned(pswf_plan p, void* data, bool forward) {
                         dir);
   };
   if (p->xfft) {
-    // x passes by the pruned kernels: planes kx >= nkx are never touched
+    // x passes by the pruned kernels: planes kx >= nkx are never touched;
+    // with yzfft the (z, y) passes are own kernels too (the y transforms run
+    // inside the multiplier)
+    const float2* tw = static_cast<const float2*>(p->xtw);
+    auto zpass = [&](bool inverse) {
+      const int rc = cuda_check(p, launch_fft_z(inverse, p->spec, h.M[2], h.M[1], h.K, p->nkx, spec_ch,
+                                                tw + p->tw_off[2], p->lmask, p->stream), "k_fft_z");
+      if (!rc) ++p->launches[p->cur_stage];
+      return rc;
+    };
     if (forward) {
       int rc = cuda_check(p, launch_rfft_x(static_cast<const float*>(data), h.M[0], h.M[1], h.M[2], h.K, p->nkx,
                                            p->xtw, p->spec, p->stream), "k_rfft_x");
       if (rc) return rc;
       ++p->launches[p->cur_stage];
+      if (p->yzfft) return zpass(false);
       for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
     } else {
-      for (int c = 0; c < h.K && r == CUFFT_SUCCESS; ++c) r = planes(c);
+      if (p->yzfft) {
+        if (int rc = zpass(true)) return rc;
+      }
+      for (int c = 0; c < h.K && r == CUFFT_SUCCESS && !p->yzfft; ++c) r = planes(c);
       if (r == CUFFT_SUCCESS) {
         int rc = cuda_check(p, launch_irfft_x(p->spec, h.M[0], h.M[1], h.M[2], h.K, p->nkx, p->xtw,
                                               static_cast<float*>(data), p->stream), "k_irfft_x");
@@ -981,6 +1045,11 @@ int make_fft(pswf_plan p) {
     p->nkx = int(std::min<double>(Mxh, std::floor(kmax_idx) + 2));
     p->pruned = p->nkx * 4 <= Mxh * 3 && h.M[0] >= 64;
     p->xfft = p->pruned && p->real_size == 4 && xfft_supported(h.M[0]);
+    p->yzfft = p->xfft && xfft_supported(h.M[1]) && xfft_supported(h.M[2]);
+  }
+  if (p->yzfft) {   // no cuFFT plan
+    p->fft_sizes.assign(1, 1);
+    return PSWF_OK;
   }
   if (p->pruned) {
     const cufftType c2c = p->real_size == 4 ? CUFFT_C2C : CUFFT_Z2Z;
@@ -1269,7 +1338,10 @@ int pswf_plan_info(pswf_plan pl, pswf_info* out) {
   out->workspace_bytes = pl->ws_bytes;
   out->B = pl->B;
   out->batch = pl->batch ? 1 : 0;
-  out->transform = pl->xfft ? PSWF_TRANSFORM_PRUNED_X : pl->pruned ? PSWF_TRANSFORM_PRUNED : PSWF_TRANSFORM_FULL;
+  out->transform = pl->yzfft  ? PSWF_TRANSFORM_OWN
+                   : pl->xfft ? PSWF_TRANSFORM_PRUNED_X
+                   : pl->pruned ? PSWF_TRANSFORM_PRUNED
+                                : PSWF_TRANSFORM_FULL;
   out->nkx = pl->pruned ? pl->nkx : 0;
   return PSWF_OK;
 }

@@ -34,6 +34,14 @@ constexpr int kRows = 16;                // rows of a (c, z) line per CTA
 constexpr int kXThreads = 16 * kRows;    // a warp per pair of rows
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // cos and sin of 2 pi j / n by their Taylor series after reducing the angle
 // to [-pi, pi]; only ever evaluated by the compiler (template constants).
 __host__ __device__ constexpr double series_sin(double x) {
@@ -166,6 +174,44 @@ __device__ __forceinline__ void lane_twiddle(float2 (&v)[N1], const float2* __re
   }
 }
 
+// The inverse 32-point DFT across the lanes for bit-reversed input order
+// (decimation in time): the upper lane multiplies by its twiddle first, then
+// lower = t + p, upper = p - t; stw are the stages' twiddles (1 on lower
+// lanes).  Output in natural lane order.
+template <int N1, bool INV>
+__device__ __forceinline__ void lane_dit(float2 (&v)[N1], const float2* __restrict__ stw, int lane) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int d = 1 << st;
+    float2 w = __ldg(stw + st * 32 + lane);
+    if (INV) w.y = -w.y;
+    const float sg = (lane & d) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float2 t = cmul(v[k1], w);
+      const float px = __shfl_xor_sync(kFull, t.x, d);
+      const float py = __shfl_xor_sync(kFull, t.y, d);
+      v[k1] = make_float2(fmaf(sg, t.x, px), fmaf(sg, t.y, py));
+    }
+  }
+}
+
+// Complex line of N = 32 N1 points in registers, lane l holding x[l + 32 m]:
+// forward -> register k1 of lane l = X[k1 + N1 brev5(l)]; the inverse takes
+// that order back to natural order (unnormalised).  tw is the length's table.
+template <int N1>
+__device__ __forceinline__ void line_forward(float2 (&v)[N1], const float2* __restrict__ tw, int lane) {
+  dft_reg<N1, false>(v);
+  lane_twiddle<N1, false>(v, tw, lane);
+  lane_dft<N1, false>(v, tw + 32 * N1, lane);
+}
+template <int N1>
+__device__ __forceinline__ void line_inverse(float2 (&v)[N1], const float2* __restrict__ tw, int lane) {
+  lane_dit<N1, true>(v, tw + 2 * 32 * N1 + 160, lane);
+  lane_twiddle<N1, true>(v, tw, lane);
+  dft_reg<N1, true>(v);
+}
+
 // Position of frequency k in a staged row.
 template <int N1>
 __device__ __forceinline__ int stage_pos(int k) {
@@ -291,6 +337,173 @@ __global__ void __launch_bounds__(kXThreads) k_irfft_x(const float2* __restrict_
   }
 }
 
+// ---- (z, y) passes of the fully own transform ---------------------------------
+constexpr int kColTile = 16;   // y columns per z-pass CTA
+constexpr int kColStride = kColTile + 1;
+
+// z pass over the nkx planes: a CTA stages 16 y columns of one (c, kx) plane
+// ([z][y], odd stride, cp.async), a warp transforms one column at a time in
+// place.  Forward: natural z in, column position l + 32 k1 holds
+// kz = k1 + N1 brev5(l), and only positions whose (kx, kz) line can hold
+// band modes (lmask[kx][pos]) are stored; inverse: that order in (other
+// positions read as zero), natural z out.
+template <int N1, bool INV>
+__global__ void __launch_bounds__(256) k_fft_z(float2* __restrict__ spec, int My, int nkx, int64_t chan,
+                                               const float2* __restrict__ tw, const unsigned char* __restrict__ lmask) {
+  constexpr int Mz = 32 * N1;
+  extern __shared__ float2 tile[];   // [Mz][kColStride]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ych = (My + kColTile - 1) / kColTile;
+  const int yc = blockIdx.x % ych, ck = blockIdx.x / ych;   // ck = c nkx + kx
+  const int kx = ck % nkx, c = ck / nkx;
+  const int y0 = yc * kColTile, ny = min(kColTile, My - y0);
+  float2* base = spec + int64_t(c) * chan + int64_t(kx) * Mz * My + y0;
+  const unsigned char* mk = lmask + int64_t(kx) * Mz;
+  for (int e = threadIdx.x; e < Mz * kColTile; e += 256) {
+    const int z = e / kColTile, yl = e % kColTile;
+    float2* dst = tile + z * kColStride + yl;
+    if (yl < ny && (!INV || mk[z]))
+      cp_async8(dst, base + int64_t(z) * My + yl);
+    else
+      *dst = make_float2(0.0f, 0.0f);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int col = warp; col < ny; col += 8) {
+    float2 v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = tile[(lane + 32 * m) * kColStride + col];
+    if (INV)
+      line_inverse<N1>(v, tw, lane);
+    else
+      line_forward<N1>(v, tw, lane);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) tile[(lane + 32 * m) * kColStride + col] = v[m];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Mz * kColTile; e += 256) {
+    const int z = e / kColTile, yl = e % kColTile;
+    if (yl < ny && (INV || mk[z])) base[int64_t(z) * My + yl] = tile[z * kColStride + yl];
+  }
+}
+
+// Steps (iii)-(iv) fused with the y transforms.  A warp takes y lines from
+// the list of lines that can hold band modes (lines[j] = kx << 16 | pz, pz a
+// column position of the z pass, kz = (pz >> 5) + N1z brev5(pz & 31)),
+// double-buffered in shared memory by cp.async; transforms the line forward
+// in registers, writes it back in its output order (position l + 32 k1 =
+// ky = k1 + N1 brev5(l)) and multiplies each mode by
+//   G = scale_c sing_p(k) (S_p(u) + log part) iw2x iw2y iw2z
+// (zero outside |k| < k_c and at k = 0), adding w_m G |rho-hat|^2 / 2 to the
+// energy (kx = 0 counted once) and, with vpart, the virial's log-derivative
+// sums; then transforms it back and stores it.  Energy partials per block in
+// FP64 (part[c][blocks]).
+template <int N1>
+__global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultParams mp, int64_t chan,
+                                                const int* __restrict__ lines, int nlines,
+                                                const int* __restrict__ pch, const double* __restrict__ scale,
+                                                const double* __restrict__ kfac, const float* __restrict__ coef,
+                                                const float* __restrict__ iw2, int iw2_stride,
+                                                const float2* __restrict__ tw, double* __restrict__ part,
+                                                int want_energy, double* __restrict__ vpart) {
+  constexpr int My = 32 * N1;
+  extern __shared__ float2 lbuf[];   // [8 warps][2][My]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* wbuf = lbuf + warp * 2 * My;
+  const int c = blockIdx.y;
+  const int p = pch[c];
+  const int Mz = mp.M[2], N1z = Mz >> 5;
+  const float sc = float(scale[c]);
+  const float* cf = coef + size_t(p - 1) * kMultSeg * (mp.deg + 1);
+  const float* iw2x = iw2;
+  const float* iw2y = iw2x + iw2_stride;
+  const float* iw2z = iw2y + iw2_stride;
+  const float kc2 = float(1.0 / (mp.inv_kc * mp.inv_kc));
+  const float inv_kc = float(mp.inv_kc);
+  const float kf0 = float(kfac[0]), kf1 = float(kfac[1]), kf2 = float(kfac[2]);
+  float2* sp = spec + int64_t(c) * chan;
+  auto line_at = [&](int j) { return sp + (int64_t(lines[j] >> 16) * Mz + (lines[j] & 0xFFFF)) * My; };
+  auto fetch = [&](int j, float2* dst) {
+    const float2* src = line_at(j);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) cp_async8(dst + lane + 32 * m, src + lane + 32 * m);
+  };
+  EnergyAcc<float> e;
+  double vx = 0.0, vy = 0.0, vz = 0.0;
+  const int jstep = gridDim.x * 8;
+  int j = blockIdx.x * 8 + warp, cur = 0;
+  if (j < nlines) fetch(j, wbuf);
+  cp_async_commit();
+  for (; j < nlines; j += jstep, cur ^= 1) {
+    __syncwarp();   // the other buffer's previous line is consumed
+    if (j + jstep < nlines) fetch(j + jstep, wbuf + (cur ^ 1) * My);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    float2* b = wbuf + cur * My;
+    const int kx = lines[j] >> 16, pz = lines[j] & 0xFFFF;
+    const int kz = (pz >> 5) + N1z * int(__brev(unsigned(pz & 31)) >> 27);
+    const int mz = kz <= Mz / 2 ? kz : kz - Mz;
+    const float fkx = kf0 * float(kx), fkz = kf2 * float(mz);
+    const float kxz2 = fkx * fkx + fkz * fkz;
+    float2 v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = b[lane + 32 * m];
+    line_forward<N1>(v, tw, lane);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) b[lane + 32 * k1] = v[k1];
+    __syncwarp();
+    const float wxz = sc * iw2x[kx] * iw2z[mz < 0 ? -mz : mz];
+    const float wedge = kx == 0 ? 0.5f : 1.0f;
+    for (int q = lane; q < My; q += 32) {
+      const int ky = (q >> 5) + N1 * int(__brev(unsigned(q & 31)) >> 27);
+      const int my = ky <= My / 2 ? ky : ky - My;
+      const float fky = kf1 * float(my);
+      const float k2 = kxz2 + fky * fky;
+      float2 x = b[q];
+      if (!(k2 < kc2) || k2 == 0.0f) {
+        x = make_float2(0.0f, 0.0f);
+      } else {
+        const float k = sqrtf(k2);
+        float u = k * inv_kc;
+        if (u >= 1.0f) u = 1.0f - 1e-7f;
+        int seg = int(u * float(kMultSeg));
+        if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+        const float sv = 2.0f * (u * float(kMultSeg) - float(seg)) - 1.0f;
+        const float* cs = cf + seg * (mp.deg + 1);
+        const float S = mult_horner(cs, mp.deg, sv);
+        const float phi = mult_value(p, S, k, k2, u);
+        const float G = phi * wxz * iw2y[my < 0 ? -my : my];
+        if (want_energy) {
+          const float em = wedge * G * (x.x * x.x + x.y * x.y);
+          e.add(em);
+          if (vpart) {
+            const float dS = mult_horner_d(cs, mp.deg, sv);
+            const double dl = double(mult_dlog(p, S, dS * float(2 * kMultSeg), u, phi)) / double(k2);
+            vx += double(em) * dl * double(fkx * fkx);
+            vy += double(em) * dl * double(fky * fky);
+            vz += double(em) * dl * double(fkz * fkz);
+          }
+        }
+        x.x *= G;
+        x.y *= G;
+      }
+      b[q] = x;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = b[lane + 32 * k1];
+    line_inverse<N1>(v, tw, lane);
+    float2* ln = line_at(j);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) ln[lane + 32 * m] = v[m];
+  }
+  cp_async_wait<0>();
+  if (!want_energy) return;
+  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
+}
+
 template <int N1>
 cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int nkx, const void* tw, void* out,
                       cudaStream_t s) {
@@ -301,14 +514,14 @@ cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int n
   const int64_t blocks = int64_t(K) * Mz * ((My + kRows - 1) / kRows);
   if (blocks == 0 || nkx <= 0) return cudaSuccess;
   if (forward) {
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {   // opt in early: static shared memory counts too
       const cudaError_t e = cudaFuncSetAttribute(k_rfft_x<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
     }
     k_rfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float*>(in), My, Mz, nkx, rs,
                                                              static_cast<const float2*>(tw), static_cast<float2*>(out));
   } else {
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {   // opt in early: static shared memory counts too
       const cudaError_t e = cudaFuncSetAttribute(k_irfft_x<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
     }
@@ -345,7 +558,7 @@ cudaError_t dispatch(bool forward, int Mx, const void* in, int My, int Mz, int K
 
 bool xfft_supported(int Mx) { return Mx % 32 == 0 && Mx >= 64 && Mx <= 512; }
 
-int xfft_table_size(int Mx) { return 2 * Mx + 5 * 32; }
+int xfft_table_size(int Mx) { return 2 * Mx + 10 * 32; }
 
 void xfft_twiddles(int Mx, std::vector<float>& out) {
   const int N1 = Mx / 32;
@@ -381,6 +594,20 @@ void xfft_twiddles(int Mx, std::vector<float>& out) {
       for (int b = 0; b < 5; ++b) r |= ((l >> b) & 1) << (4 - b);
       put(Mx + 160 + n1 * 32 + l, long(n1) * r, Mx);
     }
+  // decimation-in-time stages st < 5 (distance d = 1 << st): e^{-2 pi i
+  // (l mod d) / 2d} on lanes with l & d set, 1 on the others
+  for (int st = 0; st < 5; ++st) {
+    const int d = 1 << st;
+    for (int l = 0; l < 32; ++l) {
+      const int idx = 2 * Mx + 160 + st * 32 + l;
+      if (l & d) {
+        put(idx, l % d, 2L * d);
+      } else {
+        out[2 * size_t(idx)] = 1.0f;
+        out[2 * size_t(idx) + 1] = 0.0f;
+      }
+    }
+  }
 }
 
 cudaError_t launch_rfft_x(const float* grid, int Mx, int My, int Mz, int K, int nkx, const void* tw, void* spec,
@@ -391,6 +618,107 @@ cudaError_t launch_rfft_x(const float* grid, int Mx, int My, int Mz, int K, int 
 cudaError_t launch_irfft_x(const void* spec, int Mx, int My, int Mz, int K, int nkx, const void* tw, float* grid,
                            cudaStream_t s) {
   return dispatch(false, Mx, spec, My, Mz, K, nkx, tw, grid, s);
+}
+
+namespace {
+template <int N1, bool INV>
+cudaError_t launch_z_n1(void* spec, int My, int K, int nkx, int64_t chan, const void* tw, const unsigned char* lmask,
+                        cudaStream_t s) {
+  const size_t smem = size_t(32 * N1) * kColStride * sizeof(float2);
+  if (smem > 32 * 1024) {   // opt in early: static shared memory counts too
+    const cudaError_t e = cudaFuncSetAttribute(k_fft_z<N1, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t blocks = int64_t(K) * nkx * ((My + kColTile - 1) / kColTile);
+  k_fft_z<N1, INV><<<unsigned(blocks), 256, smem, s>>>(static_cast<float2*>(spec), My, nkx, chan,
+                                                      static_cast<const float2*>(tw), lmask);
+  return cudaGetLastError();
+}
+template <bool INV>
+cudaError_t launch_z(int Mz, void* spec, int My, int K, int nkx, int64_t chan, const void* tw,
+                     const unsigned char* lmask, cudaStream_t s) {
+  switch (Mz / 32) {
+    case 2: return launch_z_n1<2, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 3: return launch_z_n1<3, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 4: return launch_z_n1<4, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 5: return launch_z_n1<5, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 6: return launch_z_n1<6, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 7: return launch_z_n1<7, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 8: return launch_z_n1<8, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 9: return launch_z_n1<9, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 10: return launch_z_n1<10, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 11: return launch_z_n1<11, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 12: return launch_z_n1<12, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 13: return launch_z_n1<13, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 14: return launch_z_n1<14, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 15: return launch_z_n1<15, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    case 16: return launch_z_n1<16, INV>(spec, My, K, nkx, chan, tw, lmask, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int N1>
+cudaError_t launch_mult_n1(const MultArgs& a, cudaStream_t s) {
+  const size_t smem = size_t(8) * 2 * 32 * N1 * sizeof(float2);
+  if (smem > 32 * 1024) {   // opt in early: static shared memory counts too
+    const cudaError_t e = cudaFuncSetAttribute(k_mult_y<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k_mult_y<N1><<<dim3(a.blocks, a.K), 256, smem, s>>>(
+      static_cast<float2*>(a.spec), a.mp, a.chan, a.lines, a.nlines, a.pch, a.scale, a.kfac,
+      static_cast<const float*>(a.coef), static_cast<const float*>(a.iw2), a.iw2_stride,
+      static_cast<const float2*>(a.tw), a.part, a.want_energy, a.vpart);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_fft_z(bool inverse, void* spec, int Mz, int My, int K, int nkx, int64_t chan, const void* tw,
+                         const unsigned char* lmask, cudaStream_t s) {
+  if (!xfft_supported(Mz)) return cudaErrorInvalidValue;
+  if (K == 0 || nkx <= 0 || My <= 0) return cudaSuccess;
+  return inverse ? launch_z<true>(Mz, spec, My, K, nkx, chan, tw, lmask, s)
+                 : launch_z<false>(Mz, spec, My, K, nkx, chan, tw, lmask, s);
+}
+
+void xfft_band_lines(int nkx, int Mz, double kf0, double kf2, double k_c, std::vector<unsigned char>& mask,
+                     std::vector<int>& lines) {
+  const int n1z = Mz / 32;
+  mask.assign(size_t(nkx) * Mz, 0);
+  lines.clear();
+  for (int kx = 0; kx < nkx; ++kx)
+    for (int pz = 0; pz < Mz; ++pz) {
+      int r = 0;
+      for (int b = 0; b < 5; ++b) r |= (((pz & 31) >> b) & 1) << (4 - b);
+      const int kz = (pz >> 5) + n1z * r;
+      const int mz = kz <= Mz / 2 ? kz : kz - Mz;
+      const double a = kf0 * kx, b = kf2 * mz;
+      if (a * a + b * b < k_c * k_c) {
+        mask[size_t(kx) * Mz + pz] = 1;
+        lines.push_back((kx << 16) | pz);
+      }
+    }
+}
+
+cudaError_t launch_mult_y(const MultArgs& a, cudaStream_t s) {
+  if (!xfft_supported(a.mp.M[1]) || !xfft_supported(a.mp.M[2])) return cudaErrorInvalidValue;
+  if (a.K == 0 || a.blocks <= 0 || a.nlines <= 0) return cudaSuccess;
+  switch (a.mp.M[1] / 32) {
+    case 2: return launch_mult_n1<2>(a, s);
+    case 3: return launch_mult_n1<3>(a, s);
+    case 4: return launch_mult_n1<4>(a, s);
+    case 5: return launch_mult_n1<5>(a, s);
+    case 6: return launch_mult_n1<6>(a, s);
+    case 7: return launch_mult_n1<7>(a, s);
+    case 8: return launch_mult_n1<8>(a, s);
+    case 9: return launch_mult_n1<9>(a, s);
+    case 10: return launch_mult_n1<10>(a, s);
+    case 11: return launch_mult_n1<11>(a, s);
+    case 12: return launch_mult_n1<12>(a, s);
+    case 13: return launch_mult_n1<13>(a, s);
+    case 14: return launch_mult_n1<14>(a, s);
+    case 15: return launch_mult_n1<15>(a, s);
+    case 16: return launch_mult_n1<16>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace pswf

@@ -21,6 +21,7 @@ PSWF_FLAG_VIRIAL = 2
 PSWF_TRANSFORM_FULL = 0
 PSWF_TRANSFORM_PRUNED = 1
 PSWF_TRANSFORM_PRUNED_X = 2
+PSWF_TRANSFORM_OWN = 3
 
 
 class PswfError(RuntimeError):

@@ -1,4 +1,5 @@
-"""Pruned x transforms of single FP32 plans (PSWF_TRANSFORM_PRUNED_X).
+"""Own transform passes of single FP32 plans (PSWF_TRANSFORM_PRUNED_X: own x
+passes, cuFFT (z, y); PSWF_TRANSFORM_OWN: every pass own).
 
 When the band |k| < k_c reaches only the lowest x frequencies, the x passes
 of the 3-D transform are this library's kernels (rows of Mx = 32 N1 points,
@@ -75,9 +76,9 @@ def test_pruned_x_matches_oracle(n1, hx):
         assert err_phi <= TOL_FP32 and err_f <= TOL_FP32
 
 
-def test_pruned_x_cubic_melt_box():
-    """Cubic ionic-melt box (K = 4, P = 7, r_c = 7) on 96^3 (N1 = 3) at the
-    plain FP32 budget."""
+def test_own_transform_cubic_melt_box():
+    """Cubic ionic-melt box (K = 4, P = 7, r_c = 7) on 96^3: every pass is
+    this library's (x, z, multiplier fused with y); plain FP32 budget."""
     from paper_2606_06617_b300 import lr
     L = 350.0 * 96 / 384
     s = wl.ionic_melt(int(round(4194304 * (L / 350.0) ** 3)), L, seed=4)
@@ -85,12 +86,38 @@ def test_pruned_x_cubic_melt_box():
     c = math.log(3.0 / 1e-5)
     cw = window_cw(s.box, M, 7, c, 7.0)
     g = run_gpu(s, 7.0, 7, M, c, cw, precision=0)
-    assert g["info"]["transform"] == lr.PSWF_TRANSFORM_PRUNED_X
+    assert g["info"]["transform"] == lr.PSWF_TRANSFORM_OWN
     o = run_oracle(s, 7.0, 7, M, c, cw)
     for ch in range(4):
         assert abs(g["E_ch"][ch] - o["E_ch"][ch]) <= TOL_FP32 * abs(o["E_ch"][ch])
     assert rel_rms(g["phi"], o["phi"]) <= TOL_FP32
     assert rel_rms(g["F"], o["F"]) <= TOL_FP32
+
+
+@pytest.mark.parametrize("n1", [(2, 2, 2), (3, 4, 5), (12, 2, 3), (5, 7, 2), (16, 3, 2), (7, 16, 2)])
+def test_own_transform_matches_oracle(n1):
+    """All passes own (PSWF_TRANSFORM_OWN) on grids 32 (N1x, N1y, N1z): the
+    column z pass and the fused y multiplier for every length class, the
+    bit-reversed kz order of the z pass decoded by the multiplier."""
+    from paper_2606_06617_b300 import lr
+    M = tuple(32 * k for k in n1)
+    h = (0.3, 0.42, 0.45)
+    box = tuple(hd * m for hd, m in zip(h, M))
+    nat = int(0.1 * box[0] * box[1] * box[2])
+    s = wl.random_system(nat, box, (1, 6), seed=200 + sum(n1), neutral=bool(n1[0] % 2))
+    cw = window_cw(s.box, M, 6, C_TOL, R_C)
+    g = run_gpu(s, R_C, 6, M, C_TOL, cw, precision=0)
+    info = g["info"]
+    assert info["transform"] == lr.PSWF_TRANSFORM_OWN, info
+    o = run_oracle(s, R_C, 6, M, C_TOL, cw)
+    e_f, phi_f, f_f = _full_transform(s, info, M)
+    for c in range(2):
+        ref = abs(o["E_ch"][c])
+        bound = _bound(abs(e_f[c] - o["E_ch"][c]) / ref)
+        assert abs(g["E_ch"][c] - o["E_ch"][c]) <= bound * ref, (c, g["E_ch"], o["E_ch"], e_f)
+    err_phi, err_f = rel_rms(g["phi"], o["phi"]), rel_rms(g["F"], o["F"])
+    assert err_phi <= _bound(rel_rms(phi_f, o["phi"])), (err_phi, rel_rms(phi_f, o["phi"]))
+    assert err_f <= _bound(rel_rms(f_f, o["F"])), (err_f, rel_rms(f_f, o["F"]))
 
 
 def test_pruned_x_and_cufft_x_agree():
