@@ -17,7 +17,13 @@ namespace pswf {
 namespace {
 
 using R = PSWF_REAL;
-constexpr int kSmemLimit = 227 * 1024;   // opt-in shared memory per CTA on sm_103a
+constexpr int kSmemPerSm = 228 * 1024;   // shared memory per SM on sm_103a (1 KB of it reserved per CTA)
+// CTAs of the stencil kernels per SM, each with its own padded region.  Two
+// (two channels each, so one CTA's staging, flush and barriers could overlap
+// the other's atom loop) measured slower on the 384^3 melt: spread 2.79 /
+// gather 3.42 ms against 2.37 / 2.64 ms with one CTA holding all four
+// channels (window tables filled twice per atom, half the slots per item).
+constexpr int kStencilCtas = 1;
 constexpr int kGatherThreads = kGatherThreadsFor<R>;
 constexpr int kDirectThreads = 256;
 
@@ -48,7 +54,7 @@ template <int P, typename Kern, typename F>
 bool pick_kc_kb(Kern kern, int K, F bytes, int* kc_out, int* kb_out) {
   cudaFuncAttributes attr;
   if (cudaFuncGetAttributes(&attr, kern) != cudaSuccess) return false;
-  const size_t budget = size_t(kSmemLimit) - attr.sharedSizeBytes;
+  const size_t budget = size_t(kSmemPerSm) / kStencilCtas - 1024 - attr.sharedSizeBytes;
   for (int kc = std::min(K, TilePad<P>::NS); kc >= 1; --kc)
     for (int kb = 256; kb >= 64; kb -= 32)
       if (bytes(kc, kb) <= budget) {
@@ -64,7 +70,7 @@ cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherThreads / kStencilCtas, smem);
   if (e != cudaSuccess) return e;
   *blocks = int(std::min<int64_t>(items, int64_t(sm_count()) * std::max(per_sm, 1)));
   return cudaSuccess;
@@ -74,7 +80,7 @@ template <int P>
 cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
-  if (!pick_kc_kb<P>(k_spread<R, P>, c.geo.K, [](int k, int b) { return spread_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
+  if (!pick_kc_kb<P>(k_spread<R, P, kStencilCtas>, c.geo.K, [](int k, int b) { return spread_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
     const int blocks = int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_spread_direct<R, P><<<std::max(blocks, 1), kDirectThreads, 0, c.stream>>>(
         c.nmax, c.geo, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell, static_cast<const R*>(c.sq), wc,
@@ -85,9 +91,9 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
   const size_t smem = spread_smem_bytes<R, P>(kc, kb);
   const int nchunk = (c.geo.K + kc - 1) / kc;
   int blocks = 0;
-  cudaError_t e = persistent_blocks<P>(k_spread<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
+  cudaError_t e = persistent_blocks<P>(k_spread<R, P, kStencilCtas>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
-  k_spread<R, P><<<blocks, kGatherThreads, smem, c.stream>>>(c.geo, c.smol, c.nmax, c.tile_start, static_cast<const R*>(c.st),
+  k_spread<R, P, kStencilCtas><<<blocks, kGatherThreads / kStencilCtas, smem, c.stream>>>(c.geo, c.smol, c.nmax, c.tile_start, static_cast<const R*>(c.st),
                                                              c.scell, static_cast<const R*>(c.sq), wc, kc, kb,
                                                              static_cast<R*>(c.grid));
   ++*nlaunch;
@@ -99,7 +105,8 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   if (c.n == 0) return cudaSuccess;
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
-  if (!pick_kc_kb<P>(k_interp<R, P>, c.geo.K, [](int k, int b) { return gather_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
+  if (!pick_kc_kb<P>(k_interp<R, P, kStencilCtas>, c.geo.K,
+                     [](int k, int b) { return gather_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
     const int blocks = int(std::min<int64_t>((c.nmax + kDirectThreads - 1) / kDirectThreads, 148 * 32));
     k_interp_direct<R, P><<<std::max(blocks, 1), kDirectThreads, 0, c.stream>>>(
         c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
@@ -116,14 +123,13 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   }
   const size_t smem = gather_smem_bytes<R, P>(kc, kb);
   int blocks = 0;
-  e = persistent_blocks<P>(k_interp<R, P>, smem, int64_t(c.ntiles) * nchunk, &blocks);
+  e = persistent_blocks<P>(k_interp<R, P, kStencilCtas>, smem, int64_t(c.ntiles) * nchunk, &blocks);
   if (e != cudaSuccess) return e;
-  const int threads = kGatherThreads;
-  k_interp<R, P><<<blocks, threads, smem, c.stream>>>(c.nmax, c.geo, c.smol, c.soff, c.tile_start,
-                                                      static_cast<const R*>(c.st),
-                                                      c.scell, static_cast<const R*>(c.sq), c.sperm, wc, kc, kb,
-                                                      static_cast<const R*>(c.grid), c.zero_coef, c.charges,
-                                                      static_cast<R*>(phi), static_cast<R*>(forces));
+  const int threads = kGatherThreads / kStencilCtas;
+  k_interp<R, P, kStencilCtas><<<blocks, threads, smem, c.stream>>>(
+      c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const R*>(c.st), c.scell,
+      static_cast<const R*>(c.sq), c.sperm, wc, kc, kb, static_cast<const R*>(c.grid), c.zero_coef, c.charges,
+      static_cast<R*>(phi), static_cast<R*>(forces));
   ++*nlaunch;
   return cudaGetLastError();
 }

@@ -54,7 +54,9 @@ struct TilePad {
   static constexpr int N = find_n();
 };
 
-// Threads of a spread or gather CTA: 1024 in FP32 (64 registers a thread), 512 in FP64.
+// Threads of the spread and gather CTAs resident on one SM: 1024 in FP32 (64
+// registers a thread), 512 in FP64; split over CTAS CTAs per SM (each with
+// its own padded region).
 template <typename R>
 constexpr int kGatherThreadsFor = sizeof(R) == 4 ? 1024 : 512;
 
@@ -200,8 +202,8 @@ constexpr size_t spread_smem_bytes(int kc, int kb) {
   return stencil_smem_bytes<R, P>(kc, kb, 3, sizeof(typename SpreadAcc<R>::T));
 }
 
-template <typename R, int P>
-__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_spread(Geometry g, const double* __restrict__ smol,
+template <typename R, int P, int CTAS>
+__global__ void __launch_bounds__(kGatherThreadsFor<R> / CTAS, CTAS) k_spread(Geometry g, const double* __restrict__ smol,
                                                                    int64_t nmax, const int* __restrict__ tile_start,
                                                                    const R* __restrict__ st,
                                                                    const uint64_t* __restrict__ scell,
@@ -384,8 +386,8 @@ __global__ void k_spread_direct(int64_t nmax, Geometry g, const int* __restrict_
 // (after it, lane group v of the slot holds sum v), the force components
 // then over the atom's slots.  With more than one chunk the force is
 // accumulated with global atomics (zeroed before the launch).
-template <typename R, int P>
-__global__ void __launch_bounds__(kGatherThreadsFor<R>, 1) k_interp(int64_t nmax, Geometry g,
+template <typename R, int P, int CTAS>
+__global__ void __launch_bounds__(kGatherThreadsFor<R> / CTAS, CTAS) k_interp(int64_t nmax, Geometry g,
                                                                    const double* __restrict__ smol,
                                                                    const int* __restrict__ soff,
                                                                    const int* __restrict__ tile_start,
