@@ -148,17 +148,25 @@ __global__ void k_set_count(int* __restrict__ soff, int n) {
 
 __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
                                    double* __restrict__ charges) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per (structure, channel): lanes stride over the block partials
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (g >= B * K) return;
   const int s = g / K, c = g - s * K;
   double a = 0.0, b = 0.0;
-  for (int i = 0; i < nblk; ++i) {
+  for (int i = lane; i < nblk; i += 32) {
     const size_t o = ((size_t(s) * nblk + i) * K + c) * 2;
     a += part[o];
     b += part[o + 1];
   }
-  charges[2 * g] = a;
-  charges[2 * g + 1] = b;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    charges[2 * g] = a;
+    charges[2 * g + 1] = b;
+  }
 }
 
 }  // namespace pswf
@@ -170,7 +178,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kEnergyBlocks = 592;   // 4 x 148 SMs
 constexpr int kQBlocks = 148;        // charge-sum blocks of pswf_self_energy_noalloc
-constexpr int kQBlocksPlan = 148;    // charge-sum blocks of a single-structure plan (1 per SM)
+constexpr int kQBlocksPlan = 592;    // charge-sum blocks of a single-structure plan (4 per SM)
 constexpr int kQBlocksBatch = 8;     // per structure in a batch plan
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
@@ -828,7 +836,7 @@ int charge_sums(pswf_plan p, const void* vals, double* out) {
                                                                           p->soff, p->qpart);
   int rc = launch_check(p, "k_charge_partials_seg");
   if (rc) return rc;
-  k_charge_final_seg<<<(p->nrun * K + 63) / 64, 64, 0, p->stream>>>(p->nqb, K, p->nrun, p->qpart, out);
+  k_charge_final_seg<<<(p->nrun * K + 7) / 8, 256, 0, p->stream>>>(p->nqb, K, p->nrun, p->qpart, out);
   return launch_check(p, "k_charge_final_seg");
 }
 

@@ -40,7 +40,7 @@ struct Geometry {
 // loops unroll and read the coefficients as constant operands.
 template <typename R>
 struct WinCoef {
-  static constexpr int kDeg = sizeof(R) == 4 ? 14 : 24;
+  static constexpr int kDeg = sizeof(R) == 4 ? 12 : 24;
   int deg;                          // the planner's degree (<= kDeg)
   R c[kMaxP * (kDeg + 1)];          // piece j, monomial n at [j * (kDeg + 1) + n]
 };
@@ -318,11 +318,18 @@ __global__ void k_charge_partials_seg(const R* __restrict__ q, int K, int B, con
                                       double* __restrict__ part) {
   const int s = blockIdx.y;
   const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
+  const int64_t step = int64_t(gridDim.x) * blockDim.x;
   for (int c = 0; c < K; ++c) {
-    ChargeAcc<R> acc;
-    for (int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a1; i += int64_t(gridDim.x) * blockDim.x)
-      acc.add(q[c * n + i]);
-    charge_block_sums(acc.sum(), acc.sumsq(), part + ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2);
+    // two interleaved accumulators: independent dependency chains
+    ChargeAcc<R> acc0, acc1;
+    int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + step < a1; i += 2 * step) {
+      acc0.add(q[c * n + i]);
+      acc1.add(q[c * n + i + step]);
+    }
+    if (i < a1) acc0.add(q[c * n + i]);
+    charge_block_sums(acc0.sum() + acc1.sum(), acc0.sumsq() + acc1.sumsq(),
+                      part + ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2);
   }
 }
 

@@ -383,8 +383,10 @@ int plan_core(const double box_max[3], int K, const int* pset, int npset, const 
     const double P = plan.P;
     for (int j = 0; j < plan.P; ++j)
       cheb[j] = cheb_fit([&](double s) { return plan.win.eval((2.0 * j - P + 1.0 + s) / P); }, nfit);
-    // the device pads FP32 pieces to degree 14 and FP64 pieces to 24
-    const int deg = std::min(family_degree(cheb, eps_poly), opt.precision == 1 ? kMaxDeg : 14);
+    // the device pads FP32 pieces to degree 12 and FP64 pieces to 24 (FP32
+    // fits need 10-12 for P >= 3; P = 2 would take 13 for 1e-9, and its
+    // degree-12 fit error is still far below FP32 rounding)
+    const int deg = std::min(family_degree(cheb, eps_poly), opt.precision == 1 ? kMaxDeg : 12);
     plan.deg_w = deg;
     plan.coef_w.assign(size_t(plan.P) * (deg + 1), 0.0);
     for (int j = 0; j < plan.P; ++j) {
