@@ -21,24 +21,35 @@ import numpy as np
 from .mollifiers import Mollifier
 
 
+def cell_matrix(box) -> np.ndarray:
+    """3 x 3 cell with the lattice vectors as rows: diag(box) for an
+    orthorhombic box given as three edge lengths."""
+    b = np.asarray(box, dtype=np.float64)
+    return np.diag(b) if b.shape == (3,) else b.reshape(3, 3)
+
+
 def kvectors(box, k_max: float):
-    """All k = 2 pi m / L with 0 < |k| < k_max (full sphere, both signs)."""
-    box = np.asarray(box, dtype=np.float64)
-    mmax = np.floor(k_max * box / (2 * math.pi)).astype(int) + 1
+    """All k = 2 pi H^-1 m (m integer, the reciprocal lattice of the cell H
+    whose rows are the lattice vectors; k = 2 pi m / L for a box) with
+    0 < |k| < k_max, full sphere, both signs.  |m_d| <= k_max |a_d| / 2 pi
+    because m_d = k . a_d / 2 pi."""
+    H = cell_matrix(box)
+    mmax = np.floor(k_max * np.linalg.norm(H, axis=1) / (2 * math.pi)).astype(int) + 1
     rng = [np.arange(-m, m + 1) for m in mmax]
     mx, my, mz = np.meshgrid(*rng, indexing="ij")
-    k = 2 * math.pi * np.stack([mx.ravel() / box[0], my.ravel() / box[1], mz.ravel() / box[2]], 1)
+    m = np.stack([mx.ravel(), my.ravel(), mz.ravel()], 1).astype(np.float64)
+    k = 2 * math.pi * m @ np.linalg.inv(H).T
     kk = np.linalg.norm(k, axis=1)
     keep = (kk > 0) & (kk < k_max)
     return k[keep], kk[keep]
 
 
 def structure_factor_sum(pos, q, box, ps, c, r_c, chunk: int = 2048):
-    """Returns dict(E, E_ch [K], E_k [K], E0 [K], phi [K,N], F [N,3], f [K,N,3])."""
+    """box: three edge lengths or a 3 x 3 cell (rows = lattice vectors).
+    Returns dict(E, E_ch [K], E_k [K], E0 [K], phi [K,N], F [N,3], f [K,N,3])."""
     pos = np.asarray(pos, dtype=np.float64)
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    box = np.asarray(box, dtype=np.float64)
-    V = float(np.prod(box))
+    V = float(abs(np.linalg.det(cell_matrix(box))))
     moll = Mollifier(c, r_c)
     kvec, kk = kvectors(box, moll.k_c)
     K, N = q.shape

@@ -27,6 +27,18 @@ Stencil (reading C5): with u = r / h, the P points of each dimension are
 i0 .. i0 + P - 1 with i0 = ceil(u - P/2), taken modulo M.  Reading C6: the
 DFT sign does not matter (G is even and rho is real); m = 0 is excluded.
 
+Cells (triclinic): with the lattice vectors a_d as the rows of H,
+r = sum_d s_d a_d, the grid is uniform in the fractional coordinates s and
+everything above is written in grid units: u_d = M_d s_d, the window per
+direction is psi^{c_w}((g_d - u_d) / (P/2)), its transform per grid cell is
+W-hat_d(m_d) = (P/2) lambda_0 psi^{c_w}(pi P m_d / (c_w M_d)), the modes are
+k_m = 2 pi H^-1 m (the reciprocal vectors b_d = columns of H^-1), and
+    E_k = 1/(2V) sum_m Phi-hat_p(|k_m|) |rho-hat(m)|^2 / prod_d W-hat_d^2,
+    Psi = 1/V IDFT[...],   F_i = q_i H^-1 diag(M) sum_g Psi_g grad_u W,
+with V = |det H|.  For an orthorhombic box (H = diag(L)) this is the formula
+above: prod_d (h_d W-hat_d) is the Cartesian window transform and
+Delta V^2 = prod h_d^2 cancels.
+
 Nothing here is blocked, fused or reordered: atoms are spread by index_add_,
 the transform is torch.fft.fftn over the full (not half) spectrum.
 """
@@ -46,27 +58,29 @@ f64 = torch.float64
 
 @dataclass
 class GridConfig:
-    box: tuple            # (L_x, L_y, L_z) in Angstrom, orthorhombic
+    box: tuple            # (L_x, L_y, L_z) in Angstrom (orthorhombic; ignored when cell is given)
     M: tuple              # grid points per dimension
     P: int                # stencil width
     c: float              # mollifier bandwidth
     r_c: float            # mollifier cutoff
     ps: tuple             # exponent p of each channel
     c_w: float | None = None   # window bandwidth (defaults to c)
+    cell: object = None   # 3 x 3, rows = lattice vectors a_d (Angstrom); None: diag(box)
 
 
 class DiscretePSWF:
-    """O1 oracle for one periodic orthorhombic system."""
+    """O1 oracle for one periodic system (orthorhombic box or general cell)."""
 
     def __init__(self, cfg: GridConfig):
         self.cfg = cfg
-        self.box = np.asarray(cfg.box, dtype=np.float64)
+        self.H = (np.diag(np.asarray(cfg.box, dtype=np.float64)) if cfg.cell is None
+                  else np.asarray(cfg.cell, dtype=np.float64).reshape(3, 3))
+        self.Hinv = np.linalg.inv(self.H)
         self.M = np.asarray(cfg.M, dtype=np.int64)
         self.P = int(cfg.P)
-        self.V = float(np.prod(self.box))
-        self.h = self.box / self.M
+        self.V = float(abs(np.linalg.det(self.H)))
         self.dV = self.V / float(np.prod(self.M))
-        self.omega = self.P * self.h / 2.0
+        self.half = self.P / 2.0            # window half-width in grid cells
         self.moll = Mollifier(cfg.c, cfg.r_c)
         c_w = cfg.c if cfg.c_w is None else cfg.c_w
         self.psi_w = self.moll.psi if c_w == cfg.c else PSWF(c_w)
@@ -78,37 +92,37 @@ class DiscretePSWF:
         |k| >= k_c, where Phi-hat_p vanishes under reading C1)."""
         if p in self._G:
             return self._G[p]
-        ks = [2.0 * math.pi * np.fft.fftfreq(int(M), d=1.0 / int(M)) / L
-              for M, L in zip(self.M, self.box)]
-        kx, ky, kz = np.meshgrid(*ks, indexing="ij")
-        kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+        ms = [np.fft.fftfreq(int(M), d=1.0 / int(M)) for M in self.M]   # signed mode numbers
+        mx, my, mz = np.meshgrid(*ms, indexing="ij")
+        B = 2.0 * math.pi * self.Hinv                 # k_m = B m
+        kv = [B[d, 0] * mx + B[d, 1] * my + B[d, 2] * mz for d in range(3)]
+        kk = np.sqrt(kv[0] ** 2 + kv[1] ** 2 + kv[2] ** 2)
         inside = (kk > 0) & (kk < self.moll.k_c)
         G = np.zeros(kk.shape)
         if np.any(inside):
             uniq, inv = np.unique(kk[inside], return_inverse=True)
             phi = self.moll.phi_hat(p, uniq)[inv]
-            what = (window_hat(self.psi_w, self.omega[0], kx[inside])
-                    * window_hat(self.psi_w, self.omega[1], ky[inside])
-                    * window_hat(self.psi_w, self.omega[2], kz[inside]))
+            # window transform per grid cell at kappa_d = 2 pi m_d / M_d
+            what = np.ones(int(np.sum(inside)))
+            for d, m in enumerate((mx, my, mz)):
+                what = what * window_hat(self.psi_w, self.half, 2.0 * math.pi * m[inside] / float(self.M[d]))
             G[inside] = phi / what ** 2
         self._G[p] = torch.tensor(G, dtype=f64)
         return self._G[p]
 
     # ---- window ---------------------------------------------------------
     def stencil(self, pos: torch.Tensor):
-        """Indices [N,3,P] (mod M), weights W_d and dW_d/d(alpha) [N,3,P],
-        where alpha = x_g - r along each dimension."""
-        h = torch.tensor(self.h, dtype=f64)
-        u = pos / h                                           # [N,3]
+        """Indices [N,3,P] (mod M), weights W_d and dW_d/d(delta) [N,3,P],
+        where delta = g_d - u_d in grid cells, u = M (H^-T r)."""
+        Hinv = torch.tensor(self.Hinv, dtype=f64)
+        u = (pos @ Hinv) * torch.tensor(self.M, dtype=f64)   # [N,3] grid coordinates
         i0 = torch.ceil(u - self.P / 2.0)                      # [N,3]
         j = torch.arange(self.P, dtype=f64)
         idx = i0.unsqueeze(-1) + j                             # [N,3,P]
-        alpha = (idx - u.unsqueeze(-1)) * h.view(1, 3, 1)      # x_g - r
-        om = torch.tensor(self.omega, dtype=f64).view(1, 3, 1)
-        x = alpha / om
+        x = (idx - u.unsqueeze(-1)) / self.half
         inside = (x.abs() <= 1.0).to(f64)
         W = self.psi_w.torch(x) * inside
-        dW = self.psi_w.torch(x, 1) / om * inside
+        dW = self.psi_w.torch(x, 1) / self.half * inside
         M = torch.tensor(self.M, dtype=torch.int64).view(1, 3, 1)
         idx = torch.remainder(idx.to(torch.int64), M)
         return idx, W, dW
@@ -143,14 +157,14 @@ class DiscretePSWF:
         for c in range(K):
             G = self.multiplier(self.cfg.ps[c])
             rh = torch.fft.fftn(rho[c])
-            E.append(self.dV ** 2 / (2.0 * self.V) * torch.sum(G * (rh.real ** 2 + rh.imag ** 2)))
-            Psi.append((self.dV ** 2 / self.V) * torch.fft.ifftn(G * rh).real * Mtot)
+            E.append(1.0 / (2.0 * self.V) * torch.sum(G * (rh.real ** 2 + rh.imag ** 2)))
+            Psi.append((1.0 / self.V) * torch.fft.ifftn(G * rh).real * Mtot)
         return torch.stack(E), torch.stack(Psi)
 
     # ---- gather -----------------------------------------------------------
     def gather(self, Psi: torch.Tensor, pos: torch.Tensor, chunk: int = 131072):
         """phi [K,N] = sum_g Psi_g W(x_g - r_i) and per-unit-charge force
-        f [K,N,3] = sum_g Psi_g (grad W)(x_g - r_i)."""
+        f [K,N,3] = -d phi / d r_i = H^-1 diag(M) sum_g Psi_g (grad_delta W)."""
         K = Psi.shape[0]
         flatPsi = Psi.reshape(K, -1)
         phis, fs = [], []
@@ -167,7 +181,9 @@ class DiscretePSWF:
                                         torch.einsum("nabc,na,nb,nc->n", g, Wx, dy, Wz),
                                         torch.einsum("nabc,na,nb,nc->n", g, Wx, Wy, dz)], -1))
             phis.append(torch.stack(ph_c))
-            fs.append(torch.stack(f_c))
+            # grid-cell derivatives -> Cartesian: f = H^-1 (M * f_u), as rows
+            J = torch.tensor(self.Hinv * self.M[None, :].astype(np.float64), dtype=f64)   # H^-1 diag(M)
+            fs.append(torch.stack(f_c) @ J.T)
         if not phis:
             return torch.zeros(K, 0, dtype=f64), torch.zeros(K, 0, 3, dtype=f64)
         return torch.cat(phis, 1), torch.cat(fs, 1)
@@ -225,6 +241,8 @@ class DiscretePSWF:
         at the same grid size, P, c and c_w; Richardson-extrapolated from
         h = eps and 2 eps (truncation O(eps^4), rounding ~1e-12 / eps)."""
         pos = np.asarray(pos, dtype=np.float64)
+        if self.cfg.cell is not None and np.any(self.H != np.diag(np.diag(self.H))):
+            raise NotImplementedError("the diagonal virial is defined for orthorhombic boxes")
         K = len(self.cfg.ps)
         c_w = self.cfg.c if self.cfg.c_w is None else self.cfg.c_w
 
