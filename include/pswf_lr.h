@@ -81,6 +81,8 @@ typedef struct {
   int batch;               /* 1 for plans made by pswf_batch_plan_create */
   int transform;           /* pswf_plan_info: PSWF_TRANSFORM_* of the plan (0 from pswf_plan_params) */
   int nkx;                 /* pruned transforms: x frequencies 0..nkx-1 kept (others are out of band) */
+  double cell[9];          /* pswf_plan_info: lattice vectors as rows (diag(box) for a box; box_max for
+                              batch plans); box[] then holds the edge lengths |a_d| */
 } pswf_info;
 
 /* Transform of a plan.  FULL: cuFFT 3-D real transforms of every structure
@@ -115,6 +117,21 @@ int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* 
  * first pswf_set_points allocates one (cudaMalloc) that the plan owns. */
 int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p,
                      const pswf_opts* opts, void* stream, pswf_plan* out);
+
+/* A single structure in a general (triclinic) periodic cell.
+ * cell: host [9], the lattice vectors a_0, a_1, a_2 as rows (Angstrom); the
+ * positions are Cartesian (any real value: wrapped through the fractional
+ * coordinates).  The grid is uniform in the fractional coordinates (M_d
+ * points along a_d), the window and its deconvolution act per grid direction
+ * and the modes are k = 2 pi H^-1 m (Methods, with the box replaced by the
+ * cell: Eq. (Fourier) sums over the reciprocal lattice); grid, P and c_w are
+ * chosen for the edge lengths |a_d|.  Forces are Cartesian.  Otherwise as
+ * pswf_plan_create; an orthorhombic cell gives the box plan.  Returns
+ * PSWF_EINVAL for non-finite or (nearly) coplanar vectors, and for
+ * PSWF_FLAG_BACKWARD or PSWF_FLAG_VIRIAL with a non-orthorhombic cell
+ * (forward only). */
+int pswf_plan_create_cell(const double cell[9], int64_t n_max, int K, const int* p, const pswf_opts* opts,
+                          void* stream, pswf_plan* out);
 
 /* Fills *out; synchronous, host only. */
 int pswf_plan_info(pswf_plan plan, pswf_info* out);

@@ -324,15 +324,17 @@ struct pswf_plan_s {
   // per-structure tables, one contiguous region (uploaded in one copy):
   void* stab = nullptr;
   int64_t stab_bytes = 0;
-  int64_t stab_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t stab_off[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   double* sbox = nullptr;    // [B][3] box edges
   double* scale = nullptr;   // [B K] multiplier scale (includes dV^2 / V)
   double* zero_coef = nullptr;  // [B K]
   int* soff = nullptr;       // [B + 1] atom offsets per structure
   int* pch = nullptr;        // [B K] exponents
   void* iw2 = nullptr;       // real [B][3][Mh]
-  double* smol = nullptr;    // [B][3] M_d / L_d (stencil location and 2/h without a division)
-  double* kfac = nullptr;    // [B][3] 2 pi / L_d
+  double* smol = nullptr;    // [B][3] M_d / L_d (stencil location and 2/h without a division; 1 for a general cell)
+  double* bmat = nullptr;    // [B][9] B = 2 pi H^-1 (k_m = B m; diag(2 pi / L) for a box)
+  double* tmat = nullptr;    // [B][9] T = diag(M) H^-T (grid coordinates u = T r; general cells)
+  bool tric = false;         // single structure in a general (non-orthorhombic) cell
   void* h_stab = nullptr;    // pinned host mirror of stab (batch plans)
   cudaEvent_t stab_ev = nullptr;  // last upload from h_stab
   std::vector<int> h_pch;    // host copy of pch
@@ -442,7 +444,7 @@ int run_size(pswf_plan p, int b) {
 // Layout of the per-structure table region (also the pinned host mirror):
 // sbox double [B][3] | scale double [B K] | zero_coef double [B K] |
 // soff int [B + 1] | pch int [B K] | iw2 real [B][3][Mh] | M/L double [B][3] |
-// 2 pi / L double [B][3]; returns bytes.
+// B = 2 pi H^-1 double [B][9] | T = diag(M) H^-T double [B][9]; returns bytes.
 int64_t stab_layout(pswf_plan p) {
   const int64_t B = p->B, K = p->host.K, rs = int64_t(p->real_size);
   auto a16 = [](int64_t b) { return (b + 15) & ~int64_t(15); };
@@ -454,7 +456,8 @@ int64_t stab_layout(pswf_plan p) {
   p->stab_off[4] = off; off = a16(off + B * K * 4);
   p->stab_off[5] = off; off = a16(off + B * 3 * int64_t(p->Mh) * rs);
   p->stab_off[6] = off; off = a16(off + B * 3 * 8);
-  p->stab_off[7] = off; off = a16(off + B * 3 * 8);
+  p->stab_off[7] = off; off = a16(off + B * 9 * 8);
+  p->stab_off[8] = off; off = a16(off + B * 9 * 8);
   return off;
 }
 
@@ -517,7 +520,8 @@ int64_t layout(pswf_plan p, char* base) {
     p->pch = reinterpret_cast<int*>(st + p->stab_off[4]);
     p->iw2 = st + p->stab_off[5];
     p->smol = reinterpret_cast<double*>(st + p->stab_off[6]);
-    p->kfac = reinterpret_cast<double*>(st + p->stab_off[7]);
+    p->bmat = reinterpret_cast<double*>(st + p->stab_off[7]);
+    p->tmat = reinterpret_cast<double*>(st + p->stab_off[8]);
   }
   p->fft_work = take(int64_t(p->fft_work_bytes));
   return off;
@@ -546,7 +550,8 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
   int* pch = reinterpret_cast<int*>(dst + p->stab_off[4]);
   char* iw2 = dst + p->stab_off[5];
   double* smol = reinterpret_cast<double*>(dst + p->stab_off[6]);
-  double* kfac = reinterpret_cast<double*>(dst + p->stab_off[7]);
+  double* bmat = reinterpret_cast<double*>(dst + p->stab_off[7]);
+  double* tmat = reinterpret_cast<double*>(dst + p->stab_off[8]);
   int pdef = 0;
   for (int q = 1; q <= 6 && !pdef; ++q)
     if (h.mult_scale_p[q] != 0.0) pdef = q;
@@ -555,7 +560,9 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
   std::string err;
   for (int sidx = 0; sidx < B; ++sidx) {
     const bool used = sidx < b;
-    if (used) {
+    if (used && !p->batch) {
+      t = h.st;   // the single structure's cell, tabulated by the planner
+    } else if (used) {
       int rc = struct_tables(h, boxes + 3 * sidx, t, err);
       if (rc) return set_err(p, rc, "structure " + std::to_string(sidx) + ": " + err);
     } else {
@@ -565,11 +572,22 @@ int fill_stab(pswf_plan p, int b, const double* boxes, const int* ps, const int6
         t.iw2[d].clear();
       }
       t.V = t.dV = 1.0;
+      t.tric = false;
+      for (int i = 0; i < 9; ++i) t.tmat[i] = t.bmat[i] = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        t.tmat[4 * d] = double(h.M[d]) / t.box[d];
+        t.bmat[4 * d] = 2.0 * 3.14159265358979323846 / t.box[d];
+      }
     }
     for (int d = 0; d < 3; ++d) {
       sbox[3 * sidx + d] = t.box[d];
-      smol[3 * sidx + d] = double(h.M[d]) / t.box[d];
-      kfac[3 * sidx + d] = 2.0 * 3.14159265358979323846 / t.box[d];
+      // general cells: the gathers work in grid coordinates (unit M / L) and
+      // the forces go through T^T afterwards
+      smol[3 * sidx + d] = t.tric ? 1.0 : double(h.M[d]) / t.box[d];
+    }
+    for (int i = 0; i < 9; ++i) {
+      bmat[9 * sidx + i] = t.bmat[i];
+      tmat[9 * sidx + i] = t.tmat[i];
     }
     const double dv2v = t.dV * t.dV / t.V;
     for (int c = 0; c < K; ++c) {
@@ -613,7 +631,8 @@ int upload_tables(pswf_plan p) {
       std::vector<unsigned char> mask;
       std::vector<int> lines;
       const double two_pi = 2.0 * 3.14159265358979323846;
-      xfft_band_lines(p->nkx, h.M[2], two_pi / h.box[0], two_pi / h.box[2], h.k_c, mask, lines);
+      (void)two_pi;
+      xfft_band_lines(p->nkx, h.M[1], h.M[2], h.st.bmat, h.k_c, mask, lines);
       p->nlines = int(lines.size());
       if ((rc = upload(p, p->lmask, mask, "upload band mask"))) return rc;
       if (!lines.empty() && (rc = upload(p, p->lines, lines, "upload band lines"))) return rc;
@@ -705,7 +724,7 @@ int multiply(pswf_plan p, int want_energy, void* data) {
     a.chan = int64_t(mp.Mxh) * h.M[1] * h.M[2];
     a.pch = p->pch;
     a.scale = p->scale;
-    a.kfac = p->kfac;
+    a.bmat = p->bmat;
     a.coef = p->coef_m;
     a.iw2 = p->iw2;
     a.iw2_stride = p->Mh;
@@ -718,12 +737,12 @@ int multiply(pswf_plan p, int want_energy, void* data) {
   if (p->pruned) {
     (void)data;   // the pruned spectrum lives in p->spec
     k_multiply_planes<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(p->spec), mp, p->nkx, p->pch, p->scale,
-                                                           p->kfac, static_cast<const R*>(p->coef_m),
+                                                           p->bmat, static_cast<const R*>(p->coef_m),
                                                            static_cast<const R*>(p->iw2), p->Mh, p->epart,
                                                            want_energy, want_energy ? p->vpart : nullptr);
     return launch_check(p, "k_multiply_planes");
   }
-  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->kfac,
+  k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->bmat,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
                                                   p->Mh, p->epart, want_energy,
                                                   want_energy ? p->vpart : nullptr);
@@ -864,11 +883,11 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   if ((rc = cuda_check(p, cudaMemsetAsync(p->tile_count, 0, size_t(ntl) * 4, s), "clear counts"))) return rc;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((p->n_max + kThreads - 1) / kThreads, 148 * 32)));
   if (pos_dtype == 0)
-    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), geo, p->smol, p->soff, p->tile_of,
+    k_bin<float, R><<<blocks, kThreads, 0, s>>>(static_cast<const float*>(pos), geo, p->smol, p->tmat, p->soff, p->tile_of,
                                                 p->rank, p->tile_count, static_cast<R*>(p->tmp_t), p->tmp_cell,
                                                 p->n_max, p->err);
   else
-    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), geo, p->smol, p->soff,
+    k_bin<double, R><<<blocks, kThreads, 0, s>>>(static_cast<const double*>(pos), geo, p->smol, p->tmat, p->soff,
                                                  p->tile_of, p->rank, p->tile_count, static_cast<R*>(p->tmp_t),
                                                  p->tmp_cell, p->n_max, p->err);
   if ((rc = launch_check(p, "k_bin"))) return rc;
@@ -935,8 +954,15 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
     int nl = 0;
     cudaError_t e = sizeof(R) == 4 ? launch_interp_float(ctx, phi, forces, &nl)
                                    : launch_interp_double(ctx, phi, forces, &nl);
-    p->launches[PSWF_STAGE_INTERP] += nl;
     if ((rc = cuda_check(p, e, "interp"))) return rc;
+    if (p->tric && forces && p->n > 0) {
+      // grid-coordinate gradients -> Cartesian forces, F = T^T f_u
+      const int blocks = int(std::min<int64_t>((p->n + kThreads - 1) / kThreads, 148 * 8));
+      k_force_cell<R><<<blocks, kThreads, 0, s>>>(p->n, p->tmat, static_cast<R*>(forces));
+      if ((rc = launch_check(p, "k_force_cell"))) return rc;
+      ++nl;
+    }
+    p->launches[PSWF_STAGE_INTERP] += nl;
   }
   return PSWF_OK;
 }
@@ -1252,6 +1278,10 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->geo.Mxp = 2 * (h.M[0] / 2 + 1);
   pl->geo.P = h.P;
   pl->geo.K = h.K;
+  pl->tric = b == 1 && h.st.tric;
+  pl->geo.tric = pl->tric ? 1 : 0;
+  if (pl->tric && (opts->flags & (PSWF_FLAG_BACKWARD | PSWF_FLAG_VIRIAL)))
+    return set_err(pl, PSWF_EINVAL, "general cells: PSWF_FLAG_BACKWARD and PSWF_FLAG_VIRIAL need an orthorhombic box");
   pl->geo.nts = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
   pl->geo.B = b;
   pl->nts = pl->geo.nts;
@@ -1280,6 +1310,26 @@ int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p, co
   pswf_plan pl = new (std::nothrow) pswf_plan_s();
   if (!pl) return PSWF_ENOMEM;
   int rc = make_plan(box, K, p, to_options(opts), pl->host);
+  if (rc) {
+    delete pl;
+    return rc;
+  }
+  if ((rc = finish_create(pl, n_max, 1, opts, stream))) {
+    pswf_plan_destroy(pl);
+    return rc;
+  }
+  *out = pl;
+  return PSWF_OK;
+}
+
+int pswf_plan_create_cell(const double cell[9], int64_t n_max, int K, const int* p, const pswf_opts* opts,
+                          void* stream, pswf_plan* out) {
+  if (!out) return PSWF_EINVAL;
+  *out = nullptr;
+  if (!cell || !p || !opts || n_max < 0 || n_max > (int64_t(1) << 31) - 1) return PSWF_EINVAL;
+  pswf_plan pl = new (std::nothrow) pswf_plan_s();
+  if (!pl) return PSWF_ENOMEM;
+  int rc = make_plan_cell(cell, K, p, to_options(opts), pl->host);
   if (rc) {
     delete pl;
     return rc;
@@ -1346,6 +1396,7 @@ int pswf_plan_info(pswf_plan pl, pswf_info* out) {
   out->workspace_bytes = pl->ws_bytes;
   out->B = pl->B;
   out->batch = pl->batch ? 1 : 0;
+  for (int i = 0; i < 9; ++i) out->cell[i] = pl->batch ? (i % 4 == 0 ? pl->host.box_max[i / 4] : 0.0) : pl->host.st.cell[i];
   out->transform = pl->yzfft  ? PSWF_TRANSFORM_OWN
                    : pl->xfft ? PSWF_TRANSFORM_PRUNED_X
                    : pl->pruned ? PSWF_TRANSFORM_PRUNED

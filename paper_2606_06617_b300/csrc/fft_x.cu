@@ -23,6 +23,7 @@
 // kx >= nkx are neither written nor read.
 #include "fft_x.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <utility>
@@ -403,7 +404,7 @@ template <int N1>
 __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultParams mp, int64_t chan,
                                                 const int* __restrict__ lines, int nlines,
                                                 const int* __restrict__ pch, const double* __restrict__ scale,
-                                                const double* __restrict__ kfac, const float* __restrict__ coef,
+                                                const double* __restrict__ bmat, const float* __restrict__ coef,
                                                 const float* __restrict__ iw2, int iw2_stride,
                                                 const float2* __restrict__ tw, double* __restrict__ part,
                                                 int want_energy, double* __restrict__ vpart) {
@@ -421,7 +422,9 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
   const float* iw2z = iw2y + iw2_stride;
   const float kc2 = float(1.0 / (mp.inv_kc * mp.inv_kc));
   const float inv_kc = float(mp.inv_kc);
-  const float kf0 = float(kfac[0]), kf1 = float(kfac[1]), kf2 = float(kfac[2]);
+  float bm[9];   // k = B m, B = 2 pi H^-1 (diagonal for a box)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) bm[i] = float(bmat[i]);
   float2* sp = spec + int64_t(c) * chan;
   auto line_at = [&](int j) { return sp + (int64_t(lines[j] >> 16) * Mz + (lines[j] & 0xFFFF)) * My; };
   auto fetch = [&](int j, float2* dst) {
@@ -445,8 +448,9 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
     const int kx = lines[j] >> 16, pz = lines[j] & 0xFFFF;
     const int kz = (pz >> 5) + N1z * int(__brev(unsigned(pz & 31)) >> 27);
     const int mz = kz <= Mz / 2 ? kz : kz - Mz;
-    const float fkx = kf0 * float(kx), fkz = kf2 * float(mz);
-    const float kxz2 = fkx * fkx + fkz * fkz;
+    // the line's part of k (kx and kz modes); + my b_y per mode
+    const float lx = bm[0] * float(kx) + bm[2] * float(mz), ly = bm[3] * float(kx) + bm[5] * float(mz),
+                lz = bm[6] * float(kx) + bm[8] * float(mz);
     float2 v[N1];
 #pragma unroll
     for (int m = 0; m < N1; ++m) v[m] = b[lane + 32 * m];
@@ -459,8 +463,8 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
     for (int q = lane; q < My; q += 32) {
       const int ky = (q >> 5) + N1 * int(__brev(unsigned(q & 31)) >> 27);
       const int my = ky <= My / 2 ? ky : ky - My;
-      const float fky = kf1 * float(my);
-      const float k2 = kxz2 + fky * fky;
+      const float fkx = lx + bm[1] * float(my), fky = ly + bm[4] * float(my), fkz = lz + bm[7] * float(my);
+      const float k2 = fkx * fkx + fky * fky + fkz * fkz;
       float2 x = b[q];
       if (!(k2 < kc2) || k2 == 0.0f) {
         x = make_float2(0.0f, 0.0f);
@@ -664,7 +668,7 @@ cudaError_t launch_mult_n1(const MultArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   k_mult_y<N1><<<dim3(a.blocks, a.K), 256, smem, s>>>(
-      static_cast<float2*>(a.spec), a.mp, a.chan, a.lines, a.nlines, a.pch, a.scale, a.kfac,
+      static_cast<float2*>(a.spec), a.mp, a.chan, a.lines, a.nlines, a.pch, a.scale, a.bmat,
       static_cast<const float*>(a.coef), static_cast<const float*>(a.iw2), a.iw2_stride,
       static_cast<const float2*>(a.tw), a.part, a.want_energy, a.vpart);
   return cudaGetLastError();
@@ -679,9 +683,12 @@ cudaError_t launch_fft_z(bool inverse, void* spec, int Mz, int My, int K, int nk
                  : launch_z<false>(Mz, spec, My, K, nkx, chan, tw, lmask, s);
 }
 
-void xfft_band_lines(int nkx, int Mz, double kf0, double kf2, double k_c, std::vector<unsigned char>& mask,
+void xfft_band_lines(int nkx, int My, int Mz, const double bmat[9], double k_c, std::vector<unsigned char>& mask,
                      std::vector<int>& lines) {
   const int n1z = Mz / 32;
+  const double by[3] = {bmat[1], bmat[4], bmat[7]};
+  const double bb = by[0] * by[0] + by[1] * by[1] + by[2] * by[2];
+  const int mlo = -((My - 1) / 2), mhi = My / 2;   // signed y modes of the kernels
   mask.assign(size_t(nkx) * Mz, 0);
   lines.clear();
   for (int kx = 0; kx < nkx; ++kx)
@@ -690,8 +697,18 @@ void xfft_band_lines(int nkx, int Mz, double kf0, double kf2, double k_c, std::v
       for (int b = 0; b < 5; ++b) r |= (((pz & 31) >> b) & 1) << (4 - b);
       const int kz = (pz >> 5) + n1z * r;
       const int mz = kz <= Mz / 2 ? kz : kz - Mz;
-      const double a = kf0 * kx, b = kf2 * mz;
-      if (a * a + b * b < k_c * k_c) {
+      const double l[3] = {bmat[0] * kx + bmat[2] * mz, bmat[3] * kx + bmat[5] * mz, bmat[6] * kx + bmat[8] * mz};
+      // |l + my b_y|^2 is convex in my: its integer minimum over the line's
+      // modes is at the clamped floor or ceiling of the real minimiser
+      const double mstar = -(l[0] * by[0] + l[1] * by[1] + l[2] * by[2]) / bb;
+      double best = 1e300;
+      for (double mc : {std::floor(mstar), std::floor(mstar) + 1.0}) {
+        const double my = std::min(double(mhi), std::max(double(mlo), mc));
+        double k2 = 0.0;
+        for (int e = 0; e < 3; ++e) k2 += (l[e] + my * by[e]) * (l[e] + my * by[e]);
+        best = std::min(best, k2);
+      }
+      if (best < k_c * k_c) {
         mask[size_t(kx) * Mz + pz] = 1;
         lines.push_back((kx << 16) | pz);
       }

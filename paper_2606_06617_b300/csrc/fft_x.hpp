@@ -42,9 +42,10 @@ cudaError_t launch_irfft_x(const void* spec, int Mx, int My, int Mz, int K, int 
 
 // Lines of the nkx planes that can hold band modes after the z pass: for kx
 // < nkx and column position pz (kz = (pz >> 5) + (Mz / 32) brev5(pz & 31),
-// signed mz), (kf0 kx)^2 + (kf2 mz)^2 < k_c^2 with kf_d = 2 pi / L_d.
-// mask[kx * Mz + pz] = 1 for those, lines lists them as kx << 16 | pz.
-void xfft_band_lines(int nkx, int Mz, double kf0, double kf2, double k_c, std::vector<unsigned char>& mask,
+// signed mz), some signed y mode my gives |B (kx, my, mz)| < k_c, B = 2 pi
+// H^-1 (row-major bmat; for a box: (2 pi kx / L_x)^2 + (2 pi mz / L_z)^2 <
+// k_c^2).  mask[kx * Mz + pz] = 1 for those, lines lists them as kx << 16 | pz.
+void xfft_band_lines(int nkx, int My, int Mz, const double bmat[9], double k_c, std::vector<unsigned char>& mask,
                      std::vector<int>& lines);
 
 // z pass of the fully own transform over the nkx planes of spec ([K][.][Mz][My],
@@ -66,7 +67,7 @@ struct MultArgs {
   int64_t chan;
   const int* pch;
   const double* scale;
-  const double* kfac;
+  const double* bmat;
   const void* coef;
   const void* iw2;
   int iw2_stride;

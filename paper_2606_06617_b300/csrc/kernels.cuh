@@ -2,8 +2,9 @@
 //
 // A plan holds B structures (B = 1 for a single system) that share one grid
 // size M and K channels; structure s has its own box (tables smol[s][3] =
-// M_d / L_d and kfac[s][3] = 2 pi / L_d) and its
-// atoms are soff[s] .. soff[s+1] - 1 of the caller's arrays.
+// M_d / L_d, bmat[s][9] = 2 pi H^-1 with the lattice vectors as the rows of
+// H, diagonal for a box, and for a general cell tmat[s][9] = diag(M) H^-T)
+// and its atoms are soff[s] .. soff[s+1] - 1 of the caller's arrays.
 // Data layout in HBM (one plan):
 //   grid   real [B][K][M_z][M_y][M_xp], M_xp = 2 (M_x / 2 + 1): the spread
 //          density, overwritten in place by the R2C transform, the multiplier
@@ -31,6 +32,7 @@ struct Geometry {
   int P;             // stencil width
   int ntile[3];      // tiles per dimension (of one structure)
   int nts;           // tiles per structure
+  int tric;          // 1: general cell (locate through T = diag(M) H^-T), 0: box
   int K;             // channels
   int B;             // structures
 };
@@ -74,8 +76,7 @@ __host__ __device__ inline void unpack_cell(uint64_t c, int& x, int& y, int& z) 
 // FP64 work is one multiply, one floor and one subtraction per direction.
 // (t = 1 only when 1 - f rounds up, f tiny: the stencil and t then still
 // describe u.)
-__device__ inline void locate(double x, double m_over_l, int M, int P, int& i0w, double& t) {
-  const double u = x * m_over_l;
+__device__ inline void locate_u(double u, int M, int P, int& i0w, double& t) {
   const double fl = floor(u);
   const double f = u - fl;
   int64_t i0;
@@ -103,14 +104,13 @@ __device__ inline void locate(double x, double m_over_l, int M, int P, int& i0w,
 // once: 2^32 [f > 0] - f 2^32 (even P), 2^31 + 2^32 [f > 1/2] - f 2^32 (odd
 // P), with the bits below 2^-32 dropped (t = 1 where that difference wraps
 // to 0).  |u| >= 2^30 takes the FP64 route.
-__device__ inline void locate_fx(double x, double m_over_l, int M, int P, int& i0w, float& t) {
-  const double u = x * m_over_l;
+__device__ inline void locate_fx_u(double u, int M, int P, int& i0w, float& t) {
   const long long bits = __double_as_longlong(u);
   const int bexp = int((bits >> 52) & 0x7FF);
   const int ex = bexp - 1075;   // |u| = m 2^ex
   if (ex > -23) {
     double td;
-    locate(x, m_over_l, M, P, i0w, td);
+    locate_u(u, M, P, i0w, td);
     t = float(td);
     return;
   }
@@ -197,28 +197,40 @@ __device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
 // k_bin: locate each atom (original order), count it into its tile and keep
 // its rank there, its offsets t and its packed start cell for k_scatter.
 // smol[s][d] = M_d / L_d of structure s.
+// tmat[s][9] = T = diag(M) H^-T of structure s (general cells, g.tric):
+// u = T r; boxes use u_d = r_d M_d / L_d (smol).
 template <typename PosT, typename R>
 __global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __restrict__ smol,
-                      const int* __restrict__ soff, int* __restrict__ tile_of, int* __restrict__ rank,
-                      int* __restrict__ tile_count, R* __restrict__ tmp_t, uint64_t* __restrict__ tmp_cell,
-                      int64_t nmax, int* __restrict__ err) {
+                      const double* __restrict__ tmat, const int* __restrict__ soff, int* __restrict__ tile_of,
+                      int* __restrict__ rank, int* __restrict__ tile_count, R* __restrict__ tmp_t,
+                      uint64_t* __restrict__ tmp_cell, int64_t nmax, int* __restrict__ err) {
   const int64_t n = soff[g.B];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int s = find_struct(soff, 1, g.B, i);
+    double x[3];
+    for (int d = 0; d < 3; ++d) {
+      x[d] = double(pos[3 * i + d]);
+      if (((__double_as_longlong(x[d]) >> 52) & 0x7FF) == 0x7FF) {   // inf or nan
+        atomicCAS(err, 0, -6);
+        x[d] = 0.0;
+      }
+    }
     int i0[3];
     for (int d = 0; d < 3; ++d) {
-      double x = double(pos[3 * i + d]);
-      if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) {   // inf or nan
-        atomicCAS(err, 0, -6);
-        x = 0.0;
+      double u;
+      if (g.tric) {
+        const double* T = tmat + 9 * s + 3 * d;
+        u = fma(T[0], x[0], fma(T[1], x[1], T[2] * x[2]));
+      } else {
+        u = x[d] * smol[3 * s + d];
       }
       if constexpr (sizeof(R) == 4) {
         float t;
-        locate_fx(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
+        locate_fx_u(u, g.M[d], g.P, i0[d], t);
         tmp_t[d * nmax + i] = t;
       } else {
         double t;
-        locate(x, smol[3 * s + d], g.M[d], g.P, i0[d], t);
+        locate_u(u, g.M[d], g.P, i0[d], t);
         tmp_t[d * nmax + i] = R(t);
       }
     }
@@ -467,7 +479,7 @@ __device__ inline void block_partials(double e, double vx, double vy, double vz,
 template <typename R>
 __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, MultParams mp,
                                                   const int* __restrict__ pch, const double* __restrict__ scale,
-                                                  const double* __restrict__ kfac, const R* __restrict__ coef,
+                                                  const double* __restrict__ bmat, const R* __restrict__ coef,
                                                   const R* __restrict__ iw2, int iw2_stride,
                                                   double* __restrict__ part, int want_energy,
                                                   double* __restrict__ vpart) {
@@ -484,7 +496,9 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   const R* iw2z = iw2y + iw2_stride;
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
-  const R kf0 = R(kfac[3 * s]), kf1 = R(kfac[3 * s + 1]), kf2 = R(kfac[3 * s + 2]);
+  R bm[9];   // k = B m, B = 2 pi H^-1 of structure s (diagonal for a box)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) bm[i] = R(bmat[9 * s + i]);
   const bool even_x = (mp.M[0] % 2) == 0;
   EnergyAcc<R> e;
   double vx = 0.0, vy = 0.0, vz = 0.0;
@@ -508,8 +522,9 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   for (int64_t el = el0; el < nel; el += stride) {
     const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
     const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
-    const R ky = kf1 * R(my), kz = kf2 * R(mz);
-    const R kx = kf0 * R(ix);
+    const R kx = bm[0] * R(ix) + bm[1] * R(my) + bm[2] * R(mz);
+    const R ky = bm[3] * R(ix) + bm[4] * R(my) + bm[5] * R(mz);
+    const R kz = bm[6] * R(ix) + bm[7] * R(my) + bm[8] * R(mz);
     const R k2 = kx * kx + ky * ky + kz * kz;
     Cplx<R>* dp = d + el;
     if (!(k2 < kc2) || k2 == R(0)) {
@@ -565,7 +580,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ data, MultParams mp, int nkx,
                                                          const int* __restrict__ pch,
                                                          const double* __restrict__ scale,
-                                                         const double* __restrict__ kfac, const R* __restrict__ coef,
+                                                         const double* __restrict__ bmat, const R* __restrict__ coef,
                                                          const R* __restrict__ iw2, int iw2_stride,
                                                          double* __restrict__ part, int want_energy,
                                                          double* __restrict__ vpart) {
@@ -580,15 +595,22 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
   const R* iw2z = iw2y + iw2_stride;
   const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
   const R inv_kc = R(mp.inv_kc);
-  const R kf0 = R(kfac[0]), kf1 = R(kfac[1]), kf2 = R(kfac[2]);
+  R bm[9];   // k = B m (B = 2 pi H^-1; diagonal for a box)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) bm[i] = R(bmat[i]);
   EnergyAcc<R> e;
   double vx = 0.0, vy = 0.0, vz = 0.0;
   const int nline = nkx * mp.M[2];
   for (int line = blockIdx.x; line < nline; line += gridDim.x) {
     const int ix = line / mp.M[2], iz = line - ix * mp.M[2];
     const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
-    const R kx = kf0 * R(ix), kz = kf2 * R(mz);
-    const R kxz2 = kx * kx + kz * kz;
+    // the line's part of k (kx and kz modes), then + my b_y per element
+    const R lx = bm[0] * R(ix) + bm[2] * R(mz), ly = bm[3] * R(ix) + bm[5] * R(mz),
+            lz = bm[6] * R(ix) + bm[8] * R(mz);
+    // smallest |k|^2 of the line over real my: |l|^2 - (l . b_y)^2 / |b_y|^2
+    // (= |l|^2 for a box, where b_y is orthogonal to l)
+    const R lb = lx * bm[1] + ly * bm[4] + lz * bm[7];
+    const R kxz2 = lx * lx + ly * ly + lz * lz - lb * lb / (bm[1] * bm[1] + bm[4] * bm[4] + bm[7] * bm[7]);
     Cplx<R>* dl = d + (int64_t(ix) * mp.M[2] + iz) * mp.M[1];
     if (!(kxz2 < kc2)) {
       for (int iy = threadIdx.x; iy < mp.M[1]; iy += blockDim.x) dl[iy] = Cplx<R>{R(0), R(0)};
@@ -599,8 +621,8 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
     const R wedge = ix == 0 ? R(0.5) : R(1);
     for (int iy = threadIdx.x; iy < mp.M[1]; iy += blockDim.x) {
       const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
-      const R ky = kf1 * R(my);
-      const R k2 = kxz2 + ky * ky;
+      const R kx = lx + bm[1] * R(my), ky = ly + bm[4] * R(my), kz = lz + bm[7] * R(my);
+      const R k2 = kx * kx + ky * ky + kz * kz;
       if (!(k2 < kc2) || k2 == R(0)) {
         dl[iy] = Cplx<R>{R(0), R(0)};
         continue;
@@ -635,6 +657,20 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
   }
   if (!want_energy) return;
   block_partials(e.value(), vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
+}
+
+// ---- general cells: forces from grid-coordinate gradients ---------------------------
+// The gathers of a general cell run with unit M/L (derivative scale 2 per
+// grid cell), so they leave f_u, the gradient with respect to the grid
+// coordinates u = T r; the Cartesian force is F = T^T f_u (T = diag(M) H^-T,
+// row-major tmat of the single structure).
+template <typename R>
+__global__ void k_force_cell(int64_t n, const double* __restrict__ tmat, R* __restrict__ forces) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double f0 = forces[3 * i], f1 = forces[3 * i + 1], f2 = forces[3 * i + 2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) forces[3 * i + d] = R(tmat[d] * f0 + tmat[3 + d] * f1 + tmat[6 + d] * f2);
+  }
 }
 
 // ---- interpolation, direct from global memory (fallback kernel) ---------------------

@@ -460,6 +460,66 @@ int plan_core(const double box_max[3], int K, const int* pset, int npset, const 
 
 }  // namespace
 
+namespace {
+
+// W-hat tables, scale and geometry matrices for lattice vectors H (rows).
+void fill_cell_tables(const Plan& plan, const double H[9], StructTables& out) {
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  // H^-1 by cofactors
+  double inv[9];
+  inv[0] = (H[4] * H[8] - H[5] * H[7]) / det;
+  inv[1] = (H[2] * H[7] - H[1] * H[8]) / det;
+  inv[2] = (H[1] * H[5] - H[2] * H[4]) / det;
+  inv[3] = (H[5] * H[6] - H[3] * H[8]) / det;
+  inv[4] = (H[0] * H[8] - H[2] * H[6]) / det;
+  inv[5] = (H[2] * H[3] - H[0] * H[5]) / det;
+  inv[6] = (H[3] * H[7] - H[4] * H[6]) / det;
+  inv[7] = (H[1] * H[6] - H[0] * H[7]) / det;
+  inv[8] = (H[0] * H[4] - H[1] * H[3]) / det;
+  out.V = std::fabs(det);
+  out.dV = 1.0;
+  out.tric = false;
+  for (int i = 0; i < 9; ++i) {
+    out.cell[i] = H[i];
+    if (i % 4 != 0 && H[i] != 0.0) out.tric = true;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const double len = std::sqrt(H[3 * d] * H[3 * d] + H[3 * d + 1] * H[3 * d + 1] + H[3 * d + 2] * H[3 * d + 2]);
+    out.box[d] = len;
+    out.h[d] = len / double(plan.M[d]);
+    out.dV *= out.h[d];
+    out.omega[d] = plan.P * out.h[d] / 2.0;
+    for (int e = 0; e < 3; ++e) {
+      out.tmat[3 * d + e] = double(plan.M[d]) * inv[3 * e + d];   // (H^-T)[d][e] = (H^-1)[e][d]
+      out.bmat[3 * d + e] = 2.0 * kPi * inv[3 * d + e];
+    }
+    // the window transform per grid cell in units of h_d: k_d = 2 pi m / |a_d|
+    // puts omega k_d = pi P m / M_d, independent of the cell
+    const int nf = plan.M[d] / 2 + 1;
+    out.iw2[d].assign(nf, 0.0);
+    for (int m = 0; m < nf; ++m) {
+      const double kd = 2.0 * kPi * m / len;
+      const double arg = out.omega[d] * kd / plan.c_w;
+      if (arg <= 1.0) {
+        const double what = out.omega[d] * plan.win.lambda0 * plan.win.eval(arg);
+        out.iw2[d][m] = 1.0 / (what * what);
+      }
+    }
+  }
+  if (!out.tric) {
+    // an orthorhombic box: the exact products V / M and M / L, 2 pi / L
+    out.V = std::fabs(H[0] * H[4] * H[8]);
+    out.dV = out.V / (double(plan.M[0]) * plan.M[1] * plan.M[2]);
+    for (int d = 0; d < 3; ++d) {
+      out.tmat[4 * d] = double(plan.M[d]) / out.box[d];
+      out.bmat[4 * d] = 2.0 * kPi / out.box[d];
+    }
+  }
+}
+
+}  // namespace
+
 int struct_tables(const Plan& plan, const double box[3], StructTables& out, std::string& error) {
   for (int d = 0; d < 3; ++d) {
     if (!(box[d] > 0.0) || !std::isfinite(box[d])) {
@@ -471,23 +531,8 @@ int struct_tables(const Plan& plan, const double box[3], StructTables& out, std:
       return PSWF_EINVAL;
     }
   }
-  out.V = box[0] * box[1] * box[2];
-  out.dV = out.V / (double(plan.M[0]) * plan.M[1] * plan.M[2]);
-  for (int d = 0; d < 3; ++d) {
-    out.box[d] = box[d];
-    out.h[d] = box[d] / double(plan.M[d]);
-    out.omega[d] = plan.P * out.h[d] / 2.0;
-    const int nf = plan.M[d] / 2 + 1;
-    out.iw2[d].assign(nf, 0.0);
-    for (int m = 0; m < nf; ++m) {
-      const double kd = 2.0 * kPi * m / box[d];
-      const double arg = out.omega[d] * kd / plan.c_w;
-      if (arg <= 1.0) {
-        const double what = out.omega[d] * plan.win.lambda0 * plan.win.eval(arg);
-        out.iw2[d][m] = 1.0 / (what * what);
-      }
-    }
-  }
+  const double H[9] = {box[0], 0, 0, 0, box[1], 0, 0, 0, box[2]};
+  fill_cell_tables(plan, H, out);
   return PSWF_OK;
 }
 
@@ -495,6 +540,32 @@ int make_batch_plan(const double box_max[3], int K, const int* pset, int npset, 
   plan = Plan();
   if (npset < 1 || !pset) return fail(plan, PSWF_EINVAL, "at least one channel exponent is required");
   return plan_core(box_max, K, pset, npset, opt, plan);
+}
+
+int make_plan_cell(const double cell[9], int K, const int* p, const Options& opt, Plan& plan) {
+  plan = Plan();
+  if (K < 1 || K > kMaxK) return fail(plan, PSWF_EINVAL, "number of channels must be in 1..64");
+  double len[3];
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) return fail(plan, PSWF_EINVAL, "cell entries must be finite");
+  for (int d = 0; d < 3; ++d)
+    len[d] = std::sqrt(cell[3 * d] * cell[3 * d] + cell[3 * d + 1] * cell[3 * d + 1] + cell[3 * d + 2] * cell[3 * d + 2]);
+  int rc = plan_core(len, K, p, K, opt, plan);
+  if (rc) return rc;
+  plan.p.assign(p, p + K);
+  fill_cell_tables(plan, cell, plan.st);
+  if (!(plan.st.V > 1e-9 * len[0] * len[1] * len[2])) return fail(plan, PSWF_EINVAL, "cell vectors are (nearly) coplanar");
+  plan.V = plan.st.V;
+  for (int d = 0; d < 3; ++d) plan.iw2[d] = plan.st.iw2[d];
+  plan.mult_scale.resize(K);
+  plan.self_coef.resize(K);
+  plan.zero_coef.resize(K);
+  for (int k = 0; k < K; ++k) {
+    plan.mult_scale[k] = plan.mult_scale_p[p[k]];
+    plan.self_coef[k] = plan.self_coef_p[p[k]];
+    plan.zero_coef[k] = plan.zero_num_p[p[k]] / plan.V;
+  }
+  return PSWF_OK;
 }
 
 int make_plan(const double box[3], int K, const int* p, const Options& opt, Plan& plan) {

@@ -60,13 +60,20 @@ struct Options {
   int precision = 0;      // 0 fp32 path, 1 fp64 path
 };
 
-// Box-dependent tables of one structure on a plan's grid.
+// Cell-dependent tables of one structure on a plan's grid.  The cell's
+// lattice vectors a_d are the rows of H (an orthorhombic box: H = diag(L));
+// the grid is uniform in the fractional coordinates, u_d = M_d s_d.
 struct StructTables {
-  double box[3] = {0, 0, 0};
-  double h[3] = {0, 0, 0};
-  double omega[3] = {0, 0, 0};
-  double V = 0, dV = 0;
-  std::vector<double> iw2[3];      // W-hat_d^-2 by |frequency| (0 .. M_d/2)
+  double box[3] = {0, 0, 0};       // edge lengths |a_d|
+  double h[3] = {0, 0, 0};         // |a_d| / M_d
+  double omega[3] = {0, 0, 0};     // P h_d / 2
+  double V = 0;                    // |det H|
+  double dV = 0;                   // prod_d h_d (= V / M for a box): the multiplier scale is dV^2 / V
+  std::vector<double> iw2[3];      // (h_d W-hat_d)^-2 by |frequency| (0 .. M_d/2)
+  double cell[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // H, row-major
+  double tmat[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // T = diag(M) H^-T: u = T r
+  double bmat[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // B = 2 pi H^-1: k_m = B m
+  bool tric = false;                              // H has off-diagonal entries
 };
 
 struct Plan {
@@ -118,6 +125,12 @@ int make_batch_plan(const double box_max[3], int K, const int* pset, int npset, 
 
 // Tables of one structure with edges `box` (each <= box_max) on the plan's grid.
 int struct_tables(const Plan& plan, const double box[3], StructTables& out, std::string& error);
+
+// Single structure in a general (triclinic) cell: lattice vectors as the rows
+// of cell[9] (right-handed or not; V = |det|).  Grid, stencil and window are
+// chosen for the edge lengths |a_d| (the spacing that bounds the band's
+// extent in each grid direction is |a_d| / M_d).
+int make_plan_cell(const double cell[9], int K, const int* p, const Options& opt, Plan& plan);
 
 // Smooth part S_p(u) of Phi-hat_p = mult_scale_p * singular_p(k) * S_p(u),
 // u = k / k_c in [0, 1] (host FP64 reference used to fit the polynomials).

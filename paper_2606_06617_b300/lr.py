@@ -46,7 +46,7 @@ class PswfInfo(ctypes.Structure):
                 ("deg_window", ctypes.c_int), ("deg_mult", ctypes.c_int), ("flags", ctypes.c_int),
                 ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("B", ctypes.c_int), ("batch", ctypes.c_int), ("transform", ctypes.c_int),
-                ("nkx", ctypes.c_int)]
+                ("nkx", ctypes.c_int), ("cell", ctypes.c_double * 9)]
 
 
 MAX_BUCKETS = 16
@@ -72,6 +72,8 @@ SIGNATURES = {
     "pswf_opts_default": ([ctypes.POINTER(PswfOpts)], None),
     "pswf_plan_params": ([_dp, ctypes.c_int, _ip, ctypes.POINTER(PswfOpts), ctypes.POINTER(PswfInfo)], ctypes.c_int),
     "pswf_plan_create": ([_dp, _i64, ctypes.c_int, _ip, ctypes.POINTER(PswfOpts), _vp, ctypes.POINTER(_vp)],
+                         ctypes.c_int),
+    "pswf_plan_create_cell": ([_dp, _i64, ctypes.c_int, _ip, ctypes.POINTER(PswfOpts), _vp, ctypes.POINTER(_vp)],
                          ctypes.c_int),
     "pswf_plan_info": ([_vp, ctypes.POINTER(PswfInfo)], ctypes.c_int),
     "pswf_plan_set_workspace": ([_vp, _vp, _i64], ctypes.c_int),
@@ -176,14 +178,23 @@ class Plan:
 
     def __init__(self, box, n_max: int, ps, r_c: float, *, tol: float = 1e-5, c: float = 0.0,
                  c_w: float = 0.0, eta: float = 0.0, P: int = 0, grid=None, precision: int = 0,
-                 flags: int = 0, device=None):
+                 flags: int = 0, device=None, cell=None):
+        """box: three edge lengths of an orthorhombic box, or None with
+        cell: 3 x 3 lattice vectors as rows (general cell,
+        pswf_plan_create_cell)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("PSWF-LR needs a CUDA device")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.K = len(ps)
         self.ps = tuple(int(p) for p in ps)
-        self.box = tuple(float(b) for b in box)
+        if cell is not None:
+            import numpy as np
+            cell_a = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(cell, dtype=np.float64).reshape(9)])
+            self.box = tuple(float(x) for x in np.linalg.norm(np.asarray(cell, dtype=np.float64).reshape(3, 3), axis=1))
+        else:
+            cell_a = None
+            self.box = tuple(float(b) for b in box)
         self.dtype = torch.float64 if precision == 1 else torch.float32
         L = lib()
         box_a = (ctypes.c_double * 3)(*self.box)
@@ -192,7 +203,12 @@ class Plan:
         h = _vp()
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
-            _check(L.pswf_plan_create(box_a, int(n_max), self.K, p_a, ctypes.byref(o), _vp(stream), ctypes.byref(h)))
+            if cell_a is not None:
+                _check(L.pswf_plan_create_cell(cell_a, int(n_max), self.K, p_a, ctypes.byref(o), _vp(stream),
+                                               ctypes.byref(h)))
+            else:
+                _check(L.pswf_plan_create(box_a, int(n_max), self.K, p_a, ctypes.byref(o), _vp(stream),
+                                          ctypes.byref(h)))
         self._h = h
         self.n_max = int(n_max)
         info = PswfInfo()
