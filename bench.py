@@ -9,10 +9,13 @@ L = 350 A, K = 4 channels p = 1, 2, 4, 6, grid 384^3, stencil P = 7), FP32
 with FP64 tables and reductions.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload melt|melt_quarter|water]
+                  [--workload melt|melt_quarter|melt_triclinic|water|serving|training]
 
 melt_quarter is the same melt at the same density in a 256^3 grid (1,242,757
 atoms, L = 233.33 A): the case the kernel-level ncu captures are taken on.
+melt_triclinic is the 4,194,304-atom melt in a sheared cell of the same
+volume (lattice vectors (350, 0, 0), (60, 350, 0), (-40, 50, 350)) on the
+same 384^3 grid (pswf_plan_create_cell).
 
 Under torchrun each rank evaluates its own replica (seed = rank): the single
 system does not shard, so N > 1 is N independent replicas (weak scaling).
@@ -41,6 +44,8 @@ WORKLOADS = {
                  grid=384),
     "melt_quarter": dict(name="ionic_melt_1242757", N=1242757, L=350.0 * 256 / 384, ps=(1, 2, 4, 6), r_c=7.0,
                          tol=1e-5, P=7, grid=256),
+    "melt_triclinic": dict(name="ionic_melt_triclinic_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0,
+                           tol=1e-5, P=7, grid=384, shear=((0.0, 0.0), (60.0, 0.0), (-40.0, 50.0))),
     "serving": dict(name="serving_stream_4096"),
     "training": dict(name="training_batch_64x16"),
     "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=5e-6, P=8, grid=64),
@@ -48,12 +53,29 @@ WORKLOADS = {
 METRIC = "LR energy+force atoms/s at 1e-5 force err"
 
 
+def shear_cell(L: float, shear, scale: float = 1.0) -> np.ndarray:
+    """Lattice vectors (rows) L e_d plus the given entries below the diagonal
+    (det = L^3: the cube's volume), times scale."""
+    H = np.diag([L, L, L]).astype(np.float64)
+    H[1, 0] = shear[1][0]
+    H[2, 0], H[2, 1] = shear[2]
+    return H * scale
+
+
 def make_system(wk: str, seed: int):
     from paper_2606_06617_b300 import workloads as wl
     w = WORKLOADS[wk]
     if wk.startswith("melt"):
-        return wl.ionic_melt(w["N"], w["L"], seed=seed)
-    return wl.water_box(seed=seed)
+        s = wl.ionic_melt(w["N"], w["L"], seed=seed)
+        s.cell = None
+        if "shear" in w:
+            # the same fractional coordinates in the sheared cell
+            s.cell = shear_cell(w["L"], w["shear"])
+            s.pos = (s.pos / w["L"]) @ s.cell
+        return s
+    s = wl.water_box(seed=seed)
+    s.cell = None
+    return s
 
 
 def algorithmic_bytes(w, K: int, n: int, rs: int = 4) -> dict:
@@ -149,13 +171,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
-    """The FP64 oracle (O1) on a bounded, density-matched sample of the
-    workload, on this host's cores.  Returns (atoms/s, cores, description)."""
-    import torch
+def oracle_sample(wk: str):
+    """The O1 oracle on a bounded, density-matched sample of the workload
+    (melts: a 64^3 sub-box, sheared like the workload's cell; water: the
+    whole box).  Returns (oracle, system, description)."""
     from oracle.grid import DiscretePSWF, GridConfig
     from paper_2606_06617_b300 import workloads as wl
     w = WORKLOADS[wk]
+    cell = None
     if wk.startswith("melt"):
         Msub = 64
         Lsub = w["L"] * Msub / w["grid"]
@@ -163,14 +186,26 @@ def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
         s = wl.ionic_melt(n, Lsub, seed=1)
         M = (Msub,) * 3
         desc = f"density-matched sub-box L={Lsub:.2f} A, {n} atoms, grid {Msub}^3, K=4, P={w['P']}"
+        if "shear" in w:
+            cell = shear_cell(w["L"], w["shear"], Msub / w["grid"])
+            s.pos = (s.pos / Lsub) @ cell
+            desc = "sheared " + desc
     else:
         s = wl.water_box(seed=1)
         M = (w["grid"],) * 3
         desc = "whole water box"
     c = math.log(3.0 / w["tol"])
-    eta = (s.box[0] / M[0]) * (c / w["r_c"]) / math.pi
+    edge = max(np.linalg.norm(cell, axis=1)) if cell is not None else s.box[0]
+    eta = (edge / M[0]) * (c / w["r_c"]) / math.pi
     cw = w["P"] * math.pi * (1 - eta / 2)
-    o = DiscretePSWF(GridConfig(s.box, M, w["P"], c, w["r_c"], s.ps, c_w=cw))
+    return DiscretePSWF(GridConfig(s.box, M, w["P"], c, w["r_c"], s.ps, c_w=cw, cell=cell)), s, desc
+
+
+def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
+    """The FP64 oracle (O1) on a bounded, density-matched sample of the
+    workload, on this host's cores.  Returns (atoms/s, cores, description)."""
+    import torch
+    o, s, desc = oracle_sample(wk)
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -361,20 +396,10 @@ def run_training(steps: int = 20, warmup: int = 5, seed: int = 0) -> dict:
 def run_reference(args, rank: int):
     """--impl reference: the CPU oracle as it stands, bounded sample per step."""
     import torch
-    from oracle.grid import DiscretePSWF, GridConfig
-    from paper_2606_06617_b300 import workloads as wl
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    melt = args.workload.startswith("melt")
-    Msub = 64 if melt else w["grid"]
-    Lsub = w["L"] * Msub / w["grid"]
-    n = int(round(w["N"] * (Lsub / w["L"]) ** 3)) if melt else 3000
-    s = wl.ionic_melt(n, Lsub, seed=1) if melt else wl.water_box(seed=1)
-    M = (Msub,) * 3
-    c = math.log(3.0 / w["tol"])
-    eta = (s.box[0] / M[0]) * (c / w["r_c"]) / math.pi
-    o = DiscretePSWF(GridConfig(s.box, M, w["P"], c, w["r_c"], s.ps, c_w=w["P"] * math.pi * (1 - eta / 2)))
+    o, s, desc = oracle_sample(args.workload)
     for _ in range(args.warmup):
         o.evaluate(s.pos, s.q)
     t0 = time.perf_counter()
@@ -382,7 +407,7 @@ def run_reference(args, rank: int):
         o.evaluate(s.pos, s.q)
     dt = (time.perf_counter() - t0) / args.steps
     value = s.n / dt
-    sample = f"density-matched sample of {w['name']}: {s.n} atoms, grid {Msub}^3, P={w['P']}"
+    sample = f"{w['name']}: {desc}"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "atoms/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
@@ -449,7 +474,8 @@ def main():
 
     w = WORKLOADS[args.workload]
     sysm = make_system(args.workload, seed=rank)
-    plan = lr.Plan(sysm.box, sysm.n, sysm.ps, w["r_c"], tol=w["tol"], P=w["P"], grid=w["grid"], device=dev)
+    plan = lr.Plan(sysm.box, sysm.n, sysm.ps, w["r_c"], tol=w["tol"], P=w["P"], grid=w["grid"], device=dev,
+                   cell=sysm.cell)
     pos = torch.tensor(sysm.pos, device=dev)
     q = torch.tensor(sysm.q, dtype=torch.float32, device=dev)
     out = (torch.empty(len(sysm.ps) + 1, dtype=torch.float64, device=dev),
@@ -547,7 +573,7 @@ def main():
 
     serving = None
     info = dict(plan.info)
-    if rank == 0 and world == 1 and not args.no_serving and args.workload.startswith("melt"):
+    if rank == 0 and world == 1 and not args.no_serving and args.workload == "melt":
         del plan, pos, q, out
         torch.cuda.empty_cache()
         serving = run_serving()
@@ -563,6 +589,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "atoms": sysm.n, "box_A": w["L"], "channels_p": list(sysm.ps),
+                       **({"cell_A": sysm.cell.tolist()} if sysm.cell is not None else {}),
                        "grid": info["grid"], "P": info["P"], "r_c": w["r_c"], "c": info["c"],
                        "c_w": info["c_w"], "tol": w["tol"],
                        "l2": "L2 flushed (256 MB write) between timed steps" if small

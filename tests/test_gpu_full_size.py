@@ -80,3 +80,29 @@ def test_ionic_melt_full_size_fp32_within_budget_of_fp64():
         assert abs(e32[c] - e64[c]) <= 2e-6 * abs(e64[c]), (c, e32[c], e64[c])
         assert rel_rms(p32[c], p64[c]) <= 2e-6, (c, rel_rms(p32[c], p64[c]))
     assert rel_rms(f32, f64) <= 2e-6, rel_rms(f32, f64)
+
+
+def test_sheared_melt_full_size_fp32_within_budget_of_fp64():
+    """The 4,194,304-atom melt in a sheared cell of the same volume
+    (pswf_plan_create_cell, 384^3): FP32 within the FP32 budget of FP64."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.ionic_melt(4194304, 350.0, seed=0)
+    H = np.array([[350.0, 0.0, 0.0], [60.0, 350.0, 0.0], [-40.0, 50.0, 350.0]])
+    pos = torch.tensor((s.pos / 350.0) @ H, device=dev)
+    out = {}
+    for prec in (0, 1):
+        plan = lr.Plan(None, s.n, s.ps, 7.0, tol=1e-5, P=7, grid=384, precision=prec, device=dev, cell=H)
+        plan.set_points(pos, torch.tensor(s.q, dtype=plan.dtype, device=dev))
+        e, phi, f = plan.execute()
+        plan.sync()
+        out[prec] = (e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy(), plan.info["transform"])
+        del plan, e, phi, f
+        torch.cuda.empty_cache()
+    (e32, p32, f32, t32), (e64, p64, f64, _) = out[0], out[1]
+    assert t32 == lr.PSWF_TRANSFORM_OWN
+    for c in range(4):
+        assert abs(e32[c] - e64[c]) <= 2e-6 * abs(e64[c]), (c, e32[c], e64[c])
+        assert rel_rms(p32[c], p64[c]) <= 2e-6, (c, rel_rms(p32[c], p64[c]))
+    assert rel_rms(f32, f64) <= 2e-6, rel_rms(f32, f64)
