@@ -197,6 +197,20 @@ __device__ inline void window_values(R t, const WinCoef<R>& wc, R (&w)[P]) {
 // k_bin: locate each atom (original order), count it into its tile and keep
 // its rank there, its offsets t and its packed start cell for k_scatter.
 // smol[s][d] = M_d / L_d of structure s.
+// Stencil start and offset of one coordinate u, stored as R.
+template <typename R>
+__device__ inline void locate_one(double u, int M, int P, int& i0, R* t_out) {
+  if constexpr (sizeof(R) == 4) {
+    float t;
+    locate_fx_u(u, M, P, i0, t);
+    *t_out = t;
+  } else {
+    double t;
+    locate_u(u, M, P, i0, t);
+    *t_out = R(t);
+  }
+}
+
 // tmat[s][9] = T = diag(M) H^-T of structure s (general cells, g.tric):
 // u = T r; boxes use u_d = r_d M_d / L_d (smol).
 template <typename PosT, typename R>
@@ -207,31 +221,33 @@ __global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __
   const int64_t n = soff[g.B];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int s = find_struct(soff, 1, g.B, i);
-    double x[3];
-    for (int d = 0; d < 3; ++d) {
-      x[d] = double(pos[3 * i + d]);
-      if (((__double_as_longlong(x[d]) >> 52) & 0x7FF) == 0x7FF) {   // inf or nan
-        atomicCAS(err, 0, -6);
-        x[d] = 0.0;
-      }
-    }
     int i0[3];
-    for (int d = 0; d < 3; ++d) {
-      double u;
-      if (g.tric) {
-        const double* T = tmat + 9 * s + 3 * d;
-        u = fma(T[0], x[0], fma(T[1], x[1], T[2] * x[2]));
-      } else {
-        u = x[d] * smol[3 * s + d];
+    if (!g.tric) {
+      // box: u_d = r_d M_d / L_d
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double x = double(pos[3 * i + d]);
+        if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) {   // inf or nan
+          atomicCAS(err, 0, -6);
+          x = 0.0;
+        }
+        locate_one<R>(x * smol[3 * s + d], g.M[d], g.P, i0[d], tmp_t + d * nmax + i);
       }
-      if constexpr (sizeof(R) == 4) {
-        float t;
-        locate_fx_u(u, g.M[d], g.P, i0[d], t);
-        tmp_t[d * nmax + i] = t;
-      } else {
-        double t;
-        locate_u(u, g.M[d], g.P, i0[d], t);
-        tmp_t[d * nmax + i] = R(t);
+    } else {
+      // general cell: u = T r
+      double x[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        x[d] = double(pos[3 * i + d]);
+        if (((__double_as_longlong(x[d]) >> 52) & 0x7FF) == 0x7FF) {
+          atomicCAS(err, 0, -6);
+          x[d] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double* T = tmat + 9 * s + 3 * d;
+        locate_one<R>(fma(T[0], x[0], fma(T[1], x[1], T[2] * x[2])), g.M[d], g.P, i0[d], tmp_t + d * nmax + i);
       }
     }
     const int tile = s * g.nts + ((i0[2] / kTile) * g.ntile[1] + i0[1] / kTile) * g.ntile[0] + i0[0] / kTile;
