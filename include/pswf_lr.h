@@ -126,10 +126,10 @@ int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p,
  * and the modes are k = 2 pi H^-1 m (Methods, with the box replaced by the
  * cell: Eq. (Fourier) sums over the reciprocal lattice); grid, P and c_w are
  * chosen for the edge lengths |a_d|.  Forces are Cartesian.  Otherwise as
- * pswf_plan_create; an orthorhombic cell gives the box plan.  Returns
- * PSWF_EINVAL for non-finite or (nearly) coplanar vectors, and for
- * PSWF_FLAG_BACKWARD or PSWF_FLAG_VIRIAL with a non-orthorhombic cell
- * (forward only). */
+ * pswf_plan_create (pswf_backward included: its dL/dr is Cartesian too);
+ * an orthorhombic cell gives the box plan.  Returns PSWF_EINVAL for
+ * non-finite or (nearly) coplanar vectors, and for PSWF_FLAG_VIRIAL with a
+ * non-orthorhombic cell (the diagonal virial is defined for boxes). */
 int pswf_plan_create_cell(const double cell[9], int64_t n_max, int K, const int* p, const pswf_opts* opts,
                           void* stream, pswf_plan* out);
 

@@ -979,10 +979,21 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
   if (!grad_q && !grad_pos) return PSWF_OK;
   StageScope scope(p, PSWF_STAGE_BACKWARD);
   const LaunchCtx ctx = make_ctx(p);
-  const BackwardArgs b{g_energy, g_phi, g_forces, grad_q, grad_pos};
   const int K = p->host.K;
   int nl = 0;
   cudaError_t e;
+  const int cblocks = int(std::min<int64_t>((std::max<int64_t>(p->n, 1) + kThreads - 1) / kThreads, 148 * 8));
+  if (p->tric && g_forces && p->n > 0) {
+    // general cell: g_F into grid coordinates, g_u = T g_F, in the binning
+    // scratch (free once set_points has sorted the atoms; n x 3 fits its
+    // 3 x n_max reals); the kernels below then run as for a box
+    k_grad_to_cell<R><<<cblocks, kThreads, 0, s>>>(p->n, p->tmat, static_cast<const R*>(g_forces),
+                                                    static_cast<R*>(p->tmp_t));
+    if ((rc = launch_check(p, "k_grad_to_cell"))) return rc;
+    ++nl;
+    g_forces = p->tmp_t;
+  }
+  const BackwardArgs b{g_energy, g_phi, g_forces, grad_q, grad_pos};
   if (g_phi) {
     if ((rc = charge_sums<R>(p, g_phi, p->bsum))) return rc;
     nl += 2;
@@ -1001,8 +1012,15 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
     if ((rc = fft_exec(p, p->grid2, false))) return rc;
   }
   e = sizeof(R) == 4 ? launch_backward_float(ctx, b, 1, &nl) : launch_backward_double(ctx, b, 1, &nl);
+  if ((rc = cuda_check(p, e, "backward gather"))) return rc;
+  if (p->tric && grad_pos && p->n > 0) {
+    // dL/dr = T^T dL/du
+    k_force_cell<R><<<cblocks, kThreads, 0, s>>>(p->n, p->tmat, static_cast<R*>(grad_pos));
+    if ((rc = launch_check(p, "k_force_cell"))) return rc;
+    ++nl;
+  }
   p->launches[PSWF_STAGE_BACKWARD] += nl;
-  return cuda_check(p, e, "backward gather");
+  return PSWF_OK;
 }
 
 // Per-batch structure tables: filled on the host into the plan's pinned
@@ -1280,8 +1298,8 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->geo.K = h.K;
   pl->tric = b == 1 && h.st.tric;
   pl->geo.tric = pl->tric ? 1 : 0;
-  if (pl->tric && (opts->flags & (PSWF_FLAG_BACKWARD | PSWF_FLAG_VIRIAL)))
-    return set_err(pl, PSWF_EINVAL, "general cells: PSWF_FLAG_BACKWARD and PSWF_FLAG_VIRIAL need an orthorhombic box");
+  if (pl->tric && (opts->flags & PSWF_FLAG_VIRIAL))
+    return set_err(pl, PSWF_EINVAL, "general cells: PSWF_FLAG_VIRIAL needs an orthorhombic box");
   pl->geo.nts = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
   pl->geo.B = b;
   pl->nts = pl->geo.nts;

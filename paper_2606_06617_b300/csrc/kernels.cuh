@@ -689,6 +689,18 @@ __global__ void k_force_cell(int64_t n, const double* __restrict__ tmat, R* __re
   }
 }
 
+// Upstream force gradients of a general cell into grid coordinates,
+// g_u = T g (the backward kernels then work as for a box with unit M / L).
+template <typename R>
+__global__ void k_grad_to_cell(int64_t n, const double* __restrict__ tmat, const R* __restrict__ g,
+                               R* __restrict__ gu) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double g0 = g[3 * i], g1 = g[3 * i + 1], g2 = g[3 * i + 2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gu[3 * i + d] = R(tmat[3 * d] * g0 + tmat[3 * d + 1] * g1 + tmat[3 * d + 2] * g2);
+  }
+}
+
 // ---- interpolation, direct from global memory (fallback kernel) ---------------------
 // One thread per sorted atom, for plans whose padded regions do not fit in
 // shared memory.  phi_c = sum Psi_c W; F = sum_c q_c sum Psi_c grad W, with

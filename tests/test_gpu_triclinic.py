@@ -4,7 +4,8 @@ The same sheared cell on every transform path (own passes FP32, pruned
 cuFFT FP32 and FP64, full cuFFT transform) against the O1 oracle of that
 cell with the same grid, P, c and c_w (FP32 2e-6, FP64 2e-9 relative RMS);
 a rotated box against the box (rotation invariance of the GPU path); a
-diagonal cell equal to the box plan; backward and virial refused."""
+diagonal cell equal to the box plan; the backward against the oracle's VJP
+in the same cell; the virial refused."""
 import math
 
 import numpy as np
@@ -102,11 +103,41 @@ def test_diagonal_cell_is_the_box_plan():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-def test_general_cell_refuses_backward_and_virial():
+def test_general_cell_refuses_virial():
     import torch
     from paper_2606_06617_b300 import lr
     dev = torch.device("cuda", 0)
-    for flags in (lr.PSWF_FLAG_BACKWARD, lr.PSWF_FLAG_VIRIAL):
-        with pytest.raises(lr.PswfError) as e:
-            lr.Plan(None, 10, (1,), R_C, P=6, grid=(32, 32, 32), flags=flags, device=dev, cell=SHEARED)
-        assert e.value.status == -1
+    with pytest.raises(lr.PswfError) as e:
+        lr.Plan(None, 10, (1,), R_C, P=6, grid=(32, 32, 32), flags=lr.PSWF_FLAG_VIRIAL, device=dev, cell=SHEARED)
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("M,precision,tol", [
+    ((64, 64, 64), 0, 2e-5),   # own transform
+    ((64, 64, 64), 1, 1e-8),   # FP64, pruned cuFFT
+    ((40, 36, 30), 1, 1e-8),   # full transform
+])
+def test_sheared_cell_backward_matches_oracle_vjp(M, precision, tol):
+    """pswf_backward in a sheared cell: L = gE.E + gphi.phi + gF.F with
+    seeded upstream gradients against the oracle's reverse-mode VJP of the
+    same discrete forward (grid coordinates inside, Cartesian dL/dr out)."""
+    import torch
+    from oracle.grid import DiscretePSWF, GridConfig
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    P = 6
+    cw = _cw(SHEARED, M, P)
+    pos, q = _system(SHEARED, 250, 21)
+    rng = np.random.default_rng(3)
+    gE, gphi, gF = rng.normal(size=2), rng.normal(size=(2, len(pos))), rng.normal(size=(len(pos), 3))
+    plan = lr.Plan(None, len(pos), (1, 6), R_C, c=C, c_w=cw, P=P, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_BACKWARD, device=dev, cell=SHEARED)
+    plan.set_points(torch.tensor(pos, device=dev), torch.tensor(q, dtype=plan.dtype, device=dev))
+    plan.execute()
+    gq, gr = plan.backward(torch.tensor(gE, device=dev), torch.tensor(gphi, dtype=plan.dtype, device=dev),
+                           torch.tensor(gF, dtype=plan.dtype, device=dev))
+    plan.sync()
+    oq, orr = DiscretePSWF(GridConfig((0, 0, 0), M, P, C, R_C, (1, 6), c_w=cw, cell=SHEARED)).vjp(
+        pos, q, gE, gphi, gF)
+    assert rel_rms(gq.cpu().double().numpy(), oq.numpy()) <= tol
+    assert rel_rms(gr.cpu().double().numpy(), orr.numpy()) <= tol
