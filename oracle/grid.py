@@ -264,6 +264,40 @@ class DiscretePSWF:
 
         return (4.0 * central(eps) - central(2.0 * eps)) / 3.0
 
+    def stress_fd(self, pos, q, eps: float = 5e-5) -> np.ndarray:
+        """Virial tensor W[c] (3 x 3, symmetric) of any cell: W_ab = -dE_c /
+        d epsilon_ab under the homogeneous symmetric strain r -> (1 +
+        epsilon) r of the cell vectors and the positions together (fixed
+        fractional coordinates), same grid size, P, c and c_w.  Central
+        differences: epsilon_aa = +-h, or epsilon_ab = epsilon_ba = +-h/2
+        for a != b (so dE = -W_ab h); Richardson-extrapolated from h = eps
+        and 2 eps.  For a box the diagonal is virial_fd."""
+        pos = np.asarray(pos, dtype=np.float64)
+        K = len(self.cfg.ps)
+        c_w = self.cfg.c if self.cfg.c_w is None else self.cfg.c_w
+
+        def energy(F):
+            cfg = GridConfig(self.cfg.box, self.cfg.M, self.cfg.P, self.cfg.c, self.cfg.r_c, self.cfg.ps,
+                             c_w=c_w, cell=self.H @ F.T)
+            return DiscretePSWF(cfg).evaluate(pos @ F.T, q)["E_ch"].numpy()
+
+        def central(h):
+            W = np.zeros((K, 3, 3))
+            for a in range(3):
+                for b in range(a, 3):
+                    Es = []
+                    for sgn in (1.0, -1.0):
+                        e = np.zeros((3, 3))
+                        if a == b:
+                            e[a, a] = sgn * h
+                        else:
+                            e[a, b] = e[b, a] = sgn * h / 2.0
+                        Es.append(energy(np.eye(3) + e))
+                    W[:, a, b] = W[:, b, a] = -(Es[0] - Es[1]) / (2.0 * h)
+            return W
+
+        return (4.0 * central(eps) - central(2.0 * eps)) / 3.0
+
     def self_energy(self, q) -> np.ndarray:
         """E_self^(p) per channel (Implementation details)."""
         q = np.asarray(q, dtype=np.float64)

@@ -111,3 +111,38 @@ def test_o1_sheared_forces_are_minus_energy_gradient():
             pm[i, d] -= eps
             g = (o.evaluate(pp, q)["E"] - o.evaluate(pm, q)["E"]) / (2 * eps)
             assert abs(-g - F[i, d]) <= 1e-6 * max(1.0, abs(F[i, d])), (i, d, -g, F[i, d])
+
+
+def test_stress_diagonal_is_the_box_virial():
+    """On a box the diagonal of the strain-derivative tensor is the
+    independently coded edge-scaling virial (virial_fd)."""
+    from oracle.grid import DiscretePSWF, GridConfig
+    box = (11.0, 12.0, 10.5)
+    M = (20, 22, 20)
+    P = 6
+    pos, q = _system(np.diag(box), 30, 7, ps=(1, 6))
+    o = DiscretePSWF(GridConfig(box, M, P, C, 4.0, (1, 6), c_w=_cw(np.diag(box), M, P, C, 4.0)))
+    W = o.stress_fd(pos, q)
+    Wd = o.virial_fd(pos, q)
+    for c in range(2):
+        assert np.allclose(np.diag(W[c]), Wd[c], rtol=1e-6, atol=1e-9 * abs(Wd[c]).max())
+        assert np.allclose(W[c], W[c].T)
+
+
+def test_stress_rotates_with_the_cell():
+    """W(R H, R r) = R W(H, r) R^T, the off-diagonal entries included."""
+    from oracle.grid import DiscretePSWF, GridConfig
+    M = (20, 20, 20)
+    P = 6
+    pos, q = _system(SHEARED, 24, 8)
+    th = 0.5
+    R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    cw = _cw(SHEARED, M, P, C, 4.0)
+    W0 = DiscretePSWF(GridConfig((0, 0, 0), M, P, C, 4.0, (1, 6), c_w=cw, cell=SHEARED)).stress_fd(pos, q)
+    W1 = DiscretePSWF(GridConfig((0, 0, 0), M, P, C, 4.0, (1, 6), c_w=cw, cell=SHEARED @ R.T)).stress_fd(
+        pos @ R.T, q)
+    for c in range(2):
+        ref = R @ W0[c] @ R.T
+        # central differences of FP64 energies: ~1e-12 / eps relative rounding
+        assert np.abs(W1[c] - ref).max() <= 1e-5 * np.abs(ref).max(), (c, W1[c], ref)
+        assert np.abs(W0[c] - np.diag(np.diag(W0[c]))).max() > 1e-3 * np.abs(W0[c]).max()   # really a tensor
