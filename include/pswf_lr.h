@@ -53,7 +53,7 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------- */
 #define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */
-#define PSWF_FLAG_VIRIAL 2         /* pswf_execute also reduces the diagonal virial (pswf_virial) */
+#define PSWF_FLAG_VIRIAL 2         /* pswf_execute also reduces the virial tensor (pswf_virial, pswf_stress) */
 
 typedef struct {
   double tol;      /* target LR tolerance eps_tot (default 1e-5) */
@@ -126,10 +126,9 @@ int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p,
  * and the modes are k = 2 pi H^-1 m (Methods, with the box replaced by the
  * cell: Eq. (Fourier) sums over the reciprocal lattice); grid, P and c_w are
  * chosen for the edge lengths |a_d|.  Forces are Cartesian.  Otherwise as
- * pswf_plan_create (pswf_backward included: its dL/dr is Cartesian too);
- * an orthorhombic cell gives the box plan.  Returns PSWF_EINVAL for
- * non-finite or (nearly) coplanar vectors, and for PSWF_FLAG_VIRIAL with a
- * non-orthorhombic cell (the diagonal virial is defined for boxes). */
+ * pswf_plan_create (pswf_backward and pswf_stress included: dL/dr and the
+ * virial tensor are Cartesian too); an orthorhombic cell gives the box plan.
+ * Returns PSWF_EINVAL for non-finite or (nearly) coplanar vectors. */
 int pswf_plan_create_cell(const double cell[9], int64_t n_max, int K, const int* p, const pswf_opts* opts,
                           void* stream, pswf_plan* out);
 
@@ -235,14 +234,26 @@ int pswf_self_energy_noalloc(pswf_plan plan, int64_t n, const void* q, double* o
 
 /* Diagonal virial of the last pswf_execute (plan created with
  * PSWF_FLAG_VIRIAL), device double [B][K][3] (B = 1 for single structures):
- * W_cd = -L_d dE_c/dL_d at fixed fractional coordinates, E_c the channel
+ * W_cd = -L_d dE_c/dL_d at fixed fractional coordinates (for a box; in a
+ * general cell the Cartesian diagonal of pswf_stress), E_c the channel
  * energy of pswf_execute (reciprocal sum and zero-frequency term; the
  * self-energy does not depend on the box).  The grid density and the window
  * transform are invariant under that scaling, so W_cd = E_c + sum_m e_m
  * (d ln Phi-hat_p / d ln k) k_d^2 / k^2 over the band modes m with energy
- * terms e_m (Eq. (Fourier), Eq. (PhiH)); orthorhombic cells only.  The
- * stress of the cell is -W / V.  Asynchronous on the plan's stream. */
+ * terms e_m (Eq. (Fourier), Eq. (PhiH)).  The stress of the cell is -W / V.
+ * Asynchronous on the plan's stream. */
 int pswf_virial(pswf_plan plan, double* virial);
+
+/* Virial tensor of the last pswf_execute (plan created with
+ * PSWF_FLAG_VIRIAL), device double [B][K][6] as (xx, yy, zz, xy, xz, yz):
+ * W_ab = -dE_c / d epsilon_ab under the symmetric strain r -> (1 + epsilon) r
+ * of the cell vectors and the atoms together (fixed fractional
+ * coordinates; any cell).  The grid density and the window transform are
+ * strain-invariant and k -> (1 - epsilon) k, V -> (1 + tr epsilon) V, so
+ * W_ab = E_c delta_ab + sum_m e_m (d ln Phi-hat_p / d ln k) k_a k_b / k^2
+ * (stress for NPT; the paper has no stress).  Stress = -W / V.
+ * Asynchronous on the plan's stream. */
+int pswf_stress(pswf_plan plan, double* virial);
 
 /* Waits for the plan's stream and returns the first device-side status
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */

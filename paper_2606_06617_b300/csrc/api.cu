@@ -104,36 +104,36 @@ __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __res
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy,
                                const double* __restrict__ vpart, double* __restrict__ virial) {
-  __shared__ double sh[4][32];
+  __shared__ double sh[7][32];
   __shared__ double tot;
   const int s = blockIdx.x;
   if (threadIdx.x == 0) tot = 0.0;
   for (int c = 0; c < K; ++c) {
     const int g = s * K + c;
-    double t4[4] = {0.0, 0.0, 0.0, 0.0};
+    double t7[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-      t4[0] += part[size_t(g) * nblk + i];
+      t7[0] += part[size_t(g) * nblk + i];
       if (vpart)
-        for (int d = 0; d < 3; ++d) t4[1 + d] += vpart[(size_t(g) * nblk + i) * 3 + d];
+        for (int d = 0; d < 6; ++d) t7[1 + d] += vpart[(size_t(g) * nblk + i) * 6 + d];
     }
-    for (int q = 0; q < 4; ++q)
-      for (int o = 16; o > 0; o >>= 1) t4[q] += __shfl_down_sync(0xffffffffu, t4[q], o);
+    for (int q = 0; q < 7; ++q)
+      for (int o = 16; o > 0; o >>= 1) t7[q] += __shfl_down_sync(0xffffffffu, t7[q], o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0)
-      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x >> 5] = t4[q];
+      for (int q = 0; q < 7; ++q) sh[q][threadIdx.x >> 5] = t7[q];
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      double t[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       for (int w = 0; w < int(blockDim.x >> 5); ++w)
-        for (int q = 0; q < 4; ++q) t[q] += sh[q][w];
+        for (int q = 0; q < 7; ++q) t[q] += sh[q][w];
       const double Q = charges[2 * g];
       const double ec = t[0] + zero_coef[g] * Q * Q;
       energy[size_t(s) * (K + 1) + c] = ec;
       tot += ec;
-      // W_d = -L_d dE/dL_d: E (the 1/V prefactor and E^0 ~ 1/V) plus the
-      // log-derivative sum of the multiplier
+      // W_ab = -dE/d epsilon_ab: E delta_ab (the 1/V prefactor and E^0 ~ 1/V)
+      // plus the log-derivative sums of the multiplier
       if (vpart && virial)
-        for (int d = 0; d < 3; ++d) virial[size_t(g) * 3 + d] = ec + t[1 + d];
+        for (int d = 0; d < 6; ++d) virial[size_t(g) * 6 + d] = (d < 3 ? ec : 0.0) + t[1 + d];
     }
   }
   if (threadIdx.x == 0) energy[size_t(s) * (K + 1) + K] = tot;
@@ -494,8 +494,8 @@ int64_t layout(pswf_plan p, char* base) {
   p->epart = reinterpret_cast<double*>(take(BK * p->eblk * 8));
   p->energy_tmp = reinterpret_cast<double*>(take(B * (K + 1) * 8));
   const bool vir = (p->flags & PSWF_FLAG_VIRIAL) != 0;
-  p->vpart = vir ? reinterpret_cast<double*>(take(BK * p->eblk * 3 * 8)) : nullptr;
-  p->virial = vir ? reinterpret_cast<double*>(take(BK * 3 * 8)) : nullptr;
+  p->vpart = vir ? reinterpret_cast<double*>(take(BK * p->eblk * 6 * 8)) : nullptr;
+  p->virial = vir ? reinterpret_cast<double*>(take(BK * 6 * 8)) : nullptr;
   p->err = reinterpret_cast<int*>(take(4));
   p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
   {
@@ -1298,8 +1298,6 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->geo.K = h.K;
   pl->tric = b == 1 && h.st.tric;
   pl->geo.tric = pl->tric ? 1 : 0;
-  if (pl->tric && (opts->flags & PSWF_FLAG_VIRIAL))
-    return set_err(pl, PSWF_EINVAL, "general cells: PSWF_FLAG_VIRIAL needs an orthorhombic box");
   pl->geo.nts = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
   pl->geo.B = b;
   pl->nts = pl->geo.nts;
@@ -1496,8 +1494,22 @@ int pswf_virial(pswf_plan pl, double* virial) {
     int rc = cuda_check(pl, cudaMemsetAsync(virial, 0, bytes, pl->stream), "clear virial");
     if (rc) return rc;
   }
-  return cuda_check(pl, cudaMemcpyAsync(virial, pl->virial, size_t(pl->nrun) * pl->host.K * 3 * 8,
-                                        cudaMemcpyDeviceToDevice, pl->stream), "copy virial");
+  // the diagonal (xx, yy, zz) of each channel's six components
+  return cuda_check(pl, cudaMemcpy2DAsync(virial, 3 * 8, pl->virial, 6 * 8, 3 * 8, size_t(pl->nrun) * pl->host.K,
+                                          cudaMemcpyDeviceToDevice, pl->stream), "copy virial");
+}
+
+int pswf_stress(pswf_plan pl, double* virial) {
+  if (!pl || !virial) return PSWF_EINVAL;
+  if (!(pl->flags & PSWF_FLAG_VIRIAL)) return set_err(pl, PSWF_ESTATE, "plan was created without PSWF_FLAG_VIRIAL");
+  if (!pl->virial_valid) return set_err(pl, PSWF_ESTATE, "pswf_stress needs a preceding pswf_execute");
+  const size_t bytes = size_t(pl->B) * pl->host.K * 6 * 8;
+  if (pl->nrun < pl->B) {
+    int rc = cuda_check(pl, cudaMemsetAsync(virial, 0, bytes, pl->stream), "clear virial");
+    if (rc) return rc;
+  }
+  return cuda_check(pl, cudaMemcpyAsync(virial, pl->virial, size_t(pl->nrun) * pl->host.K * 6 * 8,
+                                        cudaMemcpyDeviceToDevice, pl->stream), "copy virial tensor");
 }
 
 int pswf_sync(pswf_plan pl) {

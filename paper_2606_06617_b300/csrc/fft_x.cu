@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
     for (int m = 0; m < N1; ++m) cp_async8(dst + lane + 32 * m, src + lane + 32 * m);
   };
   EnergyAcc<float> e;
-  double vx = 0.0, vy = 0.0, vz = 0.0;
+  double vt[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int jstep = gridDim.x * 8;
   int j = blockIdx.x * 8 + warp, cur = 0;
   if (j < nlines) fetch(j, wbuf);
@@ -485,9 +485,7 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
           if (vpart) {
             const float dS = mult_horner_d(cs, mp.deg, sv);
             const double dl = double(mult_dlog(p, S, dS * float(2 * kMultSeg), u, phi)) / double(k2);
-            vx += double(em) * dl * double(fkx * fkx);
-            vy += double(em) * dl * double(fky * fky);
-            vz += double(em) * dl * double(fkz * fkz);
+            virial_add(vt, double(em) * dl, double(fkx), double(fky), double(fkz));
           }
         }
         x.x *= G;
@@ -505,7 +503,7 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
   }
   cp_async_wait<0>();
   if (!want_energy) return;
-  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
+  block_partials(e.value(), vt, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
 }
 
 template <int N1>

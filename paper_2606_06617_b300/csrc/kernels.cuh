@@ -387,7 +387,8 @@ __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restr
                                    double* __restrict__ charges);
 // One block per structure: energy[s][c] = sum of the multiplier partials of
 // channel g = s K + c plus zero_coef[g] Q_net^2; energy[s][K] = their total.
-// With vpart: virial[g][d] = energy[s][c] + sum of the virial partials.
+// With vpart: virial[g][6] (xx, yy, zz, xy, xz, yz) = energy[s][c] on the
+// diagonal plus the sums of the virial partials.
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy,
                                const double* __restrict__ vpart, double* __restrict__ virial);
@@ -455,35 +456,39 @@ __device__ inline R mult_dlog(int p, R S, R dSu, R u, R phi) {
   }
 }
 
-// Block sums of the energy partial (and, with vpart, the three virial
-// partials) written at index `slot` of part / vpart[slot][3].
-__device__ inline void block_partials(double e, double vx, double vy, double vz, double* __restrict__ part,
+// Block sums of the energy partial (and, with vpart, the six virial
+// partials xx, yy, zz, xy, xz, yz) written at index `slot` of part /
+// vpart[slot][6].
+__device__ inline void block_partials(double e, const double (&v)[6], double* __restrict__ part,
                                       double* __restrict__ vpart, size_t slot) {
-  __shared__ double sh[4][32];
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_down_sync(0xffffffffu, e, o);
-    vx += __shfl_down_sync(0xffffffffu, vx, o);
-    vy += __shfl_down_sync(0xffffffffu, vy, o);
-    vz += __shfl_down_sync(0xffffffffu, vz, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sh[0][threadIdx.x >> 5] = e;
-    sh[1][threadIdx.x >> 5] = vx;
-    sh[2][threadIdx.x >> 5] = vy;
-    sh[3][threadIdx.x >> 5] = vz;
-  }
+  __shared__ double sh[7][32];
+  double t7[7] = {e, v[0], v[1], v[2], v[3], v[4], v[5]};
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 7; ++i) t7[i] += __shfl_down_sync(0xffffffffu, t7[i], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < 7; ++i) sh[i][threadIdx.x >> 5] = t7[i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    double t[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int w = 0; w < int(blockDim.x >> 5); ++w)
-      for (int i = 0; i < 4; ++i) t[i] += sh[i][w];
+#pragma unroll
+      for (int i = 0; i < 7; ++i) t[i] += sh[i][w];
     part[slot] = t[0];
-    if (vpart) {
-      vpart[3 * slot] = t[1];
-      vpart[3 * slot + 1] = t[2];
-      vpart[3 * slot + 2] = t[3];
-    }
+    if (vpart)
+      for (int i = 0; i < 6; ++i) vpart[6 * slot + i] = t[1 + i];
   }
+}
+
+// Virial partial of one mode: v_ab += e_m D k_a k_b / k^2 (dlk = D / k^2).
+__device__ inline void virial_add(double (&v)[6], double w, double kx, double ky, double kz) {
+  v[0] += w * kx * kx;
+  v[1] += w * ky * ky;
+  v[2] += w * kz * kz;
+  v[3] += w * kx * ky;
+  v[4] += w * kx * kz;
+  v[5] += w * ky * kz;
 }
 
 // ---- multiplier and energy (steps (iii)-(iv)) --------------------------------------
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   for (int i = 0; i < 9; ++i) bm[i] = R(bmat[9 * s + i]);
   const bool even_x = (mp.M[0] % 2) == 0;
   EnergyAcc<R> e;
-  double vx = 0.0, vy = 0.0, vz = 0.0;
+  double vt[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   // Elements of the half spectrum in storage order, spread over the
   // channel's blocks (rows of small grids are shorter than a block).  The
   // element's (ix, iy, iz) advance by the grid stride's own digits with
@@ -565,9 +570,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
         if (vpart) {
           const R dS = mult_horner_d(cs, mp.deg, sv);
           const double dl = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
-          vx += double(em) * dl * double(kx * kx);
-          vy += double(em) * dl * double(ky * ky);
-          vz += double(em) * dl * double(kz * kz);
+          virial_add(vt, double(em) * dl, double(kx), double(ky), double(kz));
         }
       }
       v.x *= G;
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
     iz += sz;
   }
   if (!want_energy) return;
-  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
+  block_partials(e.value(), vt, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
 }
 
 // Multiplier on the pruned spectrum of a single structure: layout
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
 #pragma unroll
   for (int i = 0; i < 9; ++i) bm[i] = R(bmat[i]);
   EnergyAcc<R> e;
-  double vx = 0.0, vy = 0.0, vz = 0.0;
+  double vt[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int nline = nkx * mp.M[2];
   for (int line = blockIdx.x; line < nline; line += gridDim.x) {
     const int ix = line / mp.M[2], iz = line - ix * mp.M[2];
@@ -661,9 +664,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
         if (vpart) {
           const R dS = mult_horner_d(cs, mp.deg, sv);
           const double dlg = double(mult_dlog(p, S, dS * R(2 * kMultSeg), u, phi)) / double(k2);
-          vx += double(em) * dlg * double(kx * kx);
-          vy += double(em) * dlg * double(ky * ky);
-          vz += double(em) * dlg * double(kz * kz);
+          virial_add(vt, double(em) * dlg, double(kx), double(ky), double(kz));
         }
       }
       v.x *= G;
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(256) k_multiply_planes(Cplx<R>* __restrict__ d
     }
   }
   if (!want_energy) return;
-  block_partials(e.value(), vx, vy, vz, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
+  block_partials(e.value(), vt, part, vpart, size_t(c) * gridDim.x + blockIdx.x);
 }
 
 // ---- general cells: forces from grid-coordinate gradients ---------------------------

@@ -83,6 +83,7 @@ SIGNATURES = {
     "pswf_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_self_energy": ([_vp, _dp], ctypes.c_int),
     "pswf_virial": ([_vp, _vp], ctypes.c_int),
+    "pswf_stress": ([_vp, _vp], ctypes.c_int),
     "pswf_sync": ([_vp], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_plan_destroy": ([_vp], None),
@@ -294,6 +295,19 @@ class Plan:
         out = torch.empty(*shape, dtype=torch.float64, device=self.device)
         self._stream()
         _check(lib().pswf_virial(self._h, _vp(out.data_ptr())), self._h)
+        return out
+
+    def stress(self):
+        """Virial tensor components (xx, yy, zz, xy, xz, yz) of the last
+        execute, W_ab = -dE_c / d epsilon_ab at fixed fractional coordinates
+        (device float64 [K, 6]; batch plans [B, K, 6]); needs
+        flags=PSWF_FLAG_VIRIAL."""
+        import torch
+        B = getattr(self, "B", None)
+        shape = (self.K, 6) if B is None else (B, self.K, 6)
+        out = torch.empty(*shape, dtype=torch.float64, device=self.device)
+        self._stream()
+        _check(lib().pswf_stress(self._h, _vp(out.data_ptr())), self._h)
         return out
 
     def self_energy(self) -> np.ndarray:

@@ -5,7 +5,8 @@ cuFFT FP32 and FP64, full cuFFT transform) against the O1 oracle of that
 cell with the same grid, P, c and c_w (FP32 2e-6, FP64 2e-9 relative RMS);
 a rotated box against the box (rotation invariance of the GPU path); a
 diagonal cell equal to the box plan; the backward against the oracle's VJP
-in the same cell; the virial refused."""
+and the virial tensor against the oracle's strain differences in the same
+cell."""
 import math
 
 import numpy as np
@@ -21,9 +22,9 @@ R_C = 4.0
 SHEARED = np.array([[19.2, 0.0, 0.0], [4.5, 18.0, 0.0], [-3.0, 3.5, 17.5]])
 
 
-def _cw(cell, M, P):
+def _cw(cell, M, P, c=C):
     h = max(float(np.linalg.norm(a)) / m for a, m in zip(np.asarray(cell, dtype=float), M))
-    return P * math.pi * (1.0 - 0.5 * h * (C / R_C) / math.pi)
+    return P * math.pi * (1.0 - 0.5 * h * (c / R_C) / math.pi)
 
 
 def _system(cell, n, seed, ps=(1, 6)):
@@ -103,13 +104,54 @@ def test_diagonal_cell_is_the_box_plan():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-def test_general_cell_refuses_virial():
+def _clear_bandwidth(cell, c0, gap=1.5e-4):
+    """The first c = c0 (1 + j / 4000) for which no reciprocal-lattice mode
+    has |k| within a relative gap of k_c = c / R_C.  Phi-hat_p drops to zero
+    at k_c (reading C1), so the energy jumps when a strain moves a mode across
+    the band edge; the oracle's central differences (strains up to 1e-4, which
+    change |k| by at most that fraction) must not straddle such a jump to
+    measure the derivative.  Modes lie about 1.4e-4 apart in |k| / k_c here."""
+    from oracle.direct import kvectors
+    for j in range(400):
+        c = c0 * (1.0 + j / 4000.0)
+        _, kk = kvectors(cell, 1.2 * c / R_C)
+        if np.min(np.abs(kk / (c / R_C) - 1.0)) > gap:
+            return c
+    raise AssertionError("no clear band edge")
+
+
+@pytest.mark.parametrize("M,precision,tol", [
+    ((64, 64, 64), 0, 2e-5),   # own transform
+    ((64, 64, 64), 1, 1e-7),   # FP64, pruned cuFFT
+    ((40, 36, 30), 1, 1e-7),   # full transform
+])
+def test_sheared_cell_stress_matches_oracle(M, precision, tol):
+    """Virial tensor (pswf_stress, xx yy zz xy xz yz) in a sheared cell
+    against the oracle's central differences under symmetric strain;
+    pswf_virial is its diagonal."""
     import torch
+    from oracle.grid import DiscretePSWF, GridConfig
     from paper_2606_06617_b300 import lr
     dev = torch.device("cuda", 0)
-    with pytest.raises(lr.PswfError) as e:
-        lr.Plan(None, 10, (1,), R_C, P=6, grid=(32, 32, 32), flags=lr.PSWF_FLAG_VIRIAL, device=dev, cell=SHEARED)
-    assert e.value.status == -1
+    P = 6
+    c = _clear_bandwidth(SHEARED, C)
+    cw = _cw(SHEARED, M, P, c)
+    pos, q = _system(SHEARED, 200, 31)
+    plan = lr.Plan(None, len(pos), (1, 6), R_C, c=c, c_w=cw, P=P, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_VIRIAL, device=dev, cell=SHEARED)
+    plan.set_points(torch.tensor(pos, device=dev), torch.tensor(q, dtype=plan.dtype, device=dev))
+    e, _, _ = plan.execute()
+    W6 = plan.stress().cpu().numpy()
+    Wd = plan.virial().cpu().numpy()
+    plan.sync()
+    assert np.array_equal(Wd, W6[:, :3])
+    ref = DiscretePSWF(GridConfig((0, 0, 0), M, P, c, R_C, (1, 6), c_w=cw, cell=SHEARED)).stress_fd(pos, q)
+    idx = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    E = e.cpu().numpy()
+    for c in range(2):
+        r6 = np.array([ref[c][a, b] for a, b in idx])
+        bound = 3 * tol * max(np.abs(r6).max(), abs(E[c]))
+        assert np.abs(W6[c] - r6).max() <= bound, (c, W6[c], r6)
 
 
 @pytest.mark.parametrize("M,precision,tol", [
