@@ -18,8 +18,12 @@ f64 = torch.float64
 
 def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
     """E_real = 1/2 sum_{|r_ij + nL| < r_c}' q_i q_j (1 - G_p(r)) / r^p.
-    Returns dict(E, phi [N], F [N,3])."""
+    Positions may lie outside the cell.  Returns dict(E, phi [N], F [N,3])."""
     moll = moll or Mollifier(c, r_c)
+    # The sum runs over every periodic image, so moving an atom by a lattice
+    # vector leaves it unchanged; with all atoms in the primary cell the
+    # image range ceil(r_c / L) + 1 per axis holds every pair closer than r_c.
+    pos = np.mod(np.asarray(pos, dtype=np.float64), np.asarray(box, dtype=np.float64))
     box_t = torch.tensor(np.asarray(box, dtype=np.float64), dtype=f64)
     pos_t = torch.tensor(np.asarray(pos, dtype=np.float64), dtype=f64, requires_grad=True)
     q_t = torch.tensor(np.asarray(q, dtype=np.float64), dtype=f64, requires_grad=True)
