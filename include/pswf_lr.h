@@ -54,6 +54,7 @@ extern "C" {
 /* ---- options ----------------------------------------------------------- */
 #define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */
 #define PSWF_FLAG_VIRIAL 2         /* pswf_execute also reduces the virial tensor (pswf_virial, pswf_stress) */
+#define PSWF_FLAG_REAL_SPACE 4     /* reserve the real-space complement's cell list (pswf_real_space) */
 
 typedef struct {
   double tol;      /* target LR tolerance eps_tot (default 1e-5) */
@@ -118,7 +119,7 @@ int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* 
 int pswf_plan_create(const double box[3], int64_t n_max, int K, const int* p,
                      const pswf_opts* opts, void* stream, pswf_plan* out);
 
-/* A single structure in a general (triclinic) periodic cell (SURVEY F3).
+/* A single structure in a general (triclinic) periodic cell.
  * cell: host [9], the lattice vectors a_0, a_1, a_2 as rows (Angstrom); the
  * positions are Cartesian (any real value: wrapped through the fractional
  * coordinates).  The grid is uniform in the fractional coordinates (M_d
@@ -251,9 +252,32 @@ int pswf_virial(pswf_plan plan, double* virial);
  * coordinates; any cell).  The grid density and the window transform are
  * strain-invariant and k -> (1 - epsilon) k, V -> (1 + tr epsilon) V, so
  * W_ab = E_c delta_ab + sum_m e_m (d ln Phi-hat_p / d ln k) k_a k_b / k^2
- * (stress for NPT; the paper has no stress).  Stress = -W / V.
+ * (stress for constant-pressure runs; the paper has no stress).  Stress = -W / V.
  * Asynchronous on the plan's stream. */
 int pswf_stress(pswf_plan plan, double* virial);
+
+/* Real-space complement (Methods, "Implementation details": the
+ * pair term that completes Eq. (Fourier); G_p = 1 beyond r_c, reading C3):
+ *   E_c = 1/2 sum_{i != j, |r_ij| < r_c} q_i^c q_j^c (1 - G_p(r_ij)) / r_ij^p
+ * with G_p of Eq. G1, G6, G (the planner's piecewise polynomial in r / r_c),
+ * its potentials phi_i^c = dE_c / dq_i^c and forces.  With the reciprocal part
+ * of pswf_execute and the self energies (pswf_self_energy) it gives the
+ * complete 1/r^p lattice sum: E = E_recip + E_real - E_self, phi and F the
+ * sums likewise (phi also takes -2 s_p q_i from the self energy).  Plans
+ * created with PSWF_FLAG_REAL_SPACE (single orthorhombic structures, K <= 16,
+ * every box edge at least 3 r_c: the cell list has >= 3 cells of width >= r_c
+ * per axis, so each pair is found once, in its nearest image).  Inputs as
+ * pswf_set_points (positions any real value, wrapped; q real [K][n] in the
+ * plan's precision); it does not touch the sorted atoms of pswf_set_points.
+ * energy: device double [K + 1] (per channel, total), written; phi: real
+ * [K][n], forces: real [n][3], written, either may be NULL.  Asynchronous on
+ * the plan's stream; non-finite positions are reported by pswf_sync.
+ * Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE; PSWF_EINVAL for a null
+ * energy, n outside 0..n_max, missing pos / q or a bad pos_dtype (pswf_plan
+ * creation with the flag already returned PSWF_EINVAL for an edge < 3 r_c,
+ * a non-orthorhombic cell, a batch or K > 16); PSWF_ECUDA if a launch fails. */
+int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
+                    void* phi, void* forces);
 
 /* Waits for the plan's stream and returns the first device-side status
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */

@@ -27,7 +27,7 @@ Stencil (reading C5): with u = r / h, the P points of each dimension are
 i0 .. i0 + P - 1 with i0 = ceil(u - P/2), taken modulo M.  Reading C6: the
 DFT sign does not matter (G is even and rho is real); m = 0 is excluded.
 
-Cells (triclinic): with the lattice vectors a_d as the rows of H,
+Cells (general, triclinic): with the lattice vectors a_d as the rows of H,
 r = sum_d s_d a_d, the grid is uniform in the fractional coordinates s and
 everything above is written in grid units: u_d = M_d s_d, the window per
 direction is psi^{c_w}((g_d - u_d) / (P/2)), its transform per grid cell is

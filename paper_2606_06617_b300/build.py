@@ -27,6 +27,7 @@ UNITS = [
     ("planner.cpp", "planner.o", []),
     ("server.cu", "server.o", []),
     ("fft_x.cu", "fft_x.o", []),
+    ("realspace.cu", "realspace.o", []),
 ]
 
 

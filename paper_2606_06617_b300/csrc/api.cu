@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fft_x.hpp"
+#include "realspace.hpp"
 #include "internal.hpp"
 #include "kernels.cuh"
 #include "launch.cuh"
@@ -360,6 +361,12 @@ struct pswf_plan_s {
   bool yzfft = false;
   void* xtw = nullptr;       // twiddle tables (float2) of Mx, then My and Mz (yzfft)
   int64_t tw_off[3] = {0, 0, 0};
+  // real-space complement (PSWF_FLAG_REAL_SPACE): its cell list and scratch
+  RealSpaceGeom rs_geo;
+  int rs_ncell = 0, rs_nsb = 0;
+  int *rs_count = nullptr, *rs_start = nullptr, *rs_cellof = nullptr, *rs_rank = nullptr, *rs_perm = nullptr,
+      *rs_scan = nullptr;
+  void *rs_lpos = nullptr, *rs_lq = nullptr, *coef_g = nullptr;
   unsigned char* lmask = nullptr;   // yzfft: [nkx][Mz] lines that can hold band modes
   int* lines = nullptr;             // yzfft: those lines, kx << 16 | pz
   int nlines = 0;
@@ -498,6 +505,17 @@ int64_t layout(pswf_plan p, char* base) {
   p->virial = vir ? reinterpret_cast<double*>(take(BK * 6 * 8)) : nullptr;
   p->err = reinterpret_cast<int*>(take(4));
   p->coef_m = take(int64_t(6) * kMultSeg * (h.deg_m + 1) * rs);
+  p->coef_g = take(int64_t(6) * kMultSeg * (h.deg_g + 1) * rs);
+  if (p->flags & PSWF_FLAG_REAL_SPACE) {
+    p->rs_count = reinterpret_cast<int*>(take(int64_t(p->rs_ncell) * 4));
+    p->rs_start = reinterpret_cast<int*>(take(int64_t(p->rs_ncell + 1) * 4));
+    p->rs_cellof = reinterpret_cast<int*>(take(nm * 4));
+    p->rs_rank = reinterpret_cast<int*>(take(nm * 4));
+    p->rs_perm = reinterpret_cast<int*>(take(nm * 4));
+    p->rs_scan = reinterpret_cast<int*>(take(int64_t(p->rs_nsb) * 4));
+    p->rs_lpos = take(4 * nm * rs);
+    p->rs_lq = take(K * nm * rs);
+  }
   {
     int64_t tw_pairs = 0;
     for (int d = 0; d < (p->yzfft ? 3 : p->xfft ? 1 : 0); ++d) {
@@ -619,6 +637,7 @@ int upload_tables(pswf_plan p) {
   int rc;
   if (p->real_size == 4) {
     if ((rc = upload(p, p->coef_m, to_real<float>(h.coef_m), "upload coef"))) return rc;
+    if ((rc = upload(p, p->coef_g, to_real<float>(h.coef_g), "upload real-space coef"))) return rc;
     if (p->xfft) {
       std::vector<float> all, tw;
       for (int d = 0; d < (p->yzfft ? 3 : 1); ++d) {
@@ -639,6 +658,7 @@ int upload_tables(pswf_plan p) {
     }
   } else {
     if ((rc = upload(p, p->coef_m, h.coef_m, "upload coef"))) return rc;
+    if ((rc = upload(p, p->coef_g, h.coef_g, "upload real-space coef"))) return rc;
   }
   std::vector<char> img(size_t(p->stab_bytes), 0);
   if (!p->batch) {
@@ -1298,6 +1318,14 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->geo.K = h.K;
   pl->tric = b == 1 && h.st.tric;
   pl->geo.tric = pl->tric ? 1 : 0;
+  if (opts->flags & PSWF_FLAG_REAL_SPACE) {
+    if (b != 1 || pl->tric) return set_err(pl, PSWF_EINVAL, "real space: single orthorhombic structures only");
+    if (h.K > kRsMaxK) return set_err(pl, PSWF_EINVAL, "real space: at most 16 channels");
+    if (!real_space_geometry(h.box, h.r_c, pl->rs_geo))
+      return set_err(pl, PSWF_EINVAL, "real space: each box edge must hold 3 cells of width >= r_c");
+    pl->rs_ncell = pl->rs_geo.nc[0] * pl->rs_geo.nc[1] * pl->rs_geo.nc[2];
+    pl->rs_nsb = (pl->rs_ncell + 16383) / 16384;
+  }
   pl->geo.nts = pl->geo.ntile[0] * pl->geo.ntile[1] * pl->geo.ntile[2];
   pl->geo.B = b;
   pl->nts = pl->geo.nts;
@@ -1510,6 +1538,48 @@ int pswf_stress(pswf_plan pl, double* virial) {
   }
   return cuda_check(pl, cudaMemcpyAsync(virial, pl->virial, size_t(pl->nrun) * pl->host.K * 6 * 8,
                                         cudaMemcpyDeviceToDevice, pl->stream), "copy virial tensor");
+}
+
+int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
+                    void* phi, void* forces) {
+  if (!pl || !energy) return PSWF_EINVAL;
+  if (!(pl->flags & PSWF_FLAG_REAL_SPACE))
+    return set_err(pl, PSWF_ESTATE, "plan was created without PSWF_FLAG_REAL_SPACE");
+  if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
+  if (n > 0 && (!pos || !q)) return set_err(pl, PSWF_EINVAL, "pos and q are required");
+  if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
+  int rc = ensure_workspace(pl);
+  if (rc) return rc;
+  StageScope scope(pl, PSWF_STAGE_OTHER);
+  RealSpaceArgs a;
+  a.geo = pl->rs_geo;
+  a.n = n;
+  a.nmax = std::max<int64_t>(pl->n_max, 1);
+  a.K = pl->host.K;
+  a.pos = pos;
+  a.pos_dtype = pos_dtype;
+  a.q = q;
+  a.pch = pl->pch;
+  a.coef_g = pl->coef_g;
+  a.deg_g = pl->host.deg_g;
+  a.count = pl->rs_count;
+  a.cell_start = pl->rs_start;
+  a.cell_of = pl->rs_cellof;
+  a.rank = pl->rs_rank;
+  a.lpos = pl->rs_lpos;
+  a.lq = pl->rs_lq;
+  a.perm = pl->rs_perm;
+  a.scan_sums = pl->rs_scan;
+  a.scan_per_block = 16384;
+  a.err = pl->err;
+  a.energy = energy;
+  a.phi = phi;
+  a.forces = forces;
+  int nl = 0;
+  const cudaError_t e = pl->real_size == 4 ? real_space_run<float>(a, pl->stream, &nl)
+                                           : real_space_run<double>(a, pl->stream, &nl);
+  pl->launches[PSWF_STAGE_OTHER] += nl;
+  return cuda_check(pl, e, "real space");
 }
 
 int pswf_sync(pswf_plan pl) {

@@ -304,6 +304,45 @@ const MultFit& mult_fit(const Prolate& moll, int p, double eps_poly) {
   return cache.emplace(key, std::move(f)).first->second;
 }
 
+// Real-space mollifier G_p(x), x = r / r_c in [0, 1] (Eq. G1, G6, G of the
+// Methods; G_p = 1 beyond r_c by reading C3), with I(x) = int_0^x psi.
+double real_mollifier(const Prolate& ps, int p, double x) {
+  const double C0 = ps.C0;
+  const double I = x > 0 ? ps.integral(0.0, x, 0) : 0.0;
+  switch (p) {
+    case 1: return I / C0;
+    case 2: return 1.0 - ps.eval(x);
+    case 3: return (I - x * ps.eval(x)) / C0;
+    case 4: return 1.0 - ps.eval(x) + 0.5 * x * ps.eval(x, 1);
+    case 5: return (I - x * ps.eval(x) + x * x / 3.0 * ps.eval(x, 1)) / C0;
+    case 6: return 1.0 - ps.eval(x) + 0.625 * x * ps.eval(x, 1) - 0.125 * x * x * ps.eval(x, 2);
+    default: return 1.0;
+  }
+}
+
+// Chebyshev fits of G_p on the kMultSeg pieces of [0, 1], shared like the
+// multiplier fits.
+const MultFit& real_fit(const Prolate& moll, int p, double eps_poly) {
+  static std::mutex mu;
+  static std::map<std::tuple<double, int, double>, MultFit> cache;
+  const auto key = std::make_tuple(moll.c, p, eps_poly);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  MultFit f;
+  const int nfit = 33;
+  f.cheb.resize(kMultSeg);
+  for (int i = 0; i < kMultSeg; ++i) {
+    const double a = double(i) / kMultSeg, b = double(i + 1) / kMultSeg;
+    f.cheb[i] = cheb_fit([&](double sv) { return real_mollifier(moll, p, a + (b - a) * 0.5 * (sv + 1.0)); }, nfit);
+  }
+  f.deg = family_degree(f.cheb, eps_poly);
+  std::lock_guard<std::mutex> lk(mu);
+  return cache.emplace(key, std::move(f)).first->second;
+}
+
 // Everything that depends on the grid spacing at box_max and on the set of
 // exponents, but not on a particular structure.
 int plan_core(const double box_max[3], int K, const int* pset, int npset, const Options& opt, Plan& plan) {
@@ -411,6 +450,25 @@ int plan_core(const double box_max[3], int K, const int* pset, int npset, const 
       if (cheb[i].empty()) continue;
       const auto mono = cheb_to_monomial(cheb[i], deg);
       for (int n = 0; n <= deg; ++n) plan.coef_m[i * (deg + 1) + n] = mono[n];
+    }
+  }
+  // ---- real-space mollifier pieces G_p(x), one row per exponent in use ----
+  {
+    std::vector<std::vector<double>> cheb(size_t(6) * kMultSeg);
+    int deg = 1;
+    for (int pp = 1; pp <= 6; ++pp) {
+      if (!use_p[pp]) continue;
+      const MultFit& f = real_fit(plan.moll, pp, eps_poly);
+      for (int i = 0; i < kMultSeg; ++i) cheb[size_t(pp - 1) * kMultSeg + i] = f.cheb[i];
+      deg = std::max(deg, f.deg);
+    }
+    deg = std::min(deg, kMaxMultDeg);
+    plan.deg_g = deg;
+    plan.coef_g.assign(size_t(6) * kMultSeg * (deg + 1), 0.0);
+    for (size_t i = 0; i < cheb.size(); ++i) {
+      if (cheb[i].empty()) continue;
+      const auto mono = cheb_to_monomial(cheb[i], deg);
+      for (int n = 0; n <= deg; ++n) plan.coef_g[i * (deg + 1) + n] = mono[n];
     }
   }
   // ---- per-exponent constants ----

@@ -100,6 +100,10 @@ struct Plan {
   // plan does not use are zero), kMultSeg pieces on u in [0, 1]
   int deg_m = 0;
   std::vector<double> coef_m;    // 6 * kMultSeg * (deg_m + 1)
+  // real-space mollifier G_p(x), x = r / r_c: same piece layout in x as the
+  // multiplier (row p - 1), for the real-space complement (1 - G_p) / r^p
+  int deg_g = 0;
+  std::vector<double> coef_g;    // 6 * kMultSeg * (deg_g + 1)
   // per exponent p (index p, 1..6): constant in front of S_p, self-energy
   // coefficient, and V times the zero-frequency coefficient
   double mult_scale_p[7] = {0, 0, 0, 0, 0, 0, 0};

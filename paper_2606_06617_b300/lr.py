@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
 
 PSWF_FLAG_BACKWARD = 1
 PSWF_FLAG_VIRIAL = 2
+PSWF_FLAG_REAL_SPACE = 4
 PSWF_TRANSFORM_FULL = 0
 PSWF_TRANSFORM_PRUNED = 1
 PSWF_TRANSFORM_PRUNED_X = 2
@@ -84,6 +85,7 @@ SIGNATURES = {
     "pswf_self_energy": ([_vp, _dp], ctypes.c_int),
     "pswf_virial": ([_vp, _vp], ctypes.c_int),
     "pswf_stress": ([_vp, _vp], ctypes.c_int),
+    "pswf_real_space": ([_vp, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_sync": ([_vp], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_plan_destroy": ([_vp], None),
@@ -309,6 +311,23 @@ class Plan:
         self._stream()
         _check(lib().pswf_stress(self._h, _vp(out.data_ptr())), self._h)
         return out
+
+    def real_space(self, pos, q):
+        """Real-space complement (pswf_real_space) of positions pos [n, 3] and
+        charges q [K, n] (device tensors): returns (energy float64 [K + 1],
+        phi [K, n], forces [n, 3]); needs flags=PSWF_FLAG_REAL_SPACE."""
+        import torch
+        n = int(pos.shape[0])
+        pos = pos.contiguous()
+        q = q.to(self.dtype).contiguous()
+        energy = torch.empty(self.K + 1, dtype=torch.float64, device=self.device)
+        phi = torch.empty(self.K, n, dtype=self.dtype, device=self.device)
+        forces = torch.empty(n, 3, dtype=self.dtype, device=self.device)
+        self._stream()
+        pdt = 1 if pos.dtype == torch.float64 else 0
+        _check(lib().pswf_real_space(self._h, n, _vp(pos.data_ptr()), pdt, _vp(q.data_ptr()),
+                                     _vp(energy.data_ptr()), _vp(phi.data_ptr()), _vp(forces.data_ptr())), self._h)
+        return energy, phi, forces
 
     def self_energy(self) -> np.ndarray:
         out = (ctypes.c_double * self.K)()

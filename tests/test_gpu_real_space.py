@@ -1,0 +1,96 @@
+"""Real-space complement on the GPU (pswf_real_space).
+
+* Against the oracle's real-space sum (oracle/realspace.py, FP64 autograd):
+  per-channel energies, potentials and the total force, all six exponents,
+  atoms far outside the box (FP64 1e-10, FP32 2e-6 relative RMS).
+* The complete lattice sum from the GPU alone, reciprocal part
+  (pswf_execute) + real-space part - self energy, against Ewald (O3) on the
+  ionic-melt sub-box at its benchmarked parameters: the 1e-5 relative force
+  tolerance the parameters are chosen for.
+* Plans without PSWF_FLAG_REAL_SPACE, or with a box edge under 3 r_c, are
+  refused."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import rel_rms
+from gpu_helpers import TOL_FP32, window_cw
+from paper_2606_06617_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+C = math.log(3.0 / 1e-5)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, TOL_FP32)])
+def test_real_space_matches_oracle(precision, tol):
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (13.0, 14.5, 12.5)
+    r_c = 4.0
+    s = wl.random_system(300, box, (1, 2, 3, 4, 5, 6), seed=41, neutral=False)
+    s.pos = s.pos + np.random.default_rng(2).integers(-2, 3, size=s.pos.shape) * np.asarray(box)
+    plan = lr.Plan(box, s.n, s.ps, r_c, c=C, P=6, grid=(28, 30, 26), precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, phi, f = plan.real_space(torch.tensor(s.pos, device=dev), torch.tensor(s.q, device=dev))
+    plan.sync()
+    e, phi, f = e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy()
+    F = np.zeros((s.n, 3))
+    for c, p in enumerate(s.ps):
+        o = real_space(s.pos, s.q[c], box, p, C, r_c)
+        assert abs(e[c] - o["E"]) <= tol * abs(o["E"]), (c, e[c], o["E"])
+        assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
+        F += o["F"]
+    assert rel_rms(f, F) <= tol, rel_rms(f, F)
+    assert abs(e[-1] - e[:-1].sum()) <= 1e-12 * abs(e[:-1]).sum()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_gpu_total_matches_ewald(precision):
+    """Ionic melt parameters (r_c = 7, c = log(3e5), P = 7, h = 0.911 A) on a
+    density-matched sub-box (L = 21.875 A, 24^3, 1024 atoms)."""
+    import torch
+    from oracle.ewald import ewald
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    L = 350.0 * 24 / 384
+    s = wl.ionic_melt(int(round(4194304 * (L / 350.0) ** 3)), L, seed=3)
+    M = (24, 24, 24)
+    r_c = 7.0
+    cw = window_cw(s.box, M, 7, C, r_c)
+    plan = lr.Plan(s.box, s.n, s.ps, r_c, c=C, c_w=cw, P=7, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    pos = torch.tensor(s.pos, device=dev)
+    q = torch.tensor(s.q, dtype=plan.dtype, device=dev)
+    plan.set_points(pos, q)
+    e_k, phi_k, f_k = plan.execute()
+    e_r, phi_r, f_r = plan.real_space(pos, q)
+    plan.sync()
+    self_e = plan.self_energy()
+    F = f_k.cpu().double().numpy() + f_r.cpu().double().numpy()
+    E = e_k.cpu().numpy()[:-1] + e_r.cpu().numpy()[:-1] - self_e
+    F_ew = np.zeros_like(F)
+    for c, p in enumerate(s.ps):
+        ew = ewald(s.pos, s.q[c], s.box, p)
+        F_ew += ew["F"]
+        assert abs(E[c] - ew["E"]) <= 1e-5 * max(abs(ew["E"]), 1e-3 * np.abs(s.q[c]).sum()), (c, E[c], ew["E"])
+    assert rel_rms(F, F_ew) <= 1e-5, rel_rms(F, F_ew)
+
+
+def test_real_space_refusals():
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    plan = lr.Plan((13.0, 13.0, 13.0), 10, (1,), 4.0, P=6, grid=(26, 26, 26), device=dev)
+    pos = torch.zeros(10, 3, dtype=torch.float64, device=dev)
+    q = torch.zeros(1, 10, dtype=torch.float32, device=dev)
+    with pytest.raises(lr.PswfError) as e:
+        plan.real_space(pos, q)
+    assert e.value.status == -8
+    with pytest.raises(lr.PswfError) as e:
+        lr.Plan((11.0, 13.0, 13.0), 10, (1,), 4.0, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE,
+                device=dev)
+    assert e.value.status == -1
