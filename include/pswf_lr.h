@@ -275,7 +275,8 @@ int pswf_stress(pswf_plan plan, double* virial);
  * Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE; PSWF_EINVAL for a null
  * energy, n outside 0..n_max, missing pos / q or a bad pos_dtype (pswf_plan
  * creation with the flag already returned PSWF_EINVAL for an edge < 3 r_c,
- * a non-orthorhombic cell, a batch or K > 16); PSWF_ECUDA if a launch fails. */
+ * a non-orthorhombic cell, a batch, K > 16 or n_max >= 2^27); PSWF_ECUDA
+ * if a launch fails. */
 int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
                     void* phi, void* forces);
 
