@@ -50,6 +50,7 @@ extern "C" {
 #define PSWF_ENONFINITE (-6)       /* NaN or Inf in the positions */
 #define PSWF_ETOLUNREACHABLE (-7)  /* grid too coarse for the mollifier band (h k_c >= pi) */
 #define PSWF_ESTATE (-8)           /* call out of order (e.g. execute before set_points) */
+#define PSWF_ECELL (-9)            /* real space: a cell of the cell list holds more than 2048 atoms */
 
 /* ---- options ----------------------------------------------------------- */
 #define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */
@@ -271,12 +272,14 @@ int pswf_stress(pswf_plan plan, double* virial);
  * plan's precision); it does not touch the sorted atoms of pswf_set_points.
  * energy: device double [K + 1] (per channel, total), written; phi: real
  * [K][n], forces: real [n][3], written, either may be NULL.  Asynchronous on
- * the plan's stream; non-finite positions are reported by pswf_sync.
- * Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE; PSWF_EINVAL for a null
- * energy, n outside 0..n_max, missing pos / q or a bad pos_dtype (pswf_plan
- * creation with the flag already returned PSWF_EINVAL for an edge < 3 r_c,
- * a non-orthorhombic cell, a batch, K > 16 or n_max >= 2^27); PSWF_ECUDA
- * if a launch fails. */
+ * the plan's stream; pswf_sync reports non-finite positions
+ * (PSWF_ENONFINITE) and a cell of width >= r_c holding more than 2048 atoms
+ * (PSWF_ECELL: such a cell's pairs are left out; no liquid or solid comes
+ * near that density).  Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE;
+ * PSWF_EINVAL for a null energy, n outside 0..n_max, missing pos / q or a
+ * bad pos_dtype (pswf_plan creation with the flag already returned
+ * PSWF_EINVAL for an edge < 3 r_c, a non-orthorhombic cell, a batch or
+ * K > 16); PSWF_ECUDA if a launch fails. */
 int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
                     void* phi, void* forces);
 

@@ -1321,7 +1321,6 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   if (opts->flags & PSWF_FLAG_REAL_SPACE) {
     if (b != 1 || pl->tric) return set_err(pl, PSWF_EINVAL, "real space: single orthorhombic structures only");
     if (h.K > kRsMaxK) return set_err(pl, PSWF_EINVAL, "real space: at most 16 channels");
-    if (pl->n_max >= (int64_t(1) << 27)) return set_err(pl, PSWF_EINVAL, "real space: n_max must be below 2^27");
     if (!real_space_geometry(h.box, h.r_c, pl->rs_geo))
       return set_err(pl, PSWF_EINVAL, "real space: each box edge must hold 3 cells of width >= r_c");
     pl->rs_ncell = pl->rs_geo.nc[0] * pl->rs_geo.nc[1] * pl->rs_geo.nc[2];

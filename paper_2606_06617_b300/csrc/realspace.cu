@@ -48,7 +48,18 @@ namespace {
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kFixBits = 29;     // FP32 plans: cell-local unit w / 2^29; |dx| <= 2^30
-constexpr int kQueueCap = 80;    // queued pairs per lane; drained above kQueueCap - 32
+constexpr int kQueueCap = 192;   // queued pairs per lane; drained early only above kQueueCap - 32
+constexpr int kCellBits = 11;    // queue entry: (neighbour o << 11) | index within that cell
+constexpr int kMaxCellAtoms = 1 << kCellBits;
+constexpr int kPswfECell = -9;   // PSWF_ECELL
+
+template <typename R>
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+  // queue [kQueueCap][32] of 16-bit entries, stage [32][4] R, neighbour
+  // starts and ends [2][27] (padded to 224 bytes)
+  return size_t(kQueueCap) * 32 * 2 + 32 * 4 * sizeof(R) + 224;
+}
+static_assert(warp_smem_bytes<float>() % 16 == 0 && warp_smem_bytes<double>() % 16 == 0, "aligned warp regions");
 
 // fixed-point copy of the cell-local coordinates: int for FP32 plans, none
 // (the FP64 copy itself) for FP64 plans
@@ -147,6 +158,7 @@ struct PairArgs {
   double* energy;
   R* phi;
   R* forces;
+  int* err;
 };
 
 template <typename R, int NC>
@@ -187,14 +199,14 @@ __device__ inline R inv_sqrt(R r2) {
 template <typename R, int NC, int KC>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
-  using R4 = typename std::conditional<std::is_same<R, float>::value, float4, double2>::type;
   extern __shared__ __align__(16) unsigned char rs_smem[];
   R* coef = reinterpret_cast<R*>(rs_smem);                       // [6][kMultSeg][NC], zero-padded
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) +
-                         size_t(warp) * (kQueueCap * 32 * 4 + 32 * 4 * sizeof(R));
-  uint32_t* queue = reinterpret_cast<uint32_t*>(wbase);          // [kQueueCap][32]: (j << 5) | o
-  R* stage = reinterpret_cast<R*>(wbase + kQueueCap * 32 * 4);   // [32][4] candidate test coordinates
+  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + size_t(warp) * warp_smem_bytes<R>();
+  uint16_t* queue = reinterpret_cast<uint16_t*>(wbase);                     // [kQueueCap][32]
+  R* stage = reinterpret_cast<R*>(wbase + kQueueCap * 32 * 2);              // [32][4] candidates
+  int* nbs = reinterpret_cast<int*>(stage + 32 * 4);                        // [27] neighbour cell starts
+  int* nbe = nbs + 27;                                                      // [27] ends
   for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
     const int k = t % NC, row = t / NC;
     coef[t] = k <= a.deg ? a.coef[size_t(row) * (a.deg + 1) + k] : R(0);
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         for (int t = 0; t < rounds; ++t) {
           if (t >= len) continue;
           const uint32_t e = queue[t * 32 + lane];
-          const int j = int(e >> 5), o = int(e & 31u);
+          const int o = int(e >> kCellBits), j = nbs[o] + int(e & (kMaxCellAtoms - 1));
           const int o3 = o / 3;
           const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
           L jx, jy, jz;
@@ -297,8 +309,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         len = 0;
       };
 
-      for (int o = 0; o < 27; ++o) {
-        const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      // the 27 neighbour cells' atom ranges, one lane each
+      if (lane < 27) {
+        const int od[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
         // cells are equal (width L / n_c), so the neighbour's corner is o w
         // from this cell's corner whether or not its index wraps
         int nc3[3];
@@ -307,10 +320,21 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           t += t < 0 ? g.nc[d] : (t >= g.nc[d] ? -g.nc[d] : 0);
           nc3[d] = t;
         }
-        const R ax = xi - R(od[0] * g.w[0]), ay = yi - R(od[1] * g.w[1]), az = zi - R(od[2] * g.w[2]);
         const int nb = (nc3[2] * g.nc[1] + nc3[1]) * g.nc[0] + nc3[0];
-        const int b0 = a.cell_start[nb], b1 = a.cell_start[nb + 1];
-        const uint32_t tag = uint32_t(o);
+        int b0 = a.cell_start[nb], b1 = a.cell_start[nb + 1];
+        if (b1 - b0 > kMaxCellAtoms) {   // not encodable: reported, cell left out
+          atomicCAS(a.err, 0, kPswfECell);
+          b1 = b0;
+        }
+        nbs[lane] = b0;
+        nbe[lane] = b1;
+      }
+      __syncwarp();
+      for (int o = 0; o < 27; ++o) {
+        const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+        const R ax = xi - R(od[0] * g.w[0]), ay = yi - R(od[1] * g.w[1]), az = zi - R(od[2] * g.w[2]);
+        const int b0 = nbs[o], b1 = nbe[o];
+        const uint32_t tag = uint32_t(o) << kCellBits;
         for (int jb = b0; jb < b1; jb += 32) {
           if (__reduce_max_sync(0xffffffffu, len) > kQueueCap - 32) drain();
           const int cnt = min(32, b1 - jb);
@@ -338,13 +362,14 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
               const R r2 = dx * dx + dy * dy + dz * dz;
               // r2 = 0 only for the atom itself (or a coincident atom, which
               // the sum excludes too)
-              if (r2 < rc2 && r2 > R(0)) queue[len++ * 32 + lane] = (uint32_t(jb + jj) << 5) | tag;
+              if (r2 < rc2 && r2 > R(0)) queue[len++ * 32 + lane] = uint16_t(tag | uint32_t(jb - b0 + jj));
             }
           }
           __syncwarp();
         }
       }
       drain();
+      __syncwarp();   // nbs / nbe are rewritten for the next chunk
 
       // the G lanes of an atom hold partial sums over its candidates
       for (int off = G / 2; off > 0; off >>= 1) {
@@ -387,7 +412,7 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
 
 template <typename R, int NC, int KC>
 cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + size_t(kRsWarps) * (kQueueCap * 32 * 4 + 32 * 4 * sizeof(R));
+  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -481,6 +506,7 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     pa.energy = a.energy;
     pa.phi = static_cast<R*>(a.phi);
     pa.forces = static_cast<R*>(a.forces);
+    pa.err = a.err;
     // coefficient rows padded to whole 16-byte loads (the planner's degree
     // is at most kMaxMultDeg = 16)
     static_assert(kMaxMultDeg + 1 <= 18, "coefficient rows");
