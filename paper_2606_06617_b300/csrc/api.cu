@@ -366,7 +366,7 @@ struct pswf_plan_s {
   int rs_ncell = 0, rs_nsb = 0;
   int *rs_count = nullptr, *rs_start = nullptr, *rs_cellof = nullptr, *rs_rank = nullptr, *rs_perm = nullptr,
       *rs_scan = nullptr;
-  void *rs_lpos = nullptr, *rs_lq = nullptr, *coef_g = nullptr;
+  void *rs_lpos = nullptr, *coef_g = nullptr;
   unsigned char* lmask = nullptr;   // yzfft: [nkx][Mz] lines that can hold band modes
   int* lines = nullptr;             // yzfft: those lines, kx << 16 | pz
   int nlines = 0;
@@ -513,8 +513,7 @@ int64_t layout(pswf_plan p, char* base) {
     p->rs_rank = reinterpret_cast<int*>(take(nm * 4));
     p->rs_perm = reinterpret_cast<int*>(take(nm * 4));
     p->rs_scan = reinterpret_cast<int*>(take(int64_t(p->rs_nsb) * 4));
-    p->rs_lpos = take(32 * nm);   // cell-local coordinates: FP32 test + fixed-point copies, or one FP64 copy
-    p->rs_lq = take(K * nm * rs);
+    p->rs_lpos = take(int64_t(real_space_bytes_per_atom(K, int(rs))) * nm);   // test coordinates, records
   }
   {
     int64_t tw_pairs = 0;
@@ -1567,7 +1566,6 @@ int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, con
   a.cell_of = pl->rs_cellof;
   a.rank = pl->rs_rank;
   a.lpos = pl->rs_lpos;
-  a.lq = pl->rs_lq;
   a.perm = pl->rs_perm;
   a.scan_sums = pl->rs_scan;
   a.scan_per_block = 16384;

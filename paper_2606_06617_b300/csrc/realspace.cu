@@ -25,15 +25,20 @@
 // atomics); the G lanes of an atom are summed with shuffles at the end.
 //
 // Coordinates: the cutoff test reads cell-local coordinates in the plan's
-// precision.  FP32 plans evaluate a queued pair from a second copy held as
-// integers in units of w / 2^29: the displacement is an exact integer
+// precision (16 or 32 bytes per atom, streamed through a shared-memory stage).
+// A queued pair is evaluated from the neighbour's record: its exact
+// coordinates and its K charges side by side (one 32-byte sector for K <= 5
+// in FP32), so the scattered reads of the pair rounds touch one record, not
+// K + 1 arrays.  FP32 records hold the coordinates as integers in units of
+// w / 2^29: the displacement is an exact integer
 // difference (the neighbour cell adds its offset o 2^29) rounded to FP32
 // once, so its relative error is that of one rounding at any distance.
 // FP32 coordinates and an FP32 cell offset would carry an absolute error
 // ~1e-7 w, which 1/r^p magnifies to p 1e-7 w / r on close pairs (5e-6 of an
 // energy at p = 4 with pairs 0.2 A apart in 4 A cells).  A pair whose FP32
 // test and exact distance straddle r_c differs from the sum by a term with
-// 1 - G_p(1) ~ 1e-5, which is negligible.  FP64 plans use one FP64 copy.
+// 1 - G_p(1) ~ 1e-5, which is negligible.  FP64 records hold FP64
+// coordinates.
 #include "realspace.hpp"
 
 #include <algorithm>
@@ -49,20 +54,20 @@ constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kFixBits = 29;     // FP32 plans: cell-local unit w / 2^29; |dx| <= 2^30
 constexpr int kQueueCap = 192;   // queued pairs per lane; drained early only above kQueueCap - 32
+constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 97 words, so lanes start in distinct banks
 constexpr int kCellBits = 11;    // queue entry: (neighbour o << 11) | index within that cell
 constexpr int kMaxCellAtoms = 1 << kCellBits;
 constexpr int kPswfECell = -9;   // PSWF_ECELL
 
 template <typename R>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-  // queue [kQueueCap][32] of 16-bit entries, stage [32][4] R, neighbour
+  // queue [32][kQueueStride] of 16-bit entries, stage [32][4] R, neighbour
   // starts and ends [2][27] (padded to 224 bytes)
-  return size_t(kQueueCap) * 32 * 2 + 32 * 4 * sizeof(R) + 224;
+  return size_t(32) * kQueueStride * 2 + 32 * 4 * sizeof(R) + 224;
 }
 static_assert(warp_smem_bytes<float>() % 16 == 0 && warp_smem_bytes<double>() % 16 == 0, "aligned warp regions");
 
-// fixed-point copy of the cell-local coordinates: int for FP32 plans, none
-// (the FP64 copy itself) for FP64 plans
+// exact cell-local coordinates: fixed-point int for FP32 plans, FP64 for FP64
 template <typename R>
 struct LocalT {
   using type = double;
@@ -72,20 +77,43 @@ struct LocalT<float> {
   using type = int;
 };
 
-template <typename T>
-__device__ inline void load3(const T* __restrict__ p, int64_t j, T& x, T& y, T& z) {
-  if constexpr (sizeof(T) == 4) {
-    using V = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
-    const V v = reinterpret_cast<const V*>(p)[j];
-    x = v.x;
-    y = v.y;
-    z = v.z;
-  } else {
-    const double2 a = reinterpret_cast<const double2*>(p)[2 * j];
-    const double2 b = reinterpret_cast<const double2*>(p)[2 * j + 1];
-    x = a.x;
-    y = a.y;
-    z = b.x;
+// 16-byte vector of the plan's real type
+template <typename R>
+using Vec = typename std::conditional<std::is_same<R, float>::value, float4, double2>::type;
+template <typename R>
+constexpr int kPerVec = 16 / int(sizeof(R));
+
+// per-atom record: 3 coordinates (FP32: fixed-point integers in float
+// bits), KC charges, zero padding to whole 16-byte vectors
+template <typename R, int KC>
+__host__ __device__ constexpr int rec_words() {
+  return (3 + KC + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
+}
+
+int channel_class(int K) { return K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : kRsMaxK; }
+
+template <typename R>
+__device__ inline void store_vec(R* p, const R (&v)[kPerVec<R>]) {
+  if constexpr (std::is_same<R, float>::value)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+
+template <typename R, int W>
+__device__ inline void load_words(const R* __restrict__ p, R (&v)[W]) {
+#pragma unroll
+  for (int k = 0; k < W; k += kPerVec<R>) {
+    const Vec<R> x = *reinterpret_cast<const Vec<R>*>(p + k);
+    if constexpr (std::is_same<R, float>::value) {
+      v[k] = x.x;
+      v[k + 1] = x.y;
+      v[k + 2] = x.z;
+      v[k + 3] = x.w;
+    } else {
+      v[k] = x.x;
+      v[k + 1] = x.y;
+    }
   }
 }
 
@@ -112,33 +140,41 @@ __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom 
   }
 }
 
-// cell-local coordinates (test copy [nmax][4] in R; FP32 plans also the
-// fixed-point copy [nmax][4]), charges [K][nmax] and the original index
+// cell-local test coordinates [nmax][4] and records [nmax][rw] (exact
+// coordinates, charges), and the original index
 template <typename PosT, typename R>
-__global__ void k_rs_scatter(int64_t n, int64_t nmax, int K, const PosT* __restrict__ pos, const R* __restrict__ q,
+__global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ pos, const R* __restrict__ q,
                              RealSpaceGeom g, const int* __restrict__ cell_of, const int* __restrict__ rank,
-                             const int* __restrict__ cell_start, R* __restrict__ lchk,
-                             typename LocalT<R>::type* __restrict__ lfix, R* __restrict__ lq,
+                             const int* __restrict__ cell_start, R* __restrict__ lchk, R* __restrict__ rec,
                              int* __restrict__ perm) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int cell = cell_of[i];
     const int64_t dst = int64_t(cell_start[cell]) + rank[i];
     int ci[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
+    R t4[4] = {R(0), R(0), R(0), R(0)};
+    R* r = rec + dst * rw;
     for (int d = 0; d < 3; ++d) {
       double x = double(pos[3 * i + d]);
       if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) x = 0.0;
       const double s = x * g.inv_len[d];
       const double local = (s - floor(s)) * g.len[d] - ci[d] * g.w[d];   // from the cell corner
-      lchk[4 * dst + d] = R(local);
+      t4[d] = R(local);
       if constexpr (std::is_same<R, float>::value) {
         double u = rint(local * (double(1 << kFixBits) / g.w[d]));
         u = u < 0.0 ? 0.0 : (u > double(1 << kFixBits) ? double(1 << kFixBits) : u);
-        lfix[4 * dst + d] = int(u);
+        r[d] = __int_as_float(int(u));
+      } else {
+        r[d] = local;
       }
     }
-    lchk[4 * dst + 3] = R(0);
-    if constexpr (std::is_same<R, float>::value) lfix[4 * dst + 3] = 0;
-    for (int c = 0; c < K; ++c) lq[int64_t(c) * nmax + dst] = q[int64_t(c) * n + i];
+    if constexpr (std::is_same<R, float>::value) {
+      store_vec<R>(lchk + 4 * dst, t4);
+    } else {
+      const R a2[2] = {t4[0], t4[1]}, b2[2] = {t4[2], R(0)};
+      store_vec<R>(lchk + 4 * dst, a2);
+      store_vec<R>(lchk + 4 * dst + 2, b2);
+    }
+    for (int w = 3; w < rw; ++w) r[w] = w - 3 < K ? q[int64_t(w - 3) * n + i] : R(0);
     perm[dst] = int(i);
   }
 }
@@ -146,12 +182,11 @@ __global__ void k_rs_scatter(int64_t n, int64_t nmax, int K, const PosT* __restr
 template <typename R>
 struct PairArgs {
   RealSpaceGeom g;
-  int64_t nmax, n;
+  int64_t n;
   int K, deg;
   const int* cell_start;
-  const R* lchk;
-  const typename LocalT<R>::type* lfix;
-  const R* lq;
+  const R* lchk;     // [nmax][4]
+  const R* rec;      // [nmax][rec_words]
   const int* perm;
   const int* pch;
   const R* coef;     // [6][kMultSeg][deg + 1]
@@ -160,27 +195,6 @@ struct PairArgs {
   R* forces;
   int* err;
 };
-
-template <typename R, int NC>
-__device__ inline void load_coefs(const R* __restrict__ cs, R (&c)[NC]) {
-  if constexpr (std::is_same<R, float>::value) {
-#pragma unroll
-    for (int k = 0; k < NC; k += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(cs + k);
-      c[k] = v.x;
-      c[k + 1] = v.y;
-      c[k + 2] = v.z;
-      c[k + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NC; k += 2) {
-      const double2 v = *reinterpret_cast<const double2*>(cs + k);
-      c[k] = v.x;
-      c[k + 1] = v.y;
-    }
-  }
-}
 
 // 1 / sqrt(r2): the hardware estimate refined by one Newton step
 // y <- y (3 - r2 y^2) / 2 (FP32); FP64 divides.
@@ -194,22 +208,46 @@ __device__ inline R inv_sqrt(R r2) {
   }
 }
 
+template <typename R>
+__device__ inline void coords(const R* v, typename LocalT<R>::type& x, typename LocalT<R>::type& y,
+                              typename LocalT<R>::type& z) {
+  if constexpr (std::is_same<R, float>::value) {
+    x = __float_as_int(v[0]);
+    y = __float_as_int(v[1]);
+    z = __float_as_int(v[2]);
+  } else {
+    x = v[0];
+    y = v[1];
+    z = v[2];
+  }
+}
+
 // KC channels per pair evaluation, fully unrolled (channels past K carry
-// zero charges); NC coefficients per mollifier piece (zero-padded).
+// zero charges); NC coefficients per mollifier piece (zero-padded).  The
+// coefficient table in shared memory is [exponent][vector][piece] of
+// 16-byte vectors, so lanes on different pieces read different banks.
 template <typename R, int NC, int KC>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
+  constexpr int RW = rec_words<R, KC>();
+  constexpr int NV = NC / kPerVec<R>;
   extern __shared__ __align__(16) unsigned char rs_smem[];
-  R* coef = reinterpret_cast<R*>(rs_smem);                       // [6][kMultSeg][NC], zero-padded
+  Vec<R>* coefv = reinterpret_cast<Vec<R>*>(rs_smem);            // [6][NV][kMultSeg]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + size_t(warp) * warp_smem_bytes<R>();
-  uint16_t* queue = reinterpret_cast<uint16_t*>(wbase);                     // [kQueueCap][32]
-  R* stage = reinterpret_cast<R*>(wbase + kQueueCap * 32 * 2);              // [32][4] candidates
-  int* nbs = reinterpret_cast<int*>(stage + 32 * 4);                        // [27] neighbour cell starts
-  int* nbe = nbs + 27;                                                      // [27] ends
-  for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
-    const int k = t % NC, row = t / NC;
-    coef[t] = k <= a.deg ? a.coef[size_t(row) * (a.deg + 1) + k] : R(0);
+  uint16_t* queue = reinterpret_cast<uint16_t*>(wbase) + lane * kQueueStride;   // this lane's column
+  R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);               // [32][4] candidates
+  int* nbs = reinterpret_cast<int*>(stage + 32 * 4);                            // [27] neighbour cell starts
+  int* nbe = nbs + 27;                                                          // [27] ends
+  {
+    R* cs = reinterpret_cast<R*>(rs_smem);
+    for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
+      // t -> (row, vector, piece, element) of the destination layout
+      const int e = t % kPerVec<R>, seg = (t / kPerVec<R>) % kMultSeg, v = (t / (kPerVec<R> * kMultSeg)) % NV,
+                row = t / (kPerVec<R> * kMultSeg * NV);
+      const int k = v * kPerVec<R> + e;
+      cs[t] = k <= a.deg ? a.coef[(size_t(row) * kMultSeg + seg) * (a.deg + 1) + k] : R(0);
+    }
   }
   __syncthreads();
 
@@ -233,35 +271,60 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
       const bool own = slot < m;
       const int i = own ? base + slot : a0;
       R xi, yi, zi;
-      load3(a.lchk, i, xi, yi, zi);
-      L ix, iy, iz;
-      if constexpr (std::is_same<R, float>::value)
-        load3(a.lfix, i, ix, iy, iz);
-      else
-        ix = xi, iy = yi, iz = zi;
-      R qi[KC], ph[KC];
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        qi[c] = c < a.K ? a.lq[int64_t(c) * a.nmax + i] : R(0);
-        ph[c] = R(0);
+      {
+        const Vec<R> v = reinterpret_cast<const Vec<R>*>(a.lchk + 4 * int64_t(i))[0];
+        xi = v.x;
+        yi = v.y;
+        if constexpr (std::is_same<R, float>::value)
+          zi = v.z;
+        else
+          zi = a.lchk[4 * int64_t(i) + 2];
       }
+      R ri[RW];
+      load_words<R, RW>(a.rec + int64_t(i) * RW, ri);
+      L ix, iy, iz;
+      coords<R>(ri, ix, iy, iz);
+      R ph[KC];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) ph[c] = R(0);
       R fx = 0, fy = 0, fz = 0;
       int len = 0;
+
+      // the 27 neighbour cells' atom ranges, one lane each
+      if (lane < 27) {
+        const int od[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+        // cells are equal (width L / n_c), so the neighbour's corner is o w
+        // from this cell's corner whether or not its index wraps
+        int nc3[3];
+        for (int d = 0; d < 3; ++d) {
+          int t = c3[d] + od[d];
+          t += t < 0 ? g.nc[d] : (t >= g.nc[d] ? -g.nc[d] : 0);
+          nc3[d] = t;
+        }
+        const int nb = (nc3[2] * g.nc[1] + nc3[1]) * g.nc[0] + nc3[0];
+        int b0 = a.cell_start[nb], b1 = a.cell_start[nb + 1];
+        if (b1 - b0 > kMaxCellAtoms) {   // not encodable: reported, cell left out
+          atomicCAS(a.err, 0, kPswfECell);
+          b1 = b0;
+        }
+        nbs[lane] = b0;
+        nbe[lane] = b1;
+      }
+      __syncwarp();
 
       // every queued pair of this lane: exact displacement, f_p and f_p'
       auto drain = [&]() {
         const int rounds = __reduce_max_sync(0xffffffffu, len);
         for (int t = 0; t < rounds; ++t) {
           if (t >= len) continue;
-          const uint32_t e = queue[t * 32 + lane];
+          const uint32_t e = queue[t];
           const int o = int(e >> kCellBits), j = nbs[o] + int(e & (kMaxCellAtoms - 1));
           const int o3 = o / 3;
           const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
+          R rj[RW];
+          load_words<R, RW>(a.rec + int64_t(j) * RW, rj);
           L jx, jy, jz;
-          load3(a.lfix, j, jx, jy, jz);
-          R qj[KC];
-#pragma unroll
-          for (int c = 0; c < KC; ++c) qj[c] = c < a.K ? a.lq[int64_t(c) * a.nmax + j] : R(0);
+          coords<R>(rj, jx, jy, jz);
           R dx, dy, dz;
           if constexpr (std::is_same<R, float>::value) {
             dx = __int2float_rn(jx + ox * (1 << kFixBits) - ix) * unit[0];
@@ -285,7 +348,19 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 #pragma unroll
           for (int c = 0; c < KC; ++c) {
             R cf[NC];
-            load_coefs<R, NC>(coef + (prow[c] * kMultSeg + seg) * NC, cf);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              const Vec<R> cv = coefv[(prow[c] * NV + v) * kMultSeg + seg];
+              if constexpr (std::is_same<R, float>::value) {
+                cf[4 * v] = cv.x;
+                cf[4 * v + 1] = cv.y;
+                cf[4 * v + 2] = cv.z;
+                cf[4 * v + 3] = cv.w;
+              } else {
+                cf[2 * v] = cv.x;
+                cf[2 * v + 1] = cv.y;
+              }
+            }
             R Gv = cf[NC - 1], dG = R(0);
 #pragma unroll
             for (int k = NC - 2; k >= 0; --k) {
@@ -296,10 +371,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
             const int p = prow[c] + 1;                    // r^-p from the bits of p
             const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
             const R one_m = R(1) - Gv;
-            const R f = one_m * rp;
-            const R fp = -(dG * inv_rc + R(p) * one_m * inv_r) * rp;
-            ph[c] += qj[c] * f;
-            fsum += qi[c] * qj[c] * fp;
+            const R qj = rj[3 + c];
+            ph[c] += qj * one_m * rp;
+            fsum -= ri[3 + c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
           }
           const R sc = fsum * inv_r;
           fx += sc * dx;
@@ -309,27 +383,6 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         len = 0;
       };
 
-      // the 27 neighbour cells' atom ranges, one lane each
-      if (lane < 27) {
-        const int od[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-        // cells are equal (width L / n_c), so the neighbour's corner is o w
-        // from this cell's corner whether or not its index wraps
-        int nc3[3];
-        for (int d = 0; d < 3; ++d) {
-          int t = c3[d] + od[d];
-          t += t < 0 ? g.nc[d] : (t >= g.nc[d] ? -g.nc[d] : 0);
-          nc3[d] = t;
-        }
-        const int nb = (nc3[2] * g.nc[1] + nc3[1]) * g.nc[0] + nc3[0];
-        int b0 = a.cell_start[nb], b1 = a.cell_start[nb + 1];
-        if (b1 - b0 > kMaxCellAtoms) {   // not encodable: reported, cell left out
-          atomicCAS(a.err, 0, kPswfECell);
-          b1 = b0;
-        }
-        nbs[lane] = b0;
-        nbe[lane] = b1;
-      }
-      __syncwarp();
       for (int o = 0; o < 27; ++o) {
         const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
         const R ax = xi - R(od[0] * g.w[0]), ay = yi - R(od[1] * g.w[1]), az = zi - R(od[2] * g.w[2]);
@@ -339,13 +392,11 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           if (__reduce_max_sync(0xffffffffu, len) > kQueueCap - 32) drain();
           const int cnt = min(32, b1 - jb);
           // one coalesced load of up to 32 candidates into the warp's stage
-          if (lane < cnt) {
-            R sx, sy, sz;
-            load3(a.lchk, jb + lane, sx, sy, sz);
-            stage[4 * lane] = sx;
-            stage[4 * lane + 1] = sy;
-            stage[4 * lane + 2] = sz;
-          }
+          if (lane < cnt)
+            reinterpret_cast<Vec<R>*>(stage)[(4 / kPerVec<R>) * lane] =
+                reinterpret_cast<const Vec<R>*>(a.lchk)[(4 / kPerVec<R>) * (int64_t(jb) + lane)];
+          if constexpr (!std::is_same<R, float>::value)
+            if (lane < cnt) stage[4 * lane + 2] = a.lchk[4 * (int64_t(jb) + lane) + 2];
           __syncwarp();
           if (own) {
 #pragma unroll 4
@@ -362,7 +413,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
               const R r2 = dx * dx + dy * dy + dz * dz;
               // r2 = 0 only for the atom itself (or a coincident atom, which
               // the sum excludes too)
-              if (r2 < rc2 && r2 > R(0)) queue[len++ * 32 + lane] = uint16_t(tag | uint32_t(jb - b0 + jj));
+              if (r2 < rc2 && r2 > R(0)) queue[len++] = uint16_t(tag | uint32_t(jb - b0 + jj));
             }
           }
           __syncwarp();
@@ -384,7 +435,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 #pragma unroll
       for (int c = 0; c < KC; ++c) {
         if (c >= a.K) break;
-        double e = lead ? 0.5 * double(qi[c]) * double(ph[c]) : 0.0;
+        double e = lead ? 0.5 * double(ri[3 + c]) * double(ph[c]) : 0.0;
         for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
         if (lane == 0 && e != 0.0) atomicAdd(a.energy + c, e);
       }
@@ -432,14 +483,31 @@ cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
 
 template <typename R, int NC>
 cudaError_t launch_pairs(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  if (pa.K <= 1) return launch_pairs_k<R, NC, 1>(pa, ncell, s);
-  if (pa.K <= 2) return launch_pairs_k<R, NC, 2>(pa, ncell, s);
-  if (pa.K <= 4) return launch_pairs_k<R, NC, 4>(pa, ncell, s);
-  if (pa.K <= 8) return launch_pairs_k<R, NC, 8>(pa, ncell, s);
-  return launch_pairs_k<R, NC, kRsMaxK>(pa, ncell, s);
+  switch (channel_class(pa.K)) {
+    case 1: return launch_pairs_k<R, NC, 1>(pa, ncell, s);
+    case 2: return launch_pairs_k<R, NC, 2>(pa, ncell, s);
+    case 4: return launch_pairs_k<R, NC, 4>(pa, ncell, s);
+    case 8: return launch_pairs_k<R, NC, 8>(pa, ncell, s);
+    default: return launch_pairs_k<R, NC, kRsMaxK>(pa, ncell, s);
+  }
+}
+
+template <typename R>
+int record_words(int K) {
+  switch (channel_class(K)) {
+    case 1: return rec_words<R, 1>();
+    case 2: return rec_words<R, 2>();
+    case 4: return rec_words<R, 4>();
+    case 8: return rec_words<R, 8>();
+    default: return rec_words<R, kRsMaxK>();
+  }
 }
 
 }  // namespace
+
+size_t real_space_bytes_per_atom(int K, int real_size) {
+  return real_size == 4 ? (4 + size_t(record_words<float>(K))) * 4 : (4 + size_t(record_words<double>(K))) * 8;
+}
 
 bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g) {
   for (int d = 0; d < 3; ++d) {
@@ -478,28 +546,25 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
   k_scan_apply<<<nsb, kScanBlock, 0, s>>>(ncell, a.count, a.scan_sums, a.scan_per_block, a.cell_start);
   *nlaunch += 3;
   if (a.n > 0) {
-    using L = typename LocalT<R>::type;
+    const int rw = record_words<R>(a.K);
     R* lchk = static_cast<R*>(a.lpos);
-    // FP32: the fixed-point copy follows the test copy; FP64: one copy
-    L* lfix = std::is_same<R, float>::value ? reinterpret_cast<L*>(lchk + 4 * a.nmax) : reinterpret_cast<L*>(lchk);
+    R* rec = lchk + 4 * a.nmax;   // records follow the test coordinates
     if (a.pos_dtype == 1)
-      k_rs_scatter<double, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.nmax, a.K, static_cast<const double*>(a.pos),
+      k_rs_scatter<double, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const double*>(a.pos),
                                                             static_cast<const R*>(a.q), g, a.cell_of, a.rank,
-                                                            a.cell_start, lchk, lfix, static_cast<R*>(a.lq), a.perm);
+                                                            a.cell_start, lchk, rec, a.perm);
     else
-      k_rs_scatter<float, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.nmax, a.K, static_cast<const float*>(a.pos),
+      k_rs_scatter<float, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const float*>(a.pos),
                                                            static_cast<const R*>(a.q), g, a.cell_of, a.rank,
-                                                           a.cell_start, lchk, lfix, static_cast<R*>(a.lq), a.perm);
+                                                           a.cell_start, lchk, rec, a.perm);
     PairArgs<R> pa;
     pa.g = g;
-    pa.nmax = a.nmax;
     pa.n = a.n;
     pa.K = a.K;
     pa.deg = a.deg_g;
     pa.cell_start = a.cell_start;
     pa.lchk = lchk;
-    pa.lfix = lfix;
-    pa.lq = static_cast<const R*>(a.lq);
+    pa.rec = rec;
     pa.perm = a.perm;
     pa.pch = a.pch;
     pa.coef = static_cast<const R*>(a.coef_g);

@@ -17,6 +17,9 @@ struct RealSpaceGeom {
   double r_c;
 };
 
+// Device bytes per atom of the cell-local coordinates and records.
+size_t real_space_bytes_per_atom(int K, int real_size);
+
 // False when a box edge holds fewer than 3 cells of width >= r_c.
 bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g);
 
@@ -31,14 +34,13 @@ struct RealSpaceArgs {
   const void* coef_g;   // device real [6][kMultSeg][deg_g + 1]
   int deg_g;
   // scratch (device): counts and starts per cell, per-atom cell and rank,
-  // cell-local positions [nmax][4] (FP32 plans: int32 fixed point, FP64
-  // plans: double), charges real [K][nmax], order
+  // cell-local test coordinates real [nmax][4] followed by the records
+  // (exact coordinates and charges; real_space_bytes_per_atom in all), order
   int* count;
   int* cell_start;      // [ncell + 1]
   int* cell_of;
   int* rank;
   void* lpos;
-  void* lq;
   int* perm;
   int* scan_sums;
   int scan_per_block;
