@@ -46,11 +46,18 @@ WORKLOADS = {
                          tol=1e-5, P=7, grid=256),
     "melt_triclinic": dict(name="ionic_melt_triclinic_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0,
                            tol=1e-5, P=7, grid=384, shear=((0.0, 0.0), (60.0, 0.0), (-40.0, 50.0))),
+    "melt_total": dict(name="ionic_melt_total_4194304", N=4194304, L=350.0, ps=(1, 2, 4, 6), r_c=7.0, tol=1e-5,
+                       P=7, grid=384),
+    "melt_total_quarter": dict(name="ionic_melt_total_1242757", N=1242757, L=350.0 * 256 / 384, ps=(1, 2, 4, 6),
+                               r_c=7.0, tol=1e-5, P=7, grid=256),
     "serving": dict(name="serving_stream_4096"),
     "training": dict(name="training_batch_64x16"),
     "water": dict(name="water_3000", N=3000, L=31.0, ps=(1, 6), r_c=4.0, tol=5e-6, P=8, grid=64),
 }
 METRIC = "LR energy+force atoms/s at 1e-5 force err"
+METRIC_TOTAL = "PSWF-LR total (reciprocal + real space) energy+force atoms/s at 1e-5 force err"
+# FP32 lanes per SM and the largest SM clock of the part: the ALU roofline
+SM_FP32_LANES, SM_MAX_MHZ = 128, 2032.0
 
 
 def shear_cell(L: float, shear, scale: float = 1.0) -> np.ndarray:
@@ -97,6 +104,23 @@ def algorithmic_bytes(w, K: int, n: int, rs: int = 4) -> dict:
         "multiply": K * inside * 2 * rs + K * Mh * 2 * rs,
         "interp": K * M * rs + atom_sorted + n * 4 + n * (K * rs + 3 * rs),
     }
+
+
+def real_space_flops(w, K: int, n: int, deg: int) -> dict:
+    """Algorithmic FP32 operations of one real-space launch at the
+    workload's uniform density (expected counts): every candidate in the 27
+    cells of width >= r_c around an atom is tested (8 flops: 3 differences,
+    a square norm), and every ordered pair closer than r_c is evaluated once
+    from each end: displacement, 1/r and the piece coordinate (25 flops),
+    then per channel the two Horner chains of G_p and G_p' (4 deg), r^-p,
+    the potential and force terms (13)."""
+    L, rc = w["L"], w["r_c"]
+    nc = int(L // rc)
+    rho = n / L ** 3
+    cand = n * 27 * n / nc ** 3
+    pairs = n * rho * 4.0 / 3.0 * math.pi * rc ** 3
+    flops = cand * 8 + pairs * (25 + K * (4 * deg + 13))
+    return {"candidates": cand, "pairs": pairs, "flops": flops}
 
 
 def csrc_digest() -> str:
@@ -215,6 +239,123 @@ def cpu_oracle_sample(wk: str, seconds_target: float = 15.0):
             break
     dt = (time.perf_counter() - t0) / reps
     return s.n / dt, torch.get_num_threads(), f"{desc}; {reps} oracle evaluations, {dt:.2f} s each"
+
+
+def cpu_total_sample(seconds_target: float = 10.0):
+    """The oracle's complete PSWF-LR evaluation (O1 plus the real-space
+    complement, FP64) on a bounded, density-matched sample of the ionic melt:
+    a 24^3 sub-box of 1024 atoms (the real-space oracle enumerates every
+    image pair, so the sample is smaller than the reciprocal one).  Returns
+    (atoms/s, cores, description)."""
+    import torch
+    from oracle.grid import DiscretePSWF, GridConfig
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import workloads as wl
+    w = WORKLOADS["melt_total"]
+    Msub = 24
+    Lsub = w["L"] * Msub / w["grid"]
+    n = int(round(w["N"] * (Lsub / w["L"]) ** 3))
+    s = wl.ionic_melt(n, Lsub, seed=1)
+    c = math.log(3.0 / w["tol"])
+    eta = (Lsub / Msub) * (c / w["r_c"]) / math.pi
+    o = DiscretePSWF(GridConfig(s.box, (Msub,) * 3, w["P"], c, w["r_c"], s.ps,
+                                c_w=w["P"] * math.pi * (1 - eta / 2)))
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        o.evaluate(s.pos, s.q)
+        for ch, p in enumerate(s.ps):
+            real_space(s.pos, s.q[ch], s.box, p, c, w["r_c"])
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target or reps >= 20:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return (s.n / dt, torch.get_num_threads(),
+            f"density-matched sub-box L={Lsub:.3f} A, {n} atoms, grid {Msub}^3, K=4, P={w['P']}, r_c={w['r_c']}; "
+            f"{reps} oracle evaluations (O1 + real space), {dt:.2f} s each")
+
+
+def run_total(steps: int, warmup: int, cpu_baseline: bool = True, wk: str = "melt_total") -> dict:
+    """The complete evaluation of the ionic melt: set_points, the reciprocal
+    step and the real-space complement (pswf_real_space) in FP32, timed with
+    CUDA events on the launching stream (inputs far larger than L2)."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    w = WORKLOADS[wk]
+    s = make_system(wk, seed=0)
+    K = len(s.ps)
+    plan = lr.Plan(s.box, s.n, s.ps, w["r_c"], tol=w["tol"], P=w["P"], grid=w["grid"], device=dev,
+                   flags=lr.PSWF_FLAG_REAL_SPACE)
+    pos = torch.tensor(s.pos, device=dev)
+    q = torch.tensor(s.q, dtype=torch.float32, device=dev)
+    out = (torch.empty(K + 1, dtype=torch.float64, device=dev), torch.empty(K, s.n, dtype=torch.float32, device=dev),
+           torch.empty(s.n, 3, dtype=torch.float32, device=dev))
+    rs_out = (torch.empty(K + 1, dtype=torch.float64, device=dev),
+              torch.empty(K, s.n, dtype=torch.float32, device=dev),
+              torch.empty(s.n, 3, dtype=torch.float32, device=dev))
+
+    def step():
+        plan.set_points(pos, q)
+        plan.execute(out=out)
+        plan.real_space(pos, q, out=rs_out)
+
+    for _ in range(warmup):
+        step()
+    plan.sync()
+    plan.profile_read()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    plan.profile(False)
+    stage_ms, launches = plan.profile_read()
+    plan.sync()
+    ms = e0.elapsed_time(e1) / steps
+    info = dict(plan.info)
+    deg = int(info["deg_real"])
+    alg = real_space_flops(w, K, s.n, deg)
+    rs_ms = stage_ms["real_space"] / steps
+    achieved = alg["flops"] / (rs_ms * 1e-3) / 1e12
+    peak = 148 * SM_FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    cpu = None
+    if cpu_baseline:
+        v, cores, desc = cpu_total_sample()
+        cpu = {"value": v, "unit": "atoms/s", "cores": cores, "kind": "oracle", "sample": desc}
+    return {
+        "metric": METRIC_TOTAL, "value": s.n / (ms * 1e-3), "unit": "atoms/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "atoms": s.n, "box_A": w["L"], "channels_p": list(s.ps),
+                   "grid": info["grid"], "P": info["P"], "r_c": w["r_c"], "c": info["c"], "c_w": info["c_w"],
+                   "tol": w["tol"],
+                   "l2": f"inputs larger than L2 (grid {4 * K * w['grid'] ** 3 / 1e9:.2f} GB, "
+                         f"real-space records {s.n * 48 / 1e9:.2f} GB)",
+                   "parallelism": "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "real_space (k_rs_pairs)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x 2032 MHz",
+                     "traffic": None, "algorithmic_flops_per_launch": alg["flops"],
+                     "expected_candidates": alg["candidates"], "expected_pairs": alg["pairs"]},
+        "stages_ms_per_step": {k: v / steps for k, v in stage_ms.items()},
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clocks,
+        "e2e": None,
+        "cpu_baseline": cpu,
+    }
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -449,6 +590,13 @@ def main():
                               "ms_per_step": tr["ms_per_step"], "higher_is_better": True, "dtype": "f32",
                               "data": "synthetic", "config": {"workload": "training_batch_64x16"},
                               "training": tr}), flush=True)
+        return
+    if args.workload.startswith("melt_total"):
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps(run_total(args.steps, args.warmup, not args.no_cpu_baseline, args.workload)),
+                  flush=True)
         return
     if args.workload == "serving":
         if rank == 0:

@@ -85,6 +85,7 @@ typedef struct {
   int nkx;                 /* pruned transforms: x frequencies 0..nkx-1 kept (others are out of band) */
   double cell[9];          /* pswf_plan_info: lattice vectors as rows (diag(box) for a box; box_max for
                               batch plans); box[] then holds the edge lengths |a_d| */
+  int deg_real;            /* degree of the real-space mollifier pieces G_p (pswf_real_space) */
 } pswf_info;
 
 /* Transform of a plan.  FULL: cuFFT 3-D real transforms of every structure
@@ -374,7 +375,7 @@ int pswf_server_last_error(pswf_server srv, char* buf, int len);
 void pswf_server_destroy(pswf_server srv);
 
 /* ---- measurement support (not part of the paper's method) -------------- */
-#define PSWF_NSTAGE 8
+#define PSWF_NSTAGE 9
 /* Stage indices for pswf_profile_read. */
 #define PSWF_STAGE_SET_POINTS 0   /* binning, sort, charge sums */
 #define PSWF_STAGE_SPREAD 1       /* step (i) */
@@ -384,6 +385,7 @@ void pswf_server_destroy(pswf_server srv);
 #define PSWF_STAGE_INTERP 5       /* gather of potentials and forces */
 #define PSWF_STAGE_BACKWARD 6     /* pswf_backward */
 #define PSWF_STAGE_OTHER 7
+#define PSWF_STAGE_REAL_SPACE 8   /* pswf_real_space (cell list and pairs) */
 
 /* enable != 0: later calls record a CUDA event pair around each stage on the
  * plan's stream (costs one event record per stage boundary). */

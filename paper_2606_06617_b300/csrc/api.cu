@@ -385,7 +385,7 @@ struct pswf_plan_s {
   bool prof_on = false;
   std::vector<StageRec> recs;
   std::vector<cudaEvent_t> pool;
-  int64_t launches[PSWF_NSTAGE] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t launches[PSWF_NSTAGE] = {};
   int cur_stage = PSWF_STAGE_OTHER;   // innermost open StageScope
 };
 
@@ -1204,6 +1204,7 @@ void fill_info(const Plan& h, int flags, pswf_info* out) {
   out->precision = h.opt.precision;
   out->deg_window = h.deg_w;
   out->deg_mult = h.deg_m;
+  out->deg_real = h.deg_g;
   out->flags = flags;
   out->B = 1;
   out->batch = 0;
@@ -1549,7 +1550,7 @@ int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, con
   if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
   int rc = ensure_workspace(pl);
   if (rc) return rc;
-  StageScope scope(pl, PSWF_STAGE_OTHER);
+  StageScope scope(pl, PSWF_STAGE_REAL_SPACE);
   RealSpaceArgs a;
   a.geo = pl->rs_geo;
   a.n = n;
@@ -1576,7 +1577,7 @@ int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, con
   int nl = 0;
   const cudaError_t e = pl->real_size == 4 ? real_space_run<float>(a, pl->stream, &nl)
                                            : real_space_run<double>(a, pl->stream, &nl);
-  pl->launches[PSWF_STAGE_OTHER] += nl;
+  pl->launches[PSWF_STAGE_REAL_SPACE] += nl;
   return cuda_check(pl, e, "real space");
 }
 
@@ -1738,7 +1739,7 @@ int pswf_profile_read(pswf_plan pl, double* stage_ms, int64_t* launches) {
   if (!pl) return PSWF_EINVAL;
   int rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "stream synchronize");
   if (rc) return rc;
-  double ms[PSWF_NSTAGE] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double ms[PSWF_NSTAGE] = {};
   for (auto& r : pl->recs) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.stage] += t;
@@ -1765,6 +1766,7 @@ const char* pswf_strerror(int status) {
     case PSWF_ENONFINITE: return "non-finite positions";
     case PSWF_ETOLUNREACHABLE: return "tolerance unreachable on this grid";
     case PSWF_ESTATE: return "call out of order";
+    case PSWF_ECELL: return "a real-space cell holds more than 2048 atoms";
   }
   return "unknown status";
 }

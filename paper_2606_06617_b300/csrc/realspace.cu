@@ -46,6 +46,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "pswf_lr.h"
 
 namespace pswf {
 namespace {
@@ -57,7 +58,6 @@ constexpr int kQueueCap = 192;   // queued pairs per lane; drained early only ab
 constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 97 words, so lanes start in distinct banks
 constexpr int kCellBits = 11;    // queue entry: (neighbour o << 11) | index within that cell
 constexpr int kMaxCellAtoms = 1 << kCellBits;
-constexpr int kPswfECell = -9;   // PSWF_ECELL
 
 template <typename R>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
@@ -126,7 +126,7 @@ __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom 
     for (int d = 0; d < 3; ++d) {
       double x = double(pos[3 * i + d]);
       if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) {
-        atomicCAS(err, 0, -6);
+        atomicCAS(err, 0, PSWF_ENONFINITE);
         x = 0.0;
       }
       const double s = x * g.inv_len[d];          // in boxes
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         const int nb = (nc3[2] * g.nc[1] + nc3[1]) * g.nc[0] + nc3[0];
         int b0 = a.cell_start[nb], b1 = a.cell_start[nb + 1];
         if (b1 - b0 > kMaxCellAtoms) {   // not encodable: reported, cell left out
-          atomicCAS(a.err, 0, kPswfECell);
+          atomicCAS(a.err, 0, PSWF_ECELL);
           b1 = b0;
         }
         nbs[lane] = b0;

@@ -47,7 +47,8 @@ class PswfInfo(ctypes.Structure):
                 ("deg_window", ctypes.c_int), ("deg_mult", ctypes.c_int), ("flags", ctypes.c_int),
                 ("n_max", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("B", ctypes.c_int), ("batch", ctypes.c_int), ("transform", ctypes.c_int),
-                ("nkx", ctypes.c_int), ("cell", ctypes.c_double * 9)]
+                ("nkx", ctypes.c_int), ("cell", ctypes.c_double * 9),
+                ("deg_real", ctypes.c_int)]
 
 
 MAX_BUCKETS = 16
@@ -109,8 +110,8 @@ SIGNATURES = {
     "pswf_server_destroy": ([_vp], None),
 }
 
-NSTAGE = 8
-STAGES = ("set_points", "spread", "fft_fwd", "multiply", "fft_inv", "interp", "backward", "other")
+NSTAGE = 9
+STAGES = ("set_points", "spread", "fft_fwd", "multiply", "fft_inv", "interp", "backward", "other", "real_space")
 
 
 def lib():
@@ -312,17 +313,21 @@ class Plan:
         _check(lib().pswf_stress(self._h, _vp(out.data_ptr())), self._h)
         return out
 
-    def real_space(self, pos, q):
+    def real_space(self, pos, q, out=None):
         """Real-space complement (pswf_real_space) of positions pos [n, 3] and
         charges q [K, n] (device tensors): returns (energy float64 [K + 1],
-        phi [K, n], forces [n, 3]); needs flags=PSWF_FLAG_REAL_SPACE."""
+        phi [K, n], forces [n, 3]); needs flags=PSWF_FLAG_REAL_SPACE.  out =
+        (energy, phi, forces) device tensors of those shapes to fill."""
         import torch
         n = int(pos.shape[0])
         pos = pos.contiguous()
         q = q.to(self.dtype).contiguous()
-        energy = torch.empty(self.K + 1, dtype=torch.float64, device=self.device)
-        phi = torch.empty(self.K, n, dtype=self.dtype, device=self.device)
-        forces = torch.empty(n, 3, dtype=self.dtype, device=self.device)
+        if out is not None:
+            energy, phi, forces = out
+        else:
+            energy = torch.empty(self.K + 1, dtype=torch.float64, device=self.device)
+            phi = torch.empty(self.K, n, dtype=self.dtype, device=self.device)
+            forces = torch.empty(n, 3, dtype=self.dtype, device=self.device)
         self._stream()
         pdt = 1 if pos.dtype == torch.float64 else 0
         _check(lib().pswf_real_space(self._h, n, _vp(pos.data_ptr()), pdt, _vp(q.data_ptr()),
