@@ -348,7 +348,7 @@ def run_total(steps: int, warmup: int, cpu_baseline: bool = True, wk: str = "mel
         "roofline": {"bound": "alu", "kernel": "real_space (k_rs_pairs)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 (FMA) x 2032 MHz",
-                     "traffic": None, "algorithmic_flops_per_launch": alg["flops"],
+                     "traffic": load_traffic(w["name"], "real_space"), "algorithmic_flops_per_launch": alg["flops"],
                      "expected_candidates": alg["candidates"], "expected_pairs": alg["pairs"]},
         "stages_ms_per_step": {k: v / steps for k, v in stage_ms.items()},
         "gpu_launches": int(sum(launches.values())),
