@@ -53,6 +53,35 @@ def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None
     return dict(E=float(E.detach()), phi=gq.numpy(), F=(-gpos).numpy())
 
 
+def real_space_atoms(idx, pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
+    """Potentials and forces of single atoms, summed directly over their
+    neighbours: phi_i = sum_{0 < |r_ij| < r_c} q_j (1 - G_p(r)) / r^p and
+    F_i = q_i sum_j q_j f_p'(r) (r_j - r_i) / r, f_p = (1 - G_p) / r^p,
+    with r_ij the minimum image (every box edge at least 2 r_c, so it is
+    the only image closer than r_c).  f_p' by FP64 autograd of f_p in r.
+    For outputs of atoms of a system too large for real_space.
+    Returns (phi [len(idx)], F [len(idx), 3])."""
+    moll = moll or Mollifier(c, r_c)
+    box = np.asarray(box, dtype=np.float64)
+    assert np.all(box >= 2.0 * r_c), "minimum image needs every edge >= 2 r_c"
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    phi = np.zeros(len(idx))
+    F = np.zeros((len(idx), 3))
+    for k, i in enumerate(idx):
+        d = pos - pos[i]
+        d -= box * np.round(d / box)
+        r2 = np.einsum("nd,nd->n", d, d)
+        nb = np.nonzero((r2 < r_c * r_c) & (r2 > 0.0))[0]
+        r = torch.tensor(np.sqrt(r2[nb]), dtype=f64, requires_grad=True)
+        f = (1.0 - moll.G_torch(p, r)) / r ** p
+        (fp,) = torch.autograd.grad(f.sum(), r)
+        qn = q[nb]
+        phi[k] = float(np.sum(qn * f.detach().numpy()))
+        F[k] = q[i] * np.sum((qn * fp.numpy() / r.detach().numpy())[:, None] * d[nb], axis=0)
+    return phi, F
+
+
 def pswf_total(recip: dict, pos, q, box, ps, c: float, r_c: float):
     """Assemble E = E_k + E^0 + E_real - E_self per channel from a reciprocal
     result (O1 or O2 dict with E_ch [K], phi [K,N], f [K,N,3]).

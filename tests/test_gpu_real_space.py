@@ -7,6 +7,9 @@
   (pswf_execute) + real-space part - self energy, against Ewald (O3) on the
   ionic-melt sub-box at its benchmarked parameters: the 1e-5 relative force
   tolerance the parameters are chosen for.
+* The full-size melt (4,194,304 atoms, r_c = 7, K = 4), the configuration
+  the benchmark times: potentials of every channel and forces of seeded
+  sampled atoms against the oracle's per-atom neighbour sums.
 * Plans without PSWF_FLAG_REAL_SPACE, or with a box edge under 3 r_c, are
   refused."""
 import math
@@ -94,3 +97,50 @@ def test_real_space_refusals():
         lr.Plan((11.0, 13.0, 13.0), 10, (1,), 4.0, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE,
                 device=dev)
     assert e.value.status == -1
+
+
+def _nearest(pos, i, box):
+    d = pos - pos[i]
+    d -= box * np.round(d / box)
+    r2 = np.einsum("nd,nd->n", d, d)
+    r2[i] = np.inf
+    return float(np.sqrt(r2.min()))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP32), (1, 1e-10)])
+def test_full_size_melt_sampled_atoms(precision, tol):
+    """48 seeded atoms of the full-size melt.  Uniform random positions put
+    a few atoms closer than 0.1 A to a neighbour; there the FP32 path's
+    fixed-point displacement (w / 2^29 = 1.3e-8 A) bounds a term's relative
+    error by p 1.3e-8 / r (8e-7 at p = 6, r = 0.1 A), so FP32 samples are
+    drawn among atoms with no neighbour closer than 0.1 A (all but about
+    4e-4 of them); FP64 samples are any atoms."""
+    import torch
+    from oracle.mollifiers import Mollifier
+    from oracle.realspace import real_space_atoms
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.ionic_melt(4194304, 350.0, seed=0)
+    box = np.asarray(s.box)
+    r_c = 7.0
+    c = math.log(3.0 / 1e-5)
+    plan = lr.Plan(s.box, s.n, s.ps, r_c, tol=1e-5, P=7, grid=384, precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, phi, f = plan.real_space(torch.tensor(s.pos, device=dev), torch.tensor(s.q, device=dev))
+    plan.sync()
+    phi, f = phi.cpu().double().numpy(), f.cpu().double().numpy()
+    rng = np.random.default_rng(17)
+    idx = []
+    while len(idx) < 48:
+        i = int(rng.integers(s.n))
+        if precision == 1 or _nearest(s.pos, i, box) >= 0.1:
+            idx.append(i)
+    moll = Mollifier(c, r_c)
+    F = np.zeros((len(idx), 3))
+    for ch, p in enumerate(s.ps):
+        o_phi, o_F = real_space_atoms(idx, s.pos, s.q[ch], box, p, c, r_c, moll)
+        assert rel_rms(phi[ch, idx], o_phi) <= tol, (ch, rel_rms(phi[ch, idx], o_phi))
+        F += o_F
+    assert rel_rms(f[idx], F) <= tol, rel_rms(f[idx], F)
+    assert abs(e.cpu().numpy()[-1] - e.cpu().numpy()[:-1].sum()) <= 1e-12 * np.abs(e.cpu().numpy()[:-1]).sum()

@@ -5,7 +5,10 @@
   cells away from the primary cell, equals the oracle's energy; its forces
   are -dE/dr by central differences.
 * Large cutoff limit: with G_p = 0 (r_c far beyond every pair) the term is
-  the bare 1/r^p pair sum, checked on two atoms at a known distance."""
+  the bare 1/r^p pair sum, checked on two atoms at a known distance.
+* The per-atom direct sum (real_space_atoms: minimum image, f_p' by
+  autograd in r) equals the potentials and forces that real_space gets by
+  differentiating the total energy in q and r."""
 import math
 
 import numpy as np
@@ -67,3 +70,21 @@ def test_real_space_bare_pair_beyond_the_mollifier():
         o = real_space(pos, q, (40.0, 40.0, 40.0), p, C, 4.0, moll)
         assert abs(o["E"] - q[0] * q[1] * g) <= 1e-14
         assert np.allclose(o["phi"], [q[1] * g, q[0] * g], rtol=1e-13)
+
+
+def test_per_atom_sums_match_the_energy_derivatives():
+    from oracle.mollifiers import Mollifier
+    from oracle.realspace import real_space, real_space_atoms
+    rng = np.random.default_rng(9)
+    box = (9.0, 8.5, 10.0)
+    r_c = 4.0
+    pos = rng.uniform(0.0, 1.0, size=(60, 3)) * np.asarray(box)
+    pos[:10] += rng.integers(-2, 3, size=(10, 3)) * np.asarray(box)
+    q = rng.normal(size=60)
+    moll = Mollifier(C, r_c)
+    idx = [0, 3, 11, 25, 59]
+    for p in (1, 4, 6):
+        o = real_space(pos, q, box, p, C, r_c, moll)
+        phi, F = real_space_atoms(idx, pos, q, box, p, C, r_c, moll)
+        assert np.allclose(phi, o["phi"][idx], rtol=1e-12, atol=1e-14)
+        assert np.allclose(F, o["F"][idx], rtol=1e-11, atol=1e-13)
