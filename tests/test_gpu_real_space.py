@@ -7,6 +7,10 @@
   (pswf_execute) + real-space part - self energy, against Ewald (O3) on the
   ionic-melt sub-box at its benchmarked parameters: the 1e-5 relative force
   tolerance the parameters are chosen for.
+* The same on the 64-charge box (L = 12 A, p = 1, r_c = 4) and the
+  water-like box at its benchmarked parameters (forces within 1e-5 of
+  Ewald, energies within 1e-5 of the per-atom energy scale), and the NaCl
+  rock-salt crystal's energy against the Madelung constant.
 * The full-size melt (4,194,304 atoms, r_c = 7, K = 4), the configuration
   the benchmark times: potentials of every channel and forces of seeded
   sampled atoms against the oracle's per-atom neighbour sums.
@@ -144,3 +148,73 @@ def test_full_size_melt_sampled_atoms(precision, tol):
         F += o_F
     assert rel_rms(f[idx], F) <= tol, rel_rms(f[idx], F)
     assert abs(e.cpu().numpy()[-1] - e.cpu().numpy()[:-1].sum()) <= 1e-12 * np.abs(e.cpu().numpy()[:-1]).sum()
+
+
+def _gpu_total(s, M, P, r_c, tol, precision):
+    """E_c and F of reciprocal part + real-space part - self energy, all on
+    the GPU."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    c = math.log(3.0 / tol)
+    cw = window_cw(s.box, M, P, c, r_c)
+    plan = lr.Plan(s.box, s.n, s.ps, r_c, c=c, c_w=cw, P=P, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    pos = torch.tensor(s.pos, device=dev)
+    q = torch.tensor(s.q, dtype=plan.dtype, device=dev)
+    plan.set_points(pos, q)
+    e_k, _, f_k = plan.execute()
+    e_r, _, f_r = plan.real_space(pos, q)
+    plan.sync()
+    E = e_k.cpu().numpy()[:-1] + e_r.cpu().numpy()[:-1] - plan.self_energy()
+    return E, f_k.cpu().double().numpy() + f_r.cpu().double().numpy()
+
+
+def _energy_scale(q, phi):
+    """1/2 sum_i |q_i phi_i|: the size of the per-atom energies, against which
+    an energy of cancelling charges (random +-1) is measured."""
+    return 0.5 * float(np.sum(np.abs(q * phi)))
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_gpu_total_random_charges_box(precision):
+    """64 charges (+-1, minimum separation 1 A) in L = 12 A, p = 1, r_c = 4
+    (the largest the cell list takes: 3 cells per edge).  A 1e-5 force error
+    then needs the mollifier of tol 5e-6 (c = log(6e5); with c = log(3e5)
+    the oracle's total stays at 1.2e-5 on any grid): P = 8, grid 28^3
+    (oracle total 6.9e-6 from Ewald).  The energy (-0.169, from cancelling
+    terms) is measured against the per-atom energy scale."""
+    from oracle.ewald import ewald
+    s = wl.random_charges(64, 12.0, 1.0, seed=5)
+    E, F = _gpu_total(s, (28, 28, 28), 8, 4.0, 5e-6, precision)
+    ew = ewald(s.pos, s.q[0], s.box, 1)
+    assert abs(E[0] - ew["E"]) <= 1e-5 * _energy_scale(s.q[0], ew["phi"]), (E[0], ew["E"])
+    assert rel_rms(F, ew["F"]) <= 1e-5, rel_rms(F, ew["F"])
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_gpu_total_water_parameters(precision):
+    """Water-like box at its benchmarked parameters (h = 31 / 64 A, P = 8,
+    r_c = 4, tol 5e-6): the 648-atom box of the same density, 38^3."""
+    from oracle.ewald import ewald
+    s = wl.water_box(n_side=6, L=18.6, seed=4)
+    E, F = _gpu_total(s, (38, 38, 38), 8, 4.0, 5e-6, precision)
+    F_ew = np.zeros_like(F)
+    for c, p in enumerate(s.ps):
+        ew = ewald(s.pos, s.q[c], s.box, p)
+        F_ew += ew["F"]
+        assert abs(E[c] - ew["E"]) <= 1e-5 * _energy_scale(s.q[c], ew["phi"]), (c, E[c], ew["E"])
+    assert rel_rms(F, F_ew) <= 1e-5, rel_rms(F, F_ew)
+
+
+def test_gpu_total_nacl_madelung():
+    """Rock salt, 2 x 2 x 2 conventional cells (64 ions, a = 5.64 A): the
+    energy is -N M / (2 d), d = a / 2, M = 1.747564594633 (the Madelung
+    constant of rock salt), and every force vanishes by symmetry."""
+    s = wl.nacl(5.64, 2)
+    M_nacl = 1.747564594633
+    d = 5.64 / 2
+    E, F = _gpu_total(s, (28, 28, 28), 7, 3.7, 1e-5, 1)
+    ref = -s.n * M_nacl / (2 * d)
+    assert abs(E[0] - ref) <= 1e-5 * abs(ref), (E[0], ref)
+    assert np.abs(F).max() <= 1e-5 * s.n / d ** 2
