@@ -123,16 +123,24 @@ def real_space_flops(w, K: int, n: int, deg: int) -> dict:
     return {"candidates": cand, "pairs": pairs, "flops": flops}
 
 
-def csrc_digest() -> str:
+STENCIL_SOURCES = ("stencil.cuh", "kernels.cuh", "launch.cu", "launch.cuh", "planner.hpp")
+REAL_SPACE_SOURCES = ("realspace.cu", "realspace.hpp", "kernels.cuh", "planner.hpp")
+
+
+def csrc_digest(files=None) -> str:
+    """SHA-1 (12 hex digits) of the named kernel sources (all of csrc/ by
+    default)."""
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2606_06617_b300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    names = sorted(files) if files else sorted(os.listdir(os.path.join(ROOT, "paper_2606_06617_b300", "csrc")))
+    for f in names:
+        h.update(open(os.path.join(ROOT, "paper_2606_06617_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
 
 def load_traffic(workload: str, stage: str):
     """Per-launch DRAM bytes of a stage from a committed ncu summary, only if
-    the kernel sources are unchanged since the counters were taken."""
+    the sources that define its kernel are unchanged since the counters were
+    taken."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(path):
         return None
@@ -140,7 +148,7 @@ def load_traffic(workload: str, stage: str):
         d = json.load(open(path))
     except ValueError:
         return None
-    if d.get("csrc_sha") != csrc_digest():
+    if d.get("sources_sha") != csrc_digest(d.get("sources")):
         return None
     return d.get("dram_bytes_per_launch", {}).get(stage)
 

@@ -336,6 +336,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
             dz = jz + oz * g.w[2] - iz;
           }
           const R r2 = dx * dx + dy * dy + dz * dz;
+          // atoms within one fixed-point step of each other (their FP32 test
+          // coordinates may still differ) count as coincident: excluded
+          if (!(r2 > R(0))) continue;
           const R inv_r = inv_sqrt(r2);
           const R r = r2 * inv_r;
           const R ir2 = inv_r * inv_r, ir4 = ir2 * ir2;
@@ -464,13 +467,10 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
 template <typename R, int NC, int KC>
 cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
   const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(smem));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // set on every launch: the opt-in is per device and cheap
+  const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(smem));
+  if (ea != cudaSuccess) return ea;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
