@@ -15,7 +15,8 @@
   the benchmark times: potentials of every channel and forces of seeded
   sampled atoms against the oracle's per-atom neighbour sums.
 * Plans without PSWF_FLAG_REAL_SPACE, or with a box edge under 3 r_c, are
-  refused."""
+  refused; no atoms give zero energies; a cell holding more than 2048 atoms
+  is reported (PSWF_ECELL) by the next synchronising call."""
 import math
 
 import numpy as np
@@ -218,3 +219,46 @@ def test_gpu_total_nacl_madelung():
     ref = -s.n * M_nacl / (2 * d)
     assert abs(E[0] - ref) <= 1e-5 * abs(ref), (E[0], ref)
     assert np.abs(F).max() <= 1e-5 * s.n / d ** 2
+
+
+def test_real_space_empty_and_tiny():
+    """n = 0 gives zero energies; a 5-atom system in a 3 x 3 x 3 cell list
+    (most cells empty) matches the oracle."""
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (12.5, 13.0, 14.0)
+    plan = lr.Plan(box, 8, (2,), 4.0, c=C, P=6, grid=(26, 26, 28), precision=1,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, _, _ = plan.real_space(torch.zeros(0, 3, dtype=torch.float64, device=dev),
+                              torch.zeros(1, 0, dtype=torch.float64, device=dev))
+    plan.sync()
+    assert np.all(e.cpu().numpy() == 0.0)
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0.0, 1.0, size=(5, 3)) * np.asarray(box)
+    q = rng.normal(size=(1, 5))
+    e, phi, f = plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    plan.sync()
+    o = real_space(pos, q[0], box, 2, C, 4.0)
+    assert abs(e.cpu().numpy()[0] - o["E"]) <= 1e-10 * max(1.0, abs(o["E"]))
+    assert np.allclose(phi.cpu().numpy()[0], o["phi"], rtol=1e-10, atol=1e-12)
+    assert np.allclose(f.cpu().numpy(), o["F"], rtol=1e-10, atol=1e-12)
+
+
+def test_real_space_overfull_cell_is_reported():
+    """2100 atoms inside one 4.3 A cell: the queue cannot encode the cell,
+    its pairs are left out and pswf_sync returns PSWF_ECELL (-9)."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (13.0, 13.0, 13.0)
+    n = 2100
+    rng = np.random.default_rng(4)
+    pos = 5.0 + rng.uniform(0.0, 3.0, size=(n, 3))
+    q = rng.normal(size=(1, n))
+    plan = lr.Plan(box, n, (1,), 4.0, c=C, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    with pytest.raises(lr.PswfError) as e:
+        plan.sync()
+    assert e.value.status == -9
