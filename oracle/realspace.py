@@ -17,19 +17,28 @@ f64 = torch.float64
 
 
 def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
-    """E_real = 1/2 sum_{|r_ij + nL| < r_c}' q_i q_j (1 - G_p(r)) / r^p.
-    Positions may lie outside the cell.  Returns dict(E, phi [N], F [N,3])."""
+    """E_real = 1/2 sum_{|r_ij + n H| < r_c}' q_i q_j (1 - G_p(r)) / r^p over
+    the lattice n H (H: the cell's lattice vectors as rows; an orthorhombic
+    box given as three edge lengths is diag(box)).  Positions may lie
+    outside the cell.  Returns dict(E, phi [N], F [N,3])."""
     moll = moll or Mollifier(c, r_c)
+    b = np.asarray(box, dtype=np.float64)
+    H = np.diag(b) if b.shape == (3,) else b.reshape(3, 3)
     # The sum runs over every periodic image, so moving an atom by a lattice
-    # vector leaves it unchanged; with all atoms in the primary cell the
-    # image range ceil(r_c / L) + 1 per axis holds every pair closer than r_c.
-    pos = np.mod(np.asarray(pos, dtype=np.float64), np.asarray(box, dtype=np.float64))
-    box_t = torch.tensor(np.asarray(box, dtype=np.float64), dtype=f64)
+    # vector leaves it unchanged; with all atoms in the primary cell (s in
+    # [0, 1) in fractional coordinates s = r H^-1) a displacement closer than
+    # r_c needs |n_d| <= ceil(r_c / h_d) + 1, h_d = V / |a_e x a_f| the
+    # cell's height across the faces spanned by the other two vectors.
+    s = np.asarray(pos, dtype=np.float64) @ np.linalg.inv(H)
+    pos = (s - np.floor(s)) @ H
+    V = abs(np.linalg.det(H))
+    heights = [V / np.linalg.norm(np.cross(H[(d + 1) % 3], H[(d + 2) % 3])) for d in range(3)]
+    H_t = torch.tensor(H, dtype=f64)
     pos_t = torch.tensor(np.asarray(pos, dtype=np.float64), dtype=f64, requires_grad=True)
     q_t = torch.tensor(np.asarray(q, dtype=np.float64), dtype=f64, requires_grad=True)
-    nmax = [int(np.ceil(r_c / float(L))) + 1 for L in box]
+    nmax = [int(np.ceil(r_c / hd)) + 1 for hd in heights]
     shifts = torch.stack(torch.meshgrid(*[torch.arange(-m, m + 1, dtype=f64) for m in nmax],
-                                        indexing="ij"), -1).reshape(-1, 3) * box_t
+                                        indexing="ij"), -1).reshape(-1, 3) @ H_t
     N = pos_t.shape[0]
     E = torch.zeros((), dtype=f64)
     B = max(1, int(2e6 // max(1, N * shifts.shape[0])))

@@ -8,7 +8,11 @@
   the bare 1/r^p pair sum, checked on two atoms at a known distance.
 * The per-atom direct sum (real_space_atoms: minimum image, f_p' by
   autograd in r) equals the potentials and forces that real_space gets by
-  differentiating the total energy in q and r."""
+  differentiating the total energy in q and r.
+* General cells: a sheared cell against brute force over every image within
+  5 cells; a rotated box equals the box (rotated forces); a unimodular
+  change of the cell vectors (same lattice) changes nothing; a diagonal cell
+  is the box."""
 import math
 
 import numpy as np
@@ -88,3 +92,60 @@ def test_per_atom_sums_match_the_energy_derivatives():
         phi, F = real_space_atoms(idx, pos, q, box, p, C, r_c, moll)
         assert np.allclose(phi, o["phi"][idx], rtol=1e-12, atol=1e-14)
         assert np.allclose(F, o["F"][idx], rtol=1e-11, atol=1e-13)
+
+
+SHEARED = np.array([[13.0, 0.0, 0.0], [3.5, 12.0, 0.0], [-2.0, 2.5, 11.0]])
+
+
+def _brute_cell(pos, q, H, p, r_c, moll):
+    E = 0.0
+    rng = range(-5, 6)
+    for i in range(len(pos)):
+        for j in range(len(pos)):
+            for a in rng:
+                for b in rng:
+                    for cc in rng:
+                        d = pos[j] + np.array([a, b, cc], dtype=float) @ H - pos[i]
+                        r = float(np.linalg.norm(d))
+                        if 0.0 < r < r_c:
+                            E += 0.5 * q[i] * q[j] * (1.0 - moll.G(p, r)) / r ** p
+    return E
+
+
+def test_real_space_sheared_cell_brute_force():
+    from oracle.mollifiers import Mollifier
+    from oracle.realspace import real_space
+    rng = np.random.default_rng(12)
+    pos = rng.uniform(-1.0, 2.0, size=(12, 3)) @ SHEARED
+    q = rng.normal(size=12)
+    moll = Mollifier(C, 4.0)
+    for p in (1, 6):
+        o = real_space(pos, q, SHEARED, p, C, 4.0, moll)
+        ref = _brute_cell(pos, q, SHEARED, p, 4.0, moll)
+        assert abs(o["E"] - ref) <= 1e-12 * max(1.0, abs(ref)), (p, o["E"], ref)
+
+
+def test_real_space_cell_invariances():
+    import math
+    from oracle.mollifiers import Mollifier
+    from oracle.realspace import real_space
+    rng = np.random.default_rng(13)
+    moll = Mollifier(C, 4.0)
+    box = (11.0, 12.5, 10.0)
+    pos = rng.uniform(0.0, 1.0, size=(40, 3)) * np.asarray(box)
+    q = rng.normal(size=40)
+    th = 0.7
+    Rz = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    a = real_space(pos, q, box, 4, C, 4.0, moll)
+    b = real_space(pos @ Rz.T, q, np.diag(box) @ Rz.T, 4, C, 4.0, moll)
+    d = real_space(pos, q, np.diag(box), 4, C, 4.0, moll)
+    assert abs(a["E"] - b["E"]) <= 1e-12 * abs(a["E"])
+    assert np.allclose(b["F"], a["F"] @ Rz.T, rtol=1e-10, atol=1e-12)
+    assert a["E"] == d["E"]
+    U = np.array([[1, 0, 0], [1, 1, 0], [0, -1, 1]], dtype=float)
+    pos2 = rng.uniform(0.0, 1.0, size=(30, 3)) @ SHEARED
+    q2 = rng.normal(size=30)
+    e1 = real_space(pos2, q2, SHEARED, 2, C, 4.0, moll)
+    e2 = real_space(pos2, q2, U @ SHEARED, 2, C, 4.0, moll)
+    assert abs(e1["E"] - e2["E"]) <= 1e-12 * abs(e1["E"])
+    assert np.allclose(e1["F"], e2["F"], rtol=1e-10, atol=1e-12)
