@@ -266,21 +266,22 @@ int pswf_stress(pswf_plan plan, double* virial);
  * of pswf_execute and the self energies (pswf_self_energy) it gives the
  * complete 1/r^p lattice sum: E = E_recip + E_real - E_self, phi and F the
  * sums likewise (phi also takes -2 s_p q_i from the self energy).  Plans
- * created with PSWF_FLAG_REAL_SPACE (single orthorhombic structures, K <= 16,
- * every box edge at least 3 r_c: the cell list has >= 3 cells of width >= r_c
- * per axis, so each pair is found once, in its nearest image).  Inputs as
+ * created with PSWF_FLAG_REAL_SPACE (single structures in a box or a general
+ * cell, K <= 16, every height of the cell across a pair of faces at least
+ * 3 r_c: the cell list has >= 3 cells per lattice vector, each at least r_c
+ * high, so each pair is found once, in its nearest image).  Inputs as
  * pswf_set_points (positions any real value, wrapped; q real [K][n] in the
  * plan's precision); it does not touch the sorted atoms of pswf_set_points.
  * energy: device double [K + 1] (per channel, total), written; phi: real
  * [K][n], forces: real [n][3], written, either may be NULL.  Asynchronous on
  * the plan's stream; pswf_sync reports non-finite positions
- * (PSWF_ENONFINITE) and a cell of width >= r_c holding more than 2048 atoms
+ * (PSWF_ENONFINITE) and a list cell holding more than 2048 atoms
  * (PSWF_ECELL: such a cell's pairs are left out; no liquid or solid comes
  * near that density).  Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE;
  * PSWF_EINVAL for a null energy, n outside 0..n_max, missing pos / q or a
  * bad pos_dtype (pswf_plan creation with the flag already returned
- * PSWF_EINVAL for an edge < 3 r_c, a non-orthorhombic cell, a batch or
- * K > 16); PSWF_ECUDA if a launch fails. */
+ * PSWF_EINVAL for a height < 3 r_c, a batch or K > 16); PSWF_ECUDA if a
+ * launch fails. */
 int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
                     void* phi, void* forces);
 

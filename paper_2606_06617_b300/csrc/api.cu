@@ -1319,10 +1319,12 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   pl->tric = b == 1 && h.st.tric;
   pl->geo.tric = pl->tric ? 1 : 0;
   if (opts->flags & PSWF_FLAG_REAL_SPACE) {
-    if (b != 1 || pl->tric) return set_err(pl, PSWF_EINVAL, "real space: single orthorhombic structures only");
+    if (b != 1) return set_err(pl, PSWF_EINVAL, "real space: single structures only");
     if (h.K > kRsMaxK) return set_err(pl, PSWF_EINVAL, "real space: at most 16 channels");
-    if (!real_space_geometry(h.box, h.r_c, pl->rs_geo))
-      return set_err(pl, PSWF_EINVAL, "real space: each box edge must hold 3 cells of width >= r_c");
+    const bool ok = pl->tric ? real_space_geometry_cell(h.st.cell, h.r_c, pl->rs_geo)
+                             : real_space_geometry(h.box, h.r_c, pl->rs_geo);
+    if (!ok)
+      return set_err(pl, PSWF_EINVAL, "real space: each cell height must hold 3 list cells of height >= r_c");
     pl->rs_ncell = pl->rs_geo.nc[0] * pl->rs_geo.nc[1] * pl->rs_geo.nc[2];
     pl->rs_nsb = (pl->rs_ncell + 16383) / 16384;
   }

@@ -42,6 +42,7 @@
 #include "realspace.hpp"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <type_traits>
 
@@ -122,15 +123,18 @@ template <typename PosT>
 __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom g, int* __restrict__ cell_of,
                          int* __restrict__ rank, int* __restrict__ count, int* __restrict__ err) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) {
+      r[d] = double(pos[3 * i + d]);
+      if (((__double_as_longlong(r[d]) >> 52) & 0x7FF) == 0x7FF) {
+        atomicCAS(err, 0, PSWF_ENONFINITE);
+        r[d] = 0.0;
+      }
+    }
     int ci[3];
     for (int d = 0; d < 3; ++d) {
-      double x = double(pos[3 * i + d]);
-      if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) {
-        atomicCAS(err, 0, PSWF_ENONFINITE);
-        x = 0.0;
-      }
-      const double s = x * g.inv_len[d];          // in boxes
-      double fs = s - floor(s);                   // [0, 1]
+      const double s = r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d];   // in cells
+      const double fs = s - floor(s);             // [0, 1]
       int c = int(fs * g.nc[d]);
       ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
     }
@@ -151,22 +155,26 @@ __global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ 
     const int cell = cell_of[i];
     const int64_t dst = int64_t(cell_start[cell]) + rank[i];
     int ci[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
-    R t4[4] = {R(0), R(0), R(0), R(0)};
     R* r = rec + dst * rw;
+    double x[3];
     for (int d = 0; d < 3; ++d) {
-      double x = double(pos[3 * i + d]);
-      if (((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) x = 0.0;
-      const double s = x * g.inv_len[d];
-      const double local = (s - floor(s)) * g.len[d] - ci[d] * g.w[d];   // from the cell corner
-      t4[d] = R(local);
+      x[d] = double(pos[3 * i + d]);
+      if (((__double_as_longlong(x[d]) >> 52) & 0x7FF) == 0x7FF) x[d] = 0.0;
+    }
+    double u[3];   // position in the list cell, in units of its edges (0 .. 1)
+    for (int d = 0; d < 3; ++d) {
+      const double s = x[0] * g.hinv[d] + x[1] * g.hinv[3 + d] + x[2] * g.hinv[6 + d];
+      u[d] = (s - floor(s)) * g.nc[d] - ci[d];
       if constexpr (std::is_same<R, float>::value) {
-        double u = rint(local * (double(1 << kFixBits) / g.w[d]));
-        u = u < 0.0 ? 0.0 : (u > double(1 << kFixBits) ? double(1 << kFixBits) : u);
-        r[d] = __int_as_float(int(u));
+        double v = rint(u[d] * double(1 << kFixBits));
+        v = v < 0.0 ? 0.0 : (v > double(1 << kFixBits) ? double(1 << kFixBits) : v);
+        r[d] = __int_as_float(int(v));
       } else {
-        r[d] = local;
+        r[d] = u[d];
       }
     }
+    R t4[4] = {R(0), R(0), R(0), R(0)};   // Cartesian, from the list cell's corner
+    for (int k = 0; k < 3; ++k) t4[k] = R(u[0] * g.cw[k] + u[1] * g.cw[3 + k] + u[2] * g.cw[6 + k]);
     if constexpr (std::is_same<R, float>::value) {
       store_vec<R>(lchk + 4 * dst, t4);
     } else {
@@ -226,7 +234,7 @@ __device__ inline void coords(const R* v, typename LocalT<R>::type& x, typename 
 // zero charges); NC coefficients per mollifier piece (zero-padded).  The
 // coefficient table in shared memory is [exponent][vector][piece] of
 // 16-byte vectors, so lanes on different pieces read different banks.
-template <typename R, int NC, int KC>
+template <typename R, int NC, int KC, bool TRIC>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
   constexpr int RW = rec_words<R, KC>();
@@ -234,7 +242,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   Vec<R>* coefv = reinterpret_cast<Vec<R>*>(rs_smem);            // [6][NV][kMultSeg]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + size_t(warp) * warp_smem_bytes<R>();
+  R* shv = reinterpret_cast<R*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [27][4] neighbour shifts
+  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + 27 * 4 * sizeof(R) +
+                         size_t(warp) * warp_smem_bytes<R>();
   uint16_t* queue = reinterpret_cast<uint16_t*>(wbase) + lane * kQueueStride;   // this lane's column
   R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);               // [32][4] candidates
   int* nbs = reinterpret_cast<int*>(stage + 32 * 4);                            // [27] neighbour cell starts
@@ -248,14 +258,26 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
       const int k = v * kPerVec<R> + e;
       cs[t] = k <= a.deg ? a.coef[(size_t(row) * kMultSeg + seg) * (a.deg + 1) + k] : R(0);
     }
+    // the neighbour o's corner relative to a cell's corner: o . (a_d / n_c)
+    // (list cells are congruent, so also across the periodic boundary)
+    if (threadIdx.x < 27) {
+      const int o = threadIdx.x;
+      const double od[3] = {double(o % 3 - 1), double((o / 3) % 3 - 1), double(o / 9 - 1)};
+      for (int k = 0; k < 3; ++k)
+        shv[4 * o + k] = R(od[0] * a.g.cw[k] + od[1] * a.g.cw[3 + k] + od[2] * a.g.cw[6 + k]);
+      shv[4 * o + 3] = R(0);
+    }
   }
   __syncthreads();
 
   const RealSpaceGeom& g = a.g;
   const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
   const R rc2 = R(g.r_c * g.r_c), inv_rc = R(1.0 / g.r_c);
-  R unit[3];   // FP32: length of one fixed-point step per axis
-  for (int d = 0; d < 3; ++d) unit[d] = R(g.w[d] / double(1 << kFixBits));
+  // list-cell edge vectors per unit of the exact coordinates (FP32: one
+  // fixed-point step; FP64: one edge); a box uses the diagonal only
+  R ew[9];
+  const double us = std::is_same<R, float>::value ? 1.0 / double(1 << kFixBits) : 1.0;
+  for (int k = 0; k < 9; ++k) ew[k] = R(g.cw[k] * us);
   int prow[KC];
 #pragma unroll
   for (int c = 0; c < KC; ++c) prow[c] = c < a.K ? a.pch[c] - 1 : 0;
@@ -325,15 +347,25 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           load_words<R, RW>(a.rec + int64_t(j) * RW, rj);
           L jx, jy, jz;
           coords<R>(rj, jx, jy, jz);
-          R dx, dy, dz;
+          R du0, du1, du2;   // displacement in list-cell units
           if constexpr (std::is_same<R, float>::value) {
-            dx = __int2float_rn(jx + ox * (1 << kFixBits) - ix) * unit[0];
-            dy = __int2float_rn(jy + oy * (1 << kFixBits) - iy) * unit[1];
-            dz = __int2float_rn(jz + oz * (1 << kFixBits) - iz) * unit[2];
+            du0 = __int2float_rn(jx + ox * (1 << kFixBits) - ix);
+            du1 = __int2float_rn(jy + oy * (1 << kFixBits) - iy);
+            du2 = __int2float_rn(jz + oz * (1 << kFixBits) - iz);
           } else {
-            dx = jx + ox * g.w[0] - ix;
-            dy = jy + oy * g.w[1] - iy;
-            dz = jz + oz * g.w[2] - iz;
+            du0 = jx + ox - ix;
+            du1 = jy + oy - iy;
+            du2 = jz + oz - iz;
+          }
+          R dx, dy, dz;
+          if constexpr (TRIC) {
+            dx = du0 * ew[0] + du1 * ew[3] + du2 * ew[6];
+            dy = du0 * ew[1] + du1 * ew[4] + du2 * ew[7];
+            dz = du0 * ew[2] + du1 * ew[5] + du2 * ew[8];
+          } else {
+            dx = du0 * ew[0];
+            dy = du1 * ew[4];
+            dz = du2 * ew[8];
           }
           const R r2 = dx * dx + dy * dy + dz * dz;
           // atoms within one fixed-point step of each other (their FP32 test
@@ -387,8 +419,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
       };
 
       for (int o = 0; o < 27; ++o) {
-        const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-        const R ax = xi - R(od[0] * g.w[0]), ay = yi - R(od[1] * g.w[1]), az = zi - R(od[2] * g.w[2]);
+        const R ax = xi - shv[4 * o], ay = yi - shv[4 * o + 1], az = zi - shv[4 * o + 2];
         const int b0 = nbs[o], b1 = nbe[o];
         const uint32_t tag = uint32_t(o) << kCellBits;
         for (int jb = b0; jb < b1; jb += 32) {
@@ -464,21 +495,27 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
   }
 }
 
-template <typename R, int NC, int KC>
-cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
+template <typename R, int NC, int KC, bool TRIC>
+cudaError_t launch_pairs_t(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
+  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + 27 * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
   // set on every launch: the opt-in is per device and cheap
-  const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC, TRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(smem));
   if (ea != cudaSuccess) return ea;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pairs<R, NC, KC>, kRsThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pairs<R, NC, KC, TRIC>, kRsThreads, smem);
   const int64_t want = (int64_t(ncell) + kRsWarps - 1) / kRsWarps;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(nsm, 1)) * std::max(per_sm, 1))));
-  k_rs_pairs<R, NC, KC><<<blocks, kRsThreads, smem, s>>>(pa);
+  k_rs_pairs<R, NC, KC, TRIC><<<blocks, kRsThreads, smem, s>>>(pa);
   return cudaGetLastError();
+}
+
+// general cells transform displacements with the full 3 x 3 edge matrix
+template <typename R, int NC, int KC>
+cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
+  return pa.g.tric ? launch_pairs_t<R, NC, KC, true>(pa, ncell, s) : launch_pairs_t<R, NC, KC, false>(pa, ncell, s);
 }
 
 template <typename R, int NC>
@@ -509,17 +546,41 @@ size_t real_space_bytes_per_atom(int K, int real_size) {
   return real_size == 4 ? (4 + size_t(record_words<float>(K))) * 4 : (4 + size_t(record_words<double>(K))) * 8;
 }
 
-bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g) {
+bool real_space_geometry_cell(const double H[9], double r_c, RealSpaceGeom& g) {
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  if (!(std::fabs(det) > 0.0) || !(r_c > 0.0)) return false;
+  // H^-1 = adj(H) / det
+  const double inv[9] = {(H[4] * H[8] - H[5] * H[7]) / det, (H[2] * H[7] - H[1] * H[8]) / det,
+                         (H[1] * H[5] - H[2] * H[4]) / det, (H[5] * H[6] - H[3] * H[8]) / det,
+                         (H[0] * H[8] - H[2] * H[6]) / det, (H[2] * H[3] - H[0] * H[5]) / det,
+                         (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
+                         (H[0] * H[4] - H[1] * H[3]) / det};
+  bool diag = true;
   for (int d = 0; d < 3; ++d) {
-    const int nc = int(box[d] / r_c);
-    if (nc < 3) return false;
-    g.nc[d] = nc;
-    g.len[d] = box[d];
-    g.inv_len[d] = 1.0 / box[d];
-    g.w[d] = box[d] / nc;
+    // height across the faces spanned by the other two vectors: V / |a_e x a_f|
+    const double* ae = H + 3 * ((d + 1) % 3);
+    const double* af = H + 3 * ((d + 2) % 3);
+    const double cx = ae[1] * af[2] - ae[2] * af[1], cy = ae[2] * af[0] - ae[0] * af[2],
+                 cz = ae[0] * af[1] - ae[1] * af[0];
+    const double height = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
+    const double ncd = std::floor(height / r_c);
+    if (!(ncd >= 3.0) || ncd > 1e6) return false;
+    g.nc[d] = int(ncd);
+    for (int k = 0; k < 3; ++k) {
+      g.cw[3 * d + k] = H[3 * d + k] / g.nc[d];
+      if (k != d && H[3 * d + k] != 0.0) diag = false;
+    }
   }
+  for (int k = 0; k < 9; ++k) g.hinv[k] = inv[k];
+  g.tric = diag ? 0 : 1;
   g.r_c = r_c;
   return true;
+}
+
+bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g) {
+  const double H[9] = {box[0], 0.0, 0.0, 0.0, box[1], 0.0, 0.0, 0.0, box[2]};
+  return real_space_geometry_cell(H, r_c, g);
 }
 
 template <typename R>

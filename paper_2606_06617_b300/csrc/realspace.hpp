@@ -10,18 +10,24 @@ namespace pswf {
 
 constexpr int kRsMaxK = 16;   // channels of one real-space call
 
-// Cells of an orthorhombic box: n_c per axis (>= 3), width w = L / n_c >= r_c.
+// Cell list of a periodic cell H (lattice vectors a_d as rows): n_c per axis
+// along each a_d (>= 3), each list cell the parallelepiped spanned by
+// a_d / n_c[d], whose height across every pair of faces is >= r_c.  For an
+// orthorhombic box H = diag(L) and the list cells are boxes of width L / n_c.
 struct RealSpaceGeom {
   int nc[3];
-  double len[3], inv_len[3], w[3];
+  int tric;            // 0: orthorhombic box (the pair kernel's 3-multiply path)
+  double hinv[9];      // H^-1, row-major: fractional s_d = sum_k r_k hinv[3 k + d]
+  double cw[9];        // rows a_d / n_c[d]: the list cell's edge vectors
   double r_c;
 };
 
 // Device bytes per atom of the cell-local coordinates and records.
 size_t real_space_bytes_per_atom(int K, int real_size);
 
-// False when a box edge holds fewer than 3 cells of width >= r_c.
+// False when an edge holds fewer than 3 list cells whose heights are >= r_c.
 bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g);
+bool real_space_geometry_cell(const double cell[9], double r_c, RealSpaceGeom& g);
 
 struct RealSpaceArgs {
   RealSpaceGeom geo;

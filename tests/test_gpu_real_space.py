@@ -14,6 +14,10 @@
 * The full-size melt (4,194,304 atoms, r_c = 7, K = 4), the configuration
   the benchmark times: potentials of every channel and forces of seeded
   sampled atoms against the oracle's per-atom neighbour sums.
+* General cells: a sheared cell against the oracle's lattice sum (FP64
+  1e-10, FP32 2e-6), and the melt sub-box rotated into a general cell:
+  reciprocal + real space - self against Ewald of the unrotated box, forces
+  rotated, within 1e-5.
 * Plans without PSWF_FLAG_REAL_SPACE, or with a box edge under 3 r_c, are
   refused; no atoms give zero energies; a cell holding more than 2048 atoms
   is reported (PSWF_ECELL) by the next synchronising call."""
@@ -262,3 +266,68 @@ def test_real_space_overfull_cell_is_reported():
     with pytest.raises(lr.PswfError) as e:
         plan.sync()
     assert e.value.status == -9
+
+
+SHEARED = np.array([[19.2, 0.0, 0.0], [4.5, 18.0, 0.0], [-3.0, 3.5, 17.5]])
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, TOL_FP32)])
+def test_real_space_sheared_cell_matches_oracle(precision, tol):
+    """Sheared cell (heights 17.5-18.0 A, 4 list cells per edge at r_c = 4),
+    p = 1 and 6, atoms up to one cell outside."""
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(21)
+    n = 500
+    pos = rng.uniform(-1.0, 2.0, size=(n, 3)) @ SHEARED
+    q = rng.normal(size=(2, n))
+    plan = lr.Plan(None, n, (1, 6), 4.0, c=C, P=6, grid=(40, 36, 36), precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev, cell=SHEARED)
+    e, phi, f = plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    plan.sync()
+    e, phi, f = e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy()
+    F = np.zeros((n, 3))
+    for c, p in enumerate((1, 6)):
+        o = real_space(pos, q[c], SHEARED, p, C, 4.0)
+        assert abs(e[c] - o["E"]) <= tol * abs(o["E"]), (c, e[c], o["E"])
+        assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
+        F += o["F"]
+    assert rel_rms(f, F) <= tol, rel_rms(f, F)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_gpu_total_rotated_melt_box_matches_ewald(precision):
+    """The ionic-melt sub-box (L = 21.875 A, 1024 atoms, r_c = 7, P = 7,
+    24^3) rotated into a general cell H = L R^T: the complete lattice sum
+    from the GPU against Ewald of the unrotated box (forces rotated back)."""
+    import torch
+    from oracle.ewald import ewald
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    L = 350.0 * 24 / 384
+    s = wl.ionic_melt(int(round(4194304 * (L / 350.0) ** 3)), L, seed=3)
+    th, ph = 0.5, 0.3
+    Rz = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, math.cos(ph), -math.sin(ph)], [0.0, math.sin(ph), math.cos(ph)]])
+    R = Rx @ Rz
+    H = np.diag(s.box) @ R.T
+    M = (24, 24, 24)
+    cw = window_cw(s.box, M, 7, C, 7.0)
+    plan = lr.Plan(None, s.n, s.ps, 7.0, c=C, c_w=cw, P=7, grid=M, precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev, cell=H)
+    pos = torch.tensor(s.pos @ R.T, device=dev)
+    q = torch.tensor(s.q, dtype=plan.dtype, device=dev)
+    plan.set_points(pos, q)
+    e_k, _, f_k = plan.execute()
+    e_r, _, f_r = plan.real_space(pos, q)
+    plan.sync()
+    E = e_k.cpu().numpy()[:-1] + e_r.cpu().numpy()[:-1] - plan.self_energy()
+    F = (f_k.cpu().double().numpy() + f_r.cpu().double().numpy()) @ R   # back to the box frame
+    F_ew = np.zeros_like(F)
+    for c, p in enumerate(s.ps):
+        ew = ewald(s.pos, s.q[c], s.box, p)
+        F_ew += ew["F"]
+        assert abs(E[c] - ew["E"]) <= 1e-5 * _energy_scale(s.q[c], ew["phi"]), (c, E[c], ew["E"])
+    assert rel_rms(F, F_ew) <= 1e-5, rel_rms(F, F_ew)
