@@ -28,6 +28,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -127,13 +128,21 @@ STENCIL_SOURCES = ("stencil.cuh", "kernels.cuh", "launch.cu", "launch.cuh", "pla
 REAL_SPACE_SOURCES = ("realspace.cu", "realspace.hpp", "kernels.cuh", "planner.hpp")
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace collapsed: a
+    comment edit leaves the digest of a kernel's code unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def csrc_digest(files=None) -> str:
-    """SHA-1 (12 hex digits) of the named kernel sources (all of csrc/ by
-    default)."""
+    """SHA-1 (12 hex digits) of the code (comments stripped) of the named
+    kernel sources (all of csrc/ by default)."""
     h = hashlib.sha1()
     names = sorted(files) if files else sorted(os.listdir(os.path.join(ROOT, "paper_2606_06617_b300", "csrc")))
     for f in names:
-        h.update(open(os.path.join(ROOT, "paper_2606_06617_b300", "csrc", f), "rb").read())
+        h.update(code_only(open(os.path.join(ROOT, "paper_2606_06617_b300", "csrc", f)).read()).encode())
     return h.hexdigest()[:12]
 
 

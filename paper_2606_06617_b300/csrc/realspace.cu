@@ -8,37 +8,44 @@
 //   f_p(r) = (1 - G_p(r / r_c)) / r^p
 //
 // with G_p the planner's piecewise polynomial in x = r / r_c (the multiplier's
-// piece layout).  Neighbours come from a cell list of its own (cells at least
-// r_c wide, at least 3 per axis, so each pair is found once, in one image):
-// atoms are counted into cells, scanned, and scattered as cell-local
-// coordinates with their charges.
+// piece layout).  Neighbours come from a cell list of its own along the
+// lattice vectors a_d of the cell H: n_c[d] >= 3 list cells per vector, each
+// the parallelepiped spanned by a_d / n_c[d] and at least r_c high across
+// every pair of faces, so a pair closer than r_c lies in adjacent list cells
+// and is found once, in one image (for a box the list cells are boxes).
+// Atoms are counted into list cells (fractional coordinates s = r H^-1),
+// scanned, and scattered in cell order with their charges.
 //
-// Pair kernel: persistent blocks of 8 warps, one warp per cell at a time,
-// its atoms in chunks of up to 32.  A chunk of m atoms gives each atom
+// Pair kernel: persistent blocks of 8 warps, one warp per list cell at a
+// time, its atoms in chunks of up to 32.  A chunk of m atoms gives each atom
 // G = 32 / m lanes (a power of two), which split the 27 neighbour cells'
 // candidates, so partial chunks keep the lanes busy.  Each lane tests its
 // candidates against r_c (about 15% pass in a liquid) and appends the ones
-// inside to its own queue in shared memory; the queues are drained in
+// inside to its own queue in shared memory (16-bit entries: neighbour and
+// index in that cell); after the 27 neighbours the queues are drained in
 // rounds in which every lane evaluates one of its queued pairs, so the
 // mollifier polynomials run on dense rounds rather than on the few lanes
-// whose candidate happens to pass.  Per-atom sums stay in registers (no
-// atomics); the G lanes of an atom are summed with shuffles at the end.
+// whose candidate happens to pass, and draining once per sweep keeps the
+// lanes' queue lengths (their atoms' pair counts) close.  Per-atom sums stay
+// in registers (no atomics); the G lanes of an atom are summed with shuffles
+// at the end.
 //
-// Coordinates: the cutoff test reads cell-local coordinates in the plan's
-// precision (16 or 32 bytes per atom, streamed through a shared-memory stage).
-// A queued pair is evaluated from the neighbour's record: its exact
-// coordinates and its K charges side by side (one 32-byte sector for K <= 5
+// Coordinates: the cutoff test reads Cartesian coordinates from the list
+// cell's corner in the plan's precision (16 or 32 bytes per atom, streamed
+// through a shared-memory stage); a neighbour's corner is o . (a_d / n_c)
+// away, from a table the block fills once.  A queued pair is evaluated from
+// the neighbour's record: its position in its list cell in units of the
+// cell's edges and its K charges side by side (one 32-byte sector for K <= 5
 // in FP32), so the scattered reads of the pair rounds touch one record, not
-// K + 1 arrays.  FP32 records hold the coordinates as integers in units of
-// w / 2^29: the displacement is an exact integer
-// difference (the neighbour cell adds its offset o 2^29) rounded to FP32
-// once, so its relative error is that of one rounding at any distance.
-// FP32 coordinates and an FP32 cell offset would carry an absolute error
-// ~1e-7 w, which 1/r^p magnifies to p 1e-7 w / r on close pairs (5e-6 of an
-// energy at p = 4 with pairs 0.2 A apart in 4 A cells).  A pair whose FP32
-// test and exact distance straddle r_c differs from the sum by a term with
-// 1 - G_p(1) ~ 1e-5, which is negligible.  FP64 records hold FP64
-// coordinates.
+// K + 1 arrays.  FP32 records hold the position as integers in units of
+// 2^-29 of an edge: the displacement is an exact integer difference (the
+// neighbour cell adds its offset o 2^29) times the edge matrix, so its
+// relative error is that of a few roundings at any distance.  FP32
+// coordinates and an FP32 cell offset would carry an absolute error ~1e-7 w,
+// which 1/r^p magnifies to p 1e-7 w / r on close pairs (5e-6 of an energy at
+// p = 4 with pairs 0.2 A apart in 4 A cells).  A pair whose FP32 test and
+// exact distance straddle r_c differs from the sum by a term with
+// 1 - G_p(1) ~ 1e-5, which is negligible.  FP64 records hold FP64 positions.
 #include "realspace.hpp"
 
 #include <algorithm>
