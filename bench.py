@@ -23,7 +23,6 @@ system does not shard, so N > 1 is N independent replicas (weak scaling).
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
