@@ -331,3 +331,35 @@ def test_gpu_total_rotated_melt_box_matches_ewald(precision):
         F_ew += ew["F"]
         assert abs(E[c] - ew["E"]) <= 1e-5 * _energy_scale(s.q[c], ew["phi"]), (c, E[c], ew["E"])
     assert rel_rms(F, F_ew) <= 1e-5, rel_rms(F, F_ew)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, TOL_FP32)])
+def test_real_space_sixteen_channels(precision, tol):
+    """K = 16 (the largest channel class of the pair kernel), exponents
+    cycling through 1..6, against the oracle channel by channel.  Random
+    non-neutral charges can make a channel's energy a small difference of
+    large pair terms (p = 5 here: E = -1.04), so energies are measured
+    against the per-atom energy scale 1/2 sum |q_i phi_i|."""
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (12.6, 13.2, 14.1)
+    ps = tuple(1 + (c % 6) for c in range(16))
+    rng = np.random.default_rng(31)
+    n = 260
+    pos = rng.uniform(-0.5, 1.5, size=(n, 3)) * np.asarray(box)
+    q = rng.normal(size=(16, n))
+    plan = lr.Plan(box, n, ps, 4.0, c=C, P=6, grid=(26, 28, 30), precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, phi, f = plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    plan.sync()
+    e, phi, f = e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy()
+    F = np.zeros((n, 3))
+    for c, p in enumerate(ps):
+        o = real_space(pos, q[c], box, p, C, 4.0)
+        scale = max(abs(o["E"]), _energy_scale(q[c], o["phi"]))
+        assert abs(e[c] - o["E"]) <= tol * scale, (c, e[c], o["E"], scale)
+        assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
+        F += o["F"]
+    assert rel_rms(f, F) <= tol, rel_rms(f, F)
