@@ -267,9 +267,12 @@ int pswf_stress(pswf_plan plan, double* virial);
  * complete 1/r^p lattice sum: E = E_recip + E_real - E_self, phi and F the
  * sums likewise (phi also takes -2 s_p q_i from the self energy).  Plans
  * created with PSWF_FLAG_REAL_SPACE (single structures in a box or a general
- * cell, K <= 16, every height of the cell across a pair of faces at least
- * 3 r_c: the cell list has >= 3 cells per lattice vector, each at least r_c
- * high, so each pair is found once, in its nearest image).  Inputs as
+ * cell, K <= 16).  When every height of the cell across a pair of faces is
+ * at least 3 r_c a cell list is used (>= 3 list cells per lattice vector,
+ * each at least r_c high, so each pair is found once, in its nearest
+ * image); otherwise every pair of atoms is summed over the images n H that
+ * can come closer than r_c (minimum image for r_c <= L/2, more images
+ * beyond), for at most 16384 atoms.  Inputs as
  * pswf_set_points (positions any real value, wrapped; q real [K][n] in the
  * plan's precision); it does not touch the sorted atoms of pswf_set_points.
  * energy: device double [K + 1] (per channel, total), written; phi: real
@@ -280,8 +283,9 @@ int pswf_stress(pswf_plan plan, double* virial);
  * near that density).  Errors: PSWF_ESTATE without PSWF_FLAG_REAL_SPACE;
  * PSWF_EINVAL for a null energy, n outside 0..n_max, missing pos / q or a
  * bad pos_dtype (pswf_plan creation with the flag already returned
- * PSWF_EINVAL for a height < 3 r_c, a batch or K > 16); PSWF_ECUDA if a
- * launch fails. */
+ * PSWF_EINVAL for a batch, K > 16, a direct sum over more than 16384
+ * atoms or r_c needing more than 4096 images); PSWF_ECUDA if a launch
+ * fails. */
 int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
                     void* phi, void* forces);
 

@@ -1323,8 +1323,10 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
     if (h.K > kRsMaxK) return set_err(pl, PSWF_EINVAL, "real space: at most 16 channels");
     const bool ok = pl->tric ? real_space_geometry_cell(h.st.cell, h.r_c, pl->rs_geo)
                              : real_space_geometry(h.box, h.r_c, pl->rs_geo);
-    if (!ok)
-      return set_err(pl, PSWF_EINVAL, "real space: each cell height must hold 3 list cells of height >= r_c");
+    if (!ok) return set_err(pl, PSWF_EINVAL, "real space: r_c needs more than 4096 images of the cell");
+    if (pl->rs_geo.direct && n_max > kRsDirectMaxAtoms)
+      return set_err(pl, PSWF_EINVAL,
+                     "real space: a cell height below 3 r_c takes the direct pair sum, at most 16384 atoms");
     pl->rs_ncell = pl->rs_geo.nc[0] * pl->rs_geo.nc[1] * pl->rs_geo.nc[2];
     pl->rs_nsb = (pl->rs_ncell + 16383) / 16384;
   }

@@ -494,6 +494,187 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   }
 }
 
+// Direct mode: one thread per atom i, every atom j in shared-memory tiles,
+// every image n H of the image table.  Both atoms are wrapped into the
+// primary cell; a FP32 test on the wrapped Cartesian positions selects the
+// pairs closer than r_c, whose displacement is then formed in FP64 and
+// rounded once.
+constexpr int kDirectThreads = 128;
+
+template <typename PosT>
+__device__ inline void wrapped(const PosT* __restrict__ pos, int64_t i, const RealSpaceGeom& g, double (&x)[3],
+                               int* err) {
+  double r[3];
+  for (int d = 0; d < 3; ++d) {
+    r[d] = double(pos[3 * i + d]);
+    if (((__double_as_longlong(r[d]) >> 52) & 0x7FF) == 0x7FF) {
+      if (err) atomicCAS(err, 0, PSWF_ENONFINITE);
+      r[d] = 0.0;
+    }
+  }
+  double s[3];
+  for (int d = 0; d < 3; ++d) {
+    s[d] = r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d];
+    s[d] -= floor(s[d]);
+  }
+  for (int k = 0; k < 3; ++k) x[k] = s[0] * g.h[k] + s[1] * g.h[3 + k] + s[2] * g.h[6 + k];
+}
+
+template <typename R, typename PosT, int NC, int KC>
+__global__ void __launch_bounds__(kDirectThreads) k_rs_direct(int64_t n, int K, const PosT* __restrict__ pos,
+                                                              const R* __restrict__ q, RealSpaceGeom g,
+                                                              const int* __restrict__ pch,
+                                                              const R* __restrict__ coef_src, int deg,
+                                                              double* __restrict__ energy, R* __restrict__ phi,
+                                                              R* __restrict__ forces, int* __restrict__ err) {
+  constexpr int NV = NC / kPerVec<R>;
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  Vec<R>* coefv = reinterpret_cast<Vec<R>*>(rs_smem);                          // [6][NV][kMultSeg]
+  double* img = reinterpret_cast<double*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [nimg][3]
+  const int nimages = (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1);
+  double* tpos = img + 3 * nimages;                                            // [kDirectThreads][3]
+  R* tq = reinterpret_cast<R*>(tpos + 3 * kDirectThreads);                     // [KC][kDirectThreads]
+  {
+    R* cs = reinterpret_cast<R*>(rs_smem);
+    for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
+      const int e = t % kPerVec<R>, seg = (t / kPerVec<R>) % kMultSeg, v = (t / (kPerVec<R> * kMultSeg)) % NV,
+                row = t / (kPerVec<R> * kMultSeg * NV);
+      const int k = v * kPerVec<R> + e;
+      cs[t] = k <= deg ? coef_src[(size_t(row) * kMultSeg + seg) * (deg + 1) + k] : R(0);
+    }
+    for (int t = threadIdx.x; t < nimages; t += blockDim.x) {
+      const int n0 = t % (2 * g.nimg[0] + 1) - g.nimg[0];
+      const int n1 = (t / (2 * g.nimg[0] + 1)) % (2 * g.nimg[1] + 1) - g.nimg[1];
+      const int n2 = t / ((2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1)) - g.nimg[2];
+      for (int k = 0; k < 3; ++k) img[3 * t + k] = n0 * g.h[k] + n1 * g.h[3 + k] + n2 * g.h[6 + k];
+    }
+  }
+  const R rc2 = R(g.r_c * g.r_c), inv_rc = R(1.0 / g.r_c);
+  int prow[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) prow[c] = c < K ? pch[c] - 1 : 0;
+  const int64_t i = blockIdx.x * int64_t(kDirectThreads) + threadIdx.x;
+  const bool own = i < n;
+  double xi[3] = {0.0, 0.0, 0.0};
+  if (own) wrapped(pos, i, g, xi, err);
+  R qi[KC], ph[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    qi[c] = own && c < K ? q[int64_t(c) * n + i] : R(0);
+    ph[c] = R(0);
+  }
+  R fx = 0, fy = 0, fz = 0;
+  for (int64_t j0 = 0; j0 < n; j0 += kDirectThreads) {
+    __syncthreads();   // the previous tile is consumed (and the tables are written)
+    const int64_t jl = j0 + threadIdx.x;
+    if (jl < n) {
+      double xj[3];
+      wrapped(pos, jl, g, xj, nullptr);
+      for (int k = 0; k < 3; ++k) tpos[3 * threadIdx.x + k] = xj[k];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) tq[c * kDirectThreads + threadIdx.x] = c < K ? q[int64_t(c) * n + jl] : R(0);
+    }
+    __syncthreads();
+    const int cnt = int(n - j0 < kDirectThreads ? n - j0 : int64_t(kDirectThreads));
+    if (!own) continue;
+    for (int jj = 0; jj < cnt; ++jj) {
+      const double b0 = tpos[3 * jj] - xi[0], b1 = tpos[3 * jj + 1] - xi[1], b2 = tpos[3 * jj + 2] - xi[2];
+      for (int t = 0; t < nimages; ++t) {
+        const float tx = float(b0 + img[3 * t]), ty = float(b1 + img[3 * t + 1]), tz = float(b2 + img[3 * t + 2]);
+        const float t2 = tx * tx + ty * ty + tz * tz;
+        if (!(t2 < float(rc2) * 1.0001f)) continue;   // FP32 test with margin; the exact test follows
+        const R dx = R(b0 + img[3 * t]), dy = R(b1 + img[3 * t + 1]), dz = R(b2 + img[3 * t + 2]);
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < rc2) || !(r2 > R(0))) continue;   // outside r_c, or the atom itself
+        const R inv_r = inv_sqrt(r2);
+        const R r = r2 * inv_r;
+        const R ir2 = inv_r * inv_r, ir4 = ir2 * ir2;
+        R x = r * inv_rc;
+        if (x >= R(1)) x = R(1) - R(1e-7);
+        int seg = int(x * R(kMultSeg));
+        if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+        const R sv = R(2) * (x * R(kMultSeg) - R(seg)) - R(1);
+        R fsum = 0;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+          R cf[NC];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const Vec<R> cv = coefv[(prow[c] * NV + v) * kMultSeg + seg];
+            if constexpr (std::is_same<R, float>::value) {
+              cf[4 * v] = cv.x;
+              cf[4 * v + 1] = cv.y;
+              cf[4 * v + 2] = cv.z;
+              cf[4 * v + 3] = cv.w;
+            } else {
+              cf[2 * v] = cv.x;
+              cf[2 * v + 1] = cv.y;
+            }
+          }
+          R Gv = cf[NC - 1], dG = R(0);
+#pragma unroll
+          for (int k = NC - 2; k >= 0; --k) {
+            dG = dG * sv + Gv;
+            Gv = Gv * sv + cf[k];
+          }
+          dG *= R(2 * kMultSeg);
+          const int p = prow[c] + 1;
+          const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
+          const R one_m = R(1) - Gv;
+          const R qj = tq[c * kDirectThreads + jj];
+          ph[c] += qj * one_m * rp;
+          fsum -= qi[c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
+        }
+        const R sc = fsum * inv_r;
+        fx += sc * dx;
+        fy += sc * dy;
+        fz += sc * dz;
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    if (c >= K) break;
+    double e = own ? 0.5 * double(qi[c]) * double(ph[c]) : 0.0;
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
+    if (lane == 0 && e != 0.0) atomicAdd(energy + c, e);
+    if (own && phi) phi[int64_t(c) * n + i] = ph[c];
+  }
+  if (own && forces) {
+    forces[3 * i] = fx;
+    forces[3 * i + 1] = fy;
+    forces[3 * i + 2] = fz;
+  }
+}
+
+template <typename R, typename PosT, int NC, int KC>
+cudaError_t launch_direct_k(const RealSpaceArgs& a, cudaStream_t s) {
+  const RealSpaceGeom& g = a.geo;
+  const int nimages = (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1);
+  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + size_t(nimages) * 3 * sizeof(double) +
+                      size_t(kDirectThreads) * 3 * sizeof(double) + size_t(KC) * kDirectThreads * sizeof(R);
+  const cudaError_t ea = cudaFuncSetAttribute(k_rs_direct<R, PosT, NC, KC>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (ea != cudaSuccess) return ea;
+  const int blocks = int((a.n + kDirectThreads - 1) / kDirectThreads);
+  k_rs_direct<R, PosT, NC, KC><<<blocks, kDirectThreads, smem, s>>>(
+      a.n, a.K, static_cast<const PosT*>(a.pos), static_cast<const R*>(a.q), g, a.pch,
+      static_cast<const R*>(a.coef_g), a.deg_g, a.energy, static_cast<R*>(a.phi), static_cast<R*>(a.forces), a.err);
+  return cudaGetLastError();
+}
+
+template <typename R, typename PosT, int NC>
+cudaError_t launch_direct(const RealSpaceArgs& a, cudaStream_t s) {
+  switch (channel_class(a.K)) {
+    case 1: return launch_direct_k<R, PosT, NC, 1>(a, s);
+    case 2: return launch_direct_k<R, PosT, NC, 2>(a, s);
+    case 4: return launch_direct_k<R, PosT, NC, 4>(a, s);
+    case 8: return launch_direct_k<R, PosT, NC, 8>(a, s);
+    default: return launch_direct_k<R, PosT, NC, kRsMaxK>(a, s);
+  }
+}
+
 __global__ void k_rs_total(int K, double* __restrict__ energy) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double t = 0.0;
@@ -564,21 +745,35 @@ bool real_space_geometry_cell(const double H[9], double r_c, RealSpaceGeom& g) {
                          (H[3] * H[7] - H[4] * H[6]) / det, (H[1] * H[6] - H[0] * H[7]) / det,
                          (H[0] * H[4] - H[1] * H[3]) / det};
   bool diag = true;
+  double height[3];
+  g.direct = 0;
   for (int d = 0; d < 3; ++d) {
     // height across the faces spanned by the other two vectors: V / |a_e x a_f|
     const double* ae = H + 3 * ((d + 1) % 3);
     const double* af = H + 3 * ((d + 2) % 3);
     const double cx = ae[1] * af[2] - ae[2] * af[1], cy = ae[2] * af[0] - ae[0] * af[2],
                  cz = ae[0] * af[1] - ae[1] * af[0];
-    const double height = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
-    const double ncd = std::floor(height / r_c);
-    if (!(ncd >= 3.0) || ncd > 1e6) return false;
-    g.nc[d] = int(ncd);
+    height[d] = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
+    const double ncd = std::floor(height[d] / r_c);
+    if (ncd > 1e6) return false;
+    if (!(ncd >= 3.0)) g.direct = 1;
+    g.nc[d] = ncd >= 3.0 ? int(ncd) : 1;
+    for (int k = 0; k < 3; ++k)
+      if (k != d && H[3 * d + k] != 0.0) diag = false;
+  }
+  long long nimages = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (g.direct) g.nc[d] = 1;
     for (int k = 0; k < 3; ++k) {
       g.cw[3 * d + k] = H[3 * d + k] / g.nc[d];
-      if (k != d && H[3 * d + k] != 0.0) diag = false;
+      g.h[3 * d + k] = H[3 * d + k];
     }
+    // with both atoms in the primary cell a displacement closer than r_c
+    // needs |n_d| <= ceil(r_c / height_d) + 1
+    g.nimg[d] = int(std::ceil(r_c / height[d])) + 1;
+    nimages *= 2 * g.nimg[d] + 1;
   }
+  if (g.direct && nimages > kRsDirectMaxImages) return false;
   for (int k = 0; k < 9; ++k) g.hinv[k] = inv[k];
   g.tric = diag ? 0 : 1;
   g.r_c = r_c;
@@ -597,6 +792,24 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
   if (a.deg_g > kMaxMultDeg) return cudaErrorInvalidValue;
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.energy, 0, size_t(a.K + 1) * sizeof(double), s)) != cudaSuccess) return e;
+  if (g.direct) {
+    if (a.n > 0) {
+      if constexpr (std::is_same<R, float>::value) {
+        const bool wide = a.deg_g + 1 > 8;
+        if (a.pos_dtype == 1)
+          e = wide ? launch_direct<R, double, 20>(a, s) : launch_direct<R, double, 8>(a, s);
+        else
+          e = wide ? launch_direct<R, float, 20>(a, s) : launch_direct<R, float, 8>(a, s);
+      } else {
+        e = a.pos_dtype == 1 ? launch_direct<R, double, 18>(a, s) : launch_direct<R, float, 18>(a, s);
+      }
+      if (e != cudaSuccess) return e;
+      ++*nlaunch;
+    }
+    k_rs_total<<<1, 32, 0, s>>>(a.K, a.energy);
+    ++*nlaunch;
+    return cudaGetLastError();
+  }
   if ((e = cudaMemsetAsync(a.count, 0, size_t(ncell) * sizeof(int), s)) != cudaSuccess) return e;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((a.n + kRsThreads - 1) / kRsThreads, 148 * 16)));
   if (a.n > 0) {

@@ -20,12 +20,23 @@ struct RealSpaceGeom {
   double hinv[9];      // H^-1, row-major: fractional s_d = sum_k r_k hinv[3 k + d]
   double cw[9];        // rows a_d / n_c[d]: the list cell's edge vectors
   double r_c;
+  // direct mode (a height below 3 r_c: no cell list): every pair of atoms
+  // over the images n H, |n_d| <= nimg[d]
+  int direct;
+  int nimg[3];
+  double h[9];         // H, rows a_d
 };
+
+constexpr int kRsDirectMaxAtoms = 16384;   // direct mode: O(n^2 images) work
+constexpr int kRsDirectMaxImages = 4096;
 
 // Device bytes per atom of the cell-local coordinates and records.
 size_t real_space_bytes_per_atom(int K, int real_size);
 
-// False when an edge holds fewer than 3 list cells whose heights are >= r_c.
+// Cell list when every height of the cell holds 3 list cells of height
+// >= r_c; otherwise direct mode with the image ranges that hold every pair
+// closer than r_c.  False for a singular cell or more than
+// kRsDirectMaxImages images.
 bool real_space_geometry(const double box[3], double r_c, RealSpaceGeom& g);
 bool real_space_geometry_cell(const double cell[9], double r_c, RealSpaceGeom& g);
 

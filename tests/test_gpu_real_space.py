@@ -18,8 +18,11 @@
   1e-10, FP32 2e-6), and the melt sub-box rotated into a general cell:
   reciprocal + real space - self against Ewald of the unrotated box, forces
   rotated, within 1e-5.
-* Plans without PSWF_FLAG_REAL_SPACE, or with a box edge under 3 r_c, are
-  refused; no atoms give zero energies; a cell holding more than 2048 atoms
+* Cells with a height below 3 r_c (no cell list: the direct sum over all
+  pairs and images): a box at r_c = L/2 and a small sheared cell with r_c
+  above its heights, against the oracle (FP64 1e-10, FP32 2e-6).
+* Plans without PSWF_FLAG_REAL_SPACE, or direct-sum plans above 16384 atoms,
+  are refused; no atoms give zero energies; a cell holding more than 2048 atoms
   is reported (PSWF_ECELL) by the next synchronising call."""
 import math
 
@@ -102,8 +105,8 @@ def test_real_space_refusals():
     with pytest.raises(lr.PswfError) as e:
         plan.real_space(pos, q)
     assert e.value.status == -8
-    with pytest.raises(lr.PswfError) as e:
-        lr.Plan((11.0, 13.0, 13.0), 10, (1,), 4.0, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE,
+    with pytest.raises(lr.PswfError) as e:   # a height below 3 r_c: direct sum, at most 16384 atoms
+        lr.Plan((11.0, 13.0, 13.0), 20000, (1,), 4.0, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE,
                 device=dev)
     assert e.value.status == -1
 
@@ -363,3 +366,36 @@ def test_real_space_sixteen_channels(precision, tol):
         assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
         F += o["F"]
     assert rel_rms(f, F) <= tol, rel_rms(f, F)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, TOL_FP32)])
+def test_real_space_direct_sum_small_cells(precision, tol):
+    """No cell list: the 64-charge box (L = 12 A) at r_c = 6 = L/2 (minimum
+    image), and the sheared cell scaled to edges of about 9.5 A with
+    r_c = 6 above its heights (images up to two cells away); p = 1, 4, 6."""
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(41)
+    s = wl.random_charges(64, 12.0, 1.0, seed=6)
+    cases = [(np.diag(s.box), s.pos, rng.normal(size=(3, 64)), (24, 24, 24))]
+    H = SHEARED / 2.0
+    pos = rng.uniform(-0.5, 1.5, size=(90, 3)) @ H
+    cases.append((H, pos, rng.normal(size=(3, 90)), (24, 24, 24)))
+    ps = (1, 4, 6)
+    for H, pos, q, M in cases:
+        n = len(pos)
+        plan = lr.Plan(None, n, ps, 6.0, c=C, P=6, grid=M, precision=precision, flags=lr.PSWF_FLAG_REAL_SPACE,
+                       device=dev, cell=H)
+        e, phi, f = plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+        plan.sync()
+        e, phi, f = e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy()
+        F = np.zeros((n, 3))
+        for c, p in enumerate(ps):
+            o = real_space(pos, q[c], H, p, C, 6.0)
+            scale = max(abs(o["E"]), _energy_scale(q[c], o["phi"]))
+            assert abs(e[c] - o["E"]) <= tol * scale, (c, e[c], o["E"])
+            assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
+            F += o["F"]
+        assert rel_rms(f, F) <= tol, rel_rms(f, F)
