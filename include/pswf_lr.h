@@ -259,7 +259,7 @@ int pswf_virial(pswf_plan plan, double* virial);
 int pswf_stress(pswf_plan plan, double* virial);
 
 /* Real-space complement (Methods, "Implementation details": the
- * pair term that completes Eq. (Fourier); G_p = 1 beyond r_c, reading C3):
+ * pair term that completes Eq. (Fourier); G_p taken as 1 beyond r_c):
  *   E_c = 1/2 sum_{i != j, |r_ij| < r_c} q_i^c q_j^c (1 - G_p(r_ij)) / r_ij^p
  * with G_p of Eq. G1, G6, G (the planner's piecewise polynomial in r / r_c),
  * its potentials phi_i^c = dE_c / dq_i^c and forces.  With the reciprocal part

@@ -2,7 +2,7 @@
 
 Eq. (Fourier) with its latent structure factor
 rho^(p)(k) = sum_i q_i^(p) exp(i k . r_i), truncated at the effective cutoff
-k_c = c / r_c (Phi-hat_p vanishes beyond it under reading C1), without any
+k_c = c / r_c (Phi-hat_p vanishes beyond it, psi_0(x/c) taken as zero for x > c), without any
 grid, window or FFT:
 
     E_k   = 1/(2V) sum_{0 < |k| < k_c} Phi-hat_p(k) |rho(k)|^2

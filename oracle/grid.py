@@ -23,9 +23,9 @@ the grid potential is Psi = (Delta V^2 / V) * IDFT[G rho-hat] (unnormalised
 inverse), and for each atom phi_i = sum_g Psi_g W(x_g - r_i) and
 F_i = q_i sum_g Psi_g (grad W)(x_g - r_i) = -dE/dr_i.
 
-Stencil (reading C5): with u = r / h, the P points of each dimension are
-i0 .. i0 + P - 1 with i0 = ceil(u - P/2), taken modulo M.  Reading C6: the
-DFT sign does not matter (G is even and rho is real); m = 0 is excluded.
+Stencil: with u = r / h, the P points of each dimension are
+i0 .. i0 + P - 1 with i0 = ceil(u - P/2), taken modulo M (an atom on a half-integer
+takes the ceiling).  The DFT sign does not matter (G is even and rho is real); m = 0 is excluded.
 
 Cells (general, triclinic): with the lattice vectors a_d as the rows of H,
 r = sum_d s_d a_d, the grid is uniform in the fractional coordinates s and
@@ -89,7 +89,7 @@ class DiscretePSWF:
     # ---- multiplier over the full spectrum --------------------------------
     def multiplier(self, p: int) -> torch.Tensor:
         """G(k_m) on the full M_x x M_y x M_z spectrum (zero at m = 0 and for
-        |k| >= k_c, where Phi-hat_p vanishes under reading C1)."""
+        |k| >= k_c, where Phi-hat_p vanishes: psi_0(x/c) taken as zero for x > c)."""
         if p in self._G:
             return self._G[p]
         ms = [np.fft.fftfreq(int(M), d=1.0 / int(M)) for M in self.M]   # signed mode numbers

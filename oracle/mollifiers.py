@@ -12,15 +12,14 @@ Every formula is written out from Methods:
 * zero-frequency term E^{0,(p)}: the p > 3 equation, Eq. (Correction) and
   Eq. (Correction3r).
 
-Readings taken where the paper is silent or inconsistent (each one is listed
-in the design notes):
+Readings taken where the paper is silent or inconsistent:
 
-* C1 -- in Eq. (PhiH) psi_0^c(x/c) is taken as zero for x > c (the PSWF lives
+* in Eq. (PhiH) psi_0^c(x/c) is taken as zero for x > c (the PSWF lives
   on [-1, 1] in the Fourier variable); so C-hat_0 = c lambda_0 C_0, every
   "int^infinity" stops at c, and Phi-hat_p(k) = 0 for k >= k_c = c / r_c.
-* C2 -- Phi-hat_1 is used exactly as printed (not re-derived from G_1).
-* C3 -- G_p(r) is its formula for r < r_c and 1 for r >= r_c.
-* C10 -- for p = 1 the zero-frequency term uses the background integral
+* Phi-hat_1 is used exactly as printed (not re-derived from G_1).
+* G_p(r) is its formula for r < r_c and 1 for r >= r_c.
+* for p = 1 the zero-frequency term uses the background integral
   int_0^{r_c} r (1 - G_1(r)) dr, i.e. the printed "r psi_0(r/r_c)" is read as
   "r G_1(r)"; E_IB = 0 (tin-foil).  The Ewald oracle decides this reading.
 """
@@ -43,12 +42,12 @@ class Mollifier:
         self.psi = psi if psi is not None else PSWF(c)
         self.lam0 = self.psi.lam0
         self.C0 = self.psi.C0
-        # C-hat_0 = int_0^inf lambda_0 psi_0(x/c) dx = c lambda_0 C_0 (reading C1)
+        # C-hat_0 = int_0^inf lambda_0 psi_0(x/c) dx = c lambda_0 C_0 (psi_0^c(x/c) taken as zero for x > c)
         self.Chat0 = self.c * self.lam0 * self.C0
         self.k_c = self.c / self.r_c
 
     # ---- the x-integrals of Eq. (PhiH) ------------------------------------
-    # With x = c s and reading C1 (psi_0^c(x/c) = 0 for x > c):
+    # With x = c s and psi_0^c(x/c) taken as zero for x > c:
     #   int_0^{k r_c} lambda_0 psi_0(x/c) dx       = c lambda_0 int_0^u psi_0
     #   int_{k r_c}^inf x^m lambda_0 psi_0(x/c) dx = c^(m+1) lambda_0 int_u^1 s^m psi_0
     #   int_{k r_c}^inf lambda_0 psi_0(x/c) / x dx = lambda_0 int_u^1 psi_0(s)/s ds
@@ -124,7 +123,7 @@ class Mollifier:
 
     # ---- real-space mollifiers (Eq. G1, G6, G) ------------------------------
     def G(self, p: int, r):
-        """G_p(r) for r < r_c; 1 for r >= r_c (reading C3).  numpy."""
+        """G_p(r) for r < r_c; 1 for r >= r_c (taken so beyond the cutoff).  numpy."""
         r = np.asarray(r, dtype=np.float64)
         x = r / self.r_c
         psi, C0 = self.psi, self.C0
@@ -187,7 +186,7 @@ class Mollifier:
         """a_p with E^{0,(p)} = a_p * Q_net^2 (so d/dq_i = 2 a_p Q_net).
 
         p > 3: Phi-hat_p(0) / (2V).  p = 2: Eq. (Correction).  p = 1:
-        Eq. (Correction) under reading C10 with E_IB = 0.  p = 3:
+        Eq. (Correction) with the background-integral reading and E_IB = 0.  p = 3:
         Eq. (Correction3r) as printed."""
         r_c = self.r_c
         if p > 3:

@@ -3,7 +3,7 @@
 Methods, "Implementation details": pairing Eq. (Fourier) with the real-space
 term (1 - G_p(r)) / r^p and subtracting E_self^(p) gives the complete
 1/r^p lattice energy, which Ewald (O3) computes independently.  Under
-reading C3 (G_p = 1 for r >= r_c) the real-space term only involves pairs
+G_p taken as 1 for r >= r_c, the real-space term only involves pairs
 closer than r_c.  Forces and potentials come from torch autograd in FP64.
 """
 from __future__ import annotations

@@ -69,7 +69,7 @@ __host__ __device__ inline void unpack_cell(uint64_t c, int& x, int& y, int& z) 
   z = int((c >> 42) & 0x1FFFFF);
 }
 
-// Stencil start (reading C5): u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2
+// Stencil start: u = x M / L, i0 = ceil(u - P/2), t = i0 + P/2
 // - u in [0, 1]; i0 wrapped into [0, M).  With u = fl + f (fl = floor(u),
 // f in [0, 1)): for even P, i0 = fl - P/2 + [f > 0] and t = [f > 0] - f; for
 // odd P = 2k + 1, i0 = fl - k + [f > 1/2] and t = [f > 1/2] + 1/2 - f.  The

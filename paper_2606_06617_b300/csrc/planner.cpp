@@ -235,7 +235,7 @@ double Prolate::integral(double a, double b, int power) const {
   return s * half;
 }
 
-// Smooth parts of Eq. (PhiH) after the substitution x = c s, reading C1
+// Smooth parts of Eq. (PhiH) after the substitution x = c s, with psi_0(x/c) taken as zero for x > c
 // (psi_0(x/c) = 0 for x > c), u = k r_c / c, with
 //   I(u) = int_0^u psi, J1(u) = int_u^1 s psi, J3(u) = int_u^1 s^3 psi,
 //   H(u) = int_u^1 (psi(s) - 1) / s ds:
@@ -305,7 +305,7 @@ const MultFit& mult_fit(const Prolate& moll, int p, double eps_poly) {
 }
 
 // Real-space mollifier G_p(x), x = r / r_c in [0, 1] (Eq. G1, G6, G of the
-// Methods; G_p = 1 beyond r_c by reading C3), with I(x) = int_0^x psi.
+// Methods; G_p taken as 1 beyond r_c), with I(x) = int_0^x psi.
 double real_mollifier(const Prolate& ps, int p, double x) {
   const double C0 = ps.C0;
   const double I = x > 0 ? ps.integral(0.0, x, 0) : 0.0;

@@ -1,6 +1,6 @@
 // Real-space complement of PSWF-LR (Methods, "Implementation
 // details": the pair term (1 - G_p(r)) / r^p that completes the reciprocal
-// sum; G_p = 1 beyond r_c by reading C3, so only pairs closer than r_c count).
+// sum; G_p taken as 1 beyond r_c, so only pairs closer than r_c count).
 //
 //   E_c   = 1/2 sum_i sum_{j != i, |r_ij| < r_c} q_i^c q_j^c f_p(r_ij)
 //   phi_i^c = sum_j q_j^c f_p(r_ij)                       (= dE_c / dq_i^c)

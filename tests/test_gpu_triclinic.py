@@ -107,7 +107,7 @@ def test_diagonal_cell_is_the_box_plan():
 def _clear_bandwidth(cell, c0, gap=1.5e-4):
     """The first c = c0 (1 + j / 4000) for which no reciprocal-lattice mode
     has |k| within a relative gap of k_c = c / R_C.  Phi-hat_p drops to zero
-    at k_c (reading C1), so the energy jumps when a strain moves a mode across
+    at k_c (psi_0 taken as zero beyond the band), so the energy jumps when a strain moves a mode across
     the band edge; the oracle's central differences (strains up to 1e-4, which
     change |k| by at most that fraction) must not straddle such a jump to
     measure the derivative.  Modes lie about 1.4e-4 apart in |k| / k_c here."""

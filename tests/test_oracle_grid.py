@@ -107,7 +107,7 @@ def test_pswf_total_matches_madelung():
 @pytest.mark.parametrize("p", [1, 2, 4, 6])
 def test_pswf_total_charged_channels(p):
     """Non-neutral channels: the zero-frequency terms (p > 3 formula,
-    Eq. Correction for p <= 2 with reading C10 for p = 1) make the PSWF total
+    Eq. Correction for p <= 2 with the background-integral reading for p = 1) make the PSWF total
     match Ewald with a neutralising background."""
     s = wl.random_system(20, (7.0, 7.0, 7.0), (p,), seed=10 + p, neutral=False)
     s.q = s.q + 0.3                                     # clearly charged

@@ -61,7 +61,7 @@ def test_small_k_limits(moll):
 
 
 def test_multiplier_vanishes_at_band_edge(moll):
-    """Reading C1: Phi-hat_p(k) = 0 for k >= k_c; p = 2..6 reach 0 continuously."""
+    """With psi_0(x/c) taken as zero for x > c: Phi-hat_p(k) = 0 for k >= k_c; p = 2..6 reach 0 continuously."""
     for p in (1, 2, 3, 4, 5, 6):
         assert abs(moll.phi_hat(p, moll.k_c * 1.001)) < 1e-12
     for p in (2, 3, 4, 5, 6):
@@ -129,7 +129,7 @@ def test_zero_frequency_p4_p6_is_phi_hat_at_zero(moll):
 
 
 def test_zero_frequency_p1_reading(moll):
-    """Reading C10: the p = 1 background term -(2 pi Q^2/V) int_0^rc r (1 - G_1) dr
+    """The p = 1 background-integral reading: the term -(2 pi Q^2/V) int_0^rc r (1 - G_1) dr
     equals Q^2/(2V) lim_{k->0} (Phi-hat_1(k) - 4 pi / k^2) to O(psi_0(1)); the
     printed 'r psi_0(r/r_c)' integrand does not (it is off by a factor ~20)."""
     V = 1000.0
