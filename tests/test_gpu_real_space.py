@@ -21,6 +21,7 @@
 * Cells with a height below 3 r_c (no cell list: the direct sum over all
   pairs and images): a box at r_c = L/2 and a small sheared cell with r_c
   above its heights, against the oracle (FP64 1e-10, FP32 2e-6).
+* Non-finite positions are reported (PSWF_ENONFINITE) in both modes.
 * Plans without PSWF_FLAG_REAL_SPACE, or direct-sum plans above 16384 atoms,
   are refused; no atoms give zero energies; a cell holding more than 2048 atoms
   is reported (PSWF_ECELL) by the next synchronising call."""
@@ -399,3 +400,22 @@ def test_real_space_direct_sum_small_cells(precision, tol):
             assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
             F += o["F"]
         assert rel_rms(f, F) <= tol, rel_rms(f, F)
+
+
+@pytest.mark.parametrize("box", [(13.0, 13.0, 13.0), (9.0, 9.0, 9.0)])   # cell list; direct sum
+def test_real_space_nonfinite_positions_reported(box):
+    """A NaN or Inf coordinate is binned at 0 and reported as
+    PSWF_ENONFINITE (-6) by the next synchronising call."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(0.0, 1.0, size=(40, 3)) * np.asarray(box)
+    pos[7, 1] = np.nan
+    pos[19, 2] = np.inf
+    q = rng.normal(size=(1, 40))
+    plan = lr.Plan(box, 40, (1,), 4.0, c=C, P=6, grid=(26, 26, 26), flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    plan.real_space(torch.tensor(pos, device=dev), torch.tensor(q, device=dev))
+    with pytest.raises(lr.PswfError) as e:
+        plan.sync()
+    assert e.value.status == -6
