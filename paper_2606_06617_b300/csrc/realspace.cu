@@ -343,15 +343,27 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 
       // every queued pair of this lane: exact displacement, f_p and f_p'
       auto drain = [&]() {
-        const int rounds = __reduce_max_sync(0xffffffffu, len);
-        for (int t = 0; t < rounds; ++t) {
-          if (t >= len) continue;
-          const uint32_t e = queue[t];
-          const int o = int(e >> kCellBits), j = nbs[o] + int(e & (kMaxCellAtoms - 1));
+        // software-pipelined: round t + 1's record is fetched while round t
+        // is evaluated (the records come from L2; their latency dominated)
+        R rn[RW];
+        int on = 0;
+        if (len > 0) {
+          const uint32_t e = queue[0];
+          on = int(e >> kCellBits);
+          load_words<R, RW>(a.rec + int64_t(nbs[on] + int(e & (kMaxCellAtoms - 1))) * RW, rn);
+        }
+        for (int t = 0; t < len; ++t) {
+          R rj[RW];
+#pragma unroll
+          for (int w = 0; w < RW; ++w) rj[w] = rn[w];
+          const int o = on;
+          if (t + 1 < len) {
+            const uint32_t e = queue[t + 1];
+            on = int(e >> kCellBits);
+            load_words<R, RW>(a.rec + int64_t(nbs[on] + int(e & (kMaxCellAtoms - 1))) * RW, rn);
+          }
           const int o3 = o / 3;
           const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
-          R rj[RW];
-          load_words<R, RW>(a.rec + int64_t(j) * RW, rj);
           L jx, jy, jz;
           coords<R>(rj, jx, jy, jz);
           R du0, du1, du2;   // displacement in list-cell units
