@@ -87,3 +87,66 @@ def test_planner_pswf_agrees_with_oracle(lr, c):
     assert info["C0"] == pytest.approx(ps.C0, rel=1e-12)
     # psi_0(1) is a cancellation of O(1) terms on both sides: absolute bound
     assert abs(info["est_err_band"] - float(ps(1.0))) < 1e-10
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "pswf_lr.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(PSWF_\w+)\s+\(?(-?\d+)\)?", src)}
+
+
+def test_binding_constants_match_header(lr):
+    """Flags, transforms, stage names and their count in the binding are the
+    header's."""
+    d = _header_defines()
+    for name in ("PSWF_FLAG_BACKWARD", "PSWF_FLAG_VIRIAL", "PSWF_FLAG_REAL_SPACE", "PSWF_TRANSFORM_FULL",
+                 "PSWF_TRANSFORM_PRUNED", "PSWF_TRANSFORM_PRUNED_X", "PSWF_TRANSFORM_OWN"):
+        assert getattr(lr, name) == d[name], name
+    assert lr.NSTAGE == d["PSWF_NSTAGE"] == len(lr.STAGES)
+    for i, stage in enumerate(lr.STAGES):
+        assert d["PSWF_STAGE_" + stage.upper()] == i, stage
+
+
+def test_info_struct_layout_matches_header(lr, tmp_path):
+    """sizeof(pswf_info) and the offsets of its last fields, from a C program
+    compiled against the header, equal the ctypes structure's."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    c = tmp_path / "layout.c"
+    c.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "pswf_lr.h"\n'
+                 'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(pswf_info), offsetof(pswf_info, cell), '
+                 'offsetof(pswf_info, deg_real), offsetof(pswf_info, nkx)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    size, off_cell, off_deg, off_nkx = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                check=True).stdout.split())
+    assert ctypes.sizeof(lr.PswfInfo) == size
+    assert lr.PswfInfo.cell.offset == off_cell
+    assert lr.PswfInfo.deg_real.offset == off_deg
+    assert lr.PswfInfo.nkx.offset == off_nkx
+
+
+def test_status_strings(lr):
+    L = lr.lib()
+    d = _header_defines()
+    import ctypes
+    L.pswf_strerror.restype = ctypes.c_char_p
+    assert b"2048" in L.pswf_strerror(d["PSWF_ECELL"])
+    for name in ("PSWF_EINVAL", "PSWF_ESTATE", "PSWF_ENONFINITE"):
+        assert L.pswf_strerror(d[name])
+
+
+def test_source_digest_ignores_comments():
+    """The digest that keys committed traffic records to a kernel's code does
+    not change with comments or whitespace, and does change with code."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) {\n  return x + 1;  // one\n}\n"
+    b = "/* header */\nint f(int x) {\n    return x + 1;\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
