@@ -222,6 +222,8 @@ int pswf_self_energy(pswf_plan plan, double* out);
  *           coefficients); its workspace, stream and points are not used;
  *   n, q:   device real [K][n] latent charges (plan precision), n <= n_max;
  *   out:    device double [K]: E_self^(p) per channel (caller-owned);
+ *           q and out live on the plan's device, which must be the current
+ *           device at the call (PSWF_EINVAL otherwise);
  *   stream: cudaStream_t the work is enqueued on (asynchronous).
  * Allocates nothing: the FP64 partial sums live in a 152,576-byte array of
  * static device memory inside this library, which every GPU that loads the

@@ -14,7 +14,14 @@ E = 1/2 sum_n sum_ij' q_i q_j / |r_ij + n L|^p (Eq. realLR with G_p = 1):
 * k = 0 term:       p > 3: pi^{3/2} 2 alpha^{p-3} / ((p-3) Gamma(p/2)) Q^2/(2V);
                     p = 1: -pi Q^2 / (2 V alpha^2) (neutralising background);
                     p = 2: -pi^{3/2} Q^2 / (alpha V) (same);
-                    p = 3: only neutral systems are accepted.
+                    p = 3: the finite part of phi-hat at k -> 0 times
+                    Q^2/(2V): phi-hat = 2 pi E_1(k^2/(4 alpha^2)) =
+                    -4 pi log k + 2 pi (log(4 alpha^2) - gamma) + O(k^2),
+                    so pi (log(4 alpha^2) - gamma) Q^2 / V (gamma: Euler's
+                    constant).  The charged p = 3 sum diverges like log R
+                    without a convention; taking the finite part of the
+                    kernel transform for the k = 0 term gives the same total
+                    for every splitting parameter (tests pin this).
 
 Gamma(s, x) for s <= 0 comes from Gamma(s+1, x) = s Gamma(s, x) + x^s e^{-x}
 started at Gamma(1/2, x) = sqrt(pi) erfc(sqrt(x)), Gamma(1, x) = e^{-x} or
@@ -130,9 +137,7 @@ def ewald(pos, q, box, p: int, alpha: float | None = None, r_cut: float | None =
     elif p == 2:
         a0 = -math.pi ** 1.5 / (alpha * V)
     else:
-        if abs(Q) > 1e-12:
-            raise ValueError("p = 3 Ewald oracle needs a neutral channel")
-        a0 = 0.0
+        a0 = math.pi * (math.log(4.0 * alpha ** 2) - np.euler_gamma) / V
     E0 = a0 * Q * Q
     phi_tot = phi + phi_r - sc * q + 2 * a0 * Q
     E = E_real + E_recip - E_self + E0

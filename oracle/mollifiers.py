@@ -187,7 +187,9 @@ class Mollifier:
 
         p > 3: Phi-hat_p(0) / (2V).  p = 2: Eq. (Correction).  p = 1:
         Eq. (Correction) with the background-integral reading and E_IB = 0.  p = 3:
-        Eq. (Correction3r) as printed."""
+        Eq. (Correction3r) as printed; it equals Q^2/(2V) times the finite part
+        lim_{k->0} (Phi-hat_3(k) + 4 pi log k), the k = 0 convention that makes
+        the charged p = 3 total independent of the splitting."""
         r_c = self.r_c
         if p > 3:
             return float(self.phi_hat(p, 0.0)) / (2.0 * V)

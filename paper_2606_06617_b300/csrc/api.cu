@@ -1239,6 +1239,9 @@ int noalloc_scratch(pswf_plan p, double** out) {
   int dev = 0;
   int rc = cuda_check(p, cudaGetDevice(&dev), "cudaGetDevice");
   if (rc) return rc;
+  if (dev != p->device)
+    return set_err(p, PSWF_EINVAL,
+                   "pswf_self_energy_noalloc: the current device is not the plan's device (make it current)");
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return set_err(p, PSWF_EINVAL, "pswf_self_energy_noalloc: device ordinal beyond 63");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);

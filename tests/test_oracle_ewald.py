@@ -22,7 +22,7 @@ def test_nacl_madelung():
     assert np.max(np.abs(e["F"])) < 1e-10
 
 
-@pytest.mark.parametrize("p,neutral", [(1, True), (1, False), (2, True), (2, False), (3, True),
+@pytest.mark.parametrize("p,neutral", [(1, True), (1, False), (2, True), (2, False), (3, True), (3, False),
                                        (4, False), (5, False), (6, True), (6, False)])
 def test_alpha_independence(p, neutral):
     s = wl.random_system(12, (6.0, 7.0, 6.5), (p,), seed=p, neutral=neutral)

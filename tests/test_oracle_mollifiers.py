@@ -139,3 +139,31 @@ def test_zero_frequency_p1_reading(moll):
     assert abs(a1 / lim - 1) < 1e-3
     printed = -2 * math.pi / V * (RC ** 2 / 2 - RC ** 2 * moll.psi.integral(0.0, 1.0, 1))
     assert abs(printed / a1) > 5
+
+
+def test_zero_frequency_p3_is_finite_part_at_zero(moll):
+    """Eq. (Correction3r): the p = 3 term a_3 Q^2 is Q^2/(2V) times the finite
+    part of Phi-hat_3 at k -> 0, i.e. lim (Phi-hat_3(k) + 4 pi log k).  The
+    limit is taken on the closed-form multiplier (moments of psi_0) at two
+    small k, the coefficient by the quadrature of the printed tail integral;
+    a flipped log or tail sign moves it by O(1)."""
+    V = 1000.0
+    a3 = moll.zero_freq_coef(3, V)
+    for k in (1e-5, 1e-6):
+        lim = (moll.phi_hat(3, k) + 4 * math.pi * math.log(k)) / (2 * V)
+        assert abs(a3 - lim) < 1e-8 * abs(a3) + 1e-12, (k, a3, lim)
+
+
+def test_zero_frequency_p5_is_phi_hat_at_zero(moll):
+    """p = 5: a_5 = Phi-hat_5(0) / (2V), and Phi-hat_5(0) = 4 pi int_0^inf
+    G_5(r) r^-3 dr (direct radial integral, up to the band truncation)."""
+    V = 1000.0
+    assert moll.zero_freq_coef(5, V) == pytest.approx(moll.phi_hat(5, 0.0) / (2 * V), rel=1e-14)
+    # below r0, the leading Taylor term of G_5 (G_5 ~ b x^5, b from the r -> 0
+    # series of the self-energy: s_5 = b / (2 r_c^5))
+    r0 = 0.3
+    r, w = gauss_legendre(r0, RC, 400)
+    b = 2 * moll.self_coef(5) * RC ** 5
+    small = b / RC ** 5 * r0 ** 3 / 3
+    ref = 4 * math.pi * (float(np.dot(w, moll.G(5, r) * r ** -3)) + small + RC ** -2 / 2)
+    assert abs(moll.phi_hat(5, 0.0) / ref - 1) < 1e-3
