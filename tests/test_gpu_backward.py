@@ -3,9 +3,11 @@ the oracle's vector-jacobian product of the same discrete forward.
 
 The loss is L = sum_c gE_c E_c + sum gphi * phi + sum gF * F with seeded
 upstream gradients; both sides use the same explicit parameters.  The FP64
-path must agree to 1e-8 relative RMS; the FP32 path to 2e-5 (the force term
-involves the second derivative of the window, whose FP32 table error is
-amplified by (2/h)^2)."""
+path must agree to 1e-8 relative RMS; the FP32 path to 4e-6, twice the
+largest error measured on a B300 over these cases and the training batch
+(grad_pos 1.3e-6 at P = 4, 1.9e-6 in the training shape; grad_q <= 5.1e-7):
+the force term involves the second derivative of the window, whose FP32
+table error is amplified by (2/h)^2."""
 import math
 
 import numpy as np
@@ -19,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 C_TOL = math.log(3.0 / 1e-5)
 TOL_BW_FP64 = 1e-8
-TOL_BW_FP32 = 2e-5
+TOL_BW_FP32 = 4e-6
 
 
 def _oracle(s, r_c, P, M, c, cw):
@@ -60,6 +62,8 @@ def _check(s, r_c, P, M, c, precision, tol, parts=("E", "phi", "F"), what="", to
     up = _upstream(s, parts=parts)
     gq, gr, _, _ = _gpu_backward(s, r_c, P, M, c, cw, precision, up)
     oq, orr = _oracle(s, r_c, P, M, c, cw).vjp(s.pos, s.q, *up)
+    print(f"backward {what} precision={precision}: grad_q {rel_rms(gq, oq.numpy()):.3e} "
+          f"grad_pos {rel_rms(gr, orr.numpy()):.3e}")
     assert rel_rms(gq, oq.numpy()) <= tol, (what, "grad_q", rel_rms(gq, oq.numpy()))
     tol_pos = tol if tol_pos is None else tol_pos
     assert rel_rms(gr, orr.numpy()) <= tol_pos, (what, "grad_pos", rel_rms(gr, orr.numpy()))

@@ -159,6 +159,75 @@ def test_full_size_melt_sampled_atoms(precision, tol):
     assert abs(e.cpu().numpy()[-1] - e.cpu().numpy()[:-1].sum()) <= 1e-12 * np.abs(e.cpu().numpy()[:-1]).sum()
 
 
+def _close_pair_bounds(idx, pos, q, box, p, r_c, moll, rel, dx):
+    """Per-atom error bounds of the FP32 path for atoms with close
+    neighbours: each pair term (|q_j f_p(r)| for phi, |q_i q_j f_p'(r)| for
+    the force components) carries a relative error rel (rounding) plus the
+    one of the fixed-point displacement, dx = 1.3e-8 A: (p + 1) dx / r for
+    f_p ~ r^-p and (p + 2) dx / r for its derivative."""
+    b_phi = np.zeros(len(idx))
+    b_f = np.zeros(len(idx))
+    for k, i in enumerate(idx):
+        d = pos - pos[i]
+        d -= box * np.round(d / box)
+        r2 = np.einsum("nd,nd->n", d, d)
+        nb = np.nonzero((r2 < r_c * r_c) & (r2 > 0.0))[0]
+        r = np.sqrt(r2[nb])
+        f = (1.0 - moll.G(p, r)) / r ** p
+        h = 1e-6 * r
+        fp = ((1.0 - moll.G(p, r + h)) / (r + h) ** p - (1.0 - moll.G(p, r - h)) / (r - h) ** p) / (2 * h)
+        b_phi[k] = np.sum(np.abs(q[nb] * f) * (rel + (p + 1) * dx / r))
+        b_f[k] = np.sum(np.abs(q[i] * q[nb] * fp) * (rel + (p + 2) * dx / r))
+    return b_phi, b_f
+
+
+@pytest.mark.slow
+def test_full_size_melt_close_pairs():
+    """Atoms of the full-size melt with a neighbour closer than 0.1 A (the
+    ones the sampled test leaves out in FP32), element by element against the
+    oracle within their own bounds: relative rounding 2e-6 on every pair term
+    plus the fixed-point displacement's p 1.3e-8 A / r (section on the
+    real-space records).  The closest pairs of 4.2M uniform atoms are ~0.01 A
+    apart, where 1/r^6 terms dominate the potential."""
+    import torch
+    from scipy.spatial import cKDTree
+    from oracle.mollifiers import Mollifier
+    from oracle.realspace import real_space_atoms
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.ionic_melt(4194304, 350.0, seed=0)
+    box = np.asarray(s.box)
+    r_c = 7.0
+    c = math.log(3.0 / 1e-5)
+    plan = lr.Plan(s.box, s.n, s.ps, r_c, tol=1e-5, P=7, grid=384, precision=0,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, phi, f = plan.real_space(torch.tensor(s.pos, device=dev), torch.tensor(s.q, device=dev))
+    plan.sync()
+    phi, f = phi.cpu().double().numpy(), f.cpu().double().numpy()
+    wrapped = s.pos - box * np.floor(s.pos / box)
+    pairs = cKDTree(wrapped, boxsize=box).query_pairs(0.1, output_type="ndarray")
+    assert len(pairs) > 100
+    close = np.unique(pairs.ravel())
+    order = np.argsort(np.linalg.norm(np.diff(wrapped[pairs], axis=1)[:, 0] -
+                                      box * np.round(np.diff(wrapped[pairs], axis=1)[:, 0] / box), axis=1))
+    # the 8 closest pairs' atoms and 24 more drawn at random among the close ones
+    rng = np.random.default_rng(23)
+    idx = list(dict.fromkeys([int(a) for a in pairs[order[:8]].ravel()] +
+                             [int(a) for a in rng.choice(close, 24, replace=False)]))
+    moll = Mollifier(c, r_c)
+    F = np.zeros((len(idx), 3))
+    bF = np.zeros(len(idx))
+    for ch, p in enumerate(s.ps):
+        o_phi, o_F = real_space_atoms(idx, s.pos, s.q[ch], box, p, c, r_c, moll)
+        b_phi, b_f = _close_pair_bounds(idx, wrapped, s.q[ch], box, p, r_c, moll, 2e-6, 1.3e-8)
+        err = np.abs(phi[ch, idx] - o_phi)
+        assert np.all(err <= b_phi), (ch, p, np.max(err / b_phi))
+        F += o_F
+        bF += b_f
+    err = np.max(np.abs(f[idx] - F), axis=1)
+    assert np.all(err <= bF), np.max(err / bF)
+
+
 def _gpu_total(s, M, P, r_c, tol, precision):
     """E_c and F of reciprocal part + real-space part - self energy, all on
     the GPU."""

@@ -2,7 +2,8 @@
 channels with exponents alternating 1, 6) through one batch plan, forward
 and hand-written backward.  Per structure, the gradients of a loss touching
 energies, potentials and forces must match the oracle's VJP of that
-structure alone on the plan's grid with the plan's c_w and P (FP32: 2e-5)."""
+structure alone on the plan's grid with the plan's c_w and P (FP32: 4e-6,
+twice the largest measured error, 1.9e-6 on grad_pos)."""
 import math
 
 import numpy as np
@@ -49,5 +50,7 @@ def test_training_batch_backward_matches_oracle():
         sl = slice(off[i], off[i + 1])
         o = DiscretePSWF(GridConfig(s.box, (M, M, M), info["P"], info["c"], R_C, s.ps, c_w=info["c_w"]))
         oq, orr = o.vjp(s.pos, s.q, gE[i], gphi[:, sl], gF[sl])
-        assert rel_rms(gq[:, sl], oq.numpy()) < 2e-5, (i, rel_rms(gq[:, sl], oq.numpy()))
-        assert rel_rms(gr[sl], orr.numpy()) < 2e-5, (i, rel_rms(gr[sl], orr.numpy()))
+        print(f"training structure {i}: grad_q {rel_rms(gq[:, sl], oq.numpy()):.3e} "
+              f"grad_pos {rel_rms(gr[sl], orr.numpy()):.3e}")
+        assert rel_rms(gq[:, sl], oq.numpy()) < 4e-6, (i, rel_rms(gq[:, sl], oq.numpy()))
+        assert rel_rms(gr[sl], orr.numpy()) < 4e-6, (i, rel_rms(gr[sl], orr.numpy()))
