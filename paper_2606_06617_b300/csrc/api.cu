@@ -147,6 +147,30 @@ __global__ void k_set_count(int* __restrict__ soff, int n) {
   }
 }
 
+__global__ void k_tile_scale(int ntl, int K, int64_t nmax, const int* __restrict__ tile_start,
+                             const float* __restrict__ sq, float* __restrict__ tscale) {
+  const int lane = threadIdx.x & 31;
+  const int nw = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+  for (int t = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < ntl; t += nw) {
+    const int a0 = tile_start[t], a1 = tile_start[t + 1];
+    for (int c = 0; c < K; ++c) {
+      float s1 = 0.0f, mq = 0.0f;
+      for (int a = a0 + lane; a < a1; a += 32) {
+        const float v = fabsf(sq[int64_t(c) * nmax + a]);
+        s1 += v;
+        mq = fmaxf(mq, v);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+      }
+      if (lane == 0)
+        tscale[int64_t(t) * K + c] =
+            s1 > 0.0f ? fminf(0.99f * 4194304.0f / mq, 0.999f * 2147483647.0f / (s1 * 1.0001f)) : 1.0f;
+    }
+  }
+}
+
 __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
                                    double* __restrict__ charges) {
   // one warp per (structure, channel): lanes stride over the block partials
@@ -311,6 +335,7 @@ struct pswf_plan_s {
   int* rank = nullptr;       // [n_max]
   int* tile_count = nullptr; // [ntiles]
   int* tile_start = nullptr; // [ntiles + 1]
+  float* tscale = nullptr;   // [ntiles][K] fixed-point unit of the FP32 four-channel spread (P <= 8)
   int* scan_sums = nullptr;  // [scan_blocks]
   double* qpart = nullptr;   // [B][nqb][K][2]
   double* charges = nullptr; // [B K][2]: Q_net, Q_self
@@ -494,6 +519,7 @@ int64_t layout(pswf_plan p, char* base) {
   p->rank = reinterpret_cast<int*>(take(nm * 4));
   p->tile_count = reinterpret_cast<int*>(take(int64_t(p->ntiles) * 4));
   p->tile_start = reinterpret_cast<int*>(take(int64_t(p->ntiles + 1) * 4));
+  p->tscale = (p->real_size == 4 && h.P <= 8) ? reinterpret_cast<float*>(take(int64_t(p->ntiles) * K * 4)) : nullptr;
   p->scan_sums = reinterpret_cast<int*>(take(int64_t(p->scan_blocks) * 4));
   p->qpart = reinterpret_cast<double*>(take(B * p->nqb * K * 2 * 8));
   p->charges = reinterpret_cast<double*>(take(BK * 2 * 8));
@@ -706,6 +732,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.smol = p->smol;
   c.soff = p->soff;
   c.tile_start = p->tile_start;
+  c.tscale = p->tscale;
   c.st = p->st;
   c.scell = p->scell;
   c.sq = p->sq;
@@ -921,6 +948,13 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
                                            p->tile_start, static_cast<const R*>(p->tmp_t), p->tmp_cell,
                                            static_cast<R*>(p->st), p->scell, static_cast<R*>(p->sq), p->sperm);
   if ((rc = launch_check(p, "k_scatter"))) return rc;
+  if (p->tscale && ntl > 0) {
+    const int tb = int(std::min<int64_t>((int64_t(ntl) * 32 + kThreads - 1) / kThreads, 148 * 64));
+    k_tile_scale<<<tb, kThreads, 0, s>>>(ntl, p->host.K, p->n_max, p->tile_start,
+                                          static_cast<const float*>(p->sq), p->tscale);
+    if ((rc = launch_check(p, "k_tile_scale"))) return rc;
+    ++p->launches[PSWF_STAGE_SET_POINTS];
+  }
   return charge_sums<R>(p, q, p->charges);
 }
 

@@ -275,6 +275,16 @@ __global__ void k_scatter(int64_t nmax, const R* __restrict__ q, Geometry g, con
   }
 }
 
+// Fixed-point unit of the FP32 four-channel spread per (tile, channel): with
+// S1 = sum |q| and Mq = max |q| over the tile's atoms, s = min(0.99 2^22 /
+// Mq, 0.999 2^31 / (1.0001 S1)) keeps each rounded contribution below 2^22
+// and every grid sum of the tile below 2^31 (the window is at most 1; the
+// 1.0001 and 0.999 factors cover the rounding of the float sum, whose
+// relative error is below (n / 32 + 5) 2^-24 for n atoms); 1 for a channel
+// of zeros.  One warp per tile, lanes strided over its atoms.
+__global__ void k_tile_scale(int ntl, int K, int64_t nmax, const int* __restrict__ tile_start,
+                             const float* __restrict__ sq, float* __restrict__ tscale);
+
 // The single-structure set_points writes its atom count here (soff = {0, n}).
 __global__ void k_set_count(int* __restrict__ soff, int n);
 

@@ -5,6 +5,7 @@
 
 #include "launch.cuh"
 #include "stencil.cuh"
+#include "stencil4.cuh"
 #include "backward.cuh"
 
 #ifndef PSWF_REAL
@@ -27,13 +28,14 @@ constexpr int kStencilCtas = 1;
 constexpr int kGatherThreads = kGatherThreadsFor<R>;
 constexpr int kDirectThreads = 256;
 
-static WinCoef<R> win_coef(const LaunchCtx& c) {
-  constexpr int D = WinCoef<R>::kDeg;
-  WinCoef<R> w;
+template <typename T = R>
+static WinCoef<T> win_coef(const LaunchCtx& c) {
+  constexpr int D = WinCoef<T>::kDeg;
+  WinCoef<T> w;
   std::memset(&w, 0, sizeof(w));
   w.deg = c.deg_w;
   for (int j = 0; j < c.geo.P; ++j)
-    for (int n = 0; n <= c.deg_w && n <= D; ++n) w.c[j * (D + 1) + n] = R(c.coef_w[j * (c.deg_w + 1) + n]);
+    for (int n = 0; n <= c.deg_w && n <= D; ++n) w.c[j * (D + 1) + n] = T(c.coef_w[j * (c.deg_w + 1) + n]);
   return w;
 }
 
@@ -66,18 +68,63 @@ bool pick_kc_kb(Kern kern, int K, F bytes, int* kc_out, int* kb_out) {
 }
 
 template <int P, typename Kern>
-cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks) {
+cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks,
+                              int threads = kGatherThreads / kStencilCtas) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGatherThreads / kStencilCtas, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
   *blocks = int(std::min<int64_t>(items, int64_t(sm_count()) * std::max(per_sm, 1)));
   return cudaSuccess;
 }
 
+// Threads of the FP32 four-channel stencil kernels (one CTA per SM).
+constexpr int kSpread4Threads = 1024;
+constexpr int kGather4Threads = 512;
+
+// FP32 kernels for P <= 8: four channels per work item, windows evaluated in
+// the lanes (stencil4.cuh).
+template <int P>
+cudaError_t spread4_P(const LaunchCtx& c, int* nlaunch) {
+  const WinCoef<float> wc = win_coef<float>(c);
+  const size_t smem = spread4_smem_bytes<P>();
+  const int nchunk = (c.geo.K + 3) / 4;
+  int blocks = 0;
+  cudaError_t e = persistent_blocks<P>(k_spread4<P, kSpread4Threads>, smem, int64_t(c.ntiles) * nchunk, &blocks,
+                                       kSpread4Threads);
+  if (e != cudaSuccess) return e;
+  k_spread4<P, kSpread4Threads><<<blocks, kSpread4Threads, smem, c.stream>>>(
+      c.geo, c.nmax, c.tile_start, static_cast<const float*>(c.st), c.scell, static_cast<const float*>(c.sq),
+      c.tscale, wc, static_cast<float*>(c.grid));
+  ++*nlaunch;
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t interp4_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
+  const WinCoef<float> wc = win_coef<float>(c);
+  const int nchunk = (c.geo.K + 3) / 4;
+  cudaError_t e;
+  if (nchunk > 1 && forces) {
+    e = cudaMemsetAsync(forces, 0, size_t(c.n) * 3 * sizeof(float), c.stream);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = gather4_smem_bytes<P>();
+  int blocks = 0;
+  e = persistent_blocks<P>(k_gather4<P, kGather4Threads>, smem, int64_t(c.ntiles) * nchunk, &blocks, kGather4Threads);
+  if (e != cudaSuccess) return e;
+  k_gather4<P, kGather4Threads><<<blocks, kGather4Threads, smem, c.stream>>>(
+      c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const float*>(c.st), c.scell,
+      static_cast<const float*>(c.sq), c.sperm, wc, static_cast<const float*>(c.grid), c.zero_coef, c.charges,
+      static_cast<float*>(phi), static_cast<float*>(forces));
+  ++*nlaunch;
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
+  if constexpr (sizeof(R) == 4 && P <= 8) return spread4_P<P>(c, nlaunch);
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
   if (!pick_kc_kb<P>(k_spread<R, P, kStencilCtas>, c.geo.K, [](int k, int b) { return spread_smem_bytes<R, P>(k, b); }, &kc, &kb)) {
@@ -103,6 +150,7 @@ cudaError_t spread_P(const LaunchCtx& c, int* nlaunch) {
 template <int P>
 cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
+  if constexpr (sizeof(R) == 4 && P <= 8) return interp4_P<P>(c, phi, forces, nlaunch);
   const WinCoef<R> wc = win_coef(c);
   int kc = 0, kb = 0;
   if (!pick_kc_kb<P>(k_interp<R, P, kStencilCtas>, c.geo.K,

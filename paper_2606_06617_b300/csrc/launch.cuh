@@ -19,6 +19,7 @@ struct LaunchCtx {
   const double* smol = nullptr;     // [B][3] M_d / L_d
   const int* soff = nullptr;        // [B + 1] atom offsets per structure (device)
   const int* tile_start = nullptr;
+  const float* tscale = nullptr;    // [B nts][K] fixed-point units of the FP32 four-channel spread
   const void* st = nullptr;         // real [3][nmax]
   const uint64_t* scell = nullptr;  // [nmax]
   const void* sq = nullptr;         // real [K][nmax]

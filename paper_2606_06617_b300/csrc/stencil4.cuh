@@ -1,0 +1,482 @@
+// FP32 stencil kernels for stencils of up to 8 points per dimension:
+// spreading of the latent charges (step (i) of "Accelerating atom-grid
+// spreading with PSWFs") and the gather of potentials and forces, with up to
+// four channels per work item.
+//
+// Both work on one tile of kTile^3 stencil-start cells at a time; the tile's
+// atoms are contiguous in the sorted arrays and its padded region, S^3 grid
+// points with S = kTile + P - 1, is the union of their stencils.  Per atom
+// the window pieces are evaluated by the lanes that use them (piece j by
+// lane j of an 8-lane group, one Horner chain per lane, coefficients held in
+// registers) and passed around the group by shuffles, so no per-batch window
+// tables, batch barriers or table shared memory are needed.
+//
+// Gather: the region holds Psi of four channels interleaved (one float4 per
+// grid point, row stride R1 odd).  An 8-lane group handles one atom (four
+// atoms per warp); lane j sweeps row j of the stencil (its P planes and P
+// points), so one 16-byte shared load feeds the eight products (value and
+// x-derivative window) of the four channels.  The eight lanes of a group hit
+// eight distinct 16-byte bank groups (j R1 mod 8), so each quarter-warp load
+// is one wavefront.  Seven sums per lane (four potentials and the three
+// force components) are reduced over the group by a transposing butterfly.
+//
+// Spread: the region holds one 32-bit fixed-point accumulator per grid point
+// and channel (channel planes, layout SPad); a warp takes one atom, its
+// lanes being four channels x eight stencil rows, so every shared atomic of
+// the warp hits 32 distinct banks.  The region is then added into the grid
+// with global atomics.
+//
+// Tiles are visited in blocked order (z-columns of tiles in x-strips of
+// four), so that neighbouring tiles, whose padded regions overlap, run close
+// together in time and their shared halo lines are reused from L2.
+#pragma once
+
+#include "stencil.cuh"
+
+namespace pswf {
+
+constexpr int kStrip = 4;   // x-width, in tiles, of the strips of the visiting order
+
+// Tile of the t-th visit (t in [0, B nts)): structure-major; within a
+// structure, z-columns of tiles, column after column along y within an
+// x-strip of kStrip tiles, strip after strip.
+__device__ inline int tile_for_visit(const Geometry& g, int t) {
+  const int s = t / g.nts;
+  int r = t - s * g.nts;
+  const int ntx = g.ntile[0], nty = g.ntile[1], ntz = g.ntile[2];
+  const int tz = r % ntz;
+  r /= ntz;
+  const int strip = r / (kStrip * nty);
+  const int rem = r - strip * kStrip * nty;
+  const int sw = min(kStrip, ntx - strip * kStrip);
+  const int ty = rem / sw;
+  const int tx = strip * kStrip + (rem - ty * sw);
+  return s * g.nts + (tz * nty + ty) * ntx + tx;
+}
+
+// Window piece j of the lane (zero for j >= P): monomial coefficients in
+// s = 2t - 1, read once per thread.
+template <int P>
+struct LanePiece {
+  static constexpr int D = WinCoef<float>::kDeg;
+  float c[D + 1];
+  __device__ void load(const WinCoef<float>& wc, int j) {
+#pragma unroll
+    for (int n = 0; n <= D; ++n) c[n] = j < P ? wc.c[j * (D + 1) + n] : 0.0f;
+  }
+  __device__ float value(float t) const {
+    const float s = 2.0f * t - 1.0f;
+    float v = c[D];
+#pragma unroll
+    for (int n = D - 1; n >= 0; --n) v = fmaf(v, s, c[n]);
+    return v;
+  }
+  // value and dW/ds
+  __device__ void value_deriv(float t, float& v, float& dv) const {
+    const float s = 2.0f * t - 1.0f;
+    v = c[D];
+    dv = 0.0f;
+#pragma unroll
+    for (int n = D - 1; n >= 0; --n) {
+      dv = fmaf(dv, s, v);
+      v = fmaf(v, s, c[n]);
+    }
+  }
+};
+
+template <int P>
+struct Pad4 {
+  static constexpr int S = kTile + P - 1;
+  static constexpr int R1 = S | 1;        // odd row stride (in float4)
+  static constexpr int R2 = S * R1;       // plane stride
+  static constexpr int ELEMS = S * R2;    // float4 elements of the region
+};
+
+template <int P>
+constexpr size_t gather4_smem_bytes() {
+  return size_t(Pad4<P>::ELEMS) * 16;
+}
+
+// ---- gather -------------------------------------------------------------------
+// phi_c = sum Psi_c W + 2 a_c Q_c, F = sum_c q_c sum Psi_c grad W (grad_d W =
+// (2 / h_d) dW/ds).  Work items are (tile, chunk of four channels); with
+// more than one chunk the forces are accumulated with global atomics (the
+// caller zeroes them).
+//
+// Staging: a job is an x-pair of one region row; its four channels' pairs
+// are read as 8-byte loads (grid rows start at even offsets and tile origins
+// are even, so a pair that does not straddle the periodic wrap is aligned)
+// and written as two float4 (x, then x + 1), several jobs' loads in flight
+// per thread.  Atom inputs of the next group of four atoms are loaded while
+// the current group is evaluated.  Window coefficients sit in shared memory
+// as [n][j], so the eight lanes of a group read eight banks and the four
+// groups of a warp share them.
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, const double* __restrict__ smol,
+                                                   const int* __restrict__ soff, const int* __restrict__ tile_start,
+                                                   const float* __restrict__ st, const uint64_t* __restrict__ scell,
+                                                   const float* __restrict__ sq, const int* __restrict__ sperm,
+                                                   const __grid_constant__ WinCoef<float> wc,
+                                                   const float* __restrict__ grid,
+                                                   const double* __restrict__ zero_coef,
+                                                   const double* __restrict__ charges, float* __restrict__ phi,
+                                                   float* __restrict__ forces) {
+  static_assert(P <= 8, "one 8-lane group per atom");
+  using L = Pad4<P>;
+  constexpr int S = L::S, R1 = L::R1, R2 = L::R2;
+  constexpr int NW = NT / 32;
+  constexpr int D = WinCoef<float>::kDeg;
+  constexpr int NPAIR = (S + 1) / 2;     // x-pairs per region row
+  constexpr int NJOB = S * S * NPAIR;    // staging jobs per item
+  constexpr int U = 2;                   // staging jobs in flight per thread
+  extern __shared__ __align__(16) float4 reg4[];   // [S][S][R1] x 4 channels
+  __shared__ float cf_s[D + 1][8];                 // window coefficients [monomial][piece]
+  __shared__ float item_s[8];                      // 2 / h_d (3), zero-frequency shifts (4)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane & 7, grp = lane >> 3, gbase = lane & ~7;
+  const int jr = j < P ? j : P - 1;
+  for (int t = threadIdx.x; t < (D + 1) * 8; t += NT) {
+    const int n = t >> 3, pj = t & 7;
+    cf_s[n][pj] = pj < P ? wc.c[pj * (D + 1) + n] : 0.0f;
+  }
+  const int nchunk = (g.K + 3) / 4;
+  const int64_t n = soff[g.B];
+  const int nitems = g.B * g.nts * nchunk;
+  const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
+  const bool xeven = (g.M[0] & 1) == 0;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int visit = item / nchunk, chunk = item - visit * nchunk;
+    const int tile = tile_for_visit(g, visit);
+    const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
+    if (a0 == a1) continue;
+    const int sidx = tile / g.nts;
+    const int c0 = chunk * 4, nk = min(4, g.K - c0);
+    const int gc0 = sidx * g.K + c0;
+    int ox, oy, oz;
+    tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
+    __syncthreads();   // the previous item's reads of the region and item_s are done
+    if (threadIdx.x < 3) {
+      item_s[threadIdx.x] = float(2.0 * smol[3 * sidx + threadIdx.x]);
+    } else if (threadIdx.x < 7) {
+      const int c = threadIdx.x - 3;
+      item_s[threadIdx.x] = c < nk ? float(2.0 * zero_coef[gc0 + c] * charges[2 * (gc0 + c)]) : 0.0f;
+    }
+    {
+      const float* gch = grid + int64_t(gc0) * chan;
+      for (int e0 = threadIdx.x; e0 < NJOB; e0 += U * NT) {
+        float2 pr[U][4];
+        int dsti[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * NT;
+          dsti[u] = -1;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pr[u][c] = make_float2(0.0f, 0.0f);
+          if (e < NJOB) {
+            const int row = e / NPAIR, x = 2 * (e - row * NPAIR);
+            const int lz = row / S, ly = row - lz * S;
+            dsti[u] = row * R1 + x;
+            const int gx = wrap_index(ox + x, g.M[0]);
+            const int64_t off = wrap_index(oz + lz, g.M[2]) * plane + int64_t(wrap_index(oy + ly, g.M[1])) * g.Mxp;
+            if (xeven && gx + 1 < g.M[0]) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (c < nk) pr[u][c] = __ldg(reinterpret_cast<const float2*>(gch + c * chan + off + gx));
+            } else {
+              const int gx1 = wrap_index(gx + 1, g.M[0]);
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (c < nk) pr[u][c] = make_float2(__ldg(gch + c * chan + off + gx), __ldg(gch + c * chan + off + gx1));
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (dsti[u] < 0) continue;
+          reg4[dsti[u]] = make_float4(pr[u][0].x, pr[u][1].x, pr[u][2].x, pr[u][3].x);
+          if ((dsti[u] % R1) + 1 < S) reg4[dsti[u] + 1] = make_float4(pr[u][0].y, pr[u][1].y, pr[u][2].y, pr[u][3].y);
+        }
+      }
+    }
+    __syncthreads();
+    const float th0 = item_s[0], th1 = item_s[1], th2 = item_s[2];
+    const float zshift = j < 4 ? item_s[3 + j] : 0.0f;
+    // group loop: four atoms per warp, the next group's inputs loaded ahead
+    int ab = a0 + 4 * warp;
+    float tnx = 0.0f, tny = 0.0f, tnz = 0.0f;
+    uint64_t celln = 0;
+    if (ab < a1) {
+      const int a = min(ab + grp, a1 - 1);
+      tnx = st[a];
+      tny = st[nmax + a];
+      tnz = st[2 * nmax + a];
+      celln = scell[a];
+    }
+    for (; ab < a1; ab += 4 * NW) {
+      const int a_raw = ab + grp;
+      const bool valid = a_raw < a1;
+      const int a = valid ? a_raw : a1 - 1;
+      const float tx = tnx, ty = tny, tz = tnz;
+      const uint64_t cell = celln;
+      if (ab + 4 * NW < a1) {
+        const int an = min(ab + 4 * NW + grp, a1 - 1);
+        tnx = st[an];
+        tny = st[nmax + an];
+        tnz = st[2 * nmax + an];
+        celln = scell[an];
+      }
+      float q[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q[c] = (valid && c < nk) ? sq[int64_t(c0 + c) * nmax + a] : 0.0f;
+      const int o = sperm[a];
+      // window piece j in x, y, z: values and dW/ds (Horner, coefficients from shared memory)
+      float wxj, dxj, wyj, dyj, wzj, dzj;
+      {
+        const float sx_ = 2.0f * tx - 1.0f, sy_ = 2.0f * ty - 1.0f, sz_ = 2.0f * tz - 1.0f;
+        const float cD = cf_s[D][j];
+        wxj = wyj = wzj = cD;
+        dxj = dyj = dzj = 0.0f;
+#pragma unroll
+        for (int m = D - 1; m >= 0; --m) {
+          const float cm = cf_s[m][j];
+          dxj = fmaf(dxj, sx_, wxj);
+          wxj = fmaf(wxj, sx_, cm);
+          dyj = fmaf(dyj, sy_, wyj);
+          wyj = fmaf(wyj, sy_, cm);
+          dzj = fmaf(dzj, sz_, wzj);
+          wzj = fmaf(wzj, sz_, cm);
+        }
+      }
+      dxj *= th0;
+      dyj *= th1;
+      dzj *= th2;
+      float wx[P], dx[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        wx[i] = __shfl_sync(0xffffffffu, wxj, gbase + i);
+        dx[i] = __shfl_sync(0xffffffffu, dxj, gbase + i);
+      }
+      int cx, cy, cz;
+      unpack_cell(cell, cx, cy, cz);
+      const float4* row = reg4 + ((cz - oz) * S + (cy - oy) + jr) * R1 + (cx - ox);
+      float A[4] = {0, 0, 0, 0}, Az[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const float wz = __shfl_sync(0xffffffffu, wzj, gbase + k);
+        const float dz = __shfl_sync(0xffffffffu, dzj, gbase + k);
+        float sx[4] = {0, 0, 0, 0}, dsx[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const float4 v = row[k * R2 + i];
+          sx[0] = fmaf(v.x, wx[i], sx[0]);
+          sx[1] = fmaf(v.y, wx[i], sx[1]);
+          sx[2] = fmaf(v.z, wx[i], sx[2]);
+          sx[3] = fmaf(v.w, wx[i], sx[3]);
+          dsx[0] = fmaf(v.x, dx[i], dsx[0]);
+          dsx[1] = fmaf(v.y, dx[i], dsx[1]);
+          dsx[2] = fmaf(v.z, dx[i], dsx[2]);
+          dsx[3] = fmaf(v.w, dx[i], dsx[3]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          A[c] = fmaf(sx[c], wz, A[c]);
+          Az[c] = fmaf(sx[c], dz, Az[c]);
+          B[c] = fmaf(dsx[c], wz, B[c]);
+        }
+      }
+      // lane j of the stencil's y rows (j >= P: weights zero)
+      const float wy = j < P ? wyj : 0.0f, dy = j < P ? dyj : 0.0f;
+      float v[8];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = A[c] * wy;
+      v[4] = wy * (q[0] * B[0] + q[1] * B[1] + q[2] * B[2] + q[3] * B[3]);
+      v[5] = dy * (q[0] * A[0] + q[1] * A[1] + q[2] * A[2] + q[3] * A[3]);
+      v[6] = wy * (q[0] * Az[0] + q[1] * Az[1] + q[2] * Az[2] + q[3] * Az[3]);
+      v[7] = 0.0f;
+      // transposing butterfly over the group: afterwards lane j holds sum j
+      {
+        const bool h4 = (j & 4) != 0;
+        float r4[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float keep = h4 ? v[4 + m] : v[m], give = h4 ? v[m] : v[4 + m];
+          r4[m] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+        }
+        const bool h2 = (j & 2) != 0;
+        float r2[2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const float keep = h2 ? r4[2 + m] : r4[m], give = h2 ? r4[m] : r4[2 + m];
+          r2[m] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+        }
+        const bool h1 = (j & 1) != 0;
+        const float keep = h1 ? r2[1] : r2[0], give = h1 ? r2[0] : r2[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
+      }
+      if (valid) {
+        if (j < 4) {
+          if (phi && j < nk) phi[int64_t(c0 + j) * n + o] = v[0] + zshift;
+        } else if (j < 7 && forces) {
+          float* fo = forces + 3 * int64_t(o) + (j - 4);
+          if (nchunk == 1)
+            *fo = v[0];
+          else
+            atomicAdd(fo, v[0]);
+        }
+      }
+    }
+  }
+}
+
+// ---- spread -------------------------------------------------------------------
+// Work items (tile, chunk of four channels).  FP32 fixed point as in k_spread:
+// contributions are rounded to integers of a per-(tile, channel) unit 1/s by
+// one FFMA with 1.5 * 2^23 and summed exactly in 32 bits; s (from
+// k_tile_scale, computed when the points are set) keeps every contribution
+// below 2^22 and every sum below 2^31.  The grid is zeroed before the launch.
+// Spreading region: channel c, point (x, y, z) at c N + z R2 + y R1 + x; R1
+// odd and N = 8 R1 (mod 32), so lane (c, j) of a warp (row j) is in bank
+// R1 (8 c + j) + const (mod 32): 32 distinct banks.
+template <int P>
+struct SPad {
+  static constexpr int S = kTile + P - 1;
+  static constexpr int R1 = S | 1;
+  static constexpr int R2 = S * R1;
+  static constexpr int find_n() {
+    int n = S * R2;
+    while (((n - R1 * 8) % 32 + 32) % 32 != 0) ++n;
+    return n;
+  }
+  static constexpr int N = (find_n() + 3) / 4 * 4;   // whole int4 per channel
+};
+
+template <int P>
+constexpr size_t spread4_smem_bytes() {
+  return size_t(4) * SPad<P>::N * sizeof(int);
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, const int* __restrict__ tile_start,
+                                                   const float* __restrict__ st, const uint64_t* __restrict__ scell,
+                                                   const float* __restrict__ sq,
+                                                   const float* __restrict__ tscale,
+                                                   const __grid_constant__ WinCoef<float> wc,
+                                                   float* __restrict__ grid) {
+  static_assert(P <= 8, "eight lanes per channel");
+  using L = SPad<P>;
+  constexpr int S = L::S, R1 = L::R1, R2 = L::R2, N = L::N;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) int regi[];   // [4][N], layout SPad
+  __shared__ float sscale[4], inv_s[4];
+  __shared__ int64_t zoff_s[SPad<P>::S], yoff_s[SPad<P>::S];   // wrapped plane and row offsets of the item
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane & 7, cl = lane >> 3;   // stencil row and channel of the lane
+  const int jr = j < P ? j : P - 1;
+  LanePiece<P> pc;
+  pc.load(wc, j);
+  // the window piece a lane evaluates: piece j of direction cl (cl = 3 idle)
+  const int nchunk = (g.K + 3) / 4;
+  const int nitems = g.B * g.nts * nchunk;
+  const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
+  const float* st_l = st + int64_t(min(cl, 2)) * nmax;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int visit = item / nchunk, chunk = item - visit * nchunk;
+    const int tile = tile_for_visit(g, visit);
+    const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
+    if (a0 == a1) continue;
+    const int sidx = tile / g.nts;
+    const int c0 = chunk * 4, nk = min(4, g.K - c0);
+    const int gc0 = sidx * g.K + c0;
+    int ox, oy, oz;
+    tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
+    __syncthreads();   // the previous item's flush is done with the region
+    {
+      int4* r4 = reinterpret_cast<int4*>(regi);   // 4 N ints = N int4
+      for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
+      if (threadIdx.x < S)
+        zoff_s[threadIdx.x] = wrap_index(oz + threadIdx.x, g.M[2]) * plane;
+      else if (threadIdx.x < 2 * S)
+        yoff_s[threadIdx.x - S] = int64_t(wrap_index(oy + threadIdx.x - S, g.M[1])) * g.Mxp;
+    }
+    if (threadIdx.x < 4) {
+      const float sc = int(threadIdx.x) < nk ? tscale[int64_t(tile) * g.K + c0 + threadIdx.x] : 1.0f;
+      sscale[threadIdx.x] = sc;
+      inv_s[threadIdx.x] = 1.0f / sc;
+    }
+    __syncthreads();
+    const bool active = j < P && cl < nk;
+    const float qscale = active ? sscale[cl] : 0.0f;
+    // one atom per warp; the next atom's inputs are loaded ahead
+    int a = a0 + warp;
+    float t_n = 0.0f, q_n = 0.0f;
+    uint64_t cell_n = 0;
+    if (a < a1) {
+      t_n = st_l[a];
+      cell_n = scell[a];
+      q_n = cl < nk ? sq[int64_t(c0 + cl) * nmax + a] : 0.0f;
+    }
+    for (; a < a1; a += NW) {
+      const float t = t_n, qv = q_n;
+      const uint64_t cell = cell_n;
+      if (a + NW < a1) {
+        t_n = st_l[a + NW];
+        cell_n = scell[a + NW];
+        q_n = cl < nk ? sq[int64_t(c0 + cl) * nmax + a + NW] : 0.0f;
+      }
+      const float w = pc.value(t);   // piece j of direction cl
+      float wx[P], wz[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        wx[i] = __shfl_sync(0xffffffffu, w, i);
+        wz[i] = __shfl_sync(0xffffffffu, w, 16 + i);
+      }
+      const float wy = __shfl_sync(0xffffffffu, w, 8 + jr);
+      int cx, cy, cz;
+      unpack_cell(cell, cx, cy, cz);
+      if (active) {
+        int* row = regi + cl * N + (cz - oz) * R2 + ((cy - oy) + j) * R1 + (cx - ox);
+        const float qy = qv * qscale * wy;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const float coef = qy * wz[k];
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const float f = fmaf(coef, wx[i], 12582912.0f);
+            atomicAdd(row + k * R2 + i, __float_as_int(f) - 0x4B400000);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    {
+      // two rows per warp iteration (half-warps), each lane adds an x pair;
+      // pairs that do not straddle the periodic wrap go as one 8-byte atomic
+      // (grid rows start at even offsets, tile origins are even)
+      const int half = lane >> 4, x0 = 2 * (lane & 15);
+      const bool has0 = x0 < S, has1 = x0 + 1 < S;
+      const int gx0 = has0 ? wrap_index(ox + x0, g.M[0]) : 0;
+      const int gx1 = has1 ? wrap_index(ox + x0 + 1, g.M[0]) : 0;
+      const bool pair = has1 && gx1 == gx0 + 1 && (gx0 & 1) == 0;
+      for (int pl = warp; pl < nk * S; pl += NW) {
+        const int c = pl / S, lz = pl - c * S;
+        const float inv = inv_s[c];
+        float* base = grid + (gc0 + c) * chan + zoff_s[lz];
+        const int* src = regi + c * N + lz * R2;
+        if (!has0) continue;
+        for (int ly = half; ly < S; ly += 2) {
+          float* rowg = base + yoff_s[ly];
+          const int v0 = src[ly * R1 + x0];
+          const int v1 = has1 ? src[ly * R1 + x0 + 1] : 0;
+          if (pair) {
+            atomicAdd(reinterpret_cast<float2*>(rowg + gx0), make_float2(float(v0) * inv, float(v1) * inv));
+          } else {
+            atomicAdd(rowg + gx0, float(v0) * inv);
+            if (has1) atomicAdd(rowg + gx1, float(v1) * inv);
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace pswf
