@@ -384,6 +384,10 @@ struct pswf_plan_s {
   // ... and when My and Mz are of that form too, the (z, y) passes as well:
   // z pass, then the multiplier fused with the y transforms (no cuFFT)
   bool yzfft = false;
+  // Psi written by the own inverse x pass as channel quadruples (K a multiple
+  // of 4, FP32 four-channel gather, no backward: the backward kernels read
+  // Psi channel-planar)
+  bool psi_il = false;
   void* xtw = nullptr;       // twiddle tables (float2) of Mx, then My and Mz (yzfft)
   int64_t tw_off[3] = {0, 0, 0};
   // real-space complement (PSWF_FLAG_REAL_SPACE): its cell list and scratch
@@ -733,6 +737,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.soff = p->soff;
   c.tile_start = p->tile_start;
   c.tscale = p->tscale;
+  c.psi_il = p->psi_il;
   c.st = p->st;
   c.scell = p->scell;
   c.sq = p->sq;
@@ -845,7 +850,7 @@ int fft_exec_pruned(pswf_plan p, void* data, bool forward) {
       for (int c = 0; c < h.K && r == CUFFT_SUCCESS && !p->yzfft; ++c) r = planes(c);
       if (r == CUFFT_SUCCESS) {
         int rc = cuda_check(p, launch_irfft_x(p->spec, h.M[0], h.M[1], h.M[2], h.K, p->nkx, p->xtw,
-                                              static_cast<float*>(data), p->stream), "k_irfft_x");
+                                              static_cast<float*>(data), p->stream, p->psi_il), "k_irfft_x");
         if (rc) return rc;
         ++p->launches[p->cur_stage];
       }
@@ -1151,6 +1156,7 @@ int make_fft(pswf_plan p) {
     p->pruned = p->nkx * 4 <= Mxh * 3 && h.M[0] >= 64;
     p->xfft = p->pruned && p->real_size == 4 && xfft_supported(h.M[0]);
     p->yzfft = p->xfft && xfft_supported(h.M[1]) && xfft_supported(h.M[2]);
+    p->psi_il = p->xfft && h.K % 4 == 0 && h.P <= 8 && !(p->flags & PSWF_FLAG_BACKWARD);
   }
   if (p->yzfft) {   // no cuFFT plan
     p->fft_sizes.assign(1, 1);

@@ -282,6 +282,38 @@ __global__ void __launch_bounds__(kXThreads) k_rfft_x(const float* __restrict__ 
   }
 }
 
+// Inverse real transform of two staged rows (sa and sa + rs, spectra at the
+// staged positions of k < nkx) packed as one complex row: the Hermitian
+// spectra at k are given for k < nkx, conjugate mirrors for N - k < nkx,
+// zero between (the DC imaginary parts dropped); afterwards register k1 of
+// lane l holds x[32 k1 + brev5(l)] of the first row (.x) and second (.y).
+template <int N1>
+__device__ __forceinline__ void irfft_rows(const float2* sa, int rs, int nkx, const float2* __restrict__ tw,
+                                           int lane, float2 (&v)[N1]) {
+  constexpr int N = 32 * N1;
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+    const int k = n1 + N1 * lane;
+    float2 a = make_float2(0.0f, 0.0f), b = a;
+    if (k < nkx) {
+      const int pk = stage_pos<N1>(k);
+      a = sa[pk];
+      b = sa[rs + pk];
+      if (k == 0) a.y = b.y = 0.0f;
+    } else if (N - k < nkx) {
+      const int pk = stage_pos<N1>(N - k);
+      a = sa[pk];
+      b = sa[rs + pk];
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    v[n1] = make_float2(a.x - b.y, a.y + b.x);   // A + i B
+  }
+  lane_dft<N1, true>(v, tw + N, lane);
+  lane_twiddle<N1, true>(v, tw + N + 160, lane);
+  dft_reg<N1, true>(v);
+}
+
 template <int N1>
 __global__ void __launch_bounds__(kXThreads) k_irfft_x(const float2* __restrict__ spec, int My, int Mz, int nkx,
                                                        int rs, const float2* __restrict__ tw,
@@ -304,37 +336,62 @@ __global__ void __launch_bounds__(kXThreads) k_irfft_x(const float2* __restrict_
   __syncthreads();
   if (ya >= My) return;
   const bool hasb = ya + 1 < My;
-  const float2* sa = stage + (2 * warp) * rs;
   float2 v[N1];
-#pragma unroll
-  for (int n1 = 0; n1 < N1; ++n1) {
-    // both rows' Hermitian spectra at k: given for k < nkx, conjugate
-    // mirrors for N - k < nkx, zero between; the DC imaginary parts dropped
-    const int k = n1 + N1 * lane;
-    float2 a = make_float2(0.0f, 0.0f), b = a;
-    if (k < nkx) {
-      const int pk = stage_pos<N1>(k);
-      a = sa[pk];
-      b = sa[rs + pk];
-      if (k == 0) a.y = b.y = 0.0f;
-    } else if (N - k < nkx) {
-      const int pk = stage_pos<N1>(N - k);
-      a = sa[pk];
-      b = sa[rs + pk];
-      a.y = -a.y;
-      b.y = -b.y;
-    }
-    v[n1] = make_float2(a.x - b.y, a.y + b.x);   // A + i B
-  }
-  lane_dft<N1, true>(v, tw + N, lane);
-  lane_twiddle<N1, true>(v, tw + N + 160, lane);
-  dft_reg<N1, true>(v);
+  irfft_rows<N1>(stage + (2 * warp) * rs, rs, nkx, tw, lane, v);
   // register k1 of lane l is x[32 k1 + brev5(l)]: 128 contiguous bytes per store
   float* ra = grid + (int64_t(cz) * My + ya) * Mxp + int(__brev(unsigned(lane)) >> 27);
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) {
     ra[32 * k1] = v[k1].x;
     if (hasb) ra[Mxp + 32 * k1] = v[k1].y;
+  }
+}
+
+// The same inverse writing the grid as channel quadruples: a CTA takes four
+// rows of one z plane for the four channels of a quadruple (warp w: channel
+// w / 2, rows 2 (w % 2) and the next), keeps the real rows in shared memory
+// (channel planes) and stores each grid point's four channels as one
+// 16-byte word.
+constexpr int kRows4 = 4;   // rows per channel of a quadruple CTA
+template <int N1>
+__global__ void __launch_bounds__(kXThreads) k_irfft_x4(const float2* __restrict__ spec, int My, int Mz, int nkx,
+                                                        int rs, const float2* __restrict__ tw,
+                                                        float4* __restrict__ grid4) {
+  constexpr int N = 32 * N1, Mxp = N + 2;
+  extern __shared__ float2 stage[];   // [4 channels][kRows4][rs], then the real rows [4][kRows4][N]
+  float* rows = reinterpret_cast<float*>(stage + 4 * kRows4 * rs);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cl = warp >> 1, rp = warp & 1;
+  const int ychunks = (My + kRows4 - 1) / kRows4;
+  const int yc = blockIdx.x % ychunks, qz = blockIdx.x / ychunks;
+  const int z = qz % Mz, q = qz / Mz;
+  const int y0 = yc * kRows4;
+  const int64_t plane = int64_t(Mz) * My;
+  const int ny = min(kRows4, My - y0);
+  for (int e = threadIdx.x; e < nkx * 4 * kRows4; e += kXThreads) {
+    const int k = e / (4 * kRows4), r = e % (4 * kRows4);
+    const int c = r / kRows4, yl = r % kRows4;
+    stage[r * rs + stage_pos<N1>(k)] =
+        yl < ny ? spec[int64_t(4 * q + c) * (N / 2 + 1) * plane + int64_t(k) * plane + int64_t(z) * My + y0 + yl]
+                : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  {
+    float2 v[N1];
+    irfft_rows<N1>(stage + (cl * kRows4 + 2 * rp) * rs, rs, nkx, tw, lane, v);
+    float* ra = rows + (cl * kRows4 + 2 * rp) * N + int(__brev(unsigned(lane)) >> 27);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      ra[32 * k1] = v[k1].x;
+      ra[N + 32 * k1] = v[k1].y;
+    }
+  }
+  __syncthreads();
+  float4* out = grid4 + ((int64_t(q) * Mz + z) * My + y0) * Mxp;
+  for (int e = threadIdx.x; e < ny * N; e += kXThreads) {
+    const int yl = e / N, x = e - yl * N;
+    out[int64_t(yl) * Mxp + x] = make_float4(rows[(0 * kRows4 + yl) * N + x], rows[(1 * kRows4 + yl) * N + x],
+                                             rows[(2 * kRows4 + yl) * N + x], rows[(3 * kRows4 + yl) * N + x]);
   }
 }
 
@@ -508,7 +565,7 @@ __global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultP
 
 template <int N1>
 cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int nkx, const void* tw, void* out,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool il) {
   // staged row stride: past the last position, odd
   int rs = (nkx - 1) + ((N1 % 2 == 0) ? (nkx - 1) / N1 : 0) + 1;
   rs += (rs % 2 == 0) ? 1 : 0;
@@ -523,6 +580,19 @@ cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int n
     k_rfft_x<N1><<<unsigned(blocks), kXThreads, smem, s>>>(static_cast<const float*>(in), My, Mz, nkx, rs,
                                                              static_cast<const float2*>(tw), static_cast<float2*>(out));
   } else {
+    if (il) {
+      const size_t smem4 = size_t(4 * kRows4) * rs * sizeof(float2) + size_t(4 * kRows4) * N1 * 32 * sizeof(float);
+      const int64_t blocks4 = int64_t(K / 4) * Mz * ((My + kRows4 - 1) / kRows4);
+      if (smem4 > 32 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_irfft_x4<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem4));
+        if (e != cudaSuccess) return e;
+      }
+      k_irfft_x4<N1><<<unsigned(blocks4), kXThreads, smem4, s>>>(static_cast<const float2*>(in), My, Mz, nkx, rs,
+                                                                  static_cast<const float2*>(tw),
+                                                                  static_cast<float4*>(out));
+      return cudaGetLastError();
+    }
     if (smem > 32 * 1024) {   // opt in early: static shared memory counts too
       const cudaError_t e = cudaFuncSetAttribute(k_irfft_x<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
@@ -534,24 +604,24 @@ cudaError_t launch_n1(bool forward, const void* in, int My, int Mz, int K, int n
 }
 
 cudaError_t dispatch(bool forward, int Mx, const void* in, int My, int Mz, int K, int nkx, const void* tw, void* out,
-                     cudaStream_t s) {
-  if (!xfft_supported(Mx) || nkx > Mx / 2) return cudaErrorInvalidValue;
+                     cudaStream_t s, bool il = false) {
+  if (!xfft_supported(Mx) || nkx > Mx / 2 || (il && K % 4 != 0)) return cudaErrorInvalidValue;
   switch (Mx / 32) {
-    case 2: return launch_n1<2>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 3: return launch_n1<3>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 4: return launch_n1<4>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 5: return launch_n1<5>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 6: return launch_n1<6>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 7: return launch_n1<7>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 8: return launch_n1<8>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 9: return launch_n1<9>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 10: return launch_n1<10>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 11: return launch_n1<11>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 12: return launch_n1<12>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 13: return launch_n1<13>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 14: return launch_n1<14>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 15: return launch_n1<15>(forward, in, My, Mz, K, nkx, tw, out, s);
-    case 16: return launch_n1<16>(forward, in, My, Mz, K, nkx, tw, out, s);
+    case 2: return launch_n1<2>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 3: return launch_n1<3>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 4: return launch_n1<4>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 5: return launch_n1<5>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 6: return launch_n1<6>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 7: return launch_n1<7>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 8: return launch_n1<8>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 9: return launch_n1<9>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 10: return launch_n1<10>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 11: return launch_n1<11>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 12: return launch_n1<12>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 13: return launch_n1<13>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 14: return launch_n1<14>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 15: return launch_n1<15>(forward, in, My, Mz, K, nkx, tw, out, s, il);
+    case 16: return launch_n1<16>(forward, in, My, Mz, K, nkx, tw, out, s, il);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -618,8 +688,8 @@ cudaError_t launch_rfft_x(const float* grid, int Mx, int My, int Mz, int K, int 
 }
 
 cudaError_t launch_irfft_x(const void* spec, int Mx, int My, int Mz, int K, int nkx, const void* tw, float* grid,
-                           cudaStream_t s) {
-  return dispatch(false, Mx, spec, My, Mz, K, nkx, tw, grid, s);
+                           cudaStream_t s, bool interleave4) {
+  return dispatch(false, Mx, spec, My, Mz, K, nkx, tw, grid, s, interleave4);
 }
 
 namespace {

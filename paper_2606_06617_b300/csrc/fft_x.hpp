@@ -37,8 +37,13 @@ void xfft_twiddles(int Mx, std::vector<float>& out);
 // tw: the device copy of the twiddle table.  One launch each.
 cudaError_t launch_rfft_x(const float* grid, int Mx, int My, int Mz, int K, int nkx, const void* tw, void* spec,
                           cudaStream_t s);
+// interleave4 (K a multiple of 4): the inverse writes the grid as channel
+// quadruples, float [K / 4][Mz][My][Mxp][4] (element (c, z, y, x) at
+// (((c / 4) Mz + z) My + y) Mxp + x) * 4 + c % 4), so one 16-byte word holds
+// four channels of a grid point (a CTA transforms the four channels of its
+// rows and writes whole quadruples).
 cudaError_t launch_irfft_x(const void* spec, int Mx, int My, int Mz, int K, int nkx, const void* tw, float* grid,
-                           cudaStream_t s);
+                           cudaStream_t s, bool interleave4 = false);
 
 // Lines of the nkx planes that can hold band modes after the z pass: for kx
 // < nkx and column position pz (kz = (pz >> 5) + (Mz / 32) brev5(pz & 31),

@@ -117,7 +117,7 @@ cudaError_t interp4_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch)
   k_gather4<P, kGather4Threads><<<blocks, kGather4Threads, smem, c.stream>>>(
       c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const float*>(c.st), c.scell,
       static_cast<const float*>(c.sq), c.sperm, wc, static_cast<const float*>(c.grid), c.zero_coef, c.charges,
-      static_cast<float*>(phi), static_cast<float*>(forces));
+      static_cast<float*>(phi), static_cast<float*>(forces), c.psi_il);
   ++*nlaunch;
   return cudaGetLastError();
 }

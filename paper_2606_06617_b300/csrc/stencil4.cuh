@@ -84,6 +84,12 @@ struct LanePiece {
   }
 };
 
+// 16-byte asynchronous global-to-shared copy (both addresses 16-byte aligned).
+__device__ inline void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int P>
 struct Pad4 {
   static constexpr int S = kTile + P - 1;
@@ -103,7 +109,9 @@ constexpr size_t gather4_smem_bytes() {
 // more than one chunk the forces are accumulated with global atomics (the
 // caller zeroes them).
 //
-// Staging: a job is an x-pair of one region row; its four channels' pairs
+// Staging: when Psi is stored as channel quadruples (psi_il, written so by
+// the own inverse x pass), one 16-byte asynchronous copy per grid point.
+// Otherwise a job is an x-pair of one region row; its four channels' pairs
 // are read as 8-byte loads (grid rows start at even offsets and tile origins
 // are even, so a pair that does not straddle the periodic wrap is aligned)
 // and written as two float4 (x, then x + 1), several jobs' loads in flight
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
                                                    const float* __restrict__ grid,
                                                    const double* __restrict__ zero_coef,
                                                    const double* __restrict__ charges, float* __restrict__ phi,
-                                                   float* __restrict__ forces) {
+                                                   float* __restrict__ forces, bool psi_il) {
   static_assert(P <= 8, "one 8-lane group per atom");
   using L = Pad4<P>;
   constexpr int S = L::S, R1 = L::R1, R2 = L::R2;
@@ -132,6 +140,8 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
   extern __shared__ __align__(16) float4 reg4[];   // [S][S][R1] x 4 channels
   __shared__ float cf_s[D + 1][8];                 // window coefficients [monomial][piece]
   __shared__ float item_s[8];                      // 2 / h_d (3), zero-frequency shifts (4)
+  __shared__ int gx_s[L::S];                       // wrapped x of the region (channel-quadruple staging)
+  __shared__ int64_t yoff_s[L::S], zoff_s[L::S];   // wrapped row and plane offsets
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = lane & 7, grp = lane >> 3, gbase = lane & ~7;
   const int jr = j < P ? j : P - 1;
@@ -161,7 +171,25 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
       const int c = threadIdx.x - 3;
       item_s[threadIdx.x] = c < nk ? float(2.0 * zero_coef[gc0 + c] * charges[2 * (gc0 + c)]) : 0.0f;
     }
-    {
+    if (psi_il) {
+      // Psi as channel quadruples: one 16-byte asynchronous copy per grid
+      // point, wrapped offsets from the item's tables
+      if (threadIdx.x < S) {
+        gx_s[threadIdx.x] = wrap_index(ox + threadIdx.x, g.M[0]);
+      } else if (threadIdx.x < 2 * S) {
+        yoff_s[threadIdx.x - S] = int64_t(wrap_index(oy + threadIdx.x - S, g.M[1])) * g.Mxp;
+      } else if (threadIdx.x < 3 * S) {
+        zoff_s[threadIdx.x - 2 * S] = wrap_index(oz + threadIdx.x - 2 * S, g.M[2]) * plane;
+      }
+      __syncthreads();
+      const float4* g4 = reinterpret_cast<const float4*>(grid) + int64_t(gc0 / 4) * chan;
+      for (int e = threadIdx.x; e < S * S * S; e += NT) {
+        const int row = e / S, x = e - row * S;
+        const int lz = row / S, ly = row - lz * S;
+        cp_async16(reg4 + row * R1 + x, g4 + zoff_s[lz] + yoff_s[ly] + gx_s[x]);
+      }
+      cp_async_wait_all();
+    } else {
       const float* gch = grid + int64_t(gc0) * chan;
       for (int e0 = threadIdx.x; e0 < NJOB; e0 += U * NT) {
         float2 pr[U][4];

@@ -105,3 +105,22 @@ def test_charged_p3_p5(precision):
         assert abs(e[c] - o["E_ch"][c]) <= tol * abs(o["E_ch"][c]), (c, e[c], o["E_ch"][c])
     assert rel_rms(ph, o["phi"]) <= tol
     assert rel_rms(f, o["F"]) <= tol
+
+
+@pytest.mark.parametrize("ps", [(1, 2, 4, 6), (1, 6, 2, 4, 6, 1, 4, 2)], ids=["K4", "K8"])
+def test_own_transform_channel_quadruples(ps):
+    """Single FP32 plans on the own transform with K a multiple of four keep
+    the potential grid as channel quadruples between the inverse transform
+    and the gather: one and two quadruples against O1, all outputs."""
+    box = (19.2, 17.6, 19.2)
+    M = (64, 64, 64)
+    s = wl.random_system(int(0.1 * np.prod(box)), box, ps, seed=41, neutral=False)
+    plan, cw = _plan(s, box, M, 7, 4.0, 0)
+    assert plan.info["transform"] == 3
+    e, ph, f = (_np(x) for x in plan.execute())
+    plan.sync()
+    o = run_oracle(s, 4.0, 7, M, C_TOL, cw)
+    for c in range(len(ps)):
+        assert abs(e[c] - o["E_ch"][c]) <= TOL_FP32 * abs(o["E_ch"][c]), (c, e[c], o["E_ch"][c])
+    assert rel_rms(ph, o["phi"]) <= TOL_FP32, rel_rms(ph, o["phi"])
+    assert rel_rms(f, o["F"]) <= TOL_FP32, rel_rms(f, o["F"])
