@@ -409,14 +409,18 @@ def _percentiles(x):
             "mean_ms": float(x.mean())}
 
 
-def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, seed: int = 0) -> dict:
+def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, n_resident: int = 1024,
+                seed: int = 0) -> dict:
     """The serving stream (K = 8 channels, p in {1, 6} per request, 32-2048
     atoms, density 0.1, Poisson arrivals) through the request server (FP32,
     continuous batching, captured graphs), open loop at `rate` and as one
-    burst; and the plain path -- one FP64 single-structure plan per request,
-    created, run and read back one at a time -- on the first n_plain requests
-    of the same stream at the same arrival times.  Latency: arrival (submit)
-    to results ready."""
+    burst; and two plain FP64 paths, one structure per launch with no graphs
+    or batching: one plan created, run and read back per request (first
+    n_plain requests), and resident single-slot plans, one per grid bucket,
+    created before timing (first n_resident requests), each at the same
+    arrival times and as a burst.  The speed-up is the server's burst
+    throughput on the same n_resident requests over the resident path's.
+    Latency: arrival (submit) to results ready."""
     import torch
     from paper_2606_06617_b300 import lr
     from paper_2606_06617_b300 import workloads as wl
@@ -496,6 +500,58 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, see
     atoms_plain = sum(r.system.n for r in sub)
     ours_burst = atoms / t_burst
     plain_burst = atoms_plain / t_plain_burst
+
+    # resident plain path: per grid bucket one FP64 single-slot plan, created
+    # before timing on the server's grids and boxes (same method parameters);
+    # each request is set_points, execute and the read-back of E, phi and F,
+    # one structure per launch, no graphs, no batching
+    res_sub = reqs[:n_resident]
+    plans = {}
+    for gi, (g, b, nb) in enumerate(buckets):
+        plans[gi] = lr.BatchPlan((g * h_max,) * 3, 1, max(1, nb // b), K, (1, 6), r_c, tol=tol, grid=g, precision=1,
+                                 device=dev)
+
+    def route(sm):
+        lmax = max(sm.box)
+        for gi, (g, b, nb) in enumerate(buckets):
+            if lmax <= g * h_max * (1.0 + 1e-12) and sm.n <= nb // b:
+                return gi
+        raise ValueError("no bucket holds the structure")
+
+    def resident_one(r):
+        sm = r.system
+        bp = plans[route(sm)]
+        bp.set_points(np.array([sm.box]), np.array([sm.ps], dtype=np.int32), np.array([0, sm.n], dtype=np.int64),
+                      torch.tensor(sm.pos, device=dev), torch.tensor(sm.q, dtype=torch.float64, device=dev))
+        e, phi, f = bp.execute()
+        return e.cpu().numpy(), phi[:, :sm.n].cpu().numpy(), f[:sm.n].cpu().numpy()
+
+    for r in res_sub[:64]:
+        resident_one(r)                    # warm-up
+    t1 = time.perf_counter()
+    for r in res_sub:
+        resident_one(r)
+    t_res_burst = time.perf_counter() - t1
+    lat_res = []
+    t0 = time.perf_counter()
+    for r in res_sub:
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        resident_one(r)
+        lat_res.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
+    t_res_total = time.perf_counter() - t0
+    atoms_res = sum(r.system.n for r in res_sub)
+    res_burst = atoms_res / t_res_burst
+    del plans
+    # the server on the same subset, one burst
+    srv2 = lr.Server(K, (1, 6), r_c, buckets, tol=tol, inflight=2, device=dev)
+    burst2 = lambda sub: [srv2.wait(t, phi=False) for t in
+                          [srv2.submit(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub]]
+    burst2(res_sub)
+    t1 = time.perf_counter()
+    burst2(res_sub)
+    ours_sub_burst = atoms_res / (time.perf_counter() - t1)
+    srv2.close()
     return {
         "workload": f"serving stream: {n_req} requests, 32-2048 atoms (log-uniform), K=8, p in {{1,6}}, "
                     f"density 0.1, Poisson {rate:.0f}/s, tol {tol:g}, r_c {r_c}",
@@ -509,7 +565,15 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, see
                        "requests": n_plain,
                        "open_loop": {**_percentiles(lat_plain), "atoms_per_s": atoms_plain / t_plain_total},
                        "burst": {"atoms_per_s": plain_burst}},
-        "speedup_atoms_per_s_burst": ours_burst / plain_burst,
+        "plain_fp64_resident": {
+            "path": "FP64, one structure per launch, no graphs or batching; one resident single-slot plan per "
+                    "grid bucket, created before timing; per request set_points, execute, read-back",
+            "requests": len(res_sub),
+            "open_loop": {**_percentiles(lat_res), "atoms_per_s": atoms_res / t_res_total},
+            "burst": {"atoms_per_s": res_burst},
+            "ours_same_requests_burst_atoms_per_s": ours_sub_burst},
+        "speedup_atoms_per_s_burst": ours_sub_burst / res_burst,
+        "speedup_vs_per_request_plan": ours_burst / plain_burst,
         "force_rel_rms_ours_vs_plain": float(np.max(agree)) if agree else None,
     }
 
@@ -732,6 +796,24 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6400.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    # energy only (no inverse transform, no gather): set_points + execute
+    energy_only_ms = None
+    if rank == 0 and world == 1:
+        e_only = out[0]
+        for _ in range(2):
+            plan.set_points(pos, q)
+            plan.execute(phi=False, forces=False, out=(e_only, None, None))
+        torch.cuda.synchronize()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ne = max(3, min(args.steps, 10))
+        a_ev.record(stream)
+        for _ in range(ne):
+            plan.set_points(pos, q)
+            plan.execute(phi=False, forces=False, out=(e_only, None, None))
+        b_ev.record(stream)
+        torch.cuda.synchronize()
+        energy_only_ms = a_ev.elapsed_time(b_ev) / ne
+
     # end-to-end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -756,11 +838,18 @@ def main():
                "ms_per_step": te * 1e3}
 
     serving = None
+    total = None
     info = dict(plan.info)
-    if rank == 0 and world == 1 and not args.no_serving and args.workload == "melt":
+    if rank == 0 and world == 1 and args.workload == "melt":
         del plan, pos, q, out
         torch.cuda.empty_cache()
-        serving = run_serving()
+        # the complete evaluation (reciprocal + real space) of the same melt
+        total = run_total(max(3, min(args.steps, 10)), 3, cpu_baseline=False)
+        total = {k: total[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "roofline",
+                                       "stages_ms_per_step", "gpu_launches", "clocks")}
+        torch.cuda.empty_cache()
+        if not args.no_serving:
+            serving = run_serving()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -784,10 +873,12 @@ def main():
                          "traffic": load_traffic(w["name"], dom),
                          "algorithmic_bytes_per_launch": alg[dom]},
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "energy_only_ms_per_step": energy_only_ms,
             "gpu_launches": int(sum(launches.values())),
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "total": total,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
