@@ -817,11 +817,18 @@ def main():
     # end-to-end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        pos_h = np.ascontiguousarray(sysm.pos)
-        q_h = np.ascontiguousarray(sysm.q)
-        # the caller's result arrays are reused across steps, as a simulation
-        # loop would (their first touch is not part of a step)
-        res_h = (np.zeros(len(sysm.ps) + 1), np.zeros((len(sysm.ps), sysm.n)), np.zeros((sysm.n, 3)))
+        # inputs and results in page-locked host memory (the caller's
+        # arrays, reused across steps as a simulation loop would)
+        def pinned(shape):
+            t = torch.zeros(shape, dtype=torch.float64).pin_memory()
+            keep.append(t)
+            return t.numpy()
+        keep = []
+        pos_h = pinned(sysm.pos.shape)
+        pos_h[...] = sysm.pos
+        q_h = pinned(sysm.q.shape)
+        q_h[...] = sysm.q
+        res_h = (np.zeros(len(sysm.ps) + 1), pinned((len(sysm.ps), sysm.n)), pinned((sysm.n, 3)))
         for _ in range(2):
             plan.compute_host(pos_h, q_h, out=res_h)
         if dist:
@@ -831,10 +838,27 @@ def main():
         for _ in range(ne):
             plan.compute_host(pos_h, q_h, out=res_h)
         te = max_over_ranks((time.perf_counter() - t0) / ne, dist, dev)
+        # phase breakdown of the same call (stream events: input copies,
+        # device stages, output copies; the rest is host time)
+        plan.profile_read()
+        plan.profile(True)
+        t1 = time.perf_counter()
+        for _ in range(3):
+            plan.compute_host(pos_h, q_h, out=res_h)
+        wall = (time.perf_counter() - t1) / 3 * 1e3
+        plan.profile(False)
+        st_e, _ = plan.profile_read()
+        st_e = {k: v / 3 for k, v in st_e.items()}
+        dev_e = sum(v for k, v in st_e.items() if k not in ("h2d", "d2h"))
+        phases = {"wall_ms": wall, "h2d_ms": st_e["h2d"], "device_ms": dev_e, "d2h_ms": st_e["d2h"],
+                  "host_rest_ms": wall - st_e["h2d"] - dev_e - st_e["d2h"]}
         K = len(sysm.ps)
         e2e = {"value": replica_throughput(sysm.n, world, te), "unit": "atoms/s",
-               "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * 4),
-               "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 4 + sysm.n * 12),
+               "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * 8),
+               "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 8 + sysm.n * 24),
+               "host_memory": "page-locked inputs and outputs, copied directly (charges rounded to FP32 "
+                              "and results widened to double on the device)",
+               "phases": phases,
                "ms_per_step": te * 1e3}
 
     serving = None

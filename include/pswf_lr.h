@@ -299,7 +299,14 @@ int pswf_sync(pswf_plan plan);
  * (host double [n][3]) and charges (host double [K][n]) to the device,
  * runs set_points + execute, and copies back energy (host double [K + 1]),
  * phi (host double [K][n], may be NULL) and forces (host double [n][3], may
- * be NULL).  Uses pinned staging buffers owned by the plan. */
+ * be NULL).  Page-locked caller arrays (cudaHostAlloc, cudaMallocHost or
+ * cudaHostRegister) are copied directly: positions and charges in (FP32
+ * plans round the charges on the device), potentials and forces out (FP32
+ * results widened to double on the device first, so the copy out is K n 8 +
+ * 24 n bytes).  Pageable arrays go through pinned staging buffers owned by
+ * the plan, filled and drained by host threads in chunks overlapped with the
+ * copies (charges rounded to the plan's precision there).  Synchronises the
+ * plan's stream. */
 int pswf_compute_host(pswf_plan plan, int64_t n, const double* pos, const double* q,
                       double* energy, double* phi, double* forces);
 
@@ -382,7 +389,7 @@ int pswf_server_last_error(pswf_server srv, char* buf, int len);
 void pswf_server_destroy(pswf_server srv);
 
 /* ---- measurement support (not part of the paper's method) -------------- */
-#define PSWF_NSTAGE 9
+#define PSWF_NSTAGE 11
 /* Stage indices for pswf_profile_read. */
 #define PSWF_STAGE_SET_POINTS 0   /* binning, sort, charge sums */
 #define PSWF_STAGE_SPREAD 1       /* step (i) */
@@ -393,6 +400,10 @@ void pswf_server_destroy(pswf_server srv);
 #define PSWF_STAGE_BACKWARD 6     /* pswf_backward */
 #define PSWF_STAGE_OTHER 7
 #define PSWF_STAGE_REAL_SPACE 8   /* pswf_real_space (cell list and pairs) */
+#define PSWF_STAGE_H2D 9          /* pswf_compute_host: call entry to the last input copy's end
+                                     (host staging of the first chunk included) */
+#define PSWF_STAGE_D2H 10         /* pswf_compute_host: end of the evaluation to the last output
+                                     copy's end */
 
 /* enable != 0: later calls record a CUDA event pair around each stage on the
  * plan's stream (costs one event record per stage boundary). */

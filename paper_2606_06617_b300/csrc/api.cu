@@ -1642,6 +1642,37 @@ int pswf_sync(pswf_plan pl) {
   return PSWF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// True for memory the GPU can copy from directly: page-locked host memory
+// (cudaHostAlloc / cudaMallocHost or registered with cudaHostRegister).
+// NULL counts as pinned (nothing to copy).
+bool host_pinned(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// out[i] = double(in[i]) for i < n (FP32 results widened for the caller).
+__global__ void k_widen(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = double(in[i]);
+}
+
+// out[i] = float(in[i]) for i < n (the caller's charges rounded to the FP32 path).
+__global__ void k_narrow(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = float(in[i]);
+}
+}  // namespace
+
+extern "C" {
+
 int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* q, double* energy, double* phi,
                       double* forces) {
   if (!pl || !energy || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
@@ -1651,9 +1682,19 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   const int64_t rs = int64_t(pl->real_size);
   int rc = ensure_workspace(pl);
   if (rc) return rc;
+  // Pinned caller arrays are copied directly (positions in; potentials and
+  // forces out, widened to double on the device first); pageable ones go
+  // through the plan's pinned staging buffers.
+  const bool pos_direct = host_pinned(pos);
+  const bool q_direct = host_pinned(q);
+  const bool narrow = q_direct && rs == 4;
+  const bool out_direct = host_pinned(phi) && host_pinned(forces);
+  const bool widen = out_direct && rs == 4;
   // device staging: pos double [n][3] | q real [K][n] | energy [K+1] | phi real [K][n] | forces real [n][3]
+  //                 (| phi double [K][n] | forces double [n][3] when widening on the device)
   const int64_t need = align256(n * 3 * 8) + align256(K * n * rs) + align256((K + 1) * 8) + align256(K * n * rs) +
-                       align256(n * 3 * rs);
+                       align256(n * 3 * rs) + (widen ? align256(K * n * 8) + align256(n * 3 * 8) : 0) +
+                       (narrow ? align256(K * n * 8) : 0);
   if (need > pl->d_stage_bytes) {
     if (pl->d_stage) cudaFree(pl->d_stage);
     pl->d_stage = nullptr;
@@ -1681,6 +1722,17 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   char* d_phi = d;
   d += align256(K * n * rs);
   char* d_f = d;
+  d += align256(n * 3 * rs);
+  double* d_phi64 = widen ? reinterpret_cast<double*>(d) : nullptr;
+  double* d_f64 = widen ? reinterpret_cast<double*>(d + align256(K * n * 8)) : nullptr;
+  if (widen) d += align256(K * n * 8) + align256(n * 3 * 8);
+  double* d_q64 = narrow ? reinterpret_cast<double*>(d) : nullptr;
+  // measurement (profiling on): stream events around the input and output copy phases
+  cudaEvent_t ev_in0 = nullptr;
+  if (pl->prof_on) {
+    ev_in0 = take_event(pl);
+    cudaEventRecord(ev_in0, pl->stream);
+  }
   char* hb = reinterpret_cast<char*>(pl->h_pin);
   double* h_pos = reinterpret_cast<double*>(hb);
   char* h_q = hb + n * 24;
@@ -1688,16 +1740,32 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   char* h_phi = reinterpret_cast<char*>(h_e + K + 1);
   char* h_f = h_phi + K * n * rs;
   cudaStream_t s = pl->stream;
+  if (pos_direct && n > 0 &&
+      (rc = cuda_check(pl, cudaMemcpyAsync(d_pos, pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos")))
+    return rc;
+  if (q_direct && n > 0) {
+    // pinned charges: copied as double, rounded to FP32 on the device
+    if ((rc = cuda_check(pl, cudaMemcpyAsync(narrow ? static_cast<void*>(d_q64) : static_cast<void*>(d_q), q,
+                                             size_t(K * n) * 8, cudaMemcpyHostToDevice, s), "h2d q")))
+      return rc;
+    if (narrow) {
+      const int nb = int(std::min<int64_t>((K * n + kThreads - 1) / kThreads, 148 * 16));
+      k_narrow<<<nb, kThreads, 0, s>>>(K * n, d_q64, reinterpret_cast<float*>(d_q));
+      if ((rc = launch_check(pl, "k_narrow"))) return rc;
+      ++pl->launches[PSWF_STAGE_OTHER];
+    }
+  }
   // Inputs in chunks of atoms: the host threads fill chunk i of the pinned
-  // staging (q rounded to the plan's precision) while chunk i - 1 is copied.
-  const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(8, n / 65536));
+  // staging (q rounded to the plan's precision; positions only when the
+  // caller's are pageable) while the copies already enqueued run.
+  const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(16, n / 65536));
   const int64_t csz = (n + nchunk - 1) / nchunk;
-  for (int64_t ci = 0; ci < nchunk && n > 0; ++ci) {
+  for (int64_t ci = 0; ci < nchunk && n > 0 && !(pos_direct && q_direct); ++ci) {
     const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
     if (a0 >= a1) break;
     parallel_for(a1 - a0, [&](int64_t lo, int64_t hi) {
-      std::memcpy(h_pos + 3 * (a0 + lo), pos + 3 * (a0 + lo), size_t(hi - lo) * 24);
-      for (int k = 0; k < K; ++k) {
+      if (!pos_direct) std::memcpy(h_pos + 3 * (a0 + lo), pos + 3 * (a0 + lo), size_t(hi - lo) * 24);
+      for (int k = 0; k < K && !q_direct; ++k) {
         const double* src = q + size_t(k) * n + a0;
         if (rs == 4) {
           float* dst = reinterpret_cast<float*>(h_q) + size_t(k) * n + a0;
@@ -1707,22 +1775,60 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
         }
       }
     });
-    if ((rc = cuda_check(pl, cudaMemcpyAsync(d_pos + 3 * a0, h_pos + 3 * a0, size_t(a1 - a0) * 24,
-                                             cudaMemcpyHostToDevice, s), "h2d pos")))
+    if (!pos_direct && (rc = cuda_check(pl, cudaMemcpyAsync(d_pos + 3 * a0, h_pos + 3 * a0, size_t(a1 - a0) * 24,
+                                                            cudaMemcpyHostToDevice, s), "h2d pos")))
       return rc;
-    if ((rc = cuda_check(pl, cudaMemcpy2DAsync(d_q + a0 * rs, size_t(n * rs), h_q + a0 * rs, size_t(n * rs),
-                                               size_t((a1 - a0) * rs), size_t(K), cudaMemcpyHostToDevice, s),
-                         "h2d q")))
+    if (!q_direct && (rc = cuda_check(pl, cudaMemcpy2DAsync(d_q + a0 * rs, size_t(n * rs), h_q + a0 * rs,
+                                                             size_t(n * rs), size_t((a1 - a0) * rs), size_t(K),
+                                                             cudaMemcpyHostToDevice, s), "h2d q")))
       return rc;
+  }
+  if (ev_in0) {
+    cudaEvent_t b = take_event(pl);
+    cudaEventRecord(b, s);
+    pl->recs.push_back({PSWF_STAGE_H2D, ev_in0, b});
   }
   if ((rc = pswf_set_points(pl, n, d_pos, 1, d_q))) return rc;
   if ((rc = pswf_execute(pl, d_e, phi ? d_phi : nullptr, forces ? d_f : nullptr))) return rc;
+  cudaEvent_t ev_out0 = nullptr;
+  if (pl->prof_on) {
+    ev_out0 = take_event(pl);
+    cudaEventRecord(ev_out0, s);
+  }
   if ((rc = cuda_check(pl, cudaMemcpyAsync(h_e, d_e, size_t(K + 1) * 8, cudaMemcpyDeviceToHost, s), "d2h energy")))
     return rc;
-  // Outputs in chunks: copy chunk i down, then the host threads widen it
-  // into the caller's arrays while chunk i + 1 is in flight.
   std::vector<cudaEvent_t> evs;
-  for (int64_t ci = 0; ci < nchunk && n > 0; ++ci) {
+  const int64_t nchunk_out = out_direct ? 0 : nchunk;
+  if (out_direct && n > 0) {
+    // straight into the caller's pinned arrays (FP32 results widened first)
+    const int wb = int(std::min<int64_t>((K * n + kThreads - 1) / kThreads, 148 * 16));
+    if (phi) {
+      const void* src = d_phi;
+      if (widen) {
+        k_widen<<<wb, kThreads, 0, s>>>(K * n, reinterpret_cast<const float*>(d_phi), d_phi64);
+        if ((rc = launch_check(pl, "k_widen"))) return rc;
+        ++pl->launches[PSWF_STAGE_OTHER];
+        src = d_phi64;
+      }
+      if ((rc = cuda_check(pl, cudaMemcpyAsync(phi, src, size_t(K * n) * 8, cudaMemcpyDeviceToHost, s), "d2h phi")))
+        return rc;
+    }
+    if (forces) {
+      const void* src = d_f;
+      if (widen) {
+        k_widen<<<wb, kThreads, 0, s>>>(3 * n, reinterpret_cast<const float*>(d_f), d_f64);
+        if ((rc = launch_check(pl, "k_widen"))) return rc;
+        ++pl->launches[PSWF_STAGE_OTHER];
+        src = d_f64;
+      }
+      if ((rc = cuda_check(pl, cudaMemcpyAsync(forces, src, size_t(3 * n) * 8, cudaMemcpyDeviceToHost, s),
+                           "d2h forces")))
+        return rc;
+    }
+  }
+  // Pageable outputs in chunks: copy chunk i down, then the host threads
+  // widen it into the caller's arrays while chunk i + 1 is in flight.
+  for (int64_t ci = 0; ci < nchunk_out && n > 0; ++ci) {
     const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
     if (a0 >= a1) break;
     if (phi && (rc = cuda_check(pl, cudaMemcpy2DAsync(h_phi + a0 * rs, size_t(n * rs), d_phi + a0 * rs, size_t(n * rs),
@@ -1735,6 +1841,11 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
     cudaEvent_t ev = take_event(pl);
     if ((rc = cuda_check(pl, cudaEventRecord(ev, s), "record chunk"))) return rc;
     evs.push_back(ev);
+  }
+  if (ev_out0) {
+    cudaEvent_t b = take_event(pl);
+    cudaEventRecord(b, s);
+    pl->recs.push_back({PSWF_STAGE_D2H, ev_out0, b});
   }
   for (int64_t ci = 0; ci < int64_t(evs.size()); ++ci) {
     const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);

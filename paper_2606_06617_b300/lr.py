@@ -110,8 +110,9 @@ SIGNATURES = {
     "pswf_server_destroy": ([_vp], None),
 }
 
-NSTAGE = 9
-STAGES = ("set_points", "spread", "fft_fwd", "multiply", "fft_inv", "interp", "backward", "other", "real_space")
+NSTAGE = 11
+STAGES = ("set_points", "spread", "fft_fwd", "multiply", "fft_inv", "interp", "backward", "other", "real_space",
+          "h2d", "d2h")
 
 
 def lib():

@@ -155,6 +155,47 @@ def test_compute_host_chunked_matches_device_path(precision):
     assert rel_rms(f, f0.cpu().double().numpy()) < 1e-6
 
 
+def _pinned(a):
+    """A numpy array in page-locked host memory holding a copy of a."""
+    import torch
+    t = torch.empty(a.shape, dtype=torch.float64).pin_memory()
+    out = t.numpy()
+    out[...] = a
+    return out, t   # the caller keeps t alive while out is in use
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("pinned", ["all", "inputs", "outputs"])
+def test_compute_host_pinned_matches_device_path(precision, pinned):
+    """Page-locked caller arrays are copied directly (positions in; potentials
+    and forces out, widened on the device in FP32 plans); mixed pinned and
+    pageable arrays take each side's own route.  Results equal the device
+    path on the same plan up to the flush order."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.random_system(300000, (60.0, 62.0, 64.0), (1, 6, 4, 2), seed=17, neutral=True)
+    plan = lr.Plan(s.box, s.n, s.ps, 6.0, P=6, grid=(64, 64, 64), precision=precision, device=dev)
+    plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=plan.dtype, device=dev))
+    e0, phi0, f0 = plan.execute()
+    plan.sync()
+    keep = []
+    pos, q = s.pos, s.q
+    if pinned in ("all", "inputs"):
+        (pos, t1), (q, t2) = _pinned(s.pos), _pinned(s.q)
+        keep += [t1, t2]
+    out = (np.zeros(len(s.ps) + 1), np.zeros((len(s.ps), s.n)), np.zeros((s.n, 3)))
+    if pinned in ("all", "outputs"):
+        (ph, t3), (ff, t4) = _pinned(out[1]), _pinned(out[2])
+        keep += [t3, t4]
+        out = (out[0], ph, ff)
+    for _ in range(2):   # a second call reuses the plan's buffers
+        e, phi, f = plan.compute_host(pos, q, out=out)
+        np.testing.assert_allclose(e, e0.cpu().numpy(), rtol=1e-6)
+        assert rel_rms(phi, phi0.cpu().double().numpy()) < 1e-6
+        assert rel_rms(f, f0.cpu().double().numpy()) < 1e-6
+
+
 def test_self_energy_matches_oracle():
     """E_self from the device FP64 reduction of the (FP32-stored) charges."""
     s = wl.water_box(n_side=5, L=15.5, seed=2)
