@@ -295,6 +295,12 @@ int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, c
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */
 int pswf_sync(pswf_plan plan);
 
+/* pswf_sync with a limit: polls the stream and returns PSWF_ETIMEOUT if its
+ * work is still running after timeout_ms milliseconds (the work continues;
+ * call again to wait further); timeout_ms < 0 waits without limit.  The
+ * paper has no counterpart (a host-side bounded wait). */
+int pswf_sync_for(pswf_plan plan, double timeout_ms);
+
 /* End-to-end evaluation from host memory (synchronising): copies positions
  * (host double [n][3]) and charges (host double [K][n]) to the device,
  * runs set_points + execute, and copies back energy (host double [K + 1]),
@@ -376,6 +382,18 @@ int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const in
  * from submit to the completion of its batch.  The ticket is released. */
 int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
                      double* latency_ms);
+
+/* pswf_server_wait with a limit: returns PSWF_ETIMEOUT if the structure is
+ * not done within timeout_ms milliseconds (the ticket stays valid and can be
+ * waited for again); timeout_ms < 0 waits without limit.  The paper has no
+ * counterpart (host-side serving). */
+int pswf_server_wait_for(pswf_server srv, int64_t ticket, double timeout_ms, double* energy, double* phi,
+                         double* forces, double* latency_ms);
+
+/* pause != 0: the scheduler starts no new batch (batches in flight finish
+ * and are collected; submissions queue); pause = 0 resumes.  For draining a
+ * server before a reconfiguration, or holding requests back. */
+int pswf_server_pause(pswf_server srv, int pause);
 
 /* Counters since creation (any may be NULL); returns the server's failure
  * status (0 if healthy). */

@@ -1,6 +1,8 @@
 // C-ABI of the PSWF-LR hot path: plan, workspace, launches, cuFFT.
 // The public contract is in include/pswf_lr.h.
 #include <cuda_runtime.h>
+
+#include <chrono>
 #include <cufft.h>
 
 #include <algorithm>
@@ -1628,10 +1630,26 @@ int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, con
   return cuda_check(pl, e, "real space");
 }
 
-int pswf_sync(pswf_plan pl) {
+int pswf_sync(pswf_plan pl) { return pswf_sync_for(pl, -1.0); }
+
+int pswf_sync_for(pswf_plan pl, double timeout_ms) {
   if (!pl) return PSWF_EINVAL;
-  int rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "stream synchronize");
-  if (rc) return rc;
+  int rc;
+  if (timeout_ms < 0) {
+    if ((rc = cuda_check(pl, cudaStreamSynchronize(pl->stream), "stream synchronize"))) return rc;
+  } else {
+    // poll the stream until it is idle or the deadline passes
+    using SC = std::chrono::steady_clock;
+    const auto limit =
+        SC::now() + std::chrono::duration_cast<SC::duration>(std::chrono::duration<double, std::milli>(timeout_ms));
+    for (;;) {
+      const cudaError_t q = cudaStreamQuery(pl->stream);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return cuda_check(pl, q, "stream query");
+      if (SC::now() >= limit) return set_err(pl, PSWF_ETIMEOUT, "pswf_sync_for: work still running at the deadline");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
   if (!pl->err) return PSWF_OK;
   int flag = 0;
   if ((rc = cuda_check(pl, cudaMemcpy(&flag, pl->err, 4, cudaMemcpyDeviceToHost), "read status"))) return rc;

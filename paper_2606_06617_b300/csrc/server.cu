@@ -32,6 +32,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "deadline.hpp"
 #include "internal.hpp"
 #include "pswf_lr.h"
 
@@ -98,6 +99,7 @@ struct pswf_server_s {
   std::condition_variable cv_sched, cv_done;
   std::thread th;
   bool stop = false;
+  bool paused = false;       // pswf_server_pause: no new batches are started
   int64_t next_id = 1;
   int64_t n_batches = 0, n_requests = 0, n_atoms = 0;
   int fatal = 0;
@@ -306,7 +308,7 @@ void scheduler(pswf_server srv) {
           progress = true;
           srv->cv_done.notify_all();
         }
-        if (!c.busy && !b.pending.empty() && !srv->fatal) {
+        if (!c.busy && !b.pending.empty() && !srv->fatal && !srv->paused) {
           int64_t atoms = 0;
           while (!b.pending.empty() && int(c.reqs.size()) < b.b_max && atoms + b.pending.front()->n <= b.n_max) {
             atoms += b.pending.front()->n;
@@ -459,6 +461,21 @@ int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const in
 
 int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
                      double* latency_ms) {
+  return pswf_server_wait_for(srv, ticket, -1.0, energy, phi, forces, latency_ms);
+}
+
+int pswf_server_pause(pswf_server srv, int pause) {
+  if (!srv) return PSWF_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->paused = pause != 0;
+  }
+  srv->cv_sched.notify_one();
+  return PSWF_OK;
+}
+
+int pswf_server_wait_for(pswf_server srv, int64_t ticket, double timeout_ms, double* energy, double* phi,
+                         double* forces, double* latency_ms) {
   if (!srv) return PSWF_EINVAL;
   std::unique_ptr<Request> r;
   {
@@ -466,7 +483,8 @@ int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* ph
     auto it = srv->reqs.find(ticket);
     if (it == srv->reqs.end()) return PSWF_EINVAL;
     Request* rp = it->second.get();
-    srv->cv_done.wait(lk, [&] { return rp->status != 1; });
+    if (!pswf::wait_until_done(lk, srv->cv_done, timeout_ms, [&] { return rp->status != 1; }))
+      return PSWF_ETIMEOUT;   // still pending: the ticket stays valid
     r = std::move(it->second);
     srv->reqs.erase(it);
   }

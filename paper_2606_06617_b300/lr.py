@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
 
+PSWF_ETIMEOUT = -5
 PSWF_FLAG_BACKWARD = 1
 PSWF_FLAG_VIRIAL = 2
 PSWF_FLAG_REAL_SPACE = 4
@@ -88,6 +89,7 @@ SIGNATURES = {
     "pswf_stress": ([_vp, _vp], ctypes.c_int),
     "pswf_real_space": ([_vp, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_sync": ([_vp], ctypes.c_int),
+    "pswf_sync_for": ([_vp, ctypes.c_double], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_plan_destroy": ([_vp], None),
     "pswf_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -104,6 +106,8 @@ SIGNATURES = {
     "pswf_server_route": ([_vp, _i64, _dp, ctypes.POINTER(PswfInfo)], ctypes.c_int),
     "pswf_server_submit": ([_vp, _i64, _dp, _ip, _dp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "pswf_server_wait": ([_vp, _i64, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "pswf_server_wait_for": ([_vp, _i64, ctypes.c_double, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "pswf_server_pause": ([_vp, ctypes.c_int], ctypes.c_int),
     "pswf_server_stats": ([_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "pswf_server_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
@@ -341,8 +345,13 @@ class Plan:
         _check(lib().pswf_self_energy(self._h, out), self._h)
         return np.array(out[:])
 
-    def sync(self):
-        _check(lib().pswf_sync(self._h), self._h)
+    def sync(self, timeout_ms: float | None = None):
+        """Waits for the plan's stream; with timeout_ms, raises PswfError
+        (status PSWF_ETIMEOUT = -5) if the work is still running then."""
+        if timeout_ms is None:
+            _check(lib().pswf_sync(self._h), self._h)
+        else:
+            _check(lib().pswf_sync_for(self._h, float(timeout_ms)), self._h)
 
     def profile(self, enable: bool = True):
         """Record CUDA events around each stage of later calls."""
@@ -521,16 +530,26 @@ class Server:
         self._n[t.value] = n
         return t.value
 
-    def wait(self, ticket: int, phi: bool = True, forces: bool = True):
-        """(energy [K+1], phi [K, n] or None, forces [n, 3] or None, latency ms)."""
-        n = self._n.pop(ticket)
+    def wait(self, ticket: int, phi: bool = True, forces: bool = True, timeout_ms: float | None = None):
+        """(energy [K+1], phi [K, n] or None, forces [n, 3] or None, latency ms).
+        With timeout_ms, raises PswfError (status PSWF_ETIMEOUT = -5) if the
+        structure is not done by then; the ticket stays valid."""
+        n = self._n[ticket]
         e = np.empty(self.K + 1)
         ph = np.empty((self.K, n)) if phi else None
         f = np.empty((n, 3)) if forces else None
         lat = ctypes.c_double()
         dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
-        self._check(lib().pswf_server_wait(self._h, ticket, dp(e), dp(ph), dp(f), ctypes.byref(lat)))
+        t = -1.0 if timeout_ms is None else float(timeout_ms)
+        st = lib().pswf_server_wait_for(self._h, ticket, t, dp(e), dp(ph), dp(f), ctypes.byref(lat))
+        if st != PSWF_ETIMEOUT:
+            del self._n[ticket]   # released by the server (done or failed)
+        self._check(st)
         return e, ph, f, lat.value
+
+    def pause(self, pause: bool = True):
+        """Holds back new batches (pause=True) or resumes them."""
+        self._check(lib().pswf_server_pause(self._h, int(bool(pause))))
 
     def stats(self) -> dict:
         b, r, a = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -117,3 +117,46 @@ def test_server_refuses_what_it_cannot_hold():
     with pytest.raises(lr.PswfError):
         srv.submit(s.pos, s.q, s.box, s.ps)
     srv.close()
+
+
+def test_wait_with_deadline_while_paused():
+    """A paused server holds its requests on the host: a wait with a limit
+    returns PSWF_ETIMEOUT and the ticket stays valid; after resuming, the same
+    ticket completes with the result the request has unpaused."""
+    from paper_2606_06617_b300 import lr
+    srv = _server(2)
+    try:
+        s = _random_structs(1, 2, seed=77)[0]
+        t_ref = srv.submit(s.pos, s.q, s.box, s.ps)
+        e_ref, phi_ref, f_ref, _ = srv.wait(t_ref, timeout_ms=30000)
+        srv.pause(True)
+        t = srv.submit(s.pos, s.q, s.box, s.ps)
+        with pytest.raises(lr.PswfError) as ei:
+            srv.wait(t, timeout_ms=50)
+        assert ei.value.status == lr.PSWF_ETIMEOUT
+        with pytest.raises(lr.PswfError):
+            srv.wait(t, timeout_ms=0)
+        srv.pause(False)
+        e, phi, f, _ = srv.wait(t, timeout_ms=30000)
+        np.testing.assert_allclose(e, e_ref, rtol=1e-6)
+        assert rel_rms(f, f_ref) < 1e-6 and rel_rms(phi, phi_ref) < 1e-6
+    finally:
+        srv.close()
+
+
+def test_plan_sync_with_deadline():
+    """pswf_sync_for: a zero limit while a melt-size evaluation runs gives
+    PSWF_ETIMEOUT (the work goes on), a generous one returns normally."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.ionic_melt(1242757, 233.3, seed=1)
+    plan = lr.Plan(s.box, s.n, s.ps, 7.0, P=7, grid=256, device=dev)
+    plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=torch.float32, device=dev))
+    plan.sync()
+    for _ in range(3):
+        plan.execute()
+    with pytest.raises(lr.PswfError) as ei:
+        plan.sync(timeout_ms=0.0)
+    assert ei.value.status == lr.PSWF_ETIMEOUT
+    plan.sync(timeout_ms=60000.0)
