@@ -46,11 +46,12 @@ extern "C" {
 #define PSWF_ENOMEM (-2)           /* device allocation failed or workspace too small */
 #define PSWF_ECUFFT (-3)           /* a cuFFT call failed */
 #define PSWF_ECUDA (-4)            /* a CUDA runtime call or kernel launch failed */
-#define PSWF_ETIMEOUT (-5)         /* a bounded device wait ran out */
+#define PSWF_ETIMEOUT (-5)         /* a bounded wait ran out (pswf_sync_for, pswf_server_wait_for) */
 #define PSWF_ENONFINITE (-6)       /* NaN or Inf in the positions */
 #define PSWF_ETOLUNREACHABLE (-7)  /* grid too coarse for the mollifier band (h k_c >= pi) */
 #define PSWF_ESTATE (-8)           /* call out of order (e.g. execute before set_points) */
 #define PSWF_ECELL (-9)            /* real space: a cell of the cell list holds more than 2048 atoms */
+#define PSWF_EBOUNDS (-10)         /* bounds-checked build only: a kernel index left its buffer (access skipped) */
 
 /* ---- options ----------------------------------------------------------- */
 #define PSWF_FLAG_BACKWARD 1       /* reserve a second grid so pswf_backward can run */

@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpswf_lr.so")
+# the same library with non-trapping bounds checks in the kernels
+# (-DPSWF_BOUNDS_CHECK; a failed check is reported by pswf_sync as
+# PSWF_EBOUNDS): for tests, not for timing
+LIB_CHECKED = os.path.join(HERE, "libpswf_lr_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object, extra flags)
 UNITS = [
@@ -43,18 +47,20 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = False) -> str:
-    if os.path.exists(LIB) and not (force or ptxas_verbose) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    if os.path.exists(lib) and not (force or ptxas_verbose) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = nvcc_path()
     common = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-I", INCLUDE, "-I", CSRC]
+              "-I", INCLUDE, "-I", CSRC] + (["-DPSWF_BOUNDS_CHECK"] if checked else [])
     if ptxas_verbose:
         common.append("-Xptxas=-v")
     procs = []
     for src, obj, extra in UNITS:
-        cmd = [nvcc, *common, *extra, "-c", os.path.join(CSRC, src), "-o", os.path.join(BUILD, obj)]
+        cmd = [nvcc, *common, *extra, "-c", os.path.join(CSRC, src), "-o", os.path.join(bdir, obj)]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
@@ -68,14 +74,15 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
             sys.stderr.write(err)
     if failed:
         raise RuntimeError("nvcc failed building libpswf_lr.so")
-    link = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *[os.path.join(BUILD, u[1]) for u in UNITS], "-lcufft"]
+    link = [nvcc, *ARCH, "-shared", "-o", lib + ".tmp", *[os.path.join(bdir, u[1]) for u in UNITS], "-lcufft"]
     res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
         raise RuntimeError("nvcc link of libpswf_lr.so failed")
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, ptxas_verbose="--ptxas" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, ptxas_verbose="--ptxas" in sys.argv, force="-f" in sys.argv,
+                checked="--checked" in sys.argv))

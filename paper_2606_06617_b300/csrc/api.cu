@@ -1650,6 +1650,14 @@ int pswf_sync_for(pswf_plan pl, double timeout_ms) {
       std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
   }
+  {
+    // bounds-checked build: the first failed index check of any kernel
+    int bw = take_bounds_word();
+    if (!bw) bw = bounds_word_float();
+    if (!bw) bw = bounds_word_double();
+    if (bw)
+      return set_err(pl, PSWF_EBOUNDS, "kernel index out of its buffer (bounds check " + std::to_string(bw) + ")");
+  }
   if (!pl->err) return PSWF_OK;
   int flag = 0;
   if ((rc = cuda_check(pl, cudaMemcpy(&flag, pl->err, 4, cudaMemcpyDeviceToHost), "read status"))) return rc;
@@ -1938,11 +1946,12 @@ const char* pswf_strerror(int status) {
     case PSWF_ENOMEM: return "out of device memory";
     case PSWF_ECUFFT: return "cuFFT error";
     case PSWF_ECUDA: return "CUDA error";
-    case PSWF_ETIMEOUT: return "device wait timed out";
+    case PSWF_ETIMEOUT: return "wait timed out";
     case PSWF_ENONFINITE: return "non-finite positions";
     case PSWF_ETOLUNREACHABLE: return "tolerance unreachable on this grid";
     case PSWF_ESTATE: return "call out of order";
     case PSWF_ECELL: return "a real-space cell holds more than 2048 atoms";
+    case PSWF_EBOUNDS: return "kernel index out of bounds (checked build)";
   }
   return "unknown status";
 }

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bounds.cuh"
 #include "planner.hpp"
 
 namespace pswf {
@@ -266,6 +267,7 @@ __global__ void k_scatter(int64_t nmax, const R* __restrict__ q, Geometry g, con
   const int64_t n = soff[g.B];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t dst = int64_t(tile_start[tile_of[i]]) + rank[i];
+    if (!in_bounds(dst, nmax, kBoundsScatter)) continue;
     st[dst] = tmp_t[i];
     st[nmax + dst] = tmp_t[nmax + i];
     st[2 * nmax + dst] = tmp_t[2 * nmax + i];

@@ -221,6 +221,8 @@ cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int
   }                                                                                                       \
   return cudaErrorInvalidValue;
 
+int PSWF_CAT(bounds_word, PSWF_REAL)() { return take_bounds_word(); }
+
 cudaError_t PSWF_CAT(launch_spread, PSWF_REAL)(const LaunchCtx& c, int* nlaunch) {
   PSWF_P_CASES(spread_P, c, nlaunch)
 }

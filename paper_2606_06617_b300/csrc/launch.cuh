@@ -52,5 +52,9 @@ cudaError_t launch_interp_double(const LaunchCtx& c, void* phi, void* forces, in
 // backward: spread of rhobar into grid2 (stage 0) or the final gather (stage 1)
 cudaError_t launch_backward_float(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch);
 cudaError_t launch_backward_double(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch);
+// Bounds-check status word of the stencil kernels of either precision
+// (checked build; read and cleared; 0 otherwise).
+int bounds_word_float();
+int bounds_word_double();
 
 }  // namespace pswf

@@ -31,6 +31,7 @@
 // together in time and their shared halo lines are reused from L2.
 #pragma once
 
+#include "bounds.cuh"
 #include "stencil.cuh"
 
 namespace pswf {
@@ -154,11 +155,12 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
   const int nitems = g.B * g.nts * nchunk;
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   const bool xeven = (g.M[0] & 1) == 0;
+  const int64_t grid_elems = int64_t(g.B) * g.K * chan;   // reals of the grid (checked build)
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int visit = item / nchunk, chunk = item - visit * nchunk;
     const int tile = tile_for_visit(g, visit);
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
-    if (a0 == a1) continue;
+    if (a0 == a1 || !in_bounds(a1 - 1, n, kBoundsTile) || !in_bounds(a0, n, kBoundsTile)) continue;
     const int sidx = tile / g.nts;
     const int c0 = chunk * 4, nk = min(4, g.K - c0);
     const int gc0 = sidx * g.K + c0;
@@ -186,7 +188,10 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
       for (int e = threadIdx.x; e < S * S * S; e += NT) {
         const int row = e / S, x = e - row * S;
         const int lz = row / S, ly = row - lz * S;
-        cp_async16(reg4 + row * R1 + x, g4 + zoff_s[lz] + yoff_s[ly] + gx_s[x]);
+        const int64_t srcq = zoff_s[lz] + yoff_s[ly] + gx_s[x];
+        if (in_bounds(row * R1 + x, L::ELEMS, kBoundsGatherStage) &&
+            in_bounds(int64_t(gc0 / 4) * chan + srcq, grid_elems / 4, kBoundsGatherGrid))
+          cp_async16(reg4 + row * R1 + x, g4 + srcq);
       }
       cp_async_wait_all();
     } else {
@@ -206,7 +211,9 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
             dsti[u] = row * R1 + x;
             const int gx = wrap_index(ox + x, g.M[0]);
             const int64_t off = wrap_index(oz + lz, g.M[2]) * plane + int64_t(wrap_index(oy + ly, g.M[1])) * g.Mxp;
-            if (xeven && gx + 1 < g.M[0]) {
+            if (!in_bounds(int64_t(gc0 + nk - 1) * chan + off + gx + 1, grid_elems, kBoundsGatherGrid)) {
+              dsti[u] = -1;
+            } else if (xeven && gx + 1 < g.M[0]) {
 #pragma unroll
               for (int c = 0; c < 4; ++c)
                 if (c < nk) pr[u][c] = __ldg(reinterpret_cast<const float2*>(gch + c * chan + off + gx));
@@ -221,6 +228,7 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (dsti[u] < 0) continue;
+          if (!in_bounds(dsti[u] + 1, L::ELEMS + 1, kBoundsGatherStage)) continue;
           reg4[dsti[u]] = make_float4(pr[u][0].x, pr[u][1].x, pr[u][2].x, pr[u][3].x);
           if ((dsti[u] % R1) + 1 < S) reg4[dsti[u] + 1] = make_float4(pr[u][0].y, pr[u][1].y, pr[u][2].y, pr[u][3].y);
         }
@@ -286,7 +294,11 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
       }
       int cx, cy, cz;
       unpack_cell(cell, cx, cy, cz);
-      const float4* row = reg4 + ((cz - oz) * S + (cy - oy) + jr) * R1 + (cx - ox);
+      int rbase = ((cz - oz) * S + (cy - oy) + jr) * R1 + (cx - ox);
+      if (!in_bounds(rbase, L::ELEMS, kBoundsGatherRegion) ||
+          !in_bounds(rbase + (P - 1) * R2 + (P - 1), L::ELEMS, kBoundsGatherRegion))
+        rbase = 0;   // checked build: read a valid place instead (the result is wrong, the status says so)
+      const float4* row = reg4 + rbase;
       float A[4] = {0, 0, 0, 0}, Az[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
 #pragma unroll
       for (int k = 0; k < P; ++k) {
@@ -343,8 +355,9 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
       }
       if (valid) {
         if (j < 4) {
-          if (phi && j < nk) phi[int64_t(c0 + j) * n + o] = v[0] + zshift;
-        } else if (j < 7 && forces) {
+          if (phi && j < nk && in_bounds(int64_t(c0 + j) * n + o, int64_t(g.K) * n, kBoundsGatherOut))
+            phi[int64_t(c0 + j) * n + o] = v[0] + zshift;
+        } else if (j < 7 && forces && in_bounds(3 * int64_t(o) + (j - 4), 3 * n, kBoundsGatherOut)) {
           float* fo = forces + 3 * int64_t(o) + (j - 4);
           if (nchunk == 1)
             *fo = v[0];
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
     const int visit = item / nchunk, chunk = item - visit * nchunk;
     const int tile = tile_for_visit(g, visit);
     const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
-    if (a0 == a1) continue;
+    if (a0 == a1 || !in_bounds(a1 - 1, nmax, kBoundsTile) || !in_bounds(a0, nmax, kBoundsTile)) continue;
     const int sidx = tile / g.nts;
     const int c0 = chunk * 4, nk = min(4, g.K - c0);
     const int gc0 = sidx * g.K + c0;
@@ -461,8 +474,10 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
       const float wy = __shfl_sync(0xffffffffu, w, 8 + jr);
       int cx, cy, cz;
       unpack_cell(cell, cx, cy, cz);
-      if (active) {
-        int* row = regi + cl * N + (cz - oz) * R2 + ((cy - oy) + j) * R1 + (cx - ox);
+      const int rb = cl * N + (cz - oz) * R2 + ((cy - oy) + j) * R1 + (cx - ox);
+      if (active && in_bounds(rb, 4 * N, kBoundsSpreadRegion) &&
+          in_bounds(rb + (P - 1) * R2 + (P - 1), 4 * N, kBoundsSpreadRegion)) {
+        int* row = regi + rb;
         const float qy = qv * qscale * wy;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
@@ -493,6 +508,9 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
         if (!has0) continue;
         for (int ly = half; ly < S; ly += 2) {
           float* rowg = base + yoff_s[ly];
+          if (!in_bounds(int64_t(c * N + lz * R2 + ly * R1 + x0 + (has1 ? 1 : 0)), 4 * N, kBoundsSpreadFlush) ||
+              !in_bounds((rowg - grid) + max(gx0, gx1), int64_t(g.B) * g.K * chan, kBoundsSpreadFlush))
+            continue;
           const int v0 = src[ly * R1 + x0];
           const int v1 = has1 ? src[ly * R1 + x0 + 1] : 0;
           if (pair) {

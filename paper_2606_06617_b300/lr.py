@@ -14,9 +14,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpswf_lr.so")
+# PSWF_LR_LIBRARY selects another build of the same library (for example
+# libpswf_lr_checked.so, the bounds-checked build the tests use)
+LIB_PATH = os.environ.get("PSWF_LR_LIBRARY") or os.path.join(_HERE, "libpswf_lr.so")
+LIB_CHECKED_PATH = os.path.join(_HERE, "libpswf_lr_checked.so")
 
 PSWF_ETIMEOUT = -5
+PSWF_EBOUNDS = -10
 PSWF_FLAG_BACKWARD = 1
 PSWF_FLAG_VIRIAL = 2
 PSWF_FLAG_REAL_SPACE = 4
