@@ -115,7 +115,10 @@ void pswf_opts_default(pswf_opts* o);
 int pswf_plan_params(const double box[3], int K, const int* p, const pswf_opts* opts, pswf_info* out);
 
 /* Creates a plan for up to n_max atoms on the current CUDA device: runs the
- * planner, builds the batched cuFFT plans (no cuFFT allocation) and records
+ * planner (the hyperparameters of "Parameter selection": c from the
+ * tolerance, grid spacing h <= eta pi / k_c with k_c = c / r_c, the stencil
+ * width P and window bandwidth c_w of "Accelerating atom-grid spreading with
+ * PSWFs"), builds the batched cuFFT plans (no cuFFT allocation) and records
  * the stream (a cudaStream_t, NULL = legacy default stream).  Device memory is
  * not allocated here: attach a workspace with pswf_plan_set_workspace, or the
  * first pswf_set_points allocates one (cudaMalloc) that the plan owns. */
@@ -147,7 +150,12 @@ int pswf_plan_set_workspace(pswf_plan plan, void* workspace, int64_t bytes);
 /* Changes the stream later calls enqueue on. */
 int pswf_plan_set_stream(pswf_plan plan, void* stream);
 
-/* Bins and sorts the atoms by grid tile (new positions and/or charges).
+/* Sets the input of step (i) of "Accelerating atom-grid spreading with
+ * PSWFs" (the atoms whose latent charges are spread onto the grid): bins and
+ * sorts the atoms by grid tile (new positions and/or charges), computes each
+ * atom's stencil start and window offsets (Eq. for W_pswf: P points per
+ * dimension around r / h), the per-channel charge sums used by the
+ * zero-frequency and self terms, and the spread's per-tile fixed-point units.
  * pos: device [n][3] float (pos_dtype 0) or double (pos_dtype 1), any real
  *   values (wrapped into the box);
  * q:   device [K][n] real latent charges.
@@ -202,7 +210,12 @@ int pswf_batch_set_points(pswf_plan plan, int b, const double* boxes, const int*
                           const void* pos, int pos_dtype, const void* q);
 
 /* Vector-Jacobian product of the last pswf_execute (asynchronous; needs
- * PSWF_FLAG_BACKWARD and the same points).  Upstream gradients, each may be
+ * PSWF_FLAG_BACKWARD and the same points): the derivatives the paper obtains
+ * by automatic differentiation of the long-range energy (forces, and the
+ * gradients that train the latent charges; Fig. 1 caption), written here as
+ * the exact adjoint of the discrete spread / transform / multiplier / gather
+ * operator: one more spread (of g_phi W and q g_F . grad W), transform pair
+ * and gather (with the Hessian of W for the force term).  Upstream gradients, each may be
  * NULL (= zero): g_energy device double [K] (d loss / d E_c), g_phi device
  * real [K][n], g_forces device real [n][3].  Outputs (may be NULL):
  * grad_q device real [K][n], grad_pos device real [n][3]. */
