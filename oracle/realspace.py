@@ -16,12 +16,9 @@ from .mollifiers import Mollifier
 f64 = torch.float64
 
 
-def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
-    """E_real = 1/2 sum_{|r_ij + n H| < r_c}' q_i q_j (1 - G_p(r)) / r^p over
-    the lattice n H (H: the cell's lattice vectors as rows; an orthorhombic
-    box given as three edge lengths is diag(box)).  Positions may lie
-    outside the cell.  Returns dict(E, phi [N], F [N,3])."""
-    moll = moll or Mollifier(c, r_c)
+def _pair_energy(pos, q, box, p: int, r_c: float, moll: Mollifier):
+    """(pos_t, q_t, E): the real-space energy of one channel as a torch FP64
+    graph in the (wrapped) positions and the charges, both requiring grad."""
     b = np.asarray(box, dtype=np.float64)
     H = np.diag(b) if b.shape == (3,) else b.reshape(3, 3)
     # The sum runs over every periodic image, so moving an atom by a lattice
@@ -54,12 +51,47 @@ def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None
         r = torch.sqrt((d * d).sum(-1))
         g = (1.0 - moll.G_torch(p, r)) / r ** p
         E = E + 0.5 * torch.sum(q_t[i0 + ii] * q_t[jj] * g)
+    return pos_t, q_t, E
+
+
+def real_space(pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):
+    """E_real = 1/2 sum_{|r_ij + n H| < r_c}' q_i q_j (1 - G_p(r)) / r^p over
+    the lattice n H (H: the cell's lattice vectors as rows; an orthorhombic
+    box given as three edge lengths is diag(box)).  Positions may lie
+    outside the cell.  Returns dict(E, phi [N], F [N,3])."""
+    moll = moll or Mollifier(c, r_c)
+    pos_t, q_t, E = _pair_energy(pos, q, box, p, r_c, moll)
+    N = pos_t.shape[0]
     if not E.requires_grad:
         return dict(E=0.0, phi=np.zeros(N), F=np.zeros((N, 3)))
     gpos, gq = torch.autograd.grad(E, (pos_t, q_t), allow_unused=True)
     gpos = torch.zeros_like(pos_t) if gpos is None else gpos
     gq = torch.zeros_like(q_t) if gq is None else gq
     return dict(E=float(E.detach()), phi=gq.numpy(), F=(-gpos).numpy())
+
+
+def real_space_vjp(pos, q, box, p: int, c: float, r_c: float, gE: float, gphi=None, gF=None,
+                   moll: Mollifier | None = None):
+    """Vector-Jacobian product of one channel's real-space outputs (E, phi =
+    dE/dq, F = -dE/dr): the gradients in q and in the positions of L = gE E
+    + sum_i gphi_i phi_i + sum_i gF_i . F_i, by differentiating the FP64
+    autograd graph of E twice (phi and F are themselves derivatives of E).
+    Returns (grad_q [N], grad_pos [N, 3])."""
+    moll = moll or Mollifier(c, r_c)
+    pos_t, q_t, E = _pair_energy(pos, q, box, p, r_c, moll)
+    N = pos_t.shape[0]
+    if not E.requires_grad:
+        return np.zeros(N), np.zeros((N, 3))
+    phi, gpos = torch.autograd.grad(E, (q_t, pos_t), create_graph=True)
+    L = float(gE) * E
+    if gphi is not None:
+        L = L + torch.sum(torch.as_tensor(np.asarray(gphi, dtype=np.float64)) * phi)
+    if gF is not None:
+        L = L - torch.sum(torch.as_tensor(np.asarray(gF, dtype=np.float64)) * gpos)
+    gq, gp = torch.autograd.grad(L, (q_t, pos_t), allow_unused=True)
+    gq = torch.zeros_like(q_t) if gq is None else gq
+    gp = torch.zeros_like(pos_t) if gp is None else gp
+    return gq.detach().numpy(), gp.detach().numpy()
 
 
 def real_space_atoms(idx, pos, q, box, p: int, c: float, r_c: float, moll: Mollifier | None = None):

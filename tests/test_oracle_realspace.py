@@ -16,6 +16,7 @@
 import math
 
 import numpy as np
+import pytest
 
 C = math.log(3.0 / 1e-5)
 
@@ -149,3 +150,40 @@ def test_real_space_cell_invariances():
     e2 = real_space(pos2, q2, U @ SHEARED, 2, C, 4.0, moll)
     assert abs(e1["E"] - e2["E"]) <= 1e-12 * abs(e1["E"])
     assert np.allclose(e1["F"], e2["F"], rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("p,cell", [(1, False), (6, False), (4, True)])
+def test_real_space_vjp_matches_finite_differences(p, cell):
+    """The oracle's VJP of the real-space outputs (double autograd) against
+    central differences of L = gE E + gphi . phi + gF . F built from the
+    forward outputs of real_space itself (a dropped term, a wrong sign or a
+    missing second-derivative term of the force fails it)."""
+    import math
+    from oracle.realspace import real_space, real_space_vjp
+    from paper_2606_06617_b300 import workloads as wl
+    s = wl.random_system(24, (7.0, 7.5, 8.0), (p,), seed=20 + p, neutral=False)
+    box = np.asarray(s.box)
+    if cell:
+        box = np.array([[7.0, 0.0, 0.0], [1.2, 7.5, 0.0], [-0.8, 0.9, 8.0]])
+    c, rc = math.log(3e5), 3.2
+    rng = np.random.default_rng(p)
+    gE, gphi, gF = 0.7, rng.normal(size=s.n), rng.normal(size=(s.n, 3))
+
+    def L(pos, q):
+        r = real_space(pos, q, box, p, c, rc)
+        return gE * r["E"] + float(np.dot(gphi, r["phi"])) + float(np.sum(gF * r["F"]))
+
+    gq, gp = real_space_vjp(s.pos, s.q[0], box, p, c, rc, gE, gphi, gF)
+    h = 1e-5
+    for k in (0, 5, 11):
+        qp, qm = s.q[0].copy(), s.q[0].copy()
+        qp[k] += h
+        qm[k] -= h
+        fd = (L(s.pos, qp) - L(s.pos, qm)) / (2 * h)
+        assert abs(fd - gq[k]) <= 1e-6 * max(1.0, abs(gq[k])), (k, fd, gq[k])
+        for d in range(3):
+            pp, pm = s.pos.copy(), s.pos.copy()
+            pp[k, d] += h
+            pm[k, d] -= h
+            fd = (L(pp, s.q[0]) - L(pm, s.q[0])) / (2 * h)
+            assert abs(fd - gp[k, d]) <= 1e-5 * max(1.0, abs(gp[k, d])), (k, d, fd, gp[k, d])
