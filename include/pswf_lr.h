@@ -305,6 +305,23 @@ int pswf_stress(pswf_plan plan, double* virial);
 int pswf_real_space(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q, double* energy,
                     void* phi, void* forces);
 
+/* Vector-Jacobian product of pswf_real_space's outputs (asynchronous; needs
+ * a preceding pswf_real_space on the same atoms, whose cell list it reuses):
+ * the gradients of L = sum_c g_energy_c E_c + sum g_phi * phi + sum g_forces
+ * . F through the pair term of "Implementation details", the derivatives the
+ * paper takes by automatic differentiation of the complete energy (Fig. 1
+ * caption), here per atom over its neighbours with G_p and its first two
+ * derivatives (the force term needs f_p'').
+ * pos, pos_dtype, q: the same inputs as that pswf_real_space call;
+ * upstream (each may be NULL = zero): g_energy device double [K], g_phi
+ * device real [K][n], g_forces device real [n][3];
+ * outputs (may be NULL, written, not accumulated): grad_q device real [K][n],
+ * grad_pos device real [n][3].
+ * PSWF_ESTATE without the preceding call (or for another atom count). */
+int pswf_real_space_backward(pswf_plan plan, int64_t n, const void* pos, int pos_dtype, const void* q,
+                             const double* g_energy, const void* g_phi, const void* g_forces, void* grad_q,
+                             void* grad_pos);
+
 /* Waits for the plan's stream and returns the first device-side status
  * raised since the last call (e.g. PSWF_ENONFINITE), clearing it. */
 int pswf_sync(pswf_plan plan);

@@ -306,6 +306,7 @@ struct pswf_plan_s {
   int64_t n_max = 0;
   int64_t n = -1;            // atoms of the last set_points (-1: none)
   bool psi_valid = false;    // grid holds Psi of the last execute (backward plans)
+  int64_t rs_n = -1;         // atoms of the last pswf_real_space (its cell list is kept)
   int flags = 0;
   bool batch = false;        // created by pswf_batch_plan_create
   int B = 1;                 // structures (slots)
@@ -1627,7 +1628,47 @@ int pswf_real_space(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, con
   const cudaError_t e = pl->real_size == 4 ? real_space_run<float>(a, pl->stream, &nl)
                                            : real_space_run<double>(a, pl->stream, &nl);
   pl->launches[PSWF_STAGE_REAL_SPACE] += nl;
-  return cuda_check(pl, e, "real space");
+  rc = cuda_check(pl, e, "real space");
+  pl->rs_n = rc ? -1 : n;
+  return rc;
+}
+
+int pswf_real_space_backward(pswf_plan pl, int64_t n, const void* pos, int pos_dtype, const void* q,
+                             const double* g_energy, const void* g_phi, const void* g_forces, void* grad_q,
+                             void* grad_pos) {
+  if (!pl) return PSWF_EINVAL;
+  if (!(pl->flags & PSWF_FLAG_REAL_SPACE))
+    return set_err(pl, PSWF_ESTATE, "plan was created without PSWF_FLAG_REAL_SPACE");
+  if (pl->rs_n < 0 || n != pl->rs_n)
+    return set_err(pl, PSWF_ESTATE, "pswf_real_space_backward needs a preceding pswf_real_space on the same atoms");
+  if (n > 0 && (!pos || !q)) return set_err(pl, PSWF_EINVAL, "pos and q are required");
+  if (pos_dtype != 0 && pos_dtype != 1) return set_err(pl, PSWF_EINVAL, "pos_dtype must be 0 (float) or 1 (double)");
+  if (!grad_q && !grad_pos) return PSWF_OK;
+  StageScope scope(pl, PSWF_STAGE_REAL_SPACE);
+  RealSpaceBwArgs a;
+  a.geo = pl->rs_geo;
+  a.n = n;
+  a.K = pl->host.K;
+  a.pos = pos;
+  a.pos_dtype = pos_dtype;
+  a.q = q;
+  a.pch = pl->pch;
+  a.coef_g = pl->coef_g;
+  a.deg_g = pl->host.deg_g;
+  a.cell_of = pl->rs_cellof;
+  a.cell_start = pl->rs_start;
+  a.perm = pl->rs_perm;
+  a.g_energy = g_energy;
+  a.g_phi = g_phi;
+  a.g_forces = g_forces;
+  a.grad_q = grad_q;
+  a.grad_pos = grad_pos;
+  a.err = pl->err;
+  int nl = 0;
+  const cudaError_t e = pl->real_size == 4 ? real_space_backward_run<float>(a, pl->stream, &nl)
+                                           : real_space_backward_run<double>(a, pl->stream, &nl);
+  pl->launches[PSWF_STAGE_REAL_SPACE] += nl;
+  return cuda_check(pl, e, "real space backward");
 }
 
 int pswf_sync(pswf_plan pl) { return pswf_sync_for(pl, -1.0); }

@@ -687,6 +687,203 @@ cudaError_t launch_direct(const RealSpaceArgs& a, cudaStream_t s) {
   }
 }
 
+// ---- backward of the real-space complement ------------------------------------
+// Vector-Jacobian product of (E_c, phi_i^c, F_i) for upstream (gE_c, gphi_i^c,
+// gF_i), summed per atom over its neighbours (each pair seen from both of its
+// atoms, so no atomics).  With d = r_i - r_j, r = |d|, f = f_p(r), h = -f'/r
+// and h' = dh/dr per channel:
+//   dL/dq_i^c = gE_c phi_i^c + sum_j gphi_j^c f + sum_j q_j^c h (gF_i - gF_j) . d
+//   dL/dr_i   = sum_j [ -sum_c (gE_c q_i^c q_j^c + gphi_i^c q_j^c + gphi_j^c q_i^c) h
+//                       + (w' / r) d . (gF_i - gF_j) ] d + w (gF_i - gF_j),
+//   w = sum_c q_i^c q_j^c h,  w' = sum_c q_i^c q_j^c h'
+// (the force term's Jacobian is w I + (w'/r) d d^T), so G_p is evaluated with
+// its first two derivatives.  One thread per atom; candidates from the 27
+// list cells around it (or, in direct mode, every atom and image).
+constexpr int kRsBwThreads = 128;
+
+template <typename R>
+struct RsBwAcc {
+  R phi, psi, tq;
+};
+
+template <typename R, int NC, int KC>
+__device__ inline void rs_bw_pair(const R (&d)[3], R r2, const R* __restrict__ cs, const int (&prow)[KC], R inv_rc,
+                                  const R (&qi)[KC], const R (&gpi)[KC], const R (&gEc)[KC], const R (&gFi)[3],
+                                  const R* qj, const R* gpj, const R (&gFj)[3], RsBwAcc<R> (&acc)[KC], R (&gr)[3]) {
+  const R inv_r = inv_sqrt(r2);
+  const R r = r2 * inv_r;
+  R x = r * inv_rc;
+  if (x >= R(1)) x = R(1) - R(1e-7);
+  int seg = int(x * R(kMultSeg));
+  if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+  const R sv = R(2) * (x * R(kMultSeg) - R(seg)) - R(1);
+  const R dsx = R(2 * kMultSeg) * inv_rc;   // d sv / d r
+  const R dg[3] = {gFi[0] - gFj[0], gFi[1] - gFj[1], gFi[2] - gFj[2]};
+  const R ddg = d[0] * dg[0] + d[1] * dg[1] + d[2] * dg[2];
+  R scal = 0, w = 0;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const R* cf = cs + (prow[c] * kMultSeg + seg) * NC;
+    R g0 = cf[NC - 1], g1 = 0, g2 = 0;   // G, G' and G'' / 2 in sv
+#pragma unroll
+    for (int k = NC - 2; k >= 0; --k) {
+      g2 = g2 * sv + g1;
+      g1 = g1 * sv + g0;
+      g0 = g0 * sv + cf[k];
+    }
+    const R Gr = g1 * dsx, Grr = R(2) * g2 * dsx * dsx;   // dG/dr, d2G/dr2
+    const int p = prow[c] + 1;
+    const R ir2 = inv_r * inv_r;
+    const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir2 * ir2 : R(1));
+    const R om = R(1) - g0;
+    const R f = om * rp;
+    const R f1 = -Gr * rp - R(p) * om * rp * inv_r;
+    const R f2 = -Grr * rp + R(2 * p) * Gr * rp * inv_r + R(p * (p + 1)) * om * rp * ir2;
+    const R h = -f1 * inv_r, h1 = -f2 * inv_r + f1 * ir2;
+    const R qq = qi[c] * qj[c];
+    acc[c].phi += qj[c] * f;
+    acc[c].psi += gpj[c] * f;
+    acc[c].tq += qj[c] * h * ddg;
+    scal += -(gEc[c] * qq + gpi[c] * qj[c] + gpj[c] * qi[c]) * h + qq * h1 * ddg * inv_r;
+    w += qq * h;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gr[k] += scal * d[k] + w * dg[k];
+}
+
+template <typename R, typename PosT, int NC, int KC>
+__global__ void __launch_bounds__(kRsBwThreads) k_rs_bw(RealSpaceBwArgs a) {
+  extern __shared__ __align__(16) unsigned char bw_smem[];
+  R* cs = reinterpret_cast<R*>(bw_smem);   // [6][kMultSeg][NC]
+  double* img = reinterpret_cast<double*>(bw_smem + (size_t(6) * kMultSeg * NC * sizeof(R) + 15) / 16 * 16);
+  const RealSpaceGeom& g = a.geo;
+  const R* coef = static_cast<const R*>(a.coef_g);
+  for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
+    const int k = t % NC, rs = t / NC;   // rs = row * kMultSeg + seg
+    cs[t] = k <= a.deg_g ? coef[size_t(rs) * (a.deg_g + 1) + k] : R(0);
+  }
+  const int nimages = g.direct ? (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1) : 0;
+  for (int t = threadIdx.x; t < nimages; t += blockDim.x) {
+    const int n0 = t % (2 * g.nimg[0] + 1) - g.nimg[0];
+    const int n1 = (t / (2 * g.nimg[0] + 1)) % (2 * g.nimg[1] + 1) - g.nimg[1];
+    const int n2 = t / ((2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1)) - g.nimg[2];
+    for (int k = 0; k < 3; ++k) img[3 * t + k] = n0 * g.h[k] + n1 * g.h[3 + k] + n2 * g.h[6 + k];
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t n = a.n;
+  const PosT* pos = static_cast<const PosT*>(a.pos);
+  const R* q = static_cast<const R*>(a.q);
+  const R* gphi = static_cast<const R*>(a.g_phi);
+  const R* gF = static_cast<const R*>(a.g_forces);
+  int prow[KC];
+  R qi[KC], gpi[KC], gEc[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    prow[c] = c < a.K ? a.pch[c] - 1 : 0;
+    qi[c] = c < a.K ? q[int64_t(c) * n + i] : R(0);
+    gpi[c] = (c < a.K && gphi) ? gphi[int64_t(c) * n + i] : R(0);
+    gEc[c] = (c < a.K && a.g_energy) ? R(a.g_energy[c]) : R(0);
+  }
+  const R gFi[3] = {gF ? gF[3 * i] : R(0), gF ? gF[3 * i + 1] : R(0), gF ? gF[3 * i + 2] : R(0)};
+  double xi[3];
+  wrapped(pos, i, g, xi, a.err);
+  const double rc2 = g.r_c * g.r_c;
+  const R inv_rc = R(1.0 / g.r_c);
+  RsBwAcc<R> acc[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) acc[c] = {R(0), R(0), R(0)};
+  R gr[3] = {0, 0, 0};
+  auto visit = [&](int64_t j, const double* shift) {
+    double xj[3];
+    wrapped(pos, j, g, xj, nullptr);
+    const double dd[3] = {xi[0] - xj[0] - shift[0], xi[1] - xj[1] - shift[1], xi[2] - xj[2] - shift[2]};
+    const double r2d = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+    if (!(r2d < rc2) || !(r2d > 0.0)) return;   // outside r_c, or the atom itself
+    const R d[3] = {R(dd[0]), R(dd[1]), R(dd[2])};
+    R qj[KC], gpj[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      qj[c] = c < a.K ? q[int64_t(c) * n + j] : R(0);
+      gpj[c] = (c < a.K && gphi) ? gphi[int64_t(c) * n + j] : R(0);
+    }
+    const R gFj[3] = {gF ? gF[3 * j] : R(0), gF ? gF[3 * j + 1] : R(0), gF ? gF[3 * j + 2] : R(0)};
+    rs_bw_pair<R, NC, KC>(d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], cs, prow, inv_rc, qi, gpi, gEc, gFi, qj, gpj,
+                          gFj, acc, gr);
+  };
+  if (g.direct) {
+    for (int64_t j = 0; j < n; ++j)
+      for (int t = 0; t < nimages; ++t) visit(j, img + 3 * t);
+  } else {
+    const int cell = a.cell_of[i];
+    const int ci[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
+    for (int o = 0; o < 27; ++o) {
+      int nb[3], wr[3];
+      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      for (int d = 0; d < 3; ++d) {
+        nb[d] = ci[d] + off[d];
+        wr[d] = nb[d] < 0 ? -1 : (nb[d] >= g.nc[d] ? 1 : 0);
+        nb[d] -= wr[d] * g.nc[d];
+      }
+      double shift[3];
+      for (int k = 0; k < 3; ++k) shift[k] = wr[0] * g.h[k] + wr[1] * g.h[3 + k] + wr[2] * g.h[6 + k];
+      const int c = (nb[2] * g.nc[1] + nb[1]) * g.nc[0] + nb[0];
+      for (int m = a.cell_start[c]; m < a.cell_start[c + 1]; ++m) visit(a.perm[m], shift);
+    }
+  }
+  R* gq = static_cast<R*>(a.grad_q);
+  R* gp = static_cast<R*>(a.grad_pos);
+#pragma unroll
+  for (int c = 0; c < KC; ++c)
+    if (c < a.K && gq) gq[int64_t(c) * n + i] = gEc[c] * acc[c].phi + acc[c].psi + acc[c].tq;
+  if (gp) {
+    gp[3 * i] = gr[0];
+    gp[3 * i + 1] = gr[1];
+    gp[3 * i + 2] = gr[2];
+  }
+}
+
+template <typename R, typename PosT, int NC, int KC>
+cudaError_t launch_bw_k(const RealSpaceBwArgs& a, cudaStream_t s) {
+  const RealSpaceGeom& g = a.geo;
+  const int nimages = g.direct ? (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1) : 0;
+  const size_t smem = (size_t(6) * kMultSeg * NC * sizeof(R) + 15) / 16 * 16 + size_t(nimages) * 3 * sizeof(double);
+  const cudaError_t ea =
+      cudaFuncSetAttribute(k_rs_bw<R, PosT, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (ea != cudaSuccess) return ea;
+  const int blocks = int((a.n + kRsBwThreads - 1) / kRsBwThreads);
+  k_rs_bw<R, PosT, NC, KC><<<blocks, kRsBwThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, typename PosT, int NC>
+cudaError_t launch_bw(const RealSpaceBwArgs& a, cudaStream_t s) {
+  switch (channel_class(a.K)) {
+    case 1: return launch_bw_k<R, PosT, NC, 1>(a, s);
+    case 2: return launch_bw_k<R, PosT, NC, 2>(a, s);
+    case 4: return launch_bw_k<R, PosT, NC, 4>(a, s);
+    case 8: return launch_bw_k<R, PosT, NC, 8>(a, s);
+    default: return launch_bw_k<R, PosT, NC, kRsMaxK>(a, s);
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t real_space_backward_run(const RealSpaceBwArgs& a, cudaStream_t s, int* nlaunch) {
+  if (a.n == 0) return cudaSuccess;
+  if (a.deg_g + 1 > 18) return cudaErrorInvalidValue;
+  cudaError_t e = a.pos_dtype == 1 ? launch_bw<R, double, 18>(a, s) : launch_bw<R, float, 18>(a, s);
+  if (e == cudaSuccess) ++*nlaunch;
+  return e;
+}
+
+template cudaError_t real_space_backward_run<float>(const RealSpaceBwArgs&, cudaStream_t, int*);
+template cudaError_t real_space_backward_run<double>(const RealSpaceBwArgs&, cudaStream_t, int*);
+
+namespace {
+
 __global__ void k_rs_total(int K, double* __restrict__ energy) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double t = 0.0;

@@ -72,4 +72,30 @@ struct RealSpaceArgs {
 template <typename R>
 cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch);
 
+// Backward of the real-space complement (see realspace.cu): needs the cell
+// list of a preceding real_space_run on the same points (cell-list mode).
+struct RealSpaceBwArgs {
+  RealSpaceGeom geo;
+  int64_t n;
+  int K;
+  const void* pos;      // [n][3], float or double (pos_dtype 0 / 1)
+  int pos_dtype;
+  const void* q;        // real [K][n]
+  const int* pch;       // device [K] exponents
+  const void* coef_g;   // device real [6][kMultSeg][deg_g + 1]
+  int deg_g;
+  const int* cell_of;     // [n] list cell of each atom (cell-list mode)
+  const int* cell_start;  // [ncell + 1]
+  const int* perm;        // [n] original index of each sorted slot
+  const double* g_energy; // device [K] or null
+  const void* g_phi;      // real [K][n] or null
+  const void* g_forces;   // real [n][3] or null
+  void* grad_q;           // real [K][n] or null (written, not accumulated)
+  void* grad_pos;         // real [n][3] or null (written, not accumulated)
+  int* err;
+};
+
+template <typename R>
+cudaError_t real_space_backward_run(const RealSpaceBwArgs& a, cudaStream_t s, int* nlaunch);
+
 }  // namespace pswf

@@ -92,6 +92,7 @@ SIGNATURES = {
     "pswf_virial": ([_vp, _vp], ctypes.c_int),
     "pswf_stress": ([_vp, _vp], ctypes.c_int),
     "pswf_real_space": ([_vp, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "pswf_real_space_backward": ([_vp, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pswf_sync": ([_vp], ctypes.c_int),
     "pswf_sync_for": ([_vp, ctypes.c_double], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
@@ -338,10 +339,46 @@ class Plan:
             phi = torch.empty(self.K, n, dtype=self.dtype, device=self.device)
             forces = torch.empty(n, 3, dtype=self.dtype, device=self.device)
         self._stream()
+        self.rs_generation = getattr(self, "rs_generation", 0) + 1
         pdt = 1 if pos.dtype == torch.float64 else 0
         _check(lib().pswf_real_space(self._h, n, _vp(pos.data_ptr()), pdt, _vp(q.data_ptr()),
                                      _vp(energy.data_ptr()), _vp(phi.data_ptr()), _vp(forces.data_ptr())), self._h)
         return energy, phi, forces
+
+    def real_space_backward(self, pos, q, g_energy=None, g_phi=None, g_forces=None, grad_q: bool = True,
+                            grad_pos: bool = True):
+        """VJP of the last real_space call's (energy, phi, forces) on the same
+        pos and q: returns (grad_q [K, n] or None, grad_pos [n, 3] or None)
+        for upstream g_energy [K] (float64), g_phi [K, n], g_forces [n, 3]
+        (device tensors, each may be None)."""
+        import torch
+        n = int(pos.shape[0])
+        pos = pos.contiguous()
+        q = q.to(self.dtype).contiguous()
+        gq = torch.empty(self.K, n, dtype=self.dtype, device=self.device) if grad_q else None
+        gr = torch.empty(n, 3, dtype=self.dtype, device=self.device) if grad_pos else None
+        ge = g_energy.to(torch.float64).contiguous() if g_energy is not None else None
+        gp = g_phi.to(self.dtype).contiguous() if g_phi is not None else None
+        gf = g_forces.to(self.dtype).contiguous() if g_forces is not None else None
+        ptr = lambda t: _vp(t.data_ptr() if (t is not None and t.numel() > 0) else 0)
+        self._stream()
+        pdt = 1 if pos.dtype == torch.float64 else 0
+        _check(lib().pswf_real_space_backward(self._h, n, ptr(pos), pdt, ptr(q), ptr(ge), ptr(gp), ptr(gf), ptr(gq),
+                                              ptr(gr)), self._h)
+        return gq, gr
+
+    def self_coefficients(self, q):
+        """s_c with E_self^(c) = s_c sum_i (q_i^c)^2 (device float64 [K]),
+        from the device self energies of charges q [K, n] (the plan's
+        noalloc entry point, so nothing is allocated on the plan's side)."""
+        import torch
+        qd = q.to(self.dtype).contiguous()
+        ones = torch.ones(self.K, 1, dtype=self.dtype, device=self.device)
+        out = torch.empty(self.K, dtype=torch.float64, device=self.device)
+        self._stream()
+        _check(lib().pswf_self_energy_noalloc(self._h, 1, _vp(ones.data_ptr()), _vp(out.data_ptr()),
+                                              _vp(torch.cuda.current_stream(self.device).cuda_stream)), self._h)
+        return out   # one unit charge per channel: E_self = s_c
 
     def self_energy(self) -> np.ndarray:
         out = (ctypes.c_double * self.K)()
@@ -625,7 +662,50 @@ def _make_function():
             gq = gq.to(ctx.q_dtype) if gq is not None else None
             return gr, gq, None
 
-    return _LongRange
+    class _Complete(torch.autograd.Function):
+        """(pos [n,3], q [K,n]) -> the complete sum per channel (E_total [K],
+        phi_total [K,n], F_total [n,3]): reciprocal part (pswf_execute) +
+        real-space complement (pswf_real_space) - self energy, with the
+        backward through pswf_backward, pswf_real_space_backward and the
+        self term E_self_c = s_c sum_i (q_i^c)^2."""
+
+        @staticmethod
+        def forward(ctx, pos, q, plan):
+            pd, qd = pos.detach().contiguous(), q.detach().to(plan.dtype).contiguous()
+            plan.set_points(pd, qd)
+            e_k, ph_k, f_k = plan.execute()
+            e_r, ph_r, f_r = plan.real_space(pd, qd)
+            s = plan.self_coefficients(qd)
+            qq = qd.to(torch.float64)
+            E = e_k[:-1] + e_r[:-1] - s * (qq * qq).sum(1)
+            phi = ph_k + ph_r - (2.0 * s[:, None] * qq).to(ph_k.dtype)
+            ctx.plan, ctx.gen, ctx.rs_gen = plan, plan.generation, plan.rs_generation
+            ctx.pos_dtype, ctx.q_dtype = pos.dtype, q.dtype
+            ctx.save_for_backward(pd, qd, s)
+            return E, phi, f_k + f_r
+
+        @staticmethod
+        @torch.autograd.function.once_differentiable
+        def backward(ctx, g_e, g_phi, g_f):
+            plan = ctx.plan
+            if plan.generation != ctx.gen or plan.rs_generation != ctx.rs_gen:
+                raise PswfError(-8, "the plan was re-run since this forward; its backward state is gone")
+            pd, qd, s = ctx.saved_tensors
+            need_q, need_pos = ctx.needs_input_grad[1], ctx.needs_input_grad[0]
+            if not (need_q or need_pos):
+                return None, None, None
+            gq, gr = plan.backward(g_e, g_phi, g_f, grad_q=need_q, grad_pos=need_pos)
+            gq_r, gr_r = plan.real_space_backward(pd, qd, g_e, g_phi, g_f, grad_q=need_q, grad_pos=need_pos)
+            if need_q:
+                ge = g_e if g_e is not None else torch.zeros_like(s)
+                gself = 2.0 * s[:, None] * (ge[:, None] * qd.to(torch.float64)
+                                            + (g_phi.to(torch.float64) if g_phi is not None else 0.0))
+                gq = (gq.to(torch.float64) + gq_r.to(torch.float64) - gself).to(ctx.q_dtype)
+            if need_pos:
+                gr = (gr + gr_r).to(ctx.pos_dtype)
+            return gr, gq, None
+
+    return _LongRange, _Complete
 
 
 _FN = None
@@ -643,4 +723,21 @@ def long_range(plan: "Plan", pos, q):
         _FN = _make_function()
     if not (plan.flags & PSWF_FLAG_BACKWARD):
         raise PswfError(-8, "long_range needs a plan created with flags=PSWF_FLAG_BACKWARD")
-    return _FN.apply(pos, q, plan)
+    return _FN[0].apply(pos, q, plan)
+
+
+def complete_sum(plan: "Plan", pos, q):
+    """Differentiable complete lattice sum per channel (Methods,
+    "Implementation details": reciprocal part + real-space complement -
+    self energy): returns (E [K] float64, phi [K, n], forces [n, 3]) with
+    gradients to pos and q through the plan's backward kernels and the
+    real-space backward.  The plan needs flags PSWF_FLAG_BACKWARD |
+    PSWF_FLAG_REAL_SPACE; calls on one plan are sequential (generation
+    counters guard the pending backward)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    need = PSWF_FLAG_BACKWARD | PSWF_FLAG_REAL_SPACE
+    if (plan.flags & need) != need:
+        raise PswfError(-8, "complete_sum needs a plan created with PSWF_FLAG_BACKWARD | PSWF_FLAG_REAL_SPACE")
+    return _FN[1].apply(pos, q, plan)
