@@ -108,18 +108,20 @@ def algorithmic_bytes(w, K: int, n: int, rs: int = 4) -> dict:
 
 def real_space_flops(w, K: int, n: int, deg: int) -> dict:
     """Algorithmic FP32 operations of one real-space launch at the
-    workload's uniform density (expected counts): every candidate in the 27
-    cells of width >= r_c around an atom is tested (8 flops: 3 differences,
-    a square norm), and every ordered pair closer than r_c is evaluated once
-    from each end: displacement, 1/r and the piece coordinate (25 flops),
-    then per channel the two Horner chains of G_p and G_p' (4 deg), r^-p,
-    the potential and force terms (13)."""
+    workload's uniform density (expected counts), each pair evaluated once:
+    every candidate of an atom's half shell (the 13 neighbour cells of width
+    >= r_c on one side and the later atoms of its own cell: 13.5 cells on
+    average) is tested (8 flops: 3 differences, a square norm), and every
+    pair closer than r_c is evaluated: displacement, 1/r and the piece
+    coordinate (25 flops), the force on both atoms (3), then per channel the
+    two Horner chains of G_p and G_p' (4 deg), r^-p, the potential terms of
+    both atoms and the force term (14)."""
     L, rc = w["L"], w["r_c"]
     nc = int(L // rc)
     rho = n / L ** 3
-    cand = n * 27 * n / nc ** 3
-    pairs = n * rho * 4.0 / 3.0 * math.pi * rc ** 3
-    flops = cand * 8 + pairs * (25 + K * (4 * deg + 13))
+    cand = n * 13.5 * n / nc ** 3
+    pairs = n * rho * 4.0 / 3.0 * math.pi * rc ** 3 / 2.0
+    flops = cand * 8 + pairs * (28 + K * (4 * deg + 14))
     return {"candidates": cand, "pairs": pairs, "flops": flops}
 
 
@@ -370,7 +372,7 @@ def run_total(steps: int, warmup: int, cpu_baseline: bool = True, wk: str = "mel
                    "grid": info["grid"], "P": info["P"], "r_c": w["r_c"], "c": info["c"], "c_w": info["c_w"],
                    "tol": w["tol"],
                    "l2": f"inputs larger than L2 (grid {4 * K * w['grid'] ** 3 / 1e9:.2f} GB, "
-                         f"real-space records {s.n * 48 / 1e9:.2f} GB)",
+                         f"real-space records and rows {s.n * 80 / 1e9:.2f} GB)",
                    "parallelism": "single GPU"},
         "roofline": {"bound": "alu", "kernel": "real_space (k_rs_pairs)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,

@@ -546,7 +546,7 @@ int64_t layout(pswf_plan p, char* base) {
     p->rs_rank = reinterpret_cast<int*>(take(nm * 4));
     p->rs_perm = reinterpret_cast<int*>(take(nm * 4));
     p->rs_scan = reinterpret_cast<int*>(take(int64_t(p->rs_nsb) * 4));
-    p->rs_lpos = take(int64_t(real_space_bytes_per_atom(K, int(rs))) * nm);   // test coordinates, records
+    p->rs_lpos = take(int64_t(real_space_bytes_per_atom(K, int(rs))) * nm);   // test coordinates, records, rows
   }
   {
     int64_t tw_pairs = 0;
@@ -1696,6 +1696,7 @@ int pswf_sync_for(pswf_plan pl, double timeout_ms) {
     int bw = take_bounds_word();
     if (!bw) bw = bounds_word_float();
     if (!bw) bw = bounds_word_double();
+    if (!bw) bw = bounds_word_real_space();
     if (bw)
       return set_err(pl, PSWF_EBOUNDS, "kernel index out of its buffer (bounds check " + std::to_string(bw) + ")");
   }

@@ -42,6 +42,9 @@ enum BoundsCode : int {
   kBoundsSpreadFlush = 6,     // spread: region read or grid write of the flush
   kBoundsScatter = 7,         // set_points: sorted position out of range
   kBoundsTile = 8,            // a tile's atom range outside the sorted arrays
+  kBoundsRsScatter = 9,       // real space: sorted position out of range
+  kBoundsRsPair = 10,         // real space: a queued neighbour or pair atom outside the sorted arrays
+  kBoundsRsFinish = 11,       // real space: original index out of range
 };
 
 }  // namespace pswf

@@ -17,18 +17,26 @@
 // scanned, and scattered in cell order with their charges.
 //
 // Pair kernel: persistent blocks of 8 warps, one warp per list cell at a
-// time, its atoms in chunks of up to 32.  A chunk of m atoms gives each atom
-// G = 32 / m lanes (a power of two), which split the 27 neighbour cells'
-// candidates, so partial chunks keep the lanes busy.  Each lane tests its
-// candidates against r_c (about 15% pass in a liquid) and appends the ones
-// inside to its own queue in shared memory (16-bit entries: neighbour and
-// index in that cell); after the 27 neighbours the queues are drained in
-// rounds in which every lane evaluates one of its queued pairs, so the
-// mollifier polynomials run on dense rounds rather than on the few lanes
-// whose candidate happens to pass, and draining once per sweep keeps the
-// lanes' queue lengths (their atoms' pair counts) close.  Per-atom sums stay
-// in registers (no atomics); the G lanes of an atom are summed with shuffles
-// at the end.
+// time, its atoms in chunks of up to 32.  Each pair is evaluated once: a
+// chunk's atoms i take as candidates the atoms of the half shell, the 13
+// neighbour cells o with (oz, oy, ox) lexicographically positive and the
+// cell itself with j > i in cell order (the other 13 neighbours pair with
+// this cell from their own half shell).  A chunk of m atoms gives each atom
+// G = 32 / m lanes (a power of two), which split the candidates, so partial
+// chunks keep the lanes busy.  Each lane tests its candidates against r_c
+// (about 15% pass in a liquid) and appends the ones inside to its own queue
+// in shared memory (16-bit entries: half-shell slot and index in that
+// cell).  After the sweep the queues are drained: their entries, taken in
+// lane order, are cut into 32 ranges of equal length, so every lane
+// evaluates the same number of pairs however the atoms' pair counts differ
+// (a half shell's counts depend strongly on where the atom sits in its
+// cell).  The i side of a pair stays in registers while a lane's range
+// stays in one atom's queue and is then added to the atom's accumulator
+// row; the j side (phi_j^c += q_i^c f_p, F_j -= F_ij) is added to j's row
+// at once, with 16-byte vector atomics in FP32.  The rows are kept in cell
+// order and copied to the caller's layouts by a last kernel; the channel
+// energies are the sums of q_i^c phi_i^c over the evaluated side, kept per
+// warp and added to the FP64 totals once per warp.
 //
 // Coordinates: the cutoff test reads Cartesian coordinates from the list
 // cell's corner in the plan's precision (16 or 32 bytes per atom, streamed
@@ -64,14 +72,20 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kFixBits = 29;     // FP32 plans: cell-local unit w / 2^29; |dx| <= 2^30
 constexpr int kQueueCap = 192;   // queued pairs per lane; drained early only above kQueueCap - 32
 constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 97 words, so lanes start in distinct banks
-constexpr int kCellBits = 11;    // queue entry: (neighbour o << 11) | index within that cell
+constexpr int kCellBits = 11;    // queue entry: (half-shell slot << 11) | index within that cell
 constexpr int kMaxCellAtoms = 1 << kCellBits;
+// half shell: neighbour offsets o = (ox + 1) + 3 (oy + 1) + 9 (oz + 1) from
+// kSelf (the cell itself, o = (0, 0, 0)) to 26, i.e. (oz, oy, ox)
+// lexicographically >= 0: slot s is offset kSelf + s
+constexpr int kSelf = 13;
+constexpr int kHalf = 14;
 
 template <typename R>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-  // queue [32][kQueueStride] of 16-bit entries, stage [32][4] R, neighbour
-  // starts and ends [2][27] (padded to 224 bytes)
-  return size_t(32) * kQueueStride * 2 + 32 * 4 * sizeof(R) + 224;
+  // queue [32][kQueueStride] of 16-bit entries, stage [32][4] R, channel
+  // energies double [16], half-shell starts and ends [2][14] and queue
+  // offsets [33] int (padded to 384 bytes)
+  return size_t(32) * kQueueStride * 2 + 32 * 4 * sizeof(R) + 384;
 }
 static_assert(warp_smem_bytes<float>() % 16 == 0 && warp_smem_bytes<double>() % 16 == 0, "aligned warp regions");
 
@@ -98,6 +112,13 @@ __host__ __device__ constexpr int rec_words() {
   return (3 + KC + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
 }
 
+// accumulator row (cell order): KC potentials, 3 force components, zero
+// padding to whole 16-byte vectors
+template <typename R, int KC>
+__host__ __device__ constexpr int acc_words() {
+  return (KC + 3 + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
+}
+
 int channel_class(int K) { return K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : kRsMaxK; }
 
 template <typename R>
@@ -122,6 +143,33 @@ __device__ inline void load_words(const R* __restrict__ p, R (&v)[W]) {
       v[k] = x.x;
       v[k + 1] = x.y;
     }
+  }
+}
+
+// row += (p_0 .. p_{KC-1}, fx, fy, fz): FP32 as 16-byte vector atomics,
+// FP64 one atomic per word (channels past K skipped)
+template <typename R, int KC>
+__device__ inline void add_row(R* row, const R (&p)[KC], R fx, R fy, R fz, int K) {
+  constexpr int AW = acc_words<R, KC>();
+  if constexpr (std::is_same<R, float>::value) {
+    float v[AW];
+#pragma unroll
+    for (int w = 0; w < AW; ++w) v[w] = 0.f;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) v[c] = p[c];
+    v[KC] = fx;
+    v[KC + 1] = fy;
+    v[KC + 2] = fz;
+#pragma unroll
+    for (int w = 0; w < AW; w += 4)
+      atomicAdd(reinterpret_cast<float4*>(row + w), make_float4(v[w], v[w + 1], v[w + 2], v[w + 3]));
+  } else {
+#pragma unroll
+    for (int c = 0; c < KC; ++c)
+      if (c < K) atomicAdd(row + c, p[c]);
+    atomicAdd(row + KC, fx);
+    atomicAdd(row + KC + 1, fy);
+    atomicAdd(row + KC + 2, fz);
   }
 }
 
@@ -152,15 +200,17 @@ __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom 
 }
 
 // cell-local test coordinates [nmax][4] and records [nmax][rw] (exact
-// coordinates, charges), and the original index
+// coordinates, charges), the original index, and zeroed accumulator rows
+// [nmax][aw] (acc may be null)
 template <typename PosT, typename R>
 __global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ pos, const R* __restrict__ q,
                              RealSpaceGeom g, const int* __restrict__ cell_of, const int* __restrict__ rank,
                              const int* __restrict__ cell_start, R* __restrict__ lchk, R* __restrict__ rec,
-                             int* __restrict__ perm) {
+                             int* __restrict__ perm, R* __restrict__ acc, int aw) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int cell = cell_of[i];
     const int64_t dst = int64_t(cell_start[cell]) + rank[i];
+    if (!in_bounds(dst, n, kBoundsRsScatter)) continue;
     int ci[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
     R* r = rec + dst * rw;
     double x[3];
@@ -191,6 +241,10 @@ __global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ 
     }
     for (int w = 3; w < rw; ++w) r[w] = w - 3 < K ? q[int64_t(w - 3) * n + i] : R(0);
     perm[dst] = int(i);
+    if (acc) {
+      const R z[kPerVec<R>] = {};
+      for (int w = 0; w < aw; w += kPerVec<R>) store_vec<R>(acc + dst * aw + w, z);
+    }
   }
 }
 
@@ -206,8 +260,7 @@ struct PairArgs {
   const int* pch;
   const R* coef;     // [6][kMultSeg][deg + 1]
   double* energy;
-  R* phi;
-  R* forces;
+  R* acc;            // [nmax][acc_words] zeroed, or null (energies only)
   int* err;
 };
 
@@ -241,21 +294,26 @@ __device__ inline void coords(const R* v, typename LocalT<R>::type& x, typename 
 // zero charges); NC coefficients per mollifier piece (zero-padded).  The
 // coefficient table in shared memory is [exponent][vector][piece] of
 // 16-byte vectors, so lanes on different pieces read different banks.
+// a.acc == nullptr: energies only (no accumulator rows).
 template <typename R, int NC, int KC, bool TRIC>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
   constexpr int RW = rec_words<R, KC>();
+  constexpr int AW = acc_words<R, KC>();
   constexpr int NV = NC / kPerVec<R>;
   extern __shared__ __align__(16) unsigned char rs_smem[];
   Vec<R>* coefv = reinterpret_cast<Vec<R>*>(rs_smem);            // [6][NV][kMultSeg]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  R* shv = reinterpret_cast<R*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [27][4] neighbour shifts
-  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + 27 * 4 * sizeof(R) +
+  R* shv = reinterpret_cast<R*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [kHalf][4] neighbour shifts
+  unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) +
                          size_t(warp) * warp_smem_bytes<R>();
-  uint16_t* queue = reinterpret_cast<uint16_t*>(wbase) + lane * kQueueStride;   // this lane's column
+  uint16_t* queues = reinterpret_cast<uint16_t*>(wbase);                        // [32][kQueueStride]
+  uint16_t* queue = queues + lane * kQueueStride;                               // this lane's column
   R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);               // [32][4] candidates
-  int* nbs = reinterpret_cast<int*>(stage + 32 * 4);                            // [27] neighbour cell starts
-  int* nbe = nbs + 27;                                                          // [27] ends
+  double* esum = reinterpret_cast<double*>(stage + 32 * 4);                     // [kRsMaxK] channel energies
+  int* nbs = reinterpret_cast<int*>(esum + kRsMaxK);                            // [kHalf] neighbour starts
+  int* nbe = nbs + kHalf;                                                       // [kHalf] ends
+  int* pref = nbe + kHalf;                                                      // [33] queue offsets
   {
     R* cs = reinterpret_cast<R*>(rs_smem);
     for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
@@ -267,13 +325,14 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
     }
     // the neighbour o's corner relative to a cell's corner: o . (a_d / n_c)
     // (list cells are congruent, so also across the periodic boundary)
-    if (threadIdx.x < 27) {
-      const int o = threadIdx.x;
+    if (threadIdx.x < kHalf) {
+      const int o = kSelf + threadIdx.x;
       const double od[3] = {double(o % 3 - 1), double((o / 3) % 3 - 1), double(o / 9 - 1)};
       for (int k = 0; k < 3; ++k)
-        shv[4 * o + k] = R(od[0] * a.g.cw[k] + od[1] * a.g.cw[3 + k] + od[2] * a.g.cw[6 + k]);
-      shv[4 * o + 3] = R(0);
+        shv[4 * threadIdx.x + k] = R(od[0] * a.g.cw[k] + od[1] * a.g.cw[3 + k] + od[2] * a.g.cw[6 + k]);
+      shv[4 * threadIdx.x + 3] = R(0);
     }
+    if (lane < kRsMaxK) esum[lane] = 0.0;
   }
   __syncthreads();
 
@@ -288,6 +347,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   int prow[KC];
 #pragma unroll
   for (int c = 0; c < KC; ++c) prow[c] = c < a.K ? a.pch[c] - 1 : 0;
+  R* const accp = a.acc;
 
   for (int cell = blockIdx.x * kRsWarps + warp; cell < ncell; cell += gridDim.x * kRsWarps) {
     const int c3[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
@@ -309,19 +369,13 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         else
           zi = a.lchk[4 * int64_t(i) + 2];
       }
-      R ri[RW];
-      load_words<R, RW>(a.rec + int64_t(i) * RW, ri);
-      L ix, iy, iz;
-      coords<R>(ri, ix, iy, iz);
-      R ph[KC];
-#pragma unroll
-      for (int c = 0; c < KC; ++c) ph[c] = R(0);
-      R fx = 0, fy = 0, fz = 0;
       int len = 0;
 
-      // the 27 neighbour cells' atom ranges, one lane each
-      if (lane < 27) {
-        const int od[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      // the half shell's atom ranges, one lane each; the cell itself from
+      // this chunk on (earlier atoms pair with it from their own chunk)
+      if (lane < kHalf) {
+        const int o = kSelf + lane;
+        const int od[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
         // cells are equal (width L / n_c), so the neighbour's corner is o w
         // from this cell's corner whether or not its index wraps
         int nc3[3];
@@ -336,111 +390,178 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           atomicCAS(a.err, 0, PSWF_ECELL);
           b1 = b0;
         }
+        if (lane == 0 && b1 > b0) b0 = base;
         nbs[lane] = b0;
         nbe[lane] = b1;
       }
       __syncwarp();
 
-      // every queued pair of this lane: exact displacement, f_p and f_p'
+      // Balanced drain: the 32 lanes' queues, concatenated in lane order,
+      // are cut into 32 ranges of equal length, one per lane.  A lane walks
+      // its range in order, crossing from one queue (one atom i) to the
+      // next; the i side of the pairs stays in registers until it crosses,
+      // and is then added to i's accumulator row.  The j side goes to j's
+      // row with vector atomics at once.
       auto drain = [&]() {
-        // software-pipelined: round t + 1's record is fetched while round t
-        // is evaluated (the records come from L2; their latency dominated)
-        R rn[RW];
-        int on = 0;
-        if (len > 0) {
-          const uint32_t e = queue[0];
-          on = int(e >> kCellBits);
-          load_words<R, RW>(a.rec + int64_t(nbs[on] + int(e & (kMaxCellAtoms - 1))) * RW, rn);
+        int incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += v;
         }
-        for (int t = 0; t < len; ++t) {
-          R rj[RW];
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        pref[lane + 1] = incl;
+        if (lane == 0) pref[0] = 0;
+        __syncwarp();
+        const int e0 = (lane * total) >> 5, e1 = ((lane + 1) * total) >> 5;
+        if (e0 < e1) {
+          int mo = 0;   // the queue holding entry e0: the last one starting at or before it
 #pragma unroll
-          for (int w = 0; w < RW; ++w) rj[w] = rn[w];
-          const int o = on;
-          if (t + 1 < len) {
-            const uint32_t e = queue[t + 1];
-            on = int(e >> kCellBits);
-            load_words<R, RW>(a.rec + int64_t(nbs[on] + int(e & (kMaxCellAtoms - 1))) * RW, rn);
-          }
-          const int o3 = o / 3;
-          const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
-          L jx, jy, jz;
-          coords<R>(rj, jx, jy, jz);
-          R du0, du1, du2;   // displacement in list-cell units
-          if constexpr (std::is_same<R, float>::value) {
-            du0 = __int2float_rn(jx + ox * (1 << kFixBits) - ix);
-            du1 = __int2float_rn(jy + oy * (1 << kFixBits) - iy);
-            du2 = __int2float_rn(jz + oz * (1 << kFixBits) - iz);
-          } else {
-            du0 = jx + ox - ix;
-            du1 = jy + oy - iy;
-            du2 = jz + oz - iz;
-          }
-          R dx, dy, dz;
-          if constexpr (TRIC) {
-            dx = du0 * ew[0] + du1 * ew[3] + du2 * ew[6];
-            dy = du0 * ew[1] + du1 * ew[4] + du2 * ew[7];
-            dz = du0 * ew[2] + du1 * ew[5] + du2 * ew[8];
-          } else {
-            dx = du0 * ew[0];
-            dy = du1 * ew[4];
-            dz = du2 * ew[8];
-          }
-          const R r2 = dx * dx + dy * dy + dz * dz;
-          // atoms within one fixed-point step of each other (their FP32 test
-          // coordinates may still differ) count as coincident: excluded
-          if (!(r2 > R(0))) continue;
-          const R inv_r = inv_sqrt(r2);
-          const R r = r2 * inv_r;
-          const R ir2 = inv_r * inv_r, ir4 = ir2 * ir2;
-          R x = r * inv_rc;
-          if (x >= R(1)) x = R(1) - R(1e-7);
-          int seg = int(x * R(kMultSeg));
-          if (seg > kMultSeg - 1) seg = kMultSeg - 1;
-          const R sv = R(2) * (x * R(kMultSeg) - R(seg)) - R(1);
-          R fsum = 0;   // sum_c q_i^c q_j^c f_p'(r)
+          for (int step = 16; step > 0; step >>= 1)
+            if (pref[mo + step] <= e0) mo += step;
+          int t = e0 - pref[mo], tend = pref[mo + 1] - pref[mo];
+          int io = base + mo / G;
+          io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;   // checked build: a bad index reads row 0
+          R ro[RW];
+          load_words<R, RW>(a.rec + int64_t(io) * RW, ro);
+          L ix, iy, iz;
+          coords<R>(ro, ix, iy, iz);
+          R ph[KC];
 #pragma unroll
-          for (int c = 0; c < KC; ++c) {
-            R cf[NC];
+          for (int c = 0; c < KC; ++c) ph[c] = R(0);
+          R fx = 0, fy = 0, fz = 0;
+          // software-pipelined: the next entry's record is fetched while the
+          // current pair is evaluated (the records come from L2)
+          uint32_t en = queues[mo * kQueueStride + t];
+          int jn = nbs[en >> kCellBits] + int(en & (kMaxCellAtoms - 1));
+          jn = in_bounds(jn, a.n, kBoundsRsPair) ? jn : 0;
+          R rn[RW];
+          load_words<R, RW>(a.rec + int64_t(jn) * RW, rn);
+          for (int e = e0; e < e1; ++e) {
+            R rj[RW];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              const Vec<R> cv = coefv[(prow[c] * NV + v) * kMultSeg + seg];
-              if constexpr (std::is_same<R, float>::value) {
-                cf[4 * v] = cv.x;
-                cf[4 * v + 1] = cv.y;
-                cf[4 * v + 2] = cv.z;
-                cf[4 * v + 3] = cv.w;
-              } else {
-                cf[2 * v] = cv.x;
-                cf[2 * v + 1] = cv.y;
+            for (int w = 0; w < RW; ++w) rj[w] = rn[w];
+            const int j = jn;
+            const int o = kSelf + int(en >> kCellBits);
+            const bool more = e + 1 < e1;
+            int mn = mo, tn = t + 1;
+            if (more) {
+              if (tn == tend) {   // on to the next non-empty queue
+                do {
+                  ++mn;
+                } while (pref[mn + 1] == pref[mn]);
+                tn = 0;
+              }
+              en = queues[mn * kQueueStride + tn];
+              jn = nbs[en >> kCellBits] + int(en & (kMaxCellAtoms - 1));
+              jn = in_bounds(jn, a.n, kBoundsRsPair) ? jn : 0;
+              load_words<R, RW>(a.rec + int64_t(jn) * RW, rn);
+            }
+            const int o3 = o / 3;
+            const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
+            L jx, jy, jz;
+            coords<R>(rj, jx, jy, jz);
+            R du0, du1, du2;   // displacement r_j - r_i in list-cell units
+            if constexpr (std::is_same<R, float>::value) {
+              du0 = __int2float_rn(jx + ox * (1 << kFixBits) - ix);
+              du1 = __int2float_rn(jy + oy * (1 << kFixBits) - iy);
+              du2 = __int2float_rn(jz + oz * (1 << kFixBits) - iz);
+            } else {
+              du0 = jx + ox - ix;
+              du1 = jy + oy - iy;
+              du2 = jz + oz - iz;
+            }
+            R dx, dy, dz;
+            if constexpr (TRIC) {
+              dx = du0 * ew[0] + du1 * ew[3] + du2 * ew[6];
+              dy = du0 * ew[1] + du1 * ew[4] + du2 * ew[7];
+              dz = du0 * ew[2] + du1 * ew[5] + du2 * ew[8];
+            } else {
+              dx = du0 * ew[0];
+              dy = du1 * ew[4];
+              dz = du2 * ew[8];
+            }
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            // atoms within one fixed-point step of each other (their FP32 test
+            // coordinates may still differ) count as coincident: excluded
+            if (r2 > R(0)) {
+              const R inv_r = inv_sqrt(r2);
+              const R r = r2 * inv_r;
+              const R ir2 = inv_r * inv_r, ir4 = ir2 * ir2;
+              R x = r * inv_rc;
+              if (x >= R(1)) x = R(1) - R(1e-7);
+              int seg = int(x * R(kMultSeg));
+              if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+              const R sv = R(2) * (x * R(kMultSeg) - R(seg)) - R(1);
+              R fsum = 0;   // sum_c q_i^c q_j^c f_p'(r)
+              R pj[KC];     // phi_j^c += q_i^c f_p(r)
+#pragma unroll
+              for (int c = 0; c < KC; ++c) {
+                R cf[NC];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                  const Vec<R> cv = coefv[(prow[c] * NV + v) * kMultSeg + seg];
+                  if constexpr (std::is_same<R, float>::value) {
+                    cf[4 * v] = cv.x;
+                    cf[4 * v + 1] = cv.y;
+                    cf[4 * v + 2] = cv.z;
+                    cf[4 * v + 3] = cv.w;
+                  } else {
+                    cf[2 * v] = cv.x;
+                    cf[2 * v + 1] = cv.y;
+                  }
+                }
+                R Gv = cf[NC - 1], dG = R(0);
+#pragma unroll
+                for (int k = NC - 2; k >= 0; --k) {
+                  dG = dG * sv + Gv;
+                  Gv = Gv * sv + cf[k];
+                }
+                dG *= R(2 * kMultSeg);                       // dG / dx
+                const int p = prow[c] + 1;                    // r^-p from the bits of p
+                const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
+                const R one_m = R(1) - Gv;
+                const R fc = one_m * rp;
+                const R qj = rj[3 + c];
+                ph[c] += qj * fc;
+                pj[c] = ro[3 + c] * fc;
+                fsum -= ro[3 + c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
+              }
+              const R sc = fsum * inv_r;   // F_i += sc d, F_j -= sc d
+              fx += sc * dx;
+              fy += sc * dy;
+              fz += sc * dz;
+              if (accp) add_row<R, KC>(accp + int64_t(j) * AW, pj, -sc * dx, -sc * dy, -sc * dz, a.K);
+            }
+            if (!more || mn != mo) {   // atom io is done in this range
+              if (accp) add_row<R, KC>(accp + int64_t(io) * AW, ph, fx, fy, fz, a.K);
+#pragma unroll
+              for (int c = 0; c < KC; ++c)
+                if (c < a.K) atomicAdd(esum + c, double(ro[3 + c]) * double(ph[c]));
+              if (more) {
+                mo = mn;
+                tend = pref[mo + 1] - pref[mo];
+                io = base + mo / G;
+                io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;
+                load_words<R, RW>(a.rec + int64_t(io) * RW, ro);
+                coords<R>(ro, ix, iy, iz);
+#pragma unroll
+                for (int c = 0; c < KC; ++c) ph[c] = R(0);
+                fx = fy = fz = R(0);
               }
             }
-            R Gv = cf[NC - 1], dG = R(0);
-#pragma unroll
-            for (int k = NC - 2; k >= 0; --k) {
-              dG = dG * sv + Gv;
-              Gv = Gv * sv + cf[k];
-            }
-            dG *= R(2 * kMultSeg);                       // dG / dx
-            const int p = prow[c] + 1;                    // r^-p from the bits of p
-            const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
-            const R one_m = R(1) - Gv;
-            const R qj = rj[3 + c];
-            ph[c] += qj * one_m * rp;
-            fsum -= ri[3 + c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
+            t = tn;
           }
-          const R sc = fsum * inv_r;
-          fx += sc * dx;
-          fy += sc * dy;
-          fz += sc * dz;
         }
+        __syncwarp();   // the queues and offsets are rewritten next
         len = 0;
       };
 
-      for (int o = 0; o < 27; ++o) {
-        const R ax = xi - shv[4 * o], ay = yi - shv[4 * o + 1], az = zi - shv[4 * o + 2];
-        const int b0 = nbs[o], b1 = nbe[o];
-        const uint32_t tag = uint32_t(o) << kCellBits;
+      for (int s = 0; s < kHalf; ++s) {
+        const R ax = xi - shv[4 * s], ay = yi - shv[4 * s + 1], az = zi - shv[4 * s + 2];
+        const int b0 = nbs[s], b1 = nbe[s];
+        const uint32_t tag = uint32_t(s) << kCellBits;
+        const int jlo = s == 0 ? i + 1 : 0;   // within the cell: j > i only
         for (int jb = b0; jb < b1; jb += 32) {
           if (__reduce_max_sync(0xffffffffu, len) > kQueueCap - 32) drain();
           const int cnt = min(32, b1 - jb);
@@ -464,9 +585,8 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
               }
               const R dx = xj - ax, dy = yj - ay, dz = zj - az;
               const R r2 = dx * dx + dy * dy + dz * dz;
-              // r2 = 0 only for the atom itself (or a coincident atom, which
-              // the sum excludes too)
-              if (r2 < rc2 && r2 > R(0)) queue[len++] = uint16_t(tag | uint32_t(jb - b0 + jj));
+              // r2 = 0 only for a coincident atom, which the sum excludes
+              if (r2 < rc2 && r2 > R(0) && jb + jj >= jlo) queue[len++] = uint16_t(tag | uint32_t(jb - b0 + jj));
             }
           }
           __syncwarp();
@@ -474,34 +594,32 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
       }
       drain();
       __syncwarp();   // nbs / nbe are rewritten for the next chunk
+    }
+  }
+  __syncwarp();
+  if (lane < KC && lane < a.K && esum[lane] != 0.0) atomicAdd(a.energy + lane, esum[lane]);
+}
 
-      // the G lanes of an atom hold partial sums over its candidates
-      for (int off = G / 2; off > 0; off >>= 1) {
+// accumulator rows (cell order) to the caller's layouts: phi real [K][n],
+// forces real [n][3]
+template <typename R, int KC>
+__global__ void k_rs_finish(int64_t n, int K, const R* __restrict__ acc, const int* __restrict__ perm,
+                            R* __restrict__ phi, R* __restrict__ forces) {
+  constexpr int AW = acc_words<R, KC>();
+  for (int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; m < n; m += int64_t(gridDim.x) * blockDim.x) {
+    R row[AW];
+    load_words<R, AW>(acc + m * AW, row);
+    const int64_t orig = perm[m];
+    if (!in_bounds(orig, n, kBoundsRsFinish)) continue;
+    if (phi) {
 #pragma unroll
-        for (int c = 0; c < KC; ++c) ph[c] += __shfl_xor_sync(0xffffffffu, ph[c], off);
-        fx += __shfl_xor_sync(0xffffffffu, fx, off);
-        fy += __shfl_xor_sync(0xffffffffu, fy, off);
-        fz += __shfl_xor_sync(0xffffffffu, fz, off);
-      }
-      const bool lead = own && sub == 0;
-      const int orig = lead ? a.perm[i] : 0;
-#pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        if (c >= a.K) break;
-        double e = lead ? 0.5 * double(ri[3 + c]) * double(ph[c]) : 0.0;
-        for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
-        if (lane == 0 && e != 0.0) atomicAdd(a.energy + c, e);
-      }
-      if (lead && a.phi) {
-#pragma unroll
-        for (int c = 0; c < KC; ++c)
-          if (c < a.K) a.phi[int64_t(c) * a.n + orig] = ph[c];
-      }
-      if (lead && a.forces) {
-        a.forces[3 * int64_t(orig)] = fx;
-        a.forces[3 * int64_t(orig) + 1] = fy;
-        a.forces[3 * int64_t(orig) + 2] = fz;
-      }
+      for (int c = 0; c < KC; ++c)
+        if (c < K) phi[int64_t(c) * n + orig] = row[c];
+    }
+    if (forces) {
+      forces[3 * orig] = row[KC];
+      forces[3 * orig + 1] = row[KC + 1];
+      forces[3 * orig + 2] = row[KC + 2];
     }
   }
 }
@@ -894,7 +1012,8 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
 
 template <typename R, int NC, int KC, bool TRIC>
 cudaError_t launch_pairs_t(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + 27 * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
+  const size_t smem =
+      size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
   // set on every launch: the opt-in is per device and cheap
   const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC, TRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(smem));
@@ -937,10 +1056,35 @@ int record_words(int K) {
   }
 }
 
+template <typename R>
+int accumulator_words(int K) {
+  switch (channel_class(K)) {
+    case 1: return acc_words<R, 1>();
+    case 2: return acc_words<R, 2>();
+    case 4: return acc_words<R, 4>();
+    case 8: return acc_words<R, 8>();
+    default: return acc_words<R, kRsMaxK>();
+  }
+}
+
+template <typename R>
+cudaError_t launch_finish(int64_t n, int K, const R* acc, const int* perm, R* phi, R* forces, int blocks,
+                          cudaStream_t s) {
+  switch (channel_class(K)) {
+    case 1: k_rs_finish<R, 1><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+    case 2: k_rs_finish<R, 2><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+    case 4: k_rs_finish<R, 4><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+    case 8: k_rs_finish<R, 8><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+    default: k_rs_finish<R, kRsMaxK><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t real_space_bytes_per_atom(int K, int real_size) {
-  return real_size == 4 ? (4 + size_t(record_words<float>(K))) * 4 : (4 + size_t(record_words<double>(K))) * 8;
+  return real_size == 4 ? (4 + size_t(record_words<float>(K)) + size_t(accumulator_words<float>(K))) * 4
+                        : (4 + size_t(record_words<double>(K)) + size_t(accumulator_words<double>(K))) * 8;
 }
 
 bool real_space_geometry_cell(const double H[9], double r_c, RealSpaceGeom& g) {
@@ -1039,14 +1183,17 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     const int rw = record_words<R>(a.K);
     R* lchk = static_cast<R*>(a.lpos);
     R* rec = lchk + 4 * a.nmax;   // records follow the test coordinates
+    const int aw = accumulator_words<R>(a.K);
+    // accumulator rows follow the records; only potentials or forces need them
+    R* acc = (a.phi || a.forces) ? rec + int64_t(rw) * a.nmax : nullptr;
     if (a.pos_dtype == 1)
       k_rs_scatter<double, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const double*>(a.pos),
                                                             static_cast<const R*>(a.q), g, a.cell_of, a.rank,
-                                                            a.cell_start, lchk, rec, a.perm);
+                                                            a.cell_start, lchk, rec, a.perm, acc, aw);
     else
       k_rs_scatter<float, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const float*>(a.pos),
                                                            static_cast<const R*>(a.q), g, a.cell_of, a.rank,
-                                                           a.cell_start, lchk, rec, a.perm);
+                                                           a.cell_start, lchk, rec, a.perm, acc, aw);
     PairArgs<R> pa;
     pa.g = g;
     pa.n = a.n;
@@ -1059,8 +1206,7 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     pa.pch = a.pch;
     pa.coef = static_cast<const R*>(a.coef_g);
     pa.energy = a.energy;
-    pa.phi = static_cast<R*>(a.phi);
-    pa.forces = static_cast<R*>(a.forces);
+    pa.acc = acc;
     pa.err = a.err;
     // coefficient rows padded to whole 16-byte loads (the planner's degree
     // is at most kMaxMultDeg = 16)
@@ -1072,11 +1218,19 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     }
     if (e != cudaSuccess) return e;
     *nlaunch += 2;
+    if (acc) {
+      if ((e = launch_finish<R>(a.n, a.K, acc, a.perm, static_cast<R*>(a.phi), static_cast<R*>(a.forces), blocks,
+                                s)) != cudaSuccess)
+        return e;
+      ++*nlaunch;
+    }
   }
   k_rs_total<<<1, 32, 0, s>>>(a.K, a.energy);
   ++*nlaunch;
   return cudaGetLastError();
 }
+
+int bounds_word_real_space() { return take_bounds_word(); }
 
 template cudaError_t real_space_run<float>(const RealSpaceArgs&, cudaStream_t, int*);
 template cudaError_t real_space_run<double>(const RealSpaceArgs&, cudaStream_t, int*);

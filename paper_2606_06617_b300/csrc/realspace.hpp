@@ -98,4 +98,8 @@ struct RealSpaceBwArgs {
 template <typename R>
 cudaError_t real_space_backward_run(const RealSpaceBwArgs& a, cudaStream_t s, int* nlaunch);
 
+// Checked build: reads and clears the status word of this file's kernels
+// (0 in the normal build).
+int bounds_word_real_space();
+
 }  // namespace pswf

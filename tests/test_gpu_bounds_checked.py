@@ -1,7 +1,8 @@
 """The bounds-checked build (libpswf_lr_checked.so, kernels compiled with
 -DPSWF_BOUNDS_CHECK: an index outside its buffer records a status and skips
-the access) on valid inputs: every case matches the oracle like the normal
-build and no check fails -- pswf_sync would report PSWF_EBOUNDS otherwise.
+the access) on valid inputs -- stencils, batches, the real-space cell list
+and its backward: every case matches the oracle like the normal build and
+no check fails -- pswf_sync would report PSWF_EBOUNDS otherwise.
 Runs in a child process that loads the checked library."""
 import os
 import subprocess
@@ -48,6 +49,22 @@ bp.set_points(np.array([t.box for t in structs]), np.array([t.ps for t in struct
               torch.tensor(np.concatenate([t.q for t in structs], axis=1), dtype=torch.float32, device=dev))
 bp.execute()
 bp.sync()
+# the real-space cell list (half-shell pairs, accumulator rows) and its backward
+from oracle.realspace import real_space
+box = (13.0, 14.5, 12.5)
+s = wl.random_system(300, box, (1, 2, 3, 4, 5, 6), seed=41, neutral=False)
+plan = lr.Plan(box, s.n, s.ps, 4.0, c=C, P=6, grid=(28, 30, 26), flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+pos_d, q_d = torch.tensor(s.pos, device=dev), torch.tensor(s.q, dtype=torch.float32, device=dev)
+e, phi, f = plan.real_space(pos_d, q_d)
+gq, gp = plan.real_space_backward(pos_d, q_d, g_energy=torch.ones(len(s.ps), dtype=torch.float64, device=dev),
+                                  g_forces=torch.ones_like(f))
+plan.sync()
+F = np.zeros((s.n, 3))
+for c, p in enumerate(s.ps):
+    o = real_space(s.pos, s.q[c], box, p, C, 4.0)
+    assert rel_rms(phi[c].cpu().double().numpy(), o["phi"]) <= TOL_FP32, c
+    F += o["F"]
+assert rel_rms(f.cpu().double().numpy(), F) <= TOL_FP32
 print("checked build: no failed check")
 """
 
