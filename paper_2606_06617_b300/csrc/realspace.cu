@@ -34,9 +34,10 @@
 // stays in one atom's queue and is then added to the atom's accumulator
 // row; the j side (phi_j^c += q_i^c f_p, F_j -= F_ij) is added to j's row
 // at once, with 16-byte vector atomics in FP32.  The rows are kept in cell
-// order and copied to the caller's layouts by a last kernel; the channel
-// energies are the sums of q_i^c phi_i^c over the evaluated side, kept per
-// warp and added to the FP64 totals once per warp.
+// order and copied to the caller's layouts by a last kernel, which also
+// forms the channel energies 1/2 sum_i q_i^c phi_i^c in FP64.  A lane that
+// crosses into another atom's queue reads that atom's record from the
+// chunk's records, staged in shared memory at the start of the drain.
 //
 // Coordinates: the cutoff test reads Cartesian coordinates from the list
 // cell's corner in the plan's precision (16 or 32 bytes per atom, streamed
@@ -70,8 +71,8 @@ namespace {
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kFixBits = 29;     // FP32 plans: cell-local unit w / 2^29; |dx| <= 2^30
-constexpr int kQueueCap = 192;   // queued pairs per lane; drained early only above kQueueCap - 32
-constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 97 words, so lanes start in distinct banks
+constexpr int kQueueCap = 176;   // queued pairs per lane; drained early only above kQueueCap - 32
+constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 89 words, so lanes start in distinct banks
 constexpr int kCellBits = 11;    // queue entry: (half-shell slot << 11) | index within that cell
 constexpr int kMaxCellAtoms = 1 << kCellBits;
 // half shell: neighbour offsets o = (ox + 1) + 3 (oy + 1) + 9 (oz + 1) from
@@ -80,14 +81,6 @@ constexpr int kMaxCellAtoms = 1 << kCellBits;
 constexpr int kSelf = 13;
 constexpr int kHalf = 14;
 
-template <typename R>
-__host__ __device__ constexpr size_t warp_smem_bytes() {
-  // queue [32][kQueueStride] of 16-bit entries, stage [32][4] R, channel
-  // energies double [16], half-shell starts and ends [2][14] and queue
-  // offsets [33] int (padded to 384 bytes)
-  return size_t(32) * kQueueStride * 2 + 32 * 4 * sizeof(R) + 384;
-}
-static_assert(warp_smem_bytes<float>() % 16 == 0 && warp_smem_bytes<double>() % 16 == 0, "aligned warp regions");
 
 // exact cell-local coordinates: fixed-point int for FP32 plans, FP64 for FP64
 template <typename R>
@@ -111,6 +104,22 @@ template <typename R, int KC>
 __host__ __device__ constexpr int rec_words() {
   return (3 + KC + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
 }
+
+// stage words per atom: the candidates' test coordinates (4) during the
+// sweep, the chunk's own records (RW) during a drain
+template <typename R, int KC>
+__host__ __device__ constexpr int stage_words() {
+  return rec_words<R, KC>() > 4 ? rec_words<R, KC>() : 4;
+}
+
+template <typename R, int KC>
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+  // queue [32][kQueueStride] of 16-bit entries, stage [32][stage_words] R,
+  // half-shell starts and ends [2][14] and queue offsets [33] int (padded
+  // to 256 bytes)
+  return size_t(32) * kQueueStride * 2 + size_t(32) * stage_words<R, KC>() * sizeof(R) + 256;
+}
+static_assert(size_t(32) * kQueueStride * 2 % 16 == 0, "aligned stage");
 
 // accumulator row (cell order): KC potentials, 3 force components, zero
 // padding to whole 16-byte vectors
@@ -260,7 +269,7 @@ struct PairArgs {
   const int* pch;
   const R* coef;     // [6][kMultSeg][deg + 1]
   double* energy;
-  R* acc;            // [nmax][acc_words] zeroed, or null (energies only)
+  R* acc;            // [nmax][acc_words], zeroed
   int* err;
 };
 
@@ -291,37 +300,32 @@ __device__ inline void coords(const R* v, typename LocalT<R>::type& x, typename 
 }
 
 // KC channels per pair evaluation, fully unrolled (channels past K carry
-// zero charges); NC coefficients per mollifier piece (zero-padded).  The
-// coefficient table in shared memory is [exponent][vector][piece] of
-// 16-byte vectors, so lanes on different pieces read different banks.
-// a.acc == nullptr: energies only (no accumulator rows).
+// zero charges); NC coefficients per mollifier piece (zero-padded, NC =
+// deg + 1 for the common degrees, so the Horner chains have no idle step).
+// The coefficient table in shared memory is [exponent][coefficient][piece]
+// of scalars: the 32 pieces lie in 32 banks, so a warp's loads are free of
+// bank conflicts whichever pieces its lanes need.
 template <typename R, int NC, int KC, bool TRIC>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
   constexpr int RW = rec_words<R, KC>();
   constexpr int AW = acc_words<R, KC>();
-  constexpr int NV = NC / kPerVec<R>;
   extern __shared__ __align__(16) unsigned char rs_smem[];
-  Vec<R>* coefv = reinterpret_cast<Vec<R>*>(rs_smem);            // [6][NV][kMultSeg]
+  R* coefs = reinterpret_cast<R*>(rs_smem);   // [6][NC][kMultSeg]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R* shv = reinterpret_cast<R*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [kHalf][4] neighbour shifts
   unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) +
-                         size_t(warp) * warp_smem_bytes<R>();
+                         size_t(warp) * warp_smem_bytes<R, KC>();
   uint16_t* queues = reinterpret_cast<uint16_t*>(wbase);                        // [32][kQueueStride]
   uint16_t* queue = queues + lane * kQueueStride;                               // this lane's column
-  R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);               // [32][4] candidates
-  double* esum = reinterpret_cast<double*>(stage + 32 * 4);                     // [kRsMaxK] channel energies
-  int* nbs = reinterpret_cast<int*>(esum + kRsMaxK);                            // [kHalf] neighbour starts
+  R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);   // [32][4] candidates or [32][RW] records
+  int* nbs = reinterpret_cast<int*>(stage + 32 * stage_words<R, KC>());         // [kHalf] neighbour starts
   int* nbe = nbs + kHalf;                                                       // [kHalf] ends
   int* pref = nbe + kHalf;                                                      // [33] queue offsets
   {
-    R* cs = reinterpret_cast<R*>(rs_smem);
     for (int t = threadIdx.x; t < 6 * kMultSeg * NC; t += blockDim.x) {
-      // t -> (row, vector, piece, element) of the destination layout
-      const int e = t % kPerVec<R>, seg = (t / kPerVec<R>) % kMultSeg, v = (t / (kPerVec<R> * kMultSeg)) % NV,
-                row = t / (kPerVec<R> * kMultSeg * NV);
-      const int k = v * kPerVec<R> + e;
-      cs[t] = k <= a.deg ? a.coef[(size_t(row) * kMultSeg + seg) * (a.deg + 1) + k] : R(0);
+      const int seg = t % kMultSeg, k = (t / kMultSeg) % NC, row = t / (kMultSeg * NC);
+      coefs[t] = k <= a.deg ? a.coef[(size_t(row) * kMultSeg + seg) * (a.deg + 1) + k] : R(0);
     }
     // the neighbour o's corner relative to a cell's corner: o . (a_d / n_c)
     // (list cells are congruent, so also across the periodic boundary)
@@ -332,7 +336,6 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         shv[4 * threadIdx.x + k] = R(od[0] * a.g.cw[k] + od[1] * a.g.cw[3 + k] + od[2] * a.g.cw[6 + k]);
       shv[4 * threadIdx.x + 3] = R(0);
     }
-    if (lane < kRsMaxK) esum[lane] = 0.0;
   }
   __syncthreads();
 
@@ -412,6 +415,19 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         pref[lane + 1] = incl;
         if (lane == 0) pref[0] = 0;
+        // the chunk's own records, one per slot, for the lanes that cross
+        // into another atom's queue (the stage is free between sweeps)
+        if (lane < m) {
+          R rs[RW];
+          load_words<R, RW>(a.rec + int64_t(base + lane) * RW, rs);
+#pragma unroll
+          for (int w = 0; w < RW; w += kPerVec<R>) {
+            R v[kPerVec<R>];
+#pragma unroll
+            for (int e = 0; e < kPerVec<R>; ++e) v[e] = rs[w + e];
+            store_vec<R>(stage + lane * RW + w, v);
+          }
+        }
         __syncwarp();
         const int e0 = (lane * total) >> 5, e1 = ((lane + 1) * total) >> 5;
         if (e0 < e1) {
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           int io = base + mo / G;
           io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;   // checked build: a bad index reads row 0
           R ro[RW];
-          load_words<R, RW>(a.rec + int64_t(io) * RW, ro);
+          load_words<R, RW>(stage + (mo / G) * RW, ro);
           L ix, iy, iz;
           coords<R>(ro, ix, iy, iz);
           R ph[KC];
@@ -498,19 +514,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 #pragma unroll
               for (int c = 0; c < KC; ++c) {
                 R cf[NC];
+                const R* cp = coefs + prow[c] * NC * kMultSeg + seg;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                  const Vec<R> cv = coefv[(prow[c] * NV + v) * kMultSeg + seg];
-                  if constexpr (std::is_same<R, float>::value) {
-                    cf[4 * v] = cv.x;
-                    cf[4 * v + 1] = cv.y;
-                    cf[4 * v + 2] = cv.z;
-                    cf[4 * v + 3] = cv.w;
-                  } else {
-                    cf[2 * v] = cv.x;
-                    cf[2 * v + 1] = cv.y;
-                  }
-                }
+                for (int k = 0; k < NC; ++k) cf[k] = cp[k * kMultSeg];
                 R Gv = cf[NC - 1], dG = R(0);
 #pragma unroll
                 for (int k = NC - 2; k >= 0; --k) {
@@ -531,19 +537,17 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
               fx += sc * dx;
               fy += sc * dy;
               fz += sc * dz;
-              if (accp) add_row<R, KC>(accp + int64_t(j) * AW, pj, -sc * dx, -sc * dy, -sc * dz, a.K);
+              add_row<R, KC>(accp + int64_t(j) * AW, pj, -sc * dx, -sc * dy, -sc * dz, a.K);
             }
             if (!more || mn != mo) {   // atom io is done in this range
-              if (accp) add_row<R, KC>(accp + int64_t(io) * AW, ph, fx, fy, fz, a.K);
+              add_row<R, KC>(accp + int64_t(io) * AW, ph, fx, fy, fz, a.K);
 #pragma unroll
-              for (int c = 0; c < KC; ++c)
-                if (c < a.K) atomicAdd(esum + c, double(ro[3 + c]) * double(ph[c]));
               if (more) {
                 mo = mn;
                 tend = pref[mo + 1] - pref[mo];
                 io = base + mo / G;
                 io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;
-                load_words<R, RW>(a.rec + int64_t(io) * RW, ro);
+                load_words<R, RW>(stage + (mo / G) * RW, ro);
                 coords<R>(ro, ix, iy, iz);
 #pragma unroll
                 for (int c = 0; c < KC; ++c) ph[c] = R(0);
@@ -596,19 +600,29 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
       __syncwarp();   // nbs / nbe are rewritten for the next chunk
     }
   }
-  __syncwarp();
-  if (lane < KC && lane < a.K && esum[lane] != 0.0) atomicAdd(a.energy + lane, esum[lane]);
 }
 
-// accumulator rows (cell order) to the caller's layouts: phi real [K][n],
-// forces real [n][3]
+// accumulator rows (cell order) to the caller's layouts, phi real [K][n]
+// and forces real [n][3] (either may be null), and the channel energies
+// E_c = 1/2 sum_i q_i^c phi_i^c (FP64 block sums, one atomic per block and
+// channel)
 template <typename R, int KC>
-__global__ void k_rs_finish(int64_t n, int K, const R* __restrict__ acc, const int* __restrict__ perm,
-                            R* __restrict__ phi, R* __restrict__ forces) {
+__global__ void __launch_bounds__(kRsThreads) k_rs_finish(int64_t n, int K, const R* __restrict__ acc,
+                                                          const R* __restrict__ rec, const int* __restrict__ perm,
+                                                          R* __restrict__ phi, R* __restrict__ forces,
+                                                          double* __restrict__ energy) {
   constexpr int AW = acc_words<R, KC>();
+  constexpr int RW = rec_words<R, KC>();
+  __shared__ double part[kRsWarps][KC];
+  double e[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) e[c] = 0.0;
   for (int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; m < n; m += int64_t(gridDim.x) * blockDim.x) {
-    R row[AW];
+    R row[AW], rq[RW];
     load_words<R, AW>(acc + m * AW, row);
+    load_words<R, RW>(rec + m * RW, rq);
+#pragma unroll
+    for (int c = 0; c < KC; ++c) e[c] += double(rq[3 + c]) * double(row[c]);
     const int64_t orig = perm[m];
     if (!in_bounds(orig, n, kBoundsRsFinish)) continue;
     if (phi) {
@@ -621,6 +635,18 @@ __global__ void k_rs_finish(int64_t n, int K, const R* __restrict__ acc, const i
       forces[3 * orig + 1] = row[KC + 1];
       forces[3 * orig + 2] = row[KC + 2];
     }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    for (int off = 16; off > 0; off >>= 1) e[c] += __shfl_down_sync(0xffffffffu, e[c], off);
+    if (lane == 0) part[warp][c] = e[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < KC && threadIdx.x < K) {
+    double t = 0.0;
+    for (int w = 0; w < kRsWarps; ++w) t += part[w][threadIdx.x];
+    if (t != 0.0) atomicAdd(energy + threadIdx.x, 0.5 * t);
   }
 }
 
@@ -1013,7 +1039,7 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
 template <typename R, int NC, int KC, bool TRIC>
 cudaError_t launch_pairs_t(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
   const size_t smem =
-      size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R>();
+      size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R, KC>();
   // set on every launch: the opt-in is per device and cheap
   const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC, TRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(smem));
@@ -1068,14 +1094,16 @@ int accumulator_words(int K) {
 }
 
 template <typename R>
-cudaError_t launch_finish(int64_t n, int K, const R* acc, const int* perm, R* phi, R* forces, int blocks,
-                          cudaStream_t s) {
+cudaError_t launch_finish(int64_t n, int K, const R* acc, const R* rec, const int* perm, R* phi, R* forces,
+                          double* energy, int blocks, cudaStream_t s) {
   switch (channel_class(K)) {
-    case 1: k_rs_finish<R, 1><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
-    case 2: k_rs_finish<R, 2><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
-    case 4: k_rs_finish<R, 4><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
-    case 8: k_rs_finish<R, 8><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
-    default: k_rs_finish<R, kRsMaxK><<<blocks, kRsThreads, 0, s>>>(n, K, acc, perm, phi, forces); break;
+    case 1: k_rs_finish<R, 1><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
+    case 2: k_rs_finish<R, 2><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
+    case 4: k_rs_finish<R, 4><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
+    case 8: k_rs_finish<R, 8><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
+    default:
+      k_rs_finish<R, kRsMaxK><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy);
+      break;
   }
   return cudaGetLastError();
 }
@@ -1184,8 +1212,7 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     R* lchk = static_cast<R*>(a.lpos);
     R* rec = lchk + 4 * a.nmax;   // records follow the test coordinates
     const int aw = accumulator_words<R>(a.K);
-    // accumulator rows follow the records; only potentials or forces need them
-    R* acc = (a.phi || a.forces) ? rec + int64_t(rw) * a.nmax : nullptr;
+    R* acc = rec + int64_t(rw) * a.nmax;   // accumulator rows follow the records
     if (a.pos_dtype == 1)
       k_rs_scatter<double, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const double*>(a.pos),
                                                             static_cast<const R*>(a.q), g, a.cell_of, a.rank,
@@ -1208,22 +1235,21 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     pa.energy = a.energy;
     pa.acc = acc;
     pa.err = a.err;
-    // coefficient rows padded to whole 16-byte loads (the planner's degree
-    // is at most kMaxMultDeg = 16)
-    static_assert(kMaxMultDeg + 1 <= 18, "coefficient rows");
+    // coefficients per piece: the FP32 fit's usual degree 6 exactly, else
+    // padded (the planner's degree is at most kMaxMultDeg = 16)
+    static_assert(kMaxMultDeg + 1 <= 17, "coefficient rows");
     if constexpr (std::is_same<R, float>::value) {
-      e = a.deg_g + 1 <= 8 ? launch_pairs<R, 8>(pa, ncell, s) : launch_pairs<R, 20>(pa, ncell, s);
+      e = a.deg_g + 1 <= 7 ? launch_pairs<R, 7>(pa, ncell, s)
+                           : (a.deg_g + 1 <= 8 ? launch_pairs<R, 8>(pa, ncell, s) : launch_pairs<R, 17>(pa, ncell, s));
     } else {
-      e = launch_pairs<R, 18>(pa, ncell, s);
+      e = launch_pairs<R, 17>(pa, ncell, s);
     }
     if (e != cudaSuccess) return e;
     *nlaunch += 2;
-    if (acc) {
-      if ((e = launch_finish<R>(a.n, a.K, acc, a.perm, static_cast<R*>(a.phi), static_cast<R*>(a.forces), blocks,
-                                s)) != cudaSuccess)
-        return e;
-      ++*nlaunch;
-    }
+    if ((e = launch_finish<R>(a.n, a.K, acc, rec, a.perm, static_cast<R*>(a.phi), static_cast<R*>(a.forces),
+                              a.energy, blocks, s)) != cudaSuccess)
+      return e;
+    ++*nlaunch;
   }
   k_rs_total<<<1, 32, 0, s>>>(a.K, a.energy);
   ++*nlaunch;
