@@ -819,49 +819,66 @@ def main():
     # end-to-end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        # inputs and results in page-locked host memory (the caller's
-        # arrays, reused across steps as a simulation loop would)
-        def pinned(shape):
-            t = torch.zeros(shape, dtype=torch.float64).pin_memory()
-            keep.append(t)
-            return t.numpy()
-        keep = []
-        pos_h = pinned(sysm.pos.shape)
-        pos_h[...] = sysm.pos
-        q_h = pinned(sysm.q.shape)
-        q_h[...] = sysm.q
-        res_h = (np.zeros(len(sysm.ps) + 1), pinned((len(sysm.ps), sysm.n)), pinned((sysm.n, 3)))
-        for _ in range(2):
-            plan.compute_host(pos_h, q_h, out=res_h)
-        if dist:
-            dist.barrier()
-        ne = max(3, min(args.steps, 10))
-        t0 = time.perf_counter()
-        for _ in range(ne):
-            plan.compute_host(pos_h, q_h, out=res_h)
-        te = max_over_ranks((time.perf_counter() - t0) / ne, dist, dev)
-        # phase breakdown of the same call (stream events: input copies,
-        # device stages, output copies; the rest is host time)
-        plan.profile_read()
-        plan.profile(True)
-        t1 = time.perf_counter()
-        for _ in range(3):
-            plan.compute_host(pos_h, q_h, out=res_h)
-        wall = (time.perf_counter() - t1) / 3 * 1e3
-        plan.profile(False)
-        st_e, _ = plan.profile_read()
-        st_e = {k: v / 3 for k, v in st_e.items()}
-        dev_e = sum(v for k, v in st_e.items() if k not in ("h2d", "d2h"))
-        phases = {"wall_ms": wall, "h2d_ms": st_e["h2d"], "device_ms": dev_e, "d2h_ms": st_e["d2h"],
-                  "host_rest_ms": wall - st_e["h2d"] - dev_e - st_e["d2h"]}
         K = len(sysm.ps)
-        e2e = {"value": replica_throughput(sysm.n, world, te), "unit": "atoms/s",
-               "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * 8),
-               "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * 8 + sysm.n * 24),
-               "host_memory": "page-locked inputs and outputs, copied directly (charges rounded to FP32 "
-                              "and results widened to double on the device)",
-               "phases": phases,
-               "ms_per_step": te * 1e3}
+        rsz = 4 if plan.dtype == torch.float32 else 8
+
+        def time_e2e(real: bool) -> dict:
+            """pswf_compute_host (real=False: charges and results float64) or
+            pswf_compute_host_real (real=True: in the plan's precision), with
+            the caller's arrays in page-locked memory, reused across steps
+            as a simulation loop would."""
+            keep = []
+
+            def pinned(shape, dt):
+                t = torch.zeros(shape, dtype=dt).pin_memory()
+                keep.append(t)
+                return t.numpy()
+            rdt = (torch.float32 if rsz == 4 else torch.float64) if real else torch.float64
+            pos_h = pinned(sysm.pos.shape, torch.float64)
+            pos_h[...] = sysm.pos
+            q_h = pinned(sysm.q.shape, rdt)
+            q_h[...] = sysm.q
+            res_h = (np.zeros(K + 1), pinned((K, sysm.n), rdt), pinned((sysm.n, 3), rdt))
+            for _ in range(2):
+                plan.compute_host(pos_h, q_h, out=res_h, real=real)
+            if dist:
+                dist.barrier()
+            ne = max(3, min(args.steps, 10))
+            t0 = time.perf_counter()
+            for _ in range(ne):
+                plan.compute_host(pos_h, q_h, out=res_h, real=real)
+            te = max_over_ranks((time.perf_counter() - t0) / ne, dist, dev)
+            # phase breakdown of the same call (stream events: input copies,
+            # device stages, output copies; the rest is host time)
+            plan.profile_read()
+            plan.profile(True)
+            t1 = time.perf_counter()
+            for _ in range(3):
+                plan.compute_host(pos_h, q_h, out=res_h, real=real)
+            wall = (time.perf_counter() - t1) / 3 * 1e3
+            plan.profile(False)
+            st_e, _ = plan.profile_read()
+            st_e = {k: v / 3 for k, v in st_e.items()}
+            dev_e = sum(v for k, v in st_e.items() if k not in ("h2d", "d2h"))
+            phases = {"wall_ms": wall, "h2d_ms": st_e["h2d"], "device_ms": dev_e, "d2h_ms": st_e["d2h"],
+                      "host_rest_ms": wall - st_e["h2d"] - dev_e - st_e["d2h"]}
+            qb = rsz if real else 8
+            ob = rsz if real else 8
+            return {"value": replica_throughput(sysm.n, world, te), "unit": "atoms/s",
+                    "h2d_bytes_per_step": int(sysm.n * 24 + K * sysm.n * qb),
+                    "d2h_bytes_per_step": int((K + 1) * 8 + K * sysm.n * ob + sysm.n * 3 * ob),
+                    "phases": phases, "ms_per_step": te * 1e3}
+
+        e2e = time_e2e(True)
+        e2e["api"] = "pswf_compute_host_real"
+        e2e["host_memory"] = ("page-locked caller arrays copied as they are: positions float64, charges, "
+                              "potentials and forces in the plan's precision, energies float64")
+        d = time_e2e(False)
+        e2e["float64_io"] = {"api": "pswf_compute_host", "value": d["value"], "ms_per_step": d["ms_per_step"],
+                             "h2d_bytes_per_step": d["h2d_bytes_per_step"],
+                             "d2h_bytes_per_step": d["d2h_bytes_per_step"], "phases": d["phases"],
+                             "host_memory": "page-locked float64 arrays, copied directly (charges rounded "
+                                            "and results widened on the device in FP32 plans)"}
 
     serving = None
     total = None

@@ -347,6 +347,18 @@ int pswf_sync_for(pswf_plan plan, double timeout_ms);
 int pswf_compute_host(pswf_plan plan, int64_t n, const double* pos, const double* q,
                       double* energy, double* phi, double* forces);
 
+/* pswf_compute_host with charges, potentials and forces in the plan's
+ * precision (float for FP32 plans, double for FP64 plans): q host real
+ * [K][n], phi host real [K][n] (may be NULL), forces host real [n][3] (may
+ * be NULL); positions host double [n][3] and energy host double [K + 1] as
+ * above.  Page-locked arrays are copied as they are, with no conversion on
+ * either side (an FP32 plan moves 24 n + 4 K n bytes in and 4 K n + 12 n
+ * out); pageable ones go through the plan's pinned staging buffers.  Same
+ * errors as pswf_compute_host.  The paper has no counterpart (host
+ * transfers). */
+int pswf_compute_host_real(pswf_plan plan, int64_t n, const double* pos, const void* q,
+                           double* energy, void* phi, void* forces);
+
 /* Releases everything the plan owns (not a caller-attached workspace). */
 void pswf_plan_destroy(pswf_plan plan);
 

@@ -1741,8 +1741,15 @@ __global__ void k_narrow(int64_t n, const double* __restrict__ in, float* __rest
 
 extern "C" {
 
-int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* q, double* energy, double* phi,
-                      double* forces) {
+namespace {
+
+// pswf_compute_host (real_io false: charges and results double) and
+// pswf_compute_host_real (real_io true: in the plan's precision)
+int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, double* energy, void* phiv,
+                 void* forcesv, bool real_io) {
+  const double* q = static_cast<const double*>(qv);
+  double* phi = static_cast<double*>(phiv);
+  double* forces = static_cast<double*>(forcesv);
   if (!pl || !energy || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
   if (pl->batch) return set_err(pl, PSWF_EINVAL, "pswf_compute_host takes a single-structure plan");
   if (n < 0 || n > pl->n_max) return set_err(pl, PSWF_EINVAL, "n outside 0..n_max");
@@ -1755,9 +1762,10 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   // through the plan's pinned staging buffers.
   const bool pos_direct = host_pinned(pos);
   const bool q_direct = host_pinned(q);
-  const bool narrow = q_direct && rs == 4;
+  const bool narrow = q_direct && rs == 4 && !real_io;
   const bool out_direct = host_pinned(phi) && host_pinned(forces);
-  const bool widen = out_direct && rs == 4;
+  const bool widen = out_direct && rs == 4 && !real_io;
+  const int64_t qs = real_io ? rs : 8;   // bytes per charge in the caller's array
   // device staging: pos double [n][3] | q real [K][n] | energy [K+1] | phi real [K][n] | forces real [n][3]
   //                 (| phi double [K][n] | forces double [n][3] when widening on the device)
   const int64_t need = align256(n * 3 * 8) + align256(K * n * rs) + align256((K + 1) * 8) + align256(K * n * rs) +
@@ -1814,7 +1822,7 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   if (q_direct && n > 0) {
     // pinned charges: copied as double, rounded to FP32 on the device
     if ((rc = cuda_check(pl, cudaMemcpyAsync(narrow ? static_cast<void*>(d_q64) : static_cast<void*>(d_q), q,
-                                             size_t(K * n) * 8, cudaMemcpyHostToDevice, s), "h2d q")))
+                                             size_t(K * n * qs), cudaMemcpyHostToDevice, s), "h2d q")))
       return rc;
     if (narrow) {
       const int nb = int(std::min<int64_t>((K * n + kThreads - 1) / kThreads, 148 * 16));
@@ -1835,7 +1843,10 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
       if (!pos_direct) std::memcpy(h_pos + 3 * (a0 + lo), pos + 3 * (a0 + lo), size_t(hi - lo) * 24);
       for (int k = 0; k < K && !q_direct; ++k) {
         const double* src = q + size_t(k) * n + a0;
-        if (rs == 4) {
+        if (real_io) {
+          std::memcpy(h_q + (size_t(k) * n + a0 + lo) * rs, static_cast<const char*>(qv) + (size_t(k) * n + a0 + lo) * rs,
+                      size_t(hi - lo) * rs);
+        } else if (rs == 4) {
           float* dst = reinterpret_cast<float*>(h_q) + size_t(k) * n + a0;
           for (int64_t i = lo; i < hi; ++i) dst[i] = float(src[i]);
         } else {
@@ -1878,7 +1889,8 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
         ++pl->launches[PSWF_STAGE_OTHER];
         src = d_phi64;
       }
-      if ((rc = cuda_check(pl, cudaMemcpyAsync(phi, src, size_t(K * n) * 8, cudaMemcpyDeviceToHost, s), "d2h phi")))
+      if ((rc = cuda_check(pl, cudaMemcpyAsync(phi, src, size_t(K * n) * (widen ? 8 : rs), cudaMemcpyDeviceToHost, s),
+                           "d2h phi")))
         return rc;
     }
     if (forces) {
@@ -1889,8 +1901,8 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
         ++pl->launches[PSWF_STAGE_OTHER];
         src = d_f64;
       }
-      if ((rc = cuda_check(pl, cudaMemcpyAsync(forces, src, size_t(3 * n) * 8, cudaMemcpyDeviceToHost, s),
-                           "d2h forces")))
+      if ((rc = cuda_check(pl, cudaMemcpyAsync(forces, src, size_t(3 * n) * (widen ? 8 : rs), cudaMemcpyDeviceToHost,
+                                               s), "d2h forces")))
         return rc;
     }
   }
@@ -1919,6 +1931,16 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
     const int64_t a0 = ci * csz, a1 = std::min(n, a0 + csz);
     if ((rc = cuda_check(pl, cudaEventSynchronize(evs[ci]), "wait for chunk"))) break;
     parallel_for(a1 - a0, [&](int64_t lo, int64_t hi) {
+      if (real_io) {   // same precision: plain copies
+        if (phi)
+          for (int k = 0; k < K; ++k)
+            std::memcpy(static_cast<char*>(phiv) + (size_t(k) * n + a0 + lo) * rs, h_phi + (size_t(k) * n + a0 + lo) * rs,
+                        size_t(hi - lo) * rs);
+        if (forces)
+          std::memcpy(static_cast<char*>(forcesv) + size_t(3 * (a0 + lo)) * rs, h_f + size_t(3 * (a0 + lo)) * rs,
+                      size_t(3 * (hi - lo)) * rs);
+        return;
+      }
       if (phi)
         for (int k = 0; k < K; ++k)
           for (int64_t i = a0 + lo; i < a0 + hi; ++i)
@@ -1934,6 +1956,18 @@ int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* 
   if ((rc = pswf_sync(pl))) return rc;
   std::memcpy(energy, h_e, size_t(K + 1) * 8);
   return PSWF_OK;
+}
+
+}  // namespace
+
+int pswf_compute_host(pswf_plan pl, int64_t n, const double* pos, const double* q, double* energy, double* phi,
+                      double* forces) {
+  return compute_host(pl, n, pos, q, energy, phi, forces, false);
+}
+
+int pswf_compute_host_real(pswf_plan pl, int64_t n, const double* pos, const void* q, double* energy, void* phi,
+                           void* forces) {
+  return compute_host(pl, n, pos, q, energy, phi, forces, true);
 }
 
 void pswf_plan_destroy(pswf_plan pl) {

@@ -541,7 +541,6 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
             }
             if (!more || mn != mo) {   // atom io is done in this range
               add_row<R, KC>(accp + int64_t(io) * AW, ph, fx, fy, fz, a.K);
-#pragma unroll
               if (more) {
                 mo = mn;
                 tend = pref[mo + 1] - pref[mo];
@@ -605,35 +604,35 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 // accumulator rows (cell order) to the caller's layouts, phi real [K][n]
 // and forces real [n][3] (either may be null), and the channel energies
 // E_c = 1/2 sum_i q_i^c phi_i^c (FP64 block sums, one atomic per block and
-// channel)
+// channel).  Threads walk the atoms in their original order: atom i's row
+// is the scatter's slot cell_start[cell_of[i]] + rank[i], so the writes are
+// coalesced and each row is one or two whole sectors read.
 template <typename R, int KC>
 __global__ void __launch_bounds__(kRsThreads) k_rs_finish(int64_t n, int K, const R* __restrict__ acc,
-                                                          const R* __restrict__ rec, const int* __restrict__ perm,
-                                                          R* __restrict__ phi, R* __restrict__ forces,
-                                                          double* __restrict__ energy) {
+                                                          const R* __restrict__ q, const int* __restrict__ cell_of,
+                                                          const int* __restrict__ rank,
+                                                          const int* __restrict__ cell_start, R* __restrict__ phi,
+                                                          R* __restrict__ forces, double* __restrict__ energy) {
   constexpr int AW = acc_words<R, KC>();
-  constexpr int RW = rec_words<R, KC>();
   __shared__ double part[kRsWarps][KC];
   double e[KC];
 #pragma unroll
   for (int c = 0; c < KC; ++c) e[c] = 0.0;
-  for (int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; m < n; m += int64_t(gridDim.x) * blockDim.x) {
-    R row[AW], rq[RW];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = int64_t(cell_start[cell_of[i]]) + rank[i];
+    if (!in_bounds(m, n, kBoundsRsFinish)) continue;
+    R row[AW];
     load_words<R, AW>(acc + m * AW, row);
-    load_words<R, RW>(rec + m * RW, rq);
 #pragma unroll
-    for (int c = 0; c < KC; ++c) e[c] += double(rq[3 + c]) * double(row[c]);
-    const int64_t orig = perm[m];
-    if (!in_bounds(orig, n, kBoundsRsFinish)) continue;
-    if (phi) {
-#pragma unroll
-      for (int c = 0; c < KC; ++c)
-        if (c < K) phi[int64_t(c) * n + orig] = row[c];
+    for (int c = 0; c < KC; ++c) {
+      if (c >= K) break;
+      e[c] += double(q[int64_t(c) * n + i]) * double(row[c]);
+      if (phi) phi[int64_t(c) * n + i] = row[c];
     }
     if (forces) {
-      forces[3 * orig] = row[KC];
-      forces[3 * orig + 1] = row[KC + 1];
-      forces[3 * orig + 2] = row[KC + 2];
+      forces[3 * i] = row[KC];
+      forces[3 * i + 1] = row[KC + 1];
+      forces[3 * i + 2] = row[KC + 2];
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1094,17 +1093,21 @@ int accumulator_words(int K) {
 }
 
 template <typename R>
-cudaError_t launch_finish(int64_t n, int K, const R* acc, const R* rec, const int* perm, R* phi, R* forces,
-                          double* energy, int blocks, cudaStream_t s) {
-  switch (channel_class(K)) {
-    case 1: k_rs_finish<R, 1><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
-    case 2: k_rs_finish<R, 2><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
-    case 4: k_rs_finish<R, 4><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
-    case 8: k_rs_finish<R, 8><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy); break;
-    default:
-      k_rs_finish<R, kRsMaxK><<<blocks, kRsThreads, 0, s>>>(n, K, acc, rec, perm, phi, forces, energy);
-      break;
+cudaError_t launch_finish(const RealSpaceArgs& a, const R* acc, int blocks, cudaStream_t s) {
+  const R* q = static_cast<const R*>(a.q);
+  R* phi = static_cast<R*>(a.phi);
+  R* forces = static_cast<R*>(a.forces);
+#define PSWF_RS_FINISH(KC)                                                                                     \
+  k_rs_finish<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, acc, q, a.cell_of, a.rank, a.cell_start, phi, forces, \
+                                                   a.energy)
+  switch (channel_class(a.K)) {
+    case 1: PSWF_RS_FINISH(1); break;
+    case 2: PSWF_RS_FINISH(2); break;
+    case 4: PSWF_RS_FINISH(4); break;
+    case 8: PSWF_RS_FINISH(8); break;
+    default: PSWF_RS_FINISH(kRsMaxK); break;
   }
+#undef PSWF_RS_FINISH
   return cudaGetLastError();
 }
 
@@ -1246,9 +1249,7 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     }
     if (e != cudaSuccess) return e;
     *nlaunch += 2;
-    if ((e = launch_finish<R>(a.n, a.K, acc, rec, a.perm, static_cast<R*>(a.phi), static_cast<R*>(a.forces),
-                              a.energy, blocks, s)) != cudaSuccess)
-      return e;
+    if ((e = launch_finish<R>(a, acc, blocks, s)) != cudaSuccess) return e;
     ++*nlaunch;
   }
   k_rs_total<<<1, 32, 0, s>>>(a.K, a.energy);

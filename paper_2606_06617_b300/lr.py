@@ -96,6 +96,7 @@ SIGNATURES = {
     "pswf_sync": ([_vp], ctypes.c_int),
     "pswf_sync_for": ([_vp, ctypes.c_double], ctypes.c_int),
     "pswf_compute_host": ([_vp, _i64, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "pswf_compute_host_real": ([_vp, _i64, _dp, _vp, _dp, _vp, _vp], ctypes.c_int),
     "pswf_plan_destroy": ([_vp], None),
     "pswf_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "pswf_plan_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
@@ -405,25 +406,36 @@ class Plan:
         _check(lib().pswf_profile_read(self._h, ms, nl), self._h)
         return dict(zip(STAGES, ms[:])), dict(zip(STAGES, nl[:]))
 
-    def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True, out=None):
-        """End-to-end from host arrays (float64); returns numpy (energy, phi,
-        forces).  out = (energy [K+1], phi [K, n] or None, forces [n, 3] or
-        None) float64 C-contiguous arrays to fill instead of new ones."""
+    def compute_host(self, pos: np.ndarray, q: np.ndarray, phi: bool = True, forces: bool = True, out=None,
+                     real: bool = False):
+        """End-to-end from host arrays; returns numpy (energy, phi, forces).
+        real=False: charges and results float64 (pswf_compute_host);
+        real=True: charges and results in the plan's precision
+        (pswf_compute_host_real).  Positions and energies are float64.
+        out = (energy [K+1], phi [K, n] or None, forces [n, 3] or None)
+        C-contiguous arrays of those dtypes to fill instead of new ones."""
+        import torch
+        rdt = (np.float32 if self.dtype == torch.float32 else np.float64) if real else np.float64
         pos = np.ascontiguousarray(pos, dtype=np.float64)
-        q = np.ascontiguousarray(q, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=rdt)
         n = pos.shape[0]
         if out is not None:
             e, ph, f = out
-            for a, shape in ((e, (self.K + 1,)), (ph, (self.K, n)), (f, (n, 3))):
-                if a is not None and (a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous):
-                    raise ValueError("out arrays must be float64, C-contiguous, of shapes [K+1], [K, n], [n, 3]")
+            for a, shape, dt in ((e, (self.K + 1,), np.float64), (ph, (self.K, n), rdt), (f, (n, 3), rdt)):
+                if a is not None and (a.dtype != dt or a.shape != shape or not a.flags.c_contiguous):
+                    raise ValueError("out arrays must be C-contiguous, of shapes [K+1], [K, n], [n, 3] and the "
+                                     "dtypes float64, then float64 or (real=True) the plan's precision")
         else:
             e = np.empty(self.K + 1)
-            ph = np.empty((self.K, n)) if phi else None
-            f = np.empty((n, 3)) if forces else None
+            ph = np.empty((self.K, n), dtype=rdt) if phi else None
+            f = np.empty((n, 3), dtype=rdt) if forces else None
         dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None
         self._stream()
-        _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)
+        if real:
+            _check(lib().pswf_compute_host_real(self._h, n, dp(pos), vp(q), dp(e), vp(ph), vp(f)), self._h)
+        else:
+            _check(lib().pswf_compute_host(self._h, n, dp(pos), dp(q), dp(e), dp(ph), dp(f)), self._h)
         return e, ph, f
 
 

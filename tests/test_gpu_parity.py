@@ -156,9 +156,10 @@ def test_compute_host_chunked_matches_device_path(precision):
 
 
 def _pinned(a):
-    """A numpy array in page-locked host memory holding a copy of a."""
+    """A numpy array in page-locked host memory holding a copy of a (same
+    dtype, float32 or float64)."""
     import torch
-    t = torch.empty(a.shape, dtype=torch.float64).pin_memory()
+    t = torch.empty(a.shape, dtype=torch.float32 if a.dtype == np.float32 else torch.float64).pin_memory()
     out = t.numpy()
     out[...] = a
     return out, t   # the caller keeps t alive while out is in use
@@ -195,6 +196,41 @@ def test_compute_host_pinned_matches_device_path(precision, pinned):
         assert rel_rms(phi, phi0.cpu().double().numpy()) < 1e-6
         assert rel_rms(f, f0.cpu().double().numpy()) < 1e-6
 
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_compute_host_real_matches_device_path(precision, pinned):
+    """pswf_compute_host_real: charges, potentials and forces in the plan's
+    precision, copied as they are when page-locked and through the staging
+    buffers otherwise; equal to the device path on the same plan up to the
+    flush order."""
+    import torch
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    s = wl.random_system(300000, (60.0, 62.0, 64.0), (1, 6, 4, 2), seed=18, neutral=True)
+    plan = lr.Plan(s.box, s.n, s.ps, 6.0, P=6, grid=(64, 64, 64), precision=precision, device=dev)
+    rdt = np.float32 if precision == 0 else np.float64
+    qr = s.q.astype(rdt)
+    plan.set_points(torch.tensor(s.pos, device=dev), torch.tensor(qr, device=dev))
+    e0, phi0, f0 = plan.execute()
+    plan.sync()
+    keep = []
+    pos, q = s.pos, qr
+    out = (np.zeros(len(s.ps) + 1), np.zeros((len(s.ps), s.n), dtype=rdt), np.zeros((s.n, 3), dtype=rdt))
+    if pinned:
+        (pos, t1), (q, t2), (ph, t3), (ff, t4) = _pinned(s.pos), _pinned(qr), _pinned(out[1]), _pinned(out[2])
+        keep += [t1, t2, t3, t4]
+        out = (out[0], ph, ff)
+    for _ in range(2):
+        e, phi, f = plan.compute_host(pos, q, out=out, real=True)
+        assert phi.dtype == rdt and f.dtype == rdt
+        np.testing.assert_allclose(e, e0.cpu().numpy(), rtol=1e-6)
+        assert rel_rms(phi.astype(np.float64), phi0.cpu().double().numpy()) < 1e-6
+        assert rel_rms(f.astype(np.float64), f0.cpu().double().numpy()) < 1e-6
+    e, phi, f = plan.compute_host(pos, q, phi=False, forces=False, real=True)
+    assert phi is None and f is None
+    np.testing.assert_allclose(e, e0.cpu().numpy(), rtol=1e-6)
 
 def test_self_energy_matches_oracle():
     """E_self from the device FP64 reduction of the (FP32-stored) charges."""
