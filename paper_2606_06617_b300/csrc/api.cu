@@ -546,7 +546,7 @@ int64_t layout(pswf_plan p, char* base) {
     p->rs_rank = reinterpret_cast<int*>(take(nm * 4));
     p->rs_perm = reinterpret_cast<int*>(take(nm * 4));
     p->rs_scan = reinterpret_cast<int*>(take(int64_t(p->rs_nsb) * 4));
-    p->rs_lpos = take(int64_t(real_space_bytes_per_atom(K, int(rs))) * nm);   // test coordinates, records, rows
+    p->rs_lpos = take(int64_t(real_space_bytes_per_atom(K, int(rs))) * nm);   // coordinates, records, rows
   }
   {
     int64_t tw_pairs = 0;
@@ -1656,8 +1656,11 @@ int pswf_real_space_backward(pswf_plan pl, int64_t n, const void* pos, int pos_d
   a.coef_g = pl->coef_g;
   a.deg_g = pl->host.deg_g;
   a.cell_of = pl->rs_cellof;
+  a.rank = pl->rs_rank;
   a.cell_start = pl->rs_start;
   a.perm = pl->rs_perm;
+  a.lpos = pl->rs_lpos;
+  a.nmax = std::max<int64_t>(pl->n_max, 1);
   a.g_energy = g_energy;
   a.g_phi = g_phi;
   a.g_forces = g_forces;

@@ -71,8 +71,17 @@ namespace {
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kFixBits = 29;     // FP32 plans: cell-local unit w / 2^29; |dx| <= 2^30
-constexpr int kQueueCap = 176;   // queued pairs per lane; drained early only above kQueueCap - 32
-constexpr int kQueueStride = kQueueCap + 2;   // a lane's column: 89 words, so lanes start in distinct banks
+// queued pairs per lane (the backward's larger records leave room for
+// fewer); a queue is drained early only above its capacity - 32.  Columns
+// of an odd number of words, so the lanes' columns start in distinct banks.
+template <bool BW>
+__host__ __device__ constexpr int queue_cap() {
+  return BW ? 160 : 176;
+}
+template <bool BW>
+__host__ __device__ constexpr int queue_stride() {
+  return queue_cap<BW>() + 2;
+}
 constexpr int kCellBits = 11;    // queue entry: (half-shell slot << 11) | index within that cell
 constexpr int kMaxCellAtoms = 1 << kCellBits;
 // half shell: neighbour offsets o = (ox + 1) + 3 (oy + 1) + 9 (oz + 1) from
@@ -105,28 +114,32 @@ __host__ __device__ constexpr int rec_words() {
   return (3 + KC + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
 }
 
-// stage words per atom: the candidates' test coordinates (4) during the
-// sweep, the chunk's own records (RW) during a drain
-template <typename R, int KC>
-__host__ __device__ constexpr int stage_words() {
-  return rec_words<R, KC>() > 4 ? rec_words<R, KC>() : 4;
-}
-
-template <typename R, int KC>
-__host__ __device__ constexpr size_t warp_smem_bytes() {
-  // queue [32][kQueueStride] of 16-bit entries, stage [32][stage_words] R,
-  // half-shell starts and ends [2][14] and queue offsets [33] int (padded
-  // to 256 bytes)
-  return size_t(32) * kQueueStride * 2 + size_t(32) * stage_words<R, KC>() * sizeof(R) + 256;
-}
-static_assert(size_t(32) * kQueueStride * 2 % 16 == 0, "aligned stage");
-
 // accumulator row (cell order): KC potentials, 3 force components, zero
-// padding to whole 16-byte vectors
+// padding to whole 16-byte vectors.  The backward's rows hold dL/dq (KC)
+// and dL/dr (3), and its second record per atom gphi (KC) and gF (3) in the
+// same layout.
 template <typename R, int KC>
 __host__ __device__ constexpr int acc_words() {
   return (KC + 3 + kPerVec<R> - 1) / kPerVec<R> * kPerVec<R>;
 }
+
+// stage words per atom: the candidates' test coordinates (4) during the
+// sweep, the chunk's own records (RW, and AW upstream words in the
+// backward) during a drain
+template <typename R, int KC, bool BW>
+__host__ __device__ constexpr int stage_words() {
+  return BW ? rec_words<R, KC>() + acc_words<R, KC>() : (rec_words<R, KC>() > 4 ? rec_words<R, KC>() : 4);
+}
+
+template <typename R, int KC, bool BW>
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+  // queue [32][queue_stride] of 16-bit entries, stage [32][stage_words] R,
+  // half-shell starts and ends [2][14] and queue offsets [33] int (padded
+  // to 256 bytes)
+  return size_t(32) * queue_stride<BW>() * 2 + size_t(32) * stage_words<R, KC, BW>() * sizeof(R) + 256;
+}
+static_assert(size_t(32) * queue_stride<false>() * 2 % 16 == 0 && size_t(32) * queue_stride<true>() * 2 % 16 == 0,
+              "aligned stage");
 
 int channel_class(int K) { return K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : kRsMaxK; }
 
@@ -265,11 +278,11 @@ struct PairArgs {
   const int* cell_start;
   const R* lchk;     // [nmax][4]
   const R* rec;      // [nmax][rec_words]
-  const int* perm;
   const int* pch;
   const R* coef;     // [6][kMultSeg][deg + 1]
-  double* energy;
   R* acc;            // [nmax][acc_words], zeroed
+  const R* brec;     // backward: [nmax][acc_words] gphi, gF per atom (cell order)
+  const double* g_energy;   // backward: [K] or null
   int* err;
 };
 
@@ -304,22 +317,26 @@ __device__ inline void coords(const R* v, typename LocalT<R>::type& x, typename 
 // deg + 1 for the common degrees, so the Horner chains have no idle step).
 // The coefficient table in shared memory is [exponent][coefficient][piece]
 // of scalars: the 32 pieces lie in 32 banks, so a warp's loads are free of
-// bank conflicts whichever pieces its lanes need.
-template <typename R, int NC, int KC, bool TRIC>
+// bank conflicts whichever pieces its lanes need.  BW: the same sweep and
+// drain evaluate the backward (a.brec holds each atom's upstream gphi and gF
+// in cell order; the rows receive dL/dq and dL/dr).
+template <typename R, int NC, int KC, bool TRIC, bool BW>
 __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   using L = typename LocalT<R>::type;
   constexpr int RW = rec_words<R, KC>();
   constexpr int AW = acc_words<R, KC>();
+  constexpr int SW = stage_words<R, KC, BW>();
+  constexpr int QS = queue_stride<BW>();
   extern __shared__ __align__(16) unsigned char rs_smem[];
   R* coefs = reinterpret_cast<R*>(rs_smem);   // [6][NC][kMultSeg]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R* shv = reinterpret_cast<R*>(rs_smem + size_t(6) * kMultSeg * NC * sizeof(R));   // [kHalf][4] neighbour shifts
   unsigned char* wbase = rs_smem + size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) +
-                         size_t(warp) * warp_smem_bytes<R, KC>();
-  uint16_t* queues = reinterpret_cast<uint16_t*>(wbase);                        // [32][kQueueStride]
-  uint16_t* queue = queues + lane * kQueueStride;                               // this lane's column
-  R* stage = reinterpret_cast<R*>(wbase + 32 * kQueueStride * 2);   // [32][4] candidates or [32][RW] records
-  int* nbs = reinterpret_cast<int*>(stage + 32 * stage_words<R, KC>());         // [kHalf] neighbour starts
+                         size_t(warp) * warp_smem_bytes<R, KC, BW>();
+  uint16_t* queues = reinterpret_cast<uint16_t*>(wbase);                        // [32][QS]
+  uint16_t* queue = queues + lane * QS;                                         // this lane's column
+  R* stage = reinterpret_cast<R*>(wbase + 32 * QS * 2);   // [32][4] candidates or [32][SW] records
+  int* nbs = reinterpret_cast<int*>(stage + 32 * SW);                           // [kHalf] neighbour starts
   int* nbe = nbs + kHalf;                                                       // [kHalf] ends
   int* pref = nbe + kHalf;                                                      // [33] queue offsets
   {
@@ -351,6 +368,9 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
 #pragma unroll
   for (int c = 0; c < KC; ++c) prow[c] = c < a.K ? a.pch[c] - 1 : 0;
   R* const accp = a.acc;
+  R gEc[KC];   // backward: upstream gradient of the channel energies
+#pragma unroll
+  for (int c = 0; c < KC; ++c) gEc[c] = (BW && c < a.K && a.g_energy) ? R(a.g_energy[c]) : R(0);
 
   for (int cell = blockIdx.x * kRsWarps + warp; cell < ncell; cell += gridDim.x * kRsWarps) {
     const int c3[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
@@ -425,7 +445,18 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
             R v[kPerVec<R>];
 #pragma unroll
             for (int e = 0; e < kPerVec<R>; ++e) v[e] = rs[w + e];
-            store_vec<R>(stage + lane * RW + w, v);
+            store_vec<R>(stage + lane * SW + w, v);
+          }
+          if constexpr (BW) {
+            R bs[AW];
+            load_words<R, AW>(a.brec + int64_t(base + lane) * AW, bs);
+#pragma unroll
+            for (int w = 0; w < AW; w += kPerVec<R>) {
+              R v[kPerVec<R>];
+#pragma unroll
+              for (int e = 0; e < kPerVec<R>; ++e) v[e] = bs[w + e];
+              store_vec<R>(stage + lane * SW + RW + w, v);
+            }
           }
         }
         __syncwarp();
@@ -438,25 +469,33 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
           int t = e0 - pref[mo], tend = pref[mo + 1] - pref[mo];
           int io = base + mo / G;
           io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;   // checked build: a bad index reads row 0
-          R ro[RW];
-          load_words<R, RW>(stage + (mo / G) * RW, ro);
+          R ro[RW], bo[BW ? AW : 1];
+          load_words<R, RW>(stage + (mo / G) * SW, ro);
+          if constexpr (BW) load_words<R, AW>(stage + (mo / G) * SW + RW, bo);
           L ix, iy, iz;
           coords<R>(ro, ix, iy, iz);
+          // the i side: phi_i (forward) or dL/dq_i (backward) partial sums,
+          // and F_i or dL/dr_i
           R ph[KC];
 #pragma unroll
           for (int c = 0; c < KC; ++c) ph[c] = R(0);
           R fx = 0, fy = 0, fz = 0;
           // software-pipelined: the next entry's record is fetched while the
           // current pair is evaluated (the records come from L2)
-          uint32_t en = queues[mo * kQueueStride + t];
+          uint32_t en = queues[mo * QS + t];
           int jn = nbs[en >> kCellBits] + int(en & (kMaxCellAtoms - 1));
           jn = in_bounds(jn, a.n, kBoundsRsPair) ? jn : 0;
-          R rn[RW];
+          R rn[RW], bn[BW ? AW : 1];
           load_words<R, RW>(a.rec + int64_t(jn) * RW, rn);
+          if constexpr (BW) load_words<R, AW>(a.brec + int64_t(jn) * AW, bn);
           for (int e = e0; e < e1; ++e) {
-            R rj[RW];
+            R rj[RW], bj[BW ? AW : 1];
 #pragma unroll
             for (int w = 0; w < RW; ++w) rj[w] = rn[w];
+            if constexpr (BW) {
+#pragma unroll
+              for (int w = 0; w < AW; ++w) bj[w] = bn[w];
+            }
             const int j = jn;
             const int o = kSelf + int(en >> kCellBits);
             const bool more = e + 1 < e1;
@@ -468,10 +507,11 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
                 } while (pref[mn + 1] == pref[mn]);
                 tn = 0;
               }
-              en = queues[mn * kQueueStride + tn];
+              en = queues[mn * QS + tn];
               jn = nbs[en >> kCellBits] + int(en & (kMaxCellAtoms - 1));
               jn = in_bounds(jn, a.n, kBoundsRsPair) ? jn : 0;
               load_words<R, RW>(a.rec + int64_t(jn) * RW, rn);
+              if constexpr (BW) load_words<R, AW>(a.brec + int64_t(jn) * AW, bn);
             }
             const int o3 = o / 3;
             const int ox = o - 3 * o3 - 1, oy = o3 - 3 * (o3 / 3) - 1, oz = o3 / 3 - 1;
@@ -509,35 +549,82 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
               int seg = int(x * R(kMultSeg));
               if (seg > kMultSeg - 1) seg = kMultSeg - 1;
               const R sv = R(2) * (x * R(kMultSeg) - R(seg)) - R(1);
-              R fsum = 0;   // sum_c q_i^c q_j^c f_p'(r)
-              R pj[KC];     // phi_j^c += q_i^c f_p(r)
+              // forward: pj = q_i^c f_p (phi_j), g = the force on i (F_j -= g);
+              // backward: pj = dL/dq_j^c, g = dL/dr_i (dL/dr_j -= g)
+              R pj[KC];
+              R gx, gy, gz;
+              if constexpr (!BW) {
+                R fsum = 0;   // sum_c q_i^c q_j^c f_p'(r)
 #pragma unroll
-              for (int c = 0; c < KC; ++c) {
-                R cf[NC];
-                const R* cp = coefs + prow[c] * NC * kMultSeg + seg;
+                for (int c = 0; c < KC; ++c) {
+                  R cf[NC];
+                  const R* cp = coefs + prow[c] * NC * kMultSeg + seg;
 #pragma unroll
-                for (int k = 0; k < NC; ++k) cf[k] = cp[k * kMultSeg];
-                R Gv = cf[NC - 1], dG = R(0);
+                  for (int k = 0; k < NC; ++k) cf[k] = cp[k * kMultSeg];
+                  R Gv = cf[NC - 1], dG = R(0);
 #pragma unroll
-                for (int k = NC - 2; k >= 0; --k) {
-                  dG = dG * sv + Gv;
-                  Gv = Gv * sv + cf[k];
+                  for (int k = NC - 2; k >= 0; --k) {
+                    dG = dG * sv + Gv;
+                    Gv = Gv * sv + cf[k];
+                  }
+                  dG *= R(2 * kMultSeg);                       // dG / dx
+                  const int p = prow[c] + 1;                    // r^-p from the bits of p
+                  const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
+                  const R one_m = R(1) - Gv;
+                  const R fc = one_m * rp;
+                  const R qj = rj[3 + c];
+                  ph[c] += qj * fc;
+                  pj[c] = ro[3 + c] * fc;
+                  fsum -= ro[3 + c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
                 }
-                dG *= R(2 * kMultSeg);                       // dG / dx
-                const int p = prow[c] + 1;                    // r^-p from the bits of p
-                const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
-                const R one_m = R(1) - Gv;
-                const R fc = one_m * rp;
-                const R qj = rj[3 + c];
-                ph[c] += qj * fc;
-                pj[c] = ro[3 + c] * fc;
-                fsum -= ro[3 + c] * qj * (dG * inv_rc + R(p) * one_m * inv_r) * rp;
+                const R sc = fsum * inv_r;
+                gx = sc * dx;
+                gy = sc * dy;
+                gz = sc * dz;
+              } else {
+                // the vector-Jacobian product of (E_c, phi, F) for upstream
+                // (g_E, g_phi, g_F), per pair: with d = r_i - r_j, f = f_p,
+                // h = -f'/r, h' = dh/dr and u = (gF_i - gF_j) . d,
+                //   dL/dq_i^c += (g_E q_j + gphi_j) f + q_j h u  (j: i <-> j)
+                //   dL/dr_i  += [-sum_c (g_E q_i q_j + gphi_i q_j + gphi_j q_i) h
+                //               + sum_c q_i q_j h' u / r] d + sum_c q_i q_j h (gF_i - gF_j)
+                // and dL/dr_j the opposite (the force term's Jacobian is
+                // w I + (w'/r) d d^T); G_p with two derivatives
+                const R dg0 = bo[KC] - bj[KC], dg1 = bo[KC + 1] - bj[KC + 1], dg2 = bo[KC + 2] - bj[KC + 2];
+                const R u = -(dx * dg0 + dy * dg1 + dz * dg2);   // (dx, dy, dz) = r_j - r_i
+                const R dsx = R(2 * kMultSeg) * inv_rc;          // d sv / d r
+                R scal = 0, w = 0;
+#pragma unroll
+                for (int c = 0; c < KC; ++c) {
+                  const R* cp = coefs + prow[c] * NC * kMultSeg + seg;
+                  R g0 = cp[(NC - 1) * kMultSeg], g1 = R(0), g2 = R(0);   // G, G' and G'' / 2 in sv
+#pragma unroll
+                  for (int k = NC - 2; k >= 0; --k) {
+                    g2 = g2 * sv + g1;
+                    g1 = g1 * sv + g0;
+                    g0 = g0 * sv + cp[k * kMultSeg];
+                  }
+                  const R Gr = g1 * dsx, Grr = R(2) * g2 * dsx * dsx;   // dG/dr, d2G/dr2
+                  const int p = prow[c] + 1;
+                  const R rp = ((p & 1) ? inv_r : R(1)) * ((p & 2) ? ir2 : R(1)) * ((p & 4) ? ir4 : R(1));
+                  const R f = (R(1) - g0) * rp;
+                  const R f1 = -Gr * rp - R(p) * f * inv_r;
+                  const R f2 = -Grr * rp + R(2 * p) * Gr * rp * inv_r + R(p * (p + 1)) * f * ir2;
+                  const R h = -f1 * inv_r, h1 = -f2 * inv_r + f1 * ir2;
+                  const R qi = ro[3 + c], qj = rj[3 + c], gpi = bo[c], gpj = bj[c];
+                  ph[c] += (gEc[c] * qj + gpj) * f + qj * h * u;
+                  pj[c] = (gEc[c] * qi + gpi) * f + qi * h * u;
+                  scal += -(gEc[c] * qi * qj + gpi * qj + gpj * qi) * h + qi * qj * h1 * u * inv_r;
+                  w += qi * qj * h;
+                }
+                gx = w * dg0 - scal * dx;
+                gy = w * dg1 - scal * dy;
+                gz = w * dg2 - scal * dz;
               }
-              const R sc = fsum * inv_r;   // F_i += sc d, F_j -= sc d
-              fx += sc * dx;
-              fy += sc * dy;
-              fz += sc * dz;
-              add_row<R, KC>(accp + int64_t(j) * AW, pj, -sc * dx, -sc * dy, -sc * dz, a.K);
+              fx += gx;
+              fy += gy;
+              fz += gz;
+              add_row<R, KC>(accp + int64_t(j) * AW, pj, -gx, -gy, -gz, a.K);
             }
             if (!more || mn != mo) {   // atom io is done in this range
               add_row<R, KC>(accp + int64_t(io) * AW, ph, fx, fy, fz, a.K);
@@ -546,7 +633,8 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
                 tend = pref[mo + 1] - pref[mo];
                 io = base + mo / G;
                 io = in_bounds(io, a.n, kBoundsRsPair) ? io : 0;
-                load_words<R, RW>(stage + (mo / G) * RW, ro);
+                load_words<R, RW>(stage + (mo / G) * SW, ro);
+                if constexpr (BW) load_words<R, AW>(stage + (mo / G) * SW + RW, bo);
                 coords<R>(ro, ix, iy, iz);
 #pragma unroll
                 for (int c = 0; c < KC; ++c) ph[c] = R(0);
@@ -566,7 +654,7 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
         const uint32_t tag = uint32_t(s) << kCellBits;
         const int jlo = s == 0 ? i + 1 : 0;   // within the cell: j > i only
         for (int jb = b0; jb < b1; jb += 32) {
-          if (__reduce_max_sync(0xffffffffu, len) > kQueueCap - 32) drain();
+          if (__reduce_max_sync(0xffffffffu, len) > queue_cap<BW>() - 32) drain();
           const int cnt = min(32, b1 - jb);
           // one coalesced load of up to 32 candidates into the warp's stage
           if (lane < cnt)
@@ -840,8 +928,9 @@ cudaError_t launch_direct(const RealSpaceArgs& a, cudaStream_t s) {
 //                       + (w' / r) d . (gF_i - gF_j) ] d + w (gF_i - gF_j),
 //   w = sum_c q_i^c q_j^c h,  w' = sum_c q_i^c q_j^c h'
 // (the force term's Jacobian is w I + (w'/r) d d^T), so G_p is evaluated with
-// its first two derivatives.  One thread per atom; candidates from the 27
-// list cells around it (or, in direct mode, every atom and image).
+// its first two derivatives.  Direct mode (cells too small for a list): one
+// thread per atom over every atom and image.  With a cell list the pair
+// kernel's backward mode evaluates the same terms once per pair.
 constexpr int kRsBwThreads = 128;
 
 template <typename R>
@@ -905,7 +994,7 @@ __global__ void __launch_bounds__(kRsBwThreads) k_rs_bw(RealSpaceBwArgs a) {
     const int k = t % NC, rs = t / NC;   // rs = row * kMultSeg + seg
     cs[t] = k <= a.deg_g ? coef[size_t(rs) * (a.deg_g + 1) + k] : R(0);
   }
-  const int nimages = g.direct ? (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1) : 0;
+  const int nimages = (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1);
   for (int t = threadIdx.x; t < nimages; t += blockDim.x) {
     const int n0 = t % (2 * g.nimg[0] + 1) - g.nimg[0];
     const int n1 = (t / (2 * g.nimg[0] + 1)) % (2 * g.nimg[1] + 1) - g.nimg[1];
@@ -955,26 +1044,8 @@ __global__ void __launch_bounds__(kRsBwThreads) k_rs_bw(RealSpaceBwArgs a) {
     rs_bw_pair<R, NC, KC>(d, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], cs, prow, inv_rc, qi, gpi, gEc, gFi, qj, gpj,
                           gFj, acc, gr);
   };
-  if (g.direct) {
-    for (int64_t j = 0; j < n; ++j)
-      for (int t = 0; t < nimages; ++t) visit(j, img + 3 * t);
-  } else {
-    const int cell = a.cell_of[i];
-    const int ci[3] = {cell % g.nc[0], (cell / g.nc[0]) % g.nc[1], cell / (g.nc[0] * g.nc[1])};
-    for (int o = 0; o < 27; ++o) {
-      int nb[3], wr[3];
-      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-      for (int d = 0; d < 3; ++d) {
-        nb[d] = ci[d] + off[d];
-        wr[d] = nb[d] < 0 ? -1 : (nb[d] >= g.nc[d] ? 1 : 0);
-        nb[d] -= wr[d] * g.nc[d];
-      }
-      double shift[3];
-      for (int k = 0; k < 3; ++k) shift[k] = wr[0] * g.h[k] + wr[1] * g.h[3 + k] + wr[2] * g.h[6 + k];
-      const int c = (nb[2] * g.nc[1] + nb[1]) * g.nc[0] + nb[0];
-      for (int m = a.cell_start[c]; m < a.cell_start[c + 1]; ++m) visit(a.perm[m], shift);
-    }
-  }
+  for (int64_t j = 0; j < n; ++j)
+    for (int t = 0; t < nimages; ++t) visit(j, img + 3 * t);
   R* gq = static_cast<R*>(a.grad_q);
   R* gp = static_cast<R*>(a.grad_pos);
 #pragma unroll
@@ -990,7 +1061,7 @@ __global__ void __launch_bounds__(kRsBwThreads) k_rs_bw(RealSpaceBwArgs a) {
 template <typename R, typename PosT, int NC, int KC>
 cudaError_t launch_bw_k(const RealSpaceBwArgs& a, cudaStream_t s) {
   const RealSpaceGeom& g = a.geo;
-  const int nimages = g.direct ? (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1) : 0;
+  const int nimages = (2 * g.nimg[0] + 1) * (2 * g.nimg[1] + 1) * (2 * g.nimg[2] + 1);
   const size_t smem = (size_t(6) * kMultSeg * NC * sizeof(R) + 15) / 16 * 16 + size_t(nimages) * 3 * sizeof(double);
   const cudaError_t ea =
       cudaFuncSetAttribute(k_rs_bw<R, PosT, NC, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1011,21 +1082,92 @@ cudaError_t launch_bw(const RealSpaceBwArgs& a, cudaStream_t s) {
   }
 }
 
-}  // namespace
-
-template <typename R>
-cudaError_t real_space_backward_run(const RealSpaceBwArgs& a, cudaStream_t s, int* nlaunch) {
-  if (a.n == 0) return cudaSuccess;
-  if (a.deg_g + 1 > 18) return cudaErrorInvalidValue;
-  cudaError_t e = a.pos_dtype == 1 ? launch_bw<R, double, 18>(a, s) : launch_bw<R, float, 18>(a, s);
-  if (e == cudaSuccess) ++*nlaunch;
-  return e;
+// backward of the cell-list path: each atom's upstream gphi (KC) and gF (3)
+// to a record in cell order, and the accumulator rows zeroed
+template <typename R, int KC>
+__global__ void __launch_bounds__(kRsThreads) k_rs_bw_scatter(int64_t n, int K, const R* __restrict__ g_phi,
+                                                              const R* __restrict__ g_forces,
+                                                              const int* __restrict__ cell_of,
+                                                              const int* __restrict__ rank,
+                                                              const int* __restrict__ cell_start,
+                                                              R* __restrict__ brec, R* __restrict__ acc) {
+  constexpr int AW = acc_words<R, KC>();
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = int64_t(cell_start[cell_of[i]]) + rank[i];
+    if (!in_bounds(m, n, kBoundsRsScatter)) continue;
+    R v[AW];
+#pragma unroll
+    for (int w = 0; w < AW; ++w) v[w] = R(0);
+#pragma unroll
+    for (int c = 0; c < KC; ++c)
+      if (c < K && g_phi) v[c] = g_phi[int64_t(c) * n + i];
+    if (g_forces) {
+      v[KC] = g_forces[3 * i];
+      v[KC + 1] = g_forces[3 * i + 1];
+      v[KC + 2] = g_forces[3 * i + 2];
+    }
+#pragma unroll
+    for (int w = 0; w < AW; w += kPerVec<R>) {
+      R x[kPerVec<R>], z[kPerVec<R>];
+#pragma unroll
+      for (int e = 0; e < kPerVec<R>; ++e) {
+        x[e] = v[w + e];
+        z[e] = R(0);
+      }
+      store_vec<R>(brec + m * AW + w, x);
+      store_vec<R>(acc + m * AW + w, z);
+    }
+  }
 }
 
-template cudaError_t real_space_backward_run<float>(const RealSpaceBwArgs&, cudaStream_t, int*);
-template cudaError_t real_space_backward_run<double>(const RealSpaceBwArgs&, cudaStream_t, int*);
+// rows (dL/dq, dL/dr in cell order) to grad_q real [K][n] and grad_pos real
+// [n][3] (either may be null), atoms in their original order
+template <typename R, int KC>
+__global__ void __launch_bounds__(kRsThreads) k_rs_bw_finish(int64_t n, int K, const R* __restrict__ acc,
+                                                             const int* __restrict__ cell_of,
+                                                             const int* __restrict__ rank,
+                                                             const int* __restrict__ cell_start,
+                                                             R* __restrict__ grad_q, R* __restrict__ grad_pos) {
+  constexpr int AW = acc_words<R, KC>();
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = int64_t(cell_start[cell_of[i]]) + rank[i];
+    if (!in_bounds(m, n, kBoundsRsFinish)) continue;
+    R row[AW];
+    load_words<R, AW>(acc + m * AW, row);
+    if (grad_q) {
+#pragma unroll
+      for (int c = 0; c < KC; ++c)
+        if (c < K) grad_q[int64_t(c) * n + i] = row[c];
+    }
+    if (grad_pos) {
+      grad_pos[3 * i] = row[KC];
+      grad_pos[3 * i + 1] = row[KC + 1];
+      grad_pos[3 * i + 2] = row[KC + 2];
+    }
+  }
+}
 
-namespace {
+template <typename R>
+cudaError_t launch_bw_rows(const RealSpaceBwArgs& a, R* brec, R* acc, bool finish, int blocks, cudaStream_t s) {
+  const R* gp = static_cast<const R*>(a.g_phi);
+  const R* gf = static_cast<const R*>(a.g_forces);
+  R* gq = static_cast<R*>(a.grad_q);
+  R* gr = static_cast<R*>(a.grad_pos);
+#define PSWF_RS_BW_ROWS(KC)                                                                                        \
+  if (finish)                                                                                                      \
+    k_rs_bw_finish<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, acc, a.cell_of, a.rank, a.cell_start, gq, gr);    \
+  else                                                                                                             \
+    k_rs_bw_scatter<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, gp, gf, a.cell_of, a.rank, a.cell_start, brec, acc)
+  switch (channel_class(a.K)) {
+    case 1: PSWF_RS_BW_ROWS(1); break;
+    case 2: PSWF_RS_BW_ROWS(2); break;
+    case 4: PSWF_RS_BW_ROWS(4); break;
+    case 8: PSWF_RS_BW_ROWS(8); break;
+    default: PSWF_RS_BW_ROWS(kRsMaxK); break;
+  }
+#undef PSWF_RS_BW_ROWS
+  return cudaGetLastError();
+}
 
 __global__ void k_rs_total(int K, double* __restrict__ energy) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1035,39 +1177,53 @@ __global__ void k_rs_total(int K, double* __restrict__ energy) {
   }
 }
 
-template <typename R, int NC, int KC, bool TRIC>
+template <typename R, int NC, int KC, bool TRIC, bool BW>
 cudaError_t launch_pairs_t(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  const size_t smem =
-      size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) + size_t(kRsWarps) * warp_smem_bytes<R, KC>();
+  const size_t smem = size_t(6) * kMultSeg * NC * sizeof(R) + kHalf * 4 * sizeof(R) +
+                      size_t(kRsWarps) * warp_smem_bytes<R, KC, BW>();
   // set on every launch: the opt-in is per device and cheap
-  const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC, TRIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(smem));
+  const cudaError_t ea = cudaFuncSetAttribute(k_rs_pairs<R, NC, KC, TRIC, BW>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (ea != cudaSuccess) return ea;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pairs<R, NC, KC, TRIC>, kRsThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_pairs<R, NC, KC, TRIC, BW>, kRsThreads, smem);
   const int64_t want = (int64_t(ncell) + kRsWarps - 1) / kRsWarps;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(std::max(nsm, 1)) * std::max(per_sm, 1))));
-  k_rs_pairs<R, NC, KC, TRIC><<<blocks, kRsThreads, smem, s>>>(pa);
+  k_rs_pairs<R, NC, KC, TRIC, BW><<<blocks, kRsThreads, smem, s>>>(pa);
   return cudaGetLastError();
 }
 
 // general cells transform displacements with the full 3 x 3 edge matrix
-template <typename R, int NC, int KC>
+template <typename R, int NC, int KC, bool BW>
 cudaError_t launch_pairs_k(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
-  return pa.g.tric ? launch_pairs_t<R, NC, KC, true>(pa, ncell, s) : launch_pairs_t<R, NC, KC, false>(pa, ncell, s);
+  return pa.g.tric ? launch_pairs_t<R, NC, KC, true, BW>(pa, ncell, s)
+                   : launch_pairs_t<R, NC, KC, false, BW>(pa, ncell, s);
 }
 
-template <typename R, int NC>
-cudaError_t launch_pairs(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
+template <typename R, int NC, bool BW>
+cudaError_t launch_pairs_nc(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
   switch (channel_class(pa.K)) {
-    case 1: return launch_pairs_k<R, NC, 1>(pa, ncell, s);
-    case 2: return launch_pairs_k<R, NC, 2>(pa, ncell, s);
-    case 4: return launch_pairs_k<R, NC, 4>(pa, ncell, s);
-    case 8: return launch_pairs_k<R, NC, 8>(pa, ncell, s);
-    default: return launch_pairs_k<R, NC, kRsMaxK>(pa, ncell, s);
+    case 1: return launch_pairs_k<R, NC, 1, BW>(pa, ncell, s);
+    case 2: return launch_pairs_k<R, NC, 2, BW>(pa, ncell, s);
+    case 4: return launch_pairs_k<R, NC, 4, BW>(pa, ncell, s);
+    case 8: return launch_pairs_k<R, NC, 8, BW>(pa, ncell, s);
+    default: return launch_pairs_k<R, NC, kRsMaxK, BW>(pa, ncell, s);
   }
+}
+
+// coefficients per piece: the FP32 fit's usual degree 6 exactly, else padded
+// (the planner's degree is at most kMaxMultDeg = 16)
+template <typename R, bool BW>
+cudaError_t launch_pairs(const PairArgs<R>& pa, int ncell, cudaStream_t s) {
+  static_assert(kMaxMultDeg + 1 <= 17, "coefficient rows");
+  if constexpr (std::is_same<R, float>::value) {
+    if (pa.deg + 1 <= 7) return launch_pairs_nc<R, 7, BW>(pa, ncell, s);
+    if constexpr (!BW)
+      if (pa.deg + 1 <= 8) return launch_pairs_nc<R, 8, BW>(pa, ncell, s);
+  }
+  return launch_pairs_nc<R, 17, BW>(pa, ncell, s);
 }
 
 template <typename R>
@@ -1114,8 +1270,9 @@ cudaError_t launch_finish(const RealSpaceArgs& a, const R* acc, int blocks, cuda
 }  // namespace
 
 size_t real_space_bytes_per_atom(int K, int real_size) {
-  return real_size == 4 ? (4 + size_t(record_words<float>(K)) + size_t(accumulator_words<float>(K))) * 4
-                        : (4 + size_t(record_words<double>(K)) + size_t(accumulator_words<double>(K))) * 8;
+  // test coordinates, records, accumulator rows, the backward's upstream records
+  return real_size == 4 ? (4 + size_t(record_words<float>(K)) + size_t(2 * accumulator_words<float>(K))) * 4
+                        : (4 + size_t(record_words<double>(K)) + size_t(2 * accumulator_words<double>(K))) * 8;
 }
 
 bool real_space_geometry_cell(const double H[9], double r_c, RealSpaceGeom& g) {
@@ -1232,22 +1389,13 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
     pa.cell_start = a.cell_start;
     pa.lchk = lchk;
     pa.rec = rec;
-    pa.perm = a.perm;
     pa.pch = a.pch;
     pa.coef = static_cast<const R*>(a.coef_g);
-    pa.energy = a.energy;
     pa.acc = acc;
+    pa.brec = nullptr;
+    pa.g_energy = nullptr;
     pa.err = a.err;
-    // coefficients per piece: the FP32 fit's usual degree 6 exactly, else
-    // padded (the planner's degree is at most kMaxMultDeg = 16)
-    static_assert(kMaxMultDeg + 1 <= 17, "coefficient rows");
-    if constexpr (std::is_same<R, float>::value) {
-      e = a.deg_g + 1 <= 7 ? launch_pairs<R, 7>(pa, ncell, s)
-                           : (a.deg_g + 1 <= 8 ? launch_pairs<R, 8>(pa, ncell, s) : launch_pairs<R, 17>(pa, ncell, s));
-    } else {
-      e = launch_pairs<R, 17>(pa, ncell, s);
-    }
-    if (e != cudaSuccess) return e;
+    if ((e = launch_pairs<R, false>(pa, ncell, s)) != cudaSuccess) return e;
     *nlaunch += 2;
     if ((e = launch_finish<R>(a, acc, blocks, s)) != cudaSuccess) return e;
     ++*nlaunch;
@@ -1261,5 +1409,50 @@ int bounds_word_real_space() { return take_bounds_word(); }
 
 template cudaError_t real_space_run<float>(const RealSpaceArgs&, cudaStream_t, int*);
 template cudaError_t real_space_run<double>(const RealSpaceArgs&, cudaStream_t, int*);
+
+// Backward: direct mode one thread per atom over every pair and image
+// (k_rs_bw); cell lists reuse the forward's list, records and test
+// coordinates: the upstream gradients to records in cell order, the pair
+// kernel in its backward mode, the rows to the caller's layouts.
+template <typename R>
+cudaError_t real_space_backward_run(const RealSpaceBwArgs& a, cudaStream_t s, int* nlaunch) {
+  if (a.n == 0) return cudaSuccess;
+  if (a.deg_g + 1 > 18) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (a.geo.direct) {
+    e = a.pos_dtype == 1 ? launch_bw<R, double, 18>(a, s) : launch_bw<R, float, 18>(a, s);
+    if (e == cudaSuccess) ++*nlaunch;
+    return e;
+  }
+  const int rw = record_words<R>(a.K), aw = accumulator_words<R>(a.K);
+  R* lchk = static_cast<R*>(a.lpos);
+  R* rec = lchk + 4 * a.nmax;
+  R* acc = rec + int64_t(rw) * a.nmax;
+  R* brec = acc + int64_t(aw) * a.nmax;
+  const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((a.n + kRsThreads - 1) / kRsThreads, 148 * 16)));
+  if ((e = launch_bw_rows<R>(a, brec, acc, false, blocks, s)) != cudaSuccess) return e;
+  PairArgs<R> pa;
+  pa.g = a.geo;
+  pa.n = a.n;
+  pa.K = a.K;
+  pa.deg = a.deg_g;
+  pa.cell_start = a.cell_start;
+  pa.lchk = lchk;
+  pa.rec = rec;
+  pa.pch = a.pch;
+  pa.coef = static_cast<const R*>(a.coef_g);
+  pa.acc = acc;
+  pa.brec = brec;
+  pa.g_energy = a.g_energy;
+  pa.err = a.err;
+  const int ncell = a.geo.nc[0] * a.geo.nc[1] * a.geo.nc[2];
+  if ((e = launch_pairs<R, true>(pa, ncell, s)) != cudaSuccess) return e;
+  if ((e = launch_bw_rows<R>(a, brec, acc, true, blocks, s)) != cudaSuccess) return e;
+  *nlaunch += 3;
+  return cudaSuccess;
+}
+
+template cudaError_t real_space_backward_run<float>(const RealSpaceBwArgs&, cudaStream_t, int*);
+template cudaError_t real_space_backward_run<double>(const RealSpaceBwArgs&, cudaStream_t, int*);
 
 }  // namespace pswf

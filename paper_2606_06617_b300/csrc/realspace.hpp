@@ -30,7 +30,8 @@ struct RealSpaceGeom {
 constexpr int kRsDirectMaxAtoms = 16384;   // direct mode: O(n^2 images) work
 constexpr int kRsDirectMaxImages = 4096;
 
-// Device bytes per atom of the cell-local coordinates and records.
+// Device bytes per atom of the cell-local coordinates, records, accumulator
+// rows and the backward's upstream records.
 size_t real_space_bytes_per_atom(int K, int real_size);
 
 // Cell list when every height of the cell holds 3 list cells of height
@@ -85,8 +86,11 @@ struct RealSpaceBwArgs {
   const void* coef_g;   // device real [6][kMultSeg][deg_g + 1]
   int deg_g;
   const int* cell_of;     // [n] list cell of each atom (cell-list mode)
+  const int* rank;        // [n] its slot within the cell
   const int* cell_start;  // [ncell + 1]
   const int* perm;        // [n] original index of each sorted slot
+  void* lpos;             // the forward's test coordinates, records and rows
+  int64_t nmax;
   const double* g_energy; // device [K] or null
   const void* g_phi;      // real [K][n] or null
   const void* g_forces;   // real [n][3] or null
