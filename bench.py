@@ -354,6 +354,20 @@ def run_total(steps: int, warmup: int, cpu_baseline: bool = True, wk: str = "mel
     stage_ms, launches = plan.profile_read()
     plan.sync()
     ms = e0.elapsed_time(e1) / steps
+    # the real-space backward (vector-Jacobian product for a force-matching
+    # style upstream: g_E = 1, g_phi and g_F random), after the forward of
+    # the last step
+    g_e = torch.ones(K, dtype=torch.float64, device=dev)
+    g_phi = torch.randn(K, s.n, device=dev)
+    g_f = torch.randn(s.n, 3, device=dev)
+    plan.real_space_backward(pos, q, g_energy=g_e, g_phi=g_phi, g_forces=g_f)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.real_space_backward(pos, q, g_energy=g_e, g_phi=g_phi, g_forces=g_f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync()
+    bw_ms = e0.elapsed_time(e1) / steps
     info = dict(plan.info)
     deg = int(info["deg_real"])
     alg = real_space_flops(w, K, s.n, deg)
@@ -380,6 +394,7 @@ def run_total(steps: int, warmup: int, cpu_baseline: bool = True, wk: str = "mel
                      "traffic": load_traffic(w["name"], "real_space"), "algorithmic_flops_per_launch": alg["flops"],
                      "expected_candidates": alg["candidates"], "expected_pairs": alg["pairs"]},
         "stages_ms_per_step": {k: v / steps for k, v in stage_ms.items()},
+        "real_space_backward_ms": bw_ms,
         "gpu_launches": int(sum(launches.values())),
         "clocks": clocks,
         "e2e": None,
@@ -889,7 +904,7 @@ def main():
         # the complete evaluation (reciprocal + real space) of the same melt
         total = run_total(max(3, min(args.steps, 10)), 3, cpu_baseline=False)
         total = {k: total[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "roofline",
-                                       "stages_ms_per_step", "gpu_launches", "clocks")}
+                                       "stages_ms_per_step", "real_space_backward_ms", "gpu_launches", "clocks")}
         torch.cuda.empty_cache()
         if not args.no_serving:
             serving = run_serving()
