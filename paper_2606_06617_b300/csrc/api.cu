@@ -796,10 +796,19 @@ int multiply(pswf_plan p, int want_energy, void* data) {
                                                            want_energy, want_energy ? p->vpart : nullptr);
     return launch_check(p, "k_multiply_planes");
   }
+  if (!(want_energy && p->vpart)) {
+    // channels in chunks of kMultGroup per work item, the multiplier once per distinct exponent
+    static_assert(kThreads == 256, "k_multiply_group's block sums assume 8 warps");
+    const dim3 ggrid(p->eblk, p->nrun * ((h.K + kMultGroup - 1) / kMultGroup));
+    k_multiply_group<R><<<ggrid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->bmat,
+                                                           static_cast<const R*>(p->coef_m),
+                                                           static_cast<const R*>(p->iw2), p->Mh, p->epart,
+                                                           want_energy);
+    return launch_check(p, "k_multiply_group");
+  }
   k_multiply<R><<<grid, kThreads, 0, p->stream>>>(static_cast<Cplx<R>*>(data), mp, p->pch, p->scale, p->bmat,
                                                   static_cast<const R*>(p->coef_m), static_cast<const R*>(p->iw2),
-                                                  p->Mh, p->epart, want_energy,
-                                                  want_energy ? p->vpart : nullptr);
+                                                  p->Mh, p->epart, want_energy, p->vpart);
   return launch_check(p, "k_multiply");
 }
 

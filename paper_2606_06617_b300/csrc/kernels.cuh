@@ -603,6 +603,136 @@ __global__ void __launch_bounds__(256) k_multiply(Cplx<R>* __restrict__ data, Mu
   block_partials(e.value(), vt, part, vpart, size_t(g) * gridDim.x + blockIdx.x);
 }
 
+// The same multiplier for up to kMultGroup channels of one structure per
+// work item (blockIdx.y = s nchunk + chunk, chunks of consecutive channels):
+// a mode's k, window correction and piece are found once, the smooth part
+// S_p and its singular factor once per distinct exponent of the chunk (so
+// channels that share an exponent share them), and each channel only scales
+// its mode and adds its energy.  Coefficients from shared memory.  No virial
+// sums (plans that want them keep k_multiply).  Energy partials at the same
+// [g][block] slots as k_multiply.
+constexpr int kMultGroup = 8;
+template <typename R>
+__global__ void __launch_bounds__(256) k_multiply_group(Cplx<R>* __restrict__ data, MultParams mp,
+                                                        const int* __restrict__ pch, const double* __restrict__ scale,
+                                                        const double* __restrict__ bmat, const R* __restrict__ coef,
+                                                        const R* __restrict__ iw2, int iw2_stride,
+                                                        double* __restrict__ part, int want_energy) {
+  __shared__ R cs_s[6 * kMultSeg * (kMaxMultDeg + 1)];
+  __shared__ int pu_s[kMultGroup], cu_s[kMultGroup], nu_s;
+  __shared__ double esum[kMultGroup][8];
+  const int nchunk = (mp.K + kMultGroup - 1) / kMultGroup;
+  const int s = blockIdx.y / nchunk, chunk = blockIdx.y - s * nchunk;
+  const int c0 = chunk * kMultGroup, nc = min(kMultGroup, mp.K - c0);
+  const int g0 = s * mp.K + c0;
+  if (threadIdx.x == 0) {
+    // the chunk's distinct exponents in first-seen order, and each channel's index among them
+    int nu = 0;
+    for (int c = 0; c < nc; ++c) {
+      const int p = pch[g0 + c];
+      int u = 0;
+      while (u < nu && pu_s[u] != p) ++u;
+      if (u == nu) pu_s[nu++] = p;
+      cu_s[c] = u;
+    }
+    nu_s = nu;
+  }
+  for (int t = threadIdx.x; t < 6 * kMultSeg * (mp.deg + 1); t += blockDim.x) cs_s[t] = coef[t];
+  __syncthreads();
+  const int nu = nu_s;
+  R sc[kMultGroup];
+  const int nrow = mp.M[1] * mp.M[2];
+  const int64_t nel = int64_t(nrow) * mp.Mxh;
+  Cplx<R>* const d0 = data + int64_t(g0) * nel;   // channel c0 + c at d0 + c nel
+#pragma unroll
+  for (int c = 0; c < kMultGroup; ++c) sc[c] = c < nc ? R(scale[g0 + c]) : R(0);
+  const R* iw2x = iw2 + size_t(3 * s) * iw2_stride;
+  const R* iw2y = iw2x + iw2_stride;
+  const R* iw2z = iw2y + iw2_stride;
+  const R kc2 = R(1.0 / (mp.inv_kc * mp.inv_kc));
+  const R inv_kc = R(mp.inv_kc);
+  R bm[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) bm[i] = R(bmat[9 * s + i]);
+  const bool even_x = (mp.M[0] % 2) == 0;
+  EnergyAcc<R> e[kMultGroup];
+  const int64_t el0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int ix, iy, iz, sx, sy, sz;
+  {
+    const int64_t r0 = el0 / mp.Mxh, rs = stride / mp.Mxh;
+    ix = int(el0 - r0 * mp.Mxh);
+    sx = int(stride - rs * mp.Mxh);
+    iz = int(r0 / mp.M[1]);
+    iy = int(r0 - int64_t(iz) * mp.M[1]);
+    sz = int(rs / mp.M[1]);
+    sy = int(rs - int64_t(sz) * mp.M[1]);
+  }
+  for (int64_t el = el0; el < nel; el += stride) {
+    const int my = iy <= mp.M[1] / 2 ? iy : iy - mp.M[1];
+    const int mz = iz <= mp.M[2] / 2 ? iz : iz - mp.M[2];
+    const R kx = bm[0] * R(ix) + bm[1] * R(my) + bm[2] * R(mz);
+    const R ky = bm[3] * R(ix) + bm[4] * R(my) + bm[5] * R(mz);
+    const R kz = bm[6] * R(ix) + bm[7] * R(my) + bm[8] * R(mz);
+    const R k2 = kx * kx + ky * ky + kz * kz;
+    if (!(k2 < kc2) || k2 == R(0)) {
+#pragma unroll
+      for (int c = 0; c < kMultGroup; ++c)
+        if (c < nc) d0[c * nel + el] = Cplx<R>{R(0), R(0)};
+    } else {
+      const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
+      const R k = sqrt(k2);
+      R u = k * inv_kc;
+      if (u >= R(1)) u = R(1) - R(1e-7);
+      int seg = int(u * R(kMultSeg));
+      if (seg > kMultSeg - 1) seg = kMultSeg - 1;
+      const R sv = R(2) * (u * R(kMultSeg) - R(seg)) - R(1);
+      const R iwp = iw2x[ix] * iw2y[ay] * iw2z[az];
+      const bool edge = (ix == 0) || (even_x && ix == mp.Mxh - 1);
+      const R wm = edge ? R(0.5) : R(1);
+      for (int uu = 0; uu < nu; ++uu) {
+        const int p = pu_s[uu];
+        const R S = mult_horner(cs_s + ((p - 1) * kMultSeg + seg) * (mp.deg + 1), mp.deg, sv);
+        const R phi = mult_value(p, S, k, k2, u) * iwp;
+#pragma unroll
+        for (int c = 0; c < kMultGroup; ++c) {
+          if (c >= nc || cu_s[c] != uu) continue;   // the same for every thread of the block
+          const R G = phi * sc[c];
+          Cplx<R> v = d0[c * nel + el];
+          if (want_energy) e[c].add(wm * G * (v.x * v.x + v.y * v.y));
+          v.x *= G;
+          v.y *= G;
+          d0[c * nel + el] = v;
+        }
+      }
+    }
+    ix += sx;
+    const int carry = ix >= mp.Mxh;
+    if (carry) ix -= mp.Mxh;
+    iy += sy + carry;
+    if (iy >= mp.M[1]) {
+      iy -= mp.M[1];
+      ++iz;
+    }
+    iz += sz;
+  }
+  if (!want_energy) return;
+  // block sums per channel (8 warps of 32): warp shuffles, then one thread per channel
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kMultGroup; ++c) {
+    double t = e[c].value();
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) esum[c][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += esum[threadIdx.x][w];
+    part[size_t(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // Multiplier on the pruned spectrum of a single structure: layout
 // [c][kx][z][y] (kx = 0 .. Mxh-1 allocated; only kx < nkx can be inside the
 // band).  One (kx, z) line of y per block iteration; the same G, energy
