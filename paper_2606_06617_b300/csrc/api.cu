@@ -339,6 +339,7 @@ struct pswf_plan_s {
   int* tile_count = nullptr; // [ntiles]
   int* tile_start = nullptr; // [ntiles + 1]
   float* tscale = nullptr;   // [ntiles][K] fixed-point unit of the FP32 four-channel spread (P <= 8)
+  float* tscale_bw = nullptr;   // the same for the backward's spread (PSWF_FLAG_BACKWARD)
   int* scan_sums = nullptr;  // [scan_blocks]
   double* qpart = nullptr;   // [B][nqb][K][2]
   double* charges = nullptr; // [B K][2]: Q_net, Q_self
@@ -527,6 +528,8 @@ int64_t layout(pswf_plan p, char* base) {
   p->tile_count = reinterpret_cast<int*>(take(int64_t(p->ntiles) * 4));
   p->tile_start = reinterpret_cast<int*>(take(int64_t(p->ntiles + 1) * 4));
   p->tscale = (p->real_size == 4 && h.P <= 8) ? reinterpret_cast<float*>(take(int64_t(p->ntiles) * K * 4)) : nullptr;
+  p->tscale_bw = (p->tscale && (p->flags & PSWF_FLAG_BACKWARD)) ? reinterpret_cast<float*>(take(int64_t(p->ntiles) * K * 4))
+                                                              : nullptr;
   p->scan_sums = reinterpret_cast<int*>(take(int64_t(p->scan_blocks) * 4));
   p->qpart = reinterpret_cast<double*>(take(B * p->nqb * K * 2 * 8));
   p->charges = reinterpret_cast<double*>(take(BK * 2 * 8));
@@ -740,6 +743,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.soff = p->soff;
   c.tile_start = p->tile_start;
   c.tscale = p->tscale;
+  c.tscale_bw = p->tscale_bw;
   c.psi_il = p->psi_il;
   c.st = p->st;
   c.scell = p->scell;

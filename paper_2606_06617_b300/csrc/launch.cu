@@ -82,6 +82,7 @@ cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks
 // Threads of the FP32 four-channel stencil kernels (one CTA per SM).
 constexpr int kSpread4Threads = 1024;
 constexpr int kGather4Threads = 512;
+constexpr int kSpread4BwThreads = 1024;
 
 // FP32 kernels for P <= 8: four channels per work item, windows evaluated in
 // the lanes (stencil4.cuh).
@@ -182,9 +183,38 @@ cudaError_t interp_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch) 
   return cudaGetLastError();
 }
 
+// FP32, P <= 8: the backward spread as k_spread4_bw (four channels per item,
+// fixed point in shared memory) after its per-(tile, channel) units.
+template <int P>
+cudaError_t spread4_bw_P(const LaunchCtx& c, const BackwardArgs& b, int* nlaunch) {
+  const WinCoef<float> wc = win_coef<float>(c);
+  const int ntl = c.ntiles;
+  const int tb = int(std::min<int64_t>((int64_t(ntl) * 32 + 255) / 256, 148 * 8));
+  k_tile_scale_bw<P><<<std::max(tb, 1), 256, 0, c.stream>>>(
+      ntl, c.geo.nts, c.geo.K, c.nmax, c.soff, c.tile_start, static_cast<const float*>(c.st),
+      static_cast<const float*>(c.sq), c.sperm, c.smol, wc, static_cast<const float*>(b.g_phi),
+      static_cast<const float*>(b.g_forces), c.tscale_bw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = spread4_smem_bytes<P>();
+  const int nchunk = (c.geo.K + 3) / 4;
+  int blocks = 0;
+  e = persistent_blocks<P>(k_spread4_bw<P, kSpread4BwThreads>, smem, int64_t(ntl) * nchunk, &blocks,
+                           kSpread4BwThreads);
+  if (e != cudaSuccess) return e;
+  k_spread4_bw<P, kSpread4BwThreads><<<blocks, kSpread4BwThreads, smem, c.stream>>>(
+      c.geo, c.nmax, c.smol, c.soff, c.tile_start, static_cast<const float*>(c.st), c.scell,
+      static_cast<const float*>(c.sq), c.sperm, c.tscale_bw, wc, static_cast<const float*>(b.g_phi),
+      static_cast<const float*>(b.g_forces), static_cast<float*>(c.grid2));
+  *nlaunch += 2;
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t backward_P(const LaunchCtx& c, const BackwardArgs& b, int stage, int* nlaunch) {
   if (c.n == 0) return cudaSuccess;
+  if constexpr (sizeof(R) == 4 && P <= 8)
+    if (stage == 0 && c.tscale_bw) return spread4_bw_P<P>(c, b, nlaunch);
   const WinCoef<R> wc = win_coef(c);
   const int64_t work = std::max<int64_t>(1, c.nmax * c.geo.K);
   const int blocks = int(std::min<int64_t>((work + kDirectThreads - 1) / kDirectThreads, 148 * 64));

@@ -20,6 +20,7 @@ struct LaunchCtx {
   const int* soff = nullptr;        // [B + 1] atom offsets per structure (device)
   const int* tile_start = nullptr;
   const float* tscale = nullptr;    // [B nts][K] fixed-point units of the FP32 four-channel spread
+  float* tscale_bw = nullptr;       // [B nts][K] the same for the backward's spread (backward plans)
   bool psi_il = false;              // Psi stored as channel quadruples [K / 4][Mz][My][Mxp][4]
   const void* st = nullptr;         // real [3][nmax]
   const uint64_t* scell = nullptr;  // [nmax]

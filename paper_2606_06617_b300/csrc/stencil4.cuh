@@ -509,4 +509,230 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
   }
 }
 
+// ---- backward spread ----------------------------------------------------------
+// The backward's source for channel c, rhobar_c(r) = sum_i gphi_i^c W(r - r_i)
+// + q_i^c gF_i . grad W(r - r_i), spread like k_spread4: one atom per warp,
+// lanes = 4 channels x 8 stencil rows, 32-bit fixed point per (tile,
+// channel) with the unit 1/s of k_tile_scale_bw.  Per point the contribution
+// is wx(i) A(k) + dwx(i) B(k) with A(k) = (gphi wy + v_y dwy) wz(k) +
+// v_z wy dwz(k), B(k) = v_x wy wz(k), v = q gF (grid-coordinate components
+// in general cells), dw the window derivatives along each axis.
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 1) k_spread4_bw(Geometry g, int64_t nmax, const double* __restrict__ smol,
+                                                      const int* __restrict__ soff,
+                                                      const int* __restrict__ tile_start,
+                                                      const float* __restrict__ st, const uint64_t* __restrict__ scell,
+                                                      const float* __restrict__ sq, const int* __restrict__ sperm,
+                                                      const float* __restrict__ tscale,
+                                                      const __grid_constant__ WinCoef<float> wc,
+                                                      const float* __restrict__ gphi, const float* __restrict__ gF,
+                                                      float* __restrict__ grid2) {
+  static_assert(P <= 8, "eight lanes per channel");
+  using L = SPad<P>;
+  constexpr int S = L::S, R1 = L::R1, R2 = L::R2, N = L::N;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) int regi[];   // [4][N], layout SPad
+  __shared__ float sscale[4], inv_s[4], two_h[3];
+  __shared__ int64_t zoff_s[SPad<P>::S], yoff_s[SPad<P>::S];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane & 7, cl = lane >> 3;   // stencil row and channel of the lane
+  const int jr = j < P ? j : P - 1;
+  LanePiece<P> pc;
+  pc.load(wc, j);
+  const int64_t n = soff[g.B];
+  const int nchunk = (g.K + 3) / 4;
+  const int nitems = g.B * g.nts * nchunk;
+  const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
+  const float* st_l = st + int64_t(min(cl, 2)) * nmax;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int visit = item / nchunk, chunk = item - visit * nchunk;
+    const int tile = tile_for_visit(g, visit);
+    const int a0 = tile_start[tile], a1 = tile_start[tile + 1];
+    if (a0 == a1 || !in_bounds(a1 - 1, nmax, kBoundsTile) || !in_bounds(a0, nmax, kBoundsTile)) continue;
+    const int sidx = tile / g.nts;
+    const int c0 = chunk * 4, nk = min(4, g.K - c0);
+    const int gc0 = sidx * g.K + c0;
+    int ox, oy, oz;
+    tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
+    __syncthreads();   // the previous item's flush is done with the region
+    {
+      int4* r4 = reinterpret_cast<int4*>(regi);
+      for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
+      if (threadIdx.x < S)
+        zoff_s[threadIdx.x] = wrap_index(oz + threadIdx.x, g.M[2]) * plane;
+      else if (threadIdx.x < 2 * S)
+        yoff_s[threadIdx.x - S] = int64_t(wrap_index(oy + threadIdx.x - S, g.M[1])) * g.Mxp;
+    }
+    if (threadIdx.x < 4) {
+      const float sc = int(threadIdx.x) < nk ? tscale[int64_t(tile) * g.K + c0 + threadIdx.x] : 1.0f;
+      sscale[threadIdx.x] = sc;
+      inv_s[threadIdx.x] = 1.0f / sc;
+    } else if (threadIdx.x < 7) {
+      two_h[threadIdx.x - 4] = float(2.0 * smol[3 * sidx + threadIdx.x - 4]);
+    }
+    __syncthreads();
+    const bool active = j < P && cl < nk;
+    const float qscale = active ? sscale[cl] : 0.0f;
+    const float th_l = two_h[min(cl, 2)];   // d s / d(grid coordinate) of the lane's direction, times the window's 2
+    // one atom per warp; the next atom's inputs are loaded ahead
+    int a = a0 + warp;
+    float t_n = 0.0f, q_n = 0.0f;
+    uint64_t cell_n = 0;
+    int o_n = 0;
+    if (a < a1) {
+      t_n = st_l[a];
+      cell_n = scell[a];
+      q_n = cl < nk ? sq[int64_t(c0 + cl) * nmax + a] : 0.0f;
+      o_n = sperm[a];
+    }
+    for (; a < a1; a += NW) {
+      const float t = t_n, qv = q_n;
+      const uint64_t cell = cell_n;
+      const int o = o_n;
+      if (a + NW < a1) {
+        t_n = st_l[a + NW];
+        cell_n = scell[a + NW];
+        q_n = cl < nk ? sq[int64_t(c0 + cl) * nmax + a + NW] : 0.0f;
+        o_n = sperm[a + NW];
+      }
+      const float gp = (gphi && cl < nk && in_bounds(int64_t(c0 + cl) * n + o, int64_t(g.K) * n, kBoundsSpreadRegion))
+                           ? gphi[int64_t(c0 + cl) * n + o] : 0.0f;
+      float gf0 = 0.0f, gf1 = 0.0f, gf2 = 0.0f;
+      if (gF && in_bounds(3 * int64_t(o) + 2, 3 * n, kBoundsSpreadRegion)) {
+        gf0 = gF[3 * int64_t(o)];
+        gf1 = gF[3 * int64_t(o) + 1];
+        gf2 = gF[3 * int64_t(o) + 2];
+      }
+      float w, dw;
+      pc.value_deriv(t, w, dw);   // piece j of direction cl
+      dw *= th_l;
+      float wx[P], dx[P], wz[P], dz[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        wx[i] = __shfl_sync(0xffffffffu, w, i);
+        dx[i] = __shfl_sync(0xffffffffu, dw, i);
+        wz[i] = __shfl_sync(0xffffffffu, w, 16 + i);
+        dz[i] = __shfl_sync(0xffffffffu, dw, 16 + i);
+      }
+      const float wy = __shfl_sync(0xffffffffu, w, 8 + jr);
+      const float dy = __shfl_sync(0xffffffffu, dw, 8 + jr);
+      int cx, cy, cz;
+      unpack_cell(cell, cx, cy, cz);
+      const int rb = cl * N + (cz - oz) * R2 + ((cy - oy) + j) * R1 + (cx - ox);
+      if (active && in_bounds(rb, 4 * N, kBoundsSpreadRegion) &&
+          in_bounds(rb + (P - 1) * R2 + (P - 1), 4 * N, kBoundsSpreadRegion)) {
+        int* row = regi + rb;
+        const float vq = qv * qscale;
+        const float al = gp * qscale * wy + vq * gf1 * dy;   // A(k) = al wz(k) + be dz(k)
+        const float be = vq * gf2 * wy;
+        const float ga = vq * gf0 * wy;                      // B(k) = ga wz(k)
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const float A = fmaf(al, wz[k], be * dz[k]);
+          const float B = ga * wz[k];
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const float f = fmaf(dx[i], B, fmaf(wx[i], A, 12582912.0f));
+            atomicAdd(row + k * R2 + i, __float_as_int(f) - 0x4B400000);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    {
+      const int half = lane >> 4, x0 = 2 * (lane & 15);
+      const bool has0 = x0 < S, has1 = x0 + 1 < S;
+      const int gx0 = has0 ? wrap_index(ox + x0, g.M[0]) : 0;
+      const int gx1 = has1 ? wrap_index(ox + x0 + 1, g.M[0]) : 0;
+      const bool pair = has1 && gx1 == gx0 + 1 && (gx0 & 1) == 0;
+      for (int pl = warp; pl < nk * S; pl += NW) {
+        const int c = pl / S, lz = pl - c * S;
+        const float inv = inv_s[c];
+        float* base = grid2 + (gc0 + c) * chan + zoff_s[lz];
+        const int* src = regi + c * N + lz * R2;
+        if (!has0) continue;
+        for (int ly = half; ly < S; ly += 2) {
+          float* rowg = base + yoff_s[ly];
+          if (!in_bounds(int64_t(c * N + lz * R2 + ly * R1 + x0 + (has1 ? 1 : 0)), 4 * N, kBoundsSpreadFlush) ||
+              !in_bounds((rowg - grid2) + max(gx0, gx1), int64_t(g.B) * g.K * chan, kBoundsSpreadFlush))
+            continue;
+          const int v0 = src[ly * R1 + x0];
+          const int v1 = has1 ? src[ly * R1 + x0 + 1] : 0;
+          if (pair) {
+            atomicAdd(reinterpret_cast<float2*>(rowg + gx0), make_float2(float(v0) * inv, float(v1) * inv));
+          } else {
+            atomicAdd(rowg + gx0, float(v0) * inv);
+            if (has1) atomicAdd(rowg + gx1, float(v1) * inv);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Fixed-point units of k_spread4_bw per (tile, channel).  An atom's
+// contribution at any point is at most M_i = |gphi_i^c| mw_x mw_y mw_z +
+// |q_i^c| (|gF_x| md_x mw_y mw_z + |gF_y| mw_x md_y mw_z + |gF_z| mw_x mw_y md_z)
+// with mw_d, md_d the largest |W| and |dW/dx_d| over the atom's P window
+// pieces at its own offsets (evaluated as the spread evaluates them); s keeps
+// every contribution below 2^22 and every sum below 2^31 (as k_tile_scale).
+// One warp per tile.
+template <int P>
+__global__ void k_tile_scale_bw(int ntl, int nts, int K, int64_t nmax, const int* __restrict__ soff,
+                                const int* __restrict__ tile_start, const float* __restrict__ st,
+                                const float* __restrict__ sq, const int* __restrict__ sperm,
+                                const double* __restrict__ smol, const __grid_constant__ WinCoef<float> wc,
+                                const float* __restrict__ gphi, const float* __restrict__ gF,
+                                float* __restrict__ tscale) {
+  constexpr int D = WinCoef<float>::kDeg;
+  const int lane = threadIdx.x & 31;
+  const int nw = int((int64_t(gridDim.x) * blockDim.x) >> 5);
+  const int64_t n = soff[ntl / nts];   // atoms of all structures (rows of gphi)
+  for (int t = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); t < ntl; t += nw) {
+    const int a0 = tile_start[t], a1 = tile_start[t + 1];
+    const int sidx = t / nts;
+    for (int c = 0; c < K; ++c) {
+      float s1 = 0.0f, mq = 0.0f;
+      for (int a = a0 + lane; a < a1; a += 32) {
+        float mw[3], md[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float sv = 2.0f * st[int64_t(d) * nmax + a] - 1.0f;
+          float vmax = 0.0f, dmax = 0.0f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            float v = wc.c[j * (D + 1) + D], dv = 0.0f;
+#pragma unroll
+            for (int m = D - 1; m >= 0; --m) {
+              dv = fmaf(dv, sv, v);
+              v = fmaf(v, sv, wc.c[j * (D + 1) + m]);
+            }
+            vmax = fmaxf(vmax, fabsf(v));
+            dmax = fmaxf(dmax, fabsf(dv));
+          }
+          mw[d] = vmax;
+          md[d] = dmax * float(2.0 * smol[3 * sidx + d]);
+        }
+        const int o = sperm[a];
+        float m = 0.0f;
+        if (gF)
+          m = fabsf(sq[int64_t(c) * nmax + a]) *
+              (fabsf(gF[3 * int64_t(o)]) * md[0] * mw[1] * mw[2] + fabsf(gF[3 * int64_t(o) + 1]) * mw[0] * md[1] * mw[2] +
+               fabsf(gF[3 * int64_t(o) + 2]) * mw[0] * mw[1] * md[2]);
+        if (gphi) m += fabsf(gphi[int64_t(c) * n + o]) * mw[0] * mw[1] * mw[2];
+        m *= 1.0001f;   // the spread's two roundings per contribution and FP32 products here
+        s1 += m;
+        mq = fmaxf(mq, m);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+      }
+      if (lane == 0)
+        tscale[int64_t(t) * K + c] =
+            s1 > 0.0f ? fminf(0.99f * 4194304.0f / mq, 0.999f * 2147483647.0f / (s1 * 1.0001f)) : 1.0f;
+    }
+  }
+}
+
 }  // namespace pswf
