@@ -438,6 +438,27 @@ int pswf_server_wait_for(pswf_server srv, int64_t ticket, double timeout_ms, dou
  * server before a reconfiguration, or holding requests back. */
 int pswf_server_pause(pswf_server srv, int pause);
 
+/* Submits count structures in one call (as count pswf_server_submit calls,
+ * in order): n host int64 [count] atoms per structure, boxes host double
+ * [count][3], ps host int [count][K], pos host array [count] of pointers to
+ * each structure's positions (double [n_i][3]), q host array [count] of
+ * pointers to its charges (double [K][n_i]); tickets host int64 [count]
+ * receives the tickets.  Copies the inputs before returning.  On an error
+ * the structures before the failing one stay submitted (their tickets are
+ * written).  For clients that hand over many structures at once. */
+int pswf_server_submit_many(pswf_server srv, int64_t count, const int64_t* n, const double* boxes, const int* ps,
+                            const double* const* pos, const double* const* q, int64_t* tickets);
+
+/* Waits for count tickets (as pswf_server_wait, in order) and writes each
+ * structure's results: energies host double [count][K + 1], phi host double
+ * with structure i's [K][n_i] at phi + K offsets[i] (may be NULL), forces
+ * host double [offsets[count]][3] (may be NULL), latency_ms host double
+ * [count] (may be NULL); offsets host int64 [count + 1], the running sums of
+ * the structures' atom counts.  Every ticket is waited for and released;
+ * returns the first error. */
+int pswf_server_wait_many(pswf_server srv, int64_t count, const int64_t* tickets, const int64_t* offsets,
+                          double* energies, double* phi, double* forces, double* latency_ms);
+
 /* Counters since creation (any may be NULL); returns the server's failure
  * status (0 if healthy). */
 int pswf_server_stats(pswf_server srv, int64_t* batches, int64_t* requests, int64_t* atoms);

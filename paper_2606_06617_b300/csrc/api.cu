@@ -107,39 +107,41 @@ __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __res
 __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part, const double* __restrict__ zero_coef,
                                const double* __restrict__ charges, double* __restrict__ energy,
                                const double* __restrict__ vpart, double* __restrict__ virial) {
-  __shared__ double sh[7][32];
-  __shared__ double tot;
+  // one block per structure, one warp per channel (channels strided over the warps)
+  __shared__ double tw[32];
   const int s = blockIdx.x;
-  if (threadIdx.x == 0) tot = 0.0;
-  for (int c = 0; c < K; ++c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+  double tot = 0.0;   // this warp's channels (lane 0)
+  for (int c = warp; c < K; c += nw) {
     const int g = s * K + c;
-    double t7[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-      t7[0] += part[size_t(g) * nblk + i];
+    double t = 0.0, v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = lane; i < nblk; i += 32) {
+      t += part[size_t(g) * nblk + i];
       if (vpart)
-        for (int d = 0; d < 6; ++d) t7[1 + d] += vpart[(size_t(g) * nblk + i) * 6 + d];
+        for (int d = 0; d < 6; ++d) v[d] += vpart[(size_t(g) * nblk + i) * 6 + d];
     }
-    for (int q = 0; q < 7; ++q)
-      for (int o = 16; o > 0; o >>= 1) t7[q] += __shfl_down_sync(0xffffffffu, t7[q], o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0)
-      for (int q = 0; q < 7; ++q) sh[q][threadIdx.x >> 5] = t7[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int w = 0; w < int(blockDim.x >> 5); ++w)
-        for (int q = 0; q < 7; ++q) t[q] += sh[q][w];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (vpart)
+      for (int d = 0; d < 6; ++d)
+        for (int o = 16; o > 0; o >>= 1) v[d] += __shfl_down_sync(0xffffffffu, v[d], o);
+    if (lane == 0) {
       const double Q = charges[2 * g];
-      const double ec = t[0] + zero_coef[g] * Q * Q;
+      const double ec = t + zero_coef[g] * Q * Q;
       energy[size_t(s) * (K + 1) + c] = ec;
       tot += ec;
       // W_ab = -dE/d epsilon_ab: E delta_ab (the 1/V prefactor and E^0 ~ 1/V)
       // plus the log-derivative sums of the multiplier
       if (vpart && virial)
-        for (int d = 0; d < 6; ++d) virial[size_t(g) * 6 + d] = (d < 3 ? ec : 0.0) + t[1 + d];
+        for (int d = 0; d < 6; ++d) virial[size_t(g) * 6 + d] = (d < 3 ? ec : 0.0) + v[d];
     }
   }
-  if (threadIdx.x == 0) energy[size_t(s) * (K + 1) + K] = tot;
+  if (lane == 0) tw[warp] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += tw[w];
+    energy[size_t(s) * (K + 1) + K] = t;
+  }
 }
 
 __global__ void k_set_count(int* __restrict__ soff, int n) {
@@ -914,10 +916,17 @@ int fft_exec(pswf_plan p, void* data, bool forward) {
   return PSWF_OK;
 }
 
-// Q_net and Q_self per (structure, channel) of values [K][n] in caller order.
+// Q_net and Q_self per (structure, channel) of values [K][n] in caller order:
+// batch plans one warp per (structure, channel) (1 launch), single plans
+// block partials and a final pass (2 launches).
 template <typename R>
 int charge_sums(pswf_plan p, const void* vals, double* out) {
   const int K = p->host.K;
+  if (p->batch) {
+    k_charge_sums_warp<R><<<(p->nrun * K + 7) / 8, 256, 0, p->stream>>>(static_cast<const R*>(vals), K, p->nrun,
+                                                                         p->soff, out);
+    return launch_check(p, "k_charge_sums_warp");
+  }
   k_charge_partials_seg<R><<<dim3(p->nqb, p->nrun), kThreads, 0, p->stream>>>(static_cast<const R*>(vals), K, p->nrun,
                                                                           p->soff, p->qpart);
   int rc = launch_check(p, "k_charge_partials_seg");
@@ -938,7 +947,7 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   p->psi_valid = false;
   p->virial_valid = false;
   StageScope scope(p, PSWF_STAGE_SET_POINTS);
-  p->launches[PSWF_STAGE_SET_POINTS] += p->batch ? 7 : 8;
+  p->launches[PSWF_STAGE_SET_POINTS] += p->batch ? 6 : 8;
   if (!p->batch) {
     k_set_count<<<1, 32, 0, s>>>(p->soff, int(n));
     if ((rc = launch_check(p, "k_set_count"))) return rc;
@@ -1070,7 +1079,7 @@ int do_backward(pswf_plan p, const double* g_energy, const void* g_phi, const vo
   const BackwardArgs b{g_energy, g_phi, g_forces, grad_q, grad_pos};
   if (g_phi) {
     if ((rc = charge_sums<R>(p, g_phi, p->bsum))) return rc;
-    nl += 2;
+    nl += p->batch ? 1 : 2;
   } else if ((rc = cuda_check(p, cudaMemsetAsync(p->bsum, 0, size_t(p->nrun) * K * 2 * sizeof(double), s),
                               "clear bsum"))) {
     return rc;
@@ -1132,6 +1141,11 @@ int plan_fill_tables(pswf_plan p, int b, const double* boxes, const int* ps, con
 }
 
 int plan_run_size(pswf_plan p) { return p->nrun; }
+
+const int* plan_run_sizes(pswf_plan p, int* count) {
+  *count = int(p->fft_sizes.size());
+  return p->fft_sizes.data();
+}
 
 int plan_upload_tables(pswf_plan p) {
   return cuda_check(p, cudaMemcpyAsync(p->stab, p->h_stab, size_t(p->stab_bytes), cudaMemcpyHostToDevice, p->stream),

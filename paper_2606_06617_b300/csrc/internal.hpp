@@ -16,6 +16,8 @@ int plan_fill_tables(pswf_plan p, int b, const double* boxes, const int* ps, con
 // Slots the next launch processes (a planned size >= b, set by
 // plan_fill_tables); captured sequences are per size.
 int plan_run_size(pswf_plan p);
+// Every size plan_run_size can return, ascending.
+const int* plan_run_sizes(pswf_plan p, int* count);
 // Copies the mirror to the device on the plan's stream (plain async copy).
 int plan_upload_tables(pswf_plan p);
 // The kernels of set_points / execute on the plan's stream; for a batch plan

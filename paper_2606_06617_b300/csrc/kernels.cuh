@@ -373,6 +373,30 @@ __global__ void k_charge_partials_seg(const R* __restrict__ q, int K, int B, con
   }
 }
 
+// Q_net and Q_self of one (structure, channel) per warp, g = s K + c:
+// charges[2 g] = sum q, charges[2 g + 1] = sum q^2 over the structure's atoms
+// (caller order, q [K][n]).  For batch plans, whose structures are small.
+template <typename R>
+__global__ void k_charge_sums_warp(const R* __restrict__ q, int K, int B, const int* __restrict__ soff,
+                                   double* __restrict__ charges) {
+  const int g = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= B * K) return;
+  const int s = g / K, c = g - s * K;
+  const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
+  ChargeAcc<R> acc;
+  for (int64_t i = a0 + lane; i < a1; i += 32) acc.add(q[c * n + i]);
+  double s1 = acc.sum(), s2 = acc.sumsq();
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    charges[2 * g] = s1;
+    charges[2 * g + 1] = s2;
+  }
+}
+
 // Per-block partial sums of q and q^2 per channel: part[(blk * K + c) * 2 + {0,1}].
 template <typename R>
 __global__ void k_charge_partials(int64_t n, const R* __restrict__ q, int K, double* __restrict__ part) {

@@ -40,20 +40,27 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// A structure in flight.  Charges and results are held in the server's
+// precision (rs bytes a value): the submitting thread converts the charges,
+// the waiting thread converts the results it asks for, so the scheduler
+// thread only copies.  Finished requests return to a pool and keep their
+// buffers' capacity, so a stream of requests does not allocate.
 struct Request {
   int64_t id = 0;
   int64_t n = 0;
   double box[3] = {0, 0, 0};
   std::vector<int> ps;          // [K]
   std::vector<double> pos;      // [n][3]
-  std::vector<double> q;        // [K][n]
+  std::vector<char> q;          // real [K][n]
   int bucket = 0;
   int status = 1;               // 1 pending, 0 done, < 0 failed
   Clock::time_point t_submit, t_done;
   std::vector<double> energy;   // [K + 1]
-  std::vector<double> phi;      // [K][n]
-  std::vector<double> forces;   // [n][3]
+  std::vector<char> phi;        // real [K][n]
+  std::vector<char> forces;     // real [n][3]
 };
+
+constexpr size_t kRequestPool = 8192;   // finished requests kept for reuse
 
 struct Context {
   pswf_plan plan = nullptr;
@@ -95,6 +102,8 @@ struct pswf_server_s {
   int device = 0;
   std::vector<std::unique_ptr<Bucket>> buckets;
   std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+  std::vector<std::unique_ptr<Request>> pool;   // finished requests (pool_mu)
+  std::mutex pool_mu;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::thread th;
@@ -175,6 +184,59 @@ void free_context(Context& c) {
   if (c.stream) cudaStreamDestroy(c.stream);
 }
 
+// The context's graph of set_points + execute for the plan's current run
+// size (captured on first use).
+int graph_for_run(pswf_server srv, Bucket& b, Context& c, cudaGraphExec_t* out) {
+  const int nrun = pswf::plan_run_size(c.plan);
+  for (auto& g : c.graphs)
+    if (g.first == nrun) {
+      *out = g.second;
+      return PSWF_OK;
+    }
+  int rc;
+  cudaGraph_t g = nullptr;
+  if ((rc = cuda_ok(srv, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed), "begin capture"))) return rc;
+  int rc1 = pswf::plan_run_set_points(c.plan, b.n_max, c.d_pos, 1, c.d_q);
+  int rc2 = rc1 ? rc1 : pswf::plan_run_execute(c.plan, c.d_e, c.d_phi, c.d_f);
+  const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
+  if (rc2) {
+    if (g) cudaGraphDestroy(g);
+    srv->error = pswf::plan_error(c.plan);
+    return rc2;
+  }
+  if ((rc = cuda_ok(srv, ec, "end capture"))) return rc;
+  cudaGraphExec_t gexec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
+  cudaGraphDestroy(g);
+  if ((rc = cuda_ok(srv, ei, "graph instantiate"))) return rc;
+  c.graphs.emplace_back(nrun, gexec);
+  *out = gexec;
+  return PSWF_OK;
+}
+
+// Captures the context's graphs for every run size ahead of serving, so no
+// capture (milliseconds each) delays a request: tables of `size` empty
+// structures set the run size; nothing is launched.
+int precapture(pswf_server srv, Bucket& b, Context& c) {
+  int count = 0;
+  const int* sizes = pswf::plan_run_sizes(c.plan, &count);
+  const std::vector<int> runs(sizes, sizes + count);
+  const int K = srv->K;
+  for (int sz : runs) {
+    std::vector<double> boxes(size_t(sz) * 3, 0.5 * b.box_max[0]);
+    std::vector<int> ps(size_t(sz) * K, srv->opt.pset[0]);
+    std::vector<int64_t> offsets(size_t(sz) + 1, 0);
+    int rc;
+    if ((rc = pswf::plan_fill_tables(c.plan, sz, boxes.data(), ps.data(), offsets.data()))) {
+      srv->error = pswf::plan_error(c.plan);
+      return rc;
+    }
+    cudaGraphExec_t gexec = nullptr;
+    if ((rc = graph_for_run(srv, b, c, &gexec))) return rc;
+  }
+  return PSWF_OK;
+}
+
 // Stages the batch in c.reqs and enqueues it on the context's stream.
 int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   const int K = srv->K;
@@ -192,17 +254,11 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   const int64_t n = c.offsets[nb];
   for (int i = 0; i < nb; ++i) {
     const Request* r = c.reqs[i];
-    if (r->n) std::memcpy(c.h_pos + 3 * c.offsets[i], r->pos.data(), size_t(r->n) * 24);
-    for (int k = 0; k < K; ++k) {
-      const double* src = r->q.data() + size_t(k) * r->n;
-      if (rs == 4) {
-        float* dst = static_cast<float*>(c.h_q) + size_t(k) * n + c.offsets[i];
-        for (int64_t a = 0; a < r->n; ++a) dst[a] = float(src[a]);
-      } else {
-        double* dst = static_cast<double*>(c.h_q) + size_t(k) * n + c.offsets[i];
-        std::memcpy(dst, src, size_t(r->n) * 8);
-      }
-    }
+    if (!r->n) continue;
+    std::memcpy(c.h_pos + 3 * c.offsets[i], r->pos.data(), size_t(r->n) * 24);
+    for (int k = 0; k < K; ++k)
+      std::memcpy(static_cast<char*>(c.h_q) + (size_t(k) * n + c.offsets[i]) * rs, r->q.data() + size_t(k) * r->n * rs,
+                  size_t(r->n) * rs);
   }
   int rc;
   if ((rc = pswf::plan_fill_tables(c.plan, nb, boxes.data(), ps.data(), c.offsets.data()))) {
@@ -215,28 +271,8 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   if ((rc = cuda_ok(srv, cudaMemcpyAsync(c.d_q, c.h_q, size_t(n) * K * rs, cudaMemcpyHostToDevice, c.stream), "h2d")))
     return rc;
   if (srv->opt.use_graphs) {
-    const int nrun = pswf::plan_run_size(c.plan);
     cudaGraphExec_t gexec = nullptr;
-    for (auto& g : c.graphs)
-      if (g.first == nrun) gexec = g.second;
-    if (!gexec) {
-      cudaGraph_t g = nullptr;
-      if ((rc = cuda_ok(srv, cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed), "begin capture")))
-        return rc;
-      int rc1 = pswf::plan_run_set_points(c.plan, b.n_max, c.d_pos, 1, c.d_q);
-      int rc2 = rc1 ? rc1 : pswf::plan_run_execute(c.plan, c.d_e, c.d_phi, c.d_f);
-      const cudaError_t ec = cudaStreamEndCapture(c.stream, &g);
-      if (rc2) {
-        if (g) cudaGraphDestroy(g);
-        srv->error = pswf::plan_error(c.plan);
-        return rc2;
-      }
-      if ((rc = cuda_ok(srv, ec, "end capture"))) return rc;
-      const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
-      cudaGraphDestroy(g);
-      if ((rc = cuda_ok(srv, ei, "graph instantiate"))) return rc;
-      c.graphs.emplace_back(nrun, gexec);
-    }
+    if ((rc = graph_for_run(srv, b, c, &gexec))) return rc;
     if ((rc = cuda_ok(srv, cudaGraphLaunch(gexec, c.stream), "graph launch"))) return rc;
   } else {
     if ((rc = pswf::plan_run_set_points(c.plan, n, c.d_pos, 1, c.d_q))) return rc;
@@ -253,7 +289,8 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   return cuda_ok(srv, cudaLaunchHostFunc(c.stream, on_batch_done, &c), "host callback");
 }
 
-// Copies a finished batch's results into its requests (outside the lock).
+// Copies a finished batch's results into its requests (outside the lock),
+// in the server's precision.
 void collect_batch(pswf_server srv, Context& c) {
   const int K = srv->K;
   const size_t rs = srv->rs;
@@ -262,18 +299,24 @@ void collect_batch(pswf_server srv, Context& c) {
   for (int i = 0; i < nb; ++i) {
     Request* r = c.reqs[i];
     r->energy.assign(c.h_e + size_t(i) * (K + 1), c.h_e + size_t(i + 1) * (K + 1));
-    r->phi.resize(size_t(K) * r->n);
-    r->forces.resize(size_t(r->n) * 3);
+    r->phi.resize(size_t(K) * r->n * rs);
+    r->forces.resize(size_t(r->n) * 3 * rs);
+    if (!r->n) continue;
     for (int k = 0; k < K; ++k)
-      for (int64_t a = 0; a < r->n; ++a) {
-        const size_t src = size_t(k) * n + c.offsets[i] + a;
-        r->phi[size_t(k) * r->n + a] =
-            rs == 4 ? double(static_cast<const float*>(c.h_phi)[src]) : static_cast<const double*>(c.h_phi)[src];
-      }
-    for (int64_t a = 0; a < 3 * r->n; ++a) {
-      const size_t src = size_t(3 * c.offsets[i] + a);
-      r->forces[a] = rs == 4 ? double(static_cast<const float*>(c.h_f)[src]) : static_cast<const double*>(c.h_f)[src];
-    }
+      std::memcpy(r->phi.data() + size_t(k) * r->n * rs,
+                  static_cast<const char*>(c.h_phi) + (size_t(k) * n + c.offsets[i]) * rs, size_t(r->n) * rs);
+    std::memcpy(r->forces.data(), static_cast<const char*>(c.h_f) + size_t(3 * c.offsets[i]) * rs,
+                size_t(r->n) * 3 * rs);
+  }
+}
+
+// Values of the server's precision to double.
+void widen(const char* src, size_t rs, size_t count, double* dst) {
+  if (rs == 8) {
+    std::memcpy(dst, src, count * 8);
+  } else {
+    const float* f = reinterpret_cast<const float*>(src);
+    for (size_t i = 0; i < count; ++i) dst[i] = double(f[i]);
   }
 }
 
@@ -405,6 +448,7 @@ int pswf_server_create(const pswf_server_opts* opts, pswf_server* out) {
     for (int j = 0; j < o.inflight && !rc; ++j) {
       b.ctx.push_back(std::make_unique<Context>());
       rc = make_context(srv, b, *b.ctx.back());
+      if (!rc && o.use_graphs) rc = precapture(srv, b, *b.ctx.back());
     }
   }
   if (rc) {
@@ -428,35 +472,7 @@ int pswf_server_route(pswf_server srv, int64_t n, const double box[3], pswf_info
 
 int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const int* ps, const double* pos,
                        const double* q, int64_t* ticket) {
-  if (!srv || !box || !ps || !ticket || n < 0 || (n > 0 && (!pos || !q))) return PSWF_EINVAL;
-  for (int d = 0; d < 3; ++d)
-    if (!(box[d] > 0.0)) return PSWF_EINVAL;
-  const int K = srv->K;
-  for (int k = 0; k < K; ++k) {
-    bool ok = false;
-    for (int i = 0; i < srv->opt.npset; ++i) ok = ok || srv->opt.pset[i] == ps[k];
-    if (!ok) return PSWF_EINVAL;
-  }
-  const int bi = route(srv, n, box);
-  if (bi < 0) return PSWF_EINVAL;
-  auto r = std::make_unique<Request>();
-  r->n = n;
-  for (int d = 0; d < 3; ++d) r->box[d] = box[d];
-  r->ps.assign(ps, ps + K);
-  r->pos.assign(pos, pos + 3 * n);
-  r->q.assign(q, q + size_t(K) * n);
-  r->bucket = bi;
-  r->t_submit = Clock::now();
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    if (srv->fatal) return srv->fatal;
-    r->id = srv->next_id++;
-    *ticket = r->id;
-    srv->buckets[bi]->pending.push_back(r.get());
-    srv->reqs.emplace(r->id, std::move(r));
-  }
-  srv->cv_sched.notify_one();
-  return PSWF_OK;
+  return pswf_server_submit_many(srv, 1, &n, box, ps, &pos, &q, ticket);
 }
 
 int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
@@ -489,12 +505,112 @@ int pswf_server_wait_for(pswf_server srv, int64_t ticket, double timeout_ms, dou
     srv->reqs.erase(it);
   }
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
-  if (r->status) return r->status;
+  const int status = r->status;
+  if (!status) {
+    const int K = srv->K;
+    if (energy) std::memcpy(energy, r->energy.data(), size_t(K + 1) * 8);
+    if (phi && r->n) widen(r->phi.data(), srv->rs, size_t(K) * r->n, phi);
+    if (forces && r->n) widen(r->forces.data(), srv->rs, size_t(r->n) * 3, forces);
+  }
+  {
+    std::lock_guard<std::mutex> lk(srv->pool_mu);
+    if (srv->pool.size() < kRequestPool) srv->pool.push_back(std::move(r));
+  }
+  return status;
+}
+
+int pswf_server_submit_many(pswf_server srv, int64_t count, const int64_t* n, const double* boxes, const int* ps,
+                            const double* const* pos, const double* const* q, int64_t* tickets) {
+  if (!srv || count < 0 || (count > 0 && (!n || !boxes || !ps || !pos || !q || !tickets))) return PSWF_EINVAL;
   const int K = srv->K;
-  if (energy) std::memcpy(energy, r->energy.data(), size_t(K + 1) * 8);
-  if (phi && r->n) std::memcpy(phi, r->phi.data(), size_t(K) * r->n * 8);
-  if (forces && r->n) std::memcpy(forces, r->forces.data(), size_t(r->n) * 24);
-  return PSWF_OK;
+  // routes first: the structures before the first invalid one are submitted
+  std::vector<int> bucket(static_cast<size_t>(count));
+  int64_t nok = 0;
+  int status = PSWF_OK;
+  for (; nok < count; ++nok) {
+    const int64_t i = nok, ni = n[i];
+    const double* box = boxes + 3 * i;
+    bool ok = ni >= 0 && (ni == 0 || (pos[i] && q[i]));
+    for (int d = 0; d < 3 && ok; ++d) ok = box[d] > 0.0;
+    for (int k = 0; k < K && ok; ++k) {
+      bool in = false;
+      for (int j = 0; j < srv->opt.npset; ++j) in = in || srv->opt.pset[j] == ps[size_t(K) * i + k];
+      ok = in;
+    }
+    const int bi = ok ? route(srv, ni, box) : -1;
+    if (bi < 0) {
+      status = PSWF_EINVAL;
+      break;
+    }
+    bucket[size_t(i)] = bi;
+  }
+  // requests from the pool, filled (copies, charges to the server's
+  // precision) and queued in chunks of about kSubmitChunk atoms, so the
+  // scheduler starts on the first chunk while the next is filled
+  constexpr int64_t kSubmitChunk = 32768;
+  const size_t rs = srv->rs;
+  int64_t i0 = 0;
+  while (i0 < nok) {
+    int64_t i1 = i0, chunk_atoms = 0;
+    while (i1 < nok && (i1 == i0 || chunk_atoms + n[i1] <= kSubmitChunk)) chunk_atoms += n[i1++];
+    std::vector<std::unique_ptr<Request>> rq(static_cast<size_t>(i1 - i0));
+    {
+      std::lock_guard<std::mutex> lk(srv->pool_mu);
+      for (size_t j = 0; j < rq.size() && !srv->pool.empty(); ++j) {
+        rq[j] = std::move(srv->pool.back());
+        srv->pool.pop_back();
+      }
+    }
+    for (int64_t i = i0; i < i1; ++i) {
+      auto& r = rq[size_t(i - i0)];
+      if (!r) r = std::make_unique<Request>();
+      const int64_t ni = n[i];
+      r->n = ni;
+      r->status = 1;
+      for (int d = 0; d < 3; ++d) r->box[d] = boxes[3 * i + d];
+      r->ps.assign(ps + size_t(K) * i, ps + size_t(K) * (i + 1));
+      r->bucket = bucket[size_t(i)];
+      r->pos.assign(pos[i], pos[i] + 3 * ni);
+      r->q.resize(size_t(K) * ni * rs);
+      if (rs == 4) {
+        float* dst = reinterpret_cast<float*>(r->q.data());
+        for (size_t j = 0; j < size_t(K) * ni; ++j) dst[j] = float(q[i][j]);
+      } else if (ni) {
+        std::memcpy(r->q.data(), q[i], size_t(K) * ni * 8);
+      }
+    }
+    const auto now = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      if (srv->fatal) return srv->fatal;
+      for (int64_t i = i0; i < i1; ++i) {
+        auto& r = rq[size_t(i - i0)];
+        r->t_submit = now;
+        r->id = srv->next_id++;
+        tickets[i] = r->id;
+        srv->buckets[size_t(r->bucket)]->pending.push_back(r.get());
+        srv->reqs.emplace(r->id, std::move(r));
+      }
+    }
+    srv->cv_sched.notify_one();
+    i0 = i1;
+  }
+  return status;
+}
+
+int pswf_server_wait_many(pswf_server srv, int64_t count, const int64_t* tickets, const int64_t* offsets,
+                          double* energies, double* phi, double* forces, double* latency_ms) {
+  if (!srv || count < 0 || (count > 0 && (!tickets || !offsets))) return PSWF_EINVAL;
+  const int K = srv->K;
+  int first = PSWF_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t a = offsets[i];
+    const int rc = pswf_server_wait(srv, tickets[i], energies ? energies + size_t(K + 1) * i : nullptr,
+                                    phi ? phi + size_t(K) * a : nullptr, forces ? forces + 3 * a : nullptr,
+                                    latency_ms ? latency_ms + i : nullptr);
+    if (rc && first == PSWF_OK) first = rc;   // every ticket is still waited for and released
+  }
+  return first;
 }
 
 int pswf_server_stats(pswf_server srv, int64_t* batches, int64_t* requests, int64_t* atoms) {

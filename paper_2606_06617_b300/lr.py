@@ -114,6 +114,10 @@ SIGNATURES = {
     "pswf_server_wait": ([_vp, _i64, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_server_wait_for": ([_vp, _i64, ctypes.c_double, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_server_pause": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pswf_server_submit_many": ([_vp, _i64, ctypes.POINTER(ctypes.c_int64), _dp, _ip, ctypes.POINTER(_dp),
+                                 ctypes.POINTER(_dp), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "pswf_server_wait_many": ([_vp, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _dp, _dp,
+                               _dp, _dp], ctypes.c_int),
     "pswf_server_stats": ([_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "pswf_server_last_error": ([_vp, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
@@ -599,6 +603,53 @@ class Server:
             del self._n[ticket]   # released by the server (done or failed)
         self._check(st)
         return e, ph, f, lat.value
+
+    def submit_many(self, structures):
+        """Submits [(pos [n, 3], q [K, n], box, ps), ...] in one call
+        (pswf_server_submit_many; each structure's arrays are passed by
+        address, float64 C-contiguous ones without a copy); returns
+        (tickets, offsets) int64 arrays, offsets the running atom counts."""
+        count = len(structures)
+        pos_l = [np.ascontiguousarray(st[0], dtype=np.float64) for st in structures]
+        q_l = [np.ascontiguousarray(st[1], dtype=np.float64) for st in structures]
+        ns = np.fromiter((a.shape[0] for a in pos_l), dtype=np.int64, count=count)
+        if any(qq.shape != (self.K, int(n)) for qq, n in zip(q_l, ns)):
+            raise ValueError("q must be [K, n]")
+        boxes = np.ascontiguousarray(np.array([st[2] for st in structures], dtype=np.float64).reshape(count, 3))
+        ps = np.ascontiguousarray(np.array([st[3] for st in structures], dtype=np.int32).reshape(count, self.K))
+        pos_a = np.fromiter((a.ctypes.data for a in pos_l), dtype=np.uintp, count=count)
+        q_a = np.fromiter((a.ctypes.data for a in q_l), dtype=np.uintp, count=count)
+        off = np.zeros(count + 1, dtype=np.int64)
+        off[1:] = np.cumsum(ns)
+        tk = np.zeros(count, dtype=np.int64)
+        i64p, dpp = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_dp)
+        self._check(lib().pswf_server_submit_many(self._h, count, ns.ctypes.data_as(i64p), boxes.ctypes.data_as(_dp),
+                                                  ps.ctypes.data_as(_ip), pos_a.ctypes.data_as(dpp),
+                                                  q_a.ctypes.data_as(dpp), tk.ctypes.data_as(i64p)))
+        self._n = getattr(self, "_n", {})
+        self._n.update(zip(tk.tolist(), ns.tolist()))
+        return tk, off
+
+    def wait_many(self, tickets, offsets, phi: bool = False, forces: bool = True):
+        """Waits for submit_many's tickets (pswf_server_wait_many): returns
+        (energies [count, K+1], phi [K * n_total] (structure i's [K, n_i] at
+        K * offsets[i]) or None, forces [n_total, 3] or None, latencies ms
+        [count])."""
+        tickets = np.ascontiguousarray(tickets, dtype=np.int64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        count, ntot = len(tickets), int(offsets[-1]) if len(offsets) else 0
+        e = np.empty((count, self.K + 1))
+        ph = np.empty(self.K * ntot) if phi else None
+        f = np.empty((ntot, 3)) if forces else None
+        lat = np.empty(count)
+        dp = lambda a: a.ctypes.data_as(_dp) if a is not None else ctypes.cast(0, _dp)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        st = lib().pswf_server_wait_many(self._h, count, tickets.ctypes.data_as(i64p), offsets.ctypes.data_as(i64p),
+                                         dp(e), dp(ph), dp(f), dp(lat))
+        for t in tickets.tolist():   # every ticket is released by the call
+            getattr(self, "_n", {}).pop(t, None)
+        self._check(st)
+        return e, ph, f, lat
 
     def pause(self, pause: bool = True):
         """Holds back new batches (pause=True) or resumes them."""

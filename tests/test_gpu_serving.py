@@ -107,6 +107,36 @@ def test_server_burst_of_serving_stream():
     srv.close()
 
 
+def test_server_submit_many_equals_single_submits():
+    """pswf_server_submit_many / pswf_server_wait_many: 64 structures of the
+    serving stream handed over in one call give the energies, potentials
+    and forces of per-structure submits (the same routes, batch-mates do not
+    change a result within FP32 flush order); latencies are returned."""
+    from paper_2606_06617_b300 import lr
+    import torch
+    reqs = wl.serving_stream(64, seed=5)
+    h_max = 0.5 * math.pi * R_C / math.log(3.0 / 1e-5)
+    srv = lr.Server(8, (1, 6), R_C, lr.serving_buckets(8, h_max), device=torch.device("cuda", 0))
+    single = []
+    for r in reqs:
+        t = srv.submit(r.system.pos, r.system.q, r.system.box, r.system.ps)
+        single.append(srv.wait(t))
+    tk, off = srv.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in reqs])
+    e, ph, f, lat = srv.wait_many(tk, off, phi=True)
+    assert lat.shape == (64,) and np.all(lat > 0)
+    for i, (e1, ph1, f1, _) in enumerate(single):
+        a, b = off[i], off[i + 1]
+        np.testing.assert_allclose(e[i], e1, rtol=1e-6, atol=1e-9 * np.abs(e1).max())
+        assert rel_rms(ph[8 * a:8 * b].reshape(8, b - a), ph1) < 1e-6
+        assert rel_rms(f[a:b], f1) < 1e-6
+    # a bad structure (exponent outside the server's set) stops the call; earlier ones stay submitted
+    bad = [(reqs[0].system.pos, reqs[0].system.q, reqs[0].system.box, reqs[0].system.ps),
+           (reqs[1].system.pos, reqs[1].system.q, reqs[1].system.box, [3] * 8)]
+    with pytest.raises(lr.PswfError):
+        srv.submit_many(bad)
+    srv.close()
+
+
 def test_server_refuses_what_it_cannot_hold():
     from paper_2606_06617_b300 import lr
     srv = _server(1)
