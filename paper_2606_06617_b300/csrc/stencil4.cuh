@@ -24,7 +24,9 @@
 // and channel (channel planes, layout SPad); a warp takes one atom, its
 // lanes being four channels x eight stencil rows, so every shared atomic of
 // the warp hits 32 distinct banks.  The region is then added into the grid
-// with global atomics.
+// with global atomics; points that received nothing are skipped (sparse
+// tiles), and the flush zeroes what it read, so the region is cleared once
+// per launch rather than per work item.
 #pragma once
 
 #include "bounds.cuh"
@@ -404,6 +406,11 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
   const int nitems = g.B * g.nts * nchunk;
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   const float* st_l = st + int64_t(min(cl, 2)) * nmax;
+  {
+    // the region starts zeroed; each item's flush zeroes what it read
+    int4* r4 = reinterpret_cast<int4*>(regi);   // 4 N ints = N int4
+    for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
+  }
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int visit = item / nchunk, chunk = item - visit * nchunk;
     const int tile = tile_for_visit(g, visit);
@@ -414,10 +421,8 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
     const int gc0 = sidx * g.K + c0;
     int ox, oy, oz;
     tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
-    __syncthreads();   // the previous item's flush is done with the region
+    __syncthreads();   // the previous item's flush is done with the region (and zeroed it)
     {
-      int4* r4 = reinterpret_cast<int4*>(regi);   // 4 N ints = N int4
-      for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
       if (threadIdx.x < S)
         zoff_s[threadIdx.x] = wrap_index(oz + threadIdx.x, g.M[2]) * plane;
       else if (threadIdx.x < 2 * S)
@@ -488,7 +493,7 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
         const int c = pl / S, lz = pl - c * S;
         const float inv = inv_s[c];
         float* base = grid + (gc0 + c) * chan + zoff_s[lz];
-        const int* src = regi + c * N + lz * R2;
+        int* src = regi + c * N + lz * R2;
         if (!has0) continue;
         for (int ly = half; ly < S; ly += 2) {
           float* rowg = base + yoff_s[ly];
@@ -497,6 +502,9 @@ __global__ void __launch_bounds__(NT, 1) k_spread4(Geometry g, int64_t nmax, con
             continue;
           const int v0 = src[ly * R1 + x0];
           const int v1 = has1 ? src[ly * R1 + x0 + 1] : 0;
+          if ((v0 | v1) == 0) continue;   // nothing reached these points
+          src[ly * R1 + x0] = 0;          // zeroed for the next item
+          if (has1) src[ly * R1 + x0 + 1] = 0;
           if (pair) {
             atomicAdd(reinterpret_cast<float2*>(rowg + gx0), make_float2(float(v0) * inv, float(v1) * inv));
           } else {
@@ -544,6 +552,11 @@ __global__ void __launch_bounds__(NT, 1) k_spread4_bw(Geometry g, int64_t nmax, 
   const int nitems = g.B * g.nts * nchunk;
   const int64_t plane = int64_t(g.M[1]) * g.Mxp, chan = int64_t(g.M[2]) * plane;
   const float* st_l = st + int64_t(min(cl, 2)) * nmax;
+  {
+    // the region starts zeroed; each item's flush zeroes what it read
+    int4* r4 = reinterpret_cast<int4*>(regi);   // 4 N ints = N int4
+    for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
+  }
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int visit = item / nchunk, chunk = item - visit * nchunk;
     const int tile = tile_for_visit(g, visit);
@@ -554,10 +567,8 @@ __global__ void __launch_bounds__(NT, 1) k_spread4_bw(Geometry g, int64_t nmax, 
     const int gc0 = sidx * g.K + c0;
     int ox, oy, oz;
     tile_origin(g, tile - sidx * g.nts, ox, oy, oz);
-    __syncthreads();   // the previous item's flush is done with the region
+    __syncthreads();   // the previous item's flush is done with the region (and zeroed it)
     {
-      int4* r4 = reinterpret_cast<int4*>(regi);
-      for (int t = threadIdx.x; t < N; t += NT) r4[t] = make_int4(0, 0, 0, 0);
       if (threadIdx.x < S)
         zoff_s[threadIdx.x] = wrap_index(oz + threadIdx.x, g.M[2]) * plane;
       else if (threadIdx.x < 2 * S)
@@ -649,7 +660,7 @@ __global__ void __launch_bounds__(NT, 1) k_spread4_bw(Geometry g, int64_t nmax, 
         const int c = pl / S, lz = pl - c * S;
         const float inv = inv_s[c];
         float* base = grid2 + (gc0 + c) * chan + zoff_s[lz];
-        const int* src = regi + c * N + lz * R2;
+        int* src = regi + c * N + lz * R2;
         if (!has0) continue;
         for (int ly = half; ly < S; ly += 2) {
           float* rowg = base + yoff_s[ly];
@@ -658,6 +669,9 @@ __global__ void __launch_bounds__(NT, 1) k_spread4_bw(Geometry g, int64_t nmax, 
             continue;
           const int v0 = src[ly * R1 + x0];
           const int v1 = has1 ? src[ly * R1 + x0 + 1] : 0;
+          if ((v0 | v1) == 0) continue;   // nothing reached these points
+          src[ly * R1 + x0] = 0;          // zeroed for the next item
+          if (has1) src[ly * R1 + x0 + 1] = 0;
           if (pair) {
             atomicAdd(reinterpret_cast<float2*>(rowg + gx0), make_float2(float(v0) * inv, float(v1) * inv));
           } else {
