@@ -148,7 +148,7 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[N]) {
 template <int N1, bool INV>
 __device__ __forceinline__ void lane_dft(float2 (&v)[N1], const float2* __restrict__ stw, int lane) {
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
+  for (int st = 0; st < 4; ++st) {
     const int d = 16 >> st;
     // lower lane: a + b; upper lane: (a - b) W_{2d}^{lane mod d}, as
     // (v + s p) w with s = -1 and w = -W on the upper lane
@@ -160,6 +160,16 @@ __device__ __forceinline__ void lane_dft(float2 (&v)[N1], const float2* __restri
       const float px = __shfl_xor_sync(kFull, v[k1].x, d);
       const float py = __shfl_xor_sync(kFull, v[k1].y, d);
       v[k1] = cmul(make_float2(fmaf(sg, px, v[k1].x), fmaf(sg, py, v[k1].y)), w);
+    }
+  }
+  {
+    // the last stage's twiddles are 1 (lower lane) and -1 (upper): v' = s v + p
+    const float sg = (lane & 1) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float px = __shfl_xor_sync(kFull, v[k1].x, 1);
+      const float py = __shfl_xor_sync(kFull, v[k1].y, 1);
+      v[k1] = make_float2(fmaf(sg, v[k1].x, px), fmaf(sg, v[k1].y, py));
     }
   }
 }
@@ -181,8 +191,18 @@ __device__ __forceinline__ void lane_twiddle(float2 (&v)[N1], const float2* __re
 // lanes).  Output in natural lane order.
 template <int N1, bool INV>
 __device__ __forceinline__ void lane_dit(float2 (&v)[N1], const float2* __restrict__ stw, int lane) {
+  {
+    // the first stage's twiddles are 1: lower = v + p, upper = p - v
+    const float sg = (lane & 1) ? -1.0f : 1.0f;
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float px = __shfl_xor_sync(kFull, v[k1].x, 1);
+      const float py = __shfl_xor_sync(kFull, v[k1].y, 1);
+      v[k1] = make_float2(fmaf(sg, v[k1].x, px), fmaf(sg, v[k1].y, py));
+    }
+  }
+#pragma unroll
+  for (int st = 1; st < 5; ++st) {
     const int d = 1 << st;
     float2 w = __ldg(stw + st * 32 + lane);
     if (INV) w.y = -w.y;
