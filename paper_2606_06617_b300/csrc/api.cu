@@ -144,6 +144,52 @@ __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part,
   }
 }
 
+__global__ void k_scatter_rec(int64_t nmax, const float* __restrict__ q, Geometry g, const int* __restrict__ soff,
+                              const int* __restrict__ tile_of, const int* __restrict__ rank,
+                              const int* __restrict__ tile_start, const float* __restrict__ tmp_t,
+                              const uint64_t* __restrict__ tmp_cell, float4* __restrict__ rec,
+                              float4* __restrict__ qrec) {
+  const int64_t n = soff[g.B];
+  const int nchunk = (g.K + 3) / 4;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t dst = int64_t(tile_start[tile_of[i]]) + rank[i];
+    if (!in_bounds(dst, nmax, kBoundsScatter)) continue;
+    const uint64_t cell = tmp_cell[i];
+    rec[2 * dst] = make_float4(tmp_t[i], tmp_t[nmax + i], tmp_t[2 * nmax + i], __int_as_float(int(i)));
+    rec[2 * dst + 1] = make_float4(__int_as_float(int(uint32_t(cell))), __int_as_float(int(uint32_t(cell >> 32))),
+                                   0.0f, 0.0f);
+    for (int c4 = 0; c4 < nchunk; ++c4) {
+      const int c = 4 * c4;
+      qrec[int64_t(c4) * nmax + dst] =
+          make_float4(q[int64_t(c) * n + i], c + 1 < g.K ? q[int64_t(c + 1) * n + i] : 0.0f,
+                      c + 2 < g.K ? q[int64_t(c + 2) * n + i] : 0.0f, c + 3 < g.K ? q[int64_t(c + 3) * n + i] : 0.0f);
+    }
+  }
+}
+
+__global__ void k_unpack_rec(int64_t nmax, int K, int B, const int* __restrict__ soff, const float4* __restrict__ rec,
+                             const float4* __restrict__ qrec, float* __restrict__ st, uint64_t* __restrict__ scell,
+                             float* __restrict__ sq, int* __restrict__ sperm) {
+  const int64_t n = soff[B];
+  const int nchunk = (K + 3) / 4;
+  for (int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; m < n; m += int64_t(gridDim.x) * blockDim.x) {
+    const float4 a = rec[2 * m], b = rec[2 * m + 1];
+    st[m] = a.x;
+    st[nmax + m] = a.y;
+    st[2 * nmax + m] = a.z;
+    sperm[m] = __float_as_int(a.w);
+    scell[m] = uint64_t(uint32_t(__float_as_int(b.x))) | (uint64_t(uint32_t(__float_as_int(b.y))) << 32);
+    for (int c4 = 0; c4 < nchunk; ++c4) {
+      const float4 v = qrec[int64_t(c4) * nmax + m];
+      const int c = 4 * c4;
+      sq[int64_t(c) * nmax + m] = v.x;
+      if (c + 1 < K) sq[int64_t(c + 1) * nmax + m] = v.y;
+      if (c + 2 < K) sq[int64_t(c + 2) * nmax + m] = v.z;
+      if (c + 3 < K) sq[int64_t(c + 3) * nmax + m] = v.w;
+    }
+  }
+}
+
 __global__ void k_set_count(int* __restrict__ soff, int n) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     soff[0] = 0;
@@ -974,10 +1020,26 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   k_scan_apply<<<nsb, kScanBlock, 0, s>>>(ntl, p->tile_count, p->scan_sums, p->scan_per_block,
                                                       p->tile_start);
   if ((rc = launch_check(p, "k_scan_apply"))) return rc;
-  k_scatter<R><<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const R*>(q), geo, p->soff, p->tile_of, p->rank,
-                                           p->tile_start, static_cast<const R*>(p->tmp_t), p->tmp_cell,
-                                           static_cast<R*>(p->st), p->scell, static_cast<R*>(p->sq), p->sperm);
-  if ((rc = launch_check(p, "k_scatter"))) return rc;
+  const int nchunk4 = (p->host.K + 3) / 4;
+  if (sizeof(R) == 4 && p->n_max * (32 + 16 * int64_t(nchunk4)) <= p->grid_elems * int64_t(sizeof(R))) {
+    // records in slot order first (in the grid, unused until execute), then unpacked
+    float4* rec = static_cast<float4*>(p->grid);
+    float4* qrec = rec + 2 * p->n_max;
+    k_scatter_rec<<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const float*>(q), geo, p->soff, p->tile_of,
+                                              p->rank, p->tile_start, static_cast<const float*>(p->tmp_t),
+                                              p->tmp_cell, rec, qrec);
+    if ((rc = launch_check(p, "k_scatter_rec"))) return rc;
+    k_unpack_rec<<<blocks, kThreads, 0, s>>>(p->n_max, p->host.K, p->nrun, p->soff, rec, qrec,
+                                             static_cast<float*>(p->st), p->scell, static_cast<float*>(p->sq),
+                                             p->sperm);
+    if ((rc = launch_check(p, "k_unpack_rec"))) return rc;
+    ++p->launches[PSWF_STAGE_SET_POINTS];
+  } else {
+    k_scatter<R><<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const R*>(q), geo, p->soff, p->tile_of, p->rank,
+                                             p->tile_start, static_cast<const R*>(p->tmp_t), p->tmp_cell,
+                                             static_cast<R*>(p->st), p->scell, static_cast<R*>(p->sq), p->sperm);
+    if ((rc = launch_check(p, "k_scatter"))) return rc;
+  }
   if (p->tscale && ntl > 0) {
     const int tb = int(std::min<int64_t>((int64_t(ntl) * 32 + kThreads - 1) / kThreads, 148 * 64));
     k_tile_scale<<<tb, kThreads, 0, s>>>(ntl, p->host.K, p->n_max, p->tile_start,
