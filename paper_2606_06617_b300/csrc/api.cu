@@ -144,6 +144,14 @@ __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part,
   }
 }
 
+// FP32 scatter in two passes.  Written in place, k_scatter's nine 4- and
+// 8-byte stores per atom land on nine partly filled 32-byte sectors at
+// random places, and the L2 write traffic is about eleven times the useful
+// bytes.  Here each atom's sorted slot instead receives two aligned records
+// (rec [n_max][2] float4: t, original index; packed start cell; and per
+// chunk of four channels qrec [nchunk][n_max] float4), placed in a scratch
+// area (the grid, idle during set_points), and k_unpack_rec then writes the
+// sorted arrays in slot order with coalesced stores.
 __global__ void k_scatter_rec(int64_t nmax, const float* __restrict__ q, Geometry g, const int* __restrict__ soff,
                               const int* __restrict__ tile_of, const int* __restrict__ rank,
                               const int* __restrict__ tile_start, const float* __restrict__ tmp_t,

@@ -258,23 +258,6 @@ __global__ void k_bin(const PosT* __restrict__ pos, Geometry g, const double* __
   }
 }
 
-// FP32 scatter in two passes.  Written in place, k_scatter's nine 4- and
-// 8-byte stores per atom land on nine partly filled 32-byte sectors at
-// random places, and the L2 write traffic is about eleven times the useful
-// bytes.  Here each atom's sorted slot instead receives two aligned records
-// (rec [n_max][2] float4: t, original index; packed start cell; and per
-// chunk of four channels qrec [nchunk][n_max] float4), placed in a scratch
-// area (the grid, idle during set_points), and k_unpack_rec then writes the
-// sorted arrays in slot order with coalesced stores.
-__global__ void k_scatter_rec(int64_t nmax, const float* __restrict__ q, Geometry g, const int* __restrict__ soff,
-                              const int* __restrict__ tile_of, const int* __restrict__ rank,
-                              const int* __restrict__ tile_start, const float* __restrict__ tmp_t,
-                              const uint64_t* __restrict__ tmp_cell, float4* __restrict__ rec,
-                              float4* __restrict__ qrec);
-__global__ void k_unpack_rec(int64_t nmax, int K, int B, const int* __restrict__ soff, const float4* __restrict__ rec,
-                             const float4* __restrict__ qrec, float* __restrict__ st, uint64_t* __restrict__ scell,
-                             float* __restrict__ sq, int* __restrict__ sperm);
-
 template <typename R>
 __global__ void k_scatter(int64_t nmax, const R* __restrict__ q, Geometry g, const int* __restrict__ soff,
                           const int* __restrict__ tile_of, const int* __restrict__ rank,

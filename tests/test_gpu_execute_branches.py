@@ -8,7 +8,9 @@ transform path a single plan can take (own passes, cuFFT pruned, cuFFT full)
 and is compared with the oracle at the path's tolerance, and with the
 full call on the same plan.  Charged p = 3 and p = 5 channels exercise the
 zero-frequency terms of "Implementation details" (Eq. Correction3r and the
-p > 3 formula) on the device."""
+p > 3 formula) on the device.  Both ways the FP32 sort can place the atoms
+(records in the idle grid and an unpack pass, or the direct scatter when
+the grid is too small to hold the records) match the oracle."""
 import math
 
 import numpy as np
@@ -124,3 +126,19 @@ def test_own_transform_channel_quadruples(ps):
         assert abs(e[c] - o["E_ch"][c]) <= TOL_FP32 * abs(o["E_ch"][c]), (c, e[c], o["E_ch"][c])
     assert rel_rms(ph, o["phi"]) <= TOL_FP32, rel_rms(ph, o["phi"])
     assert rel_rms(f, o["F"]) <= TOL_FP32, rel_rms(f, o["F"])
+
+
+@pytest.mark.parametrize("natoms", [150, 6000], ids=["records", "direct_scatter"])
+def test_sort_paths_small_grid(natoms):
+    """A 12^3 grid with one channel holds 1 x 12 x 12 x 14 reals = 8064
+    bytes: 150 atoms' records (48 bytes each) fit and take the two-pass
+    scatter, 6000 do not and take the direct scatter.  Both against O1."""
+    box = (9.0, 9.0, 9.0)
+    s = wl.random_system(natoms, box, (1,), seed=31, neutral=True)
+    M, P, r_c = (12, 12, 12), 5, 4.0
+    plan, cw = _plan(s, box, M, P, r_c, 0)
+    e, phi, f = plan.execute()
+    plan.sync()
+    o = run_oracle(s, r_c, P, M, C_TOL, cw)
+    assert rel_rms(phi.cpu().double().numpy(), o["phi"]) <= TOL_FP32
+    assert rel_rms(f.cpu().double().numpy(), o["F"]) <= TOL_FP32
