@@ -454,10 +454,11 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, n_r
     atoms = sum(r.system.n for r in reqs)
 
     def burst(sub):
-        # the whole set handed over at once (pswf_server_submit_many), the
-        # energies and forces read back (pswf_server_wait_many)
+        # the whole set handed over at once (pswf_server_submit_many; the
+        # server reads the arrays when it stages them), the energies and
+        # forces read back (pswf_server_wait_many)
         t0 = time.perf_counter()
-        tk, off = srv.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub])
+        tk, off = srv.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub], borrow=True)
         lat = srv.wait_many(tk, off, phi=False)[3]
         return time.perf_counter() - t0, list(lat)
 
@@ -570,7 +571,8 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, n_r
     srv2 = lr.Server(K, (1, 6), r_c, buckets, tol=tol, inflight=2, device=dev)
 
     def burst2(sub):
-        tk, off = srv2.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub])
+        tk, off = srv2.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in sub],
+                                   borrow=True)
         srv2.wait_many(tk, off, phi=False)
     burst2(res_sub)
     burst2(res_sub)

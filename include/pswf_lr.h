@@ -443,11 +443,16 @@ int pswf_server_pause(pswf_server srv, int pause);
  * [count][3], ps host int [count][K], pos host array [count] of pointers to
  * each structure's positions (double [n_i][3]), q host array [count] of
  * pointers to its charges (double [K][n_i]); tickets host int64 [count]
- * receives the tickets.  Copies the inputs before returning.  On an error
- * the structures before the failing one stay submitted (their tickets are
- * written).  For clients that hand over many structures at once. */
+ * receives the tickets.  flags 0: the inputs are copied before the call
+ * returns; PSWF_SUBMIT_BORROW: they are only referenced, read when the
+ * structure's batch is staged, and the caller keeps them valid and
+ * unchanged until the structure has been waited for.  On an error the
+ * structures before the failing one stay submitted (their tickets are
+ * written); PSWF_EINVAL for unknown flags.  For clients that hand over many
+ * structures at once. */
+#define PSWF_SUBMIT_BORROW 1
 int pswf_server_submit_many(pswf_server srv, int64_t count, const int64_t* n, const double* boxes, const int* ps,
-                            const double* const* pos, const double* const* q, int64_t* tickets);
+                            const double* const* pos, const double* const* q, int64_t* tickets, int flags);
 
 /* Waits for count tickets (as pswf_server_wait, in order) and writes each
  * structure's results: energies host double [count][K + 1], phi host double

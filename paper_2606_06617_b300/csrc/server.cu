@@ -52,6 +52,10 @@ struct Request {
   std::vector<int> ps;          // [K]
   std::vector<double> pos;      // [n][3]
   std::vector<char> q;          // real [K][n]
+  // borrowed inputs (pswf_server_submit_many with PSWF_SUBMIT_BORROW): the
+  // caller's arrays, read when the batch is staged; null when copied
+  const double* pos_ref = nullptr;   // [n][3]
+  const double* q_ref = nullptr;     // [K][n]
   int bucket = 0;
   int status = 1;               // 1 pending, 0 done, < 0 failed
   Clock::time_point t_submit, t_done;
@@ -255,10 +259,21 @@ int launch_batch(pswf_server srv, Bucket& b, Context& c) {
   for (int i = 0; i < nb; ++i) {
     const Request* r = c.reqs[i];
     if (!r->n) continue;
-    std::memcpy(c.h_pos + 3 * c.offsets[i], r->pos.data(), size_t(r->n) * 24);
-    for (int k = 0; k < K; ++k)
-      std::memcpy(static_cast<char*>(c.h_q) + (size_t(k) * n + c.offsets[i]) * rs, r->q.data() + size_t(k) * r->n * rs,
-                  size_t(r->n) * rs);
+    std::memcpy(c.h_pos + 3 * c.offsets[i], r->pos_ref ? r->pos_ref : r->pos.data(), size_t(r->n) * 24);
+    for (int k = 0; k < K; ++k) {
+      char* dst = static_cast<char*>(c.h_q) + (size_t(k) * n + c.offsets[i]) * rs;
+      if (r->q_ref) {   // borrowed: rounded to the server's precision on the way
+        const double* src = r->q_ref + size_t(k) * r->n;
+        if (rs == 4) {
+          float* d = reinterpret_cast<float*>(dst);
+          for (int64_t a = 0; a < r->n; ++a) d[a] = float(src[a]);
+        } else {
+          std::memcpy(dst, src, size_t(r->n) * 8);
+        }
+      } else {
+        std::memcpy(dst, r->q.data() + size_t(k) * r->n * rs, size_t(r->n) * rs);
+      }
+    }
   }
   int rc;
   if ((rc = pswf::plan_fill_tables(c.plan, nb, boxes.data(), ps.data(), c.offsets.data()))) {
@@ -472,7 +487,7 @@ int pswf_server_route(pswf_server srv, int64_t n, const double box[3], pswf_info
 
 int pswf_server_submit(pswf_server srv, int64_t n, const double box[3], const int* ps, const double* pos,
                        const double* q, int64_t* ticket) {
-  return pswf_server_submit_many(srv, 1, &n, box, ps, &pos, &q, ticket);
+  return pswf_server_submit_many(srv, 1, &n, box, ps, &pos, &q, ticket, 0);
 }
 
 int pswf_server_wait(pswf_server srv, int64_t ticket, double* energy, double* phi, double* forces,
@@ -520,8 +535,10 @@ int pswf_server_wait_for(pswf_server srv, int64_t ticket, double timeout_ms, dou
 }
 
 int pswf_server_submit_many(pswf_server srv, int64_t count, const int64_t* n, const double* boxes, const int* ps,
-                            const double* const* pos, const double* const* q, int64_t* tickets) {
+                            const double* const* pos, const double* const* q, int64_t* tickets, int flags) {
   if (!srv || count < 0 || (count > 0 && (!n || !boxes || !ps || !pos || !q || !tickets))) return PSWF_EINVAL;
+  if (flags & ~PSWF_SUBMIT_BORROW) return PSWF_EINVAL;
+  const bool borrow = (flags & PSWF_SUBMIT_BORROW) != 0;
   const int K = srv->K;
   // routes first: the structures before the first invalid one are submitted
   std::vector<int> bucket(static_cast<size_t>(count));
@@ -570,6 +587,13 @@ int pswf_server_submit_many(pswf_server srv, int64_t count, const int64_t* n, co
       for (int d = 0; d < 3; ++d) r->box[d] = boxes[3 * i + d];
       r->ps.assign(ps + size_t(K) * i, ps + size_t(K) * (i + 1));
       r->bucket = bucket[size_t(i)];
+      if (borrow) {
+        r->pos_ref = pos[i];
+        r->q_ref = q[i];
+        continue;
+      }
+      r->pos_ref = nullptr;
+      r->q_ref = nullptr;
       r->pos.assign(pos[i], pos[i] + 3 * ni);
       r->q.resize(size_t(K) * ni * rs);
       if (rs == 4) {

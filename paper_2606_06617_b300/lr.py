@@ -20,6 +20,7 @@ LIB_PATH = os.environ.get("PSWF_LR_LIBRARY") or os.path.join(_HERE, "libpswf_lr.
 LIB_CHECKED_PATH = os.path.join(_HERE, "libpswf_lr_checked.so")
 
 PSWF_ETIMEOUT = -5
+PSWF_SUBMIT_BORROW = 1
 PSWF_EBOUNDS = -10
 PSWF_FLAG_BACKWARD = 1
 PSWF_FLAG_VIRIAL = 2
@@ -115,7 +116,7 @@ SIGNATURES = {
     "pswf_server_wait_for": ([_vp, _i64, ctypes.c_double, _dp, _dp, _dp, _dp], ctypes.c_int),
     "pswf_server_pause": ([_vp, ctypes.c_int], ctypes.c_int),
     "pswf_server_submit_many": ([_vp, _i64, ctypes.POINTER(ctypes.c_int64), _dp, _ip, ctypes.POINTER(_dp),
-                                 ctypes.POINTER(_dp), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+                                 ctypes.POINTER(_dp), ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
     "pswf_server_wait_many": ([_vp, _i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _dp, _dp,
                                _dp, _dp], ctypes.c_int),
     "pswf_server_stats": ([_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -601,14 +602,19 @@ class Server:
         st = lib().pswf_server_wait_for(self._h, ticket, t, dp(e), dp(ph), dp(f), ctypes.byref(lat))
         if st != PSWF_ETIMEOUT:
             del self._n[ticket]   # released by the server (done or failed)
+            getattr(self, "_borrowed", {}).pop(ticket, None)
         self._check(st)
         return e, ph, f, lat.value
 
-    def submit_many(self, structures):
+    def submit_many(self, structures, borrow: bool = False):
         """Submits [(pos [n, 3], q [K, n], box, ps), ...] in one call
         (pswf_server_submit_many; each structure's arrays are passed by
         address, float64 C-contiguous ones without a copy); returns
-        (tickets, offsets) int64 arrays, offsets the running atom counts."""
+        (tickets, offsets) int64 arrays, offsets the running atom counts.
+        borrow=True (PSWF_SUBMIT_BORROW): the server reads the arrays when
+        it stages their batch instead of copying them now; they stay
+        referenced by this object until wait_many releases the tickets, and
+        the caller must not change them before that."""
         count = len(structures)
         pos_l = [np.ascontiguousarray(st[0], dtype=np.float64) for st in structures]
         q_l = [np.ascontiguousarray(st[1], dtype=np.float64) for st in structures]
@@ -623,11 +629,19 @@ class Server:
         off[1:] = np.cumsum(ns)
         tk = np.zeros(count, dtype=np.int64)
         i64p, dpp = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_dp)
-        self._check(lib().pswf_server_submit_many(self._h, count, ns.ctypes.data_as(i64p), boxes.ctypes.data_as(_dp),
-                                                  ps.ctypes.data_as(_ip), pos_a.ctypes.data_as(dpp),
-                                                  q_a.ctypes.data_as(dpp), tk.ctypes.data_as(i64p)))
+        st = lib().pswf_server_submit_many(self._h, count, ns.ctypes.data_as(i64p), boxes.ctypes.data_as(_dp),
+                                           ps.ctypes.data_as(_ip), pos_a.ctypes.data_as(dpp), q_a.ctypes.data_as(dpp),
+                                           tk.ctypes.data_as(i64p), PSWF_SUBMIT_BORROW if borrow else 0)
+        # the structures submitted before an error have their tickets written
         self._n = getattr(self, "_n", {})
-        self._n.update(zip(tk.tolist(), ns.tolist()))
+        self._borrowed = getattr(self, "_borrowed", {})
+        for t, n, a, b in zip(tk.tolist(), ns.tolist(), pos_l, q_l):
+            if t == 0:
+                break
+            self._n[t] = n
+            if borrow:   # referenced by the server until the ticket is released
+                self._borrowed[t] = (a, b)
+        self._check(st)
         return tk, off
 
     def wait_many(self, tickets, offsets, phi: bool = False, forces: bool = True):
@@ -648,6 +662,7 @@ class Server:
                                          dp(e), dp(ph), dp(f), dp(lat))
         for t in tickets.tolist():   # every ticket is released by the call
             getattr(self, "_n", {}).pop(t, None)
+            getattr(self, "_borrowed", {}).pop(t, None)
         self._check(st)
         return e, ph, f, lat
 

@@ -121,14 +121,16 @@ def test_server_submit_many_equals_single_submits():
     for r in reqs:
         t = srv.submit(r.system.pos, r.system.q, r.system.box, r.system.ps)
         single.append(srv.wait(t))
-    tk, off = srv.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in reqs])
-    e, ph, f, lat = srv.wait_many(tk, off, phi=True)
-    assert lat.shape == (64,) and np.all(lat > 0)
-    for i, (e1, ph1, f1, _) in enumerate(single):
-        a, b = off[i], off[i + 1]
-        np.testing.assert_allclose(e[i], e1, rtol=1e-6, atol=1e-9 * np.abs(e1).max())
-        assert rel_rms(ph[8 * a:8 * b].reshape(8, b - a), ph1) < 1e-6
-        assert rel_rms(f[a:b], f1) < 1e-6
+    for borrow in (False, True):   # inputs copied at submission, or read when staged
+        tk, off = srv.submit_many([(r.system.pos, r.system.q, r.system.box, r.system.ps) for r in reqs],
+                                  borrow=borrow)
+        e, ph, f, lat = srv.wait_many(tk, off, phi=True)
+        assert lat.shape == (64,) and np.all(lat > 0)
+        for i, (e1, ph1, f1, _) in enumerate(single):
+            a, b = off[i], off[i + 1]
+            np.testing.assert_allclose(e[i], e1, rtol=1e-6, atol=1e-9 * np.abs(e1).max())
+            assert rel_rms(ph[8 * a:8 * b].reshape(8, b - a), ph1) < 1e-6
+            assert rel_rms(f[a:b], f1) < 1e-6
     # a bad structure (exponent outside the server's set) stops the call; earlier ones stay submitted
     bad = [(reqs[0].system.pos, reqs[0].system.q, reqs[0].system.box, reqs[0].system.ps),
            (reqs[1].system.pos, reqs[1].system.q, reqs[1].system.box, [3] * 8)]
