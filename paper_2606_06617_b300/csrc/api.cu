@@ -805,6 +805,12 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.scell = p->scell;
   c.sq = p->sq;
   c.sperm = p->sperm;
+  c.tile_of = p->tile_of;
+  c.rank = p->rank;
+  c.out_scratch = p->spec;
+  c.out_scratch_bytes = p->spec ? int64_t(p->host.K) * (p->host.M[0] / 2 + 1) * p->host.M[1] * p->host.M[2] * 2 *
+                                      int64_t(p->real_size)
+                                : 0;
   c.grid = p->grid;
   c.zero_coef = p->zero_coef;
   c.charges = p->charges;

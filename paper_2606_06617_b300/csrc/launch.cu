@@ -115,11 +115,24 @@ cudaError_t interp4_P(const LaunchCtx& c, void* phi, void* forces, int* nlaunch)
   int blocks = 0;
   e = persistent_blocks<P>(k_gather4<P, kGather4Threads>, smem, int64_t(c.ntiles) * nchunk, &blocks, kGather4Threads);
   if (e != cudaSuccess) return e;
+  // one channel chunk and an idle buffer of 32 bytes per atom: outputs as
+  // records in sorted order, then one coalesced pass to the caller's order
+  float* rec = (nchunk == 1 && c.out_scratch && c.out_scratch_bytes >= c.nmax * 32 && c.tile_of && c.rank)
+                   ? static_cast<float*>(c.out_scratch)
+                   : nullptr;
   k_gather4<P, kGather4Threads><<<blocks, kGather4Threads, smem, c.stream>>>(
       c.nmax, c.geo, c.smol, c.soff, c.tile_start, static_cast<const float*>(c.st), c.scell,
       static_cast<const float*>(c.sq), c.sperm, wc, static_cast<const float*>(c.grid), c.zero_coef, c.charges,
-      static_cast<float*>(phi), static_cast<float*>(forces), c.psi_il);
+      static_cast<float*>(phi), static_cast<float*>(forces), c.psi_il, rec);
   ++*nlaunch;
+  if (rec) {
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int ub = int(std::min<int64_t>((c.nmax + 255) / 256, 148 * 16));
+    k_unpack_gather<<<std::max(ub, 1), 256, 0, c.stream>>>(c.geo, c.nmax, c.soff, c.tile_of, c.rank, c.tile_start,
+                                                           reinterpret_cast<const float4*>(rec),
+                                                           static_cast<float*>(phi), static_cast<float*>(forces));
+    ++*nlaunch;
+  }
   return cudaGetLastError();
 }
 

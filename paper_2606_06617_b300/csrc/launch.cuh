@@ -26,6 +26,10 @@ struct LaunchCtx {
   const uint64_t* scell = nullptr;  // [nmax]
   const void* sq = nullptr;         // real [K][nmax]
   const int* sperm = nullptr;       // [nmax]
+  const int* tile_of = nullptr;     // [nmax] tile of each atom (caller order)
+  const int* rank = nullptr;        // [nmax] its slot within the tile
+  void* out_scratch = nullptr;      // idle during the gather (single structures' spectrum), or null
+  int64_t out_scratch_bytes = 0;
   void* grid = nullptr;             // real [B][K][Mz][My][Mxp]
   const double* zero_coef = nullptr;   // [B K]
   const double* charges = nullptr;     // [B K][2]

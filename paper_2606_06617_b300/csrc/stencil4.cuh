@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
                                                    const float* __restrict__ grid,
                                                    const double* __restrict__ zero_coef,
                                                    const double* __restrict__ charges, float* __restrict__ phi,
-                                                   float* __restrict__ forces, bool psi_il) {
+                                                   float* __restrict__ forces, bool psi_il,
+                                                   float* __restrict__ out_rec) {
   static_assert(P <= 8, "one 8-lane group per atom");
   using L = Pad4<P>;
   constexpr int S = L::S, R1 = L::R1, R2 = L::R2;
@@ -339,7 +340,13 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
         const float keep = h1 ? r2[1] : r2[0], give = h1 ? r2[0] : r2[1];
         v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
       }
-      if (valid) {
+      if (valid && out_rec) {
+        // one channel chunk: the atom's record in its sorted slot (the 8
+        // lanes of the group fill one 32-byte sector); k_unpack_gather
+        // writes the caller's layouts
+        if (j < 7 && in_bounds(8 * int64_t(a) + j, 8 * nmax, kBoundsGatherOut))
+          out_rec[8 * int64_t(a) + j] = j < 4 ? v[0] + zshift : v[0];
+      } else if (valid) {
         if (j < 4) {
           if (phi && j < nk && in_bounds(int64_t(c0 + j) * n + o, int64_t(g.K) * n, kBoundsGatherOut))
             phi[int64_t(c0 + j) * n + o] = v[0] + zshift;
@@ -351,6 +358,32 @@ __global__ void __launch_bounds__(NT, 1) k_gather4(int64_t nmax, Geometry g, con
             atomicAdd(fo, v[0]);
         }
       }
+    }
+  }
+}
+
+// Records of k_gather4 (sorted slot m: four potentials, three force
+// components) to phi [K][n] and forces [n][3] in the caller's order: atom
+// i's slot is tile_start[tile_of[i]] + rank[i], so the writes are coalesced
+// and each record is one 32-byte sector read.
+static __global__ void k_unpack_gather(Geometry g, int64_t nmax, const int* __restrict__ soff, const int* __restrict__ tile_of,
+                                const int* __restrict__ rank, const int* __restrict__ tile_start,
+                                const float4* __restrict__ rec, float* __restrict__ phi, float* __restrict__ forces) {
+  const int64_t n = soff[g.B];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t m = int64_t(tile_start[tile_of[i]]) + rank[i];
+    if (!in_bounds(m, nmax, kBoundsGatherOut)) continue;
+    const float4 a = rec[2 * m], b = rec[2 * m + 1];
+    if (phi) {
+      const float v[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < g.K) phi[int64_t(c) * n + i] = v[c];
+    }
+    if (forces) {
+      forces[3 * i] = b.x;
+      forces[3 * i + 1] = b.y;
+      forces[3 * i + 2] = b.z;
     }
   }
 }
