@@ -914,6 +914,7 @@ def main():
 
     serving = None
     total = None
+    training = None
     info = dict(plan.info)
     if rank == 0 and world == 1 and args.workload == "melt":
         del plan, pos, q, out
@@ -922,6 +923,9 @@ def main():
         total = run_total(max(3, min(args.steps, 10)), 3, cpu_baseline=False)
         total = {k: total[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "roofline",
                                        "stages_ms_per_step", "real_space_backward_ms", "gpu_launches", "clocks")}
+        torch.cuda.empty_cache()
+        # the training-step shape (forward + force-matching backward of a batch)
+        training = run_training(steps=max(5, min(args.steps, 20)), warmup=3)
         torch.cuda.empty_cache()
         if not args.no_serving:
             serving = run_serving()
@@ -954,6 +958,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "total": total,
+            "training": training,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
