@@ -261,7 +261,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kEnergyBlocks = 592;   // 4 x 148 SMs
 constexpr int kQBlocks = 148;        // charge-sum blocks of pswf_self_energy_noalloc
-constexpr int kQBlocksPlan = 592;    // charge-sum blocks of a single-structure plan (4 per SM)
+constexpr int kQBlocksPlan = 1184;   // charge-sum blocks of a single-structure plan (8 per SM)
 constexpr int kQBlocksBatch = 8;     // per structure in a batch plan
 
 int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }

@@ -292,9 +292,9 @@ __global__ void k_set_count(int* __restrict__ soff, int n);
 
 // Per-thread sums of q and q^2.  FP32 charges: double-float sums (a float
 // sum and its running rounding error by TwoSum; q^2 split exactly into
-// v*v and fma(v, v, -v*v)), converted to FP64 once per thread, so the FP64
-// pipe (narrow on this GPU) only sees the reductions across threads.  FP64
-// charges: FP64 sums.
+// v*v and fma(v, v, -v*v)), merged across a warp in the same form and
+// converted to FP64 once per warp, so the FP64 pipe (narrow on this GPU)
+// only sees the sums across warps.  FP64 charges: FP64 sums.
 template <typename R>
 struct ChargeAcc {
   double a = 0.0, b = 0.0;
@@ -302,6 +302,16 @@ struct ChargeAcc {
     const double d = double(v);
     a += d;
     b += d * d;
+  }
+  __device__ void merge(const ChargeAcc& o) {
+    a += o.a;
+    b += o.b;
+  }
+  __device__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
   }
   __device__ double sum() const { return a; }
   __device__ double sumsq() const { return b; }
@@ -321,21 +331,37 @@ struct ChargeAcc<float> {
     two_sum(a, ae, v);
     two_sum(b, be, p);
   }
+  __device__ void merge(const ChargeAcc& o) {
+    two_sum(a, ae, o.a);
+    ae += o.ae;
+    two_sum(b, be, o.b);
+    be += o.be;
+  }
+  // lane 0 ends with the warp's sums
+  __device__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      ChargeAcc t;
+      t.a = __shfl_down_sync(0xffffffffu, a, o);
+      t.ae = __shfl_down_sync(0xffffffffu, ae, o);
+      t.b = __shfl_down_sync(0xffffffffu, b, o);
+      t.be = __shfl_down_sync(0xffffffffu, be, o);
+      merge(t);
+    }
+  }
   __device__ double sum() const { return double(a) + double(ae); }
   __device__ double sumsq() const { return double(b) + double(be); }
 };
 
-// Block sums of the two per-thread values, written by thread 0.
-__device__ inline void charge_block_sums(double s1, double s2, double* __restrict__ out) {
+// Block sums of the threads' accumulators, written by thread 0: merged
+// within each warp in the accumulator's form, then across warps in FP64.
+template <typename R>
+__device__ inline void charge_block_sums(ChargeAcc<R> acc, double* __restrict__ out) {
   __shared__ double sh[2][32];
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    s2 += __shfl_down_sync(0xffffffffu, s2, o);
-  }
+  acc.warp_reduce();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    sh[0][wid] = s1;
-    sh[1][wid] = s2;
+    sh[0][wid] = acc.sum();
+    sh[1][wid] = acc.sumsq();
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -360,16 +386,20 @@ __global__ void k_charge_partials_seg(const R* __restrict__ q, int K, int B, con
   const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
   const int64_t step = int64_t(gridDim.x) * blockDim.x;
   for (int c = 0; c < K; ++c) {
-    // two interleaved accumulators: independent dependency chains
+    // four loads in flight per thread, two interleaved accumulators
     ChargeAcc<R> acc0, acc1;
+    const R* qc = q + c * n;
     int64_t i = a0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    for (; i + step < a1; i += 2 * step) {
-      acc0.add(q[c * n + i]);
-      acc1.add(q[c * n + i + step]);
+    for (; i + 3 * step < a1; i += 4 * step) {
+      const R v0 = qc[i], v1 = qc[i + step], v2 = qc[i + 2 * step], v3 = qc[i + 3 * step];
+      acc0.add(v0);
+      acc1.add(v1);
+      acc0.add(v2);
+      acc1.add(v3);
     }
-    if (i < a1) acc0.add(q[c * n + i]);
-    charge_block_sums(acc0.sum() + acc1.sum(), acc0.sumsq() + acc1.sumsq(),
-                      part + ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2);
+    for (; i < a1; i += step) acc0.add(qc[i]);
+    acc0.merge(acc1);
+    charge_block_sums(acc0, part + ((size_t(s) * gridDim.x + blockIdx.x) * K + c) * 2);
   }
 }
 
@@ -386,14 +416,10 @@ __global__ void k_charge_sums_warp(const R* __restrict__ q, int K, int B, const 
   const int64_t n = soff[B], a0 = soff[s], a1 = soff[s + 1];
   ChargeAcc<R> acc;
   for (int64_t i = a0 + lane; i < a1; i += 32) acc.add(q[c * n + i]);
-  double s1 = acc.sum(), s2 = acc.sumsq();
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    s2 += __shfl_down_sync(0xffffffffu, s2, o);
-  }
+  acc.warp_reduce();
   if (lane == 0) {
-    charges[2 * g] = s1;
-    charges[2 * g + 1] = s2;
+    charges[2 * g] = acc.sum();
+    charges[2 * g + 1] = acc.sumsq();
   }
 }
 
@@ -404,7 +430,7 @@ __global__ void k_charge_partials(int64_t n, const R* __restrict__ q, int K, dou
     ChargeAcc<R> acc;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
       acc.add(q[c * n + i]);
-    charge_block_sums(acc.sum(), acc.sumsq(), part + (size_t(blockIdx.x) * K + c) * 2);
+    charge_block_sums(acc, part + (size_t(blockIdx.x) * K + c) * 2);
   }
 }
 

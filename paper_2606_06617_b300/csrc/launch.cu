@@ -80,9 +80,9 @@ cudaError_t persistent_blocks(Kern kern, size_t smem, int64_t items, int* blocks
 }
 
 // Threads of the FP32 four-channel stencil kernels (one CTA per SM).
-constexpr int kSpread4Threads = 1024;
-constexpr int kGather4Threads = 512;
-constexpr int kSpread4BwThreads = 1024;
+[[maybe_unused]] constexpr int kSpread4Threads = 1024;
+[[maybe_unused]] constexpr int kGather4Threads = 512;
+[[maybe_unused]] constexpr int kSpread4BwThreads = 1024;
 
 // FP32 kernels for P <= 8: four channels per work item, windows evaluated in
 // the lanes (stencil4.cuh).

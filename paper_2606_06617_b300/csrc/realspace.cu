@@ -195,10 +195,15 @@ __device__ inline void add_row(R* row, const R (&p)[KC], R fx, R fy, R fz, int K
   }
 }
 
-// cell of a wrapped position (count and rank within the cell)
+// cell of a wrapped position (count and rank within the cell).  With ufix
+// (FP32 plans) also the fixed-point cell-local coordinates and the cell,
+// ufix[i] = (u_x, u_y, u_z, cell), so that the scatter needs no FP64
+// arithmetic (FP64 runs at a small fraction of the FP32 rate here).  Boxes
+// take the diagonal of H^-1 alone (the off-diagonal terms are exact zeros).
 template <typename PosT>
 __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom g, int* __restrict__ cell_of,
-                         int* __restrict__ rank, int* __restrict__ count, int* __restrict__ err) {
+                         int* __restrict__ rank, int* __restrict__ count, int4* __restrict__ ufix,
+                         int* __restrict__ err) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     double r[3];
     for (int d = 0; d < 3; ++d) {
@@ -209,26 +214,126 @@ __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom 
       }
     }
     int ci[3];
+    double fs[3];
     for (int d = 0; d < 3; ++d) {
-      const double s = r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d];   // in cells
-      const double fs = s - floor(s);             // [0, 1]
-      int c = int(fs * g.nc[d]);
+      const double s = g.tric ? r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d]
+                              : r[d] * g.hinv[4 * d];   // in cells
+      fs[d] = s - floor(s);                             // [0, 1]
+      const int c = int(fs[d] * g.nc[d]);
       ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
     }
     const int cell = (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
     cell_of[i] = cell;
     rank[i] = atomicAdd(count + cell, 1);
+    if (ufix) {
+      // rint((fs n_c - c) 2^kFixBits) clamped to [0, 2^kFixBits]: fs n_c - c
+      // is exact and the scaling by 2^kFixBits too, so this equals the
+      // rounded fs n_c 2^kFixBits less c 2^kFixBits, taken in integers
+      int u[3];
+      for (int d = 0; d < 3; ++d) {
+        const long long w = __double2ll_rn(fs[d] * g.nc[d] * double(1 << kFixBits)) - (static_cast<long long>(ci[d]) << kFixBits);
+        u[d] = int(w < 0 ? 0 : (w > (1LL << kFixBits) ? (1LL << kFixBits) : w));
+      }
+      ufix[i] = make_int4(u[0], u[1], u[2], cell);
+    }
   }
 }
 
-// cell-local test coordinates [nmax][4] and records [nmax][rw] (exact
-// coordinates, charges), the original index, and zeroed accumulator rows
-// [nmax][aw] (acc may be null)
+// FP32 scatter from k_rs_bin's ufix: test coordinates t = u . (edges /
+// 2^kFixBits) in FP32, records as whole 16-byte vectors, zeroed accumulator
+// rows.  ew[9] = the list cell's edge vectors per fixed-point step.
+struct EdgeStep {
+  float ew[9];
+};
+__global__ void k_rs_scatter_fix(int64_t n, int K, int rw, const float* __restrict__ q, EdgeStep es,
+                                 const int4* __restrict__ ufix, const int* __restrict__ rank,
+                                 const int* __restrict__ cell_start, float4* __restrict__ lchk,
+                                 float* __restrict__ rec, int* __restrict__ perm, float4* __restrict__ acc, int aw) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int4 u = ufix[i];
+    const int64_t dst = int64_t(cell_start[u.w]) + rank[i];
+    if (!in_bounds(dst, n, kBoundsRsScatter)) continue;
+    const float fu[3] = {float(u.x), float(u.y), float(u.z)};
+    float t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = fmaf(fu[0], es.ew[k], fmaf(fu[1], es.ew[3 + k], fu[2] * es.ew[6 + k]));
+    lchk[dst] = make_float4(t[0], t[1], t[2], 0.0f);
+    float4* r4 = reinterpret_cast<float4*>(rec + dst * rw);
+    for (int w = 0; w < rw; w += 4) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = w + e;
+        v[e] = x < 3 ? __int_as_float(x == 0 ? u.x : (x == 1 ? u.y : u.z))
+                     : (x - 3 < K ? q[int64_t(x - 3) * n + i] : 0.0f);
+      }
+      r4[w / 4] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    perm[dst] = int(i);
+    for (int w = 0; w < aw; w += 4) acc[(dst * aw + w) / 4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// FP32 scatter in two passes (random 16-byte and 4-byte stores to the
+// sorted arrays fill partial sectors, which cost DRAM read-modify-writes
+// once the arrays exceed L2).  k_rs_scatter_rec moves each atom's
+// fixed-point coordinates, original index and charges as one aligned record
+// [4 + 4 ceil(K / 4)] words to its slot in the backward's record area (row
+// stride aw words); k_rs_unpack then writes the test coordinates, records,
+// order and zeroed accumulator rows in slot order, coalesced.
+__global__ void k_rs_scatter_rec(int64_t n, int K, int aw, const float* __restrict__ q,
+                                 const int4* __restrict__ ufix, const int* __restrict__ rank,
+                                 const int* __restrict__ cell_start, float4* __restrict__ brec) {
+  const int nq4 = (K + 3) / 4;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int4 u = ufix[i];
+    const int64_t dst = int64_t(cell_start[u.w]) + rank[i];
+    if (!in_bounds(dst, n, kBoundsRsScatter)) continue;
+    float4* r = brec + dst * (aw / 4);
+    r[0] = make_float4(__int_as_float(u.x), __int_as_float(u.y), __int_as_float(u.z), __int_as_float(int(i)));
+    for (int c4 = 0; c4 < nq4; ++c4) {
+      const int c = 4 * c4;
+      r[1 + c4] = make_float4(q[int64_t(c) * n + i], c + 1 < K ? q[int64_t(c + 1) * n + i] : 0.0f,
+                              c + 2 < K ? q[int64_t(c + 2) * n + i] : 0.0f, c + 3 < K ? q[int64_t(c + 3) * n + i] : 0.0f);
+    }
+  }
+}
+
+__global__ void k_rs_unpack(int64_t n, int K, int rw, int aw, EdgeStep es, const float* __restrict__ brec,
+                            float4* __restrict__ lchk, float* __restrict__ rec, int* __restrict__ perm,
+                            float4* __restrict__ acc) {
+  for (int64_t m = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; m < n; m += int64_t(gridDim.x) * blockDim.x) {
+    const float* rf = brec + m * aw;
+    const float4 h = reinterpret_cast<const float4*>(rf)[0];
+    const float fu[3] = {float(__float_as_int(h.x)), float(__float_as_int(h.y)), float(__float_as_int(h.z))};
+    float t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] = fmaf(fu[0], es.ew[k], fmaf(fu[1], es.ew[3 + k], fu[2] * es.ew[6 + k]));
+    lchk[m] = make_float4(t[0], t[1], t[2], 0.0f);
+    float4* r4 = reinterpret_cast<float4*>(rec + m * rw);
+    for (int w = 0; w < rw; w += 4) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = w + e;
+        v[e] = x < 3 ? (x == 0 ? h.x : (x == 1 ? h.y : h.z)) : (x - 3 < K ? rf[x + 1] : 0.0f);
+      }
+      r4[w / 4] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    perm[m] = __float_as_int(h.w);
+    for (int w = 0; w < aw; w += 4) acc[(m * aw + w) / 4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// FP64 plans: cell-local test coordinates [nmax][4] and records [nmax][rw]
+// (exact coordinates, charges), the original index, and zeroed accumulator
+// rows [nmax][aw]
 template <typename PosT, typename R>
 __global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ pos, const R* __restrict__ q,
                              RealSpaceGeom g, const int* __restrict__ cell_of, const int* __restrict__ rank,
                              const int* __restrict__ cell_start, R* __restrict__ lchk, R* __restrict__ rec,
                              int* __restrict__ perm, R* __restrict__ acc, int aw) {
+  static_assert(std::is_same<R, double>::value, "FP32 plans scatter with k_rs_scatter_fix");
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int cell = cell_of[i];
     const int64_t dst = int64_t(cell_start[cell]) + rank[i];
@@ -244,23 +349,13 @@ __global__ void k_rs_scatter(int64_t n, int K, int rw, const PosT* __restrict__ 
     for (int d = 0; d < 3; ++d) {
       const double s = x[0] * g.hinv[d] + x[1] * g.hinv[3 + d] + x[2] * g.hinv[6 + d];
       u[d] = (s - floor(s)) * g.nc[d] - ci[d];
-      if constexpr (std::is_same<R, float>::value) {
-        double v = rint(u[d] * double(1 << kFixBits));
-        v = v < 0.0 ? 0.0 : (v > double(1 << kFixBits) ? double(1 << kFixBits) : v);
-        r[d] = __int_as_float(int(v));
-      } else {
-        r[d] = u[d];
-      }
+      r[d] = u[d];
     }
     R t4[4] = {R(0), R(0), R(0), R(0)};   // Cartesian, from the list cell's corner
     for (int k = 0; k < 3; ++k) t4[k] = R(u[0] * g.cw[k] + u[1] * g.cw[3 + k] + u[2] * g.cw[6 + k]);
-    if constexpr (std::is_same<R, float>::value) {
-      store_vec<R>(lchk + 4 * dst, t4);
-    } else {
-      const R a2[2] = {t4[0], t4[1]}, b2[2] = {t4[2], R(0)};
-      store_vec<R>(lchk + 4 * dst, a2);
-      store_vec<R>(lchk + 4 * dst + 2, b2);
-    }
+    const R a2[2] = {t4[0], t4[1]}, b2[2] = {t4[2], R(0)};
+    store_vec<R>(lchk + 4 * dst, a2);
+    store_vec<R>(lchk + 4 * dst + 2, b2);
     for (int w = 3; w < rw; ++w) r[w] = w - 3 < K ? q[int64_t(w - 3) * n + i] : R(0);
     perm[dst] = int(i);
     if (acc) {
@@ -689,10 +784,48 @@ __global__ void __launch_bounds__(kRsThreads, 2) k_rs_pairs(PairArgs<R> a) {
   }
 }
 
+// Sum of products q phi per thread.  FP32: double-float (a float sum and
+// its running rounding error by TwoSum, each product split exactly by an
+// FMA), merged across the warp in that form and converted to FP64 once per
+// warp, since FP64 runs at a small fraction of the FP32 rate here.  FP64:
+// plain FP64.
+template <typename R>
+struct EnergyAcc {
+  double s = 0.0;
+  __device__ void add_prod(R a, R b) { s += double(a) * double(b); }
+  __device__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __device__ double value() const { return s; }
+};
+template <>
+struct EnergyAcc<float> {
+  float s = 0.0f, e = 0.0f;
+  __device__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ void add_prod(float a, float b) {
+    const float p = a * b;
+    e += fmaf(a, b, -p);
+    add(p);
+  }
+  __device__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_down_sync(0xffffffffu, s, o), oe = __shfl_down_sync(0xffffffffu, e, o);
+      add(os);
+      e += oe;
+    }
+  }
+  __device__ double value() const { return double(s) + double(e); }
+};
+
 // accumulator rows (cell order) to the caller's layouts, phi real [K][n]
 // and forces real [n][3] (either may be null), and the channel energies
-// E_c = 1/2 sum_i q_i^c phi_i^c (FP64 block sums, one atomic per block and
-// channel).  Threads walk the atoms in their original order: atom i's row
+// E_c = 1/2 sum_i q_i^c phi_i^c (EnergyAcc per thread, FP64 block sums, one
+// atomic per block and channel).  Threads walk the atoms in their original order: atom i's row
 // is the scatter's slot cell_start[cell_of[i]] + rank[i], so the writes are
 // coalesced and each row is one or two whole sectors read.
 template <typename R, int KC>
@@ -703,9 +836,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_finish(int64_t n, int K, cons
                                                           R* __restrict__ forces, double* __restrict__ energy) {
   constexpr int AW = acc_words<R, KC>();
   __shared__ double part[kRsWarps][KC];
-  double e[KC];
-#pragma unroll
-  for (int c = 0; c < KC; ++c) e[c] = 0.0;
+  EnergyAcc<R> e[KC];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t m = int64_t(cell_start[cell_of[i]]) + rank[i];
     if (!in_bounds(m, n, kBoundsRsFinish)) continue;
@@ -714,7 +845,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_finish(int64_t n, int K, cons
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
       if (c >= K) break;
-      e[c] += double(q[int64_t(c) * n + i]) * double(row[c]);
+      e[c].add_prod(q[int64_t(c) * n + i], row[c]);
       if (phi) phi[int64_t(c) * n + i] = row[c];
     }
     if (forces) {
@@ -726,8 +857,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_finish(int64_t n, int K, cons
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < KC; ++c) {
-    for (int off = 16; off > 0; off >>= 1) e[c] += __shfl_down_sync(0xffffffffu, e[c], off);
-    if (lane == 0) part[warp][c] = e[c];
+    e[c].warp_reduce();
+    if (lane == 0) part[warp][c] = e[c].value();
   }
   __syncthreads();
   if (threadIdx.x < KC && threadIdx.x < K) {
@@ -1083,14 +1214,16 @@ cudaError_t launch_bw(const RealSpaceBwArgs& a, cudaStream_t s) {
 }
 
 // backward of the cell-list path: each atom's upstream gphi (KC) and gF (3)
-// to a record in cell order, and the accumulator rows zeroed
+// to a record in cell order (the accumulator rows are cleared by a memset:
+// zero rows written at random slots would cost a second random sector per
+// atom)
 template <typename R, int KC>
 __global__ void __launch_bounds__(kRsThreads) k_rs_bw_scatter(int64_t n, int K, const R* __restrict__ g_phi,
                                                               const R* __restrict__ g_forces,
                                                               const int* __restrict__ cell_of,
                                                               const int* __restrict__ rank,
                                                               const int* __restrict__ cell_start,
-                                                              R* __restrict__ brec, R* __restrict__ acc) {
+                                                              R* __restrict__ brec) {
   constexpr int AW = acc_words<R, KC>();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t m = int64_t(cell_start[cell_of[i]]) + rank[i];
@@ -1108,14 +1241,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_bw_scatter(int64_t n, int K, 
     }
 #pragma unroll
     for (int w = 0; w < AW; w += kPerVec<R>) {
-      R x[kPerVec<R>], z[kPerVec<R>];
+      R x[kPerVec<R>];
 #pragma unroll
-      for (int e = 0; e < kPerVec<R>; ++e) {
-        x[e] = v[w + e];
-        z[e] = R(0);
-      }
+      for (int e = 0; e < kPerVec<R>; ++e) x[e] = v[w + e];
       store_vec<R>(brec + m * AW + w, x);
-      store_vec<R>(acc + m * AW + w, z);
     }
   }
 }
@@ -1157,7 +1286,16 @@ cudaError_t launch_bw_rows(const RealSpaceBwArgs& a, R* brec, R* acc, bool finis
   if (finish)                                                                                                      \
     k_rs_bw_finish<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, acc, a.cell_of, a.rank, a.cell_start, gq, gr);    \
   else                                                                                                             \
-    k_rs_bw_scatter<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, gp, gf, a.cell_of, a.rank, a.cell_start, brec, acc)
+    k_rs_bw_scatter<R, KC><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, gp, gf, a.cell_of, a.rank, a.cell_start, brec)
+  if (!finish) {
+    const int aw = channel_class(a.K) == 1 ? acc_words<R, 1>()
+                   : channel_class(a.K) == 2 ? acc_words<R, 2>()
+                   : channel_class(a.K) == 4 ? acc_words<R, 4>()
+                   : channel_class(a.K) == 8 ? acc_words<R, 8>()
+                                             : acc_words<R, kRsMaxK>();
+    const cudaError_t e = cudaMemsetAsync(acc, 0, size_t(a.n) * aw * sizeof(R), s);
+    if (e != cudaSuccess) return e;
+  }
   switch (channel_class(a.K)) {
     case 1: PSWF_RS_BW_ROWS(1); break;
     case 2: PSWF_RS_BW_ROWS(2); break;
@@ -1353,13 +1491,26 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
   }
   if ((e = cudaMemsetAsync(a.count, 0, size_t(ncell) * sizeof(int), s)) != cudaSuccess) return e;
   const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((a.n + kRsThreads - 1) / kRsThreads, 148 * 16)));
+  const int rw = record_words<R>(a.K);
+  const int aw = accumulator_words<R>(a.K);
+  R* lchk = static_cast<R*>(a.lpos);
+  R* rec = lchk + 4 * a.nmax;              // records follow the test coordinates
+  R* acc = rec + int64_t(rw) * a.nmax;     // accumulator rows follow the records
+  // FP32: the fixed-point coordinates wait between the bin and the scatter
+  // in the accumulator rows (by original index; the records then go to the
+  // backward's record area, idle during the forward, which unpack clears
+  // the rows after) or, where a record does not fit an accumulator row
+  // (one channel), in the backward's record area
+  const bool recs = std::is_same<R, float>::value && 4 + 4 * ((a.K + 3) / 4) <= aw;
+  R* brec = acc + int64_t(aw) * a.nmax;
+  int4* ufix = !std::is_same<R, float>::value ? nullptr : reinterpret_cast<int4*>(recs ? acc : brec);
   if (a.n > 0) {
     if (a.pos_dtype == 1)
       k_rs_bin<double><<<blocks, kRsThreads, 0, s>>>(a.n, static_cast<const double*>(a.pos), g, a.cell_of, a.rank,
-                                                     a.count, a.err);
+                                                     a.count, ufix, a.err);
     else
       k_rs_bin<float><<<blocks, kRsThreads, 0, s>>>(a.n, static_cast<const float*>(a.pos), g, a.cell_of, a.rank,
-                                                    a.count, a.err);
+                                                    a.count, ufix, a.err);
     ++*nlaunch;
   }
   const int nsb = (ncell + a.scan_per_block - 1) / a.scan_per_block;
@@ -1368,12 +1519,21 @@ cudaError_t real_space_run(const RealSpaceArgs& a, cudaStream_t s, int* nlaunch)
   k_scan_apply<<<nsb, kScanBlock, 0, s>>>(ncell, a.count, a.scan_sums, a.scan_per_block, a.cell_start);
   *nlaunch += 3;
   if (a.n > 0) {
-    const int rw = record_words<R>(a.K);
-    R* lchk = static_cast<R*>(a.lpos);
-    R* rec = lchk + 4 * a.nmax;   // records follow the test coordinates
-    const int aw = accumulator_words<R>(a.K);
-    R* acc = rec + int64_t(rw) * a.nmax;   // accumulator rows follow the records
-    if (a.pos_dtype == 1)
+    if constexpr (std::is_same<R, float>::value) {
+      EdgeStep es;
+      for (int k = 0; k < 9; ++k) es.ew[k] = float(g.cw[k] / double(1 << kFixBits));
+      if (recs) {
+        k_rs_scatter_rec<<<blocks, kRsThreads, 0, s>>>(a.n, a.K, aw, static_cast<const float*>(a.q), ufix, a.rank,
+                                                       a.cell_start, reinterpret_cast<float4*>(brec));
+        k_rs_unpack<<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, aw, es, brec, reinterpret_cast<float4*>(lchk), rec,
+                                                  a.perm, reinterpret_cast<float4*>(acc));
+        ++*nlaunch;
+      } else {
+        k_rs_scatter_fix<<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const float*>(a.q), es, ufix,
+                                                       a.rank, a.cell_start, reinterpret_cast<float4*>(lchk), rec,
+                                                       a.perm, reinterpret_cast<float4*>(acc), aw);
+      }
+    } else if (a.pos_dtype == 1)
       k_rs_scatter<double, R><<<blocks, kRsThreads, 0, s>>>(a.n, a.K, rw, static_cast<const double*>(a.pos),
                                                             static_cast<const R*>(a.q), g, a.cell_of, a.rank,
                                                             a.cell_start, lchk, rec, a.perm, acc, aw);
