@@ -388,12 +388,16 @@ __global__ void __launch_bounds__(kXThreads) k_irfft_x4(const float2* __restrict
   const int y0 = yc * kRows4;
   const int64_t plane = int64_t(Mz) * My;
   const int ny = min(kRows4, My - y0);
-  for (int e = threadIdx.x; e < nkx * 4 * kRows4; e += kXThreads) {
-    const int k = e / (4 * kRows4), r = e % (4 * kRows4);
-    const int c = r / kRows4, yl = r % kRows4;
-    stage[r * rs + stage_pos<N1>(k)] =
-        yl < ny ? spec[int64_t(4 * q + c) * (N / 2 + 1) * plane + int64_t(k) * plane + int64_t(z) * My + y0 + yl]
-                : make_float2(0.0f, 0.0f);
+  {
+    // a thread's line (channel c, row yl) is the same at every step
+    static_assert(kXThreads % (4 * kRows4) == 0, "whole line groups per step");
+    const int r = threadIdx.x % (4 * kRows4), c = r / kRows4, yl = r % kRows4;
+    const bool ok = yl < ny;
+    const float2* src = spec + int64_t(4 * q + c) * (N / 2 + 1) * plane + int64_t(z) * My + y0 + (ok ? yl : 0);
+    float2* dst = stage + r * rs;
+#pragma unroll 4
+    for (int k = threadIdx.x / (4 * kRows4); k < nkx; k += kXThreads / (4 * kRows4))
+      dst[stage_pos<N1>(k)] = ok ? src[int64_t(k) * plane] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
   {
