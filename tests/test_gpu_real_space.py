@@ -39,15 +39,20 @@ pytestmark = pytest.mark.gpu
 C = math.log(3.0 / 1e-5)
 
 
+@pytest.mark.parametrize("ps", [(1, 2, 3, 4, 5, 6), (1,), (6, 1, 4, 2)])
 @pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, TOL_FP32)])
-def test_real_space_matches_oracle(precision, tol):
+def test_real_space_matches_oracle(precision, tol, ps):
+    """Cell list (3 x 3 x 3 at r_c = 4), atoms up to two boxes outside the
+    cell.  One channel takes the FP32 plans' direct scatter (its record does
+    not fit an accumulator row), two to sixteen the record scatter and
+    unpack."""
     import torch
     from oracle.realspace import real_space
     from paper_2606_06617_b300 import lr
     dev = torch.device("cuda", 0)
     box = (13.0, 14.5, 12.5)
     r_c = 4.0
-    s = wl.random_system(300, box, (1, 2, 3, 4, 5, 6), seed=41, neutral=False)
+    s = wl.random_system(300, box, ps, seed=41, neutral=False)
     s.pos = s.pos + np.random.default_rng(2).integers(-2, 3, size=s.pos.shape) * np.asarray(box)
     plan = lr.Plan(box, s.n, s.ps, r_c, c=C, P=6, grid=(28, 30, 26), precision=precision,
                    flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
