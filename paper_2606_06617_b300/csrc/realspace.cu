@@ -198,12 +198,23 @@ __device__ inline void add_row(R* row, const R (&p)[KC], R fx, R fy, R fz, int K
 // cell of a wrapped position (count and rank within the cell).  With ufix
 // (FP32 plans) also the fixed-point cell-local coordinates and the cell,
 // ufix[i] = (u_x, u_y, u_z, cell), so that the scatter needs no FP64
-// arithmetic (FP64 runs at a small fraction of the FP32 rate here).  Boxes
-// take the diagonal of H^-1 alone (the off-diagonal terms are exact zeros).
+// arithmetic: the position along each lattice vector, in units of the
+// list cell's edge / 2^kFixBits, is rounded once to a 64-bit integer W
+// (for a box one FP64 product r_d (n_c[d] 2^kFixBits / L_d)), whose high
+// bits give the cell (wrapped mod n_c) and whose low kFixBits bits the
+// coordinate; FP64 runs at a small fraction of the FP32 rate here.  FP64
+// plans: fractional coordinates s = r H^-1 wrapped by floor, the cell from
+// s n_c (boxes take the diagonal of H^-1 alone: the off-diagonal terms are
+// exact zeros).
 template <typename PosT>
 __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom g, int* __restrict__ cell_of,
                          int* __restrict__ rank, int* __restrict__ count, int4* __restrict__ ufix,
                          int* __restrict__ err) {
+  double scale[3], abox[3];   // n_c 2^kFixBits, and for boxes times the diagonal of H^-1
+  for (int d = 0; d < 3; ++d) {
+    scale[d] = double(g.nc[d]) * double(1 << kFixBits);
+    abox[d] = g.hinv[4 * d] * scale[d];
+  }
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     double r[3];
     for (int d = 0; d < 3; ++d) {
@@ -213,29 +224,34 @@ __global__ void k_rs_bin(int64_t n, const PosT* __restrict__ pos, RealSpaceGeom 
         r[d] = 0.0;
       }
     }
-    int ci[3];
-    double fs[3];
-    for (int d = 0; d < 3; ++d) {
-      const double s = g.tric ? r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d]
-                              : r[d] * g.hinv[4 * d];   // in cells
-      fs[d] = s - floor(s);                             // [0, 1]
-      const int c = int(fs[d] * g.nc[d]);
-      ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+    int ci[3], u[3];
+    if (ufix) {
+      for (int d = 0; d < 3; ++d) {
+        const double v = g.tric ? (r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d]) * scale[d]
+                                : r[d] * abox[d];
+        const long long w = __double2ll_rn(v);
+        const long long ct = w >> kFixBits;   // floor(w / 2^kFixBits)
+        u[d] = int(w & ((1LL << kFixBits) - 1));
+        int c = int(ct);
+        if (ct < 0 || ct >= g.nc[d]) {
+          c = int(ct % g.nc[d]);
+          c += c < 0 ? g.nc[d] : 0;
+        }
+        ci[d] = c;
+      }
+    } else {
+      for (int d = 0; d < 3; ++d) {
+        const double sv = g.tric ? r[0] * g.hinv[d] + r[1] * g.hinv[3 + d] + r[2] * g.hinv[6 + d]
+                                 : r[d] * g.hinv[4 * d];   // in box fractions
+        const double fs = sv - floor(sv);                  // [0, 1]
+        const int c = int(fs * g.nc[d]);
+        ci[d] = c < 0 ? 0 : (c >= g.nc[d] ? g.nc[d] - 1 : c);
+      }
     }
     const int cell = (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
     cell_of[i] = cell;
     rank[i] = atomicAdd(count + cell, 1);
-    if (ufix) {
-      // rint((fs n_c - c) 2^kFixBits) clamped to [0, 2^kFixBits]: fs n_c - c
-      // is exact and the scaling by 2^kFixBits too, so this equals the
-      // rounded fs n_c 2^kFixBits less c 2^kFixBits, taken in integers
-      int u[3];
-      for (int d = 0; d < 3; ++d) {
-        const long long w = __double2ll_rn(fs[d] * g.nc[d] * double(1 << kFixBits)) - (static_cast<long long>(ci[d]) << kFixBits);
-        u[d] = int(w < 0 ? 0 : (w > (1LL << kFixBits) ? (1LL << kFixBits) : w));
-      }
-      ufix[i] = make_int4(u[0], u[1], u[2], cell);
-    }
+    if (ufix) ufix[i] = make_int4(u[0], u[1], u[2], cell);
   }
 }
 
