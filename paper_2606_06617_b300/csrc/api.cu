@@ -231,13 +231,13 @@ __global__ void k_tile_scale(int ntl, int K, int64_t nmax, const int* __restrict
 
 __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
                                    double* __restrict__ charges) {
-  // one warp per (structure, channel): lanes stride over the block partials
-  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  // one block per (structure, channel): threads stride over the block
+  // partials (several loads in flight each), then warp and block sums
+  const int g = blockIdx.x;
   if (g >= B * K) return;
   const int s = g / K, c = g - s * K;
   double a = 0.0, b = 0.0;
-  for (int i = lane; i < nblk; i += 32) {
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
     const size_t o = ((size_t(s) * nblk + i) * K + c) * 2;
     a += part[o];
     b += part[o + 1];
@@ -246,9 +246,21 @@ __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restr
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
   }
+  __shared__ double sh[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    charges[2 * g] = a;
-    charges[2 * g + 1] = b;
+    sh[0][wid] = a;
+    sh[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      x += sh[0][w];
+      y += sh[1][w];
+    }
+    charges[2 * g] = x;
+    charges[2 * g + 1] = y;
   }
 }
 
@@ -991,7 +1003,7 @@ int charge_sums(pswf_plan p, const void* vals, double* out) {
                                                                           p->soff, p->qpart);
   int rc = launch_check(p, "k_charge_partials_seg");
   if (rc) return rc;
-  k_charge_final_seg<<<(p->nrun * K + 7) / 8, 256, 0, p->stream>>>(p->nqb, K, p->nrun, p->qpart, out);
+  k_charge_final_seg<<<p->nrun * K, 256, 0, p->stream>>>(p->nqb, K, p->nrun, p->qpart, out);
   return launch_check(p, "k_charge_final_seg");
 }
 
@@ -1487,7 +1499,7 @@ int finish_create(pswf_plan pl, int64_t n_max, int b, const pswf_opts* opts, voi
   // multiplier blocks per channel: about 8 half-spectrum elements a thread
   pl->eblk = int(std::max<int64_t>(
       1, std::min<int64_t>(kEnergyBlocks, int64_t(h.M[1]) * h.M[2] * (h.M[0] / 2 + 1) / (8 * kThreads))));
-  pl->scan_per_block = 16384;
+  pl->scan_per_block = 2048;   // two tiles per thread: short strips, several blocks in flight
   pl->scan_blocks = (pl->ntiles + pl->scan_per_block - 1) / pl->scan_per_block;
   pl->grid_elems = int64_t(b) * h.K * h.M[2] * h.M[1] * pl->geo.Mxp;
   int rc = make_fft(pl);

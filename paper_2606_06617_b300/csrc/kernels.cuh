@@ -444,7 +444,7 @@ __global__ void k_scan_sums(int nb, int* __restrict__ sums);
 __global__ void k_scan_apply(int n, const int* __restrict__ in, const int* __restrict__ sums, int per_block,
                              int* __restrict__ out);
 // k_charge_final_seg: charges[g][0] = Q_net, charges[g][1] = Q_self from the
-// k_charge_partials_seg partials, one thread per (structure, channel).
+// k_charge_partials_seg partials, one block per (structure, channel).
 __global__ void k_charge_final_seg(int nblk, int K, int B, const double* __restrict__ part,
                                    double* __restrict__ charges);
 // One block per structure: energy[s][c] = sum of the multiplier partials of
