@@ -440,7 +440,27 @@ def run_serving(n_req: int = 4096, rate: float = 2000.0, n_plain: int = 160, n_r
     per grid bucket, created before timing (first n_resident requests), each
     at the same arrival times and as a burst.  The speed-up is the server's
     burst throughput on the same n_resident requests over the resident
-    path's.  Latency: arrival (submit) to results ready."""
+    path's.  Latency: arrival (submit) to results ready.
+
+    Objects left in reference cycles by earlier work (the training step's
+    autograd graph holds plans) are collected first and Python's cycle
+    collector stays off while the server is measured: a plan destroyed in
+    the middle of the stream frees device memory, which synchronizes the
+    device and held the stream for 25-55 ms (p99 30-57 ms against 2-6 ms)."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        return _run_serving(n_req, rate, n_plain, n_resident, seed)
+    finally:
+        if gc_was_enabled:
+            gc.enable()
+
+
+def _run_serving(n_req, rate, n_plain, n_resident, seed) -> dict:
     import torch
     from paper_2606_06617_b300 import lr
     from paper_2606_06617_b300 import workloads as wl

@@ -359,7 +359,10 @@ int pswf_compute_host(pswf_plan plan, int64_t n, const double* pos, const double
 int pswf_compute_host_real(pswf_plan plan, int64_t n, const double* pos, const void* q,
                            double* energy, void* phi, void* forces);
 
-/* Releases everything the plan owns (not a caller-attached workspace). */
+/* Releases everything the plan owns (not a caller-attached workspace).
+ * Freeing device memory waits for all outstanding work on the device, so a
+ * plan destroyed while a server runs stalls the server's streams until
+ * then: destroy plans outside latency-critical windows. */
 void pswf_plan_destroy(pswf_plan plan);
 
 /* Human-readable name of a status code (static string). */
