@@ -69,6 +69,41 @@ def test_real_space_matches_oracle(precision, tol, ps):
     assert abs(e[-1] - e[:-1].sum()) <= 1e-12 * abs(e[:-1]).sum()
 
 
+@pytest.mark.parametrize("precision,tol,reach", [(1, 1e-10, 50), (0, TOL_FP32, 5000)])
+def test_real_space_distant_images(precision, tol, reach):
+    """Atoms moved by up to +-reach box lengths, others exactly on the cell's
+    faces or just below zero: the binning wraps them (FP32 plans form the
+    fixed-point cell coordinates as one rounded integer and take the cell
+    modulo n_c), and the results equal the oracle's on the unmoved atoms.
+    (Moving an atom by 5000 boxes already rounds its double coordinates by
+    1.5e-11 A, beyond the FP64 bound's reach on close pairs; 50 boxes round
+    them by 1e-13 A.)"""
+    import torch
+    from oracle.realspace import real_space
+    from paper_2606_06617_b300 import lr
+    dev = torch.device("cuda", 0)
+    box = (13.0, 14.5, 12.5)
+    r_c = 4.0
+    s = wl.random_system(300, box, (1, 4), seed=43, neutral=False)
+    rng = np.random.default_rng(5)
+    base = s.pos.copy()
+    base[:3] = [[0.0, 0.0, 0.0], [box[0], 7.0, 3.0], [5.0, -1e-12, box[2]]]
+    moved = base + rng.integers(-reach, reach + 1, size=base.shape) * np.asarray(box)
+    moved[:3] = base[:3]
+    plan = lr.Plan(box, s.n, s.ps, r_c, c=C, P=6, grid=(28, 30, 26), precision=precision,
+                   flags=lr.PSWF_FLAG_REAL_SPACE, device=dev)
+    e, phi, f = plan.real_space(torch.tensor(moved, device=dev), torch.tensor(s.q, device=dev))
+    plan.sync()
+    e, phi, f = e.cpu().numpy(), phi.cpu().double().numpy(), f.cpu().double().numpy()
+    F = np.zeros((s.n, 3))
+    for c, p in enumerate(s.ps):
+        o = real_space(base, s.q[c], box, p, C, r_c)
+        assert abs(e[c] - o["E"]) <= tol * abs(o["E"]), (c, e[c], o["E"])
+        assert rel_rms(phi[c], o["phi"]) <= tol, (c, rel_rms(phi[c], o["phi"]))
+        F += o["F"]
+    assert rel_rms(f, F) <= tol, rel_rms(f, F)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_gpu_total_matches_ewald(precision):
     """Ionic melt parameters (r_c = 7, c = log(3e5), P = 7, h = 0.911 A) on a
