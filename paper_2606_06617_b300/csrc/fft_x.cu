@@ -474,9 +474,11 @@ __global__ void __launch_bounds__(256) k_fft_z(float2* __restrict__ spec, int My
 // (zero outside |k| < k_c and at k = 0), adding w_m G |rho-hat|^2 / 2 to the
 // energy (kx = 0 counted once) and, with vpart, the virial's log-derivative
 // sums; then transforms it back and stores it.  Energy partials per block in
-// FP64 (part[c][blocks]).
+// FP64 (part[c][blocks]).  Three CTAs per SM (at most 80 registers): 0.315
+// against 0.346 ms per 384^3 step at the 64 registers, with spills, that
+// the compiler took for four.
 template <int N1>
-__global__ void __launch_bounds__(256) k_mult_y(float2* __restrict__ spec, MultParams mp, int64_t chan,
+__global__ void __launch_bounds__(256, 3) k_mult_y(float2* __restrict__ spec, MultParams mp, int64_t chan,
                                                 const int* __restrict__ lines, int nlines,
                                                 const int* __restrict__ pch, const double* __restrict__ scale,
                                                 const double* __restrict__ bmat, const float* __restrict__ coef,
