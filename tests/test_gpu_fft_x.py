@@ -34,7 +34,7 @@ def _full_transform(s, info, M):
     import torch
     from paper_2606_06617_b300 import lr
     dev = torch.device("cuda", 0)
-    bp = lr.BatchPlan(tuple(s.box), 2, s.n, 2, s.ps, R_C, c=C_TOL, c_w=info["c_w"], P=info["P"], grid=M,
+    bp = lr.BatchPlan(tuple(s.box), 2, s.n, len(s.ps), s.ps, R_C, c=C_TOL, c_w=info["c_w"], P=info["P"], grid=M,
                       device=dev)
     assert bp.info["transform"] == lr.PSWF_TRANSFORM_FULL
     bp.set_points(np.array([s.box]), np.array([s.ps], dtype=np.int32), np.array([0, s.n], dtype=np.int64),
@@ -135,3 +135,31 @@ def test_pruned_x_and_cufft_x_agree():
     assert g32["info"]["nkx"] == g64["info"]["nkx"]
     assert rel_rms(g32["phi"], g64["phi"]) <= TOL_FP32
     assert rel_rms(g32["F"], g64["F"]) <= TOL_FP32
+
+
+@pytest.mark.parametrize("n1", [(2, 2, 3), (5, 2, 2), (7, 3, 2), (15, 2, 2), (16, 2, 3)])
+def test_quadruple_inverse_x_matches_oracle(n1):
+    """Four channels (p = 1, 2, 4, 6) on own-transform grids: FP32 plans
+    with K a multiple of 4, P <= 8 and no backward end the inverse
+    transform with the pass that writes Psi as channel quadruples (one y
+    row per warp, two complex rows per warp), which the gather reads as
+    16-byte words; every row-length class, ragged y rows included."""
+    from paper_2606_06617_b300 import lr
+    M = tuple(32 * k for k in n1)
+    h = (0.3, 0.42, 0.45)
+    box = tuple(hd * m for hd, m in zip(h, M))
+    nat = int(0.1 * box[0] * box[1] * box[2])
+    s = wl.random_system(nat, box, (1, 2, 4, 6), seed=300 + sum(n1), neutral=bool(n1[0] % 2))
+    cw = window_cw(s.box, M, 6, C_TOL, R_C)
+    g = run_gpu(s, R_C, 6, M, C_TOL, cw, precision=0)
+    info = g["info"]
+    assert info["transform"] == lr.PSWF_TRANSFORM_OWN, info
+    o = run_oracle(s, R_C, 6, M, C_TOL, cw)
+    e_f, phi_f, f_f = _full_transform(s, info, M)
+    for c in range(4):
+        ref = abs(o["E_ch"][c])
+        bound = _bound(abs(e_f[c] - o["E_ch"][c]) / ref)
+        assert abs(g["E_ch"][c] - o["E_ch"][c]) <= bound * ref, (c, g["E_ch"], o["E_ch"], e_f)
+    err_phi, err_f = rel_rms(g["phi"], o["phi"]), rel_rms(g["F"], o["F"])
+    assert err_phi <= _bound(rel_rms(phi_f, o["phi"])), (err_phi, rel_rms(phi_f, o["phi"]))
+    assert err_f <= _bound(rel_rms(f_f, o["F"])), (err_f, rel_rms(f_f, o["F"]))
