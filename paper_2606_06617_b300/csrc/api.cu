@@ -474,6 +474,11 @@ struct pswf_plan_s {
   size_t fft_work_bytes = 0;
   // host staging for pswf_compute_host
   double* h_pin = nullptr;
+  // pswf_compute_host: the charges' copy on a second stream after the
+  // positions' (ev_pos), so that the bin and the scan run meanwhile; while
+  // set via q_ready, set_points waits for it before reading the charges
+  cudaStream_t q_stream = nullptr;
+  cudaEvent_t ev_pos = nullptr, ev_q = nullptr, q_ready = nullptr;
   int64_t h_pin_elems = 0;
   void* d_stage = nullptr;
   int64_t d_stage_bytes = 0;
@@ -525,6 +530,14 @@ struct StageScope {
   StageScope(pswf_plan p_, int stage_) : p(p_), stage(stage_), outer(p_->cur_stage) {
     p->cur_stage = stage;
     if (p->prof_on) {
+      a = take_event(p);
+      cudaEventRecord(a, p->stream);
+    }
+  }
+  // the stage's time starts here instead (work before it overlaps another phase)
+  void restart() {
+    if (a) {
+      p->pool.push_back(a);
       a = take_event(p);
       cudaEventRecord(a, p->stream);
     }
@@ -1046,6 +1059,13 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
   k_scan_apply<<<nsb, kScanBlock, 0, s>>>(ntl, p->tile_count, p->scan_sums, p->scan_per_block,
                                                       p->tile_start);
   if ((rc = launch_check(p, "k_scan_apply"))) return rc;
+  // the charges are read from here on; when their copy runs on another
+  // stream, the binning and the scan above overlap it and the stage's time
+  // starts once they have arrived
+  if (p->q_ready) {
+    if ((rc = cuda_check(p, cudaStreamWaitEvent(s, p->q_ready, 0), "wait for the charges"))) return rc;
+    scope.restart();
+  }
   const int nchunk4 = (p->host.K + 3) / 4;
   if (sizeof(R) == 4 && p->n_max * (32 + 16 * int64_t(nchunk4)) <= p->grid_elems * int64_t(sizeof(R))) {
     // records in slot order first (in the grid, unused until execute), then unpacked
@@ -1937,17 +1957,37 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   if (pos_direct && n > 0 &&
       (rc = cuda_check(pl, cudaMemcpyAsync(d_pos, pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos")))
     return rc;
+  // the charges' stream: with both arrays page-locked, their copy (and the
+  // rounding of float64 charges) runs on it after the positions' copy, and
+  // set_points waits for it only before its first kernel that reads them
+  cudaStream_t sq = s;
+  if (pos_direct && q_direct && n > 0) {
+    if (!pl->q_stream &&
+        ((rc = cuda_check(pl, cudaStreamCreateWithFlags(&pl->q_stream, cudaStreamNonBlocking), "charge stream")) ||
+         (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_pos, cudaEventDisableTiming), "copy event")) ||
+         (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_q, cudaEventDisableTiming), "copy event"))))
+      return rc;
+    if ((rc = cuda_check(pl, cudaEventRecord(pl->ev_pos, s), "record positions copied")) ||
+        (rc = cuda_check(pl, cudaStreamWaitEvent(pl->q_stream, pl->ev_pos, 0), "order the charges' copy")))
+      return rc;
+    sq = pl->q_stream;
+  }
   if (q_direct && n > 0) {
     // pinned charges: copied as double, rounded to FP32 on the device
     if ((rc = cuda_check(pl, cudaMemcpyAsync(narrow ? static_cast<void*>(d_q64) : static_cast<void*>(d_q), q,
-                                             size_t(K * n * qs), cudaMemcpyHostToDevice, s), "h2d q")))
+                                             size_t(K * n * qs), cudaMemcpyHostToDevice, sq), "h2d q")))
       return rc;
     if (narrow) {
       const int nb = int(std::min<int64_t>((K * n + kThreads - 1) / kThreads, 148 * 16));
-      k_narrow<<<nb, kThreads, 0, s>>>(K * n, d_q64, reinterpret_cast<float*>(d_q));
+      k_narrow<<<nb, kThreads, 0, sq>>>(K * n, d_q64, reinterpret_cast<float*>(d_q));
       if ((rc = launch_check(pl, "k_narrow"))) return rc;
       ++pl->launches[PSWF_STAGE_OTHER];
     }
+  }
+  cudaEvent_t q_done = nullptr;
+  if (sq != s) {
+    if ((rc = cuda_check(pl, cudaEventRecord(pl->ev_q, sq), "record charges copied"))) return rc;
+    q_done = pl->ev_q;
   }
   // Inputs in chunks of atoms: the host threads fill chunk i of the pinned
   // staging (q rounded to the plan's precision; positions only when the
@@ -1982,10 +2022,13 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   }
   if (ev_in0) {
     cudaEvent_t b = take_event(pl);
-    cudaEventRecord(b, s);
+    cudaEventRecord(b, sq);   // the end of the last copy (the charges' stream when it has its own)
     pl->recs.push_back({PSWF_STAGE_H2D, ev_in0, b});
   }
-  if ((rc = pswf_set_points(pl, n, d_pos, 1, d_q))) return rc;
+  pl->q_ready = q_done;
+  rc = pswf_set_points(pl, n, d_pos, 1, d_q);
+  pl->q_ready = nullptr;
+  if (rc) return rc;
   if ((rc = pswf_execute(pl, d_e, phi ? d_phi : nullptr, forces ? d_f : nullptr))) return rc;
   cudaEvent_t ev_out0 = nullptr;
   if (pl->prof_on) {
@@ -2099,6 +2142,9 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (pl->h_pin) cudaFreeHost(pl->h_pin);
   if (pl->h_stab) cudaFreeHost(pl->h_stab);
   if (pl->stab_ev) cudaEventDestroy(pl->stab_ev);
+  if (pl->ev_pos) cudaEventDestroy(pl->ev_pos);
+  if (pl->ev_q) cudaEventDestroy(pl->ev_q);
+  if (pl->q_stream) cudaStreamDestroy(pl->q_stream);
   for (auto& r : pl->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
