@@ -150,7 +150,8 @@ __global__ void k_energy_final(int K, int nblk, const double* __restrict__ part,
 // bytes.  Here each atom's sorted slot instead receives two aligned records
 // (rec [n_max][2] float4: t, original index; packed start cell; and per
 // chunk of four channels qrec [nchunk][n_max] float4), placed in a scratch
-// area (the grid, idle during set_points), and k_unpack_rec then writes the
+// area (the spectrum buffer, else the grid: both idle during set_points;
+// record_buffer), and k_unpack_rec then writes the
 // sorted arrays in slot order with coalesced stores.
 __global__ void k_scatter_rec(int64_t nmax, const float* __restrict__ q, Geometry g, const int* __restrict__ soff,
                               const int* __restrict__ tile_of, const int* __restrict__ rank,
@@ -478,7 +479,8 @@ struct pswf_plan_s {
   // positions' (ev_pos), so that the bin and the scan run meanwhile; while
   // set via q_ready, set_points waits for it before reading the charges
   cudaStream_t q_stream = nullptr;
-  cudaEvent_t ev_pos = nullptr, ev_q = nullptr, q_ready = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_pos = nullptr, ev_q = nullptr, q_ready = nullptr;
+  bool grid_zeroed = false;   // the grid was cleared for the next spread (pswf_compute_host)
   int64_t h_pin_elems = 0;
   void* d_stage = nullptr;
   int64_t d_stage_bytes = 0;
@@ -554,6 +556,24 @@ struct StageScope {
 
 // Grid elements of the slots processed per launch.
 int64_t run_grid_elems(pswf_plan p) { return p->grid_elems / p->B * p->nrun; }
+
+// Bytes of the spectrum buffer (pruned and own-transform plans; 0 without one).
+int64_t spec_bytes(pswf_plan p) {
+  return p->spec ? int64_t(p->host.K) * (p->host.M[0] / 2 + 1) * p->host.M[1] * p->host.M[2] * 2 *
+                       int64_t(p->real_size)
+                 : 0;
+}
+
+// Where the FP32 set_points parks its per-atom records before unpacking
+// them: the spectrum buffer when it holds them, else the grid (both idle
+// until execute), else nowhere (the direct scatter).
+void* record_buffer(pswf_plan p) {
+  if (p->real_size != 4) return nullptr;
+  const int64_t bytes = p->n_max * (32 + 16 * int64_t((p->host.K + 3) / 4));
+  if (p->spec && bytes <= spec_bytes(p)) return p->spec;
+  if (bytes <= p->grid_elems * int64_t(p->real_size)) return p->grid;
+  return nullptr;
+}
 
 // Smallest planned launch size holding b structures.
 int run_size(pswf_plan p, int b) {
@@ -833,9 +853,7 @@ LaunchCtx make_ctx(pswf_plan p) {
   c.tile_of = p->tile_of;
   c.rank = p->rank;
   c.out_scratch = p->spec;
-  c.out_scratch_bytes = p->spec ? int64_t(p->host.K) * (p->host.M[0] / 2 + 1) * p->host.M[1] * p->host.M[2] * 2 *
-                                      int64_t(p->real_size)
-                                : 0;
+  c.out_scratch_bytes = spec_bytes(p);
   c.grid = p->grid;
   c.zero_coef = p->zero_coef;
   c.charges = p->charges;
@@ -1066,10 +1084,11 @@ int do_set_points(pswf_plan p, int64_t n, const void* pos, int pos_dtype, const 
     if ((rc = cuda_check(p, cudaStreamWaitEvent(s, p->q_ready, 0), "wait for the charges"))) return rc;
     scope.restart();
   }
-  const int nchunk4 = (p->host.K + 3) / 4;
-  if (sizeof(R) == 4 && p->n_max * (32 + 16 * int64_t(nchunk4)) <= p->grid_elems * int64_t(sizeof(R))) {
-    // records in slot order first (in the grid, unused until execute), then unpacked
-    float4* rec = static_cast<float4*>(p->grid);
+  void* recbuf = record_buffer(p);
+  if (recbuf == p->grid) p->grid_zeroed = false;
+  if (recbuf) {
+    // records in slot order first (in a buffer unused until execute), then unpacked
+    float4* rec = static_cast<float4*>(recbuf);
     float4* qrec = rec + 2 * p->n_max;
     k_scatter_rec<<<blocks, kThreads, 0, s>>>(p->n_max, static_cast<const float*>(q), geo, p->soff, p->tile_of,
                                               p->rank, p->tile_start, static_cast<const float*>(p->tmp_t),
@@ -1103,7 +1122,10 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   const LaunchCtx ctx = make_ctx(p);
   {
     StageScope scope(p, PSWF_STAGE_SPREAD);
-    if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * sizeof(R), s), "clear grid")))
+    if (p->grid_zeroed)
+      p->grid_zeroed = false;   // cleared while the inputs were copied
+    else if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * sizeof(R), s),
+                              "clear grid")))
       return rc;
     if (p->n > 0 || p->batch) {
       int nl = 0;
@@ -1954,6 +1976,14 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   char* h_phi = reinterpret_cast<char*>(h_e + K + 1);
   char* h_f = h_phi + K * n * rs;
   cudaStream_t s = pl->stream;
+  const bool split = pos_direct && q_direct && n > 0;   // the charges' copy on its own stream
+  if (split && !pl->q_stream &&
+      ((rc = cuda_check(pl, cudaStreamCreateWithFlags(&pl->q_stream, cudaStreamNonBlocking), "charge stream")) ||
+       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming), "copy event")) ||
+       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_pos, cudaEventDisableTiming), "copy event")) ||
+       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_q, cudaEventDisableTiming), "copy event"))))
+    return rc;
+  if (split && (rc = cuda_check(pl, cudaEventRecord(pl->ev_in, s), "record call start"))) return rc;
   if (pos_direct && n > 0 &&
       (rc = cuda_check(pl, cudaMemcpyAsync(d_pos, pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos")))
     return rc;
@@ -1961,12 +1991,17 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   // rounding of float64 charges) runs on it after the positions' copy, and
   // set_points waits for it only before its first kernel that reads them
   cudaStream_t sq = s;
-  if (pos_direct && q_direct && n > 0) {
-    if (!pl->q_stream &&
-        ((rc = cuda_check(pl, cudaStreamCreateWithFlags(&pl->q_stream, cudaStreamNonBlocking), "charge stream")) ||
-         (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_pos, cudaEventDisableTiming), "copy event")) ||
-         (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_q, cudaEventDisableTiming), "copy event"))))
-      return rc;
+  if (split) {
+    // the grid is cleared for the spread while the positions are copied,
+    // unless set_points parks its records there (after all earlier work on
+    // the plan's stream, ev_in)
+    if (record_buffer(pl) != pl->grid) {
+      if ((rc = cuda_check(pl, cudaStreamWaitEvent(pl->q_stream, pl->ev_in, 0), "order the grid clearing")) ||
+          (rc = cuda_check(pl, cudaMemsetAsync(pl->grid, 0, size_t(run_grid_elems(pl)) * size_t(rs), pl->q_stream),
+                           "clear grid")))
+        return rc;
+      pl->grid_zeroed = true;
+    }
     if ((rc = cuda_check(pl, cudaEventRecord(pl->ev_pos, s), "record positions copied")) ||
         (rc = cuda_check(pl, cudaStreamWaitEvent(pl->q_stream, pl->ev_pos, 0), "order the charges' copy")))
       return rc;
@@ -2142,6 +2177,7 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (pl->h_pin) cudaFreeHost(pl->h_pin);
   if (pl->h_stab) cudaFreeHost(pl->h_stab);
   if (pl->stab_ev) cudaEventDestroy(pl->stab_ev);
+  if (pl->ev_in) cudaEventDestroy(pl->ev_in);
   if (pl->ev_pos) cudaEventDestroy(pl->ev_pos);
   if (pl->ev_q) cudaEventDestroy(pl->ev_q);
   if (pl->q_stream) cudaStreamDestroy(pl->q_stream);
