@@ -480,7 +480,12 @@ struct pswf_plan_s {
   // set via q_ready, set_points waits for it before reading the charges
   cudaStream_t q_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_pos = nullptr, ev_q = nullptr, q_ready = nullptr;
-  bool grid_zeroed = false;   // the grid was cleared for the next spread (pswf_compute_host)
+  // the grid is being cleared for the next spread on the side stream (by
+  // pswf_compute_host, under the positions' copy), done at ev_clear.
+  // Clearing it there during set_points instead gained nothing: the sort's
+  // kernels slowed by what the spread saved (HBM shared by both)
+  bool grid_zeroed = false;
+  cudaEvent_t ev_clear = nullptr;
   int64_t h_pin_elems = 0;
   void* d_stage = nullptr;
   int64_t d_stage_bytes = 0;
@@ -562,6 +567,33 @@ int64_t spec_bytes(pswf_plan p) {
   return p->spec ? int64_t(p->host.K) * (p->host.M[0] / 2 + 1) * p->host.M[1] * p->host.M[2] * 2 *
                        int64_t(p->real_size)
                  : 0;
+}
+
+// The side stream and its events (created on first use).
+int ensure_side_stream(pswf_plan p) {
+  if (p->q_stream) return PSWF_OK;
+  int rc;
+  if ((rc = cuda_check(p, cudaStreamCreateWithFlags(&p->q_stream, cudaStreamNonBlocking), "side stream")) ||
+      (rc = cuda_check(p, cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming), "side event")) ||
+      (rc = cuda_check(p, cudaEventCreateWithFlags(&p->ev_pos, cudaEventDisableTiming), "side event")) ||
+      (rc = cuda_check(p, cudaEventCreateWithFlags(&p->ev_q, cudaEventDisableTiming), "side event")) ||
+      (rc = cuda_check(p, cudaEventCreateWithFlags(&p->ev_clear, cudaEventDisableTiming), "side event")))
+    return rc;
+  return PSWF_OK;
+}
+
+// Clears the grid for the next spread on the side stream, after all work
+// enqueued so far on the plan's stream; execute waits for ev_clear.
+int clear_grid_aside(pswf_plan p) {
+  int rc;
+  if ((rc = ensure_side_stream(p)) || (rc = cuda_check(p, cudaEventRecord(p->ev_in, p->stream), "side event")) ||
+      (rc = cuda_check(p, cudaStreamWaitEvent(p->q_stream, p->ev_in, 0), "order the grid clearing")) ||
+      (rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * size_t(p->real_size), p->q_stream),
+                       "clear grid")) ||
+      (rc = cuda_check(p, cudaEventRecord(p->ev_clear, p->q_stream), "side event")))
+    return rc;
+  p->grid_zeroed = true;
+  return PSWF_OK;
 }
 
 // Where the FP32 set_points parks its per-atom records before unpacking
@@ -1122,9 +1154,10 @@ int do_execute(pswf_plan p, double* energy, void* phi, void* forces) {
   const LaunchCtx ctx = make_ctx(p);
   {
     StageScope scope(p, PSWF_STAGE_SPREAD);
-    if (p->grid_zeroed)
-      p->grid_zeroed = false;   // cleared while the inputs were copied
-    else if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * sizeof(R), s),
+    if (p->grid_zeroed) {   // cleared on the side stream meanwhile
+      p->grid_zeroed = false;
+      if ((rc = cuda_check(p, cudaStreamWaitEvent(s, p->ev_clear, 0), "wait for the grid clearing"))) return rc;
+    } else if ((rc = cuda_check(p, cudaMemsetAsync(p->grid, 0, size_t(run_grid_elems(p)) * sizeof(R), s),
                               "clear grid")))
       return rc;
     if (p->n > 0 || p->batch) {
@@ -1977,13 +2010,10 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   char* h_f = h_phi + K * n * rs;
   cudaStream_t s = pl->stream;
   const bool split = pos_direct && q_direct && n > 0;   // the charges' copy on its own stream
-  if (split && !pl->q_stream &&
-      ((rc = cuda_check(pl, cudaStreamCreateWithFlags(&pl->q_stream, cudaStreamNonBlocking), "charge stream")) ||
-       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming), "copy event")) ||
-       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_pos, cudaEventDisableTiming), "copy event")) ||
-       (rc = cuda_check(pl, cudaEventCreateWithFlags(&pl->ev_q, cudaEventDisableTiming), "copy event"))))
-    return rc;
-  if (split && (rc = cuda_check(pl, cudaEventRecord(pl->ev_in, s), "record call start"))) return rc;
+  if (split && (rc = ensure_side_stream(pl))) return rc;
+  // the grid is cleared for the spread while the positions are copied,
+  // unless set_points parks its records there
+  if (split && record_buffer(pl) != pl->grid && (rc = clear_grid_aside(pl))) return rc;
   if (pos_direct && n > 0 &&
       (rc = cuda_check(pl, cudaMemcpyAsync(d_pos, pos, size_t(n) * 24, cudaMemcpyHostToDevice, s), "h2d pos")))
     return rc;
@@ -1992,16 +2022,6 @@ int compute_host(pswf_plan pl, int64_t n, const double* pos, const void* qv, dou
   // set_points waits for it only before its first kernel that reads them
   cudaStream_t sq = s;
   if (split) {
-    // the grid is cleared for the spread while the positions are copied,
-    // unless set_points parks its records there (after all earlier work on
-    // the plan's stream, ev_in)
-    if (record_buffer(pl) != pl->grid) {
-      if ((rc = cuda_check(pl, cudaStreamWaitEvent(pl->q_stream, pl->ev_in, 0), "order the grid clearing")) ||
-          (rc = cuda_check(pl, cudaMemsetAsync(pl->grid, 0, size_t(run_grid_elems(pl)) * size_t(rs), pl->q_stream),
-                           "clear grid")))
-        return rc;
-      pl->grid_zeroed = true;
-    }
     if ((rc = cuda_check(pl, cudaEventRecord(pl->ev_pos, s), "record positions copied")) ||
         (rc = cuda_check(pl, cudaStreamWaitEvent(pl->q_stream, pl->ev_pos, 0), "order the charges' copy")))
       return rc;
@@ -2178,6 +2198,7 @@ void pswf_plan_destroy(pswf_plan pl) {
   if (pl->h_stab) cudaFreeHost(pl->h_stab);
   if (pl->stab_ev) cudaEventDestroy(pl->stab_ev);
   if (pl->ev_in) cudaEventDestroy(pl->ev_in);
+  if (pl->ev_clear) cudaEventDestroy(pl->ev_clear);
   if (pl->ev_pos) cudaEventDestroy(pl->ev_pos);
   if (pl->ev_q) cudaEventDestroy(pl->ev_q);
   if (pl->q_stream) cudaStreamDestroy(pl->q_stream);
